@@ -1,0 +1,153 @@
+"""Pins for the oracle's nearest-neighbour Tm (Section "Implementations": AHv2's C Tm_NN; Section
+"Primer degeneracy": Tm over primer variants).
+
+* hand-worked sums (tests/golden/tm_worked.md) pin which terms apply: terminal mismatches, the
+  reversed-step lookup, initiation on the written strand's ends, tandem G.T steps, undefined steps;
+* a fully Watson-Crick duplex reduces to the closed form built from a second, independent entry of
+  the stack parameters (a 16-dinucleotide matrix), which also double-checks the oracle's table;
+* reading a duplex from the other strand leaves Tm unchanged (no terminal mismatch);
+* the salt correction of method 5 vanishes at 1 M monovalent salt and raises Tm with [Na+];
+* every single mismatch next to a Watson-Crick pair has a parameter;
+* the degenerate-primer Tm is the maximum over the brute-force list of concrete variants.
+"""
+import math
+import os
+import re
+
+import pytest
+
+import oracle
+import synth
+from tests import brute
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "tm_worked.md")
+COMP = {"A": "T", "C": "G", "G": "C", "T": "A"}
+
+
+def _worked():
+    text = open(GOLDEN).read()
+    out = []
+    for block in re.split(r"\n## ", text)[1:]:
+        head = block.splitlines()[0]
+        m = re.match(r"(\S+) seq=(\S+) cseq=(\S+)", head)
+        rows = re.findall(r"^\| ([^|]+?) \| [^|]*\| (-?\d+\.\d+) \| (-?\d+\.\d+) \|$", block, re.M)
+        out.append((m.group(1), m.group(2), m.group(3), [(r[0], float(r[1]), float(r[2])) for r in rows]))
+    return out
+
+
+@pytest.mark.parametrize("name,seq,cseq,rows", _worked())
+def test_hand_worked_sums(name, seq, cseq, rows):
+    got = oracle.duplex_sums(seq, cseq)
+    if name == "undefined":
+        assert got is None
+        return
+    terms = [r for r in rows if r[0] != "total"]
+    (total,) = [r for r in rows if r[0] == "total"]
+    assert abs(sum(t[1] for t in terms) - total[1]) < 1e-9
+    assert abs(sum(t[2] for t in terms) - total[2]) < 1e-9
+    assert got is not None
+    assert abs(got[0] - total[1]) < 1e-9 and abs(got[1] - total[2]) < 1e-9
+
+
+# Second entry of the Watson-Crick stacks (Allawi & SantaLucia 1997), indexed by the top-strand
+# dinucleotide 5'->3' of a fully paired duplex: (dH kcal/mol, dS cal/(K mol)).
+DINUC = {
+    "AA": (-7.9, -22.2), "AC": (-8.4, -22.4), "AG": (-7.8, -21.0), "AT": (-7.2, -20.4),
+    "CA": (-8.5, -22.7), "CC": (-8.0, -19.9), "CG": (-10.6, -27.2), "CT": (-7.8, -21.0),
+    "GA": (-8.2, -22.2), "GC": (-9.8, -24.4), "GG": (-8.0, -19.9), "GT": (-8.4, -22.4),
+    "TA": (-7.2, -21.3), "TC": (-8.2, -22.2), "TG": (-8.5, -22.7), "TT": (-7.9, -22.2),
+}
+END = {"A": (2.3, 4.1), "T": (2.3, 4.1), "G": (0.1, -2.8), "C": (0.1, -2.8)}
+
+
+def closed_form_tm(seq, Na=50.0, c1=25.0, c2=25.0):
+    dh = sum(DINUC[seq[i:i + 2]][0] for i in range(len(seq) - 1)) + END[seq[0]][0] + END[seq[-1]][0]
+    ds = sum(DINUC[seq[i:i + 2]][1] for i in range(len(seq) - 1)) + END[seq[0]][1] + END[seq[-1]][1]
+    ds += 0.368 * (len(seq) - 1) * math.log(Na / 1000.0)
+    return 1000.0 * dh / (ds + 1.987 * math.log((c1 - c2 / 2.0) * 1e-9)) - 273.15
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_watson_crick_closed_form(seed):
+    st = synth.Stream(synth.make_key(seed, 77, 0))
+    seq = "".join(st.choice("ACGT") for _ in range(st.randint(8, 30)))
+    cseq = "".join(COMP[c] for c in seq)
+    Na = [50.0, 10.0, 200.0][seed % 3]
+    tm = oracle.tm_duplex(seq, cseq, synth.TmParams(Na=Na))
+    assert abs(tm - closed_form_tm(seq, Na=Na)) < 1e-9
+
+
+def test_duplex_read_from_other_strand():
+    st = synth.Stream(synth.make_key(5, 78, 0))
+    n = 0
+    for _ in range(300):
+        L = st.randint(10, 26)
+        seq = "".join(st.choice("ACGT") for _ in range(L))
+        cseq = list(COMP[c] for c in seq)
+        # up to two isolated internal mismatches, ends stay paired
+        for p in st.sample(L - 4, 2)[: st.randint(0, 2)]:
+            q = p + 2
+            cseq[q] = st.choice([b for b in "ACGT" if b != COMP[seq[q]]])
+        cseq = "".join(cseq)
+        t1 = oracle.tm_duplex(seq, cseq, synth.TmParams())
+        t2 = oracle.tm_duplex(cseq[::-1], seq[::-1], synth.TmParams())
+        assert (t1 is None) == (t2 is None)
+        if t1 is not None:
+            assert abs(t1 - t2) < 1e-9
+            n += 1
+    assert n > 100
+
+
+def test_every_single_mismatch_step_has_a_parameter():
+    wc = [("A", "T"), ("C", "G"), ("G", "C"), ("T", "A")]
+    mism = [(x, y) for x in "ACGT" for y in "ACGT" if COMP[x] != y]
+    for a, ca in wc:
+        for x, y in mism:
+            for left in (True, False):
+                # G.C clamps on both sides keep the mismatch internal
+                s = "GC" + (a + x if left else x + a) + "GC"
+                c = "CG" + (ca + y if left else y + ca) + "CG"
+                assert oracle.duplex_sums(s, c) is not None, (s, c)
+                # as a terminal mismatch next to a Watson-Crick pair (right end of the duplex)
+                s2, c2 = "GCGC" + a + x, "CGCG" + ca + y
+                ref = oracle.duplex_sums(s2[:-1], c2[:-1])
+                got = oracle.duplex_sums(s2, c2)
+                assert got is not None and ref is not None
+
+
+def test_salt_method5():
+    seq = "AGCTTGACCGTAGGCATTA"
+    cseq = "".join(COMP[c] for c in seq)
+    at_1M = oracle.tm_duplex(seq, cseq, synth.TmParams(Na=1000.0))
+    none = oracle.tm_duplex(seq, cseq, synth.TmParams(saltcorr=0))
+    assert abs(at_1M - none) < 1e-9
+    ts = [oracle.tm_duplex(seq, cseq, synth.TmParams(Na=na)) for na in (5, 20, 50, 100, 300)]
+    assert all(a < b for a, b in zip(ts, ts[1:]))
+
+
+def test_concentration_term():
+    seq = "AGCTTGACCGTAGGCATTA"
+    cseq = "".join(COMP[c] for c in seq)
+    # C = c1 - c2/2: 25/25 nM equals 12.5/0 nM
+    a = oracle.tm_duplex(seq, cseq, synth.TmParams(dnac1=25, dnac2=25))
+    b = oracle.tm_duplex(seq, cseq, synth.TmParams(dnac1=12.5, dnac2=0))
+    assert abs(a - b) < 1e-12
+    assert oracle.tm_duplex(seq, cseq, synth.TmParams(dnac1=250, dnac2=250)) > a
+
+
+@pytest.mark.parametrize("primer,site", [
+    ("ACGTRYACGTAGG", "ACGTACACGTAGG"),
+    ("NACGTAGCWAGT", "TACGTAGCAAGT"),
+    ("GGCATKMSACGTTA", "GGCATGCCACGTTA"),
+    ("BDHVACGGT", "CATGACGGT"),
+    ("ACGGTTNNAC", "ACGGTTAGAC"),
+])
+def test_degenerate_tm_is_max_over_variants(primer, site):
+    cseq = "".join(COMP[c] for c in site)
+    vals = [oracle.tm_duplex(v, cseq, synth.TmParams()) for v in brute.variants(primer)]
+    vals = [v for v in vals if v is not None]
+    got = oracle.tm_site(primer, site, synth.TmParams())
+    if not vals:
+        assert got is None
+    else:
+        assert got is not None and abs(got - max(vals)) < 1e-12
