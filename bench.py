@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Throughput of the in-silico PCR path (scan, site compaction, pairing, FP64 Tm, trimming and
+barcodes) on GB300, as Gbp/s, with the scan kernel's roofline fraction.
+
+Default workload (N=1): 2,000 synthetic genomes, lognormal lengths (median 3.5 Mbp, sigma 0.4,
+~7.6 Gbp), per-genome GC ~ U(0.30, 0.70), 0.5 % N in runs of 1-50, 1-15 planted 16S-like
+templates per genome; one degenerate pair (19 nt with 2 codes, 20 nt with 3), k=3, clamp 3,
+window 50-2000, all four orientations, primer trimming and 16-nt barcodes.
+
+`value` times one step over the packed genomes already resident in HBM.  `e2e` times the same
+step through the C ABI from pinned host ASCII: host->device copy and packing, the step, and the
+device->host copy of sites, amplicons and sequences.  `--impl reference` times the oracle (plain
+C on the host cores) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gbp/s scanned (k=2, 4 orientations), % of HBM roofline; p99 request latency"
+# ALU-pipe peak from unit counts and clocks: 152 SMs x 4 sub-partitions x 16 lanes of LOP3/SHF per
+# clock x 2.07 GHz maximum SM clock (LOP3 and SHF share this pipe; integer adds run beside it).
+SM_COUNT, ALU_LANES_PER_SM_CLK, SM_MAX_GHZ = 152, 64, 2.07
+ALU_PEAK_TOPS = SM_COUNT * ALU_LANES_PER_SM_CLK * SM_MAX_GHZ / 1e3   # T lane-ops/s
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def alg_ops_per_base(fwd, rev, clamp):
+    """Algorithmic lane-ops per base of the bit-sliced scan: per oriented pattern of length L, one
+    lane-op per position for the IUPAC test, two for carry-save counting of each non-clamp
+    position, one to fold each clamp position into the failure word; one lane-op covers 32
+    positions."""
+    total = 0
+    for p in list(fwd) + list(rev):
+        L = len(p)
+        total += 2 * (3 * (L - clamp) + 2 * clamp)   # both strands
+    return total / 32.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_workload(args):
+    import synth
+
+    if args.workload == "plain_scale":
+        return synth.plain_scale(n_genomes=args.genomes or 2000)
+    if args.workload == "plain_small":
+        return synth.plain_small(n_genomes=args.genomes or 16)
+    if args.workload == "batched":
+        return synth.batched(n_genomes=args.genomes or 2000)
+    if args.workload == "dense":
+        return synth.dense(n_genomes=args.genomes or 500)
+    raise SystemExit(f"unknown workload {args.workload}")
+
+
+def describe(wl):
+    return {"workload": f"{wl.name}: {wl.n_records} synthetic genomes, {wl.total_bp / 1e9:.3f} Gbp, "
+                        f"{len(wl.fwd)} degenerate primer pair(s), k={wl.k}, clamp {wl.clamp}, "
+                        f"window {wl.min_len}-{wl.max_len}, orientations mask {wl.orient_mask}, "
+                        f"trim={wl.trim}, barcodes {wl.fb_len}/{wl.rb_len}, "
+                        f"Tm filter {wl.tm.min_tm}",
+            "genomes": wl.n_records, "bases": wl.total_bp, "pairs": len(wl.fwd),
+            "l2": "inputs larger than L2 (packed genomes %.2f GB >> 129 MB)" % (wl.total_bp / 4e9)}
+
+
+# ------------------------------------------------------------------------------------------ oracle arm
+def oracle_sample_seconds(wl, n_genomes):
+    import oracle
+
+    sub = wl.subset(range(n_genomes))
+    t = time.perf_counter()
+    oracle.run(sub, threads=os.cpu_count() or 1)
+    return time.perf_counter() - t, sub.total_bp
+
+
+def pick_sample(wl, target_s):
+    """Number of leading genomes whose oracle run takes about target_s on the host cores."""
+    t1, bp1 = oracle_sample_seconds(wl, min(2, wl.n_records))
+    rate = bp1 / max(t1, 1e-3)
+    want = rate * target_s
+    n, acc = 0, 0
+    lens = wl.lengths()
+    while n < wl.n_records and acc < want:
+        acc += int(lens[n])
+        n += 1
+    return max(1, n)
+
+
+def cpu_baseline(wl, target_s=15.0):
+    n = pick_sample(wl, target_s)
+    t, bp = oracle_sample_seconds(wl, n)
+    return {"value": bp / t / 1e9, "unit": "Gbp/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {n} of {wl.n_records} genomes ({bp / 1e6:.1f} Mbp), whole path "
+                      f"(scan, pair, Tm, extract), {os.cpu_count()} threads, {t:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_workload(args)
+    n = pick_sample(wl, 2.0)
+    import oracle
+
+    sub = wl.subset(range(n))
+    for _ in range(args.warmup):
+        oracle.run(sub, threads=os.cpu_count() or 1)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(sub, threads=os.cpu_count() or 1)
+    dt = (time.perf_counter() - t) / args.steps
+    v = sub.total_bp / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gbp/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8+f64", "data": "synthetic",
+            "config": describe(wl),
+            "cpu_baseline": {"value": v, "unit": "Gbp/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step: first {n} genomes ({sub.total_bp / 1e6:.1f} Mbp), whole path"},
+            "e2e": {"value": v, "unit": "Gbp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------ engine arm
+def run_engine(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+
+    wl = make_workload(args)
+    base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        base = cpu_baseline(wl, args.cpu_seconds)   # host cores only; before the engine's GPU work
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Engine, Params
+
+    eng = Engine(local)
+    stream = torch.cuda.ExternalStream(ah.ah_ctx_stream(eng.ctx))
+    params = Params.from_workload(wl)
+    d_seq = torch.from_numpy(wl.seq).to(f"cuda:{local}")
+    torch.cuda.synchronize()
+    batch = eng.pack_device(d_seq.data_ptr(), wl.offsets.astype(np.uint64), wl.genome_ids)
+    ah.ah_ctx_synchronize(eng.ctx)
+    del d_seq
+    torch.cuda.empty_cache()
+
+    def one_step():
+        hits, amps = eng.step(batch, params, with_seqs=True, copy_out=False)
+        ah.ah_hits_free(hits)
+        ah.ah_amplicons_free(amps)
+
+    for _ in range(max(3, args.warmup)):
+        one_step()
+    ah.ah_ctx_synchronize(eng.ctx)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    ah.ah_ctx_stats_reset(eng.ctx)
+    ah.ah_ctx_set_timing(eng.ctx, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ah.ah_ctx_set_timing(eng.ctx, False)
+    ms = e0.elapsed_time(e1) / args.steps
+    stats = ah.ah_ctx_stats_get(eng.ctx)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * wl.total_bp / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the bit-sliced scan), from its own CUDA-event times
+    scan_ms = stats["scan_ms"] / max(1, stats["scan_launches"])
+    bases_per_launch = stats["scan_bases"] / max(1, stats["scan_launches"])
+    ops_per_base = alg_ops_per_base(wl.fwd, wl.rev, wl.clamp)
+    achieved = ops_per_base * bases_per_launch / (scan_ms * 1e-3) / 1e12
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_achieved = 0.25 * bases_per_launch / (scan_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tlane-op/s",
+                "frac": achieved / ALU_PEAK_TOPS, "traffic": None,
+                "kernel": "ah_scan_jit (bit-sliced scan)", "kernel_ms": scan_ms,
+                "ops_per_base": ops_per_base,
+                "peak_source": "derived: 152 SMs x 64 ALU lanes/clk x 2.07 GHz",
+                "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak,
+                        "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                        "frac": hbm_achieved / hbm_peak, "algorithmic_bytes_per_base": 0.25},
+                "step_gbps_frac_of_alu_bound": value / (ALU_PEAK_TOPS * 1e3 / ops_per_base) / world}
+
+    # end to end through the C ABI from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.empty(wl.total_bp, dtype=torch.uint8, pin_memory=True)
+        pinned.numpy()[:] = wl.seq
+        host = pinned.numpy()
+        h2d = d2h = 0
+        times = []
+        for it in range(1 + args.e2e_steps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            b = eng.pack(host, wl.offsets, wl.genome_ids)
+            out = eng.step(b, params, with_seqs=True, copy_out=True)
+            ah.ah_batch_free(b)
+            ah.ah_ctx_synchronize(eng.ctx)
+            dt = time.perf_counter() - t
+            if it > 0:
+                times.append(dt)
+            h2d = wl.total_bp + 16 * wl.n_records
+            d2h = out.hits.nbytes + out.amps.nbytes + len(out.arena or b"") + out.field_off.nbytes
+        e2e = {"value": wl.total_bp / statistics.median(times) / 1e9, "unit": "Gbp/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": len(times), "ms_per_step": statistics.median(times) * 1e3,
+               "path": "pinned host ASCII -> ah_pack_batch (H2D + pack) -> scan/pair/Tm/extract -> D2H results"}
+        del pinned
+
+    ah.ah_batch_free(batch)
+    eng.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gbp/s", "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32+f64", "data": "synthetic", "config": describe(wl),
+                "clocks": clk.summary(), "e2e": e2e, "gpu_launches": stats["kernel_launches"],
+                "gpu_launches_per_step": stats["kernel_launches"] / args.steps, "roofline": roofline,
+                "cpu_baseline": base}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--workload", default="plain_scale")
+    ap.add_argument("--genomes", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_engine(args)
+
+
+if __name__ == "__main__":
+    main()

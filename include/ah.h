@@ -1,0 +1,245 @@
+/*
+ * ah.h -- C ABI of the GB300 in-silico PCR engine.
+ *
+ * The engine implements the hot path of AmpliconHunter2 (Howard-Stone & Mandoiu, arXiv
+ * 2511.00170):
+ *   1. pack genome records to 2 bits (Abstract; Section "Implementations", AHv2.alpha);
+ *   2. scan both strands for degenerate primers with <= k mismatches and an exact 3' clamp
+ *      (Supplementary, "Primer matching and clamp logic");
+ *   3. pair sites into FR/RF/FF/RR amplicons inside a length window, stopping at the next
+ *      same-sense site (Supplementary, "Amplicon calling and orientation");
+ *   4. nearest-neighbour melting temperature in double precision and an optional minimum-Tm
+ *      filter (Section "Implementations", AHv2; Section "Primer degeneracy");
+ *   5. amplicon sequences, primer trimming, flanking barcodes and primer-site snippets
+ *      (Supplementary, "Primer trimming and barcode extraction", "Headers and outputs").
+ *
+ * Conventions
+ *   - Every call returns ah_status.  On failure the context keeps a message for ah_last_error().
+ *   - Work is enqueued on the context's CUDA stream.  Calls that must size an output read a count
+ *     back from the device and therefore synchronise that stream; this is stated per call.
+ *   - Objects (ah_batch, ah_primers, ah_hits, ah_amplicons) are owned by the library and released
+ *     only by their ah_*_free call, which enqueues the release on the owning context's stream.
+ *     Freeing NULL is a no-op.  An object may only be used with the context that made it.
+ *   - Host pointers are plain host memory (pinned memory makes copies asynchronous and fast).
+ *   - Device-side checks never trap: a kernel that detects an inconsistency sets a status word
+ *     that the next synchronising call turns into AH_EINTERNAL.
+ *   - All sizes are in bases unless stated otherwise.
+ */
+#ifndef AH_H
+#define AH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AH_OK = 0,
+  AH_EINVAL = 1,     /* invalid argument (bad IUPAC code, sizes, parameters) */
+  AH_ENOMEM = 2,     /* device or host allocation failed */
+  AH_ECUDA = 3,      /* a CUDA runtime/driver call failed */
+  AH_EOVERFLOW = 4,  /* an output would exceed a caller-given capacity */
+  AH_ETIMEOUT = 5,   /* a bounded device wait ran out */
+  AH_EJIT = 6,       /* run-time compilation of a specialised kernel failed */
+  AH_EINTERNAL = 7   /* a device self-check failed */
+} ah_status;
+
+typedef struct ah_ctx ah_ctx;
+typedef struct ah_batch ah_batch;
+typedef struct ah_primers ah_primers;
+typedef struct ah_hits ah_hits;
+typedef struct ah_amplicons ah_amplicons;
+
+/* ------------------------------------------------------------------------------------------ */
+/* context                                                                                      */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to enqueue on, or
+ * NULL for a stream the context creates (non-blocking) and destroys. */
+ah_status ah_ctx_create(ah_ctx** out, int device, void* cuda_stream);
+void ah_ctx_destroy(ah_ctx* ctx);
+/* Message of the last failing call on this context (owned by the context, valid until the next
+ * call). */
+const char* ah_last_error(const ah_ctx* ctx);
+/* Wait for all work enqueued on the context's stream and report device self-check failures. */
+ah_status ah_ctx_synchronize(ah_ctx* ctx);
+/* The stream the context enqueues on (a cudaStream_t). */
+void* ah_ctx_stream(const ah_ctx* ctx);
+
+/* Diagnostics of one context (not part of the paper's method): how many kernels it launched,
+ * and, when timing is enabled, the device time of the bit-sliced scan kernel measured with CUDA
+ * events recorded on the context's stream around each of its launches. */
+typedef struct {
+  uint64_t kernel_launches; /* kernels launched by this context since the last reset */
+  uint64_t scan_launches;   /* launches of the scan kernel */
+  double scan_ms;           /* summed device time of those launches (timing enabled) */
+  uint64_t scan_bases;      /* bases covered by those launches */
+} ah_ctx_stats;
+ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out);
+ah_status ah_ctx_stats_reset(ah_ctx* ctx);
+ah_status ah_ctx_set_timing(ah_ctx* ctx, int enable);
+
+/* ------------------------------------------------------------------------------------------ */
+/* 1. packing                                                                                   */
+/*
+ * Device layout of a packed batch (Section "Implementations": FASTA is compressed into 2-bit
+ * batches that store headers, lengths and packed bases; here headers stay on the host):
+ *   - bases are grouped 32 to a group; group g holds bases [32g, 32g+32) of the batch;
+ *   - planes[g] is a uint2 {lo, hi}: bit b of lo/hi is the low/high bit of the 2-bit code of
+ *     base 32g+b, with codes A=0, C=1, T=2, G=3 (lo = ASCII bit 1, hi = ASCII bit 2 of ACGTacgt);
+ *   - invalid[g] is a uint32: bit b set iff base 32g+b is not one of ACGTacgt (N, other IUPAC
+ *     codes, padding); such bases are stored as code 0;
+ *   - record r starts at group rec_group[r] (a multiple of 2, so every record starts 16-byte
+ *     aligned) and has rec_len[r] bases; the bases after rec_len up to the next record are
+ *     padding;
+ *   - the plane and invalid arrays extend at least 64 zero groups past the last record.
+ */
+typedef struct {
+  uint32_t n_records;
+  uint64_t n_bases;          /* sum of record lengths */
+  uint64_t n_groups;         /* groups covered by records, padding included */
+  const void* planes;        /* device uint2[n_groups + tail] */
+  const uint32_t* invalid;   /* device uint32[n_groups + tail] */
+  const uint64_t* rec_group; /* device uint64[n_records] */
+  const uint32_t* rec_len;   /* device uint32[n_records] */
+  const uint32_t* genome_id; /* device uint32[n_records] */
+} ah_batch_view;
+
+/* Pack host ASCII records.  seqs[i] points at lens[i] characters (no terminator needed);
+ * genome_ids may be NULL (then record i has genome id i).  Characters other than ACGTacgt are
+ * invalid bases.  Records are copied to the device in chunks of 64 Mi bases (16 MB packed) and
+ * packed by a kernel while the next chunk is in flight.  Synchronises the stream before
+ * returning (the host buffers may be reused afterwards).  AH_EINVAL: n_rec == 0, a record longer
+ * than 2^32-1 bases, or a NULL pointer with a nonzero length. */
+ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, const uint64_t* lens,
+                        const uint32_t* genome_ids, ah_batch** out);
+
+/* Pack records that are already in device memory: d_seq holds all records back to back and
+ * h_offsets (host, n_rec+1 entries) gives record r as d_seq[h_offsets[r], h_offsets[r+1]).
+ * Asynchronous; d_seq must stay valid until the stream reaches this work. */
+ah_status ah_pack_batch_device(ah_ctx* ctx, uint32_t n_rec, const uint8_t* d_seq, const uint64_t* h_offsets,
+                               const uint32_t* genome_ids, ah_batch** out);
+
+ah_status ah_batch_view_get(const ah_batch* b, ah_batch_view* out);
+void ah_batch_free(ah_batch* b);
+
+/* ------------------------------------------------------------------------------------------ */
+/* primers                                                                                      */
+
+/* n_pairs pairs of IUPAC primers (5'->3', any case) with a mismatch budget per pair and one 3'
+ * clamp length.  AH_EINVAL: n_pairs == 0 or > 256, a character outside the 15 IUPAC codes, a
+ * length outside [clamp+1, 32], k > 15 or k > length. */
+ah_status ah_primers_create(ah_ctx* ctx, uint32_t n_pairs, const char* const* fwd, const char* const* rev,
+                            const uint8_t* k, uint8_t clamp, ah_primers** out);
+void ah_primers_free(ah_primers* p);
+
+/* ------------------------------------------------------------------------------------------ */
+/* 2. scan                                                                                      */
+
+/* One binding site.  pattern = 4 * pair + orient, orient = 2 * strand + primer, where primer 0
+ * is the forward primer, 1 the reverse primer, strand 0 means the primer as written matches the
+ * top strand and strand 1 means its reverse complement does.  [pos, pos + length of the primer)
+ * is the site on the top strand of record `record`; mism counts mismatched primer positions. */
+typedef struct {
+  uint32_t record;
+  uint32_t pos;
+  uint16_t pattern;
+  uint8_t mism;
+  uint8_t flags;  /* reserved, 0 */
+} ah_hit;
+
+/* Every site of every pattern: a window [pos, pos+L) inside its record with no invalid base,
+ * at most k mismatches against the pattern's IUPAC sets, and all c clamp positions matching
+ * (the primer's 3' end: the last c positions as written, the first c of its reverse complement).
+ * Hits are ordered by (pair, record, pos, orient).  Synchronises the stream to size the output. */
+ah_status ah_scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out);
+
+ah_status ah_hits_count(const ah_hits* h, uint64_t* n);
+/* Device view: hits in device memory (ah_hit[n]) and, per pair, the range of its hits
+ * (uint64[n_pairs+1], device). */
+ah_status ah_hits_device(const ah_hits* h, const ah_hit** d_hits, const uint64_t** d_pair_offsets);
+/* Copy min(n, cap) hits to host memory; synchronises. */
+ah_status ah_hits_copy(const ah_hits* h, ah_hit* host_out, uint64_t cap);
+void ah_hits_free(ah_hits* h);
+
+/* ------------------------------------------------------------------------------------------ */
+/* 3. pairing                                                                                   */
+
+#define AH_FR 1u
+#define AH_RF 2u
+#define AH_FF 4u
+#define AH_RR 8u
+
+/* Amplicon record.  [start, end) on the top strand; orient 0 FR, 1 RF, 2 FF, 3 RR.
+ * tm is filled by ah_tm_filter (NaN before).  flags: bit0 kept by the Tm filter, bit1 Tm within
+ * 1e-9 C of the threshold, bit2 Tm undefined (a site with no parameterised variant). */
+typedef struct {
+  uint32_t hit_i, hit_j; /* indices into the hits: the + anchor site and the - site */
+  uint32_t record;
+  uint32_t start, end;
+  uint16_t pair;
+  uint8_t orient;
+  uint8_t flags;
+  double tm;
+} ah_amplicon;
+
+/* For each + site i of a pair (in site order), walk the following sites of the same record and
+ * pair: a + site stops the walk; a - site j whose amplicon end_j - pos_i exceeds max_len stops
+ * it; a - site with min_len <= length is paired.  Orientation (primer_i, primer_j): (F,R) FR,
+ * (R,F) RF, (F,F) FF, (R,R) RR; only orientations in orient_mask are output (the walk is not
+ * affected).  Amplicons are ordered by (hit_i, hit_j).  Synchronises the stream. */
+ah_status ah_pair_amplicons(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h,
+                            uint32_t min_len, uint32_t max_len, uint32_t orient_mask, ah_amplicons** out);
+
+/* ------------------------------------------------------------------------------------------ */
+/* 4. melting temperature                                                                       */
+
+typedef struct {
+  double Na, K, Tris, Mg, dNTPs; /* mM */
+  double dnac1, dnac2;           /* nM, the two strand concentrations */
+  int32_t saltcorr;              /* 0 none; 1-6 as in Biopython's salt_correction; default 5 */
+  int32_t filter;                /* nonzero: drop amplicons with Tm < min_tm or undefined Tm */
+  double min_tm;                 /* degrees C */
+} ah_tm_params;
+
+/* Fill tm and flags of every amplicon: the nearest-neighbour Tm (FP64) of each site is the
+ * maximum over the primer's concrete variants of Tm(variant, site); the amplicon's Tm is the lower
+ * of its two sites'.  With filter set, the amplicon list is compacted to the kept ones (order
+ * preserved).  Synchronises the stream when filter is set. */
+ah_status ah_tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a,
+                       const ah_tm_params* params);
+
+/* Tm of n given duplexes (utility and test surface): seqs[i] (5'->3', ACGT) over cseqs[i] (the
+ * opposite strand written 3'->5', same length 2..32).  Writes tm_out[i] (NaN if undefined).
+ * Synchronises. */
+ah_status ah_tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const char* const* cseqs,
+                         const ah_tm_params* params, double* tm_out);
+
+/* ------------------------------------------------------------------------------------------ */
+/* 5. sequences and barcodes                                                                    */
+
+/* For every amplicon, five strings into one device byte arena: the amplicon (top strand for FR,
+ * FF, RR; reverse complement for RF) or, with trim, the part between its two sites (empty when
+ * they overlap); the forward barcode (fb_len bases upstream of the forward primer: left of site i
+ * for FR/FF/RR, right of site j reverse-complemented for RF); the reverse barcode (rb_len bases:
+ * right of site j, or left of site i reverse-complemented for RF); and the bases of site i and of
+ * site j in their primers' 5'->3' orientation.  Barcodes are clipped at record ends.  Invalid
+ * bases are written as 'N'.  Synchronises the stream to size the arena. */
+ah_status ah_extract_barcodes(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h,
+                              ah_amplicons* a, int trim, uint32_t fb_len, uint32_t rb_len);
+
+ah_status ah_amplicons_count(const ah_amplicons* a, uint64_t* n);
+ah_status ah_amplicons_copy(const ah_amplicons* a, ah_amplicon* host_out, uint64_t cap);
+/* Bytes in the arena written by ah_extract_barcodes (0 before). */
+ah_status ah_amplicons_arena_size(const ah_amplicons* a, uint64_t* bytes);
+/* Copy the arena and the field offsets (uint64[5*n+1]: field f of amplicon m spans
+ * [off[5m+f], off[5m+f+1])).  Synchronises. */
+ah_status ah_amplicons_seq_copy(const ah_amplicons* a, char* arena_out, uint64_t arena_cap, uint64_t* offsets_out,
+                                uint64_t offsets_cap);
+void ah_amplicons_free(ah_amplicons* a);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AH_H */

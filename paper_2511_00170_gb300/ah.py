@@ -1,0 +1,293 @@
+"""ctypes binding of the engine's C ABI (``include/ah.h``).
+
+Argument marshalling only: every function has the name of the C entry point it calls, converts
+Python/numpy arguments to plain pointers and sizes, raises :class:`AhError` on a non-OK status,
+and returns handles or numpy arrays.  All computation happens in ``libah.so``.  There is no
+fallback: if the library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libah.so")
+
+AH_OK, AH_EINVAL, AH_ENOMEM, AH_ECUDA, AH_EOVERFLOW, AH_ETIMEOUT, AH_EJIT, AH_EINTERNAL = range(8)
+STATUS_NAMES = {0: "AH_OK", 1: "AH_EINVAL", 2: "AH_ENOMEM", 3: "AH_ECUDA", 4: "AH_EOVERFLOW", 5: "AH_ETIMEOUT",
+                6: "AH_EJIT", 7: "AH_EINTERNAL"}
+AH_FR, AH_RF, AH_FF, AH_RR = 1, 2, 4, 8
+
+HIT_DTYPE = np.dtype([("record", "<u4"), ("pos", "<u4"), ("pattern", "<u2"), ("mism", "u1"), ("flags", "u1")])
+AMP_DTYPE = np.dtype([("hit_i", "<u4"), ("hit_j", "<u4"), ("record", "<u4"), ("start", "<u4"), ("end", "<u4"),
+                      ("pair", "<u2"), ("orient", "u1"), ("flags", "u1"), ("tm", "<f8")])
+assert HIT_DTYPE.itemsize == 12 and AMP_DTYPE.itemsize == 32
+
+
+class AhError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ah_tm_params(ctypes.Structure):
+    _fields_ = [("Na", ctypes.c_double), ("K", ctypes.c_double), ("Tris", ctypes.c_double), ("Mg", ctypes.c_double),
+                ("dNTPs", ctypes.c_double), ("dnac1", ctypes.c_double), ("dnac2", ctypes.c_double),
+                ("saltcorr", ctypes.c_int32), ("filter", ctypes.c_int32), ("min_tm", ctypes.c_double)]
+
+
+class ah_ctx_stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_uint64), ("scan_launches", ctypes.c_uint64), ("scan_ms", ctypes.c_double),
+                ("scan_bases", ctypes.c_uint64)]
+
+
+class ah_batch_view(ctypes.Structure):
+    _fields_ = [("n_records", ctypes.c_uint32), ("n_bases", ctypes.c_uint64), ("n_groups", ctypes.c_uint64),
+                ("planes", ctypes.c_void_p), ("invalid", ctypes.c_void_p), ("rec_group", ctypes.c_void_p),
+                ("rec_len", ctypes.c_void_p), ("genome_id", ctypes.c_void_p)]
+
+
+# name -> (restype, argtypes)
+_VP, _U32, _U64, _I32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+_PVP = ctypes.POINTER(ctypes.c_void_p)
+SIGNATURES = {
+    "ah_ctx_create": (_I32, [_PVP, _I32, _VP]),
+    "ah_ctx_destroy": (None, [_VP]),
+    "ah_last_error": (ctypes.c_char_p, [_VP]),
+    "ah_ctx_synchronize": (_I32, [_VP]),
+    "ah_ctx_stream": (_VP, [_VP]),
+    "ah_ctx_stats_get": (_I32, [_VP, ctypes.POINTER(ah_ctx_stats)]),
+    "ah_ctx_stats_reset": (_I32, [_VP]),
+    "ah_ctx_set_timing": (_I32, [_VP, _I32]),
+    "ah_pack_batch": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
+    "ah_pack_batch_device": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
+    "ah_batch_view_get": (_I32, [_VP, ctypes.POINTER(ah_batch_view)]),
+    "ah_batch_free": (None, [_VP]),
+    "ah_primers_create": (_I32, [_VP, _U32, _VP, _VP, _VP, ctypes.c_uint8, _PVP]),
+    "ah_primers_free": (None, [_VP]),
+    "ah_scan_primers": (_I32, [_VP, _VP, _VP, _PVP]),
+    "ah_hits_count": (_I32, [_VP, ctypes.POINTER(ctypes.c_uint64)]),
+    "ah_hits_device": (_I32, [_VP, _PVP, _PVP]),
+    "ah_hits_copy": (_I32, [_VP, _VP, _U64]),
+    "ah_hits_free": (None, [_VP]),
+    "ah_pair_amplicons": (_I32, [_VP, _VP, _VP, _VP, _U32, _U32, _U32, _PVP]),
+    "ah_tm_filter": (_I32, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ah_tm_params)]),
+    "ah_tm_duplexes": (_I32, [_VP, _U32, _VP, _VP, ctypes.POINTER(ah_tm_params), _VP]),
+    "ah_extract_barcodes": (_I32, [_VP, _VP, _VP, _VP, _VP, _I32, _U32, _U32]),
+    "ah_amplicons_count": (_I32, [_VP, ctypes.POINTER(ctypes.c_uint64)]),
+    "ah_amplicons_copy": (_I32, [_VP, _VP, _U64]),
+    "ah_amplicons_arena_size": (_I32, [_VP, ctypes.POINTER(ctypes.c_uint64)]),
+    "ah_amplicons_seq_copy": (_I32, [_VP, _VP, _U64, _VP, _U64]),
+    "ah_amplicons_free": (None, [_VP]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libah.so (built by ``paper_2511_00170_gb300.build``).  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with `python -m paper_2511_00170_gb300.build` "
+                              "(the engine has no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(st: int, ctx=None):
+    if st != AH_OK:
+        msg = load().ah_last_error(ctx).decode() if ctx else ""
+        raise AhError(st, msg)
+
+
+# ------------------------------------------------------------------------------------------ context
+def ah_ctx_create(device: int = 0, stream: Optional[int] = None):
+    out = ctypes.c_void_p()
+    _check(load().ah_ctx_create(ctypes.byref(out), device, stream))
+    return out
+
+
+def ah_ctx_destroy(ctx) -> None:
+    load().ah_ctx_destroy(ctx)
+
+
+def ah_last_error(ctx) -> str:
+    return load().ah_last_error(ctx).decode()
+
+
+def ah_ctx_synchronize(ctx) -> None:
+    _check(load().ah_ctx_synchronize(ctx), ctx)
+
+
+def ah_ctx_stream(ctx) -> int:
+    return load().ah_ctx_stream(ctx) or 0
+
+
+def ah_ctx_stats_get(ctx) -> dict:
+    s = ah_ctx_stats()
+    _check(load().ah_ctx_stats_get(ctx, ctypes.byref(s)), ctx)
+    return {f: getattr(s, f) for f, _ in ah_ctx_stats._fields_}
+
+
+def ah_ctx_stats_reset(ctx) -> None:
+    _check(load().ah_ctx_stats_reset(ctx), ctx)
+
+
+def ah_ctx_set_timing(ctx, enable: bool) -> None:
+    _check(load().ah_ctx_set_timing(ctx, int(bool(enable))), ctx)
+
+
+# ------------------------------------------------------------------------------------------ packing
+def ah_pack_batch(ctx, seq: np.ndarray, offsets: np.ndarray, genome_ids: Optional[np.ndarray] = None):
+    """Records are seq[offsets[r]:offsets[r+1]] of a contiguous host uint8 buffer (pinned is faster)."""
+    seq = np.ascontiguousarray(seq).view(np.uint8).reshape(-1)
+    offsets = np.asarray(offsets, dtype=np.uint64)
+    n = len(offsets) - 1
+    ptrs = (np.uint64(seq.ctypes.data) + offsets[:-1]).astype(np.uint64)
+    lens = np.diff(offsets).astype(np.uint64)
+    gid = None if genome_ids is None else np.ascontiguousarray(genome_ids, dtype=np.uint32)
+    out = ctypes.c_void_p()
+    _check(load().ah_pack_batch(ctx, n, ptrs.ctypes.data, lens.ctypes.data, None if gid is None else gid.ctypes.data,
+                                ctypes.byref(out)), ctx)
+    return out
+
+
+def ah_pack_batch_device(ctx, d_seq: int, offsets: np.ndarray, genome_ids: Optional[np.ndarray] = None):
+    """Records already in device memory at address d_seq; offsets (host) delimit them."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    gid = None if genome_ids is None else np.ascontiguousarray(genome_ids, dtype=np.uint32)
+    out = ctypes.c_void_p()
+    _check(load().ah_pack_batch_device(ctx, len(offsets) - 1, d_seq, offsets.ctypes.data,
+                                       None if gid is None else gid.ctypes.data, ctypes.byref(out)), ctx)
+    return out
+
+
+def ah_batch_view_get(batch) -> dict:
+    v = ah_batch_view()
+    _check(load().ah_batch_view_get(batch, ctypes.byref(v)))
+    return {f: getattr(v, f) for f, _ in ah_batch_view._fields_}
+
+
+def ah_batch_free(batch) -> None:
+    load().ah_batch_free(batch)
+
+
+# ------------------------------------------------------------------------------------------ primers
+def ah_primers_create(ctx, fwd: Sequence[str], rev: Sequence[str], k: Sequence[int], clamp: int):
+    n = len(fwd)
+    fa = (ctypes.c_char_p * n)(*[s.encode("ascii") for s in fwd])
+    ra = (ctypes.c_char_p * n)(*[s.encode("ascii") for s in rev])
+    ka = np.ascontiguousarray(np.asarray(k, dtype=np.uint8))
+    out = ctypes.c_void_p()
+    _check(load().ah_primers_create(ctx, n, ctypes.cast(fa, ctypes.c_void_p), ctypes.cast(ra, ctypes.c_void_p),
+                                    ka.ctypes.data, clamp, ctypes.byref(out)), ctx)
+    return out
+
+
+def ah_primers_free(p) -> None:
+    load().ah_primers_free(p)
+
+
+# ------------------------------------------------------------------------------------------ scan
+def ah_scan_primers(ctx, batch, primers):
+    out = ctypes.c_void_p()
+    _check(load().ah_scan_primers(ctx, batch, primers, ctypes.byref(out)), ctx)
+    return out
+
+
+def ah_hits_count(hits) -> int:
+    n = ctypes.c_uint64()
+    _check(load().ah_hits_count(hits, ctypes.byref(n)))
+    return n.value
+
+
+def ah_hits_device(hits):
+    d, off = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().ah_hits_device(hits, ctypes.byref(d), ctypes.byref(off)))
+    return d.value, off.value
+
+
+def ah_hits_copy(hits) -> np.ndarray:
+    n = ah_hits_count(hits)
+    out = np.empty(n, dtype=HIT_DTYPE)
+    _check(load().ah_hits_copy(hits, out.ctypes.data if n else None, n))
+    return out
+
+
+def ah_hits_free(hits) -> None:
+    load().ah_hits_free(hits)
+
+
+# ------------------------------------------------------------------------------------------ pairing
+def ah_pair_amplicons(ctx, batch, primers, hits, min_len: int, max_len: int, orient_mask: int = 15):
+    out = ctypes.c_void_p()
+    _check(load().ah_pair_amplicons(ctx, batch, primers, hits, min_len, max_len, orient_mask, ctypes.byref(out)), ctx)
+    return out
+
+
+# ------------------------------------------------------------------------------------------ Tm
+def tm_params(Na=50.0, K=0.0, Tris=0.0, Mg=0.0, dNTPs=0.0, dnac1=25.0, dnac2=25.0, saltcorr=5, min_tm=None) -> ah_tm_params:
+    return ah_tm_params(Na, K, Tris, Mg, dNTPs, dnac1, dnac2, saltcorr, 0 if min_tm is None else 1,
+                        0.0 if min_tm is None else float(min_tm))
+
+
+def ah_tm_filter(ctx, batch, primers, hits, amps, params: ah_tm_params) -> None:
+    _check(load().ah_tm_filter(ctx, batch, primers, hits, amps, ctypes.byref(params)), ctx)
+
+
+def ah_tm_duplexes(ctx, seqs: Sequence[str], cseqs: Sequence[str], params: ah_tm_params) -> np.ndarray:
+    n = len(seqs)
+    sa = (ctypes.c_char_p * n)(*[s.encode("ascii") for s in seqs])
+    ca = (ctypes.c_char_p * n)(*[s.encode("ascii") for s in cseqs])
+    out = np.empty(n, dtype=np.float64)
+    _check(load().ah_tm_duplexes(ctx, n, ctypes.cast(sa, ctypes.c_void_p), ctypes.cast(ca, ctypes.c_void_p),
+                                 ctypes.byref(params), out.ctypes.data), ctx)
+    return out
+
+
+# ------------------------------------------------------------------------------------------ extraction
+def ah_extract_barcodes(ctx, batch, primers, hits, amps, trim: bool, fb_len: int, rb_len: int) -> None:
+    _check(load().ah_extract_barcodes(ctx, batch, primers, hits, amps, int(bool(trim)), fb_len, rb_len), ctx)
+
+
+def ah_amplicons_count(amps) -> int:
+    n = ctypes.c_uint64()
+    _check(load().ah_amplicons_count(amps, ctypes.byref(n)))
+    return n.value
+
+
+def ah_amplicons_copy(amps) -> np.ndarray:
+    n = ah_amplicons_count(amps)
+    out = np.empty(n, dtype=AMP_DTYPE)
+    _check(load().ah_amplicons_copy(amps, out.ctypes.data if n else None, n))
+    return out
+
+
+def ah_amplicons_arena_size(amps) -> int:
+    n = ctypes.c_uint64()
+    _check(load().ah_amplicons_arena_size(amps, ctypes.byref(n)))
+    return n.value
+
+
+def ah_amplicons_seq_copy(amps):
+    """(arena bytes, offsets uint64[5n+1])"""
+    n = ah_amplicons_count(amps)
+    size = ctypes.c_uint64()
+    _check(load().ah_amplicons_arena_size(amps, ctypes.byref(size)))
+    arena = np.empty(max(1, size.value), dtype=np.uint8)
+    off = np.empty(5 * n + 1, dtype=np.uint64)
+    _check(load().ah_amplicons_seq_copy(amps, arena.ctypes.data, size.value, off.ctypes.data, len(off)))
+    return arena[:size.value].tobytes(), off
+
+
+def ah_amplicons_free(amps) -> None:
+    load().ah_amplicons_free(amps)

@@ -1,0 +1,569 @@
+// C ABI entry points: context, packing, primers, object accessors.  The path's stages live in
+// ah_scan.cu, ah_pair.cu, ah_tm.cu and ah_extract.cu.
+#include <algorithm>
+#include <cctype>
+#include <cmath>
+#include <cstring>
+
+#include "ah_internal.h"
+
+using namespace ah;
+
+// ------------------------------------------------------------------------------------------
+// packing kernel
+//
+// One CTA per item (a piece of one record); each warp turns 32 groups (1024 bases) into plane
+// words at a time: for group i of the block every lane loads one byte (32 consecutive bytes per
+// warp load), three warp ballots assemble the lo, hi and invalid words, and lane i keeps group i's
+// words for one coalesced store at the end.
+namespace {
+
+struct PackItem {
+  uint64_t src_off;    // byte offset of the item's first base in the source buffer
+  uint64_t dst_group;  // first output group
+  uint32_t n_valid;    // bases present in the source for this item
+  uint32_t n_groups;   // groups to write (padding included)
+};
+
+constexpr int kPackThreads = 256;
+
+__global__ void k_pack(const uint8_t* __restrict__ src, const PackItem* __restrict__ items, uint2* __restrict__ planes,
+                       uint32_t* __restrict__ invalid) {
+  const PackItem it = items[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (uint32_t blk = warp; blk * 32u < it.n_groups; blk += nwarps) {
+    uint32_t my_lo = 0, my_hi = 0, my_inv = 0;
+    const uint32_t g0 = blk * 32u;
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+      const uint32_t x = (g0 + (uint32_t)i) * 32u + (uint32_t)lane;  // base index within the item
+      uint32_t c = 'N';
+      if (x < it.n_valid) c = __ldg(src + it.src_off + x);
+      const uint32_t u = c | 0x20u;
+      const bool valid = (u == 'a') | (u == 'c') | (u == 'g') | (u == 't');
+      const uint32_t lo = __ballot_sync(0xffffffffu, valid && ((c >> 1) & 1u));
+      const uint32_t hi = __ballot_sync(0xffffffffu, valid && ((c >> 2) & 1u));
+      const uint32_t inv = __ballot_sync(0xffffffffu, !valid);
+      if (lane == i) {
+        my_lo = lo;
+        my_hi = hi;
+        my_inv = inv;
+      }
+    }
+    const uint32_t g = g0 + (uint32_t)lane;
+    if (g < it.n_groups) {
+      planes[it.dst_group + g] = make_uint2(my_lo, my_hi);
+      invalid[it.dst_group + g] = my_inv;
+    }
+  }
+}
+
+void free_batch_arrays(ah_batch* b) {
+  if (!b || !b->ctx) return;
+  dfree(b->ctx, b->planes);
+  dfree(b->ctx, b->invalid);
+  dfree(b->ctx, b->rec_group);
+  dfree(b->ctx, b->rec_len);
+  dfree(b->ctx, b->genome_id);
+}
+
+// record layout shared by both packing paths
+ah_status layout_batch(ah_ctx* ctx, uint32_t n_rec, const uint64_t* lens, const uint32_t* genome_ids, ah_batch* b) {
+  b->ctx = ctx;
+  b->n_records = n_rec;
+  b->h_rec_group.resize(n_rec);
+  b->h_rec_len.resize(n_rec);
+  uint64_t cursor = 0, bases = 0;
+  for (uint32_t r = 0; r < n_rec; ++r) {
+    if (lens[r] > 0xffffffffull) return fail(ctx, AH_EINVAL, "record %u is longer than 2^32-1 bases", r);
+    b->h_rec_group[r] = cursor;
+    b->h_rec_len[r] = (uint32_t)lens[r];
+    cursor += ((lens[r] + 63) / 64) * 2;  // 64-base (16-byte) aligned records
+    bases += lens[r];
+  }
+  b->n_bases = bases;
+  b->n_groups = cursor;
+  b->alloc_groups = cursor + kTailGroups;
+  ah_status st;
+  if ((st = dalloc(ctx, &b->planes, b->alloc_groups))) return st;
+  if ((st = dalloc(ctx, &b->invalid, b->alloc_groups))) return st;
+  if ((st = dalloc(ctx, &b->rec_group, n_rec))) return st;
+  if ((st = dalloc(ctx, &b->rec_len, n_rec))) return st;
+  if ((st = dalloc(ctx, &b->genome_id, n_rec))) return st;
+  std::vector<uint32_t> gid(n_rec);
+  for (uint32_t r = 0; r < n_rec; ++r) gid[r] = genome_ids ? genome_ids[r] : r;
+  AH_CUDA(ctx, cudaMemcpyAsync(b->rec_group, b->h_rec_group.data(), n_rec * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                               ctx->stream));
+  AH_CUDA(ctx, cudaMemcpyAsync(b->rec_len, b->h_rec_len.data(), n_rec * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                               ctx->stream));
+  AH_CUDA(ctx, cudaMemcpyAsync(b->genome_id, gid.data(), n_rec * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+  // the tail past the last record reads as code 0 and valid; windows there fail the length check
+  AH_CUDA(ctx, cudaMemsetAsync(b->planes + b->n_groups, 0, kTailGroups * sizeof(uint2), ctx->stream));
+  AH_CUDA(ctx, cudaMemsetAsync(b->invalid + b->n_groups, 0, kTailGroups * sizeof(uint32_t), ctx->stream));
+  // host vectors above must outlive the async copies
+  AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return AH_OK;
+}
+
+// items for record r's bases [from, to) placed at source offset src_off; the last piece of a
+// record also writes the record's padding groups
+void add_items(std::vector<PackItem>& items, const ah_batch* b, uint32_t r, uint64_t from, uint64_t to,
+               uint64_t src_off) {
+  const uint64_t piece = 1ull << 20;  // bases per item (multiple of 32)
+  const uint64_t len = b->h_rec_len[r];
+  const uint64_t rec_groups = ((len + 63) / 64) * 2;
+  for (uint64_t a = from; a < to || (a == from && to == from && from == 0 && len == 0); a += piece) {
+    uint64_t e = std::min(to, a + piece);
+    PackItem it;
+    it.src_off = src_off + (a - from);
+    it.dst_group = b->h_rec_group[r] + a / 32;
+    it.n_valid = (uint32_t)(e - a);
+    uint64_t gend = (e == len) ? rec_groups : (e + 31) / 32;
+    it.n_groups = (uint32_t)(gend - a / 32);
+    if (it.n_groups) items.push_back(it);
+    if (e == to) break;
+  }
+}
+
+ah_status run_pack(ah_ctx* ctx, const uint8_t* d_src, const std::vector<PackItem>& items, ah_batch* b) {
+  if (items.empty()) return AH_OK;
+  PackItem* d_items;
+  ah_status st = dalloc(ctx, &d_items, items.size());
+  if (st) return st;
+  AH_CUDA(ctx, cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(PackItem), cudaMemcpyHostToDevice,
+                               ctx->stream));
+  for (size_t i = 0; i < items.size(); i += 65535) {
+    unsigned n = (unsigned)std::min<size_t>(65535, items.size() - i);
+    k_pack<<<n, kPackThreads, 0, ctx->stream>>>(d_src, d_items + i, b->planes, b->invalid);
+    launched(ctx);
+  }
+  AH_CUDA(ctx, cudaGetLastError());
+  // items (host) must stay alive until the copy has been consumed
+  AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  dfree(ctx, d_items);
+  return AH_OK;
+}
+
+// IUPAC nomenclature -> set over the packed codes (A=1, C=2, T=4, G=8); 0 if not a code
+uint8_t iupac(char ch) {
+  switch (std::toupper((unsigned char)ch)) {
+    case 'A': return SET_A;
+    case 'C': return SET_C;
+    case 'G': return SET_G;
+    case 'T': return SET_T;
+    case 'R': return SET_A | SET_G;
+    case 'Y': return SET_C | SET_T;
+    case 'S': return SET_C | SET_G;
+    case 'W': return SET_A | SET_T;
+    case 'K': return SET_G | SET_T;
+    case 'M': return SET_A | SET_C;
+    case 'B': return SET_C | SET_G | SET_T;
+    case 'D': return SET_A | SET_G | SET_T;
+    case 'H': return SET_A | SET_C | SET_T;
+    case 'V': return SET_A | SET_C | SET_G;
+    case 'N': return SET_A | SET_C | SET_G | SET_T;
+    default: return 0;
+  }
+}
+
+// complement of a set: code c pairs with code c ^ 2 (A<->T, C<->G)
+uint8_t set_complement(uint8_t s) {
+  return (uint8_t)(((s & 1) << 2) | ((s & 4) >> 2) | ((s & 2) << 2) | ((s & 8) >> 2));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+ah_status ah_ctx_create(ah_ctx** out, int device, void* cuda_stream) {
+  if (!out) return AH_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return AH_ECUDA;
+  ah_ctx* ctx = new ah_ctx();
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess || cudaFree(nullptr) != cudaSuccess) {
+    delete ctx;
+    return AH_ECUDA;
+  }
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return AH_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&ctx->d_status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+    ah_ctx_destroy(ctx);
+    return AH_ENOMEM;
+  }
+  // keep freed pool memory cached for reuse across steps
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t threshold = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+  }
+  ctx->jit.reset(new JitCache());
+  *out = ctx;
+  return AH_OK;
+}
+
+void ah_ctx_destroy(ah_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  ctx->jit.reset();
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* ah_last_error(const ah_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+ah_status ah_ctx_synchronize(ah_ctx* ctx) {
+  if (!ctx) return AH_EINVAL;
+  AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx);
+}
+
+void* ah_ctx_stream(const ah_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out) {
+  if (!ctx || !out) return AH_EINVAL;
+  out->kernel_launches = ctx->n_launches;
+  out->scan_launches = ctx->n_scan_launches;
+  out->scan_ms = ctx->scan_ms;
+  out->scan_bases = ctx->scan_bases;
+  return AH_OK;
+}
+
+ah_status ah_ctx_stats_reset(ah_ctx* ctx) {
+  if (!ctx) return AH_EINVAL;
+  ctx->n_launches = ctx->n_scan_launches = ctx->scan_bases = 0;
+  ctx->scan_ms = 0.0;
+  return AH_OK;
+}
+
+ah_status ah_ctx_set_timing(ah_ctx* ctx, int enable) {
+  if (!ctx) return AH_EINVAL;
+  cudaSetDevice(ctx->device);
+  for (int i = 0; i < 2 && enable; ++i)
+    if (!ctx->ev[i]) AH_CUDA(ctx, cudaEventCreate(&ctx->ev[i]));
+  ctx->timing = enable != 0;
+  return AH_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, const uint64_t* lens,
+                        const uint32_t* genome_ids, ah_batch** out) {
+  if (!ctx || !out || !lens || (n_rec && !seqs) || n_rec == 0) return fail(ctx, AH_EINVAL, "ah_pack_batch: bad arguments");
+  for (uint32_t r = 0; r < n_rec; ++r)
+    if (lens[r] && !seqs[r]) return fail(ctx, AH_EINVAL, "ah_pack_batch: record %u has no data", r);
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  ah_batch* b = new ah_batch();
+  ah_status st = layout_batch(ctx, n_rec, lens, genome_ids, b);
+  uint8_t* staging[2] = {nullptr, nullptr};
+  if (!st) st = dalloc(ctx, &staging[0], kChunkBases);
+  if (!st) st = dalloc(ctx, &staging[1], kChunkBases);
+  // stream records (split at chunk boundaries) through two device staging chunks
+  int which = 0;
+  uint64_t fill = 0;
+  std::vector<PackItem> items;
+  auto flush = [&]() -> ah_status {
+    ah_status s = run_pack(ctx, staging[which], items, b);
+    items.clear();
+    fill = 0;
+    which ^= 1;
+    return s;
+  };
+  for (uint32_t r = 0; r < n_rec && !st; ++r) {
+    uint64_t len = lens[r], done = 0;
+    if (len == 0) {
+      add_items(items, b, r, 0, 0, fill);
+      continue;
+    }
+    while (done < len && !st) {
+      uint64_t room = kChunkBases - fill;
+      uint64_t take = std::min(room, len - done);
+      if (take < len - done) take &= ~uint64_t(31);  // split records on group boundaries
+      if (take == 0) {
+        st = flush();
+        continue;
+      }
+      cudaError_t e = cudaMemcpyAsync(staging[which] + fill, seqs[r] + done, take, cudaMemcpyHostToDevice, ctx->stream);
+      if (e != cudaSuccess) st = fail(ctx, AH_ECUDA, "host-to-device copy failed: %s", cudaGetErrorString(e));
+      add_items(items, b, r, done, done + take, fill);
+      fill += take;
+      done += take;
+      if (fill == kChunkBases && !st) st = flush();
+    }
+  }
+  if (!st) st = flush();
+  dfree(ctx, staging[0]);
+  dfree(ctx, staging[1]);
+  if (!st) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) st = fail(ctx, AH_ECUDA, "packing failed: %s", cudaGetErrorString(e));
+  }
+  if (st) {
+    free_batch_arrays(b);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return AH_OK;
+}
+
+ah_status ah_pack_batch_device(ah_ctx* ctx, uint32_t n_rec, const uint8_t* d_seq, const uint64_t* h_offsets,
+                               const uint32_t* genome_ids, ah_batch** out) {
+  if (!ctx || !out || !h_offsets || n_rec == 0 || !d_seq) return fail(ctx, AH_EINVAL, "ah_pack_batch_device: bad arguments");
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  std::vector<uint64_t> lens(n_rec);
+  for (uint32_t r = 0; r < n_rec; ++r) {
+    if (h_offsets[r + 1] < h_offsets[r]) return fail(ctx, AH_EINVAL, "ah_pack_batch_device: offsets decrease");
+    lens[r] = h_offsets[r + 1] - h_offsets[r];
+  }
+  ah_batch* b = new ah_batch();
+  ah_status st = layout_batch(ctx, n_rec, lens.data(), genome_ids, b);
+  std::vector<PackItem> items;
+  for (uint32_t r = 0; r < n_rec && !st; ++r) add_items(items, b, r, 0, lens[r], h_offsets[r]);
+  if (!st) st = run_pack(ctx, d_seq, items, b);
+  if (st) {
+    free_batch_arrays(b);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return AH_OK;
+}
+
+ah_status ah_batch_view_get(const ah_batch* b, ah_batch_view* out) {
+  if (!b || !out) return AH_EINVAL;
+  out->n_records = b->n_records;
+  out->n_bases = b->n_bases;
+  out->n_groups = b->n_groups;
+  out->planes = b->planes;
+  out->invalid = b->invalid;
+  out->rec_group = b->rec_group;
+  out->rec_len = b->rec_len;
+  out->genome_id = b->genome_id;
+  return AH_OK;
+}
+
+void ah_batch_free(ah_batch* b) {
+  if (!b) return;
+  free_batch_arrays(b);
+  delete b;
+}
+
+// ------------------------------------------------------------------------------------------
+ah_status ah_primers_create(ah_ctx* ctx, uint32_t n_pairs, const char* const* fwd, const char* const* rev,
+                            const uint8_t* k, uint8_t clamp, ah_primers** out) {
+  if (!ctx || !out || !fwd || !rev || !k) return fail(ctx, AH_EINVAL, "ah_primers_create: NULL argument");
+  if (n_pairs == 0 || n_pairs > 256) return fail(ctx, AH_EINVAL, "ah_primers_create: n_pairs must be 1..256");
+  *out = nullptr;
+  ah_primers* p = new ah_primers();
+  p->ctx = ctx;
+  p->n_pairs = n_pairs;
+  p->clamp = clamp;
+  std::vector<uint8_t> plen(4 * n_pairs), psets(n_pairs * 2 * 32, 0);
+  for (uint32_t i = 0; i < n_pairs; ++i) {
+    for (int x = 0; x < 2; ++x) {
+      const char* s = x == 0 ? fwd[i] : rev[i];
+      if (!s) {
+        delete p;
+        return fail(ctx, AH_EINVAL, "pair %u: NULL primer", i);
+      }
+      size_t L = strlen(s);
+      if (L < 2 || L > 32 || L < clamp) {
+        delete p;
+        return fail(ctx, AH_EINVAL, "pair %u: primer length %zu outside [max(2, clamp), 32]", i, L);
+      }
+      if (k[i] > 15 || k[i] > L) {
+        delete p;
+        return fail(ctx, AH_EINVAL, "pair %u: k=%u exceeds 15 or the primer length", i, (unsigned)k[i]);
+      }
+      std::string up(L, ' ');
+      for (size_t j = 0; j < L; ++j) {
+        uint8_t set = iupac(s[j]);
+        if (!set) {
+          delete p;
+          return fail(ctx, AH_EINVAL, "pair %u: '%c' is not an IUPAC nucleotide code", i, s[j]);
+        }
+        up[j] = (char)std::toupper((unsigned char)s[j]);
+        psets[(i * 2 + x) * 32 + j] = set;
+      }
+      (x == 0 ? p->fwd : p->rev).push_back(up);
+    }
+    p->k.push_back(k[i]);
+  }
+  // oriented patterns: orient = 2 * strand + primer
+  p->pats.resize(4 * n_pairs);
+  for (uint32_t i = 0; i < n_pairs; ++i) {
+    for (int strand = 0; strand < 2; ++strand) {
+      for (int x = 0; x < 2; ++x) {
+        const std::string& s = x == 0 ? p->fwd[i] : p->rev[i];
+        const int L = (int)s.size();
+        Pattern& P = p->pats[4 * i + 2 * strand + x];
+        memset(&P, 0, sizeof P);
+        P.len = (uint8_t)L;
+        P.k = k[i];
+        P.id = (uint16_t)(4 * i + 2 * strand + x);
+        for (int j = 0; j < L; ++j)
+          P.set[j] = strand == 0 ? iupac(s[j]) : set_complement(iupac(s[L - 1 - j]));
+        // the primer's 3' end: last c positions as written, first c of the reverse complement
+        P.clamp_lo = (uint8_t)(strand == 0 ? L - clamp : 0);
+        P.clamp_hi = (uint8_t)(strand == 0 ? L : clamp);
+        plen[P.id] = (uint8_t)L;
+      }
+    }
+  }
+  ah_status st = dalloc(ctx, &p->d_plen, plen.size());
+  if (!st) st = dalloc(ctx, &p->d_psets, psets.size());
+  if (!st) {
+    cudaMemcpyAsync(p->d_plen, plen.data(), plen.size(), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(p->d_psets, psets.data(), psets.size(), cudaMemcpyHostToDevice, ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = fail(ctx, AH_ECUDA, "primer upload failed");
+  }
+  if (st) {
+    ah_primers_free(p);
+    return st;
+  }
+  *out = p;
+  return AH_OK;
+}
+
+void ah_primers_free(ah_primers* p) {
+  if (!p) return;
+  if (p->ctx) {
+    dfree(p->ctx, p->d_plen);
+    dfree(p->ctx, p->d_psets);
+  }
+  delete p;
+}
+
+// ------------------------------------------------------------------------------------------
+ah_status ah_scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out) {
+  if (!ctx || !b || !p || !out) return fail(ctx, AH_EINVAL, "ah_scan_primers: NULL argument");
+  if (b->ctx != ctx || p->ctx != ctx) return fail(ctx, AH_EINVAL, "ah_scan_primers: object from another context");
+  cudaSetDevice(ctx->device);
+  return scan_primers(ctx, b, p, out);
+}
+
+ah_status ah_hits_count(const ah_hits* h, uint64_t* n) {
+  if (!h || !n) return AH_EINVAL;
+  *n = h->n;
+  return AH_OK;
+}
+
+ah_status ah_hits_device(const ah_hits* h, const ah_hit** d_hits, const uint64_t** d_pair_offsets) {
+  if (!h) return AH_EINVAL;
+  if (d_hits) *d_hits = h->d;
+  if (d_pair_offsets) *d_pair_offsets = h->d_pair_off;
+  return AH_OK;
+}
+
+ah_status ah_hits_copy(const ah_hits* h, ah_hit* host_out, uint64_t cap) {
+  if (!h || (!host_out && cap)) return AH_EINVAL;
+  uint64_t n = std::min(cap, h->n);
+  if (n) AH_CUDA(h->ctx, cudaMemcpyAsync(host_out, h->d, n * sizeof(ah_hit), cudaMemcpyDeviceToHost, h->ctx->stream));
+  AH_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
+  return AH_OK;
+}
+
+void ah_hits_free(ah_hits* h) {
+  if (!h) return;
+  dfree(h->ctx, h->d);
+  dfree(h->ctx, h->d_pair_off);
+  delete h;
+}
+
+ah_status ah_pair_amplicons(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, uint32_t min_len,
+                            uint32_t max_len, uint32_t orient_mask, ah_amplicons** out) {
+  if (!ctx || !b || !p || !h || !out) return fail(ctx, AH_EINVAL, "ah_pair_amplicons: NULL argument");
+  if (min_len > max_len) return fail(ctx, AH_EINVAL, "ah_pair_amplicons: min_len > max_len");
+  if (h->n_pairs != p->n_pairs) return fail(ctx, AH_EINVAL, "ah_pair_amplicons: hits come from another primer set");
+  cudaSetDevice(ctx->device);
+  return pair_amplicons(ctx, b, p, h, min_len, max_len, orient_mask & 15u, out);
+}
+
+ah_status ah_tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a,
+                       const ah_tm_params* params) {
+  if (!ctx || !b || !p || !h || !a || !params) return fail(ctx, AH_EINVAL, "ah_tm_filter: NULL argument");
+  if (params->saltcorr < 0 || params->saltcorr > 6)
+    return fail(ctx, AH_EINVAL, "ah_tm_filter: salt correction method %d is not supported (0-6)", params->saltcorr);
+  cudaSetDevice(ctx->device);
+  return tm_filter(ctx, b, p, h, a, params);
+}
+
+ah_status ah_tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const char* const* cseqs,
+                         const ah_tm_params* params, double* tm_out) {
+  if (!ctx || (n && (!seqs || !cseqs || !tm_out)) || !params) return fail(ctx, AH_EINVAL, "ah_tm_duplexes: NULL argument");
+  if (params->saltcorr < 0 || params->saltcorr > 6)
+    return fail(ctx, AH_EINVAL, "ah_tm_duplexes: salt correction method %d is not supported (0-6)", params->saltcorr);
+  cudaSetDevice(ctx->device);
+  return tm_duplexes(ctx, n, seqs, cseqs, params, tm_out);
+}
+
+ah_status ah_extract_barcodes(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a,
+                              int trim, uint32_t fb_len, uint32_t rb_len) {
+  if (!ctx || !b || !p || !h || !a) return fail(ctx, AH_EINVAL, "ah_extract_barcodes: NULL argument");
+  cudaSetDevice(ctx->device);
+  return extract(ctx, b, p, h, a, trim, fb_len, rb_len);
+}
+
+ah_status ah_amplicons_count(const ah_amplicons* a, uint64_t* n) {
+  if (!a || !n) return AH_EINVAL;
+  *n = a->n;
+  return AH_OK;
+}
+
+ah_status ah_amplicons_copy(const ah_amplicons* a, ah_amplicon* host_out, uint64_t cap) {
+  if (!a || (!host_out && cap)) return AH_EINVAL;
+  uint64_t n = std::min(cap, a->n);
+  if (n) AH_CUDA(a->ctx, cudaMemcpyAsync(host_out, a->d, n * sizeof(ah_amplicon), cudaMemcpyDeviceToHost, a->ctx->stream));
+  AH_CUDA(a->ctx, cudaStreamSynchronize(a->ctx->stream));
+  return AH_OK;
+}
+
+ah_status ah_amplicons_arena_size(const ah_amplicons* a, uint64_t* bytes) {
+  if (!a || !bytes) return AH_EINVAL;
+  *bytes = a->arena_bytes;
+  return AH_OK;
+}
+
+ah_status ah_amplicons_seq_copy(const ah_amplicons* a, char* arena_out, uint64_t arena_cap, uint64_t* offsets_out,
+                                uint64_t offsets_cap) {
+  if (!a) return AH_EINVAL;
+  if (!a->d_field_off) return fail(a->ctx, AH_EINVAL, "ah_amplicons_seq_copy: sequences were not extracted");
+  if (arena_cap < a->arena_bytes || offsets_cap < 5 * a->n + 1)
+    return fail(a->ctx, AH_EOVERFLOW, "ah_amplicons_seq_copy: need %llu arena bytes and %llu offsets",
+                (unsigned long long)a->arena_bytes, (unsigned long long)(5 * a->n + 1));
+  if (a->arena_bytes)
+    AH_CUDA(a->ctx, cudaMemcpyAsync(arena_out, a->d_arena, a->arena_bytes, cudaMemcpyDeviceToHost, a->ctx->stream));
+  AH_CUDA(a->ctx, cudaMemcpyAsync(offsets_out, a->d_field_off, (5 * a->n + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                  a->ctx->stream));
+  AH_CUDA(a->ctx, cudaStreamSynchronize(a->ctx->stream));
+  return AH_OK;
+}
+
+void ah_amplicons_free(ah_amplicons* a) {
+  if (!a) return;
+  dfree(a->ctx, a->d);
+  dfree(a->ctx, a->d_arena);
+  dfree(a->ctx, a->d_field_off);
+  delete a;
+}
+
+}  // extern "C"

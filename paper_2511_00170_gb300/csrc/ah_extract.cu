@@ -1,0 +1,129 @@
+// Extraction stage (Supplementary, "Primer trimming and barcode extraction", "Headers and
+// outputs"; "Amplicon calling and orientation": RF amplicons are reverse-complemented).
+//
+// Per amplicon five fields go into one byte arena: amplicon (or trimmed interior), forward barcode,
+// reverse barcode, site i and site j in primer orientation.  A length pass and an exclusive scan
+// place every amplicon; then one warp per amplicon decodes its fields from the 2-bit planes (lanes
+// take consecutive output bytes, so stores are coalesced).
+#include "ah_internal.h"
+
+namespace ah {
+namespace {
+
+struct Fields {
+  int64_t a[5], b[5];  // top-strand ranges [a, b) per field, clipped
+  bool rc[5];          // write the range reverse-complemented
+};
+
+__device__ __forceinline__ int64_t clip(int64_t x, int64_t len) { return x < 0 ? 0 : (x > len ? len : x); }
+
+__device__ Fields fields_of(const ah_amplicon& m, const ah_hit& hi, const ah_hit& hj, const uint8_t* plen,
+                            int64_t len, int trim, int64_t fb, int64_t rb) {
+  Fields f;
+  const int64_t s_i = hi.pos, e_i = hi.pos + plen[hi.pattern], s_j = hj.pos, e_j = hj.pos + plen[hj.pattern];
+  const bool rc = m.orient == 1;
+  if (trim) {
+    f.a[0] = e_i;
+    f.b[0] = s_j < e_i ? e_i : s_j;
+  } else {
+    f.a[0] = s_i;
+    f.b[0] = e_j;
+  }
+  f.rc[0] = rc;
+  if (!rc) {
+    f.a[1] = clip(s_i - fb, len), f.b[1] = clip(s_i, len);
+    f.a[2] = clip(e_j, len), f.b[2] = clip(e_j + rb, len);
+  } else {
+    f.a[1] = clip(e_j, len), f.b[1] = clip(e_j + fb, len);
+    f.a[2] = clip(s_i - rb, len), f.b[2] = clip(s_i, len);
+  }
+  f.rc[1] = f.rc[2] = rc;
+  f.a[3] = s_i, f.b[3] = e_i, f.rc[3] = ((hi.pattern >> 1) & 1u) != 0;
+  f.a[4] = s_j, f.b[4] = e_j, f.rc[4] = ((hj.pattern >> 1) & 1u) != 0;
+  return f;
+}
+
+__global__ void k_extract_len(const ah_amplicon* __restrict__ amps, uint64_t n, const ah_hit* __restrict__ hits,
+                              const uint32_t* __restrict__ rec_len, const uint8_t* __restrict__ plen, int trim,
+                              int64_t fb, int64_t rb, uint64_t* __restrict__ total) {
+  const uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  const ah_amplicon A = amps[m];
+  const Fields f = fields_of(A, hits[A.hit_i], hits[A.hit_j], plen, rec_len[A.record], trim, fb, rb);
+  uint64_t t = 0;
+  for (int q = 0; q < 5; ++q) t += (uint64_t)(f.b[q] - f.a[q]);
+  total[m] = t;
+}
+
+__device__ __forceinline__ char decode(const uint2* planes, const uint32_t* invalid, uint64_t g0, int64_t x, bool comp) {
+  const uint64_t g = g0 + ((uint64_t)x >> 5);
+  const uint32_t bit = (uint32_t)(x & 31);
+  if ((invalid[g] >> bit) & 1u) return 'N';
+  const uint2 w = planes[g];
+  uint32_t code = ((w.x >> bit) & 1u) | (((w.y >> bit) & 1u) << 1);
+  if (comp) code ^= 2u;
+  return "ACTG"[code];
+}
+
+__global__ void k_extract_write(const ah_amplicon* __restrict__ amps, uint64_t n, const ah_hit* __restrict__ hits,
+                                const uint2* __restrict__ planes, const uint32_t* __restrict__ invalid,
+                                const uint64_t* __restrict__ rec_group, const uint32_t* __restrict__ rec_len,
+                                const uint8_t* __restrict__ plen, int trim, int64_t fb, int64_t rb,
+                                const uint64_t* __restrict__ base, char* __restrict__ arena,
+                                uint64_t* __restrict__ field_off) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t m = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (m >= n) return;
+  const ah_amplicon A = amps[m];
+  const Fields f = fields_of(A, hits[A.hit_i], hits[A.hit_j], plen, rec_len[A.record], trim, fb, rb);
+  const uint64_t g0 = rec_group[A.record];
+  uint64_t w = base[m];
+  for (int q = 0; q < 5; ++q) {
+    if (lane == 0) field_off[5 * m + q] = w;
+    const int64_t len = f.b[q] - f.a[q];
+    for (int64_t i = lane; i < len; i += 32) {
+      // reverse complement: output i takes top-strand base b-1-i, complemented
+      arena[w + i] = f.rc[q] ? decode(planes, invalid, g0, f.b[q] - 1 - i, true) : decode(planes, invalid, g0, f.a[q] + i, false);
+    }
+    w += (uint64_t)len;
+  }
+  if (m == n - 1 && lane == 0) field_off[5 * n] = w;
+}
+
+}  // namespace
+
+ah_status extract(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a, int trim,
+                  uint32_t fb, uint32_t rb) {
+  ah_status st;
+  dfree(ctx, a->d_arena);
+  dfree(ctx, a->d_field_off);
+  a->d_arena = nullptr;
+  a->d_field_off = nullptr;
+  a->arena_bytes = 0;
+  const uint64_t n = a->n;
+  uint64_t *tot = nullptr, *base = nullptr;
+  if ((st = dalloc(ctx, &tot, n)) || (st = dalloc(ctx, &base, n + 1))) return st;
+  if (n)
+    k_extract_len<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(a->d, n, h->d, b->rec_len, p->d_plen, trim,
+                                                                       (int64_t)fb, (int64_t)rb, tot);
+  if (n) launched(ctx);
+  if ((st = exclusive_scan_u64(ctx, tot, base, n))) return st;
+  uint64_t bytes = 0;
+  if ((st = read_u64(ctx, base + n, &bytes))) return st;
+  if ((st = dalloc(ctx, &a->d_arena, bytes)) || (st = dalloc(ctx, &a->d_field_off, 5 * n + 1))) return st;
+  if (n) {
+    k_extract_write<<<(unsigned)((n + 7) / 8), 256, 0, ctx->stream>>>(a->d, n, h->d, b->planes, b->invalid, b->rec_group,
+                                                                     b->rec_len, p->d_plen, trim, (int64_t)fb,
+                                                                     (int64_t)rb, base, a->d_arena, a->d_field_off);
+    launched(ctx);
+  } else {
+    AH_CUDA(ctx, cudaMemsetAsync(a->d_field_off, 0, sizeof(uint64_t), ctx->stream));
+  }
+  AH_CUDA(ctx, cudaGetLastError());
+  a->arena_bytes = bytes;
+  dfree(ctx, tot);
+  dfree(ctx, base);
+  return AH_OK;
+}
+
+}  // namespace ah

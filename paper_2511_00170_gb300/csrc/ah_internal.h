@@ -1,0 +1,180 @@
+// Internal declarations shared by the engine's translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ah.h"
+
+namespace ah {
+
+// Base codes of the packed layout: A=0, C=1, T=2, G=3 (bit 0 = ASCII bit 1, bit 1 = ASCII bit 2).
+// An IUPAC code is held as a 4-bit set over these codes: bit c set iff code c is allowed.
+enum : uint8_t { SET_A = 1, SET_C = 2, SET_T = 4, SET_G = 8 };
+
+// Geometry shared by kernels and host code.
+constexpr int kGroupBases = 32;            // bases per plane word
+constexpr int kTailGroups = 64;            // zero groups after the last record
+constexpr uint64_t kChunkBases = 64ull << 20;  // host->device streaming chunk (16 MB packed)
+
+// Device status word bits (set by kernels, read by synchronising calls).
+enum : uint32_t {
+  ST_SCAN_MISMATCH = 1u << 0,   // bit-sliced matcher and exact re-check disagree
+  ST_PAIR_OVERFLOW = 1u << 1,
+  ST_BAD_INPUT = 1u << 2,
+};
+
+struct Pattern {
+  uint8_t set[32];     // IUPAC set per position, 5'->3' of the oriented pattern on the top strand
+  uint8_t len;
+  uint8_t clamp_lo;    // clamp positions [clamp_lo, clamp_hi) must match
+  uint8_t clamp_hi;
+  uint8_t k;
+  uint16_t id;         // 4 * pair + orient
+};
+
+struct ScanConfig {
+  int threads = 256;        // threads per CTA
+  int groups_per_thread = 4;
+  int slot_cap = 256;       // hit slots per tile before overflow
+};
+
+class JitCache;
+
+}  // namespace ah
+
+struct ah_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  uint32_t* d_status = nullptr;      // device status word
+  uint32_t* h_status = nullptr;      // pinned mirror
+  std::unique_ptr<ah::JitCache> jit;
+  ah::ScanConfig scan_cfg;
+  int sm_count = 0;
+  // diagnostics
+  uint64_t n_launches = 0;
+  uint64_t n_scan_launches = 0;
+  uint64_t scan_bases = 0;
+  double scan_ms = 0.0;
+  bool timing = false;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+struct ah_batch {
+  ah_ctx* ctx = nullptr;
+  uint32_t n_records = 0;
+  uint64_t n_bases = 0;
+  uint64_t n_groups = 0;      // covered by records (padding included)
+  uint64_t alloc_groups = 0;  // n_groups + tail
+  uint2* planes = nullptr;
+  uint32_t* invalid = nullptr;
+  uint64_t* rec_group = nullptr;
+  uint32_t* rec_len = nullptr;
+  uint32_t* genome_id = nullptr;
+  std::vector<uint64_t> h_rec_group;
+  std::vector<uint32_t> h_rec_len;
+};
+
+struct ah_primers {
+  ah_ctx* ctx = nullptr;
+  uint32_t n_pairs = 0;
+  uint8_t clamp = 0;
+  std::vector<std::string> fwd, rev;   // upper-case
+  std::vector<uint8_t> k;
+  std::vector<ah::Pattern> pats;       // 4 per pair, index 4 * pair + orient
+  // device copies for pairing / Tm / extraction
+  uint8_t* d_plen = nullptr;           // per pattern length
+  uint8_t* d_psets = nullptr;          // [n_pairs][2 primers][32] IUPAC sets of the primers as written
+};
+
+struct ah_hits {
+  ah_ctx* ctx = nullptr;
+  uint64_t n = 0;
+  uint32_t n_pairs = 0;
+  ah_hit* d = nullptr;
+  uint64_t* d_pair_off = nullptr;      // n_pairs + 1
+  std::vector<uint64_t> h_pair_off;
+};
+
+struct ah_amplicons {
+  ah_ctx* ctx = nullptr;
+  uint64_t n = 0;
+  ah_amplicon* d = nullptr;
+  char* d_arena = nullptr;
+  uint64_t arena_bytes = 0;
+  uint64_t* d_field_off = nullptr;     // 5 n + 1 when extracted
+};
+
+namespace ah {
+
+// ---- error helpers -----------------------------------------------------------------------
+ah_status fail(ah_ctx* ctx, ah_status st, const char* fmt, ...);
+#define AH_CUDA(ctx, call)                                                                      \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) return ::ah::fail((ctx), AH_ECUDA, "%s failed: %s (%s:%d)", #call, \
+                                             cudaGetErrorString(e_), __FILE__, __LINE__);       \
+  } while (0)
+
+// ---- device memory (stream-ordered pool) ---------------------------------------------------
+template <class T>
+ah_status dalloc(ah_ctx* ctx, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, AH_ENOMEM, "device allocation of %zu bytes failed: %s", count * sizeof(T),
+                                    cudaGetErrorString(e));
+  return AH_OK;
+}
+void dfree(ah_ctx* ctx, void* p);
+
+// ---- exclusive scan over counts: out[i] = sum(in[0..i)), out[n] = total ------------------------
+ah_status exclusive_scan_u32(ah_ctx* ctx, const uint32_t* d_in, uint64_t* d_out, uint64_t n);
+ah_status exclusive_scan_u64(ah_ctx* ctx, const uint64_t* d_in, uint64_t* d_out, uint64_t n);
+// read one uint64 from device memory (synchronises the stream)
+ah_status read_u64(ah_ctx* ctx, const uint64_t* d, uint64_t* h);
+// read and clear the device status word (synchronises)
+ah_status check_status(ah_ctx* ctx);
+
+// count a kernel launch of this context (diagnostics)
+inline void launched(ah_ctx* ctx, uint64_t n = 1) { ctx->n_launches += n; }
+
+// scan pipeline (ah_scan.cu)
+ah_status scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out);
+// pairing (ah_pair.cu)
+ah_status pair_amplicons(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, uint32_t min_len,
+                         uint32_t max_len, uint32_t orient_mask, ah_amplicons** out);
+// melting temperature (ah_tm.cu)
+ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a,
+                    const ah_tm_params* params);
+ah_status tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const char* const* cseqs,
+                      const ah_tm_params* params, double* out);
+// extraction (ah_extract.cu)
+ah_status extract(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a, int trim,
+                  uint32_t fb, uint32_t rb);
+
+// ---- run-time specialised scan kernels (ah_jit.cpp) ------------------------------------------
+struct ScanKernel {
+  cudaKernel_t fn = nullptr;
+  int threads = 0, groups_per_thread = 0;
+};
+std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg);
+class JitCache {
+ public:
+  ah_status get(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out);
+  ~JitCache();
+ private:
+  std::mutex mu_;
+  std::unordered_map<std::string, std::pair<cudaLibrary_t, ScanKernel>> cache_;
+};
+
+}  // namespace ah

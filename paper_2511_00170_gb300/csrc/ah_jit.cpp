@@ -1,0 +1,347 @@
+// Run-time specialisation of the scan kernel for one primer set (Supplementary, "Primer matching
+// and clamp logic": per-base IUPAC masks, mismatch counting, exact 3' clamp).
+//
+// The kernel is bit-sliced: one 32-bit word holds one bit for each of 32 consecutive genome
+// positions.  For pattern position j the genome is read through "planes" shifted by j bases
+// (a funnel shift of two consecutive plane words), so word bit b answers "does the base at
+// position p+j, p = 32g+b, belong to the IUPAC set of pattern position j?" for 32 positions at
+// once.  The mismatch bits of the non-clamp positions are summed by a carry-save tree of full
+// adders that only keeps the count up to the threshold k+1; the clamp positions are OR-ed into the
+// failure word directly.  Because each IUPAC set becomes a fixed boolean function of the two code
+// bits, and each adder a fixed three-input function, everything compiles to LOP3 and SHF
+// instructions with constant truth tables -- which is why the source is generated per primer set.
+//
+// Candidate bits are rare; they go to an out-of-line routine that re-checks the window exactly
+// (and flags any disagreement), rejects windows with invalid bases or past the record end, and
+// appends a 64-bit key to the tile's slot list.
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstring>
+#include <map>
+#include <sstream>
+
+#include "ah_internal.h"
+
+namespace ah {
+namespace {
+
+// plane kinds computed from the two code bits (lo, hi) of a group word
+enum Kind { K_A = 0, K_C, K_T, K_G, K_LO, K_HI, K_XOR, K_COUNT };
+const char* kKindName[K_COUNT] = {"A", "C", "T", "G", "LO", "HI", "XO"};
+// plane of one kind computed from the code-bit words lo<w>, hi<w>
+std::string kind_expr(int kind, int w) {
+  const std::string lo = "lo" + std::to_string(w), hi = "hi" + std::to_string(w);
+  switch (kind) {
+    case K_A: return "~(" + lo + " | " + hi + ")";
+    case K_C: return "(" + lo + " & ~" + hi + ")";
+    case K_T: return "(~" + lo + " & " + hi + ")";
+    case K_G: return "(" + lo + " & " + hi + ")";
+    case K_LO: return lo;
+    case K_HI: return hi;
+    default: return "(" + lo + " ^ " + hi + ")";
+  }
+}
+
+// IUPAC set (over codes A=1, C=2, T=4, G=8) -> the plane whose bit says "base in set", possibly
+// complemented.  Returns false for N (always matches).
+bool set_plane(uint8_t set, int* kind, bool* inverted) {
+  *inverted = false;
+  switch (set) {
+    case SET_A: *kind = K_A; return true;
+    case SET_C: *kind = K_C; return true;
+    case SET_T: *kind = K_T; return true;
+    case SET_G: *kind = K_G; return true;
+    case SET_A | SET_G: *kind = K_XOR; *inverted = true; return true;  // R: lo == hi
+    case SET_C | SET_T: *kind = K_XOR; return true;                    // Y: lo != hi
+    case SET_C | SET_G: *kind = K_LO; return true;                     // S: lo set
+    case SET_A | SET_T: *kind = K_LO; *inverted = true; return true;   // W: lo clear
+    case SET_T | SET_G: *kind = K_HI; return true;                     // K: hi set
+    case SET_A | SET_C: *kind = K_HI; *inverted = true; return true;   // M: hi clear
+    case SET_C | SET_T | SET_G: *kind = K_A; *inverted = true; return true;  // B: not A
+    case SET_A | SET_T | SET_G: *kind = K_C; *inverted = true; return true;  // D: not C
+    case SET_A | SET_C | SET_T: *kind = K_G; *inverted = true; return true;  // H: not G
+    case SET_A | SET_C | SET_G: *kind = K_T; *inverted = true; return true;  // V: not T
+    default: return false;                                                   // N
+  }
+}
+
+struct Emitter {
+  std::ostringstream os;
+  int tmp = 0;
+  std::string def(const std::string& expr) {
+    std::string n = "t" + std::to_string(tmp++);
+    os << "      const u32 " << n << " = " << expr << ";\n";
+    return n;
+  }
+};
+
+std::string plane_name(int kind, int j) { return "p" + std::string(kKindName[kind]) + "_" + std::to_string(j); }
+
+// OR-reduce with three-input ORs
+std::string or_reduce(Emitter& E, std::vector<std::string> v) {
+  if (v.empty()) return "0u";
+  while (v.size() > 1) {
+    std::vector<std::string> nv;
+    size_t i = 0;
+    for (; i + 2 < v.size(); i += 3) nv.push_back(E.def("(" + v[i] + " | " + v[i + 1] + " | " + v[i + 2] + ")"));
+    if (i + 1 < v.size()) {
+      nv.push_back(E.def("(" + v[i] + " | " + v[i + 1] + ")"));
+      i += 2;
+    }
+    for (; i < v.size(); ++i) nv.push_back(v[i]);
+    v.swap(nv);
+  }
+  return v[0];
+}
+
+// failure word of one pattern: bit set iff clamp mismatch or (#non-clamp mismatches >= k+1)
+std::string gen_pattern(Emitter& E, const Pattern& P, std::map<std::pair<int, int>, bool>& used) {
+  std::vector<std::string> fail_terms, x1;
+  for (int j = 0; j < P.len; ++j) {
+    int kind;
+    bool inv;
+    if (!set_plane(P.set[j], &kind, &inv)) continue;  // N never mismatches
+    used[{kind, j}] = true;
+    std::string pl = plane_name(kind, j);
+    std::string x = inv ? pl : "(~" + pl + ")";     // mismatch bit
+    if (j >= P.clamp_lo && j < P.clamp_hi)
+      fail_terms.push_back(x);
+    else
+      x1.push_back(x);
+  }
+  const int T = P.k + 1;  // failing count
+  if ((int)x1.size() >= T) {
+    int wsat = 1;
+    while (wsat < T) wsat *= 2;
+    if (wsat == 1) {
+      for (auto& x : x1) fail_terms.push_back(x);
+    } else {
+      std::map<int, std::vector<std::string>> bits;
+      bits[1] = x1;
+      auto carry = [&](int w, const std::string& c) {
+        if (w >= wsat)
+          fail_terms.push_back(c);
+        else
+          bits[w].push_back(c);
+      };
+      for (int w = 1; w < wsat; w *= 2) {
+        std::vector<std::string> list = bits[w];
+        while (list.size() >= 3) {
+          std::vector<std::string> nl;
+          size_t i = 0;
+          for (; i + 2 < list.size(); i += 3) {
+            const std::string &a = list[i], &b = list[i + 1], &c = list[i + 2];
+            nl.push_back(E.def("(" + a + " ^ " + b + " ^ " + c + ")"));
+            carry(2 * w, E.def("((" + a + " & " + b + ") | (" + c + " & (" + a + " | " + b + ")))"));
+          }
+          for (; i < list.size(); ++i) nl.push_back(list[i]);
+          list.swap(nl);
+        }
+        if (list.size() == 2) {
+          const std::string a = list[0], b = list[1];
+          list = {E.def("(" + a + " ^ " + b + ")")};
+          carry(2 * w, E.def("(" + a + " & " + b + ")"));
+        }
+        bits[w] = list;
+      }
+      if (T != wsat) {
+        // x >= T over the reduced low bits (weights 1 .. wsat/2), most significant first
+        std::vector<std::string> b;
+        for (int w = 1; w < wsat; w *= 2) b.push_back(bits[w].empty() ? "0u" : bits[w][0]);
+        std::string ge = "0xffffffffu";
+        for (size_t i = 0; i < b.size(); ++i) {
+          bool tbit = (T >> i) & 1;
+          ge = tbit ? "(" + b[i] + " & " + ge + ")" : "(" + b[i] + " | " + ge + ")";
+        }
+        fail_terms.push_back(E.def(ge));
+      }
+    }
+  }
+  return or_reduce(E, fail_terms);
+}
+
+const char* kPrelude = R"(
+typedef unsigned int u32;
+typedef unsigned long long u64;
+struct ScanParams {
+  const uint2* planes;
+  const u32* invalid;
+  const u64* rec_group;
+  const u32* rec_len;
+  u32 n_rec;
+  u32 slot_cap;
+  u64 group_begin;
+  u64 n_groups;
+  u64* slots;
+  u32* tile_count;
+  u32* status;
+  u64 tile_begin;
+};
+static __device__ __forceinline__ u32 fshr(u32 a, u32 b, u32 s) { return __funnelshift_r(a, b, s); }
+
+// exact re-check of candidate bits, validity, record bounds, and slot append
+static __device__ __noinline__ void emit(u32 h, int q, u64 g, uint2 a, uint2 b, const ScanParams& P, u64 tile,
+                                         u64 tile_pos) {
+  const u64 lo64 = (u64)a.x | ((u64)b.x << 32), hi64 = (u64)a.y | ((u64)b.y << 32);
+  const u64 inv64 = (u64)P.invalid[g] | ((u64)P.invalid[g + 1] << 32);
+  const int L = PLEN[q];
+  while (h) {
+    const int i = __ffs(h) - 1;
+    h &= h - 1;
+    int mism = 0, clamp_bad = 0;
+    for (int j = 0; j < L; ++j) {
+      const int code = (int)((lo64 >> (i + j)) & 1) | ((int)((hi64 >> (i + j)) & 1) << 1);
+      if (!((PSET[q][j] >> code) & 1)) {
+        ++mism;
+        if (j >= PCLO[q] && j < PCHI[q]) clamp_bad = 1;
+      }
+    }
+    if (clamp_bad || mism > PK[q]) {
+      atomicOr(P.status, 1u);
+      continue;
+    }
+    const u64 wmask = (L == 64) ? ~0ull : ((1ull << L) - 1ull);
+    if ((inv64 >> i) & wmask) continue;
+    const u64 pos = g * 32ull + (u64)i;
+    u32 lo = 0, hi = P.n_rec;
+    while (hi - lo > 1) {
+      const u32 mid = (lo + hi) >> 1;
+      if (P.rec_group[mid] * 32ull <= pos) lo = mid; else hi = mid;
+    }
+    const u64 local = pos - P.rec_group[lo] * 32ull;
+    if (local + (u64)L > (u64)P.rec_len[lo]) continue;
+    const u64 key = ((u64)PPAIR[q] << 48) | ((pos - tile_pos) << 16) | ((u64)PORIENT[q] << 8) | (u64)mism;
+    const u32 idx = atomicAdd(P.tile_count + tile, 1u);
+    if (idx < P.slot_cap) P.slots[tile * (u64)P.slot_cap + idx] = key;
+  }
+}
+)";
+
+}  // namespace
+
+std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg) {
+  const int Q = (int)pats.size();
+  std::ostringstream os;
+  os << "// generated scan kernel: " << Q << " patterns\n";
+  os << "#define NT " << cfg.threads << "\n#define GPT " << cfg.groups_per_thread << "\n";
+  auto table = [&](const char* type, const char* name, auto get) {
+    os << "static __device__ const " << type << " " << name << "[" << Q << "] = {";
+    for (int q = 0; q < Q; ++q) os << (q ? "," : "") << (unsigned)get(pats[q]);
+    os << "};\n";
+  };
+  table("unsigned char", "PLEN", [](const Pattern& p) { return p.len; });
+  table("unsigned char", "PCLO", [](const Pattern& p) { return p.clamp_lo; });
+  table("unsigned char", "PCHI", [](const Pattern& p) { return p.clamp_hi; });
+  table("unsigned char", "PK", [](const Pattern& p) { return p.k; });
+  table("unsigned short", "PPAIR", [](const Pattern& p) { return p.id / 4; });
+  table("unsigned char", "PORIENT", [](const Pattern& p) { return p.id % 4; });
+  os << "static __device__ const unsigned char PSET[" << Q << "][32] = {";
+  for (int q = 0; q < Q; ++q) {
+    os << (q ? "," : "") << "{";
+    for (int j = 0; j < 32; ++j) os << (j ? "," : "") << (unsigned)(j < pats[q].len ? pats[q].set[j] : 15);
+    os << "}";
+  }
+  os << "};\n";
+  os << kPrelude;
+
+  // body: per group of 32 positions
+  Emitter E;
+  std::map<std::pair<int, int>, bool> used;
+  std::vector<std::string> fails(Q);
+  for (int q = 0; q < Q; ++q) fails[q] = gen_pattern(E, pats[q], used);
+  bool kind_used[K_COUNT] = {};
+  for (auto& u : used) kind_used[u.first.first] = true;
+
+  os << "extern \"C\" __global__ void __launch_bounds__(NT) ah_scan_jit(const ScanParams P) {\n";
+  os << "  const u64 tile = P.tile_begin + blockIdx.x;\n";
+  os << "  const u64 tile_first = (u64)blockIdx.x * (u64)(NT * GPT);\n";
+  os << "  const u64 tile_pos = (P.group_begin + tile_first) * 32ull;\n";
+  os << "  u64 gl = tile_first + threadIdx.x;\n";
+  os << "  uint2 na = make_uint2(0u, 0u), nb = na;\n";
+  os << "  if (gl < P.n_groups) { na = __ldg(P.planes + P.group_begin + gl); nb = __ldg(P.planes + P.group_begin + gl + 1); }\n";
+  os << "#pragma unroll 1\n";
+  os << "  for (int it = 0; it < GPT; ++it, gl += NT) {\n";
+  os << "    if (gl >= P.n_groups) break;\n";
+  os << "    const uint2 a = na, b = nb;\n";
+  os << "    const u64 gn = gl + NT;\n";
+  os << "    if (it + 1 < GPT && gn < P.n_groups) { na = __ldg(P.planes + P.group_begin + gn); nb = __ldg(P.planes + P.group_begin + gn + 1); }\n";
+  os << "    const u64 g = P.group_begin + gl;\n";
+  os << "    const u32 lo0 = a.x, hi0 = a.y, lo1 = b.x, hi1 = b.y;\n";
+  for (int k = 0; k < K_COUNT; ++k) {
+    if (!kind_used[k]) continue;
+    for (int w = 0; w < 2; ++w) os << "    const u32 " << kKindName[k] << w << " = " << kind_expr(k, w) << ";\n";
+  }
+  for (auto& u : used) {
+    int kind = u.first.first, j = u.first.second;
+    os << "    const u32 " << plane_name(kind, j) << " = ";
+    if (j == 0)
+      os << kKindName[kind] << "0;\n";
+    else
+      os << "fshr(" << kKindName[kind] << "0, " << kKindName[kind] << "1, " << j << "u);\n";
+  }
+  os << "    {\n" << E.os.str();
+  // hit words and the rare emission path, in blocks of four patterns
+  for (int q0 = 0; q0 < Q; q0 += 4) {
+    int q1 = std::min(Q, q0 + 4);
+    os << "      if (__builtin_expect((";
+    for (int q = q0; q < q1; ++q) os << (q > q0 ? " & " : "") << fails[q];
+    os << ") != 0xffffffffu, 0)) {\n";
+    for (int q = q0; q < q1; ++q)
+      os << "        if (~" << fails[q] << ") emit(~" << fails[q] << ", " << q << ", g, a, b, P, tile, tile_pos);\n";
+    os << "      }\n";
+  }
+  os << "    }\n  }\n}\n";
+  return os.str();
+}
+
+ah_status JitCache::get(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out) {
+  std::string src = scan_source(pats, cfg);
+  std::lock_guard<std::mutex> lock(mu_);
+  auto it = cache_.find(src);
+  if (it != cache_.end()) {
+    *out = it->second.second;
+    return AH_OK;
+  }
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "ah_scan_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+    return fail(ctx, AH_EJIT, "nvrtcCreateProgram failed");
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, ctx->device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, ctx->device);
+  std::string arch = "-arch=sm_" + std::to_string(major * 10 + minor) + (major >= 9 ? "a" : "");
+  const char* opts[] = {arch.c_str(), "-default-device", "-lineinfo"};
+  nvrtcResult r = nvrtcCompileProgram(prog, 3, opts);
+  if (r != NVRTC_SUCCESS) {
+    size_t n = 0;
+    nvrtcGetProgramLogSize(prog, &n);
+    std::string log(n, '\0');
+    nvrtcGetProgramLog(prog, &log[0]);
+    nvrtcDestroyProgram(&prog);
+    return fail(ctx, AH_EJIT, "scan kernel compilation failed: %s", log.substr(0, 2000).c_str());
+  }
+  size_t cubin_size = 0;
+  nvrtcGetCUBINSize(prog, &cubin_size);
+  std::vector<char> cubin(cubin_size);
+  nvrtcGetCUBIN(prog, cubin.data());
+  nvrtcDestroyProgram(&prog);
+  // the runtime's library API keeps the engine free of a link-time driver dependency
+  cudaLibrary_t lib;
+  cudaError_t ce = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (ce != cudaSuccess) return fail(ctx, AH_EJIT, "cudaLibraryLoadData failed: %s", cudaGetErrorString(ce));
+  ScanKernel k;
+  ce = cudaLibraryGetKernel(&k.fn, lib, "ah_scan_jit");
+  if (ce != cudaSuccess) return fail(ctx, AH_EJIT, "cudaLibraryGetKernel failed: %s", cudaGetErrorString(ce));
+  k.threads = cfg.threads;
+  k.groups_per_thread = cfg.groups_per_thread;
+  cache_.emplace(src, std::make_pair(lib, k));
+  *out = k;
+  return AH_OK;
+}
+
+JitCache::~JitCache() {
+  for (auto& kv : cache_) cudaLibraryUnload(kv.second.first);
+}
+
+}  // namespace ah

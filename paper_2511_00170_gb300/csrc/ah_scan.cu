@@ -1,0 +1,255 @@
+// Scan stage (Supplementary, "Primer matching and clamp logic"; "We sort candidate sites"):
+//   1. the run-time specialised bit-sliced kernel marks candidate sites and appends a 64-bit key
+//      (pair | tile-local position | orient | mismatches) to its tile's slot list;
+//   2. each tile's keys are sorted (warp bitonic sort in shared memory) and counted per pair;
+//   3. an exclusive scan over the pair-major (pair, tile) counts gives every tile's output range;
+//   4. keys become ah_hit records (record lookup by binary search) in (pair, record, pos, orient)
+//      order, so pairing needs no global sort.
+#include <algorithm>
+
+#include "ah_internal.h"
+
+namespace ah {
+namespace {
+
+// must match the ScanParams of the generated source
+struct ScanParamsHost {
+  const uint2* planes;
+  const uint32_t* invalid;
+  const uint64_t* rec_group;
+  const uint32_t* rec_len;
+  uint32_t n_rec;
+  uint32_t slot_cap;
+  uint64_t group_begin;
+  uint64_t n_groups;
+  uint64_t* slots;
+  uint32_t* tile_count;
+  uint32_t* status;
+  uint64_t tile_begin;
+};
+
+__global__ void k_tile_max(const uint32_t* __restrict__ tile_count, uint64_t n_tiles, uint32_t* __restrict__ out) {
+  uint32_t m = 0;
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n_tiles; t += (uint64_t)gridDim.x * blockDim.x)
+    m = max(m, tile_count[t]);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+__device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* a, uint32_t n, uint64_t key) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// one warp per tile: sort the tile's keys in shared memory, write them back, count per pair
+__global__ void k_tile_sort(uint64_t* __restrict__ slots, const uint32_t* __restrict__ tile_count, uint32_t cap,
+                            uint32_t cap_pow2, uint64_t n_tiles, uint32_t n_pairs,
+                            uint32_t* __restrict__ tile_pair_count) {
+  extern __shared__ uint64_t sm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (t >= n_tiles) return;
+  const uint32_t n = min(tile_count[t], cap);
+  if (n == 0) return;
+  uint64_t* tk = slots + t * cap;
+  if (n > 1) {
+    uint32_t m = 2;
+    while (m < n) m <<= 1;
+    uint64_t* buf = sm + (uint64_t)warp * cap_pow2;
+    for (uint32_t i = lane; i < m; i += 32) buf[i] = i < n ? tk[i] : ~0ull;
+    __syncwarp();
+    for (uint32_t k = 2; k <= m; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = lane; i < m; i += 32) {
+          const uint32_t ixj = i ^ j;
+          if (ixj > i) {
+            const uint64_t a = buf[i], b = buf[ixj];
+            const bool up = (i & k) == 0;
+            if ((a > b) == up) {
+              buf[i] = b;
+              buf[ixj] = a;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    for (uint32_t i = lane; i < n; i += 32) tk[i] = buf[i];
+    __syncwarp();
+  }
+  // per-pair counts from the sorted keys (pair in the top 16 bits)
+  const uint32_t p_first = (uint32_t)(tk[0] >> 48), p_last = (uint32_t)(tk[n - 1] >> 48);
+  for (uint32_t p = p_first + lane; p <= p_last && p < n_pairs; p += 32) {
+    const uint32_t a = lower_bound_u64(tk, n, (uint64_t)p << 48);
+    const uint32_t b = lower_bound_u64(tk, n, (uint64_t)(p + 1) << 48);
+    if (b > a) tile_pair_count[(uint64_t)p * n_tiles + t] = b - a;
+  }
+}
+
+// one warp per tile: sorted keys -> hit records at their pair-major output positions
+__global__ void k_emit_hits(const uint64_t* __restrict__ slots, const uint32_t* __restrict__ tile_count, uint32_t cap,
+                            uint64_t n_tiles, uint64_t tile_groups, const uint64_t* __restrict__ off,
+                            const uint64_t* __restrict__ rec_group, uint32_t n_rec, ah_hit* __restrict__ hits) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (t >= n_tiles) return;
+  const uint32_t n = min(tile_count[t], cap);
+  const uint64_t* tk = slots + t * cap;
+  const uint64_t tile_pos = t * tile_groups * 32ull;
+  for (uint32_t i = lane; i < n; i += 32) {
+    const uint64_t key = tk[i];
+    const uint32_t pair = (uint32_t)(key >> 48);
+    const uint32_t first = lower_bound_u64(tk, n, (uint64_t)pair << 48);
+    const uint64_t o = off[(uint64_t)pair * n_tiles + t] + (i - first);
+    const uint64_t pos = tile_pos + ((key >> 16) & 0xffffffffull);
+    uint32_t lo = 0, hi = n_rec;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (rec_group[mid] * 32ull <= pos) lo = mid; else hi = mid;
+    }
+    ah_hit h;
+    h.record = lo;
+    h.pos = (uint32_t)(pos - rec_group[lo] * 32ull);
+    h.pattern = (uint16_t)(pair * 4u + ((key >> 8) & 3u));
+    h.mism = (uint8_t)(key & 0xffu);
+    h.flags = 0;
+    hits[o] = h;
+  }
+}
+
+__global__ void k_pair_offsets(const uint64_t* __restrict__ off, uint64_t n_tiles, uint32_t n_pairs,
+                               uint64_t* __restrict__ pair_off) {
+  uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p <= n_pairs) pair_off[p] = off[(uint64_t)p * n_tiles];
+}
+
+}  // namespace
+
+ah_status scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out) {
+  *out = nullptr;
+  ScanConfig cfg = ctx->scan_cfg;
+  const uint32_t n_pairs = p->n_pairs;
+  ah_status st;
+  uint64_t* slots = nullptr;
+  uint32_t* tile_count = nullptr;
+  uint32_t* d_max = nullptr;
+  if ((st = dalloc(ctx, &d_max, 1))) return st;
+  uint64_t n_tiles = 0, tile_groups = 0;
+  uint32_t cap = (uint32_t)cfg.slot_cap;
+  for (int attempt = 0;; ++attempt) {
+    ScanKernel kern;
+    if ((st = ctx->jit->get(ctx, p->pats, cfg, &kern))) break;
+    tile_groups = (uint64_t)cfg.threads * cfg.groups_per_thread;
+    n_tiles = std::max<uint64_t>(1, (b->n_groups + tile_groups - 1) / tile_groups);
+    if ((st = dalloc(ctx, &slots, n_tiles * cap))) break;
+    if ((st = dalloc(ctx, &tile_count, n_tiles))) break;
+    AH_CUDA(ctx, cudaMemsetAsync(tile_count, 0, n_tiles * sizeof(uint32_t), ctx->stream));
+    AH_CUDA(ctx, cudaMemsetAsync(d_max, 0, sizeof(uint32_t), ctx->stream));
+    ScanParamsHost P{b->planes, b->invalid, b->rec_group, b->rec_len, b->n_records, cap, 0, b->n_groups,
+                     slots, tile_count, ctx->d_status, 0};
+    if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
+    for (uint64_t t0 = 0; t0 < n_tiles; t0 += 0x7fffffffull) {
+      uint64_t nt = std::min<uint64_t>(0x7fffffffull, n_tiles - t0);
+      P.tile_begin = t0;
+      P.group_begin = t0 * tile_groups;
+      P.n_groups = std::min<uint64_t>(b->n_groups - std::min(b->n_groups, P.group_begin), nt * tile_groups);
+      void* args[] = {&P};
+      cudaError_t le = cudaLaunchKernel((const void*)kern.fn, dim3((unsigned)nt), dim3((unsigned)cfg.threads), args, 0,
+                                        ctx->stream);
+      if (le != cudaSuccess) return fail(ctx, AH_ECUDA, "scan kernel launch failed: %s", cudaGetErrorString(le));
+      launched(ctx);
+      ctx->n_scan_launches++;
+    }
+    if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
+    ctx->scan_bases += b->n_bases;
+    k_tile_max<<<std::max<uint64_t>(1, std::min<uint64_t>(1024, (n_tiles + 255) / 256)), 256, 0, ctx->stream>>>(
+        tile_count, n_tiles, d_max);
+    launched(ctx);
+    uint32_t mx = 0;
+    AH_CUDA(ctx, cudaMemcpyAsync(ctx->h_status + 0, d_max, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    mx = *ctx->h_status;
+    *ctx->h_status = 0;
+    if (ctx->timing) {
+      float ms = 0.f;
+      AH_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+      ctx->scan_ms += ms;
+    }
+    if (mx <= cap) break;
+    // a tile overflowed: retry with room for the fullest tile, shrinking tiles when that is large
+    dfree(ctx, slots);
+    dfree(ctx, tile_count);
+    slots = nullptr;
+    tile_count = nullptr;
+    uint32_t need = 1;
+    while (need < mx) need <<= 1;
+    if (need <= 4096) {
+      cap = need;
+    } else {
+      cap = 4096;
+      if (cfg.groups_per_thread > 1) cfg.groups_per_thread = 1;
+      else if (cfg.threads > 64) cfg.threads /= 2;
+      else return fail(ctx, AH_EOVERFLOW, "scan: more than %u sites in a tile of %d groups", mx, cfg.threads);
+    }
+  }
+  if (st) {
+    dfree(ctx, slots);
+    dfree(ctx, tile_count);
+    dfree(ctx, d_max);
+    return st;
+  }
+  // sort each tile, count per (pair, tile)
+  uint32_t* tpc = nullptr;
+  uint64_t* off = nullptr;
+  const uint64_t n_cells = (uint64_t)n_pairs * n_tiles;
+  if ((st = dalloc(ctx, &tpc, n_cells))) return st;
+  if ((st = dalloc(ctx, &off, n_cells + 1))) return st;
+  AH_CUDA(ctx, cudaMemsetAsync(tpc, 0, n_cells * sizeof(uint32_t), ctx->stream));
+  uint32_t cap_pow2 = 2;
+  while (cap_pow2 < cap) cap_pow2 <<= 1;
+  int warps = (int)std::max<uint32_t>(1, std::min<uint32_t>(8, 16384 / cap_pow2));
+  size_t smem = (size_t)warps * cap_pow2 * sizeof(uint64_t);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  uint64_t blocks = (n_tiles + warps - 1) / warps;
+  k_tile_sort<<<(unsigned)blocks, warps * 32, smem, ctx->stream>>>(slots, tile_count, cap, cap_pow2, n_tiles, n_pairs,
+                                                                     tpc);
+  launched(ctx);
+  AH_CUDA(ctx, cudaGetLastError());
+  if ((st = exclusive_scan_u32(ctx, tpc, off, n_cells))) return st;
+  uint64_t total = 0;
+  if ((st = read_u64(ctx, off + n_cells, &total))) return st;
+  ah_hits* h = new ah_hits();
+  h->ctx = ctx;
+  h->n = total;
+  h->n_pairs = n_pairs;
+  if ((st = dalloc(ctx, &h->d, total)) || (st = dalloc(ctx, &h->d_pair_off, n_pairs + 1))) {
+    ah_hits_free(h);
+    return st;
+  }
+  k_emit_hits<<<(unsigned)((n_tiles + 7) / 8), 256, 0, ctx->stream>>>(slots, tile_count, cap, n_tiles, tile_groups, off,
+                                                                      b->rec_group, b->n_records, h->d);
+  k_pair_offsets<<<(n_pairs + 256) / 256, 256, 0, ctx->stream>>>(off, n_tiles, n_pairs, h->d_pair_off);
+  launched(ctx, 2);
+  AH_CUDA(ctx, cudaGetLastError());
+  h->h_pair_off.resize(n_pairs + 1);
+  AH_CUDA(ctx, cudaMemcpyAsync(h->h_pair_off.data(), h->d_pair_off, (n_pairs + 1) * sizeof(uint64_t),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  dfree(ctx, slots);
+  dfree(ctx, tile_count);
+  dfree(ctx, d_max);
+  dfree(ctx, tpc);
+  dfree(ctx, off);
+  if ((st = check_status(ctx))) {
+    ah_hits_free(h);
+    return st;
+  }
+  *out = h;
+  return AH_OK;
+}
+
+}  // namespace ah

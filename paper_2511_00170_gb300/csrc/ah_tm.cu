@@ -1,0 +1,418 @@
+// Melting-temperature stage (Section "Implementations": AHv2 reimplements Biopython's Tm_NN in
+// double precision; Section "Primer degeneracy": Tm is evaluated for the primer's variants).
+//
+// Every site gets the maximum, over the concrete variants of its (degenerate) primer, of the
+// nearest-neighbour Tm of the variant paired with the site; an amplicon gets the lower of its two
+// site values.  All arithmetic is FP64: the Tm threshold decision needs it.  The parameter tables
+// below are expanded on the host into direct lookups indexed by the four base codes of a step
+// (top 5'-ab-3' over bottom 3'-xy-5'), so a step costs one constant-memory load.
+#include <cmath>
+#include <cstring>
+
+#include "ah_internal.h"
+
+namespace ah {
+namespace {
+
+struct Step {
+  char a, b, x, y;  // 5'-ab-3' over 3'-xy-5'
+  double dh, ds;    // kcal/mol, cal/(K mol)
+};
+
+// Watson-Crick nearest-neighbour stacks (Allawi & SantaLucia 1997, Biochemistry 36:10581).
+const Step kStacks[] = {
+    {'A', 'A', 'T', 'T', -7.9, -22.2}, {'A', 'T', 'T', 'A', -7.2, -20.4}, {'T', 'A', 'A', 'T', -7.2, -21.3},
+    {'C', 'A', 'G', 'T', -8.5, -22.7}, {'G', 'T', 'C', 'A', -8.4, -22.4}, {'C', 'T', 'G', 'A', -7.8, -21.0},
+    {'G', 'A', 'C', 'T', -8.2, -22.2}, {'C', 'G', 'G', 'C', -10.6, -27.2}, {'G', 'C', 'C', 'G', -9.8, -24.4},
+    {'G', 'G', 'C', 'C', -8.0, -19.9},
+};
+
+// Internal mismatches adjacent to a Watson-Crick pair and the tandem G.T steps:
+// G.T (Allawi & SantaLucia 1997), G.A (Allawi & SantaLucia 1998, Biochemistry 37:2170),
+// C.T (Allawi & SantaLucia 1998, Nucleic Acids Res 26:2694), A.C (Allawi & SantaLucia 1998,
+// Biochemistry 37:9435), A.A / C.C / G.G / T.T (Peyret et al. 1999, Biochemistry 38:3468).
+const Step kInternal[] = {
+    // G.T
+    {'A', 'G', 'T', 'T', 1.0, 0.9}, {'A', 'T', 'T', 'G', -2.5, -8.3}, {'C', 'G', 'G', 'T', -4.1, -11.7},
+    {'C', 'T', 'G', 'G', -2.8, -8.0}, {'G', 'G', 'C', 'T', 3.3, 10.4}, {'G', 'G', 'T', 'T', 5.8, 16.3},
+    {'G', 'T', 'C', 'G', -4.4, -12.3}, {'G', 'T', 'T', 'G', 4.1, 9.5}, {'T', 'G', 'A', 'T', -0.1, -1.7},
+    {'T', 'G', 'G', 'T', -1.4, -6.2}, {'T', 'T', 'A', 'G', -1.3, -5.3},
+    // G.A
+    {'A', 'A', 'T', 'G', -0.6, -2.3}, {'A', 'G', 'T', 'A', -0.7, -2.3}, {'C', 'A', 'G', 'G', -0.7, -2.3},
+    {'C', 'G', 'G', 'A', -4.0, -13.2}, {'G', 'A', 'C', 'G', -0.6, -1.0}, {'G', 'G', 'C', 'A', 0.5, 3.2},
+    {'T', 'A', 'A', 'G', 0.7, 0.7}, {'T', 'G', 'A', 'A', 3.0, 7.4},
+    // C.T
+    {'A', 'C', 'T', 'T', 0.7, 0.2}, {'A', 'T', 'T', 'C', -1.2, -6.2}, {'C', 'C', 'G', 'T', -0.8, -4.5},
+    {'C', 'T', 'G', 'C', -1.5, -6.1}, {'G', 'C', 'C', 'T', 2.3, 5.4}, {'G', 'T', 'C', 'C', 5.2, 13.5},
+    {'T', 'C', 'A', 'T', 1.2, 0.7}, {'T', 'T', 'A', 'C', 1.0, 0.7},
+    // A.C
+    {'A', 'A', 'T', 'C', 2.3, 4.6}, {'A', 'C', 'T', 'A', 5.3, 14.6}, {'C', 'A', 'G', 'C', 1.9, 3.7},
+    {'C', 'C', 'G', 'A', 0.6, -0.6}, {'G', 'A', 'C', 'C', 5.2, 14.2}, {'G', 'C', 'C', 'A', -0.7, -3.8},
+    {'T', 'A', 'A', 'C', 3.4, 8.0}, {'T', 'C', 'A', 'A', 7.6, 20.2},
+    // A.A, C.C, G.G, T.T
+    {'A', 'A', 'T', 'A', 1.2, 1.7}, {'C', 'A', 'G', 'A', -0.9, -4.2}, {'G', 'A', 'C', 'A', -2.9, -9.8},
+    {'T', 'A', 'A', 'A', 4.7, 12.9}, {'A', 'C', 'T', 'C', 0.0, -4.4}, {'C', 'C', 'G', 'C', -1.5, -7.2},
+    {'G', 'C', 'C', 'C', 3.6, 8.9}, {'T', 'C', 'A', 'C', 6.1, 16.4}, {'A', 'G', 'T', 'G', -3.1, -9.5},
+    {'C', 'G', 'G', 'G', -4.9, -15.3}, {'G', 'G', 'C', 'G', -6.0, -15.8}, {'T', 'G', 'A', 'G', 1.6, 3.6},
+    {'A', 'T', 'T', 'T', -2.7, -10.8}, {'C', 'T', 'G', 'T', -5.0, -15.8}, {'G', 'T', 'C', 'T', -2.2, -8.4},
+    {'T', 'T', 'A', 'T', 0.2, -1.5},
+};
+
+// Terminal mismatches: 5'-ab-3'/3'-xy-5' with a.x Watson-Crick and the end pair b.y mismatched
+// (SantaLucia & Peyret 2001, WO 01/94611).
+const Step kTerminal[] = {
+    {'A', 'A', 'T', 'A', -3.1, -7.8},  {'T', 'A', 'A', 'A', -2.5, -6.3},  {'C', 'A', 'G', 'A', -4.3, -10.7},
+    {'G', 'A', 'C', 'A', -8.0, -22.5}, {'A', 'C', 'T', 'C', -0.1, 0.5},   {'T', 'C', 'A', 'C', -0.7, -1.3},
+    {'C', 'C', 'G', 'C', -2.1, -5.1},  {'G', 'C', 'C', 'C', -3.9, -10.6}, {'A', 'G', 'T', 'G', -1.1, -2.1},
+    {'T', 'G', 'A', 'G', -1.1, -2.7},  {'C', 'G', 'G', 'G', -3.8, -9.5},  {'G', 'G', 'C', 'G', -0.7, -19.2},
+    {'A', 'T', 'T', 'T', -2.4, -6.5},  {'T', 'T', 'A', 'T', -3.2, -8.9},  {'C', 'T', 'G', 'T', -6.1, -16.9},
+    {'G', 'T', 'C', 'T', -7.4, -21.2}, {'A', 'A', 'T', 'C', -1.6, -4.0},  {'A', 'C', 'T', 'A', -1.8, -3.8},
+    {'C', 'A', 'G', 'C', -2.6, -5.9},  {'C', 'C', 'G', 'A', -2.7, -6.0},  {'G', 'A', 'C', 'C', -5.0, -13.8},
+    {'G', 'C', 'C', 'A', -3.2, -7.1},  {'T', 'A', 'A', 'C', -2.3, -5.9},  {'T', 'C', 'A', 'A', -2.7, -7.0},
+    {'A', 'C', 'T', 'T', -0.9, -1.7},  {'A', 'T', 'T', 'C', -2.3, -6.3},  {'C', 'C', 'G', 'T', -3.2, -8.0},
+    {'C', 'T', 'G', 'C', -3.9, -10.6}, {'G', 'C', 'C', 'T', -4.9, -13.5}, {'G', 'T', 'C', 'C', -3.0, -7.8},
+    {'T', 'C', 'A', 'T', -2.5, -6.3},  {'T', 'T', 'A', 'C', -0.7, -1.2},  {'A', 'A', 'T', 'G', -1.9, -4.4},
+    {'A', 'G', 'T', 'A', -2.5, -5.9},  {'C', 'A', 'G', 'G', -3.9, -9.6},  {'C', 'G', 'G', 'A', -6.0, -15.5},
+    {'G', 'A', 'C', 'G', -4.3, -11.1}, {'G', 'G', 'C', 'A', -4.6, -11.4}, {'T', 'A', 'A', 'G', -2.0, -4.7},
+    {'T', 'G', 'A', 'A', -2.4, -5.8},  {'A', 'G', 'T', 'T', -3.2, -8.7},  {'A', 'T', 'T', 'G', -3.5, -9.4},
+    {'C', 'G', 'G', 'T', -3.8, -9.0},  {'C', 'T', 'G', 'G', -6.6, -18.7}, {'G', 'G', 'C', 'T', -5.7, -15.9},
+    {'G', 'T', 'C', 'G', -5.9, -16.1}, {'T', 'G', 'A', 'T', -3.9, -10.5}, {'T', 'T', 'A', 'G', -3.6, -9.8},
+};
+
+// Initiation terms of the same parameter set.
+constexpr double kInitH = 0.0, kInitS = 0.0;
+constexpr double kTermATH = 2.3, kTermATS = 4.1;
+constexpr double kTermGCH = 0.1, kTermGCS = -2.8;
+constexpr double kOneGCH = 0.0, kOneGCS = 0.0, kAllATH = 0.0, kAllATS = 0.0, k5TAH = 0.0, k5TAS = 0.0;
+
+struct NNTables {
+  double step_h[256], step_s[256];  // NaN: no parameter
+  double term_h[256], term_s[256];  // NaN: not a terminal-mismatch step
+};
+__constant__ NNTables c_nn;
+
+int code_of(char c) {  // A=0, C=1, T=2, G=3
+  switch (c) {
+    case 'A': return 0;
+    case 'C': return 1;
+    case 'T': return 2;
+    default: return 3;
+  }
+}
+int idx4(int a, int b, int x, int y) { return a * 64 + b * 16 + x * 4 + y; }
+
+void build_tables(NNTables* t) {
+  const double nan = std::nan("");
+  for (int i = 0; i < 256; ++i) t->step_h[i] = t->step_s[i] = t->term_h[i] = t->term_s[i] = nan;
+  // step lookup: internal-mismatch entry as written, then read from the other strand, then the
+  // Watson-Crick entry as written, then read from the other strand
+  auto put = [&](const Step* v, int n, bool reversed) {
+    for (int i = 0; i < n; ++i) {
+      const Step& s = v[i];
+      int k = reversed ? idx4(code_of(s.y), code_of(s.x), code_of(s.b), code_of(s.a))
+                       : idx4(code_of(s.a), code_of(s.b), code_of(s.x), code_of(s.y));
+      if (std::isnan(t->step_h[k])) {
+        t->step_h[k] = s.dh;
+        t->step_s[k] = s.ds;
+      }
+    }
+  };
+  put(kInternal, sizeof kInternal / sizeof kInternal[0], false);
+  put(kInternal, sizeof kInternal / sizeof kInternal[0], true);
+  put(kStacks, sizeof kStacks / sizeof kStacks[0], false);
+  put(kStacks, sizeof kStacks / sizeof kStacks[0], true);
+  for (const Step& s : kTerminal) {
+    int k = idx4(code_of(s.a), code_of(s.b), code_of(s.x), code_of(s.y));
+    t->term_h[k] = s.dh;
+    t->term_s[k] = s.ds;
+  }
+}
+
+std::mutex g_tables_mu;
+bool g_tables_loaded[64] = {};
+
+ah_status load_tables(ah_ctx* ctx) {
+  std::lock_guard<std::mutex> lock(g_tables_mu);
+  if (ctx->device < 64 && g_tables_loaded[ctx->device]) return AH_OK;
+  static NNTables host;
+  build_tables(&host);
+  AH_CUDA(ctx, cudaMemcpyToSymbolAsync(c_nn, &host, sizeof host, 0, cudaMemcpyHostToDevice, ctx->stream));
+  AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->device < 64) g_tables_loaded[ctx->device] = true;
+  return AH_OK;
+}
+
+// run constants computed once on the host
+struct TmRun {
+  double rlnk;       // R ln(C)
+  double ln_mon;     // ln of the monovalent-equivalent concentration (M)
+  double corr_const; // methods 1-4: Tm correction
+  int saltcorr;
+  int selfcomp;
+};
+
+ah_status make_run(ah_ctx* ctx, const ah_tm_params* p, TmRun* r) {
+  double mon_mM = p->Na + p->K + p->Tris / 2.0;
+  if ((p->K + p->Mg + p->Tris + p->dNTPs) > 0 && p->dNTPs < p->Mg) mon_mM += 120.0 * std::sqrt(p->Mg - p->dNTPs);
+  const double mon = mon_mM * 1e-3;
+  if (p->saltcorr != 0 && !(mon > 0)) return fail(ctx, AH_EINVAL, "Tm: salt correction needs a positive cation concentration");
+  const double conc = (p->dnac1 - p->dnac2 / 2.0) * 1e-9;
+  if (!(conc > 0)) return fail(ctx, AH_EINVAL, "Tm: strand concentrations give C <= 0");
+  r->rlnk = 1.987 * std::log(conc);
+  r->ln_mon = p->saltcorr ? std::log(mon) : 0.0;
+  r->saltcorr = p->saltcorr;
+  r->selfcomp = 0;
+  switch (p->saltcorr) {
+    case 1: r->corr_const = 16.6 * std::log10(mon); break;
+    case 2: r->corr_const = 16.6 * std::log10(mon / (1.0 + 0.7 * mon)); break;
+    case 3: r->corr_const = 12.5 * std::log10(mon); break;
+    case 4: r->corr_const = 11.7 * std::log10(mon); break;
+    default: r->corr_const = 0.0;
+  }
+  return AH_OK;
+}
+
+// Tm of variant v (codes, 5'->3') over c (codes of the opposite strand, 3'->5'); false if undefined
+__device__ bool duplex_tm(const uint8_t* v, const uint8_t* c, int L, const TmRun& R, double* tm) {
+  double dh = 0.0, ds = 0.0;
+  int lo = 0, hi = L;
+  {
+    // left end read from the opposite strand: 5'-c1 c0-3' over 3'-v1 v0-5'
+    const int k = c[1] * 64 + c[0] * 16 + v[1] * 4 + v[0];
+    const double th = c_nn.term_h[k];
+    if (!isnan(th)) {
+      dh += th;
+      ds += c_nn.term_s[k];
+      lo = 1;
+    }
+  }
+  if (hi - lo >= 2) {
+    const int k = v[L - 2] * 64 + v[L - 1] * 16 + c[L - 2] * 4 + c[L - 1];
+    const double th = c_nn.term_h[k];
+    if (!isnan(th)) {
+      dh += th;
+      ds += c_nn.term_s[k];
+      hi = L - 1;
+    }
+  }
+  // initiation, from the variant's own end bases (A=0, C=1, T=2, G=3: A/T have bit 0 clear)
+  dh += kInitH;
+  ds += kInitS;
+  int gc = 0;
+  for (int j = 0; j < L; ++j) gc += v[j] & 1;
+  if (gc == 0) {
+    dh += kAllATH;
+    ds += kAllATS;
+  } else {
+    dh += kOneGCH;
+    ds += kOneGCS;
+  }
+  if (v[0] == 2) {  // 5' T
+    dh += k5TAH;
+    ds += k5TAS;
+  }
+  if (v[L - 1] == 0) {  // 3' A
+    dh += k5TAH;
+    ds += k5TAS;
+  }
+  if (v[0] & 1) { dh += kTermGCH; ds += kTermGCS; } else { dh += kTermATH; ds += kTermATS; }
+  if (v[L - 1] & 1) { dh += kTermGCH; ds += kTermGCS; } else { dh += kTermATH; ds += kTermATS; }
+  for (int i = lo; i + 1 < hi; ++i) {
+    const int k = v[i] * 64 + v[i + 1] * 16 + c[i] * 4 + c[i + 1];
+    const double sh = c_nn.step_h[k];
+    if (isnan(sh)) return false;
+    dh += sh;
+    ds += c_nn.step_s[k];
+  }
+  double corr = 0.0;
+  if (R.saltcorr == 5) {
+    ds += 0.368 * (double)(L - 1) * R.ln_mon;
+  } else if (R.saltcorr == 6) {
+    const double f = (double)gc / (double)L;
+    corr = (4.29 * f - 3.95) * 1e-5 * R.ln_mon + 9.40e-6 * R.ln_mon * R.ln_mon;
+  } else {
+    corr = R.corr_const;
+  }
+  double t = (1000.0 * dh) / (ds + R.rlnk) - 273.15;
+  if (R.saltcorr >= 1 && R.saltcorr <= 4) t += corr;
+  if (R.saltcorr == 6) t = 1.0 / (1.0 / (t + 273.15) + corr) - 273.15;
+  *tm = t;
+  return true;
+}
+
+// maximum over the concrete variants of `sets` (IUPAC sets over codes) paired with site `s`
+__device__ double site_tm(const uint8_t* sets, const uint8_t* s, int L, const TmRun& R) {
+  uint8_t v[32], c[32], choice[32][4], nch[32], idx[32];
+  for (int j = 0; j < L; ++j) {
+    c[j] = s[j] ^ 2u;  // complement code
+    nch[j] = 0;
+    for (int code = 0; code < 4; ++code)
+      if ((sets[j] >> code) & 1) choice[j][nch[j]++] = (uint8_t)code;
+    idx[j] = 0;
+  }
+  double best = -INFINITY;
+  bool any = false;
+  for (;;) {
+    for (int j = 0; j < L; ++j) v[j] = choice[j][idx[j]];
+    double t;
+    if (duplex_tm(v, c, L, R, &t)) {
+      any = true;
+      best = fmax(best, t);
+    }
+    int j = L - 1;
+    while (j >= 0) {
+      if (++idx[j] < nch[j]) break;
+      idx[j] = 0;
+      --j;
+    }
+    if (j < 0) break;
+  }
+  return any ? best : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+__device__ __forceinline__ uint8_t base_code(const uint2* planes, uint64_t group0, uint64_t x) {
+  const uint2 w = planes[group0 + (x >> 5)];
+  const uint32_t bit = (uint32_t)(x & 31);
+  return (uint8_t)(((w.x >> bit) & 1u) | (((w.y >> bit) & 1u) << 1));
+}
+
+__global__ void k_tm_hits(const ah_hit* __restrict__ hits, uint64_t n, const uint2* __restrict__ planes,
+                          const uint64_t* __restrict__ rec_group, const uint8_t* __restrict__ plen,
+                          const uint8_t* __restrict__ psets, const TmRun R, double* __restrict__ out) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const ah_hit h = hits[i];
+  const int L = plen[h.pattern];
+  const uint32_t pair = h.pattern >> 2, primer = h.pattern & 1u, strand = (h.pattern >> 1) & 1u;
+  const uint64_t g0 = rec_group[h.record];
+  uint8_t site[32], sets[32];
+  for (int j = 0; j < L; ++j) {
+    // site bases in the primer's 5'->3' orientation
+    site[j] = strand == 0 ? base_code(planes, g0, (uint64_t)h.pos + j)
+                          : (uint8_t)(base_code(planes, g0, (uint64_t)h.pos + L - 1 - j) ^ 2u);
+    sets[j] = psets[(pair * 2 + primer) * 32 + j];
+  }
+  out[i] = site_tm(sets, site, L, R);
+}
+
+__global__ void k_tm_amps(ah_amplicon* __restrict__ a, uint64_t n, const double* __restrict__ hit_tm, int filter,
+                          double min_tm, uint32_t* __restrict__ keep) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  ah_amplicon m = a[i];
+  const double ti = hit_tm[m.hit_i], tj = hit_tm[m.hit_j];
+  const bool undefined = isnan(ti) || isnan(tj);
+  const double t = undefined ? __longlong_as_double(0x7ff8000000000000ll) : fmin(ti, tj);
+  uint8_t flags = 0;
+  bool k = !filter || (!undefined && t >= min_tm);
+  if (k) flags |= 1;
+  if (!undefined && fabs(t - min_tm) <= 1e-9) flags |= 2;
+  if (undefined) flags |= 4;
+  m.tm = t;
+  m.flags = flags;
+  a[i] = m;
+  if (keep) keep[i] = k ? 1u : 0u;
+}
+
+__global__ void k_compact_amps(const ah_amplicon* __restrict__ in, uint64_t n, const uint32_t* __restrict__ keep,
+                               const uint64_t* __restrict__ off, ah_amplicon* __restrict__ out) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && keep[i]) out[off[i]] = in[i];
+}
+
+__global__ void k_tm_duplexes(const uint8_t* __restrict__ v, const uint8_t* __restrict__ c,
+                              const uint32_t* __restrict__ len, uint32_t n, const TmRun R, double* __restrict__ out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double t;
+  out[i] = duplex_tm(v + 32 * (uint64_t)i, c + 32 * (uint64_t)i, (int)len[i], R, &t)
+               ? t
+               : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+}  // namespace
+
+ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a,
+                    const ah_tm_params* params) {
+  ah_status st;
+  if ((st = load_tables(ctx))) return st;
+  TmRun R;
+  if ((st = make_run(ctx, params, &R))) return st;
+  double* hit_tm = nullptr;
+  uint32_t* keep = nullptr;
+  if ((st = dalloc(ctx, &hit_tm, h->n))) return st;
+  if (h->n)
+    k_tm_hits<<<(unsigned)((h->n + 127) / 128), 128, 0, ctx->stream>>>(h->d, h->n, b->planes, b->rec_group, p->d_plen,
+                                                                      p->d_psets, R, hit_tm);
+  if (h->n) launched(ctx);
+  if (params->filter && (st = dalloc(ctx, &keep, a->n))) return st;
+  if (a->n)
+    k_tm_amps<<<(unsigned)((a->n + 255) / 256), 256, 0, ctx->stream>>>(a->d, a->n, hit_tm, params->filter,
+                                                                      params->min_tm, keep);
+  if (a->n) launched(ctx);
+  AH_CUDA(ctx, cudaGetLastError());
+  if (params->filter) {
+    uint64_t* off;
+    if ((st = dalloc(ctx, &off, a->n + 1))) return st;
+    if ((st = exclusive_scan_u32(ctx, keep, off, a->n))) return st;
+    uint64_t kept = 0;
+    if ((st = read_u64(ctx, off + a->n, &kept))) return st;
+    ah_amplicon* nd;
+    if ((st = dalloc(ctx, &nd, kept))) return st;
+    if (a->n)
+      k_compact_amps<<<(unsigned)((a->n + 255) / 256), 256, 0, ctx->stream>>>(a->d, a->n, keep, off, nd);
+    if (a->n) launched(ctx);
+    AH_CUDA(ctx, cudaGetLastError());
+    dfree(ctx, a->d);
+    dfree(ctx, off);
+    a->d = nd;
+    a->n = kept;
+  }
+  dfree(ctx, hit_tm);
+  dfree(ctx, keep);
+  return AH_OK;
+}
+
+ah_status tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const char* const* cseqs,
+                      const ah_tm_params* params, double* out) {
+  ah_status st;
+  if ((st = load_tables(ctx))) return st;
+  TmRun R;
+  if ((st = make_run(ctx, params, &R))) return st;
+  if (n == 0) return AH_OK;
+  std::vector<uint8_t> v(32 * (size_t)n, 0), c(32 * (size_t)n, 0);
+  std::vector<uint32_t> len(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    size_t L = strlen(seqs[i]);
+    if (L < 2 || L > 32 || strlen(cseqs[i]) != L) return fail(ctx, AH_EINVAL, "duplex %u: lengths must match, 2..32", i);
+    for (size_t j = 0; j < L; ++j) {
+      char a = (char)toupper((unsigned char)seqs[i][j]), x = (char)toupper((unsigned char)cseqs[i][j]);
+      if (!strchr("ACGT", a) || !strchr("ACGT", x) || !a || !x)
+        return fail(ctx, AH_EINVAL, "duplex %u: only A, C, G, T are allowed", i);
+      v[32 * (size_t)i + j] = (uint8_t)code_of(a);
+      c[32 * (size_t)i + j] = (uint8_t)code_of(x);
+    }
+    len[i] = (uint32_t)L;
+  }
+  uint8_t *dv, *dc;
+  uint32_t* dl;
+  double* dout;
+  if ((st = dalloc(ctx, &dv, v.size())) || (st = dalloc(ctx, &dc, c.size())) || (st = dalloc(ctx, &dl, n)) ||
+      (st = dalloc(ctx, &dout, n)))
+    return st;
+  AH_CUDA(ctx, cudaMemcpyAsync(dv, v.data(), v.size(), cudaMemcpyHostToDevice, ctx->stream));
+  AH_CUDA(ctx, cudaMemcpyAsync(dc, c.data(), c.size(), cudaMemcpyHostToDevice, ctx->stream));
+  AH_CUDA(ctx, cudaMemcpyAsync(dl, len.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+  k_tm_duplexes<<<(n + 127) / 128, 128, 0, ctx->stream>>>(dv, dc, dl, n, R, dout);
+  launched(ctx);
+  AH_CUDA(ctx, cudaGetLastError());
+  AH_CUDA(ctx, cudaMemcpyAsync(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  dfree(ctx, dv);
+  dfree(ctx, dc);
+  dfree(ctx, dl);
+  dfree(ctx, dout);
+  return AH_OK;
+}
+
+}  // namespace ah

@@ -1,0 +1,86 @@
+"""Helpers that put the CUDA path's outputs and the oracle's into one comparable form.
+
+The CUDA path orders hits by (pair, record, pos, orient) and amplicons by (anchor, partner);
+the oracle orders by (record, pair, pos, strand, primer).  Both are unique orders of the same
+sets, so comparisons sort both sides by the same keys and compare element by element.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, List, Tuple
+
+import numpy as np
+
+TM_TOL = 1e-9  # degrees C
+
+
+def gpu_hit_tuples(h) -> List[Tuple]:
+    p = h["pattern"].astype(np.int64)
+    out = list(zip(h["record"].tolist(), (p >> 2).tolist(), h["pos"].tolist(), ((p >> 1) & 1).tolist(),
+                   (p & 1).tolist(), h["mism"].tolist()))
+    return sorted(out)
+
+
+def oracle_hit_tuples(h) -> List[Tuple]:
+    return sorted(zip(h["record"].tolist(), h["pair"].tolist(), h["pos"].tolist(), h["strand"].tolist(),
+                      h["primer"].tolist(), h["mism"].tolist()))
+
+
+def _gpu_site(h, i):
+    x = h[i]
+    return (int(x["pos"]), int((x["pattern"] >> 1) & 1), int(x["pattern"] & 1))
+
+
+def _or_site(h, i):
+    x = h[i]
+    return (int(x["pos"]), int(x["strand"]), int(x["primer"]))
+
+
+def gpu_amp_keys(out) -> List[Tuple]:
+    return [(int(a["record"]), int(a["pair"]), int(a["start"]), int(a["end"]), int(a["orient"]),
+             _gpu_site(out.hits, a["hit_i"]), _gpu_site(out.hits, a["hit_j"])) for a in out.amps]
+
+
+def oracle_amp_keys(hits, amps) -> List[Tuple]:
+    return [(int(a["record"]), int(a["pair"]), int(a["start"]), int(a["end"]), int(a["orient"]),
+             _or_site(hits, a["hit_i"]), _or_site(hits, a["hit_j"])) for a in amps]
+
+
+def assert_same_hits(out, ref):
+    g, o = gpu_hit_tuples(out.hits), oracle_hit_tuples(ref.hits)
+    assert len(g) == len(o), f"hit count {len(g)} vs oracle {len(o)}"
+    for a, b in zip(g, o):
+        assert a == b, f"hit {a} vs oracle {b}"
+
+
+def assert_same_amplicons(out, ref, filtered: bool):
+    """filtered: the CUDA output went through the Tm filter (compare with the oracle's kept set)."""
+    ref_amps = ref.amps[ref.keep] if filtered else ref.amps
+    ref_tm = ref.amp_tm[ref.keep] if filtered else ref.amp_tm
+    ref_st = ref.amp_status[ref.keep] if filtered else ref.amp_status
+    gk = gpu_amp_keys(out)
+    ok = oracle_amp_keys(ref.hits, ref_amps)
+    assert sorted(gk) == sorted(ok), f"amplicon sets differ: {len(gk)} vs oracle {len(ok)}"
+    ref_by: Dict[Tuple, Tuple[float, int]] = {k: (float(t), int(s)) for k, t, s in zip(ok, ref_tm, ref_st)}
+    worst = 0.0
+    for k, a in zip(gk, out.amps):
+        t, s = ref_by[k]
+        undefined = bool(a["flags"] & 4)
+        assert undefined == bool(s), f"Tm definedness differs at {k}"
+        if not undefined:
+            d = abs(float(a["tm"]) - t)
+            worst = max(worst, d)
+            assert d <= TM_TOL, f"Tm {a['tm']!r} vs oracle {t!r} at {k}"
+        else:
+            assert math.isnan(float(a["tm"]))
+    return worst
+
+
+def assert_same_sequences(out, ref):
+    """Sequences of the kept amplicons (the oracle extracts only kept ones, in order)."""
+    ok = oracle_amp_keys(ref.hits, ref.amps[ref.keep])
+    ref_seq = dict(zip(ok, ref.seqs))
+    gk = gpu_amp_keys(out)
+    assert len(gk) == len(ok)
+    for m, k in enumerate(gk):
+        assert out.fields(m) == ref_seq[k], f"sequence fields differ at {k}"

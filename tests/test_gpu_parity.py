@@ -1,0 +1,198 @@
+"""CUDA path vs oracle, element by element, through the C ABI (needs a GPU).
+
+Hits, amplicons, orientations, trimmed sequences, barcodes and primer snippets must match the
+oracle exactly; Tm must agree within 1e-9 C (FP64 on both sides; the tolerance covers summation
+order and libm differences, ~1e-13 relative).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def engine():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2511_00170_gb300.pipeline import Engine
+
+    e = Engine(0)
+    yield e
+    e.close()
+
+
+def _run_both(engine, wl, filtered=True):
+    from paper_2511_00170_gb300.pipeline import Params
+
+    ref = oracle.run(wl)
+    p = Params.from_workload(wl)
+    p_unf = Params.from_workload(wl)
+    p_unf.min_tm = None
+    batch = engine.pack(wl.seq, wl.offsets, wl.genome_ids)
+    try:
+        out_unf = engine.step(batch, p_unf, with_seqs=False)
+        out = engine.step(batch, p, with_seqs=True)
+    finally:
+        from paper_2511_00170_gb300 import ah
+
+        ah.ah_batch_free(batch)
+    compare.assert_same_hits(out_unf, ref)
+    compare.assert_same_hits(out, ref)
+    compare.assert_same_amplicons(out_unf, ref, filtered=False)
+    compare.assert_same_amplicons(out, ref, filtered=wl.tm.min_tm is not None)
+    compare.assert_same_sequences(out, ref)
+    return out, ref
+
+
+def _random_case(seed):
+    st = synth.Stream(synth.make_key(seed, 555, 0))
+    wl = synth.random_small(seed, n_records=st.randint(1, 6), len_lo=0, len_hi=st.choice([300, 2000, 5000]),
+                            n_pairs=st.randint(1, 3), plen_lo=st.randint(4, 12), plen_hi=st.randint(12, 26),
+                            n_deg=st.randint(0, 5), k_max=st.randint(0, 4), clamp=st.randint(0, 4),
+                            n_frac=st.choice([0.0, 0.01, 0.05]), alphabet=st.choice(["ACGT", "ACGTacgt", "AT", "ACGTTTTT"]),
+                            plant=st.randint(0, 4), min_len=st.randint(1, 60), max_len=st.randint(60, 1500),
+                            fb=st.randint(0, 20), rb=st.randint(0, 20), trim=bool(st.randint(0, 1)))
+    if st.randint(0, 1):
+        wl.tm.min_tm = float(st.randint(-20, 40))
+    wl.tm.saltcorr = st.choice([5, 5, 5, 0, 1, 2, 3, 4, 6])
+    wl.tm.Na = float(st.choice([50, 10, 200]))
+    return wl
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_small(engine, seed):
+    _run_both(engine, _random_case(seed))
+
+
+def test_plain_small_full(engine):
+    """The 16-genome single-pair workload (U(1,3) Mbp, k=2, clamp 3, Tm >= 45 C), every output."""
+    out, ref = _run_both(engine, synth.plain_small())
+    assert len(ref.hits) > 0 and len(ref.amps) > 0 and ref.keep.any()
+
+
+def test_edge_records(engine):
+    """Empty records, records shorter than the primers, exact 64-base multiples, all-N, lower case."""
+    recs = ["", "A", "ACG", "ACGTACGTAC" * 6 + "ACGT", "N" * 100, "acgtagctagctgatcgatgctagctagctgatcgat" * 5,
+            "ACGT" * 16, "ACGT" * 16 + "A", "ACGT" * 16 + "ACG", "TTTTTTTTTTTTTTTTTTTTTTTTTTTTTTTT" * 3, ""]
+    wl = synth.random_small(1, n_records=1, len_lo=10, len_hi=10, n_pairs=1, plant=0)
+    wl.seq = np.frombuffer("".join(recs).encode(), dtype=np.uint8).copy()
+    wl.offsets = np.cumsum([0] + [len(r) for r in recs]).astype(np.int64)
+    wl.genome_ids = np.arange(len(recs), dtype=np.uint32)
+    for fwd, rev, k, clamp in [("ACGTA", "TACGT", 0, 0), ("ACGTA", "TACGT", 1, 5), ("AGCTAGCTGATC", "GATCGATG", 3, 2),
+                               ("TTTTTTTT", "AAAAAAAA", 2, 3), ("NN", "AC", 0, 1), ("ACGTACGTACGTACGTACGTACGTACGTACGT",
+                                                                                 "TTTTTTTTTTTTTTTTTTTTTTTTTTTTTTTT", 15, 3)]:
+        wl.fwd, wl.rev, wl.k, wl.clamp = [fwd], [rev], [k], clamp
+        wl.min_len, wl.max_len, wl.fb_len, wl.rb_len, wl.trim = 1, 500, 7, 9, True
+        _run_both(engine, wl)
+
+
+def test_dense_sites_overflow_retry(engine):
+    """Every window of a homopolymer run is a site: tiles overflow their slot lists and are re-run."""
+    g = "A" * 300_000 + "ACGT" * 1000 + "T" * 200_000
+    wl = synth.random_small(2, n_records=1, len_lo=10, len_hi=10, n_pairs=1, plant=0)
+    wl.seq = np.frombuffer(g.encode(), dtype=np.uint8).copy()
+    wl.offsets = np.array([0, len(g)], dtype=np.int64)
+    wl.fwd, wl.rev, wl.k, wl.clamp = ["AAAAAAAAAA"], ["AAAAAAAAAAAA"], [1], 2
+    wl.min_len, wl.max_len, wl.orient_mask = 20, 60, 15
+    wl.fb_len = wl.rb_len = 3
+    out, ref = _run_both(engine, wl)
+    assert len(ref.hits) > 500_000
+
+
+def test_several_pairs(engine):
+    wl = synth.batched(n_genomes=40, len_lo=2e3, len_hi=2e5, n_pairs=8)
+    _run_both(engine, wl)
+
+
+def test_deterministic(engine):
+    from paper_2511_00170_gb300.pipeline import Params
+
+    wl = synth.plain_small(n_genomes=4, len_lo=200_000, len_hi=400_000)
+    a = engine.run_workload(wl)
+    b = engine.run_workload(wl)
+    assert a.hits.tobytes() == b.hits.tobytes()
+    assert a.amps.tobytes() == b.amps.tobytes()
+    assert a.arena == b.arena
+
+
+COMP = {"A": "T", "C": "G", "G": "C", "T": "A"}
+
+
+def test_tm_duplexes(engine):
+    """Random duplexes, 2-32 nt, 0-5 mismatches anywhere (every internal and terminal table entry is
+    reached), all salt methods."""
+    from paper_2511_00170_gb300 import ah
+
+    st = synth.Stream(synth.make_key(3, 901, 0))
+    seqs, cseqs = [], []
+    for _ in range(20000):
+        L = st.randint(2, 32)
+        s = "".join(st.choice("ACGT") for _ in range(L))
+        c = [COMP[x] for x in s]
+        for _ in range(st.randint(0, 5)):
+            p = st.randint(0, L - 1)
+            c[p] = st.choice([b for b in "ACGT" if b != COMP[s[p]]])
+        seqs.append(s)
+        cseqs.append("".join(c))
+    worst = 0.0
+    for method, na in [(5, 50.0), (0, 50.0), (1, 20.0), (2, 100.0), (3, 50.0), (4, 10.0), (6, 50.0)]:
+        tmp = synth.TmParams(Na=na, saltcorr=method)
+        got = ah.ah_tm_duplexes(engine.ctx, seqs, cseqs, ah.tm_params(Na=na, saltcorr=method))
+        for s, c, g in zip(seqs, cseqs, got):
+            r = oracle.tm_duplex(s, c, tmp)
+            if r is None:
+                assert math.isnan(g), (s, c)
+            else:
+                worst = max(worst, abs(g - r))
+                assert abs(g - r) <= compare.TM_TOL, (s, c, g, r)
+    assert worst <= compare.TM_TOL
+
+
+def test_pack_layout(engine):
+    """Planes and invalid words against the layout in include/ah.h, read back from the device."""
+    import torch
+
+    from paper_2511_00170_gb300 import ah
+
+    wl = synth.random_small(9, n_records=5, len_lo=0, len_hi=700, n_frac=0.05, alphabet="ACGTacgtRYN")
+    batch = engine.pack(wl.seq, wl.offsets)
+    try:
+        v = ah.ah_batch_view_get(batch)
+        n = v["n_groups"]
+
+        class _Dev:
+            def __init__(self, ptr, shape, typestr):
+                self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3}
+
+        planes = torch.as_tensor(_Dev(v["planes"], (n, 2), "<u4"), device="cuda").cpu().numpy()
+        inval = torch.as_tensor(_Dev(v["invalid"], (n,), "<u4"), device="cuda").cpu().numpy()
+        rg = torch.as_tensor(_Dev(v["rec_group"], (wl.n_records,), "<u8"), device="cuda").cpu().numpy()
+    finally:
+        ah.ah_batch_free(batch)
+    code = {"A": 0, "C": 1, "T": 2, "G": 3}
+    expect_lo = np.zeros(n * 32, dtype=np.uint8)
+    expect_hi = np.zeros(n * 32, dtype=np.uint8)
+    expect_inv = np.ones(n * 32, dtype=np.uint8)
+    g = 0
+    for r in range(wl.n_records):
+        s = wl.record_str(r)
+        assert rg[r] == g and g % 2 == 0
+        for i, ch in enumerate(s):
+            c = ch.upper()
+            if c in code:
+                expect_lo[g * 32 + i] = code[c] & 1
+                expect_hi[g * 32 + i] = code[c] >> 1
+                expect_inv[g * 32 + i] = 0
+        g += ((len(s) + 63) // 64) * 2
+    assert g == n
+    bits = lambda w: np.unpackbits(w.astype("<u4").view(np.uint8), bitorder="little")
+    assert np.array_equal(bits(planes[:, 0]), expect_lo)
+    assert np.array_equal(bits(planes[:, 1]), expect_hi)
+    assert np.array_equal(bits(inval), expect_inv)
