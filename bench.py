@@ -143,7 +143,8 @@ def oracle_sample_seconds(wl, n_genomes):
 
 def pick_sample(wl, target_s):
     """Number of leading genomes whose oracle run takes about target_s on the host cores."""
-    t1, bp1 = oracle_sample_seconds(wl, min(2, wl.n_records))
+    # the oracle runs records in parallel, so calibrate on one record per host core
+    t1, bp1 = oracle_sample_seconds(wl, min(os.cpu_count() or 1, wl.n_records))
     rate = bp1 / max(t1, 1e-3)
     want = rate * target_s
     n, acc = 0, 0
