@@ -192,6 +192,31 @@ typedef struct {
 ah_status ah_pair_amplicons(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h,
                             uint32_t min_len, uint32_t max_len, uint32_t orient_mask, ah_amplicons** out);
 
+/* Allocation-free pairing (the paper has no counterpart; this exists for callers of the library).
+ * Some callers cannot allocate device memory while they run this step: an application that has
+ * handed all of the GPU's memory to its own pool before loading the library, or a latency-bound
+ * loop that cannot accept a cudaMalloc and the synchronisation it brings.  This call does the same
+ * pairing as ah_pair_amplicons on buffers the caller owns and allocates nothing:
+ *   d_hits, n_hits      sites in ah_scan_primers order (device), e.g. from ah_hits_device();
+ *   d_pair_offsets      per-pair site ranges, n_pairs + 1 entries (device);
+ *   d_pattern_len       primer length per pattern id 4 * pair + orient (device, uint8);
+ *   d_out, out_capacity amplicon records (device) and their capacity;
+ *   *n_out              (host) number of amplicons found, also when they do not fit.
+ * Returns AH_EINVAL when n_hits exceeds AH_PAIR_NOALLOC_MAX_SITES (1,048,576) or an argument is
+ * missing, AH_EOVERFLOW (with *n_out set, nothing written) when the amplicons exceed out_capacity.
+ * Scratch memory is one file-scope device array of about 12 MiB (partner counts, prefix sums and
+ * block sums for up to AH_PAIR_NOALLOC_MAX_SITES sites); every GPU that loads the library holds it
+ * until the process exits.  The first call on a device looks up that array's device address, so
+ * make it before any stream capture.  All calls share the array: calls whose work overlaps on the
+ * GPU (other streams, other threads) race and must be serialised by the caller.  The call works on
+ * the current device and enqueues on `cuda_stream`; it waits for the count pass, then returns with
+ * the emit pass enqueued. */
+#define AH_PAIR_NOALLOC_MAX_SITES (1u << 20)
+ah_status ah_pair_amplicons_noalloc(void* cuda_stream, const ah_hit* d_hits, uint64_t n_hits,
+                                    const uint64_t* d_pair_offsets, const uint8_t* d_pattern_len, uint32_t min_len,
+                                    uint32_t max_len, uint32_t orient_mask, ah_amplicon* d_out,
+                                    uint64_t out_capacity, uint64_t* n_out);
+
 /* ------------------------------------------------------------------------------------------ */
 /* 4. melting temperature                                                                       */
 

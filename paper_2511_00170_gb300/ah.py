@@ -74,6 +74,8 @@ SIGNATURES = {
     "ah_hits_copy": (_I32, [_VP, _VP, _U64]),
     "ah_hits_free": (None, [_VP]),
     "ah_pair_amplicons": (_I32, [_VP, _VP, _VP, _VP, _U32, _U32, _U32, _PVP]),
+    "ah_pair_amplicons_noalloc": (_I32, [_VP, _VP, _U64, _VP, _VP, _U32, _U32, _U32, _VP, _U64,
+                                         ctypes.POINTER(ctypes.c_uint64)]),
     "ah_tm_filter": (_I32, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ah_tm_params)]),
     "ah_tm_duplexes": (_I32, [_VP, _U32, _VP, _VP, ctypes.POINTER(ah_tm_params), _VP]),
     "ah_extract_barcodes": (_I32, [_VP, _VP, _VP, _VP, _VP, _I32, _U32, _U32]),
@@ -232,6 +234,21 @@ def ah_pair_amplicons(ctx, batch, primers, hits, min_len: int, max_len: int, ori
     out = ctypes.c_void_p()
     _check(load().ah_pair_amplicons(ctx, batch, primers, hits, min_len, max_len, orient_mask, ctypes.byref(out)), ctx)
     return out
+
+
+AH_PAIR_NOALLOC_MAX_SITES = 1 << 20
+
+
+def ah_pair_amplicons_noalloc(stream: int, d_hits: int, n_hits: int, d_pair_offsets: int, d_pattern_len: int,
+                              min_len: int, max_len: int, orient_mask: int, d_out: int, out_capacity: int) -> int:
+    """Pairing on caller-owned device buffers, allocating nothing (see include/ah.h).  Returns the
+    number of amplicons written to d_out."""
+    n = ctypes.c_uint64()
+    st = load().ah_pair_amplicons_noalloc(stream, d_hits, n_hits, d_pair_offsets, d_pattern_len, min_len, max_len,
+                                          orient_mask, d_out, out_capacity, ctypes.byref(n))
+    if st != AH_OK:
+        raise AhError(st, f"ah_pair_amplicons_noalloc ({n.value} amplicons found)")
+    return n.value
 
 
 # ------------------------------------------------------------------------------------------ Tm

@@ -100,3 +100,154 @@ ah_status pair_amplicons(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
 }
 
 }  // namespace ah
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free pairing.
+//
+// Some callers cannot allocate device memory while they run this step. One example is an
+// application that hands all of the GPU's memory to its own pool before it loads this library.
+// Another is a latency-bound loop where a cudaMalloc, with its implicit synchronisation, is not
+// acceptable. ah_pair_amplicons_noalloc gives them the pairing stage with every buffer supplied by
+// the caller. Its only scratch memory (per-site partner counts, their prefix sums and per-block
+// partial sums) lives in the file-scope array below, sized for kNoAllocMaxSites sites and held by
+// every GPU that loads the library until the process exits.
+namespace ah {
+namespace {
+
+constexpr uint64_t kNoAllocMaxSites = 1ull << 20;
+constexpr int kNaThreads = 256;
+constexpr int kNaItems = 8;
+constexpr uint64_t kNaTile = (uint64_t)kNaThreads * kNaItems;
+constexpr uint64_t kNaBlocks = (kNoAllocMaxSites + kNaTile - 1) / kNaTile;  // 512
+constexpr size_t kNaCountsOff = 0;
+constexpr size_t kNaOffsetsOff = kNoAllocMaxSites * sizeof(uint32_t);
+constexpr size_t kNaSumsOff = kNaOffsetsOff + ((kNoAllocMaxSites + 1) * sizeof(uint64_t) + 255) / 256 * 256;
+constexpr size_t kNaScratchBytes = kNaSumsOff + kNaBlocks * sizeof(uint64_t);
+
+static __device__ __align__(256) unsigned char g_pair_scratch[kNaScratchBytes];
+
+// device address of g_pair_scratch per device, resolved once with that device current
+std::mutex g_na_mu;
+unsigned char* g_na_addr[64] = {};
+
+cudaError_t na_scratch(int device, unsigned char** out) {
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_na_mu);
+  if (!g_na_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_pair_scratch);
+    if (e != cudaSuccess) return e;
+    g_na_addr[device] = (unsigned char*)p;
+  }
+  *out = g_na_addr[device];
+  return cudaSuccess;
+}
+
+__device__ __forceinline__ uint64_t na_block_exclusive(uint64_t v, uint64_t* total) {
+  __shared__ uint64_t ws[kNaThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t s = lane < kNaThreads / 32 ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kNaThreads / 32) ws[lane] = s;
+  }
+  __syncthreads();
+  const uint64_t before = (warp ? ws[warp - 1] : 0) + x - v;
+  *total = ws[kNaThreads / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+// each thread owns kNaItems consecutive counts; pass 1 writes per-block sums
+__global__ void k_na_sums(const uint32_t* __restrict__ counts, uint64_t n, uint64_t* __restrict__ sums) {
+  const uint64_t base = (uint64_t)blockIdx.x * kNaTile + (uint64_t)threadIdx.x * kNaItems;
+  uint64_t s = 0;
+  for (int i = 0; i < kNaItems; ++i)
+    if (base + i < n) s += counts[base + i];
+  uint64_t total;
+  na_block_exclusive(s, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// one CTA: exclusive scan of at most kNaBlocks block sums (two per thread); total -> offsets[n]
+__global__ void k_na_scan_sums(uint64_t* __restrict__ sums, uint64_t nb, uint64_t* __restrict__ total_out) {
+  const uint64_t i0 = 2 * (uint64_t)threadIdx.x, i1 = i0 + 1;
+  const uint64_t a = i0 < nb ? sums[i0] : 0, b = i1 < nb ? sums[i1] : 0;
+  uint64_t total;
+  const uint64_t ex = na_block_exclusive(a + b, &total);
+  if (i0 < nb) sums[i0] = ex;
+  if (i1 < nb) sums[i1] = ex + a;
+  if (threadIdx.x == 0) *total_out = total;
+}
+
+__global__ void k_na_apply(const uint32_t* __restrict__ counts, uint64_t n, const uint64_t* __restrict__ sums,
+                           uint64_t* __restrict__ offsets) {
+  const uint64_t base = (uint64_t)blockIdx.x * kNaTile + (uint64_t)threadIdx.x * kNaItems;
+  uint64_t v[kNaItems], s = 0;
+  for (int i = 0; i < kNaItems; ++i) {
+    v[i] = base + i < n ? counts[base + i] : 0;
+    s += v[i];
+  }
+  uint64_t total;
+  uint64_t ex = na_block_exclusive(s, &total) + sums[blockIdx.x];
+  for (int i = 0; i < kNaItems; ++i) {
+    if (base + i < n) offsets[base + i] = ex;
+    ex += v[i];
+  }
+}
+
+}  // namespace
+}  // namespace ah
+
+extern "C" ah_status ah_pair_amplicons_noalloc(void* cuda_stream, const ah_hit* d_hits, uint64_t n_hits,
+                                               const uint64_t* d_pair_offsets, const uint8_t* d_pattern_len,
+                                               uint32_t min_len, uint32_t max_len, uint32_t orient_mask,
+                                               ah_amplicon* d_out, uint64_t out_capacity, uint64_t* n_out) {
+  using namespace ah;
+  if (!n_out || min_len > max_len) return AH_EINVAL;
+  *n_out = 0;
+  if (n_hits > kNoAllocMaxSites) return AH_EINVAL;
+  if (n_hits && (!d_hits || !d_pair_offsets || !d_pattern_len)) return AH_EINVAL;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return AH_ECUDA;
+  unsigned char* scratch = nullptr;
+  if (na_scratch(device, &scratch) != cudaSuccess) return AH_ECUDA;
+  if (n_hits == 0) return AH_OK;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  uint32_t* counts = (uint32_t*)(scratch + kNaCountsOff);
+  uint64_t* offsets = (uint64_t*)(scratch + kNaOffsetsOff);
+  uint64_t* sums = (uint64_t*)(scratch + kNaSumsOff);
+  const unsigned blocks = (unsigned)((n_hits + 255) / 256);
+  const unsigned nb = (unsigned)((n_hits + kNaTile - 1) / kNaTile);
+  // every count, offset and block sum for the n_hits sites is written before it is read, so the
+  // previous call's contents need no clearing
+  k_pair_walk<false><<<blocks, 256, 0, stream>>>(d_hits, n_hits, d_pair_offsets, d_pattern_len, min_len, max_len,
+                                                 orient_mask & 15u, counts, nullptr, nullptr);
+  k_na_sums<<<nb, kNaThreads, 0, stream>>>(counts, n_hits, sums);
+  k_na_scan_sums<<<1, kNaThreads, 0, stream>>>(sums, nb, offsets + n_hits);
+  k_na_apply<<<nb, kNaThreads, 0, stream>>>(counts, n_hits, sums, offsets);
+  if (cudaGetLastError() != cudaSuccess) return AH_ECUDA;
+  uint64_t total = 0;
+  if (cudaMemcpyAsync(&total, offsets + n_hits, sizeof total, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return AH_ECUDA;
+  *n_out = total;
+  if (total > out_capacity) return AH_EOVERFLOW;
+  if (total && !d_out) return AH_EINVAL;
+  if (total)
+    k_pair_walk<true><<<blocks, 256, 0, stream>>>(d_hits, n_hits, d_pair_offsets, d_pattern_len, min_len, max_len,
+                                                  orient_mask & 15u, nullptr, offsets, d_out);
+  return cudaGetLastError() == cudaSuccess ? AH_OK : AH_ECUDA;
+}
