@@ -80,6 +80,13 @@ ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out);
 ah_status ah_ctx_stats_reset(ah_ctx* ctx);
 ah_status ah_ctx_set_timing(ah_ctx* ctx, int enable);
 
+/* Shape of the scan kernel used by ah_scan_primers on this context (a tuning knob; results do not
+ * depend on it): threads per CTA (32..1024, a multiple of 32), groups of 32 positions per thread
+ * (1..16), initial site slots per tile (16..4096, a power of two), and how pattern positions are
+ * aligned (0: funnel shifts on the ALU pipe, 1: pairs of integer multiply-adds on the FMA pipe,
+ * 2: alternate).  AH_EINVAL outside those ranges. */
+ah_status ah_ctx_set_scan_config(ah_ctx* ctx, int threads, int groups_per_thread, int slot_cap, int shift_mode);
+
 /* ------------------------------------------------------------------------------------------ */
 /* 1. packing                                                                                   */
 /*
@@ -154,6 +161,11 @@ typedef struct {
  * (the primer's 3' end: the last c positions as written, the first c of its reverse complement).
  * Hits are ordered by (pair, record, pos, orient).  Synchronises the stream to size the output. */
 ah_status ah_scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out);
+
+/* The same sites as ah_scan_primers, scanned in the plain form: one kernel launch per record and
+ * per primer pair (each with that pair's four oriented patterns), as a baseline for the batched
+ * forms.  Same output order and contents.  Synchronises the stream. */
+ah_status ah_scan_primers_per_record(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out);
 
 ah_status ah_hits_count(const ah_hits* h, uint64_t* n);
 /* Device view: hits in device memory (ah_hit[n]) and, per pair, the range of its hits
@@ -263,6 +275,49 @@ ah_status ah_amplicons_arena_size(const ah_amplicons* a, uint64_t* bytes);
 ah_status ah_amplicons_seq_copy(const ah_amplicons* a, char* arena_out, uint64_t arena_cap, uint64_t* offsets_out,
                                 uint64_t offsets_cap);
 void ah_amplicons_free(ah_amplicons* a);
+
+/* ------------------------------------------------------------------------------------------ */
+/* batched, graph-captured form                                                                 */
+/*
+ * A plan holds the whole path for one packed batch and one primer set as a CUDA graph: one launch
+ * scans every record for every pair (optionally with persistent CTAs taking tiles from a device
+ * counter), and the site compaction, pairing, Tm, filter and extraction that follow are sized on
+ * the device, so a replay needs no host round trip.  The scan kernel's shape is chosen by an
+ * autotuner that times candidate shapes on the batch.  Outputs live in fixed-capacity buffers
+ * sized from one exact run at creation (plus 25 %); a run that exceeds a capacity is reported, and
+ * ah_plan_run grows the buffers, re-captures and runs again.
+ */
+typedef struct ah_plan ah_plan;
+typedef struct {
+  uint32_t min_len, max_len, orient_mask; /* as ah_pair_amplicons */
+  ah_tm_params tm;                        /* as ah_tm_filter */
+  int32_t extract;                        /* nonzero: sequences, trimming and barcodes as ah_extract_barcodes */
+  int32_t trim;
+  uint32_t fb_len, rb_len;
+  int32_t autotune;                       /* nonzero: choose the scan kernel shape by timing candidates */
+  int32_t persistent;                     /* -1 autotuner decides, 0 one CTA per tile, 1 persistent CTAs */
+  uint64_t hit_capacity, amp_capacity, arena_capacity; /* 0: sized from an exact run */
+} ah_plan_params;
+typedef struct {
+  int32_t threads, groups_per_thread, shift_mode, persistent, grid;
+  uint32_t slot_cap, max_tile_sites;
+  uint64_t hit_capacity, amp_capacity, arena_capacity;
+  uint64_t n_hits, n_amps, n_kept, arena_bytes; /* of the last checked run */
+  double autotune_ms, best_scan_ms;
+} ah_plan_info;
+/* Build (autotune, size, capture).  The batch and primers must outlive the plan.  Synchronises. */
+ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_plan_params* params,
+                         ah_plan** out);
+/* One graph launch of the whole step on the context's stream (asynchronous). */
+ah_status ah_plan_launch(ah_plan* plan);
+/* Synchronise and check the last run: AH_EOVERFLOW when a capacity was exceeded (sizes in the info). */
+ah_status ah_plan_check(ah_plan* plan);
+/* Launch and check, growing capacities and re-capturing on overflow. */
+ah_status ah_plan_run(ah_plan* plan);
+ah_status ah_plan_info_get(const ah_plan* plan, ah_plan_info* out);
+/* Copies of the last run's sites and (kept) amplicons, with sequences when extraction is on. */
+ah_status ah_plan_results(ah_plan* plan, ah_hits** hits, ah_amplicons** amps);
+void ah_plan_free(ah_plan* plan);
 
 #ifdef __cplusplus
 }

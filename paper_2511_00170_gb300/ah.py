@@ -39,6 +39,23 @@ class ah_tm_params(ctypes.Structure):
                 ("saltcorr", ctypes.c_int32), ("filter", ctypes.c_int32), ("min_tm", ctypes.c_double)]
 
 
+class ah_plan_params(ctypes.Structure):
+    _fields_ = [("min_len", ctypes.c_uint32), ("max_len", ctypes.c_uint32), ("orient_mask", ctypes.c_uint32),
+                ("tm", ah_tm_params), ("extract", ctypes.c_int32), ("trim", ctypes.c_int32),
+                ("fb_len", ctypes.c_uint32), ("rb_len", ctypes.c_uint32), ("autotune", ctypes.c_int32),
+                ("persistent", ctypes.c_int32), ("hit_capacity", ctypes.c_uint64), ("amp_capacity", ctypes.c_uint64),
+                ("arena_capacity", ctypes.c_uint64)]
+
+
+class ah_plan_info(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("groups_per_thread", ctypes.c_int32), ("shift_mode", ctypes.c_int32),
+                ("persistent", ctypes.c_int32), ("grid", ctypes.c_int32), ("slot_cap", ctypes.c_uint32),
+                ("max_tile_sites", ctypes.c_uint32), ("hit_capacity", ctypes.c_uint64),
+                ("amp_capacity", ctypes.c_uint64), ("arena_capacity", ctypes.c_uint64), ("n_hits", ctypes.c_uint64),
+                ("n_amps", ctypes.c_uint64), ("n_kept", ctypes.c_uint64), ("arena_bytes", ctypes.c_uint64),
+                ("autotune_ms", ctypes.c_double), ("best_scan_ms", ctypes.c_double)]
+
+
 class ah_ctx_stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("scan_launches", ctypes.c_uint64), ("scan_ms", ctypes.c_double),
                 ("scan_bases", ctypes.c_uint64)]
@@ -62,6 +79,7 @@ SIGNATURES = {
     "ah_ctx_stats_get": (_I32, [_VP, ctypes.POINTER(ah_ctx_stats)]),
     "ah_ctx_stats_reset": (_I32, [_VP]),
     "ah_ctx_set_timing": (_I32, [_VP, _I32]),
+    "ah_ctx_set_scan_config": (_I32, [_VP, _I32, _I32, _I32, _I32]),
     "ah_pack_batch": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
     "ah_pack_batch_device": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
     "ah_batch_view_get": (_I32, [_VP, ctypes.POINTER(ah_batch_view)]),
@@ -69,6 +87,7 @@ SIGNATURES = {
     "ah_primers_create": (_I32, [_VP, _U32, _VP, _VP, _VP, ctypes.c_uint8, _PVP]),
     "ah_primers_free": (None, [_VP]),
     "ah_scan_primers": (_I32, [_VP, _VP, _VP, _PVP]),
+    "ah_scan_primers_per_record": (_I32, [_VP, _VP, _VP, _PVP]),
     "ah_hits_count": (_I32, [_VP, ctypes.POINTER(ctypes.c_uint64)]),
     "ah_hits_device": (_I32, [_VP, _PVP, _PVP]),
     "ah_hits_copy": (_I32, [_VP, _VP, _U64]),
@@ -84,6 +103,13 @@ SIGNATURES = {
     "ah_amplicons_arena_size": (_I32, [_VP, ctypes.POINTER(ctypes.c_uint64)]),
     "ah_amplicons_seq_copy": (_I32, [_VP, _VP, _U64, _VP, _U64]),
     "ah_amplicons_free": (None, [_VP]),
+    "ah_plan_create": (_I32, [_VP, _VP, _VP, ctypes.POINTER(ah_plan_params), _PVP]),
+    "ah_plan_launch": (_I32, [_VP]),
+    "ah_plan_check": (_I32, [_VP]),
+    "ah_plan_run": (_I32, [_VP]),
+    "ah_plan_info_get": (_I32, [_VP, ctypes.POINTER(ah_plan_info)]),
+    "ah_plan_results": (_I32, [_VP, _PVP, _PVP]),
+    "ah_plan_free": (None, [_VP]),
 }
 
 _lib = None
@@ -148,6 +174,11 @@ def ah_ctx_set_timing(ctx, enable: bool) -> None:
     _check(load().ah_ctx_set_timing(ctx, int(bool(enable))), ctx)
 
 
+def ah_ctx_set_scan_config(ctx, threads: int = 256, groups_per_thread: int = 4, slot_cap: int = 256,
+                           shift_mode: int = 0) -> None:
+    _check(load().ah_ctx_set_scan_config(ctx, threads, groups_per_thread, slot_cap, shift_mode), ctx)
+
+
 # ------------------------------------------------------------------------------------------ packing
 def ah_pack_batch(ctx, seq: np.ndarray, offsets: np.ndarray, genome_ids: Optional[np.ndarray] = None):
     """Records are seq[offsets[r]:offsets[r+1]] of a contiguous host uint8 buffer (pinned is faster)."""
@@ -203,6 +234,12 @@ def ah_primers_free(p) -> None:
 def ah_scan_primers(ctx, batch, primers):
     out = ctypes.c_void_p()
     _check(load().ah_scan_primers(ctx, batch, primers, ctypes.byref(out)), ctx)
+    return out
+
+
+def ah_scan_primers_per_record(ctx, batch, primers):
+    out = ctypes.c_void_p()
+    _check(load().ah_scan_primers_per_record(ctx, batch, primers, ctypes.byref(out)), ctx)
     return out
 
 
@@ -308,3 +345,45 @@ def ah_amplicons_seq_copy(amps):
 
 def ah_amplicons_free(amps) -> None:
     load().ah_amplicons_free(amps)
+
+
+# ------------------------------------------------------------------------------------------ plans
+def plan_params(min_len, max_len, orient_mask=15, tm: Optional[ah_tm_params] = None, extract=True, trim=False, fb_len=0,
+                rb_len=0, autotune=False, persistent=-1, hit_capacity=0, amp_capacity=0, arena_capacity=0) -> ah_plan_params:
+    return ah_plan_params(min_len, max_len, orient_mask, tm if tm is not None else tm_params(), int(bool(extract)),
+                          int(bool(trim)), fb_len, rb_len, int(bool(autotune)), persistent, hit_capacity, amp_capacity,
+                          arena_capacity)
+
+
+def ah_plan_create(ctx, batch, primers, params: ah_plan_params):
+    out = ctypes.c_void_p()
+    _check(load().ah_plan_create(ctx, batch, primers, ctypes.byref(params), ctypes.byref(out)), ctx)
+    return out
+
+
+def ah_plan_launch(plan, ctx=None) -> None:
+    _check(load().ah_plan_launch(plan), ctx)
+
+
+def ah_plan_check(plan, ctx=None) -> None:
+    _check(load().ah_plan_check(plan), ctx)
+
+
+def ah_plan_run(plan, ctx=None) -> None:
+    _check(load().ah_plan_run(plan), ctx)
+
+
+def ah_plan_info_get(plan) -> dict:
+    i = ah_plan_info()
+    _check(load().ah_plan_info_get(plan, ctypes.byref(i)))
+    return {f: getattr(i, f) for f, _ in ah_plan_info._fields_}
+
+
+def ah_plan_results(plan, ctx=None):
+    h, a = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().ah_plan_results(plan, ctypes.byref(h), ctypes.byref(a)), ctx)
+    return h, a
+
+
+def ah_plan_free(plan) -> None:
+    load().ah_plan_free(plan)

@@ -253,6 +253,18 @@ ah_status ah_ctx_stats_reset(ah_ctx* ctx) {
   return AH_OK;
 }
 
+ah_status ah_ctx_set_scan_config(ah_ctx* ctx, int threads, int groups_per_thread, int slot_cap, int shift_mode) {
+  if (!ctx) return AH_EINVAL;
+  if (threads < 32 || threads > 1024 || threads % 32 || groups_per_thread < 1 || groups_per_thread > 16 ||
+      slot_cap < 16 || slot_cap > 4096 || (slot_cap & (slot_cap - 1)) || shift_mode < 0 || shift_mode > 2)
+    return fail(ctx, AH_EINVAL, "ah_ctx_set_scan_config: values out of range");
+  ctx->scan_cfg.threads = threads;
+  ctx->scan_cfg.groups_per_thread = groups_per_thread;
+  ctx->scan_cfg.slot_cap = slot_cap;
+  ctx->scan_cfg.shift_mode = shift_mode;
+  return AH_OK;
+}
+
 ah_status ah_ctx_set_timing(ah_ctx* ctx, int enable) {
   if (!ctx) return AH_EINVAL;
   cudaSetDevice(ctx->device);
@@ -459,6 +471,13 @@ ah_status ah_scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, a
   if (b->ctx != ctx || p->ctx != ctx) return fail(ctx, AH_EINVAL, "ah_scan_primers: object from another context");
   cudaSetDevice(ctx->device);
   return scan_primers(ctx, b, p, out);
+}
+
+ah_status ah_scan_primers_per_record(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out) {
+  if (!ctx || !b || !p || !out) return fail(ctx, AH_EINVAL, "ah_scan_primers_per_record: NULL argument");
+  if (b->ctx != ctx || p->ctx != ctx) return fail(ctx, AH_EINVAL, "ah_scan_primers_per_record: object from another context");
+  cudaSetDevice(ctx->device);
+  return scan_primers_per_record(ctx, b, p, out);
 }
 
 ah_status ah_hits_count(const ah_hits* h, uint64_t* n) {

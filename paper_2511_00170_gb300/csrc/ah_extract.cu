@@ -45,9 +45,14 @@ __device__ Fields fields_of(const ah_amplicon& m, const ah_hit& hi, const ah_hit
 
 __global__ void k_extract_len(const ah_amplicon* __restrict__ amps, uint64_t n, const ah_hit* __restrict__ hits,
                               const uint32_t* __restrict__ rec_len, const uint8_t* __restrict__ plen, int trim,
-                              int64_t fb, int64_t rb, uint64_t* __restrict__ total) {
+                              int64_t fb, int64_t rb, uint64_t* __restrict__ total,
+                              const uint64_t* __restrict__ d_n = nullptr) {
   const uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n) return;
+  if (d_n && m >= *d_n) {
+    total[m] = 0;
+    return;
+  }
   const ah_amplicon A = amps[m];
   const Fields f = fields_of(A, hits[A.hit_i], hits[A.hit_j], plen, rec_len[A.record], trim, fb, rb);
   uint64_t t = 0;
@@ -70,14 +75,25 @@ __global__ void k_extract_write(const ah_amplicon* __restrict__ amps, uint64_t n
                                 const uint64_t* __restrict__ rec_group, const uint32_t* __restrict__ rec_len,
                                 const uint8_t* __restrict__ plen, int trim, int64_t fb, int64_t rb,
                                 const uint64_t* __restrict__ base, char* __restrict__ arena,
-                                uint64_t* __restrict__ field_off) {
+                                uint64_t* __restrict__ field_off, const uint64_t* __restrict__ d_n = nullptr,
+                                uint64_t arena_cap = ~0ull, uint32_t* __restrict__ overflow = nullptr) {
   const int lane = threadIdx.x & 31;
   const uint64_t m = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (d_n) {
+    const uint64_t live = min(*d_n, n);
+    if (m == 0 && lane == 0 && live == 0) field_off[0] = 0;
+    n = live;
+  }
   if (m >= n) return;
   const ah_amplicon A = amps[m];
   const Fields f = fields_of(A, hits[A.hit_i], hits[A.hit_j], plen, rec_len[A.record], trim, fb, rb);
   const uint64_t g0 = rec_group[A.record];
   uint64_t w = base[m];
+  if (base[m + 1] > arena_cap) {  // base[m + 1] is the end of this amplicon's fields
+    if (lane == 0 && overflow) atomicOr(overflow, 8u);
+    if (m == n - 1 && lane == 0) field_off[5 * n] = base[m + 1];
+    return;
+  }
   for (int q = 0; q < 5; ++q) {
     if (lane == 0) field_off[5 * m + q] = w;
     const int64_t len = f.b[q] - f.a[q];
@@ -91,6 +107,20 @@ __global__ void k_extract_write(const ah_amplicon* __restrict__ amps, uint64_t n
 }
 
 }  // namespace
+
+void launch_extract(cudaStream_t s, bool write, const ah_amplicon* amps, uint64_t cap, const uint64_t* d_n,
+                    const ah_hit* hits, const uint2* planes, const uint32_t* invalid, const uint64_t* rec_group,
+                    const uint32_t* rec_len, const uint8_t* plen, int trim, uint32_t fb, uint32_t rb, uint64_t* len_or_base,
+                    char* arena, uint64_t* field_off, uint64_t arena_cap, uint32_t* overflow) {
+  if (!write)
+    k_extract_len<<<(unsigned)std::max<uint64_t>(1, (cap + 255) / 256), 256, 0, s>>>(amps, cap, hits, rec_len, plen, trim,
+                                                                                    (int64_t)fb, (int64_t)rb,
+                                                                                    len_or_base, d_n);
+  else
+    k_extract_write<<<(unsigned)std::max<uint64_t>(1, (cap + 7) / 8), 256, 0, s>>>(
+        amps, cap, hits, planes, invalid, rec_group, rec_len, plen, trim, (int64_t)fb, (int64_t)rb, len_or_base, arena,
+        field_off, d_n, arena_cap, overflow);
+}
 
 ah_status extract(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a, int trim,
                   uint32_t fb, uint32_t rb) {

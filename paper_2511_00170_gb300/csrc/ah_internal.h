@@ -41,9 +41,12 @@ struct Pattern {
 };
 
 struct ScanConfig {
-  int threads = 256;        // threads per CTA
-  int groups_per_thread = 4;
+  int threads = 128;        // threads per CTA (128 x 8 was fastest for a single pair in a sweep on GB300)
+  int groups_per_thread = 8;
   int slot_cap = 256;       // hit slots per tile before overflow
+  int shift_mode = 0;       // pattern-position alignment: 0 funnel shifts (ALU pipe), 1 multiply pairs
+                            // (FMA pipe), 2 alternate the two
+  int persistent = 0;       // 1: CTAs loop over tiles taken from a device counter
 };
 
 class JitCache;
@@ -150,6 +153,7 @@ inline void launched(ah_ctx* ctx, uint64_t n = 1) { ctx->n_launches += n; }
 
 // scan pipeline (ah_scan.cu)
 ah_status scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out);
+ah_status scan_primers_per_record(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out);
 // pairing (ah_pair.cu)
 ah_status pair_amplicons(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, uint32_t min_len,
                          uint32_t max_len, uint32_t orient_mask, ah_amplicons** out);
@@ -161,6 +165,36 @@ ah_status tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const ch
 // extraction (ah_extract.cu)
 ah_status extract(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a, int trim,
                   uint32_t fb, uint32_t rb);
+
+// ---- stream-level launchers used by captured plans (no allocation, no host synchronisation) -----
+struct ScanKernel;
+uint64_t scan_scratch_elems(uint64_t n);
+void exclusive_scan_u32_s(cudaStream_t s, const uint32_t* d_in, uint64_t* d_out, uint64_t n, uint64_t* scratch);
+void exclusive_scan_u64_s(cudaStream_t s, const uint64_t* d_in, uint64_t* d_out, uint64_t n, uint64_t* scratch);
+void launch_scan_kernel(cudaStream_t s, const ScanKernel& k, const ah_batch* b, uint64_t* slots, uint32_t* tile_count,
+                        uint32_t cap, uint32_t* status, unsigned long long* work, uint64_t n_tiles, int grid);
+void launch_tile_max(cudaStream_t s, const uint32_t* tile_count, uint64_t n_tiles, uint32_t* out);
+size_t prepare_tile_sort(uint32_t cap, int* warps_out);
+void launch_tile_sort(cudaStream_t s, uint64_t* slots, const uint32_t* tile_count, uint32_t cap, uint64_t n_tiles,
+                      uint32_t n_pairs, uint32_t* tpc);
+void launch_emit_hits(cudaStream_t s, const uint64_t* slots, const uint32_t* tile_count, uint32_t cap, uint64_t n_tiles,
+                      uint64_t tile_groups, const uint64_t* off, const ah_batch* b, ah_hit* hits,
+                      const uint64_t* tile_base, uint64_t hit_cap, uint32_t* overflow, uint64_t* pair_off,
+                      uint32_t n_pairs);
+void launch_pair_walk(cudaStream_t s, bool emit, const ah_hit* hits, uint64_t cap, const uint64_t* d_n,
+                      const uint64_t* pair_off, const uint8_t* plen, uint32_t min_len, uint32_t max_len, uint32_t mask,
+                      uint32_t* counts, const uint64_t* out_off, ah_amplicon* out, uint64_t out_cap,
+                      uint32_t* overflow);
+ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, size_t run_size);
+void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit_cap, const uint64_t* d_nhits,
+               const uint2* planes, const uint64_t* rec_group, const uint8_t* plen, const uint8_t* psets, double* hit_tm,
+               ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep);
+void launch_compact_amps(cudaStream_t s, const ah_amplicon* in, uint64_t cap, const uint32_t* keep, const uint64_t* off,
+                         ah_amplicon* out);
+void launch_extract(cudaStream_t s, bool write, const ah_amplicon* amps, uint64_t cap, const uint64_t* d_n,
+                    const ah_hit* hits, const uint2* planes, const uint32_t* invalid, const uint64_t* rec_group,
+                    const uint32_t* rec_len, const uint8_t* plen, int trim, uint32_t fb, uint32_t rb, uint64_t* len_or_base,
+                    char* arena, uint64_t* field_off, uint64_t arena_cap, uint32_t* overflow);
 
 // ---- run-time specialised scan kernels (ah_jit.cpp) ------------------------------------------
 struct ScanKernel {

@@ -177,13 +177,15 @@ struct ScanParams {
   u64* slots;
   u32* tile_count;
   u32* status;
-  u64 tile_begin;
+  u64 tile_groups;          // groups per tile of the slot lists: the tile of group g is g / tile_groups
+  unsigned long long* work;
+  u64 n_blocks;             // persistent kernels: blocks of NT * GPT groups in this launch
 };
 static __device__ __forceinline__ u32 fshr(u32 a, u32 b, u32 s) { return __funnelshift_r(a, b, s); }
 
 // exact re-check of candidate bits, validity, record bounds, and slot append
-static __device__ __noinline__ void emit(u32 h, int q, u64 g, uint2 a, uint2 b, const ScanParams& P, u64 tile,
-                                         u64 tile_pos) {
+static __device__ __noinline__ void emit(u32 h, int q, u64 g, uint2 a, uint2 b, const ScanParams& P) {
+  const u64 tile = g / P.tile_groups, tile_pos = tile * P.tile_groups * 32ull;
   const u64 lo64 = (u64)a.x | ((u64)b.x << 32), hi64 = (u64)a.y | ((u64)b.y << 32);
   const u64 inv64 = (u64)P.invalid[g] | ((u64)P.invalid[g + 1] << 32);
   const int L = PLEN[q];
@@ -225,7 +227,8 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg)
   const int Q = (int)pats.size();
   std::ostringstream os;
   os << "// generated scan kernel: " << Q << " patterns\n";
-  os << "#define NT " << cfg.threads << "\n#define GPT " << cfg.groups_per_thread << "\n";
+  os << "#define NT " << cfg.threads << "\n#define GPT " << cfg.groups_per_thread << "\n// shift mode "
+     << cfg.shift_mode << ", persistent " << cfg.persistent << "\n";
   auto table = [&](const char* type, const char* name, auto get) {
     os << "static __device__ const " << type << " " << name << "[" << Q << "] = {";
     for (int q = 0; q < Q; ++q) os << (q ? "," : "") << (unsigned)get(pats[q]);
@@ -254,11 +257,10 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg)
   bool kind_used[K_COUNT] = {};
   for (auto& u : used) kind_used[u.first.first] = true;
 
-  os << "extern \"C\" __global__ void __launch_bounds__(NT) ah_scan_jit(const ScanParams P) {\n";
-  os << "  const u64 tile = P.tile_begin + blockIdx.x;\n";
-  os << "  const u64 tile_first = (u64)blockIdx.x * (u64)(NT * GPT);\n";
-  os << "  const u64 tile_pos = (P.group_begin + tile_first) * 32ull;\n";
-  os << "  u64 gl = tile_first + threadIdx.x;\n";
+  // one block of the launch: NT threads x GPT groups of 32 positions, from group_begin
+  os << "static __device__ __forceinline__ void scan_block(const ScanParams& P, const u64 blk) {\n";
+  os << "  const u64 first = blk * (u64)(NT * GPT);\n";
+  os << "  u64 gl = first + threadIdx.x;\n";
   os << "  uint2 na = make_uint2(0u, 0u), nb = na;\n";
   os << "  if (gl < P.n_groups) { na = __ldg(P.planes + P.group_begin + gl); nb = __ldg(P.planes + P.group_begin + gl + 1); }\n";
   os << "#pragma unroll 1\n";
@@ -273,13 +275,26 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg)
     if (!kind_used[k]) continue;
     for (int w = 0; w < 2; ++w) os << "    const u32 " << kKindName[k] << w << " = " << kind_expr(k, w) << ";\n";
   }
+  int nshift = 0;
   for (auto& u : used) {
     int kind = u.first.first, j = u.first.second;
-    os << "    const u32 " << plane_name(kind, j) << " = ";
-    if (j == 0)
-      os << kKindName[kind] << "0;\n";
-    else
-      os << "fshr(" << kKindName[kind] << "0, " << kKindName[kind] << "1, " << j << "u);\n";
+    const std::string name = plane_name(kind, j), w0 = std::string(kKindName[kind]) + "0",
+                      w1 = std::string(kKindName[kind]) + "1";
+    if (j == 0) {
+      os << "    const u32 " << name << " = " << w0 << ";\n";
+      continue;
+    }
+    const bool by_multiply = cfg.shift_mode == 1 || (cfg.shift_mode == 2 && (nshift++ & 1));
+    if (!by_multiply) {
+      os << "    const u32 " << name << " = fshr(" << w0 << ", " << w1 << ", " << j << "u);\n";
+    } else {
+      // (w0 >> j) | (w1 << (32 - j)) as hi(w0 * 2^(32-j)) + lo(w1 * 2^(32-j)): two integer
+      // multiply-adds on the FMA pipe instead of one funnel shift on the ALU pipe
+      const unsigned long long m = 1ull << (32 - j);
+      os << "    u32 " << name << ";\n    { u32 t_; asm(\"mul.lo.u32 %0, %1, " << m << ";\" : \"=r\"(t_) : \"r\"(" << w1
+         << ")); asm(\"mad.hi.u32 %0, %1, " << m << ", %2;\" : \"=r\"(" << name << ") : \"r\"(" << w0
+         << "), \"r\"(t_)); }\n";
+    }
   }
   os << "    {\n" << E.os.str();
   // hit words and the rare emission path, in blocks of four patterns
@@ -289,10 +304,20 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg)
     for (int q = q0; q < q1; ++q) os << (q > q0 ? " & " : "") << fails[q];
     os << ") != 0xffffffffu, 0)) {\n";
     for (int q = q0; q < q1; ++q)
-      os << "        if (~" << fails[q] << ") emit(~" << fails[q] << ", " << q << ", g, a, b, P, tile, tile_pos);\n";
+      os << "        if (~" << fails[q] << ") emit(~" << fails[q] << ", " << q << ", g, a, b, P);\n";
     os << "      }\n";
   }
   os << "    }\n  }\n}\n";
+  os << "extern \"C\" __global__ void __launch_bounds__(NT) ah_scan_jit(const ScanParams P) {\n";
+  if (cfg.persistent) {
+    // persistent CTAs take tiles from a counter until none are left
+    os << "  __shared__ u64 s_tile;\n  for (;;) {\n";
+    os << "    if (threadIdx.x == 0) s_tile = atomicAdd(P.work, 1ull);\n    __syncthreads();\n";
+    os << "    const u64 t = s_tile;\n    __syncthreads();\n    if (t >= P.n_blocks) break;\n";
+    os << "    scan_block(P, t);\n  }\n}\n";
+  } else {
+    os << "  scan_block(P, blockIdx.x);\n}\n";
+  }
   return os.str();
 }
 

@@ -14,20 +14,28 @@ __device__ __forceinline__ uint8_t orientation(uint32_t primer_i, uint32_t prime
   return (uint8_t)(primer_i == primer_j ? 2u + primer_i : primer_i);
 }
 
+// d_n (optional): live site count in device memory, n is then the capacity; out_cap and overflow
+// (optional) bound the emitted records
 template <bool kEmit>
 __global__ void k_pair_walk(const ah_hit* __restrict__ hits, uint64_t n, const uint64_t* __restrict__ pair_off,
                             const uint8_t* __restrict__ plen, uint32_t min_len, uint32_t max_len, uint32_t mask,
                             uint32_t* __restrict__ counts, const uint64_t* __restrict__ out_off,
-                            ah_amplicon* __restrict__ out) {
+                            ah_amplicon* __restrict__ out, const uint64_t* __restrict__ d_n = nullptr,
+                            uint64_t out_cap = ~0ull, uint32_t* __restrict__ overflow = nullptr) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const uint64_t n_live = d_n ? min(*d_n, n) : n;
+  if (i >= n_live) {
+    if (!kEmit) counts[i] = 0;
+    return;
+  }
   const ah_hit a = hits[i];
   const uint32_t oa = a.pattern & 3u;
   uint32_t cnt = 0;
   uint64_t w = kEmit ? out_off[i] : 0;
   if (oa < 2) {  // anchors are + strand sites
     const uint32_t pair = a.pattern >> 2;
-    const uint64_t seg_end = pair_off[pair + 1];
+    const uint64_t seg_end = min(pair_off[pair + 1], n_live);
     for (uint64_t j = i + 1; j < seg_end; ++j) {
       const ah_hit b = hits[j];
       if (b.record != a.record) break;
@@ -50,7 +58,11 @@ __global__ void k_pair_walk(const ah_hit* __restrict__ hits, uint64_t n, const u
         m.orient = o;
         m.flags = 0;
         m.tm = __longlong_as_double(0x7ff8000000000000ll);
-        out[w++] = m;
+        if (w < out_cap)
+          out[w] = m;
+        else if (overflow)
+          atomicOr(overflow, 4u);
+        ++w;
       } else {
         ++cnt;
       }
@@ -60,6 +72,19 @@ __global__ void k_pair_walk(const ah_hit* __restrict__ hits, uint64_t n, const u
 }
 
 }  // namespace
+
+void launch_pair_walk(cudaStream_t s, bool emit, const ah_hit* hits, uint64_t cap, const uint64_t* d_n,
+                      const uint64_t* pair_off, const uint8_t* plen, uint32_t min_len, uint32_t max_len, uint32_t mask,
+                      uint32_t* counts, const uint64_t* out_off, ah_amplicon* out, uint64_t out_cap,
+                      uint32_t* overflow) {
+  const unsigned blocks = (unsigned)std::max<uint64_t>(1, (cap + 255) / 256);
+  if (emit)
+    k_pair_walk<true><<<blocks, 256, 0, s>>>(hits, cap, pair_off, plen, min_len, max_len, mask, nullptr, out_off, out,
+                                             d_n, out_cap, overflow);
+  else
+    k_pair_walk<false><<<blocks, 256, 0, s>>>(hits, cap, pair_off, plen, min_len, max_len, mask, counts, nullptr,
+                                              nullptr, d_n, out_cap, overflow);
+}
 
 ah_status pair_amplicons(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, uint32_t min_len,
                          uint32_t max_len, uint32_t orient_mask, ah_amplicons** out) {

@@ -1,0 +1,405 @@
+// Batched, graph-captured form of the whole path over one packed batch and one primer set.
+//
+// ah_plan_create picks the scan kernel's shape with an autotuner (timing candidate shapes, shift
+// modes and the persistent form on the batch), sizes every output from one exact run of the
+// step, allocates fixed-capacity buffers, and captures the step into a CUDA graph: memsets, the
+// scan (one launch over all records and pairs), per-tile sort, prefix sums, site emission,
+// pairing, FP64 Tm, the Tm filter and extraction, all sized on the device.  ah_plan_launch replays
+// it as one graph launch.  Capacities are checked after a run (ah_plan_check); ah_plan_run grows
+// them and re-captures when a different batch of the same size would not fit.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "ah_internal.h"
+
+struct ah_plan {
+  ah_ctx* ctx = nullptr;
+  const ah_batch* b = nullptr;
+  const ah_primers* p = nullptr;
+  ah_plan_params prm{};
+  ah::ScanConfig cfg;
+  ah::ScanKernel kern;
+  int grid = 0;                 // persistent grid (0: one CTA per tile)
+  uint64_t tile_groups = 0, n_tiles = 0, n_cells = 0;
+  uint32_t slot_cap = 0;
+  uint64_t hit_cap = 0, amp_cap = 0, arena_cap = 0;
+  // device buffers
+  uint64_t* slots = nullptr;
+  uint32_t* tile_count = nullptr;
+  uint32_t* tpc = nullptr;
+  uint64_t* tpc_off = nullptr;  // n_cells + 1; [n_cells] = sites found
+  uint64_t* scratch = nullptr;  // prefix-sum block sums
+  ah_hit* hits = nullptr;
+  uint64_t* pair_off = nullptr;
+  uint32_t* pcount = nullptr;
+  uint64_t* poff = nullptr;     // hit_cap + 1; [hit_cap] = amplicons found
+  ah_amplicon* amps = nullptr;
+  double* hit_tm = nullptr;
+  uint32_t* keep = nullptr;
+  uint64_t* koff = nullptr;     // amp_cap + 1; [amp_cap] = amplicons kept
+  ah_amplicon* kept = nullptr;
+  uint64_t* elen = nullptr;
+  uint64_t* ebase = nullptr;    // amp_cap + 1; [amp_cap] = arena bytes
+  char* arena = nullptr;
+  uint64_t* field_off = nullptr;
+  uint32_t* ctr = nullptr;      // [0] fullest tile, [1] overflow bits, [2..3] persistent work counter
+  uint64_t* h_out = nullptr;    // pinned: counters read back after a run
+  unsigned char tm_run[64];
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ah_plan_info info{};
+};
+
+namespace ah {
+namespace {
+
+void free_buffers(ah_plan* pl) {
+  ah_ctx* c = pl->ctx;
+  for (void* q : {(void*)pl->slots, (void*)pl->tile_count, (void*)pl->tpc, (void*)pl->tpc_off, (void*)pl->scratch,
+                  (void*)pl->hits, (void*)pl->pair_off, (void*)pl->pcount, (void*)pl->poff, (void*)pl->amps,
+                  (void*)pl->hit_tm, (void*)pl->keep, (void*)pl->koff, (void*)pl->kept, (void*)pl->elen,
+                  (void*)pl->ebase, (void*)pl->arena, (void*)pl->field_off, (void*)pl->ctr})
+    dfree(c, q);
+  pl->slots = nullptr, pl->tile_count = nullptr, pl->tpc = nullptr, pl->tpc_off = nullptr, pl->scratch = nullptr;
+  pl->hits = nullptr, pl->pair_off = nullptr, pl->pcount = nullptr, pl->poff = nullptr, pl->amps = nullptr;
+  pl->hit_tm = nullptr, pl->keep = nullptr, pl->koff = nullptr, pl->kept = nullptr, pl->elen = nullptr;
+  pl->ebase = nullptr, pl->arena = nullptr, pl->field_off = nullptr, pl->ctr = nullptr;
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  pl->exec = nullptr;
+  pl->graph = nullptr;
+}
+
+ah_status alloc_buffers(ah_plan* pl) {
+  ah_ctx* c = pl->ctx;
+  ah_status st;
+  const uint64_t scan_n = std::max({pl->n_cells, pl->hit_cap, pl->amp_cap});
+  if ((st = dalloc(c, &pl->slots, pl->n_tiles * pl->slot_cap)) || (st = dalloc(c, &pl->tile_count, pl->n_tiles)) ||
+      (st = dalloc(c, &pl->tpc, pl->n_cells)) || (st = dalloc(c, &pl->tpc_off, pl->n_cells + 1)) ||
+      (st = dalloc(c, &pl->scratch, scan_scratch_elems(scan_n))) || (st = dalloc(c, &pl->hits, pl->hit_cap)) ||
+      (st = dalloc(c, &pl->pair_off, pl->p->n_pairs + 1)) || (st = dalloc(c, &pl->pcount, pl->hit_cap)) ||
+      (st = dalloc(c, &pl->poff, pl->hit_cap + 1)) || (st = dalloc(c, &pl->amps, pl->amp_cap)) ||
+      (st = dalloc(c, &pl->hit_tm, pl->hit_cap)) || (st = dalloc(c, &pl->keep, pl->amp_cap)) ||
+      (st = dalloc(c, &pl->koff, pl->amp_cap + 1)) || (st = dalloc(c, &pl->kept, pl->amp_cap)) ||
+      (st = dalloc(c, &pl->elen, pl->amp_cap)) || (st = dalloc(c, &pl->ebase, pl->amp_cap + 1)) ||
+      (st = dalloc(c, &pl->arena, pl->arena_cap)) || (st = dalloc(c, &pl->field_off, 5 * pl->amp_cap + 1)) ||
+      (st = dalloc(c, &pl->ctr, 4)))
+    return st;
+  return AH_OK;
+}
+
+// the step, enqueued on stream s (captured into the graph)
+void enqueue_step(ah_plan* pl, cudaStream_t s) {
+  const ah_batch* b = pl->b;
+  const ah_primers* p = pl->p;
+  const ah_plan_params& q = pl->prm;
+  cudaMemsetAsync(pl->tile_count, 0, pl->n_tiles * sizeof(uint32_t), s);
+  cudaMemsetAsync(pl->tpc, 0, pl->n_cells * sizeof(uint32_t), s);
+  cudaMemsetAsync(pl->ctr, 0, 4 * sizeof(uint32_t), s);
+  launch_scan_kernel(s, pl->kern, b, pl->slots, pl->tile_count, pl->slot_cap, pl->ctx->d_status,
+                     (unsigned long long*)(pl->ctr + 2), pl->n_tiles, pl->grid);
+  launch_tile_max(s, pl->tile_count, pl->n_tiles, pl->ctr + 0);
+  launch_tile_sort(s, pl->slots, pl->tile_count, pl->slot_cap, pl->n_tiles, p->n_pairs, pl->tpc);
+  exclusive_scan_u32_s(s, pl->tpc, pl->tpc_off, pl->n_cells, pl->scratch);
+  launch_emit_hits(s, pl->slots, pl->tile_count, pl->slot_cap, pl->n_tiles, pl->tile_groups, pl->tpc_off, b, pl->hits,
+                   nullptr, pl->hit_cap, pl->ctr + 1, pl->pair_off, p->n_pairs);
+  const uint64_t* n_hits = pl->tpc_off + pl->n_cells;
+  launch_pair_walk(s, false, pl->hits, pl->hit_cap, n_hits, pl->pair_off, p->d_plen, q.min_len, q.max_len,
+                   q.orient_mask & 15u, pl->pcount, nullptr, nullptr, 0, nullptr);
+  exclusive_scan_u32_s(s, pl->pcount, pl->poff, pl->hit_cap, pl->scratch);
+  launch_pair_walk(s, true, pl->hits, pl->hit_cap, n_hits, pl->pair_off, p->d_plen, q.min_len, q.max_len,
+                   q.orient_mask & 15u, nullptr, pl->poff, pl->amps, pl->amp_cap, pl->ctr + 1);
+  const uint64_t* n_amps = pl->poff + pl->hit_cap;
+  launch_tm(s, pl->tm_run, pl->hits, pl->hit_cap, n_hits, b->planes, b->rec_group, p->d_plen, p->d_psets, pl->hit_tm,
+            pl->amps, pl->amp_cap, n_amps, q.tm.filter, q.tm.min_tm, pl->keep);
+  const ah_amplicon* out = pl->amps;
+  const uint64_t* n_out = n_amps;
+  if (q.tm.filter) {
+    exclusive_scan_u32_s(s, pl->keep, pl->koff, pl->amp_cap, pl->scratch);
+    launch_compact_amps(s, pl->amps, pl->amp_cap, pl->keep, pl->koff, pl->kept);
+    out = pl->kept;
+    n_out = pl->koff + pl->amp_cap;
+  }
+  if (q.extract) {
+    launch_extract(s, false, out, pl->amp_cap, n_out, pl->hits, b->planes, b->invalid, b->rec_group, b->rec_len,
+                   p->d_plen, q.trim, q.fb_len, q.rb_len, pl->elen, nullptr, nullptr, 0, nullptr);
+    exclusive_scan_u64_s(s, pl->elen, pl->ebase, pl->amp_cap, pl->scratch);
+    launch_extract(s, true, out, pl->amp_cap, n_out, pl->hits, b->planes, b->invalid, b->rec_group, b->rec_len,
+                   p->d_plen, q.trim, q.fb_len, q.rb_len, pl->ebase, pl->arena, pl->field_off, pl->arena_cap,
+                   pl->ctr + 1);
+  }
+}
+
+ah_status capture(ah_plan* pl) {
+  ah_ctx* c = pl->ctx;
+  cudaStream_t s = c->stream;
+  AH_CUDA(c, cudaStreamSynchronize(s));
+  prepare_tile_sort(pl->slot_cap, nullptr);
+  AH_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  enqueue_step(pl, s);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess) return fail(c, AH_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  pl->graph = g;
+  AH_CUDA(c, cudaGraphInstantiate(&pl->exec, g, 0));
+  return AH_OK;
+}
+
+// time the scan kernel of one shape through the regular path (ms per launch, on this batch)
+ah_status time_shape(ah_ctx* c, const ah_batch* b, const ah_primers* p, const ScanConfig& cfg, int reps, double* ms,
+                     uint64_t* n_hits) {
+  const ScanConfig saved = c->scan_cfg;
+  const bool timing = c->timing;
+  c->scan_cfg = cfg;
+  ah_status st = ah_ctx_set_timing(c, 1);
+  ah_hits* h = nullptr;
+  if (!st) st = scan_primers(c, b, p, &h);  // compiles and warms
+  if (h) {
+    *n_hits = h->n;
+    ah_hits_free(h);
+  }
+  const double ms0 = c->scan_ms;
+  const uint64_t l0 = c->n_scan_launches;
+  for (int r = 0; r < reps && !st; ++r) {
+    h = nullptr;
+    st = scan_primers(c, b, p, &h);
+    ah_hits_free(h);
+  }
+  if (!st) *ms = (c->scan_ms - ms0) / std::max<uint64_t>(1, c->n_scan_launches - l0);
+  c->scan_cfg = saved;
+  c->timing = timing;
+  return st;
+}
+
+}  // namespace
+}  // namespace ah
+
+using namespace ah;
+
+extern "C" {
+
+ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_plan_params* prm,
+                         ah_plan** out) {
+  if (!ctx || !b || !p || !prm || !out) return fail(ctx, AH_EINVAL, "ah_plan_create: NULL argument");
+  if (prm->min_len > prm->max_len) return fail(ctx, AH_EINVAL, "ah_plan_create: min_len > max_len");
+  if (prm->tm.saltcorr < 0 || prm->tm.saltcorr > 6) return fail(ctx, AH_EINVAL, "ah_plan_create: bad salt method");
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  ah_plan* pl = new ah_plan();
+  pl->ctx = ctx;
+  pl->b = b;
+  pl->p = p;
+  pl->prm = *prm;
+  pl->cfg = ctx->scan_cfg;
+  ah_status st = tm_prepare(ctx, &prm->tm, pl->tm_run, sizeof pl->tm_run);
+  const auto t0 = std::chrono::steady_clock::now();
+  uint64_t n_hits = 0;
+  if (!st && prm->autotune) {
+    // candidate shapes x alignment modes, then the persistent form of the best
+    const int shapes[][2] = {{128, 8}, {256, 4}, {128, 4}, {256, 8}};
+    double best = 1e30;
+    ScanConfig win = pl->cfg;
+    for (int mode = 0; mode < 2 && !st; ++mode) {
+      for (auto& sh : shapes) {
+        ScanConfig c = pl->cfg;
+        c.threads = sh[0];
+        c.groups_per_thread = sh[1];
+        c.shift_mode = mode;
+        c.persistent = 0;
+        double ms = 0;
+        if ((st = time_shape(ctx, b, p, c, 2, &ms, &n_hits))) break;
+        if (ms < best) best = ms, win = c;
+      }
+    }
+    if (!st && prm->persistent != 0) {
+      ScanConfig c = win;
+      c.persistent = 1;
+      double ms = 0;
+      if (!(st = time_shape(ctx, b, p, c, 2, &ms, &n_hits)) && (ms < best || prm->persistent > 0)) best = ms, win = c;
+    }
+    pl->cfg = win;
+    pl->info.best_scan_ms = best;
+  } else if (prm->persistent > 0) {
+    pl->cfg.persistent = 1;
+  }
+  pl->info.autotune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  // one exact run of the regular path sizes every buffer
+  ah_hits* h = nullptr;
+  ah_amplicons* a = nullptr;
+  const ScanConfig saved = ctx->scan_cfg;
+  ctx->scan_cfg = pl->cfg;
+  if (!st) st = scan_primers(ctx, b, p, &h);
+  if (!st) st = pair_amplicons(ctx, b, p, h, prm->min_len, prm->max_len, prm->orient_mask & 15u, &a);
+  const uint64_t n_amps_all = a ? a->n : 0;
+  if (!st) st = tm_filter(ctx, b, p, h, a, &prm->tm);
+  if (!st && prm->extract) st = extract(ctx, b, p, h, a, prm->trim, prm->fb_len, prm->rb_len);
+  ctx->scan_cfg = saved;
+  if (!st) {
+    auto grow = [](uint64_t x) { return x + x / 4 + 1024; };
+    pl->hit_cap = prm->hit_capacity ? prm->hit_capacity : grow(h->n);
+    pl->amp_cap = prm->amp_capacity ? prm->amp_capacity : grow(n_amps_all);
+    pl->arena_cap = prm->arena_capacity ? prm->arena_capacity : grow(a->arena_bytes);
+  }
+  ah_hits_free(h);
+  ah_amplicons_free(a);
+  if (!st) st = ctx->jit->get(ctx, p->pats, pl->cfg, &pl->kern);
+  if (!st) {
+    pl->tile_groups = (uint64_t)pl->cfg.threads * pl->cfg.groups_per_thread;
+    pl->n_tiles = std::max<uint64_t>(1, (b->n_groups + pl->tile_groups - 1) / pl->tile_groups);
+    pl->n_cells = (uint64_t)p->n_pairs * pl->n_tiles;
+    pl->slot_cap = (uint32_t)pl->cfg.slot_cap;
+    if (pl->n_tiles > 0x7fffffffull) st = fail(ctx, AH_EINVAL, "ah_plan_create: batch too large for one launch");
+  }
+  if (!st && pl->cfg.persistent) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)pl->kern.fn, pl->cfg.threads, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    pl->grid = (int)std::min<uint64_t>(pl->n_tiles, (uint64_t)per_sm * ctx->sm_count);
+  }
+  if (!st && cudaMallocHost(&pl->h_out, 8 * sizeof(uint64_t)) != cudaSuccess)
+    st = fail(ctx, AH_ENOMEM, "ah_plan_create: pinned allocation failed");
+  if (!st) st = alloc_buffers(pl);
+  if (!st) st = capture(pl);
+  if (st) {
+    ah_plan_free(pl);
+    return st;
+  }
+  pl->info.threads = pl->cfg.threads;
+  pl->info.groups_per_thread = pl->cfg.groups_per_thread;
+  pl->info.shift_mode = pl->cfg.shift_mode;
+  pl->info.persistent = pl->cfg.persistent;
+  pl->info.grid = pl->grid ? pl->grid : (int32_t)pl->n_tiles;
+  *out = pl;
+  return AH_OK;
+}
+
+ah_status ah_plan_launch(ah_plan* pl) {
+  if (!pl) return AH_EINVAL;
+  ah_ctx* c = pl->ctx;
+  AH_CUDA(c, cudaGraphLaunch(pl->exec, c->stream));
+  launched(c);
+  return AH_OK;
+}
+
+ah_status ah_plan_check(ah_plan* pl) {
+  if (!pl) return AH_EINVAL;
+  ah_ctx* c = pl->ctx;
+  cudaStream_t s = c->stream;
+  AH_CUDA(c, cudaMemcpyAsync(pl->h_out + 0, pl->ctr, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  AH_CUDA(c, cudaMemcpyAsync(pl->h_out + 1, pl->tpc_off + pl->n_cells, 8, cudaMemcpyDeviceToHost, s));
+  AH_CUDA(c, cudaMemcpyAsync(pl->h_out + 2, pl->poff + pl->hit_cap, 8, cudaMemcpyDeviceToHost, s));
+  if (pl->prm.tm.filter)
+    AH_CUDA(c, cudaMemcpyAsync(pl->h_out + 3, pl->koff + pl->amp_cap, 8, cudaMemcpyDeviceToHost, s));
+  if (pl->prm.extract)
+    AH_CUDA(c, cudaMemcpyAsync(pl->h_out + 4, pl->ebase + pl->amp_cap, 8, cudaMemcpyDeviceToHost, s));
+  AH_CUDA(c, cudaStreamSynchronize(s));
+  ah_status st = check_status(c);
+  if (st) return st;
+  const uint32_t* cw = (const uint32_t*)pl->h_out;
+  const uint32_t max_tile = cw[0];
+  pl->info.n_hits = pl->h_out[1];
+  pl->info.n_amps = pl->h_out[2];
+  pl->info.n_kept = pl->prm.tm.filter ? pl->h_out[3] : std::min(pl->h_out[2], pl->amp_cap);
+  pl->info.arena_bytes = pl->prm.extract ? pl->h_out[4] : 0;
+  pl->info.max_tile_sites = max_tile;
+  const bool over = max_tile > pl->slot_cap || pl->info.n_hits > pl->hit_cap || pl->info.n_amps > pl->amp_cap ||
+                    (pl->prm.extract && pl->info.arena_bytes > pl->arena_cap);
+  if (over)
+    return fail(c, AH_EOVERFLOW, "plan capacities exceeded: tile %u/%u sites %llu/%llu amplicons %llu/%llu arena %llu/%llu",
+                max_tile, pl->slot_cap, (unsigned long long)pl->info.n_hits, (unsigned long long)pl->hit_cap,
+                (unsigned long long)pl->info.n_amps, (unsigned long long)pl->amp_cap,
+                (unsigned long long)pl->info.arena_bytes, (unsigned long long)pl->arena_cap);
+  return AH_OK;
+}
+
+ah_status ah_plan_run(ah_plan* pl) {
+  if (!pl) return AH_EINVAL;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    ah_status st = ah_plan_launch(pl);
+    if (st) return st;
+    st = ah_plan_check(pl);
+    if (st != AH_EOVERFLOW) return st;
+    // grow what overflowed, re-capture
+    const ah_plan_info& i = pl->info;
+    if (i.max_tile_sites > pl->slot_cap) {
+      uint32_t need = 1;
+      while (need < i.max_tile_sites) need <<= 1;
+      if (need > 4096) return fail(pl->ctx, AH_EOVERFLOW, "plan: a tile holds more than 4096 sites");
+      pl->slot_cap = need;
+    }
+    pl->hit_cap = std::max(pl->hit_cap, i.n_hits + i.n_hits / 4 + 1024);
+    pl->amp_cap = std::max(pl->amp_cap, i.n_amps + i.n_amps / 4 + 1024);
+    pl->arena_cap = std::max(pl->arena_cap, i.arena_bytes + i.arena_bytes / 4 + 4096);
+    free_buffers(pl);
+    if ((st = alloc_buffers(pl)) || (st = capture(pl))) return st;
+  }
+  return fail(pl->ctx, AH_EOVERFLOW, "plan: capacities kept overflowing");
+}
+
+ah_status ah_plan_info_get(const ah_plan* pl, ah_plan_info* out) {
+  if (!pl || !out) return AH_EINVAL;
+  *out = pl->info;
+  out->slot_cap = pl->slot_cap;
+  out->hit_capacity = pl->hit_cap;
+  out->amp_capacity = pl->amp_cap;
+  out->arena_capacity = pl->arena_cap;
+  return AH_OK;
+}
+
+ah_status ah_plan_results(ah_plan* pl, ah_hits** hits_out, ah_amplicons** amps_out) {
+  if (!pl || !hits_out || !amps_out) return AH_EINVAL;
+  *hits_out = nullptr;
+  *amps_out = nullptr;
+  ah_status st = ah_plan_check(pl);
+  if (st) return st;
+  ah_ctx* c = pl->ctx;
+  cudaStream_t s = c->stream;
+  ah_hits* h = new ah_hits();
+  h->ctx = c;
+  h->n = pl->info.n_hits;
+  h->n_pairs = pl->p->n_pairs;
+  ah_amplicons* a = new ah_amplicons();
+  a->ctx = c;
+  a->n = pl->info.n_kept;
+  const uint64_t nf = pl->prm.extract ? 5 * a->n + 1 : 0;
+  if ((st = dalloc(c, &h->d, h->n)) || (st = dalloc(c, &h->d_pair_off, h->n_pairs + 1)) || (st = dalloc(c, &a->d, a->n)) ||
+      (pl->prm.extract && ((st = dalloc(c, &a->d_arena, pl->info.arena_bytes)) || (st = dalloc(c, &a->d_field_off, nf))))) {
+    ah_hits_free(h);
+    ah_amplicons_free(a);
+    return st;
+  }
+  AH_CUDA(c, cudaMemcpyAsync(h->d, pl->hits, h->n * sizeof(ah_hit), cudaMemcpyDeviceToDevice, s));
+  AH_CUDA(c, cudaMemcpyAsync(h->d_pair_off, pl->pair_off, (h->n_pairs + 1) * sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                             s));
+  AH_CUDA(c, cudaMemcpyAsync(a->d, pl->prm.tm.filter ? pl->kept : pl->amps, a->n * sizeof(ah_amplicon),
+                             cudaMemcpyDeviceToDevice, s));
+  if (pl->prm.extract) {
+    a->arena_bytes = pl->info.arena_bytes;
+    if (a->arena_bytes)
+      AH_CUDA(c, cudaMemcpyAsync(a->d_arena, pl->arena, a->arena_bytes, cudaMemcpyDeviceToDevice, s));
+    AH_CUDA(c, cudaMemcpyAsync(a->d_field_off, pl->field_off, nf * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+  }
+  h->h_pair_off.resize(h->n_pairs + 1);
+  AH_CUDA(c, cudaMemcpyAsync(h->h_pair_off.data(), pl->pair_off, (h->n_pairs + 1) * sizeof(uint64_t),
+                             cudaMemcpyDeviceToHost, s));
+  AH_CUDA(c, cudaStreamSynchronize(s));
+  *hits_out = h;
+  *amps_out = a;
+  return AH_OK;
+}
+
+void ah_plan_free(ah_plan* pl) {
+  if (!pl) return;
+  if (pl->ctx) {
+    cudaSetDevice(pl->ctx->device);
+    free_buffers(pl);
+    if (pl->h_out) cudaFreeHost(pl->h_out);
+  }
+  delete pl;
+}
+
+}  // extern "C"

@@ -25,7 +25,9 @@ struct ScanParamsHost {
   uint64_t* slots;
   uint32_t* tile_count;
   uint32_t* status;
-  uint64_t tile_begin;
+  uint64_t tile_groups;      // groups per slot-list tile: the tile of group g is g / tile_groups
+  unsigned long long* work;  // persistent kernels: next block to take
+  uint64_t n_blocks;         // persistent kernels: blocks of threads * groups_per_thread groups
 };
 
 __global__ void k_tile_max(const uint32_t* __restrict__ tile_count, uint64_t n_tiles, uint32_t* __restrict__ out) {
@@ -92,15 +94,19 @@ __global__ void k_tile_sort(uint64_t* __restrict__ slots, const uint32_t* __rest
 }
 
 // one warp per tile: sorted keys -> hit records at their pair-major output positions
+// tile_base (optional) gives each tile's first position; otherwise tile t starts at t * tile_groups * 32.
+// Hits at output positions >= hit_cap are dropped and flagged.
 __global__ void k_emit_hits(const uint64_t* __restrict__ slots, const uint32_t* __restrict__ tile_count, uint32_t cap,
                             uint64_t n_tiles, uint64_t tile_groups, const uint64_t* __restrict__ off,
-                            const uint64_t* __restrict__ rec_group, uint32_t n_rec, ah_hit* __restrict__ hits) {
+                            const uint64_t* __restrict__ rec_group, uint32_t n_rec, ah_hit* __restrict__ hits,
+                            const uint64_t* __restrict__ tile_base = nullptr, uint64_t hit_cap = ~0ull,
+                            uint32_t* __restrict__ overflow = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (t >= n_tiles) return;
   const uint32_t n = min(tile_count[t], cap);
   const uint64_t* tk = slots + t * cap;
-  const uint64_t tile_pos = t * tile_groups * 32ull;
+  const uint64_t tile_pos = tile_base ? tile_base[t] : t * tile_groups * 32ull;
   for (uint32_t i = lane; i < n; i += 32) {
     const uint64_t key = tk[i];
     const uint32_t pair = (uint32_t)(key >> 48);
@@ -118,7 +124,10 @@ __global__ void k_emit_hits(const uint64_t* __restrict__ slots, const uint32_t* 
     h.pattern = (uint16_t)(pair * 4u + ((key >> 8) & 3u));
     h.mism = (uint8_t)(key & 0xffu);
     h.flags = 0;
-    hits[o] = h;
+    if (o < hit_cap)
+      hits[o] = h;
+    else if (overflow)
+      atomicOr(overflow, 2u);
   }
 }
 
@@ -130,7 +139,125 @@ __global__ void k_pair_offsets(const uint64_t* __restrict__ off, uint64_t n_tile
 
 }  // namespace
 
-ah_status scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out) {
+void launch_scan_kernel(cudaStream_t s, const ScanKernel& k, const ah_batch* b, uint64_t* slots, uint32_t* tile_count,
+                        uint32_t cap, uint32_t* status, unsigned long long* work, uint64_t n_tiles, int grid) {
+  // whole batch, tiles of threads * groups_per_thread groups; grid > 0 selects the persistent form
+  const uint64_t tg = (uint64_t)k.threads * k.groups_per_thread;
+  ScanParamsHost P{b->planes, b->invalid, b->rec_group, b->rec_len, b->n_records, cap, 0, b->n_groups,
+                   slots, tile_count, status, tg, work, n_tiles};
+  void* args[] = {&P};
+  cudaLaunchKernel((const void*)k.fn, dim3((unsigned)(grid > 0 ? grid : n_tiles)), dim3((unsigned)k.threads), args, 0, s);
+}
+
+void launch_tile_max(cudaStream_t s, const uint32_t* tile_count, uint64_t n_tiles, uint32_t* out) {
+  k_tile_max<<<std::max<uint64_t>(1, std::min<uint64_t>(1024, (n_tiles + 255) / 256)), 256, 0, s>>>(tile_count, n_tiles,
+                                                                                                     out);
+}
+
+// shared memory the tile sort needs for slot lists of `cap` keys; sets the kernel attribute when that
+// exceeds the default (call before any stream capture)
+size_t prepare_tile_sort(uint32_t cap, int* warps_out) {
+  uint32_t cap_pow2 = 2;
+  while (cap_pow2 < cap) cap_pow2 <<= 1;
+  const int warps = (int)std::max<uint32_t>(1, std::min<uint32_t>(8, 16384 / cap_pow2));
+  const size_t smem = (size_t)warps * cap_pow2 * sizeof(uint64_t);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (warps_out) *warps_out = warps;
+  return smem;
+}
+
+void launch_tile_sort(cudaStream_t s, uint64_t* slots, const uint32_t* tile_count, uint32_t cap, uint64_t n_tiles,
+                      uint32_t n_pairs, uint32_t* tpc) {
+  uint32_t cap_pow2 = 2;
+  while (cap_pow2 < cap) cap_pow2 <<= 1;
+  const int warps = (int)std::max<uint32_t>(1, std::min<uint32_t>(8, 16384 / cap_pow2));
+  const size_t smem = (size_t)warps * cap_pow2 * sizeof(uint64_t);
+  k_tile_sort<<<(unsigned)((n_tiles + warps - 1) / warps), warps * 32, smem, s>>>(slots, tile_count, cap, cap_pow2,
+                                                                                  n_tiles, n_pairs, tpc);
+}
+
+void launch_emit_hits(cudaStream_t s, const uint64_t* slots, const uint32_t* tile_count, uint32_t cap, uint64_t n_tiles,
+                      uint64_t tile_groups, const uint64_t* off, const ah_batch* b, ah_hit* hits,
+                      const uint64_t* tile_base, uint64_t hit_cap, uint32_t* overflow, uint64_t* pair_off,
+                      uint32_t n_pairs) {
+  k_emit_hits<<<(unsigned)((n_tiles + 7) / 8), 256, 0, s>>>(slots, tile_count, cap, n_tiles, tile_groups, off,
+                                                            b->rec_group, b->n_records, hits, tile_base, hit_cap, overflow);
+  k_pair_offsets<<<(n_pairs + 256) / 256, 256, 0, s>>>(off, n_tiles, n_pairs, pair_off);
+}
+
+namespace {
+
+// persistent grid: resident CTAs per SM x SMs
+int persistent_grid(ah_ctx* ctx, const ScanKernel& k) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k.fn, k.threads, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm * ctx->sm_count;
+}
+
+// Launch the scan over the batch.  per_record: one launch per record and pair (the plain form),
+// otherwise one launch over everything (grid of tiles, or persistent CTAs).
+ah_status launch_scan(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ScanConfig& cfg, bool per_record,
+                      uint64_t tile_groups, uint64_t n_tiles, uint64_t* slots, uint32_t* tile_count, uint32_t cap) {
+  ah_status st;
+  if (!per_record) {
+    ScanKernel kern;
+    if ((st = ctx->jit->get(ctx, p->pats, cfg, &kern))) return st;
+    unsigned long long* work = nullptr;
+    if (cfg.persistent) {
+      if ((st = dalloc(ctx, &work, 1))) return st;
+      AH_CUDA(ctx, cudaMemsetAsync(work, 0, sizeof *work, ctx->stream));
+    }
+    if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
+    for (uint64_t t0 = 0; t0 < n_tiles; t0 += 0x7fffffffull) {
+      const uint64_t nt = std::min<uint64_t>(0x7fffffffull, n_tiles - t0);
+      const uint64_t g0 = t0 * tile_groups;
+      ScanParamsHost P{b->planes, b->invalid, b->rec_group, b->rec_len, b->n_records, cap, g0,
+                       std::min<uint64_t>(b->n_groups - std::min(b->n_groups, g0), nt * tile_groups),
+                       slots, tile_count, ctx->d_status, tile_groups, work, nt};
+      void* args[] = {&P};
+      const unsigned grid = cfg.persistent ? (unsigned)std::min<uint64_t>(nt, persistent_grid(ctx, kern)) : (unsigned)nt;
+      cudaError_t le = cudaLaunchKernel((const void*)kern.fn, dim3(grid), dim3((unsigned)cfg.threads), args, 0,
+                                        ctx->stream);
+      if (le != cudaSuccess) return fail(ctx, AH_ECUDA, "scan kernel launch failed: %s", cudaGetErrorString(le));
+      launched(ctx);
+      ctx->n_scan_launches++;
+      if (cfg.persistent && t0 + nt < n_tiles) AH_CUDA(ctx, cudaMemsetAsync(work, 0, sizeof *work, ctx->stream));
+    }
+    if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
+    dfree(ctx, work);
+    ctx->scan_bases += b->n_bases;
+    return AH_OK;
+  }
+  // one launch per record per pair, each with the pair's four oriented patterns
+  const uint64_t blk_groups = (uint64_t)cfg.threads * cfg.groups_per_thread;
+  if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
+  for (uint32_t pair = 0; pair < p->n_pairs; ++pair) {
+    std::vector<Pattern> pats(p->pats.begin() + 4 * pair, p->pats.begin() + 4 * pair + 4);
+    ScanKernel kern;
+    if ((st = ctx->jit->get(ctx, pats, cfg, &kern))) return st;
+    for (uint32_t r = 0; r < b->n_records; ++r) {
+      const uint64_t g0 = b->h_rec_group[r];
+      const uint64_t ng = ((uint64_t)b->h_rec_len[r] + 63) / 64 * 2;
+      if (ng == 0) continue;
+      ScanParamsHost P{b->planes, b->invalid, b->rec_group, b->rec_len, b->n_records, cap, g0, ng,
+                       slots, tile_count, ctx->d_status, tile_groups, nullptr, 0};
+      void* args[] = {&P};
+      cudaError_t le = cudaLaunchKernel((const void*)kern.fn, dim3((unsigned)((ng + blk_groups - 1) / blk_groups)),
+                                        dim3((unsigned)cfg.threads), args, 0, ctx->stream);
+      if (le != cudaSuccess) return fail(ctx, AH_ECUDA, "scan kernel launch failed: %s", cudaGetErrorString(le));
+      launched(ctx);
+      ctx->n_scan_launches++;
+    }
+  }
+  if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
+  ctx->scan_bases += b->n_bases * p->n_pairs;
+  return AH_OK;
+}
+
+// scan, then sort / count / place the sites; shared by the one-launch and per-record forms
+ah_status scan_sites(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, bool per_record, ah_hits** out) {
   *out = nullptr;
   ScanConfig cfg = ctx->scan_cfg;
   const uint32_t n_pairs = p->n_pairs;
@@ -141,39 +268,19 @@ ah_status scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_h
   if ((st = dalloc(ctx, &d_max, 1))) return st;
   uint64_t n_tiles = 0, tile_groups = 0;
   uint32_t cap = (uint32_t)cfg.slot_cap;
-  for (int attempt = 0;; ++attempt) {
-    ScanKernel kern;
-    if ((st = ctx->jit->get(ctx, p->pats, cfg, &kern))) break;
+  for (;;) {
     tile_groups = (uint64_t)cfg.threads * cfg.groups_per_thread;
     n_tiles = std::max<uint64_t>(1, (b->n_groups + tile_groups - 1) / tile_groups);
     if ((st = dalloc(ctx, &slots, n_tiles * cap))) break;
     if ((st = dalloc(ctx, &tile_count, n_tiles))) break;
     AH_CUDA(ctx, cudaMemsetAsync(tile_count, 0, n_tiles * sizeof(uint32_t), ctx->stream));
     AH_CUDA(ctx, cudaMemsetAsync(d_max, 0, sizeof(uint32_t), ctx->stream));
-    ScanParamsHost P{b->planes, b->invalid, b->rec_group, b->rec_len, b->n_records, cap, 0, b->n_groups,
-                     slots, tile_count, ctx->d_status, 0};
-    if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
-    for (uint64_t t0 = 0; t0 < n_tiles; t0 += 0x7fffffffull) {
-      uint64_t nt = std::min<uint64_t>(0x7fffffffull, n_tiles - t0);
-      P.tile_begin = t0;
-      P.group_begin = t0 * tile_groups;
-      P.n_groups = std::min<uint64_t>(b->n_groups - std::min(b->n_groups, P.group_begin), nt * tile_groups);
-      void* args[] = {&P};
-      cudaError_t le = cudaLaunchKernel((const void*)kern.fn, dim3((unsigned)nt), dim3((unsigned)cfg.threads), args, 0,
-                                        ctx->stream);
-      if (le != cudaSuccess) return fail(ctx, AH_ECUDA, "scan kernel launch failed: %s", cudaGetErrorString(le));
-      launched(ctx);
-      ctx->n_scan_launches++;
-    }
-    if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
-    ctx->scan_bases += b->n_bases;
-    k_tile_max<<<std::max<uint64_t>(1, std::min<uint64_t>(1024, (n_tiles + 255) / 256)), 256, 0, ctx->stream>>>(
-        tile_count, n_tiles, d_max);
+    if ((st = launch_scan(ctx, b, p, cfg, per_record, tile_groups, n_tiles, slots, tile_count, cap))) break;
+    launch_tile_max(ctx->stream, tile_count, n_tiles, d_max);
     launched(ctx);
-    uint32_t mx = 0;
-    AH_CUDA(ctx, cudaMemcpyAsync(ctx->h_status + 0, d_max, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    AH_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, d_max, 4, cudaMemcpyDeviceToHost, ctx->stream));
     AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    mx = *ctx->h_status;
+    const uint32_t mx = *ctx->h_status;
     *ctx->h_status = 0;
     if (ctx->timing) {
       float ms = 0.f;
@@ -210,14 +317,8 @@ ah_status scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_h
   if ((st = dalloc(ctx, &tpc, n_cells))) return st;
   if ((st = dalloc(ctx, &off, n_cells + 1))) return st;
   AH_CUDA(ctx, cudaMemsetAsync(tpc, 0, n_cells * sizeof(uint32_t), ctx->stream));
-  uint32_t cap_pow2 = 2;
-  while (cap_pow2 < cap) cap_pow2 <<= 1;
-  int warps = (int)std::max<uint32_t>(1, std::min<uint32_t>(8, 16384 / cap_pow2));
-  size_t smem = (size_t)warps * cap_pow2 * sizeof(uint64_t);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  uint64_t blocks = (n_tiles + warps - 1) / warps;
-  k_tile_sort<<<(unsigned)blocks, warps * 32, smem, ctx->stream>>>(slots, tile_count, cap, cap_pow2, n_tiles, n_pairs,
-                                                                     tpc);
+  prepare_tile_sort(cap, nullptr);
+  launch_tile_sort(ctx->stream, slots, tile_count, cap, n_tiles, n_pairs, tpc);
   launched(ctx);
   AH_CUDA(ctx, cudaGetLastError());
   if ((st = exclusive_scan_u32(ctx, tpc, off, n_cells))) return st;
@@ -231,9 +332,8 @@ ah_status scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_h
     ah_hits_free(h);
     return st;
   }
-  k_emit_hits<<<(unsigned)((n_tiles + 7) / 8), 256, 0, ctx->stream>>>(slots, tile_count, cap, n_tiles, tile_groups, off,
-                                                                      b->rec_group, b->n_records, h->d);
-  k_pair_offsets<<<(n_pairs + 256) / 256, 256, 0, ctx->stream>>>(off, n_tiles, n_pairs, h->d_pair_off);
+  launch_emit_hits(ctx->stream, slots, tile_count, cap, n_tiles, tile_groups, off, b, h->d, nullptr, ~0ull, nullptr,
+                   h->d_pair_off, n_pairs);
   launched(ctx, 2);
   AH_CUDA(ctx, cudaGetLastError());
   h->h_pair_off.resize(n_pairs + 1);
@@ -250,6 +350,16 @@ ah_status scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_h
   }
   *out = h;
   return AH_OK;
+}
+
+}  // namespace
+
+ah_status scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out) {
+  return scan_sites(ctx, b, p, false, out);
+}
+
+ah_status scan_primers_per_record(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out) {
+  return scan_sites(ctx, b, p, true, out);
 }
 
 }  // namespace ah

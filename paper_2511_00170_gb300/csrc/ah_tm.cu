@@ -278,9 +278,10 @@ __device__ __forceinline__ uint8_t base_code(const uint2* planes, uint64_t group
 
 __global__ void k_tm_hits(const ah_hit* __restrict__ hits, uint64_t n, const uint2* __restrict__ planes,
                           const uint64_t* __restrict__ rec_group, const uint8_t* __restrict__ plen,
-                          const uint8_t* __restrict__ psets, const TmRun R, double* __restrict__ out) {
+                          const uint8_t* __restrict__ psets, const TmRun R, double* __restrict__ out,
+                          const uint64_t* __restrict__ d_n = nullptr) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || (d_n && i >= *d_n)) return;
   const ah_hit h = hits[i];
   const int L = plen[h.pattern];
   const uint32_t pair = h.pattern >> 2, primer = h.pattern & 1u, strand = (h.pattern >> 1) & 1u;
@@ -296,9 +297,13 @@ __global__ void k_tm_hits(const ah_hit* __restrict__ hits, uint64_t n, const uin
 }
 
 __global__ void k_tm_amps(ah_amplicon* __restrict__ a, uint64_t n, const double* __restrict__ hit_tm, int filter,
-                          double min_tm, uint32_t* __restrict__ keep) {
+                          double min_tm, uint32_t* __restrict__ keep, const uint64_t* __restrict__ d_n = nullptr) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (d_n && i >= *d_n) {
+    if (keep) keep[i] = 0;
+    return;
+  }
   ah_amplicon m = a[i];
   const double ti = hit_tm[m.hit_i], tj = hit_tm[m.hit_j];
   const bool undefined = isnan(ti) || isnan(tj);
@@ -331,6 +336,28 @@ __global__ void k_tm_duplexes(const uint8_t* __restrict__ v, const uint8_t* __re
 }
 
 }  // namespace
+
+ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, size_t run_size) {
+  ah_status st;
+  if ((st = load_tables(ctx))) return st;
+  if (run_size < sizeof(TmRun)) return fail(ctx, AH_EINTERNAL, "tm_prepare: buffer too small");
+  return make_run(ctx, params, (TmRun*)run_out);
+}
+
+void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit_cap, const uint64_t* d_nhits,
+               const uint2* planes, const uint64_t* rec_group, const uint8_t* plen, const uint8_t* psets, double* hit_tm,
+               ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep) {
+  const TmRun R = *(const TmRun*)run;
+  k_tm_hits<<<(unsigned)std::max<uint64_t>(1, (hit_cap + 127) / 128), 128, 0, s>>>(hits, hit_cap, planes, rec_group,
+                                                                                  plen, psets, R, hit_tm, d_nhits);
+  k_tm_amps<<<(unsigned)std::max<uint64_t>(1, (amp_cap + 255) / 256), 256, 0, s>>>(amps, amp_cap, hit_tm, filter,
+                                                                                  min_tm, keep, d_namps);
+}
+
+void launch_compact_amps(cudaStream_t s, const ah_amplicon* in, uint64_t cap, const uint32_t* keep, const uint64_t* off,
+                         ah_amplicon* out) {
+  k_compact_amps<<<(unsigned)std::max<uint64_t>(1, (cap + 255) / 256), 256, 0, s>>>(in, cap, keep, off, out);
+}
 
 ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a,
                     const ah_tm_params* params) {

@@ -1,4 +1,5 @@
 // Shared device utilities: error reporting, status word, device-wide exclusive scan, packing.
+#include <algorithm>
 #include <cstdarg>
 #include <cstring>
 
@@ -145,7 +146,26 @@ ah_status exclusive_scan(ah_ctx* ctx, const T* d_in, uint64_t* d_out, uint64_t n
   AH_CUDA(ctx, cudaGetLastError());
   return AH_OK;
 }
+template <class T>
+void exclusive_scan_s(cudaStream_t s, const T* d_in, uint64_t* d_out, uint64_t n, uint64_t* sums) {
+  if (n == 0) {
+    cudaMemsetAsync(d_out, 0, sizeof(uint64_t), s);
+    return;
+  }
+  const uint64_t nb = (n + kScanTile - 1) / kScanTile;
+  k_block_sums<T><<<(unsigned)nb, kScanThreads, 0, s>>>(d_in, n, sums);
+  k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb, d_out + n);
+  k_scan_apply<T><<<(unsigned)nb, kScanThreads, 0, s>>>(d_in, n, sums, d_out);
+}
 }  // namespace
+
+uint64_t scan_scratch_elems(uint64_t n) { return std::max<uint64_t>(1, (n + kScanTile - 1) / kScanTile); }
+void exclusive_scan_u32_s(cudaStream_t s, const uint32_t* d_in, uint64_t* d_out, uint64_t n, uint64_t* scratch) {
+  exclusive_scan_s<uint32_t>(s, d_in, d_out, n, scratch);
+}
+void exclusive_scan_u64_s(cudaStream_t s, const uint64_t* d_in, uint64_t* d_out, uint64_t n, uint64_t* scratch) {
+  exclusive_scan_s<uint64_t>(s, d_in, d_out, n, scratch);
+}
 
 ah_status exclusive_scan_u32(ah_ctx* ctx, const uint32_t* d_in, uint64_t* d_out, uint64_t n) {
   return exclusive_scan<uint32_t>(ctx, d_in, d_out, n);

@@ -115,6 +115,23 @@ class Engine:
             ah.ah_hits_free(hits)
             ah.ah_amplicons_free(amps)
 
+    def plan(self, batch, p: Params, with_seqs: bool = True, autotune: bool = False, persistent: int = -1, **caps):
+        """A graph-captured plan of the whole step over `batch` (see ah_plan_create)."""
+        prm = ah.plan_params(p.min_len, p.max_len, p.orient_mask, p.tm_params(), with_seqs, p.trim, p.fb_len, p.rb_len,
+                             autotune, persistent, **caps)
+        return ah.ah_plan_create(self.ctx, batch, self.primers(p), prm)
+
+    def plan_output(self, plan, with_seqs: bool = True) -> Output:
+        hits, amps = ah.ah_plan_results(plan, self.ctx)
+        try:
+            h = ah.ah_hits_copy(hits)
+            a = ah.ah_amplicons_copy(amps)
+            arena, off = ah.ah_amplicons_seq_copy(amps) if with_seqs else (None, None)
+            return Output(h, a, arena, off)
+        finally:
+            ah.ah_hits_free(hits)
+            ah.ah_amplicons_free(amps)
+
     def run_workload(self, wl, with_seqs: bool = True) -> Output:
         batch = self.pack(wl.seq, wl.offsets, wl.genome_ids)
         try:

@@ -1,0 +1,108 @@
+"""Batched forms through the C ABI (needs a GPU): the graph-captured plan (autotuned, persistent or
+not, with capacities that overflow and grow) and the one-launch-per-record-per-pair scan give
+exactly the outputs of the regular path, which the parity tests pin to the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def engine():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2511_00170_gb300.pipeline import Engine
+
+    e = Engine(0)
+    yield e
+    e.close()
+
+
+def _same(a, b):
+    assert a.hits.tobytes() == b.hits.tobytes()
+    assert a.amps.tobytes() == b.amps.tobytes()
+    assert (a.arena or b"") == (b.arena or b"")
+    if a.field_off is not None:
+        assert np.array_equal(a.field_off, b.field_off)
+
+
+@pytest.mark.parametrize("persistent,autotune", [(0, False), (1, False), (-1, True)])
+def test_plan_matches_regular_path_and_oracle(engine, persistent, autotune):
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Params
+
+    wl = synth.batched(n_genomes=60, len_lo=5e3, len_hi=4e5, n_pairs=4)
+    wl.tm.min_tm = 30.0
+    wl.trim, wl.fb_len, wl.rb_len = True, 12, 9
+    p = Params.from_workload(wl)
+    batch = engine.pack(wl.seq, wl.offsets)
+    try:
+        ref = engine.step(batch, p)
+        plan = engine.plan(batch, p, with_seqs=True, autotune=autotune, persistent=persistent)
+        try:
+            for _ in range(3):   # replays of the same graph
+                ah.ah_plan_run(plan, engine.ctx)
+            out = engine.plan_output(plan)
+            info = ah.ah_plan_info_get(plan)
+        finally:
+            ah.ah_plan_free(plan)
+    finally:
+        ah.ah_batch_free(batch)
+    _same(out, ref)
+    assert info["n_hits"] == len(ref.hits) and info["n_kept"] == len(ref.amps)
+    if persistent == 1:
+        assert info["persistent"] == 1
+    orc = oracle.run(wl)
+    compare.assert_same_hits(out, orc)
+    compare.assert_same_amplicons(out, orc, filtered=True)
+    compare.assert_same_sequences(out, orc)
+
+
+def test_plan_grows_capacities(engine):
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Params
+
+    wl = synth.plain_small(n_genomes=5, len_lo=100_000, len_hi=300_000)
+    p = Params.from_workload(wl)
+    batch = engine.pack(wl.seq, wl.offsets)
+    try:
+        ref = engine.step(batch, p)
+        ah.ah_ctx_set_scan_config(engine.ctx, 128, 8, 16, 0)
+        plan = engine.plan(batch, p, hit_capacity=3, amp_capacity=1, arena_capacity=5)
+        try:
+            with pytest.raises(ah.AhError) as e:
+                ah.ah_plan_launch(plan, engine.ctx)
+                ah.ah_plan_check(plan, engine.ctx)
+            assert e.value.status == ah.AH_EOVERFLOW
+            ah.ah_plan_run(plan, engine.ctx)
+            out = engine.plan_output(plan)
+        finally:
+            ah.ah_plan_free(plan)
+            ah.ah_ctx_set_scan_config(engine.ctx, 128, 8, 256, 0)
+    finally:
+        ah.ah_batch_free(batch)
+    _same(out, ref)
+
+
+def test_per_record_scan_matches(engine):
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Params
+
+    wl = synth.batched(n_genomes=25, len_lo=1e3, len_hi=3e5, n_pairs=3)
+    p = Params.from_workload(wl)
+    batch = engine.pack(wl.seq, wl.offsets)
+    try:
+        pr = engine.primers(p)
+        h1 = ah.ah_scan_primers(engine.ctx, batch, pr)
+        h2 = ah.ah_scan_primers_per_record(engine.ctx, batch, pr)
+        a, b = ah.ah_hits_copy(h1), ah.ah_hits_copy(h2)
+        ah.ah_hits_free(h1)
+        ah.ah_hits_free(h2)
+    finally:
+        ah.ah_batch_free(batch)
+    assert len(a) > 0 and a.tobytes() == b.tobytes()

@@ -106,6 +106,21 @@ def test_dense_sites_overflow_retry(engine):
     assert len(ref.hits) > 500_000
 
 
+@pytest.mark.parametrize("threads,gpt,slots,shift", [(256, 4, 256, 1), (256, 4, 256, 2), (128, 1, 16, 0),
+                                                     (512, 8, 64, 2), (64, 16, 4096, 1)])
+def test_scan_shapes_and_shift_modes(engine, threads, gpt, slots, shift):
+    """Every kernel shape and pattern-alignment mode gives the same sites (tiny slot lists force the
+    overflow re-run)."""
+    from paper_2511_00170_gb300 import ah
+
+    ah.ah_ctx_set_scan_config(engine.ctx, threads, gpt, slots, shift)
+    try:
+        _run_both(engine, synth.batched(n_genomes=12, len_lo=2e3, len_hi=3e5, n_pairs=3))
+        _run_both(engine, _random_case(1000 + threads + gpt + shift))
+    finally:
+        ah.ah_ctx_set_scan_config(engine.ctx, 256, 4, 256, 0)
+
+
 def test_several_pairs(engine):
     wl = synth.batched(n_genomes=40, len_lo=2e3, len_hi=2e5, n_pairs=8)
     _run_both(engine, wl)
