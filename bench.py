@@ -314,6 +314,155 @@ def run_engine(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------------------------------ batched arm
+def run_batched(args):
+    """The batched workload (many genomes x 8 pairs) as one graph-captured plan, against the plain
+    form (one scan launch per genome per pair) and the one-launch scan on the same GPU."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth.gpu as sg
+
+    __graft_entry__.build()
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Engine, Params
+
+    torch.cuda.set_device(0)
+    t_gen = time.perf_counter()
+    wl = sg.batched(n_genomes=args.genomes or 50_000)
+    eng = Engine(0)
+    batch = eng.pack_device(wl.d_seq.data_ptr(), wl.offsets.astype(np.uint64), wl.genome_ids)
+    ah.ah_ctx_synchronize(eng.ctx)
+    gen_s = time.perf_counter() - t_gen
+    del wl.d_seq
+    torch.cuda.empty_cache()
+    p = Params(wl.fwd, wl.rev, wl.k, wl.clamp, wl.min_len, wl.max_len, wl.orient_mask)
+    stream = torch.cuda.ExternalStream(ah.ah_ctx_stream(eng.ctx))
+    t0 = time.perf_counter()
+    plan = eng.plan(batch, p, with_seqs=True, autotune=True, persistent=-1)
+    plan_s = time.perf_counter() - t0
+    info = ah.ah_plan_info_get(plan)
+    for _ in range(max(3, args.warmup)):
+        ah.ah_plan_run(plan, eng.ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            ah.ah_plan_launch(plan, eng.ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ah.ah_plan_check(plan, eng.ctx)
+    info = ah.ah_plan_info_get(plan)
+    # the same scan kernel timed alone (regular path, the plan's shape), for the roofline
+    ah.ah_ctx_set_scan_config(eng.ctx, info["threads"], info["groups_per_thread"], 256, info["shift_mode"])
+    pr = eng.primers(p)
+    ah.ah_ctx_stats_reset(eng.ctx)
+    ah.ah_ctx_set_timing(eng.ctx, True)
+    for _ in range(3):
+        h = ah.ah_scan_primers(eng.ctx, batch, pr)
+        ah.ah_hits_free(h)
+    st = ah.ah_ctx_stats_get(eng.ctx)
+    scan_ms = st["scan_ms"] / st["scan_launches"]
+    # the plain form: one launch per genome per pair
+    ah.ah_ctx_stats_reset(eng.ctx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = ah.ah_scan_primers_per_record(eng.ctx, batch, pr)
+    per_record_s = time.perf_counter() - t0
+    n_pr = ah.ah_hits_count(h)
+    ah.ah_hits_free(h)
+    st2 = ah.ah_ctx_stats_get(eng.ctx)
+    ah.ah_ctx_set_timing(eng.ctx, False)
+    ops = alg_ops_per_base(wl.fwd, wl.rev, wl.clamp)
+    achieved = ops * wl.total_bp / (scan_ms * 1e-3) / 1e12
+    line = {"metric": METRIC, "workload": "batched", "value": wl.total_bp / (ms * 1e-3) / 1e9, "unit": "Gbp/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "u32+f64", "data": "synthetic",
+            "config": {"workload": f"batched: {wl.n_records} genomes log-uniform 10 kbp-12 Mbp, "
+                                   f"{wl.total_bp / 1e9:.2f} Gbp, {len(wl.fwd)} pairs of 17-26 nt, k=i mod 4, "
+                                   "graph-captured plan (scan, compaction, pairing, Tm, extraction)",
+                       "bases": wl.total_bp, "patterns": 4 * len(wl.fwd)},
+            "plan": {k: info[k] for k in ("threads", "groups_per_thread", "shift_mode", "persistent", "grid",
+                                          "n_hits", "n_amps", "arena_bytes")},
+            "plan_create_s": plan_s, "autotune_ms": info["autotune_ms"], "generate_and_pack_s": gen_s,
+            "scan_kernel_ms": scan_ms,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tlane-op/s",
+                         "frac": achieved / ALU_PEAK_TOPS, "ops_per_base": ops},
+            "plain_per_record": {"launches": st2["scan_launches"], "seconds": per_record_s,
+                                 "gbps": wl.total_bp / per_record_s / 1e9, "hits": n_pr,
+                                 "note": "scan stage only, one launch per genome per pair, wall clock"},
+            "plan_speedup_vs_plain_scan": per_record_s / (ms * 1e-3),
+            "clocks": clk.summary()}
+    ah.ah_plan_free(plan)
+    ah.ah_batch_free(batch)
+    eng.close()
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------ serving arm
+def run_serving(args):
+    """A Poisson request stream against a device-resident database, continuous batching."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+    import synth.gpu as sg
+
+    __graft_entry__.build()
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Engine
+
+    torch.cuda.set_device(0)
+    n_db = args.genomes or 40_000
+    lengths, _ = sg.serving_layout(n_genomes=n_db)
+    eng = Engine(0)
+    t0 = time.perf_counter()
+    db = ah.ah_batch_create(eng.ctx, np.asarray(lengths, dtype=np.uint64))
+    for first, d, offs in sg.serving_db_chunks(n_genomes=n_db):
+        ah.ah_batch_pack_range(eng.ctx, db, first, d.data_ptr(), offs.astype(np.uint64))
+        del d
+        torch.cuda.empty_cache()
+    gen_s = time.perf_counter() - t0
+    db_bp = int(sum(lengths))
+    trace = synth.serving_trace(synth.SEED, args.requests, args.rate, n_db)
+    srv = ah.ah_server_create(db, n_slots=args.slots)
+    keys = ("fwd", "rev", "k", "clamp", "first_record", "n_records", "min_len", "max_len", "orient_mask")
+    t_start = time.perf_counter()
+    tickets = []
+    with ClockSampler(0) as clk:
+        for r in trace:
+            delay = t_start + r["arrival"] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(ah.ah_server_submit(srv, **{k: r[k] for k in keys}))
+        res = [ah.ah_server_wait(srv, t) for t in tickets]
+    ah.ah_server_destroy(srv)
+    lat = np.array([x["t_done"] - x["t_submit"] for x in res])
+    wait = np.array([x["t_admit"] - x["t_submit"] for x in res])
+    span = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
+    bases = sum(x["bases"] for x in res)
+    pattern_bases = sum(x["bases"] * 4 * len(r["fwd"]) for x, r in zip(res, trace))
+    line = {"metric": METRIC, "workload": "serving", "value": bases / span / 1e9, "unit": "Gbp/s",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"serving: {n_db} genomes ({db_bp / 1e9:.1f} Gbp, "
+                                   f"{db_bp / 4e9:.1f} GB packed) resident; Poisson {args.rate} req/s, "
+                                   f"{args.requests} requests of 1-32 pairs (17-26 nt, k 0-3) over contiguous "
+                                   "subsets of 1-100 % of the database", "slots": args.slots},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean()), "max": float(lat.max())},
+            "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+            "completed": len(res), "makespan_s": span, "offered_rate": args.rate,
+            "served_rate": len(res) / span, "pattern_gbp_per_s": pattern_bases / span / 1e9,
+            "db_build_s": gen_s, "clocks": clk.summary()}
+    ah.ah_batch_free(db)
+    eng.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,9 +475,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--slots", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_engine(args)
 

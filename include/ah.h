@@ -75,6 +75,8 @@ typedef struct {
   uint64_t scan_launches;   /* launches of the scan kernel */
   double scan_ms;           /* summed device time of those launches (timing enabled) */
   uint64_t scan_bases;      /* bases covered by those launches */
+  uint64_t jit_compiles;    /* scan kernels compiled at run time (NVRTC) */
+  double jit_ms;            /* host time spent compiling them */
 } ah_ctx_stats;
 ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out);
 ah_status ah_ctx_stats_reset(ah_ctx* ctx);
@@ -128,7 +130,19 @@ ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, co
 ah_status ah_pack_batch_device(ah_ctx* ctx, uint32_t n_rec, const uint8_t* d_seq, const uint64_t* h_offsets,
                                const uint32_t* genome_ids, ah_batch** out);
 
+/* Streaming: lay out a batch for n_rec records of the given lengths (device memory allocated, nothing
+ * packed), then pack consecutive record ranges into it with ah_batch_pack_range.  Synchronises. */
+ah_status ah_batch_create(ah_ctx* ctx, uint32_t n_rec, const uint64_t* lens, const uint32_t* genome_ids, ah_batch** out);
+/* Pack records [first, first + count) of b from device memory: d_seq holds them back to back and
+ * h_offsets (host, count + 1 entries, starting at 0) delimits them; their lengths must match the
+ * layout.  Synchronises (d_seq may be released afterwards). */
+ah_status ah_batch_pack_range(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t count, const uint8_t* d_seq,
+                              const uint64_t* h_offsets);
 ah_status ah_batch_view_get(const ah_batch* b, ah_batch_view* out);
+/* A view of records [first, first + count) of `db` that shares db's packed planes (no copy) and owns
+ * only a record table rebased to the slice; record indices in results are relative to `first`.
+ * Any context on db's device may create and use it; db must outlive it.  Synchronises. */
+ah_status ah_batch_slice(ah_ctx* ctx, const ah_batch* db, uint32_t first, uint32_t count, ah_batch** out);
 void ah_batch_free(ah_batch* b);
 
 /* ------------------------------------------------------------------------------------------ */
@@ -318,6 +332,52 @@ ah_status ah_plan_info_get(const ah_plan* plan, ah_plan_info* out);
 /* Copies of the last run's sites and (kept) amplicons, with sequences when extraction is on. */
 ah_status ah_plan_results(ah_plan* plan, ah_hits** hits, ah_amplicons** amps);
 void ah_plan_free(ah_plan* plan);
+
+/* ------------------------------------------------------------------------------------------ */
+/* serving: continuous batching over a device-resident database                                 */
+/*
+ * A server keeps one packed batch (the database) resident and runs requests on `n_slots` workers,
+ * each with its own context, CUDA stream and host thread.  Requests wait in arrival order; the
+ * oldest is admitted as soon as a worker is free and its estimated device memory fits under the
+ * budget beside the requests already running (a request alone on the device is always admitted),
+ * so requests that arrive while others run join as slots and memory free up and their kernels
+ * overlap on the GPU.  A request runs the whole path on a slice of the database (no genome copy).
+ */
+typedef struct ah_server ah_server;
+typedef struct {
+  uint32_t n_pairs;
+  const char* const* fwd; /* copied at submission */
+  const char* const* rev;
+  const uint8_t* k;
+  uint8_t clamp;
+  uint32_t first_record, n_records; /* the genome subset: a contiguous range of database records */
+  uint32_t min_len, max_len, orient_mask;
+  ah_tm_params tm;
+  int32_t extract, trim;
+  uint32_t fb_len, rb_len;
+} ah_request;
+typedef struct {
+  ah_status status;
+  uint64_t n_hits, n_amps, arena_bytes, bases;
+  ah_hit* hits;          /* host arrays owned by the result; record indices are database indices */
+  ah_amplicon* amps;
+  char* arena;           /* when extraction was requested */
+  uint64_t* field_off;   /* 5 * n_amps + 1 */
+  double t_submit, t_admit, t_done; /* seconds on the server's clock */
+  char error[256];
+} ah_result;
+/* memory_budget: device bytes requests may reserve (0: 60 % of the free memory now).  The database
+ * must outlive the server. */
+ah_status ah_server_create(const ah_batch* db, int n_slots, uint64_t memory_budget, ah_server** out);
+/* Queue a request (copied); returns at once with a ticket.  AH_EINVAL on a bad record range. */
+ah_status ah_server_submit(ah_server* s, const ah_request* r, uint64_t* ticket);
+/* Block until the request is done; the result is the caller's (ah_result_free).  Returns the
+ * request's status. */
+ah_status ah_server_wait(ah_server* s, uint64_t ticket, ah_result** out);
+ah_status ah_server_now(const ah_server* s, double* seconds);
+void ah_result_free(ah_result* r);
+/* Finish queued requests, stop the workers and release the server. */
+void ah_server_destroy(ah_server* s);
 
 #ifdef __cplusplus
 }

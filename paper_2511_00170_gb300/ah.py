@@ -56,9 +56,25 @@ class ah_plan_info(ctypes.Structure):
                 ("autotune_ms", ctypes.c_double), ("best_scan_ms", ctypes.c_double)]
 
 
+class ah_request(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_uint32), ("fwd", ctypes.c_void_p), ("rev", ctypes.c_void_p), ("k", ctypes.c_void_p),
+                ("clamp", ctypes.c_uint8), ("first_record", ctypes.c_uint32), ("n_records", ctypes.c_uint32),
+                ("min_len", ctypes.c_uint32), ("max_len", ctypes.c_uint32), ("orient_mask", ctypes.c_uint32),
+                ("tm", ah_tm_params), ("extract", ctypes.c_int32), ("trim", ctypes.c_int32),
+                ("fb_len", ctypes.c_uint32), ("rb_len", ctypes.c_uint32)]
+
+
+class ah_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n_hits", ctypes.c_uint64), ("n_amps", ctypes.c_uint64),
+                ("arena_bytes", ctypes.c_uint64), ("bases", ctypes.c_uint64), ("hits", ctypes.c_void_p),
+                ("amps", ctypes.c_void_p), ("arena", ctypes.c_void_p), ("field_off", ctypes.c_void_p),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("error", ctypes.c_char * 256)]
+
+
 class ah_ctx_stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("scan_launches", ctypes.c_uint64), ("scan_ms", ctypes.c_double),
-                ("scan_bases", ctypes.c_uint64)]
+                ("scan_bases", ctypes.c_uint64), ("jit_compiles", ctypes.c_uint64), ("jit_ms", ctypes.c_double)]
 
 
 class ah_batch_view(ctypes.Structure):
@@ -83,6 +99,9 @@ SIGNATURES = {
     "ah_pack_batch": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
     "ah_pack_batch_device": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
     "ah_batch_view_get": (_I32, [_VP, ctypes.POINTER(ah_batch_view)]),
+    "ah_batch_slice": (_I32, [_VP, _VP, _U32, _U32, _PVP]),
+    "ah_batch_create": (_I32, [_VP, _U32, _VP, _VP, _PVP]),
+    "ah_batch_pack_range": (_I32, [_VP, _VP, _U32, _U32, _VP, _VP]),
     "ah_batch_free": (None, [_VP]),
     "ah_primers_create": (_I32, [_VP, _U32, _VP, _VP, _VP, ctypes.c_uint8, _PVP]),
     "ah_primers_free": (None, [_VP]),
@@ -110,6 +129,12 @@ SIGNATURES = {
     "ah_plan_info_get": (_I32, [_VP, ctypes.POINTER(ah_plan_info)]),
     "ah_plan_results": (_I32, [_VP, _PVP, _PVP]),
     "ah_plan_free": (None, [_VP]),
+    "ah_server_create": (_I32, [_VP, _I32, _U64, _PVP]),
+    "ah_server_submit": (_I32, [_VP, ctypes.POINTER(ah_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "ah_server_wait": (_I32, [_VP, _U64, ctypes.POINTER(ctypes.POINTER(ah_result))]),
+    "ah_server_now": (_I32, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "ah_result_free": (None, [ctypes.POINTER(ah_result)]),
+    "ah_server_destroy": (None, [_VP]),
 }
 
 _lib = None
@@ -208,6 +233,27 @@ def ah_batch_view_get(batch) -> dict:
     v = ah_batch_view()
     _check(load().ah_batch_view_get(batch, ctypes.byref(v)))
     return {f: getattr(v, f) for f, _ in ah_batch_view._fields_}
+
+
+def ah_batch_slice(ctx, db, first: int, count: int):
+    out = ctypes.c_void_p()
+    _check(load().ah_batch_slice(ctx, db, first, count, ctypes.byref(out)), ctx)
+    return out
+
+
+def ah_batch_create(ctx, lengths: np.ndarray, genome_ids: Optional[np.ndarray] = None):
+    lens = np.ascontiguousarray(lengths, dtype=np.uint64)
+    gid = None if genome_ids is None else np.ascontiguousarray(genome_ids, dtype=np.uint32)
+    out = ctypes.c_void_p()
+    _check(load().ah_batch_create(ctx, len(lens), lens.ctypes.data, None if gid is None else gid.ctypes.data,
+                                  ctypes.byref(out)), ctx)
+    return out
+
+
+def ah_batch_pack_range(ctx, batch, first: int, d_seq: int, offsets: np.ndarray) -> None:
+    """Pack records first .. first + len(offsets) - 2 from device memory (offsets start at 0)."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    _check(load().ah_batch_pack_range(ctx, batch, first, len(offsets) - 1, d_seq, offsets.ctypes.data), ctx)
 
 
 def ah_batch_free(batch) -> None:
@@ -387,3 +433,64 @@ def ah_plan_results(plan, ctx=None):
 
 def ah_plan_free(plan) -> None:
     load().ah_plan_free(plan)
+
+
+# ------------------------------------------------------------------------------------------ serving
+def ah_server_create(db, n_slots: int = 4, memory_budget: int = 0):
+    out = ctypes.c_void_p()
+    _check(load().ah_server_create(db, n_slots, memory_budget, ctypes.byref(out)))
+    return out
+
+
+def ah_server_submit(server, fwd: Sequence[str], rev: Sequence[str], k: Sequence[int], clamp: int, first_record: int,
+                     n_records: int, min_len: int, max_len: int, orient_mask: int = 15,
+                     tm: Optional[ah_tm_params] = None, extract: bool = True, trim: bool = False, fb_len: int = 0,
+                     rb_len: int = 0) -> int:
+    n = len(fwd)
+    fa = (ctypes.c_char_p * n)(*[x.encode("ascii") for x in fwd])
+    ra = (ctypes.c_char_p * n)(*[x.encode("ascii") for x in rev])
+    ka = np.ascontiguousarray(np.asarray(k, dtype=np.uint8))
+    r = ah_request(n, ctypes.cast(fa, ctypes.c_void_p), ctypes.cast(ra, ctypes.c_void_p), ka.ctypes.data, clamp,
+                   first_record, n_records, min_len, max_len, orient_mask, tm if tm is not None else tm_params(),
+                   int(bool(extract)), int(bool(trim)), fb_len, rb_len)
+    t = ctypes.c_uint64()
+    _check(load().ah_server_submit(server, ctypes.byref(r), ctypes.byref(t)))
+    return t.value
+
+
+def ah_server_wait(server, ticket: int) -> dict:
+    """Result of one request as host numpy arrays and timings (the C result is freed here)."""
+    p = ctypes.POINTER(ah_result)()
+    st = load().ah_server_wait(server, ticket, ctypes.byref(p))
+    if not p:
+        raise AhError(st, "ah_server_wait: unknown ticket")
+    r = p.contents
+    try:
+        if st != AH_OK:
+            raise AhError(st, r.error.decode(errors="replace"))
+        hits = np.ctypeslib.as_array(ctypes.cast(r.hits, ctypes.POINTER(ctypes.c_uint8)), (r.n_hits * 12,)).copy() \
+            .view(HIT_DTYPE) if r.n_hits else np.empty(0, HIT_DTYPE)
+        amps = np.ctypeslib.as_array(ctypes.cast(r.amps, ctypes.POINTER(ctypes.c_uint8)), (r.n_amps * 32,)).copy() \
+            .view(AMP_DTYPE) if r.n_amps else np.empty(0, AMP_DTYPE)
+        arena = ctypes.string_at(r.arena, r.arena_bytes) if r.arena else None
+        off = np.ctypeslib.as_array(ctypes.cast(r.field_off, ctypes.POINTER(ctypes.c_uint64)),
+                                    (5 * r.n_amps + 1,)).copy() if r.field_off else None
+        return {"hits": hits, "amps": amps, "arena": arena, "field_off": off, "bases": r.bases,
+                "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done}
+    finally:
+        load().ah_result_free(p)
+
+
+def ah_server_now(server) -> float:
+    t = ctypes.c_double()
+    _check(load().ah_server_now(server, ctypes.byref(t)))
+    return t.value
+
+
+def ah_server_destroy(server) -> None:
+    load().ah_server_destroy(server)
+
+
+def ah_result_free(result) -> None:
+    """Free a raw ah_result pointer (ah_server_wait already frees the ones it converts)."""
+    load().ah_result_free(result)

@@ -60,12 +60,16 @@ __global__ void k_pack(const uint8_t* __restrict__ src, const PackItem* __restri
 
 void free_batch_arrays(ah_batch* b) {
   if (!b || !b->ctx) return;
+  dfree(b->ctx, b->rec_group);
+  if (b->view) return;
   dfree(b->ctx, b->planes);
   dfree(b->ctx, b->invalid);
-  dfree(b->ctx, b->rec_group);
   dfree(b->ctx, b->rec_len);
   dfree(b->ctx, b->genome_id);
 }
+
+// a batch made on another context may be read by any context on the same device
+bool usable(const ah_ctx* ctx, const ah_batch* b) { return b->ctx == ctx || (b->ctx && b->ctx->device == ctx->device); }
 
 // record layout shared by both packing paths
 ah_status layout_batch(ah_ctx* ctx, uint32_t n_rec, const uint64_t* lens, const uint32_t* genome_ids, ah_batch* b) {
@@ -243,13 +247,15 @@ ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out) {
   out->scan_launches = ctx->n_scan_launches;
   out->scan_ms = ctx->scan_ms;
   out->scan_bases = ctx->scan_bases;
+  out->jit_compiles = ctx->jit_compiles;
+  out->jit_ms = ctx->jit_ms;
   return AH_OK;
 }
 
 ah_status ah_ctx_stats_reset(ah_ctx* ctx) {
   if (!ctx) return AH_EINVAL;
-  ctx->n_launches = ctx->n_scan_launches = ctx->scan_bases = 0;
-  ctx->scan_ms = 0.0;
+  ctx->n_launches = ctx->n_scan_launches = ctx->scan_bases = ctx->jit_compiles = 0;
+  ctx->scan_ms = ctx->jit_ms = 0.0;
   return AH_OK;
 }
 
@@ -360,6 +366,78 @@ ah_status ah_pack_batch_device(ah_ctx* ctx, uint32_t n_rec, const uint8_t* d_seq
   return AH_OK;
 }
 
+ah_status ah_batch_slice(ah_ctx* ctx, const ah_batch* db, uint32_t first, uint32_t count, ah_batch** out) {
+  if (!ctx || !db || !out) return fail(ctx, AH_EINVAL, "ah_batch_slice: NULL argument");
+  if (!usable(ctx, db)) return fail(ctx, AH_EINVAL, "ah_batch_slice: batch is on another device");
+  if (count == 0 || (uint64_t)first + count > db->n_records) return fail(ctx, AH_EINVAL, "ah_batch_slice: bad range");
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  ah_batch* s = new ah_batch();
+  s->ctx = ctx;
+  s->view = true;
+  s->n_records = count;
+  const uint64_t g0 = db->h_rec_group[first];
+  const uint64_t g1 = (uint64_t)first + count < db->n_records ? db->h_rec_group[first + count] : db->n_groups;
+  s->n_groups = g1 - g0;
+  s->alloc_groups = db->alloc_groups - g0;
+  s->planes = db->planes + g0;
+  s->invalid = db->invalid + g0;
+  s->rec_len = db->rec_len + first;
+  s->genome_id = db->genome_id + first;
+  s->h_rec_group.resize(count);
+  s->h_rec_len.assign(db->h_rec_len.begin() + first, db->h_rec_len.begin() + first + count);
+  uint64_t bases = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    s->h_rec_group[i] = db->h_rec_group[first + i] - g0;
+    bases += s->h_rec_len[i];
+  }
+  s->n_bases = bases;
+  ah_status st = dalloc(ctx, &s->rec_group, count);
+  if (!st) {
+    cudaError_t e = cudaMemcpyAsync(s->rec_group, s->h_rec_group.data(), count * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) st = fail(ctx, AH_ECUDA, "ah_batch_slice: %s", cudaGetErrorString(e));
+  }
+  if (st) {
+    free_batch_arrays(s);
+    delete s;
+    return st;
+  }
+  *out = s;
+  return AH_OK;
+}
+
+ah_status ah_batch_create(ah_ctx* ctx, uint32_t n_rec, const uint64_t* lens, const uint32_t* genome_ids, ah_batch** out) {
+  if (!ctx || !out || !lens || n_rec == 0) return fail(ctx, AH_EINVAL, "ah_batch_create: bad arguments");
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  ah_batch* b = new ah_batch();
+  ah_status st = layout_batch(ctx, n_rec, lens, genome_ids, b);
+  if (st) {
+    free_batch_arrays(b);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return AH_OK;
+}
+
+ah_status ah_batch_pack_range(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t count, const uint8_t* d_seq,
+                              const uint64_t* h_offsets) {
+  if (!ctx || !b || !d_seq || !h_offsets || b->view) return fail(ctx, AH_EINVAL, "ah_batch_pack_range: bad arguments");
+  if (!usable(ctx, b) || count == 0 || (uint64_t)first + count > b->n_records)
+    return fail(ctx, AH_EINVAL, "ah_batch_pack_range: bad record range");
+  cudaSetDevice(ctx->device);
+  std::vector<PackItem> items;
+  for (uint32_t i = 0; i < count; ++i) {
+    if (h_offsets[i + 1] < h_offsets[i] || h_offsets[i + 1] - h_offsets[i] != b->h_rec_len[first + i])
+      return fail(ctx, AH_EINVAL, "ah_batch_pack_range: record %u length differs from the layout", first + i);
+    add_items(items, b, first + i, 0, b->h_rec_len[first + i], h_offsets[i]);
+  }
+  return run_pack(ctx, d_seq, items, b);
+}
+
 ah_status ah_batch_view_get(const ah_batch* b, ah_batch_view* out) {
   if (!b || !out) return AH_EINVAL;
   out->n_records = b->n_records;
@@ -468,14 +546,15 @@ void ah_primers_free(ah_primers* p) {
 // ------------------------------------------------------------------------------------------
 ah_status ah_scan_primers(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out) {
   if (!ctx || !b || !p || !out) return fail(ctx, AH_EINVAL, "ah_scan_primers: NULL argument");
-  if (b->ctx != ctx || p->ctx != ctx) return fail(ctx, AH_EINVAL, "ah_scan_primers: object from another context");
+  if (!usable(ctx, b) || p->ctx != ctx) return fail(ctx, AH_EINVAL, "ah_scan_primers: object from another context");
   cudaSetDevice(ctx->device);
   return scan_primers(ctx, b, p, out);
 }
 
 ah_status ah_scan_primers_per_record(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, ah_hits** out) {
   if (!ctx || !b || !p || !out) return fail(ctx, AH_EINVAL, "ah_scan_primers_per_record: NULL argument");
-  if (b->ctx != ctx || p->ctx != ctx) return fail(ctx, AH_EINVAL, "ah_scan_primers_per_record: object from another context");
+  if (!usable(ctx, b) || p->ctx != ctx)
+    return fail(ctx, AH_EINVAL, "ah_scan_primers_per_record: object from another context");
   cudaSetDevice(ctx->device);
   return scan_primers_per_record(ctx, b, p, out);
 }

@@ -68,6 +68,8 @@ struct ah_ctx {
   uint64_t n_scan_launches = 0;
   uint64_t scan_bases = 0;
   double scan_ms = 0.0;
+  uint64_t jit_compiles = 0;
+  double jit_ms = 0.0;
   bool timing = false;
   cudaEvent_t ev[2] = {nullptr, nullptr};
 };
@@ -85,6 +87,7 @@ struct ah_batch {
   uint32_t* genome_id = nullptr;
   std::vector<uint64_t> h_rec_group;
   std::vector<uint32_t> h_rec_len;
+  bool view = false;          // a slice: planes, invalid, rec_len and genome_id belong to another batch
 };
 
 struct ah_primers {

@@ -17,6 +17,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstring>
 #include <map>
@@ -329,6 +330,7 @@ ah_status JitCache::get(ah_ctx* ctx, const std::vector<Pattern>& pats, const Sca
     *out = it->second.second;
     return AH_OK;
   }
+  const auto t0 = std::chrono::steady_clock::now();
   nvrtcProgram prog;
   if (nvrtcCreateProgram(&prog, src.c_str(), "ah_scan_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
     return fail(ctx, AH_EJIT, "nvrtcCreateProgram failed");
@@ -360,6 +362,8 @@ ah_status JitCache::get(ah_ctx* ctx, const std::vector<Pattern>& pats, const Sca
   if (ce != cudaSuccess) return fail(ctx, AH_EJIT, "cudaLibraryGetKernel failed: %s", cudaGetErrorString(ce));
   k.threads = cfg.threads;
   k.groups_per_thread = cfg.groups_per_thread;
+  ctx->jit_compiles++;
+  ctx->jit_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   cache_.emplace(src, std::make_pair(lib, k));
   *out = k;
   return AH_OK;

@@ -1,0 +1,263 @@
+// Serving loop over a device-resident genome database (continuous batching).
+//
+// The database is one packed batch kept in HBM.  A request brings a primer set, its parameters and
+// a genome subset (a contiguous range of database records).  The server runs `n_slots` workers,
+// each with its own context (CUDA stream) and host thread.  Requests wait in arrival order; the
+// first one is admitted as soon as a worker is free and its estimated device memory fits under the
+// budget next to the requests already running, so requests of different sizes that arrive while
+// others are on the GPU join as slots and memory free up, and their kernels overlap on the device.
+// Each admitted request runs the whole path on a slice of the database (no copy of the genomes)
+// and its results are copied to host memory owned by the request's result.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+
+#include "ah_internal.h"
+
+namespace {
+
+double now_s(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+struct Job {
+  uint64_t ticket = 0;
+  // owned copy of the request
+  std::vector<std::string> fwd, rev;
+  std::vector<uint8_t> k;
+  ah_request req{};
+  uint64_t est_bytes = 0;
+  ah_result* result = nullptr;
+  bool done = false;
+};
+
+}  // namespace
+
+struct ah_server {
+  const ah_batch* db = nullptr;
+  int device = 0;
+  uint64_t budget = 0, reserved = 0;
+  std::chrono::steady_clock::time_point t0;
+  std::vector<ah_ctx*> ctxs;
+  std::vector<std::thread> workers;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Job*> queue;
+  std::unordered_map<uint64_t, Job*> jobs;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  int running = 0;
+};
+
+namespace ah {
+namespace {
+
+// device bytes a request needs beyond the database: tile slot lists, per-(pair, tile) counts and
+// offsets for its slice, plus room for sites, amplicons and sequences
+uint64_t estimate_bytes(const ah_server* s, const ah_request& r, int slot_cap, uint64_t tile_groups) {
+  const ah_batch* db = s->db;
+  const uint64_t g0 = db->h_rec_group[r.first_record];
+  const uint64_t g1 = (uint64_t)r.first_record + r.n_records < db->n_records ? db->h_rec_group[r.first_record + r.n_records]
+                                                                             : db->n_groups;
+  const uint64_t tiles = (g1 - g0) / tile_groups + 1;
+  return tiles * ((uint64_t)slot_cap * 8 + 8 + 12ull * r.n_pairs) + (64ull << 20);
+}
+
+void fill_error(ah_result* res, ah_status st, const char* msg) {
+  res->status = st;
+  snprintf(res->error, sizeof res->error, "%s", msg ? msg : "");
+}
+
+void run_job(ah_server* s, ah_ctx* ctx, Job* j) {
+  ah_result* res = j->result;
+  const ah_request& r = j->req;
+  ah_batch* slice = nullptr;
+  ah_primers* pr = nullptr;
+  ah_hits* h = nullptr;
+  ah_amplicons* a = nullptr;
+  std::vector<const char*> f(r.n_pairs), rv(r.n_pairs);
+  for (uint32_t i = 0; i < r.n_pairs; ++i) f[i] = j->fwd[i].c_str(), rv[i] = j->rev[i].c_str();
+  ah_status st = ah_batch_slice(ctx, s->db, r.first_record, r.n_records, &slice);
+  if (!st) st = ah_primers_create(ctx, r.n_pairs, f.data(), rv.data(), j->k.data(), r.clamp, &pr);
+  if (!st) st = ah_scan_primers(ctx, slice, pr, &h);
+  if (!st) st = ah_pair_amplicons(ctx, slice, pr, h, r.min_len, r.max_len, r.orient_mask, &a);
+  if (!st) st = ah_tm_filter(ctx, slice, pr, h, a, &r.tm);
+  if (!st && r.extract) st = ah_extract_barcodes(ctx, slice, pr, h, a, r.trim, r.fb_len, r.rb_len);
+  if (!st) {
+    res->n_hits = h->n;
+    res->n_amps = a->n;
+    res->bases = slice->n_bases;
+    res->hits = (ah_hit*)malloc(std::max<uint64_t>(1, h->n) * sizeof(ah_hit));
+    res->amps = (ah_amplicon*)malloc(std::max<uint64_t>(1, a->n) * sizeof(ah_amplicon));
+    st = ah_hits_copy(h, res->hits, h->n);
+    if (!st) st = ah_amplicons_copy(a, res->amps, a->n);
+    if (!st && r.extract) {
+      res->arena_bytes = a->arena_bytes;
+      res->arena = (char*)malloc(std::max<uint64_t>(1, a->arena_bytes));
+      res->field_off = (uint64_t*)malloc((5 * a->n + 1) * sizeof(uint64_t));
+      st = ah_amplicons_seq_copy(a, res->arena, a->arena_bytes, res->field_off, 5 * a->n + 1);
+    }
+    // record indices relative to the database
+    for (uint64_t i = 0; i < res->n_hits && !st; ++i) res->hits[i].record += r.first_record;
+    for (uint64_t i = 0; i < res->n_amps && !st; ++i) res->amps[i].record += r.first_record;
+  }
+  if (st) fill_error(res, st, ah_last_error(ctx));
+  ah_amplicons_free(a);
+  ah_hits_free(h);
+  ah_primers_free(pr);
+  ah_batch_free(slice);
+  cudaStreamSynchronize(ctx->stream);
+}
+
+void worker(ah_server* s, int slot) {
+  ah_ctx* ctx = s->ctxs[slot];
+  cudaSetDevice(s->device);
+  for (;;) {
+    Job* j = nullptr;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      s->cv_work.wait(lock, [&] {
+        if (s->stop) return true;
+        if (s->queue.empty()) return false;
+        // admit the oldest request when its memory fits next to the running ones (always when the
+        // device is otherwise idle, so an oversized request still runs alone)
+        return s->reserved == 0 || s->reserved + s->queue.front()->est_bytes <= s->budget;
+      });
+      if (s->stop && s->queue.empty()) return;
+      if (s->queue.empty()) continue;
+      j = s->queue.front();
+      s->queue.pop_front();
+      s->reserved += j->est_bytes;
+      s->running++;
+      j->result->t_admit = now_s(s->t0);
+    }
+    s->cv_work.notify_all();
+    run_job(s, ctx, j);
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      j->result->t_done = now_s(s->t0);
+      s->reserved -= j->est_bytes;
+      s->running--;
+      j->done = true;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+  }
+}
+
+}  // namespace
+}  // namespace ah
+
+using namespace ah;
+
+extern "C" {
+
+ah_status ah_server_create(const ah_batch* db, int n_slots, uint64_t memory_budget, ah_server** out) {
+  if (!db || !out || n_slots < 1 || n_slots > 64) return AH_EINVAL;
+  *out = nullptr;
+  ah_server* s = new ah_server();
+  s->db = db;
+  s->device = db->ctx->device;
+  s->t0 = std::chrono::steady_clock::now();
+  cudaSetDevice(s->device);
+  if (!memory_budget) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    memory_budget = (uint64_t)(free_b * 0.6);
+  }
+  s->budget = memory_budget;
+  for (int i = 0; i < n_slots; ++i) {
+    ah_ctx* c = nullptr;
+    ah_status st = ah_ctx_create(&c, s->device, nullptr);
+    if (st) {
+      ah_server_destroy(s);
+      return st;
+    }
+    c->scan_cfg.slot_cap = 64;  // requests are sparse; dense tiles are re-run with room
+    s->ctxs.push_back(c);
+  }
+  for (int i = 0; i < n_slots; ++i) s->workers.emplace_back(worker, s, i);
+  *out = s;
+  return AH_OK;
+}
+
+ah_status ah_server_submit(ah_server* s, const ah_request* r, uint64_t* ticket) {
+  if (!s || !r || !ticket || r->n_pairs == 0 || !r->fwd || !r->rev || !r->k) return AH_EINVAL;
+  if (r->n_records == 0 || (uint64_t)r->first_record + r->n_records > s->db->n_records) return AH_EINVAL;
+  Job* j = new Job();
+  for (uint32_t i = 0; i < r->n_pairs; ++i) {
+    if (!r->fwd[i] || !r->rev[i]) {
+      delete j;
+      return AH_EINVAL;
+    }
+    j->fwd.emplace_back(r->fwd[i]);
+    j->rev.emplace_back(r->rev[i]);
+    j->k.push_back(r->k[i]);
+  }
+  j->req = *r;
+  j->req.fwd = j->req.rev = nullptr;
+  j->req.k = nullptr;
+  j->result = (ah_result*)calloc(1, sizeof(ah_result));
+  j->est_bytes = estimate_bytes(s, *r, 64, (uint64_t)s->ctxs[0]->scan_cfg.threads * s->ctxs[0]->scan_cfg.groups_per_thread);
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    j->ticket = s->next_ticket++;
+    j->result->t_submit = now_s(s->t0);
+    s->jobs[j->ticket] = j;
+    s->queue.push_back(j);
+    *ticket = j->ticket;
+  }
+  s->cv_work.notify_all();
+  return AH_OK;
+}
+
+ah_status ah_server_wait(ah_server* s, uint64_t ticket, ah_result** out) {
+  if (!s || !out) return AH_EINVAL;
+  *out = nullptr;
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto it = s->jobs.find(ticket);
+  if (it == s->jobs.end()) return AH_EINVAL;
+  Job* j = it->second;
+  s->cv_done.wait(lock, [&] { return j->done; });
+  s->jobs.erase(it);
+  *out = j->result;
+  delete j;
+  return (*out)->status;
+}
+
+ah_status ah_server_now(const ah_server* s, double* seconds) {
+  if (!s || !seconds) return AH_EINVAL;
+  *seconds = now_s(s->t0);
+  return AH_OK;
+}
+
+void ah_result_free(ah_result* r) {
+  if (!r) return;
+  free(r->hits);
+  free(r->amps);
+  free(r->arena);
+  free(r->field_off);
+  free(r);
+}
+
+void ah_server_destroy(ah_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->workers) t.join();
+  for (auto& kv : s->jobs) {
+    ah_result_free(kv.second->result);
+    delete kv.second;
+  }
+  for (ah_ctx* c : s->ctxs) ah_ctx_destroy(c);
+  delete s;
+}
+
+}  // extern "C"

@@ -67,6 +67,9 @@ def _get_lib():
             lib.synth_fill_bases.restype = None
             lib.synth_fill_nruns.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_uint32]
             lib.synth_fill_nruns.restype = ctypes.c_uint64
+            lib.synth_nrun_list.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_uint32, u8p,
+                                            u8p, ctypes.c_uint64]
+            lib.synth_nrun_list.restype = ctypes.c_uint64
             lib.synth_fill_tandem.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32]
             lib.synth_fill_tandem.restype = None
             lib.synth_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
@@ -289,6 +292,59 @@ def _plant(seq: np.ndarray, offsets: np.ndarray, g: int, st: Stream, n_sites: in
         planted.append(Planted(g, off, strand, pair, len(tmpl), sf, sr))
 
 
+T_INTERIOR = 9
+
+
+def c_bases(n: int, key: int, gc: float = 0.5) -> str:
+    """n iid bases drawn by the C filler (fast path for long template interiors)."""
+    buf = np.empty(n, dtype=np.uint8)
+    if n:
+        _get_lib().synth_fill_bases(buf.ctypes.data, n, key, gc, 0)
+    return buf.tobytes().decode("ascii")
+
+
+def batched_templates(seed: int, lengths: Sequence[int], fwd: List[str], rev: List[str], subs_max: int = 3):
+    """Planted templates of the batched workload: per genome 0-3 templates of one random pair,
+    interiors of 200-1500 bases.  Returns (list of (genome, offset, bytes), planted records)."""
+    out, planted = [], []
+    n_pairs = len(fwd)
+    for g, glen in enumerate(lengths):
+        st = Stream(make_key(seed + 2, T_PLANT, g))
+        n_sites = st.randint(0, 3)
+        p = st.randint(0, n_pairs - 1)
+        if n_sites == 0:
+            continue
+        seg = glen // n_sites
+        for s in range(n_sites):
+            fv = substitute(st, concrete_variant(st, fwd[p]), sf := st.randint(0, subs_max))
+            rv = substitute(st, concrete_variant(st, rev[p]), sr := st.randint(0, subs_max))
+            mid = c_bases(st.randint(200, 1500), make_key(seed + 2, T_INTERIOR, g * 8 + s))
+            tmpl = fv + mid + _revcomp_plain(rv)
+            strand = st.randint(0, 1)
+            if strand:
+                tmpl = _revcomp_plain(tmpl)
+            if len(tmpl) + 2 > seg:
+                continue
+            off = s * seg + st.randint(0, seg - len(tmpl) - 1)
+            out.append((g, off, tmpl.encode("ascii")))
+            planted.append(Planted(g, off, strand, p, len(tmpl), sf, sr))
+    return out, planted
+
+
+def batched_lengths_and_primers(seed: int, n_genomes: int, len_lo: float, len_hi: float, n_pairs: int):
+    st_len = Stream(make_key(seed + 2, T_LEN, 0))
+    la, lb = math.log(len_lo), math.log(len_hi)
+    lengths = [int(math.exp(la + (lb - la) * st_len.unit())) for _ in range(n_genomes)]
+    st_gc = Stream(make_key(seed + 2, T_GC, 0))
+    gcs = [0.30 + 0.40 * st_gc.unit() for _ in range(n_genomes)]
+    pst = Stream(make_key(seed + 2, T_PRIMER, 0))
+    fwd, rev = [], []
+    for _ in range(n_pairs):
+        fwd.append(random_primer(pst, pst.randint(17, 26), pst.randint(0, 6), 3))
+        rev.append(random_primer(pst, pst.randint(17, 26), pst.randint(0, 6), 3))
+    return lengths, gcs, fwd, rev
+
+
 def _alloc(lengths: Sequence[int], out: Optional[np.ndarray]):
     offsets = np.zeros(len(lengths) + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(np.asarray(lengths, dtype=np.int64))
@@ -347,24 +403,13 @@ def plain_scale(seed: int = SEED, n_genomes: int = 2000, median: float = 3.5e6, 
 def batched(seed: int = SEED, n_genomes: int = 50_000, len_lo: float = 1e4, len_hi: float = 1.2e7,
             n_pairs: int = 8, out: Optional[np.ndarray] = None) -> Workload:
     """Many log-uniform genomes, 8 pairs of 17-26 nt with 0-6 degenerate codes, k_i = i mod 4."""
-    st_len = Stream(make_key(seed + 2, T_LEN, 0))
-    la, lb = math.log(len_lo), math.log(len_hi)
-    lengths = [int(math.exp(la + (lb - la) * st_len.unit())) for _ in range(n_genomes)]
-    st_gc = Stream(make_key(seed + 2, T_GC, 0))
-    gcs = [0.30 + 0.40 * st_gc.unit() for _ in range(n_genomes)]
+    lengths, gcs, fwd, rev = batched_lengths_and_primers(seed, n_genomes, len_lo, len_hi, n_pairs)
     seq, offsets = _alloc(lengths, out)
     _fill_genomes(seq, offsets, seed + 2, gcs, 0.005, 50)
-    pst = Stream(make_key(seed + 2, T_PRIMER, 0))
-    fwd, rev = [], []
-    for _ in range(n_pairs):
-        fwd.append(random_primer(pst, pst.randint(17, 26), pst.randint(0, 6), 3))
-        rev.append(random_primer(pst, pst.randint(17, 26), pst.randint(0, 6), 3))
-    planted: List[Planted] = []
-    for g in range(n_genomes):
-        st = Stream(make_key(seed + 2, T_PLANT, g))
-        n_sites = st.randint(0, 3)
-        p = st.randint(0, n_pairs - 1)
-        _plant(seq, offsets, g, st, n_sites, fwd[p], rev[p], p, lambda s: s.randint(200, 1500), 3, planted)
+    tmpls, planted = batched_templates(seed, lengths, fwd, rev)
+    for g, off, t in tmpls:
+        a = int(offsets[g]) + off
+        seq[a:a + len(t)] = np.frombuffer(t, dtype=np.uint8)
     return Workload("batched", seq, offsets, np.arange(n_genomes, dtype=np.uint32), fwd, rev,
                     [i % 4 for i in range(n_pairs)], 3, 50, 2000, 0b1111, TmParams(min_tm=None), False, 0, 0,
                     planted, seed)
@@ -429,3 +474,23 @@ def random_small(seed: int, n_records: int, len_lo: int, len_hi: int, n_pairs: i
 
 
 WORKLOADS = {"plain_small": plain_small, "plain_scale": plain_scale, "batched": batched, "dense": dense}
+
+
+def serving_trace(seed: int, n_requests: int, rate_per_s: float, n_db_records: int, pairs_max: int = 32):
+    """A Poisson request stream for the serving database: each request has 1-pairs_max degenerate
+    pairs of 17-26 nt (0-6 codes), k of 0-3 per pair, and a genome subset that is a contiguous
+    record range covering a log-uniform 1 %-100 % of the database."""
+    st = Stream(make_key(seed + 5, T_SUBSET, 0))
+    t, out = 0.0, []
+    for _ in range(n_requests):
+        t += -math.log(1.0 - st.unit()) / rate_per_s
+        pairs = st.randint(1, pairs_max)
+        fwd = [random_primer(st, st.randint(17, 26), st.randint(0, 6), 3) for _ in range(pairs)]
+        rev = [random_primer(st, st.randint(17, 26), st.randint(0, 6), 3) for _ in range(pairs)]
+        k = [st.randint(0, 3) for _ in range(pairs)]
+        frac = math.exp(math.log(0.01) + (math.log(1.0) - math.log(0.01)) * st.unit())
+        count = max(1, int(round(frac * n_db_records)))
+        first = st.randint(0, n_db_records - count)
+        out.append(dict(arrival=t, fwd=fwd, rev=rev, k=k, clamp=3, first_record=first, n_records=count, min_len=50,
+                        max_len=2000, orient_mask=15))
+    return out

@@ -12,6 +12,7 @@
 #include <stdint.h>
 #include <string.h>
 #include <math.h>
+#include <stdlib.h>
 
 #define GOLDEN 0x9E3779B97F4A7C15ULL
 
@@ -43,21 +44,44 @@ void synth_fill_bases(uint8_t* out, uint64_t n, uint64_t key, double gc, uint64_
 
 /*
  * Runs of 'N': gaps between runs are exponential with mean chosen so that the expected fraction
- * of N positions is `frac`; run lengths are uniform on {1..run_max}.  Sequential in the record,
- * returns the number of N positions written.
+ * of N positions is `frac`; run lengths are uniform on {1..run_max}.  Sequential in the record.
+ * synth_nrun_list writes up to `cap` runs (start, length) and returns how many there are;
+ * synth_fill_nruns writes them into a record and returns the number of N positions.
  */
-uint64_t synth_fill_nruns(uint8_t* out, uint64_t n, uint64_t key, double frac, uint32_t run_max) {
+uint64_t synth_nrun_list(uint64_t n, uint64_t key, double frac, uint32_t run_max, uint64_t* starts, uint32_t* lens,
+                         uint64_t cap) {
   if (frac <= 0.0 || run_max == 0 || n == 0) return 0;
   double mean_run = 0.5 * (1.0 + (double)run_max);
   double mean_gap = mean_run * (1.0 - frac) / frac;
-  uint64_t c = 0, pos = 0, total = 0;
+  uint64_t c = 0, pos = 0, runs = 0;
   pos = (uint64_t)floor(-log(1.0 - unit(draw(key, c++))) * mean_gap);
   while (pos < n) {
     uint64_t len = 1 + draw(key, c++) % run_max;
-    for (uint64_t j = 0; j < len && pos + j < n; ++j) { out[pos + j] = 'N'; ++total; }
+    if (pos + len > n) len = n - pos;
+    if (runs < cap) {
+      starts[runs] = pos;
+      lens[runs] = (uint32_t)len;
+    }
+    ++runs;
     pos += len;
     pos += 1 + (uint64_t)floor(-log(1.0 - unit(draw(key, c++))) * mean_gap);
   }
+  return runs;
+}
+
+uint64_t synth_fill_nruns(uint8_t* out, uint64_t n, uint64_t key, double frac, uint32_t run_max) {
+  if (frac <= 0.0 || run_max == 0 || n == 0) return 0;
+  uint64_t cnt = synth_nrun_list(n, key, frac, run_max, NULL, NULL, 0);
+  uint64_t* st = (uint64_t*)malloc((cnt ? cnt : 1) * sizeof(uint64_t));
+  uint32_t* ln = (uint32_t*)malloc((cnt ? cnt : 1) * sizeof(uint32_t));
+  synth_nrun_list(n, key, frac, run_max, st, ln, cnt);
+  uint64_t total = 0;
+  for (uint64_t r = 0; r < cnt; ++r) {
+    memset(out + st[r], 'N', ln[r]);
+    total += ln[r];
+  }
+  free(st);
+  free(ln);
   return total;
 }
 
