@@ -77,6 +77,8 @@ typedef struct {
   uint64_t scan_bases;      /* bases covered by those launches */
   uint64_t jit_compiles;    /* scan kernels compiled at run time (NVRTC) */
   double jit_ms;            /* host time spent compiling them */
+  int32_t scan_ops_per_group; /* ALU instructions (LOP3 and funnel shifts) of the last one-launch scan
+                                 kernel's generated circuit per 32 positions */
 } ah_ctx_stats;
 ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out);
 ah_status ah_ctx_stats_reset(ah_ctx* ctx);

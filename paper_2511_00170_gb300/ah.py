@@ -74,7 +74,8 @@ class ah_result(ctypes.Structure):
 
 class ah_ctx_stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("scan_launches", ctypes.c_uint64), ("scan_ms", ctypes.c_double),
-                ("scan_bases", ctypes.c_uint64), ("jit_compiles", ctypes.c_uint64), ("jit_ms", ctypes.c_double)]
+                ("scan_bases", ctypes.c_uint64), ("jit_compiles", ctypes.c_uint64), ("jit_ms", ctypes.c_double),
+                ("scan_ops_per_group", ctypes.c_int32)]
 
 
 class ah_batch_view(ctypes.Structure):

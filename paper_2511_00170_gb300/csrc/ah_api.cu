@@ -249,6 +249,7 @@ ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out) {
   out->scan_bases = ctx->scan_bases;
   out->jit_compiles = ctx->jit_compiles;
   out->jit_ms = ctx->jit_ms;
+  out->scan_ops_per_group = ctx->scan_ops_per_group;
   return AH_OK;
 }
 

@@ -70,6 +70,7 @@ struct ah_ctx {
   double scan_ms = 0.0;
   uint64_t jit_compiles = 0;
   double jit_ms = 0.0;
+  int scan_ops_per_group = 0;  // of the last scan kernel launched
   bool timing = false;
   cudaEvent_t ev[2] = {nullptr, nullptr};
 };
@@ -203,8 +204,9 @@ void launch_extract(cudaStream_t s, bool write, const ah_amplicon* amps, uint64_
 struct ScanKernel {
   cudaKernel_t fn = nullptr;
   int threads = 0, groups_per_thread = 0;
+  int alu_ops_per_group = 0;  // LOP3 + funnel-shift instructions of the generated circuit per 32 positions
 };
-std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg);
+std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg, int* alu_ops_per_group = nullptr);
 class JitCache {
  public:
   ah_status get(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out);

@@ -68,27 +68,67 @@ bool set_plane(uint8_t set, int* kind, bool* inverted) {
   }
 }
 
+// A 32-bit value of the generated code, possibly complemented: the value is ~name when inv.
+struct Val {
+  std::string name;
+  bool inv = false;
+  bool is_const = false;  // all ones (inv=false) or all zeros (inv=true)
+};
+
+Val ones() { return Val{"", false, true}; }
+
 struct Emitter {
   std::ostringstream os;
   int tmp = 0;
-  std::string def(const std::string& expr) {
-    std::string n = "t" + std::to_string(tmp++);
-    os << "      const u32 " << n << " = " << expr << ";\n";
-    return n;
+  int ops = 0;  // LOP3 instructions emitted
+  // one LOP3 computing f(a, b, c) on the actual (complement-resolved) values; f works bitwise on
+  // the 8-bit patterns a = 0xF0, b = 0xCC, c = 0xAA, the PTX truth-table convention
+  template <class F>
+  Val lop3(const Val& a, const Val& b, const Val& c, F f) {
+    auto pat = [](const Val& v, unsigned base) -> unsigned {
+      if (v.is_const) return v.inv ? 0x00u : 0xFFu;
+      return v.inv ? (~base & 0xFFu) : base;
+    };
+    const unsigned lut = f(pat(a, 0xF0u), pat(b, 0xCCu), pat(c, 0xAAu)) & 0xFFu;
+    auto reg = [&](const Val& v) { return v.is_const ? std::string("0u") : v.name; };
+    Val out{"t" + std::to_string(tmp++), false, false};
+    char buf[32];
+    snprintf(buf, sizeof buf, "0x%02x", lut);
+    os << "      u32 " << out.name << "; asm(\"lop3.b32 %0, %1, %2, %3, " << buf << ";\" : \"=r\"(" << out.name
+       << ") : \"r\"(" << reg(a) << "), \"r\"(" << reg(b) << "), \"r\"(" << reg(c) << "));\n";
+    ++ops;
+    return out;
+  }
+  Val xor3(const Val& a, const Val& b, const Val& c) {
+    return lop3(a, b, c, [](unsigned x, unsigned y, unsigned z) { return x ^ y ^ z; });
+  }
+  Val maj(const Val& a, const Val& b, const Val& c) {
+    return lop3(a, b, c, [](unsigned x, unsigned y, unsigned z) { return (x & y) | (z & (x | y)); });
+  }
+  Val xor2(const Val& a, const Val& b) { return lop3(a, b, a, [](unsigned x, unsigned y, unsigned) { return x ^ y; }); }
+  Val and2(const Val& a, const Val& b) { return lop3(a, b, a, [](unsigned x, unsigned y, unsigned) { return x & y; }); }
+  Val or2(const Val& a, const Val& b) { return lop3(a, b, a, [](unsigned x, unsigned y, unsigned) { return x | y; }); }
+  Val or3(const Val& a, const Val& b, const Val& c) {
+    return lop3(a, b, c, [](unsigned x, unsigned y, unsigned z) { return x | y | z; });
   }
 };
 
 std::string plane_name(int kind, int j) { return "p" + std::string(kKindName[kind]) + "_" + std::to_string(j); }
 
+std::string expr_of(const Val& v) {
+  if (v.is_const) return v.inv ? "0u" : "0xffffffffu";
+  return v.inv ? "(~" + v.name + ")" : v.name;
+}
+
 // OR-reduce with three-input ORs
-std::string or_reduce(Emitter& E, std::vector<std::string> v) {
-  if (v.empty()) return "0u";
+Val or_reduce(Emitter& E, std::vector<Val> v) {
+  if (v.empty()) return Val{"", true, true};  // all zeros
   while (v.size() > 1) {
-    std::vector<std::string> nv;
+    std::vector<Val> nv;
     size_t i = 0;
-    for (; i + 2 < v.size(); i += 3) nv.push_back(E.def("(" + v[i] + " | " + v[i + 1] + " | " + v[i + 2] + ")"));
+    for (; i + 2 < v.size(); i += 3) nv.push_back(E.or3(v[i], v[i + 1], v[i + 2]));
     if (i + 1 < v.size()) {
-      nv.push_back(E.def("(" + v[i] + " | " + v[i + 1] + ")"));
+      nv.push_back(E.or2(v[i], v[i + 1]));
       i += 2;
     }
     for (; i < v.size(); ++i) nv.push_back(v[i]);
@@ -98,15 +138,15 @@ std::string or_reduce(Emitter& E, std::vector<std::string> v) {
 }
 
 // failure word of one pattern: bit set iff clamp mismatch or (#non-clamp mismatches >= k+1)
-std::string gen_pattern(Emitter& E, const Pattern& P, std::map<std::pair<int, int>, bool>& used) {
-  std::vector<std::string> fail_terms, x1;
+Val gen_pattern(Emitter& E, const Pattern& P, std::map<std::pair<int, int>, bool>& used) {
+  std::vector<Val> fail_terms, x1;
   for (int j = 0; j < P.len; ++j) {
     int kind;
     bool inv;
     if (!set_plane(P.set[j], &kind, &inv)) continue;  // N never mismatches
     used[{kind, j}] = true;
-    std::string pl = plane_name(kind, j);
-    std::string x = inv ? pl : "(~" + pl + ")";     // mismatch bit
+    // mismatch bit: the complement of the match plane
+    const Val x{plane_name(kind, j), !inv, false};
     if (j >= P.clamp_lo && j < P.clamp_hi)
       fail_terms.push_back(x);
     else
@@ -119,44 +159,48 @@ std::string gen_pattern(Emitter& E, const Pattern& P, std::map<std::pair<int, in
     if (wsat == 1) {
       for (auto& x : x1) fail_terms.push_back(x);
     } else {
-      std::map<int, std::vector<std::string>> bits;
+      std::map<int, std::vector<Val>> bits;
       bits[1] = x1;
-      auto carry = [&](int w, const std::string& c) {
+      auto carry = [&](int w, const Val& c) {
         if (w >= wsat)
           fail_terms.push_back(c);
         else
           bits[w].push_back(c);
       };
       for (int w = 1; w < wsat; w *= 2) {
-        std::vector<std::string> list = bits[w];
+        std::vector<Val> list = bits[w];
         while (list.size() >= 3) {
-          std::vector<std::string> nl;
+          std::vector<Val> nl;
           size_t i = 0;
           for (; i + 2 < list.size(); i += 3) {
-            const std::string &a = list[i], &b = list[i + 1], &c = list[i + 2];
-            nl.push_back(E.def("(" + a + " ^ " + b + " ^ " + c + ")"));
-            carry(2 * w, E.def("((" + a + " & " + b + ") | (" + c + " & (" + a + " | " + b + ")))"));
+            nl.push_back(E.xor3(list[i], list[i + 1], list[i + 2]));
+            carry(2 * w, E.maj(list[i], list[i + 1], list[i + 2]));
           }
           for (; i < list.size(); ++i) nl.push_back(list[i]);
           list.swap(nl);
         }
         if (list.size() == 2) {
-          const std::string a = list[0], b = list[1];
-          list = {E.def("(" + a + " ^ " + b + ")")};
-          carry(2 * w, E.def("(" + a + " & " + b + ")"));
+          const Val a = list[0], b = list[1];
+          list = {E.xor2(a, b)};
+          carry(2 * w, E.and2(a, b));
         }
         bits[w] = list;
       }
       if (T != wsat) {
-        // x >= T over the reduced low bits (weights 1 .. wsat/2), most significant first
-        std::vector<std::string> b;
-        for (int w = 1; w < wsat; w *= 2) b.push_back(bits[w].empty() ? "0u" : bits[w][0]);
-        std::string ge = "0xffffffffu";
-        for (size_t i = 0; i < b.size(); ++i) {
-          bool tbit = (T >> i) & 1;
-          ge = tbit ? "(" + b[i] + " & " + ge + ")" : "(" + b[i] + " | " + ge + ")";
+        // count >= T over the reduced low bits (weights 1 .. wsat/2), least significant first
+        Val ge = ones();
+        for (int w = 1, i = 0; w < wsat; w *= 2, ++i) {
+          const Val b = bits[w].empty() ? Val{"", true, true} : bits[w][0];
+          const bool tbit = (T >> i) & 1;
+          if (ge.is_const && !ge.inv) {
+            ge = tbit ? b : ones();  // b & 1 = b ; b | 1 = 1
+          } else if (b.is_const) {
+            ge = tbit ? Val{"", true, true} : ge;  // 0 & ge = 0 ; 0 | ge = ge
+          } else {
+            ge = tbit ? E.and2(b, ge) : E.or2(b, ge);
+          }
         }
-        fail_terms.push_back(E.def(ge));
+        if (!(ge.is_const && ge.inv)) fail_terms.push_back(ge);
       }
     }
   }
@@ -224,7 +268,7 @@ static __device__ __noinline__ void emit(u32 h, int q, u64 g, uint2 a, uint2 b, 
 
 }  // namespace
 
-std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg) {
+std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg, int* alu_ops_per_group) {
   const int Q = (int)pats.size();
   std::ostringstream os;
   os << "// generated scan kernel: " << Q << " patterns\n";
@@ -254,9 +298,18 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg)
   Emitter E;
   std::map<std::pair<int, int>, bool> used;
   std::vector<std::string> fails(Q);
-  for (int q = 0; q < Q; ++q) fails[q] = gen_pattern(E, pats[q], used);
+  for (int q = 0; q < Q; ++q) fails[q] = expr_of(gen_pattern(E, pats[q], used));
   bool kind_used[K_COUNT] = {};
   for (auto& u : used) kind_used[u.first.first] = true;
+  if (alu_ops_per_group) {
+    // the circuit's ALU instructions per group of 32 positions: LOP3 of the trees, one funnel
+    // shift per (plane, offset) used, plane derivations (one per derived kind and word), and the
+    // AND-reduction of failure words per block of four patterns
+    int shifts = 0, derived = 0;
+    for (auto& u : used) shifts += u.first.second > 0;
+    for (int k = 0; k < K_COUNT; ++k) derived += kind_used[k] && k != K_LO && k != K_HI ? 2 : 0;
+    *alu_ops_per_group = E.ops + shifts + derived + 2 * ((Q + 3) / 4);
+  }
 
   // one block of the launch: NT threads x GPT groups of 32 positions, from group_begin
   os << "static __device__ __forceinline__ void scan_block(const ScanParams& P, const u64 blk) {\n";
@@ -323,7 +376,8 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg)
 }
 
 ah_status JitCache::get(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out) {
-  std::string src = scan_source(pats, cfg);
+  int ops = 0;
+  std::string src = scan_source(pats, cfg, &ops);
   std::lock_guard<std::mutex> lock(mu_);
   auto it = cache_.find(src);
   if (it != cache_.end()) {
@@ -362,6 +416,7 @@ ah_status JitCache::get(ah_ctx* ctx, const std::vector<Pattern>& pats, const Sca
   if (ce != cudaSuccess) return fail(ctx, AH_EJIT, "cudaLibraryGetKernel failed: %s", cudaGetErrorString(ce));
   k.threads = cfg.threads;
   k.groups_per_thread = cfg.groups_per_thread;
+  k.alu_ops_per_group = ops;
   ctx->jit_compiles++;
   ctx->jit_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   cache_.emplace(src, std::make_pair(lib, k));

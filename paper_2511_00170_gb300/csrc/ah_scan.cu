@@ -223,6 +223,7 @@ ah_status launch_scan(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const
       if (le != cudaSuccess) return fail(ctx, AH_ECUDA, "scan kernel launch failed: %s", cudaGetErrorString(le));
       launched(ctx);
       ctx->n_scan_launches++;
+      ctx->scan_ops_per_group = kern.alu_ops_per_group;
       if (cfg.persistent && t0 + nt < n_tiles) AH_CUDA(ctx, cudaMemsetAsync(work, 0, sizeof *work, ctx->stream));
     }
     if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));

@@ -1,0 +1,40 @@
+// Test helper: print the scan kernel source the engine generates for a primer set.
+// usage: jit_dump k clamp primer [primer ...]   (each primer gives its + and - strand patterns)
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../paper_2511_00170_gb300/csrc/ah_internal.h"
+
+static uint8_t set_of(char c) {
+  switch (c) {
+    case 'A': return 1; case 'C': return 2; case 'T': return 4; case 'G': return 8;
+    case 'R': return 9; case 'Y': return 6; case 'S': return 10; case 'W': return 5; case 'K': return 12;
+    case 'M': return 3; case 'B': return 14; case 'D': return 13; case 'H': return 7; case 'V': return 11;
+    default: return 15;
+  }
+}
+static uint8_t comp(uint8_t s) { return (uint8_t)(((s & 1) << 2) | ((s & 4) >> 2) | ((s & 2) << 2) | ((s & 8) >> 2)); }
+
+int main(int argc, char** argv) {
+  const int k = atoi(argv[1]), clamp = atoi(argv[2]);
+  std::vector<ah::Pattern> pats;
+  for (int a = 3; a < argc; ++a)
+    for (int strand = 0; strand < 2; ++strand) {
+      ah::Pattern P;
+      memset(&P, 0, sizeof P);
+      const char* pr = argv[a];
+      const int L = (int)strlen(pr);
+      P.len = (uint8_t)L;
+      P.k = (uint8_t)k;
+      P.id = (uint16_t)pats.size();
+      for (int j = 0; j < L; ++j) P.set[j] = strand == 0 ? set_of(pr[j]) : comp(set_of(pr[L - 1 - j]));
+      P.clamp_lo = (uint8_t)(strand == 0 ? L - clamp : 0);
+      P.clamp_hi = (uint8_t)(strand == 0 ? L : clamp);
+      pats.push_back(P);
+    }
+  ah::ScanConfig cfg;
+  puts(ah::scan_source(pats, cfg).c_str());
+  return 0;
+}

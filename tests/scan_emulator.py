@@ -1,0 +1,86 @@
+"""CPU execution of the straight-line logic of a generated scan kernel.
+
+The generated kernel computes, for 32 positions at once, a failure word per pattern from the two
+code-bit planes of two consecutive groups.  This module runs exactly those statements with numpy:
+plane definitions, funnel shifts and LOP3 instructions (evaluated from their truth tables), and
+compares each failure word with an exact per-position mismatch count and clamp check.
+"""
+import re
+
+import numpy as np
+
+M = np.uint32(0xFFFFFFFF)
+SETS = {"A": "A", "C": "C", "G": "G", "T": "T", "R": "AG", "Y": "CT", "S": "CG", "W": "AT", "K": "GT", "M": "AC",
+        "B": "CGT", "D": "AGT", "H": "ACT", "V": "ACG", "N": "ACGT"}
+CODE = {"A": 0, "C": 1, "T": 2, "G": 3}
+COMP = {"A": "T", "C": "G", "G": "C", "T": "A", "R": "Y", "Y": "R", "S": "S", "W": "W", "K": "M", "M": "K", "B": "V",
+        "V": "B", "D": "H", "H": "D", "N": "N"}
+
+
+def fshr(a, b, s):
+    s = int(s)
+    return a if s == 0 else ((a >> np.uint32(s)) | (b << np.uint32(32 - s))) & M
+
+
+def _expr(e, env):
+    e = e.replace("0xffffffffu", "M")
+    e = re.sub(r"\b(\d+)u\b", r"\1", e)
+    e = re.sub(r"~(\w+)", r"(M ^ \1)", e).replace("~(", "M ^ (")
+    return np.asarray(eval(e, {"np": np, "M": M, "fshr": fshr}, env), dtype=np.uint32)
+
+
+def failure_words(src, lo0, hi0, lo1, hi1):
+    """Run the generated body; returns the failure word of every pattern."""
+    body = src[src.index("const u32 lo0 = a.x"):src.index("if (__builtin_expect")]
+    env = {"lo0": lo0, "hi0": hi0, "lo1": lo1, "hi1": hi1}
+    zero = np.zeros_like(lo0)
+    for line in body.split("\n"):
+        m = re.match(r"\s*const u32 (\w+) = (.*?);$", line)
+        if m:
+            if m.group(1) not in env:
+                env[m.group(1)] = _expr(m.group(2), env)
+            continue
+        m = re.match(r'\s*u32 (\w+); asm\("lop3.b32 %0, %1, %2, %3, (0x[0-9a-f]+);" : "=r"\(\w+\) : '
+                     r'"r"\((\w+)\), "r"\((\w+)\), "r"\((\w+)\)\);', line)
+        if m:
+            lut = int(m.group(2), 16)
+            a, b, c = (zero if x == "0u" else env[x] for x in m.group(3, 4, 5))
+            r = np.zeros_like(a)
+            for idx in range(8):
+                if (lut >> idx) & 1:
+                    r |= (a if idx & 4 else M ^ a) & (b if idx & 2 else M ^ b) & (c if idx & 1 else M ^ c)
+            env[m.group(1)] = r
+    out = []
+    for f in re.findall(r"if \(~(\(~\w+\)|\w+)\) emit", src):
+        if f.startswith("(~"):
+            out.append(M ^ env[f[2:-1]])
+        elif f == "0u":
+            out.append(zero)
+        else:
+            out.append(env[f])
+    return out
+
+
+def exact_failure_words(primers, k, clamp, lo0, hi0, lo1, hi1):
+    lo64 = lo0.astype(np.uint64) | (lo1.astype(np.uint64) << np.uint64(32))
+    hi64 = hi0.astype(np.uint64) | (hi1.astype(np.uint64) << np.uint64(32))
+    out = []
+    for p in primers:
+        rc = "".join(COMP[c] for c in reversed(p))
+        for pat, cl in ((p, range(len(p) - clamp, len(p))), (rc, range(0, clamp))):
+            word = np.zeros(len(lo0), dtype=np.uint32)
+            for i in range(32):
+                mism = np.zeros(len(lo0), dtype=np.int64)
+                bad = np.zeros(len(lo0), dtype=bool)
+                for j, ch in enumerate(pat):
+                    code = ((lo64 >> np.uint64(i + j)) & np.uint64(1)) | \
+                           (((hi64 >> np.uint64(i + j)) & np.uint64(1)) << np.uint64(1))
+                    ok = np.zeros(len(lo0), dtype=bool)
+                    for base in SETS[ch]:
+                        ok |= code == CODE[base]
+                    mism += ~ok
+                    if j in cl:
+                        bad |= ~ok
+                word |= ((bad | (mism > k)).astype(np.uint32) << np.uint32(i))
+            out.append(word)
+    return out
