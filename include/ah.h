@@ -269,6 +269,14 @@ ah_status ah_tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, cons
 ah_status ah_tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const char* const* cseqs,
                          const ah_tm_params* params, double* tm_out);
 
+/* Tm of n (possibly degenerate) primers at given sites: primers[i] in IUPAC codes (5'->3'), sites[i]
+ * the genome bases under it in the primer's orientation (A, C, G, T; same length 2..32).  The
+ * maximum over the primer's concrete variants, as ah_tm_filter computes per site: enumerated for at
+ * most 64 variants (or salt method 6), otherwise exact by Dinkelbach iterations over a chain
+ * Viterbi.  tm_out[i] is NaN when no variant has a defined Tm.  Synchronises. */
+ah_status ah_tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const char* const* sites,
+                      const ah_tm_params* params, double* tm_out);
+
 /* ------------------------------------------------------------------------------------------ */
 /* 5. sequences and barcodes                                                                    */
 

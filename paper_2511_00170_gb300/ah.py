@@ -117,6 +117,7 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_uint64)]),
     "ah_tm_filter": (_I32, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ah_tm_params)]),
     "ah_tm_duplexes": (_I32, [_VP, _U32, _VP, _VP, ctypes.POINTER(ah_tm_params), _VP]),
+    "ah_tm_sites": (_I32, [_VP, _U32, _VP, _VP, ctypes.POINTER(ah_tm_params), _VP]),
     "ah_extract_barcodes": (_I32, [_VP, _VP, _VP, _VP, _VP, _I32, _U32, _U32]),
     "ah_amplicons_count": (_I32, [_VP, ctypes.POINTER(ctypes.c_uint64)]),
     "ah_amplicons_copy": (_I32, [_VP, _VP, _U64]),
@@ -352,6 +353,16 @@ def ah_tm_duplexes(ctx, seqs: Sequence[str], cseqs: Sequence[str], params: ah_tm
     out = np.empty(n, dtype=np.float64)
     _check(load().ah_tm_duplexes(ctx, n, ctypes.cast(sa, ctypes.c_void_p), ctypes.cast(ca, ctypes.c_void_p),
                                  ctypes.byref(params), out.ctypes.data), ctx)
+    return out
+
+
+def ah_tm_sites(ctx, primers: Sequence[str], sites: Sequence[str], params: ah_tm_params) -> np.ndarray:
+    n = len(primers)
+    pa = (ctypes.c_char_p * n)(*[s.encode("ascii") for s in primers])
+    sa = (ctypes.c_char_p * n)(*[s.encode("ascii") for s in sites])
+    out = np.empty(n, dtype=np.float64)
+    _check(load().ah_tm_sites(ctx, n, ctypes.cast(pa, ctypes.c_void_p), ctypes.cast(sa, ctypes.c_void_p),
+                              ctypes.byref(params), out.ctypes.data), ctx)
     return out
 
 

@@ -615,6 +615,15 @@ ah_status ah_tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const
   return tm_duplexes(ctx, n, seqs, cseqs, params, tm_out);
 }
 
+ah_status ah_tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const char* const* sites,
+                      const ah_tm_params* params, double* tm_out) {
+  if (!ctx || (n && (!primers || !sites || !tm_out)) || !params) return fail(ctx, AH_EINVAL, "ah_tm_sites: NULL argument");
+  if (params->saltcorr < 0 || params->saltcorr > 6)
+    return fail(ctx, AH_EINVAL, "ah_tm_sites: salt correction method %d is not supported (0-6)", params->saltcorr);
+  cudaSetDevice(ctx->device);
+  return tm_sites(ctx, n, primers, sites, params, tm_out);
+}
+
 ah_status ah_extract_barcodes(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a,
                               int trim, uint32_t fb_len, uint32_t rb_len) {
   if (!ctx || !b || !p || !h || !a) return fail(ctx, AH_EINVAL, "ah_extract_barcodes: NULL argument");

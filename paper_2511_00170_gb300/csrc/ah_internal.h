@@ -166,6 +166,8 @@ ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const a
                     const ah_tm_params* params);
 ah_status tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const char* const* cseqs,
                       const ah_tm_params* params, double* out);
+ah_status tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const char* const* sites,
+                   const ah_tm_params* params, double* out);
 // extraction (ah_extract.cu)
 ah_status extract(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a, int trim,
                   uint32_t fb, uint32_t rb);

@@ -89,7 +89,9 @@ struct NNTables {
   double step_h[256], step_s[256];  // NaN: no parameter
   double term_h[256], term_s[256];  // NaN: not a terminal-mismatch step
 };
-__constant__ NNTables c_nn;
+// global (not constant) memory: threads of a warp look up different steps, which the constant cache
+// would serialise
+__device__ NNTables c_nn;
 
 int code_of(char c) {  // A=0, C=1, T=2, G=3
   switch (c) {
@@ -100,6 +102,27 @@ int code_of(char c) {  // A=0, C=1, T=2, G=3
   }
 }
 int idx4(int a, int b, int x, int y) { return a * 64 + b * 16 + x * 4 + y; }
+
+uint8_t iupac_set(char ch) {
+  switch (toupper((unsigned char)ch)) {
+    case 'A': return SET_A;
+    case 'C': return SET_C;
+    case 'G': return SET_G;
+    case 'T': return SET_T;
+    case 'R': return SET_A | SET_G;
+    case 'Y': return SET_C | SET_T;
+    case 'S': return SET_C | SET_G;
+    case 'W': return SET_A | SET_T;
+    case 'K': return SET_G | SET_T;
+    case 'M': return SET_A | SET_C;
+    case 'B': return SET_C | SET_G | SET_T;
+    case 'D': return SET_A | SET_G | SET_T;
+    case 'H': return SET_A | SET_C | SET_T;
+    case 'V': return SET_A | SET_C | SET_G;
+    case 'N': return SET_A | SET_C | SET_G | SET_T;
+    default: return 0;
+  }
+}
 
 void build_tables(NNTables* t) {
   const double nan = std::nan("");
@@ -179,19 +202,19 @@ __device__ bool duplex_tm(const uint8_t* v, const uint8_t* c, int L, const TmRun
   {
     // left end read from the opposite strand: 5'-c1 c0-3' over 3'-v1 v0-5'
     const int k = c[1] * 64 + c[0] * 16 + v[1] * 4 + v[0];
-    const double th = c_nn.term_h[k];
+    const double th = __ldg(&c_nn.term_h[k]);
     if (!isnan(th)) {
       dh += th;
-      ds += c_nn.term_s[k];
+      ds += __ldg(&c_nn.term_s[k]);
       lo = 1;
     }
   }
   if (hi - lo >= 2) {
     const int k = v[L - 2] * 64 + v[L - 1] * 16 + c[L - 2] * 4 + c[L - 1];
-    const double th = c_nn.term_h[k];
+    const double th = __ldg(&c_nn.term_h[k]);
     if (!isnan(th)) {
       dh += th;
-      ds += c_nn.term_s[k];
+      ds += __ldg(&c_nn.term_s[k]);
       hi = L - 1;
     }
   }
@@ -219,10 +242,10 @@ __device__ bool duplex_tm(const uint8_t* v, const uint8_t* c, int L, const TmRun
   if (v[L - 1] & 1) { dh += kTermGCH; ds += kTermGCS; } else { dh += kTermATH; ds += kTermATS; }
   for (int i = lo; i + 1 < hi; ++i) {
     const int k = v[i] * 64 + v[i + 1] * 16 + c[i] * 4 + c[i + 1];
-    const double sh = c_nn.step_h[k];
+    const double sh = __ldg(&c_nn.step_h[k]);
     if (isnan(sh)) return false;
     dh += sh;
-    ds += c_nn.step_s[k];
+    ds += __ldg(&c_nn.step_s[k]);
   }
   double corr = 0.0;
   if (R.saltcorr == 5) {
@@ -240,8 +263,137 @@ __device__ bool duplex_tm(const uint8_t* v, const uint8_t* c, int L, const TmRun
   return true;
 }
 
+// nearest-neighbour sums of edge (i, i+1) of the variant chain for bases (a, b) at positions i, i+1
+// over the opposite-strand codes c: the terminal-mismatch entry replaces the stack at either end
+__device__ __forceinline__ bool edge_sums(int i, int L, uint8_t a, uint8_t b, const uint8_t* c, double* dh, double* ds) {
+  if (i == 0) {
+    const int k = c[1] * 64 + c[0] * 16 + b * 4 + a;  // left end read from the opposite strand
+    const double th = __ldg(&c_nn.term_h[k]);
+    if (!isnan(th)) {
+      *dh = th;
+      *ds = __ldg(&c_nn.term_s[k]);
+      return true;
+    }
+  }
+  if (i == L - 2) {
+    const int k = a * 64 + b * 16 + c[L - 2] * 4 + c[L - 1];
+    const double th = __ldg(&c_nn.term_h[k]);
+    if (!isnan(th)) {
+      *dh = th;
+      *ds = __ldg(&c_nn.term_s[k]);
+      return true;
+    }
+  }
+  const int k = a * 64 + b * 16 + c[i] * 4 + c[i + 1];
+  const double sh = __ldg(&c_nn.step_h[k]);
+  if (isnan(sh)) return false;
+  *dh = sh;
+  *ds = __ldg(&c_nn.step_s[k]);
+  return true;
+}
+
+// initiation terms that depend on the variant's end bases
+__device__ __forceinline__ void end_sums(int j, int L, uint8_t v, double* dh, double* ds) {
+  *dh = (v & 1) ? kTermGCH : kTermATH;
+  *ds = (v & 1) ? kTermGCS : kTermATS;
+  if (j == 0 && v == 2) *dh += k5TAH, *ds += k5TAS;       // 5' T
+  if (j == L - 1 && v == 0) *dh += k5TAH, *ds += k5TAS;   // 3' A
+}
+
+// Exact maximum of Tm over the variants of `sets` at site `s` for salt methods 0-5 and L >= 3.
+// Tm + 273.15 = N(v) / D(v) with N = 1000 dH and D = dS + S0 < 0, and every term of N and D depends on
+// at most two adjacent variant bases.  Dinkelbach's iteration for fractional programmes: for the
+// current ratio lam, a Viterbi pass over the chain (at most four states per position) finds the
+// variant maximising lam * D - N; its ratio becomes the next lam; at the optimum the maximum is 0.
+// Returns false when no variant is defined or D could reach 0.
+__device__ bool site_tm_chain(const uint8_t* sets, const uint8_t* s, int L, const TmRun& R, double* out) {
+  uint8_t c[32], ch[32][4], nch[32], back[32][4], v[32];
+  for (int j = 0; j < L; ++j) {
+    c[j] = s[j] ^ 2u;
+    nch[j] = 0;
+    for (int code = 0; code < 4; ++code)
+      if ((sets[j] >> code) & 1) ch[j][nch[j]++] = (uint8_t)code;
+  }
+  // constant part of D: salt (method 5) and R ln(C); methods 1-4 shift Tm by a constant
+  const double S0 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
+  const double H0 = kInitH + kOneGCH, Sc = kInitS + kOneGCS;  // all-A/T and one-G/C terms are equal here
+  // Viterbi: maximise sum of (lam * ds - 1000 * dh) (lam = 0 with sign -1 on dh .. see callers)
+  auto viterbi = [&](double wl, double wn, double* best_score) -> bool {
+    double cur[4], nxt[4];
+    for (int a = 0; a < nch[0]; ++a) {
+      double dh, ds;
+      end_sums(0, L, ch[0][a], &dh, &ds);
+      cur[a] = wl * ds - wn * 1000.0 * dh;
+    }
+    for (int i = 0; i + 1 < L; ++i) {
+      for (int b = 0; b < nch[i + 1]; ++b) {
+        double best = -INFINITY;
+        int arg = -1;
+        for (int a = 0; a < nch[i]; ++a) {
+          if (cur[a] == -INFINITY) continue;
+          double dh, ds;
+          if (!edge_sums(i, L, ch[i][a], ch[i + 1][b], c, &dh, &ds)) continue;
+          const double sc = cur[a] + (wl * ds - wn * 1000.0 * dh);
+          if (sc > best) best = sc, arg = a;
+        }
+        if (i + 1 == L - 1 && arg >= 0) {
+          double dh, ds;
+          end_sums(L - 1, L, ch[i + 1][b], &dh, &ds);
+          best += wl * ds - wn * 1000.0 * dh;
+        }
+        nxt[b] = best;
+        back[i + 1][b] = (uint8_t)(arg < 0 ? 0 : arg);
+      }
+      for (int b = 0; b < nch[i + 1]; ++b) cur[b] = nxt[b];
+    }
+    double best = -INFINITY;
+    int arg = -1;
+    for (int b = 0; b < nch[L - 1]; ++b)
+      if (cur[b] > best) best = cur[b], arg = b;
+    if (arg < 0) return false;
+    for (int j = L - 1; j >= 0; --j) {
+      v[j] = ch[j][arg];
+      if (j) arg = back[j][arg];
+    }
+    *best_score = best;
+    return true;
+  };
+  // D must stay negative for every variant: maximise dS (wl = 1, wn = 0)
+  double maxS;
+  if (!viterbi(1.0, 0.0, &maxS)) return false;
+  if (maxS + Sc + S0 >= 0.0) return false;
+  // start from the variant that maximises dS - dH / 300 (any defined variant works)
+  double sc;
+  if (!viterbi(300.0, 1.0, &sc)) return false;
+  double t;
+  if (!duplex_tm(v, c, L, R, &t)) return false;
+  double lam = t + 273.15 - (R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0);
+  double best_t = t;
+  for (int it = 0; it < 64; ++it) {
+    if (!viterbi(lam, 1.0, &sc)) break;
+    // score + lam * (Sc + S0) - 1000 * H0 = lam * D(v) - N(v) for the maximising variant
+    const double F = sc + lam * (Sc + S0) - 1000.0 * H0;
+    if (F <= 1e-7) break;
+    if (!duplex_tm(v, c, L, R, &t)) break;
+    const double nl = t + 273.15 - (R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0);
+    if (!(nl > lam)) break;
+    lam = nl;
+    best_t = t;
+  }
+  *out = best_t;
+  return true;
+}
+
 // maximum over the concrete variants of `sets` (IUPAC sets over codes) paired with site `s`
 __device__ double site_tm(const uint8_t* sets, const uint8_t* s, int L, const TmRun& R) {
+  {
+    uint64_t nv = 1;
+    for (int j = 0; j < L; ++j) nv *= (uint64_t)__popc(sets[j]);
+    if (nv > 64 && L >= 3 && R.saltcorr <= 5) {
+      double t;
+      return site_tm_chain(sets, s, L, R, &t) ? t : __longlong_as_double(0x7ff8000000000000ll);
+    }
+  }
   uint8_t v[32], c[32], choice[32][4], nch[32], idx[32];
   for (int j = 0; j < L; ++j) {
     c[j] = s[j] ^ 2u;  // complement code
@@ -335,7 +487,56 @@ __global__ void k_tm_duplexes(const uint8_t* __restrict__ v, const uint8_t* __re
                : __longlong_as_double(0x7ff8000000000000ll);
 }
 
+__global__ void k_tm_sites(const uint8_t* __restrict__ sets, const uint8_t* __restrict__ site,
+                           const uint32_t* __restrict__ len, uint32_t n, const TmRun R, double* __restrict__ out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = site_tm(sets + 32 * (uint64_t)i, site + 32 * (uint64_t)i, (int)len[i], R);
+}
+
 }  // namespace
+
+ah_status tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const char* const* sites,
+                   const ah_tm_params* params, double* out) {
+  ah_status st;
+  if ((st = load_tables(ctx))) return st;
+  TmRun R;
+  if ((st = make_run(ctx, params, &R))) return st;
+  if (n == 0) return AH_OK;
+  std::vector<uint8_t> sets(32 * (size_t)n, 0), sv(32 * (size_t)n, 0);
+  std::vector<uint32_t> len(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    const size_t L = strlen(primers[i]);
+    if (L < 2 || L > 32 || strlen(sites[i]) != L) return fail(ctx, AH_EINVAL, "site %u: lengths must match, 2..32", i);
+    for (size_t j = 0; j < L; ++j) {
+      const char x = (char)toupper((unsigned char)sites[i][j]);
+      const uint8_t set = iupac_set(primers[i][j]);
+      if (!set || !strchr("ACGT", x) || !x) return fail(ctx, AH_EINVAL, "site %u: bad primer code or site base", i);
+      sets[32 * (size_t)i + j] = set;
+      sv[32 * (size_t)i + j] = (uint8_t)code_of(x);
+    }
+    len[i] = (uint32_t)L;
+  }
+  uint8_t *ds, *dv;
+  uint32_t* dl;
+  double* dout;
+  if ((st = dalloc(ctx, &ds, sets.size())) || (st = dalloc(ctx, &dv, sv.size())) || (st = dalloc(ctx, &dl, n)) ||
+      (st = dalloc(ctx, &dout, n)))
+    return st;
+  AH_CUDA(ctx, cudaMemcpyAsync(ds, sets.data(), sets.size(), cudaMemcpyHostToDevice, ctx->stream));
+  AH_CUDA(ctx, cudaMemcpyAsync(dv, sv.data(), sv.size(), cudaMemcpyHostToDevice, ctx->stream));
+  AH_CUDA(ctx, cudaMemcpyAsync(dl, len.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+  k_tm_sites<<<(n + 63) / 64, 64, 0, ctx->stream>>>(ds, dv, dl, n, R, dout);
+  launched(ctx);
+  AH_CUDA(ctx, cudaGetLastError());
+  AH_CUDA(ctx, cudaMemcpyAsync(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  dfree(ctx, ds);
+  dfree(ctx, dv);
+  dfree(ctx, dl);
+  dfree(ctx, dout);
+  return AH_OK;
+}
 
 ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, size_t run_size) {
   ah_status st;

@@ -211,3 +211,51 @@ def test_pack_layout(engine):
     assert np.array_equal(bits(planes[:, 0]), expect_lo)
     assert np.array_equal(bits(planes[:, 1]), expect_hi)
     assert np.array_equal(bits(inval), expect_inv)
+
+
+def _degenerate_sites(seed, n, codes_lo, codes_hi):
+    st = synth.Stream(synth.make_key(seed, 77, 1))
+    prims, sites = [], []
+    for _ in range(n):
+        L = st.randint(12, 26)
+        p = synth.random_primer(st, L, st.randint(codes_lo, codes_hi), 0, "RYSWKMBDHVNNN")
+        v = synth.concrete_variant(st, p)
+        sites.append(synth.substitute(st, v, st.randint(0, 4)))
+        prims.append(p)
+    return prims, sites
+
+
+@pytest.mark.parametrize("method,na", [(5, 50.0), (0, 50.0), (1, 20.0), (3, 50.0), (4, 10.0), (2, 200.0)])
+def test_degenerate_site_tm_exact_max(engine, method, na):
+    """Sites of primers with 7-9 degenerate codes (128 to 262,144 variants) take the chain method on
+    the GPU; the oracle enumerates every variant."""
+    from paper_2511_00170_gb300 import ah
+
+    prims, sites = _degenerate_sites(method, 30, 7, 9)
+    got = ah.ah_tm_sites(engine.ctx, prims, sites, ah.tm_params(Na=na, saltcorr=method))
+    for p, s, g in zip(prims, sites, got):
+        r = oracle.tm_site(p, s, synth.TmParams(Na=na, saltcorr=method))
+        if r is None:
+            assert math.isnan(g), (p, s)
+        else:
+            assert abs(g - r) <= compare.TM_TOL, (p, s, g, r)
+
+
+def test_degenerate_site_tm_small_sets_and_method6(engine):
+    """Up to 64 variants, and salt method 6 at any count, enumerate on the GPU too."""
+    from paper_2511_00170_gb300 import ah
+
+    prims, sites = _degenerate_sites(11, 40, 0, 6)
+    for method in (5, 6):
+        got = ah.ah_tm_sites(engine.ctx, prims, sites, ah.tm_params(saltcorr=method))
+        for p, s, g in zip(prims, sites, got):
+            r = oracle.tm_site(p, s, synth.TmParams(saltcorr=method))
+            assert (r is None and math.isnan(g)) or abs(g - r) <= compare.TM_TOL, (p, s, g, r)
+
+
+def test_dense_workload_small(engine):
+    """Tandem repeats and highly degenerate primers (dense sites, overflowing tiles, chain Tm)."""
+    wl = synth.dense(n_genomes=10, median=2e5, sigma=0.3)
+    wl.fwd = ["NNRYTGACCGTAGSAN"[:16]]
+    wl.rev = ["NAGYCGATWKSGNACT"[:16]]
+    _run_both(engine, wl)
