@@ -43,7 +43,8 @@ typedef enum {
   AH_EOVERFLOW = 4,  /* an output would exceed a caller-given capacity */
   AH_ETIMEOUT = 5,   /* a bounded device wait ran out */
   AH_EJIT = 6,       /* run-time compilation of a specialised kernel failed */
-  AH_EINTERNAL = 7   /* a device self-check failed */
+  AH_EINTERNAL = 7,  /* a device self-check failed */
+  AH_ELIMIT = 8      /* an exact computation would exceed its work bound (degenerate site Tm) */
 } ah_status;
 
 typedef struct ah_ctx ah_ctx;
@@ -254,12 +255,18 @@ typedef struct {
   int32_t saltcorr;              /* 0 none; 1-6 as in Biopython's salt_correction; default 5 */
   int32_t filter;                /* nonzero: drop amplicons with Tm < min_tm or undefined Tm */
   double min_tm;                 /* degrees C */
+  int32_t variants;              /* degenerate primers: 0 every concrete variant (default);
+                                    1 only variants matching the site within k and the clamp */
 } ah_tm_params;
 
-/* Fill tm and flags of every amplicon: the nearest-neighbour Tm (FP64) of each site is the
- * maximum over the primer's concrete variants of Tm(variant, site); the amplicon's Tm is the lower
- * of its two sites'.  With filter set, the amplicon list is compacted to the kept ones (order
- * preserved).  Synchronises the stream when filter is set. */
+/* Fill tm and flags of every amplicon (Section "Implementations": Biopython's Tm_NN in C; Section
+ * "Primer degeneracy": Tm over the primer's variants).  The nearest-neighbour Tm (FP64) of each site
+ * is the maximum of Tm(variant, site) over every concrete variant of its primer, or with
+ * params->variants = 1 over those that match the site under the scan's rule (at most the pair's k
+ * differing positions, none in the 3' clamp).  The amplicon's Tm is the lower of its two sites'.  With filter set, the amplicon list is compacted to
+ * the kept ones (order preserved).  Synchronises the stream.  AH_ELIMIT when a site has more than
+ * 2^20 qualifying variants and the exact chain method does not apply (salt method 6, or a variant
+ * whose entropy sum could reach zero); that site's Tm is then NaN. */
 ah_status ah_tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a,
                        const ah_tm_params* params);
 
@@ -271,11 +278,16 @@ ah_status ah_tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const
 
 /* Tm of n (possibly degenerate) primers at given sites: primers[i] in IUPAC codes (5'->3'), sites[i]
  * the genome bases under it in the primer's orientation (A, C, G, T; same length 2..32).  The
- * maximum over the primer's concrete variants, as ah_tm_filter computes per site: enumerated for at
- * most 64 variants (or salt method 6), otherwise exact by Dinkelbach iterations over a chain
- * Viterbi.  tm_out[i] is NaN when no variant has a defined Tm.  Synchronises. */
+ * maximum over the primer's concrete variants with at most k[i] positions differing from the site
+ * and none among its last clamp[i] positions, as ah_tm_filter computes per site: enumerated for at
+ * most 64 such variants, otherwise exact by Dinkelbach iterations over a chain Viterbi whose states
+ * count mismatches, falling back to enumeration (up to 2^20 variants) for salt method 6.  k == NULL
+ * or k[i] >= the primer length: no mismatch limit; otherwise k[i] <= 15.  clamp == NULL: no clamp;
+ * clamp[i] <= length (params->variants is not read: k and clamp say which variants count).
+ * tm_out[i] is NaN when no qualifying variant has a defined Tm.  Synchronises; AH_ELIMIT as for
+ * ah_tm_filter. */
 ah_status ah_tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const char* const* sites,
-                      const ah_tm_params* params, double* tm_out);
+                      const uint8_t* k, const uint8_t* clamp, const ah_tm_params* params, double* tm_out);
 
 /* ------------------------------------------------------------------------------------------ */
 /* 5. sequences and barcodes                                                                    */

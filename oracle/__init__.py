@@ -42,7 +42,8 @@ ORIENT_NAMES = ("FR", "RF", "FF", "RR")
 class _TmParams(ctypes.Structure):
     _fields_ = [("Na", ctypes.c_double), ("K", ctypes.c_double), ("Tris", ctypes.c_double),
                 ("Mg", ctypes.c_double), ("dNTPs", ctypes.c_double), ("dnac1", ctypes.c_double),
-                ("dnac2", ctypes.c_double), ("saltcorr", ctypes.c_int), ("selfcomp", ctypes.c_int)]
+                ("dnac2", ctypes.c_double), ("saltcorr", ctypes.c_int), ("selfcomp", ctypes.c_int),
+                ("variants", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -73,10 +74,10 @@ def _get():
             L.or_tm_duplex.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int,
                                        ctypes.POINTER(_TmParams), ctypes.POINTER(ctypes.c_int)]
             L.or_tm_duplex.restype = ctypes.c_double
-            L.or_tm_site.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(_TmParams),
-                                     ctypes.POINTER(ctypes.c_int)]
+            L.or_tm_site.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(_TmParams), ctypes.POINTER(ctypes.c_int)]
             L.or_tm_site.restype = ctypes.c_double
-            L.or_tm_hits.argtypes = [vp, vp, vp, i64, vp, vp, ctypes.POINTER(_TmParams), vp, vp]
+            L.or_tm_hits.argtypes = [vp, vp, vp, i64, vp, vp, vp, ctypes.c_int, ctypes.POINTER(_TmParams), vp, vp]
             L.or_tm_hits.restype = None
             L.or_extract.argtypes = [vp, vp, vp, vp, i64, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
             L.or_extract.restype = i64
@@ -88,7 +89,8 @@ def _get():
 
 def _params(tm) -> _TmParams:
     return _TmParams(float(tm.Na), float(tm.K), float(tm.Tris), float(tm.Mg), float(tm.dNTPs), float(tm.dnac1),
-                     float(tm.dnac2), int(tm.saltcorr), int(getattr(tm, "selfcomp", 0)))
+                     float(tm.dnac2), int(tm.saltcorr), int(getattr(tm, "selfcomp", 0)),
+                     int(getattr(tm, "variants", 0)))
 
 
 def _strs(xs: Sequence[str]):
@@ -154,15 +156,21 @@ def tm_duplex(seq: str, cseq: str, tm) -> Optional[float]:
     return t if d.value else None
 
 
-def tm_site(primer: str, site: str, tm) -> Optional[float]:
+def tm_site(primer: str, site: str, tm, k: Optional[int] = None, clamp: int = 0) -> Optional[float]:
+    """Tm of `primer` at `site` (site bases in the primer's 5'->3' orientation): the maximum over the
+    primer's concrete variants with at most `k` mismatches to the site (default: any number) and an
+    exact match over the last `clamp` positions (reading R14); None when no such variant is defined."""
     st = ctypes.c_int()
     p = _params(tm)
-    t = _get().or_tm_site(primer.encode(), site.encode(), len(primer), ctypes.byref(p), ctypes.byref(st))
+    k = len(primer) if k is None else k
+    t = _get().or_tm_site(primer.encode(), site.encode(), len(primer), int(k), int(clamp), ctypes.byref(p),
+                          ctypes.byref(st))
     return None if st.value else t
 
 
 def tm_hits(wl, hits: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
-    """Per hit: Tm (max over the primer's concrete variants) and status (0 ok, 1 undefined)."""
+    """Per hit: Tm (max over the primer's concrete variants; with ``wl.tm.variants == 1`` only those
+    that match the site within the pair's k and the clamp) and status (0 ok, 1 undefined)."""
     L = _get()
     hits = np.ascontiguousarray(hits, dtype=HIT_DTYPE)
     seq = np.ascontiguousarray(wl.seq, dtype=np.uint8)
@@ -171,8 +179,10 @@ def tm_hits(wl, hits: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
     st = np.empty(len(hits), dtype=np.uint8)
     fw, rv = _strs(wl.fwd), _strs(wl.rev)
     p = _params(wl.tm)
+    ks = np.ascontiguousarray(np.asarray(wl.k, dtype=np.uint8))
     L.or_tm_hits(seq.ctypes.data, offs.ctypes.data, hits.ctypes.data, len(hits), ctypes.cast(fw, ctypes.c_void_p),
-                 ctypes.cast(rv, ctypes.c_void_p), ctypes.byref(p), tm.ctypes.data, st.ctypes.data)
+                 ctypes.cast(rv, ctypes.c_void_p), ks.ctypes.data, int(wl.clamp), ctypes.byref(p), tm.ctypes.data,
+                 st.ctypes.data)
     return tm, st
 
 

@@ -14,8 +14,8 @@
  *              stops the walk; orientation FR/RF/FF/RR; RF is reverse-complemented.
  *   extract -- Supplementary "Primer trimming and barcode extraction" and "Headers and outputs".
  *   Tm      -- Section "Implementations" (AHv2): the nearest-neighbour Tm of Biopython's Tm_NN,
- *              in double precision; Section "Primer degeneracy": Tm is evaluated for every
- *              concrete variant of a degenerate primer.
+ *              in double precision; Section "Primer degeneracy": Tm is evaluated over the
+ *              concrete variants of a degenerate primer.
  *
  * Readings where the paper is silent (each is listed in the design notes):
  *   R1 a window holding any non-ACGT genome base is not a hit; lower-case acgt are bases.
@@ -32,7 +32,11 @@
  *   R11 a trimmed amplicon whose sites overlap is empty (the amplicon is still reported).
  *   R12 barcodes are clipped at record ends; non-ACGT bases are written as N.
  *   R13 the amplicon Tm is the lower of its two site Tms.
- *   R14 the Tm of a degenerate primer at a site is the maximum over all its concrete variants.
+ *   R14 the Tm of a degenerate primer at a site is the maximum over every concrete variant of
+ *       the primer, variants that mismatch the site included.  Option (variants = 1): only the
+ *       variants that themselves match the site under the scan's rule count (at most k
+ *       mismatching positions, an exact 3' clamp); the variant that agrees with the site wherever
+ *       the primer allows it always qualifies.
  *   R15 a variant whose duplex needs a parameter the tables do not have (e.g. two adjacent
  *       mismatches other than the tandem G.T steps) has no Tm; a site with no defined variant
  *       has an undefined Tm, and an amplicon with an undefined Tm is dropped by the filter.
@@ -435,6 +439,7 @@ typedef struct {
   double dnac1, dnac2;           /* nM */
   int saltcorr;                  /* 0 none, 1..6 */
   int selfcomp;
+  int variants;                  /* 0: every concrete variant (R14); 1: only those matching the site */
 } or_tm_params;
 
 static double gc_fraction(const char* s, int L) {
@@ -581,11 +586,14 @@ double or_tm_duplex(const char* seq, const char* cseq, int L, const or_tm_params
 }
 
 /*
- * Tm of a (possibly degenerate) primer at a site: the maximum over every concrete variant of the
- * primer (reading R14).  `site` holds the genome bases in the primer's own 5'->3' orientation;
- * the opposite strand under the primer is their complement.  *status: 0 ok, 1 undefined.
+ * Tm of a (possibly degenerate) primer at a site (reading R14): the maximum over every concrete
+ * variant of the primer that has at most k positions differing from the site and none in the
+ * last `clamp` positions (k = L, clamp = 0: every variant).  `site` holds the genome bases in the primer's own 5'->3' orientation;
+ * the opposite strand under the primer is their complement.  *status: 0 ok, 1 undefined (no
+ * qualifying variant, or none whose duplex is defined).
  */
-double or_tm_site(const char* primer, const char* site, int L, const or_tm_params* p, int* status) {
+double or_tm_site(const char* primer, const char* site, int L, int k, int clamp, const or_tm_params* p,
+                  int* status) {
   char cseq[40], var[40];
   char choices[40][4];
   int nchoice[40], idx[40];
@@ -604,12 +612,21 @@ double or_tm_site(const char* primer, const char* site, int L, const or_tm_param
   double best = -INFINITY;
   int any = 0;
   for (;;) {
-    for (int i = 0; i < L; ++i) var[i] = choices[i][idx[i]];
-    int defined = 0;
-    double t = or_tm_duplex(var, cseq, L, p, &defined);
-    if (defined) {
-      any = 1;
-      if (t > best) best = t;
+    int mism = 0, clamp_ok = 1;
+    for (int i = 0; i < L; ++i) {
+      var[i] = choices[i][idx[i]];
+      if (var[i] != toupper((unsigned char)site[i])) {
+        ++mism;
+        if (i >= L - clamp) clamp_ok = 0;
+      }
+    }
+    if (clamp_ok && mism <= k) {
+      int defined = 0;
+      double t = or_tm_duplex(var, cseq, L, p, &defined);
+      if (defined) {
+        any = 1;
+        if (t > best) best = t;
+      }
     }
     /* next variant (odometer over the degenerate positions) */
     int i = L - 1;
@@ -634,10 +651,10 @@ static void hit_site(const uint8_t* g, const or_hit* h, int L, char* out) {
   out[L] = 0;
 }
 
-/* Tm of every hit (NaN + status 1 when undefined). */
+/* Tm of every hit (NaN + status 1 when undefined); k and clamp matter only with variants = 1. */
 void or_tm_hits(const uint8_t* seq, const int64_t* offsets, const or_hit* hits, int64_t n_hits,
-                const char* const* fwd, const char* const* rev, const or_tm_params* p, double* tm,
-                uint8_t* status) {
+                const char* const* fwd, const char* const* rev, const uint8_t* k, int clamp,
+                const or_tm_params* p, double* tm, uint8_t* status) {
   for (int64_t i = 0; i < n_hits; ++i) {
     const or_hit* h = &hits[i];
     const char* P = h->primer == 0 ? fwd[h->pair] : rev[h->pair];
@@ -645,7 +662,7 @@ void or_tm_hits(const uint8_t* seq, const int64_t* offsets, const or_hit* hits, 
     char site[40];
     hit_site(seq + offsets[h->record], h, L, site);
     int st = 0;
-    tm[i] = or_tm_site(P, site, L, p, &st);
+    tm[i] = p->variants ? or_tm_site(P, site, L, k[h->pair], clamp, p, &st) : or_tm_site(P, site, L, L, 0, p, &st);
     status[i] = (uint8_t)st;
   }
 }

@@ -16,9 +16,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libah.so")
 
-AH_OK, AH_EINVAL, AH_ENOMEM, AH_ECUDA, AH_EOVERFLOW, AH_ETIMEOUT, AH_EJIT, AH_EINTERNAL = range(8)
+AH_OK, AH_EINVAL, AH_ENOMEM, AH_ECUDA, AH_EOVERFLOW, AH_ETIMEOUT, AH_EJIT, AH_EINTERNAL, AH_ELIMIT = range(9)
 STATUS_NAMES = {0: "AH_OK", 1: "AH_EINVAL", 2: "AH_ENOMEM", 3: "AH_ECUDA", 4: "AH_EOVERFLOW", 5: "AH_ETIMEOUT",
-                6: "AH_EJIT", 7: "AH_EINTERNAL"}
+                6: "AH_EJIT", 7: "AH_EINTERNAL", 8: "AH_ELIMIT"}
 AH_FR, AH_RF, AH_FF, AH_RR = 1, 2, 4, 8
 
 HIT_DTYPE = np.dtype([("record", "<u4"), ("pos", "<u4"), ("pattern", "<u2"), ("mism", "u1"), ("flags", "u1")])
@@ -36,7 +36,8 @@ class AhError(RuntimeError):
 class ah_tm_params(ctypes.Structure):
     _fields_ = [("Na", ctypes.c_double), ("K", ctypes.c_double), ("Tris", ctypes.c_double), ("Mg", ctypes.c_double),
                 ("dNTPs", ctypes.c_double), ("dnac1", ctypes.c_double), ("dnac2", ctypes.c_double),
-                ("saltcorr", ctypes.c_int32), ("filter", ctypes.c_int32), ("min_tm", ctypes.c_double)]
+                ("saltcorr", ctypes.c_int32), ("filter", ctypes.c_int32), ("min_tm", ctypes.c_double),
+                ("variants", ctypes.c_int32)]
 
 
 class ah_plan_params(ctypes.Structure):
@@ -117,7 +118,7 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_uint64)]),
     "ah_tm_filter": (_I32, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ah_tm_params)]),
     "ah_tm_duplexes": (_I32, [_VP, _U32, _VP, _VP, ctypes.POINTER(ah_tm_params), _VP]),
-    "ah_tm_sites": (_I32, [_VP, _U32, _VP, _VP, ctypes.POINTER(ah_tm_params), _VP]),
+    "ah_tm_sites": (_I32, [_VP, _U32, _VP, _VP, _VP, _VP, ctypes.POINTER(ah_tm_params), _VP]),
     "ah_extract_barcodes": (_I32, [_VP, _VP, _VP, _VP, _VP, _I32, _U32, _U32]),
     "ah_amplicons_count": (_I32, [_VP, ctypes.POINTER(ctypes.c_uint64)]),
     "ah_amplicons_copy": (_I32, [_VP, _VP, _U64]),
@@ -337,9 +338,10 @@ def ah_pair_amplicons_noalloc(stream: int, d_hits: int, n_hits: int, d_pair_offs
 
 
 # ------------------------------------------------------------------------------------------ Tm
-def tm_params(Na=50.0, K=0.0, Tris=0.0, Mg=0.0, dNTPs=0.0, dnac1=25.0, dnac2=25.0, saltcorr=5, min_tm=None) -> ah_tm_params:
+def tm_params(Na=50.0, K=0.0, Tris=0.0, Mg=0.0, dNTPs=0.0, dnac1=25.0, dnac2=25.0, saltcorr=5, min_tm=None,
+              variants=0) -> ah_tm_params:
     return ah_tm_params(Na, K, Tris, Mg, dNTPs, dnac1, dnac2, saltcorr, 0 if min_tm is None else 1,
-                        0.0 if min_tm is None else float(min_tm))
+                        0.0 if min_tm is None else float(min_tm), int(variants))
 
 
 def ah_tm_filter(ctx, batch, primers, hits, amps, params: ah_tm_params) -> None:
@@ -356,12 +358,18 @@ def ah_tm_duplexes(ctx, seqs: Sequence[str], cseqs: Sequence[str], params: ah_tm
     return out
 
 
-def ah_tm_sites(ctx, primers: Sequence[str], sites: Sequence[str], params: ah_tm_params) -> np.ndarray:
+def ah_tm_sites(ctx, primers: Sequence[str], sites: Sequence[str], params: ah_tm_params,
+                k: Optional[Sequence[int]] = None, clamp: Optional[Sequence[int]] = None) -> np.ndarray:
+    """Per site: the maximum Tm over the primer's variants with at most k[i] mismatches and an exact
+    clamp of clamp[i] bases (None: no limit / no clamp)."""
     n = len(primers)
     pa = (ctypes.c_char_p * n)(*[s.encode("ascii") for s in primers])
     sa = (ctypes.c_char_p * n)(*[s.encode("ascii") for s in sites])
+    ka = None if k is None else np.ascontiguousarray(np.asarray(k, dtype=np.uint8))
+    ca = None if clamp is None else np.ascontiguousarray(np.asarray(clamp, dtype=np.uint8))
     out = np.empty(n, dtype=np.float64)
     _check(load().ah_tm_sites(ctx, n, ctypes.cast(pa, ctypes.c_void_p), ctypes.cast(sa, ctypes.c_void_p),
+                              None if ka is None else ka.ctypes.data, None if ca is None else ca.ctypes.data,
                               ctypes.byref(params), out.ctypes.data), ctx)
     return out
 

@@ -58,6 +58,53 @@ __global__ void k_pack(const uint8_t* __restrict__ src, const PackItem* __restri
   }
 }
 
+// Items whose source is 16-byte aligned: every lane converts 16 bases fetched with one 16-byte load
+// (a warp covers 512 bases = 16 groups); the code bits of four bytes are gathered with one
+// multiply each, and lanes 2l and 2l+1 join their halves of group l with a shuffle.
+__device__ __forceinline__ uint32_t gather4(uint32_t b) {  // bit 0 of bytes 0..3 -> bits 0..3
+  return (b * 0x10204080u) >> 28;
+}
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {  // 0x80 in each zero byte, exactly
+  return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
+}
+
+__global__ void k_pack16(const uint8_t* __restrict__ src, const PackItem* __restrict__ items, uint2* __restrict__ planes,
+                         uint32_t* __restrict__ invalid) {
+  const PackItem it = items[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (uint32_t blk = warp; blk * 16u < it.n_groups; blk += nwarps) {
+    const uint32_t x0 = blk * 512u + (uint32_t)lane * 16u;  // first base of this lane's 16
+    uint32_t w[4] = {0x4E4E4E4Eu, 0x4E4E4E4Eu, 0x4E4E4E4Eu, 0x4E4E4E4Eu};  // 'N' past the record
+    if (x0 + 16u <= it.n_valid) {
+      const uint4 v = __ldg((const uint4*)(src + it.src_off + x0));
+      w[0] = v.x, w[1] = v.y, w[2] = v.z, w[3] = v.w;
+    } else if (x0 < it.n_valid) {
+      for (uint32_t i = 0; i < it.n_valid - x0; ++i)
+        w[i >> 2] = (w[i >> 2] & ~(0xFFu << (8 * (i & 3)))) | ((uint32_t)__ldg(src + it.src_off + x0 + i) << (8 * (i & 3)));
+    }
+    uint32_t lo = 0, hi = 0, inv = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t u = w[q] | 0x20202020u;  // lower case
+      const uint32_t ok = zero_bytes(u ^ 0x61616161u) | zero_bytes(u ^ 0x63636363u) | zero_bytes(u ^ 0x67676767u) |
+                          zero_bytes(u ^ 0x74747474u);
+      const uint32_t bad = ((~ok) >> 7) & 0x01010101u;
+      lo |= gather4((w[q] >> 1) & 0x01010101u) << (4 * q);
+      hi |= gather4((w[q] >> 2) & 0x01010101u) << (4 * q);
+      inv |= gather4(bad) << (4 * q);
+    }
+    lo &= ~inv;
+    hi &= ~inv;
+    const uint32_t lo2 = __shfl_xor_sync(0xffffffffu, lo, 1), hi2 = __shfl_xor_sync(0xffffffffu, hi, 1),
+                   inv2 = __shfl_xor_sync(0xffffffffu, inv, 1);
+    const uint32_t g = blk * 16u + ((uint32_t)lane >> 1);
+    if (!(lane & 1) && g < it.n_groups) {
+      planes[it.dst_group + g] = make_uint2(lo | (lo2 << 16), hi | (hi2 << 16));
+      invalid[it.dst_group + g] = inv | (inv2 << 16);
+    }
+  }
+}
+
 void free_batch_arrays(ah_batch* b) {
   if (!b || !b->ctx) return;
   dfree(b->ctx, b->rec_group);
@@ -129,6 +176,26 @@ void add_items(std::vector<PackItem>& items, const ah_batch* b, uint32_t r, uint
   }
 }
 
+bool aligned16(const uint8_t* base, const PackItem* items, size_t n) {
+  if ((uintptr_t)base & 15) return false;
+  for (size_t i = 0; i < n; ++i)
+    if (items[i].src_off & 15) return false;
+  return true;
+}
+
+void launch_pack(cudaStream_t s, const uint8_t* d_src, const PackItem* d_items, const PackItem* h_items, size_t n,
+                 ah_batch* b, ah_ctx* ctx) {
+  const bool vec = aligned16(d_src, h_items, n);
+  for (size_t i = 0; i < n; i += 65535) {
+    const unsigned m = (unsigned)std::min<size_t>(65535, n - i);
+    if (vec)
+      k_pack16<<<m, kPackThreads, 0, s>>>(d_src, d_items + i, b->planes, b->invalid);
+    else
+      k_pack<<<m, kPackThreads, 0, s>>>(d_src, d_items + i, b->planes, b->invalid);
+    launched(ctx);
+  }
+}
+
 ah_status run_pack(ah_ctx* ctx, const uint8_t* d_src, const std::vector<PackItem>& items, ah_batch* b) {
   if (items.empty()) return AH_OK;
   PackItem* d_items;
@@ -136,11 +203,7 @@ ah_status run_pack(ah_ctx* ctx, const uint8_t* d_src, const std::vector<PackItem
   if (st) return st;
   AH_CUDA(ctx, cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(PackItem), cudaMemcpyHostToDevice,
                                ctx->stream));
-  for (size_t i = 0; i < items.size(); i += 65535) {
-    unsigned n = (unsigned)std::min<size_t>(65535, items.size() - i);
-    k_pack<<<n, kPackThreads, 0, ctx->stream>>>(d_src, d_items + i, b->planes, b->invalid);
-    launched(ctx);
-  }
+  launch_pack(ctx->stream, d_src, d_items, items.data(), items.size(), b, ctx);
   AH_CUDA(ctx, cudaGetLastError());
   // items (host) must stay alive until the copy has been consumed
   AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -291,49 +354,89 @@ ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, co
   cudaSetDevice(ctx->device);
   ah_batch* b = new ah_batch();
   ah_status st = layout_batch(ctx, n_rec, lens, genome_ids, b);
-  uint8_t* staging[2] = {nullptr, nullptr};
-  if (!st) st = dalloc(ctx, &staging[0], kChunkBases);
-  if (!st) st = dalloc(ctx, &staging[1], kChunkBases);
-  // stream records (split at chunk boundaries) through two device staging chunks
-  int which = 0;
-  uint64_t fill = 0;
-  std::vector<PackItem> items;
-  auto flush = [&]() -> ah_status {
-    ah_status s = run_pack(ctx, staging[which], items, b);
-    items.clear();
-    fill = 0;
-    which ^= 1;
-    return s;
+  if (st) {
+    free_batch_arrays(b);
+    delete b;
+    return st;
+  }
+  // Plan: records (split on group boundaries) fill chunks of up to kChunkBases bases, each piece at a
+  // 16-byte aligned offset of its chunk's staging buffer.
+  struct Piece {
+    const char* src;
+    uint64_t bytes, stage_off;
   };
-  for (uint32_t r = 0; r < n_rec && !st; ++r) {
+  std::vector<std::vector<Piece>> pieces(1);
+  std::vector<std::vector<PackItem>> items(1);
+  uint64_t fill = 0, stage_max = 0;
+  for (uint32_t r = 0; r < n_rec; ++r) {
     uint64_t len = lens[r], done = 0;
-    if (len == 0) {
-      add_items(items, b, r, 0, 0, fill);
-      continue;
-    }
-    while (done < len && !st) {
-      uint64_t room = kChunkBases - fill;
+    while (done < len) {
+      uint64_t room = kChunkBases - std::min(fill, kChunkBases);
       uint64_t take = std::min(room, len - done);
       if (take < len - done) take &= ~uint64_t(31);  // split records on group boundaries
       if (take == 0) {
-        st = flush();
+        pieces.emplace_back();
+        items.emplace_back();
+        fill = 0;
         continue;
       }
-      cudaError_t e = cudaMemcpyAsync(staging[which] + fill, seqs[r] + done, take, cudaMemcpyHostToDevice, ctx->stream);
-      if (e != cudaSuccess) st = fail(ctx, AH_ECUDA, "host-to-device copy failed: %s", cudaGetErrorString(e));
-      add_items(items, b, r, done, done + take, fill);
-      fill += take;
+      const uint64_t off = (fill + 15) & ~uint64_t(15);
+      pieces.back().push_back({seqs[r] + done, take, off});
+      add_items(items.back(), b, r, done, done + take, off);
+      fill = off + take;
+      stage_max = std::max(stage_max, fill);
       done += take;
-      if (fill == kChunkBases && !st) st = flush();
     }
   }
-  if (!st) st = flush();
+  // all items uploaded once; the chunks then alternate between two staging buffers: copies on a
+  // second stream, packing on the context's stream, ordered by events
+  std::vector<PackItem> all;
+  std::vector<size_t> first;
+  for (auto& v : items) {
+    first.push_back(all.size());
+    all.insert(all.end(), v.begin(), v.end());
+  }
+  uint8_t* staging[2] = {nullptr, nullptr};
+  PackItem* d_items = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, packed[2] = {nullptr, nullptr};
+  if (!st) st = dalloc(ctx, &staging[0], std::max<uint64_t>(stage_max, 16));
+  if (!st && pieces.size() > 1) st = dalloc(ctx, &staging[1], std::max<uint64_t>(stage_max, 16));
+  if (!st) st = dalloc(ctx, &d_items, std::max<size_t>(all.size(), 1));
+  cudaError_t e = cudaSuccess;
+  if (!st) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess && !st; ++i) {
+    e = cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&packed[i], cudaEventDisableTiming);
+  }
+  if (!st && e == cudaSuccess && !all.empty())
+    e = cudaMemcpyAsync(d_items, all.data(), all.size() * sizeof(PackItem), cudaMemcpyHostToDevice, ctx->stream);
+  for (size_t c = 0; c < pieces.size() && !st && e == cudaSuccess; ++c) {
+    const int w = (int)(c & 1);
+    if (c >= 2) e = cudaStreamWaitEvent(cs, packed[w], 0);  // the buffer's previous chunk is packed
+    for (const Piece& pc : pieces[c]) {
+      if (e != cudaSuccess) break;
+      e = cudaMemcpyAsync(staging[w] + pc.stage_off, pc.src, pc.bytes, cudaMemcpyHostToDevice, cs);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(copied[w], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, copied[w], 0);
+    if (e == cudaSuccess && !items[c].empty())
+      launch_pack(ctx->stream, staging[w], d_items + first[c], items[c].data(), items[c].size(), b, ctx);
+    if (e == cudaSuccess) e = cudaEventRecord(packed[w], ctx->stream);
+  }
+  if (!st && e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (!st && e != cudaSuccess) st = fail(ctx, AH_ECUDA, "packing failed: %s", cudaGetErrorString(e));
+  if (cs) {
+    cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (copied[i]) cudaEventDestroy(copied[i]);
+    if (packed[i]) cudaEventDestroy(packed[i]);
+  }
   dfree(ctx, staging[0]);
   dfree(ctx, staging[1]);
-  if (!st) {
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) st = fail(ctx, AH_ECUDA, "packing failed: %s", cudaGetErrorString(e));
-  }
+  dfree(ctx, d_items);
   if (st) {
     free_batch_arrays(b);
     delete b;
@@ -522,9 +625,11 @@ ah_status ah_primers_create(ah_ctx* ctx, uint32_t n_pairs, const char* const* fw
   }
   ah_status st = dalloc(ctx, &p->d_plen, plen.size());
   if (!st) st = dalloc(ctx, &p->d_psets, psets.size());
+  if (!st) st = dalloc(ctx, &p->d_pk, p->k.size());
   if (!st) {
     cudaMemcpyAsync(p->d_plen, plen.data(), plen.size(), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemcpyAsync(p->d_psets, psets.data(), psets.size(), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(p->d_pk, p->k.data(), p->k.size(), cudaMemcpyHostToDevice, ctx->stream);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = fail(ctx, AH_ECUDA, "primer upload failed");
   }
   if (st) {
@@ -540,6 +645,7 @@ void ah_primers_free(ah_primers* p) {
   if (p->ctx) {
     dfree(p->ctx, p->d_plen);
     dfree(p->ctx, p->d_psets);
+    dfree(p->ctx, p->d_pk);
   }
   delete p;
 }
@@ -615,13 +721,14 @@ ah_status ah_tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const
   return tm_duplexes(ctx, n, seqs, cseqs, params, tm_out);
 }
 
-ah_status ah_tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const char* const* sites,
+ah_status ah_tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const char* const* sites, const uint8_t* k,
+                      const uint8_t* clamp,
                       const ah_tm_params* params, double* tm_out) {
   if (!ctx || (n && (!primers || !sites || !tm_out)) || !params) return fail(ctx, AH_EINVAL, "ah_tm_sites: NULL argument");
   if (params->saltcorr < 0 || params->saltcorr > 6)
     return fail(ctx, AH_EINVAL, "ah_tm_sites: salt correction method %d is not supported (0-6)", params->saltcorr);
   cudaSetDevice(ctx->device);
-  return tm_sites(ctx, n, primers, sites, params, tm_out);
+  return tm_sites(ctx, n, primers, sites, k, clamp, params, tm_out);
 }
 
 ah_status ah_extract_barcodes(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a,

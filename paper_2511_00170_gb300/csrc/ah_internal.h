@@ -29,6 +29,7 @@ enum : uint32_t {
   ST_SCAN_MISMATCH = 1u << 0,   // bit-sliced matcher and exact re-check disagree
   ST_PAIR_OVERFLOW = 1u << 1,
   ST_BAD_INPUT = 1u << 2,
+  ST_TM_LIMIT = 1u << 3,        // a degenerate site Tm needed more than its enumeration bound
 };
 
 struct Pattern {
@@ -101,6 +102,7 @@ struct ah_primers {
   // device copies for pairing / Tm / extraction
   uint8_t* d_plen = nullptr;           // per pattern length
   uint8_t* d_psets = nullptr;          // [n_pairs][2 primers][32] IUPAC sets of the primers as written
+  uint8_t* d_pk = nullptr;             // [n_pairs] mismatch budget
 };
 
 struct ah_hits {
@@ -166,8 +168,8 @@ ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const a
                     const ah_tm_params* params);
 ah_status tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const char* const* cseqs,
                       const ah_tm_params* params, double* out);
-ah_status tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const char* const* sites,
-                   const ah_tm_params* params, double* out);
+ah_status tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const char* const* sites, const uint8_t* k,
+                   const uint8_t* clamp, const ah_tm_params* params, double* out);
 // extraction (ah_extract.cu)
 ah_status extract(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a, int trim,
                   uint32_t fb, uint32_t rb);
@@ -193,6 +195,7 @@ void launch_pair_walk(cudaStream_t s, bool emit, const ah_hit* hits, uint64_t ca
                       uint32_t* overflow);
 ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, size_t run_size);
 void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit_cap, const uint64_t* d_nhits,
+               const uint8_t* pk, int clamp, uint32_t* status,
                const uint2* planes, const uint64_t* rec_group, const uint8_t* plen, const uint8_t* psets, double* hit_tm,
                ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep);
 void launch_compact_amps(cudaStream_t s, const ah_amplicon* in, uint64_t cap, const uint32_t* keep, const uint64_t* off,

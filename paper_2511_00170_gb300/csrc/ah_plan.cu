@@ -112,7 +112,7 @@ void enqueue_step(ah_plan* pl, cudaStream_t s) {
   launch_pair_walk(s, true, pl->hits, pl->hit_cap, n_hits, pl->pair_off, p->d_plen, q.min_len, q.max_len,
                    q.orient_mask & 15u, nullptr, pl->poff, pl->amps, pl->amp_cap, pl->ctr + 1);
   const uint64_t* n_amps = pl->poff + pl->hit_cap;
-  launch_tm(s, pl->tm_run, pl->hits, pl->hit_cap, n_hits, b->planes, b->rec_group, p->d_plen, p->d_psets, pl->hit_tm,
+  launch_tm(s, pl->tm_run, pl->hits, pl->hit_cap, n_hits, p->d_pk, p->clamp, pl->ctx->d_status, b->planes, b->rec_group, p->d_plen, p->d_psets, pl->hit_tm,
             pl->amps, pl->amp_cap, n_amps, q.tm.filter, q.tm.min_tm, pl->keep);
   const ah_amplicon* out = pl->amps;
   const uint64_t* n_out = n_amps;

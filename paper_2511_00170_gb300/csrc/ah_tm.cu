@@ -85,6 +85,10 @@ constexpr double kTermATH = 2.3, kTermATS = 4.1;
 constexpr double kTermGCH = 0.1, kTermGCS = -2.8;
 constexpr double kOneGCH = 0.0, kOneGCS = 0.0, kAllATH = 0.0, kAllATS = 0.0, k5TAH = 0.0, k5TAS = 0.0;
 
+// degenerate site Tm: largest mismatch budget, and the enumeration bounds
+constexpr int kMaxK = 15;
+constexpr uint64_t kEnumSmall = 64, kEnumLimit = 1ull << 20;
+
 struct NNTables {
   double step_h[256], step_s[256];  // NaN: no parameter
   double term_h[256], term_s[256];  // NaN: not a terminal-mismatch step
@@ -172,6 +176,7 @@ struct TmRun {
   double corr_const; // methods 1-4: Tm correction
   int saltcorr;
   int selfcomp;
+  int variants;      // 1: degenerate site Tm over the variants matching the site only
 };
 
 ah_status make_run(ah_ctx* ctx, const ah_tm_params* p, TmRun* r) {
@@ -183,8 +188,10 @@ ah_status make_run(ah_ctx* ctx, const ah_tm_params* p, TmRun* r) {
   if (!(conc > 0)) return fail(ctx, AH_EINVAL, "Tm: strand concentrations give C <= 0");
   r->rlnk = 1.987 * std::log(conc);
   r->ln_mon = p->saltcorr ? std::log(mon) : 0.0;
+  if (p->variants != 0 && p->variants != 1) return fail(ctx, AH_EINVAL, "Tm: variants must be 0 or 1");
   r->saltcorr = p->saltcorr;
   r->selfcomp = 0;
+  r->variants = p->variants;
   switch (p->saltcorr) {
     case 1: r->corr_const = 16.6 * std::log10(mon); break;
     case 2: r->corr_const = 16.6 * std::log10(mon / (1.0 + 0.7 * mon)); break;
@@ -300,126 +307,198 @@ __device__ __forceinline__ void end_sums(int j, int L, uint8_t v, double* dh, do
   if (j == L - 1 && v == 0) *dh += k5TAH, *ds += k5TAS;   // 3' A
 }
 
-// Exact maximum of Tm over the variants of `sets` at site `s` for salt methods 0-5 and L >= 3.
+// The variants that count at a site (reading R14): per position the primer's codes, only the site's
+// own base inside the 3' clamp; at most k positions may differ from the site (k < 0: no limit).
+struct SiteVariants {
+  uint8_t s[32], c[32], ch[32][4], nch[32];
+  int L, k;  // k = -1 when every combination of choices qualifies
+};
+
+// false when some position has no choice (the site breaks the clamp or a primer code)
+__device__ bool site_variants(const uint8_t* sets, const uint8_t* s, int L, int k, int clamp, SiteVariants* V) {
+  V->L = L;
+  V->k = k >= L ? -1 : k;
+  for (int j = 0; j < L; ++j) {
+    V->s[j] = s[j];
+    V->c[j] = s[j] ^ 2u;  // complement code
+    V->nch[j] = 0;
+    for (int code = 0; code < 4; ++code)
+      if (((sets[j] >> code) & 1) && (j < L - clamp || code == s[j])) V->ch[j][V->nch[j]++] = (uint8_t)code;
+    if (!V->nch[j]) return false;
+  }
+  return true;
+}
+
+// number of qualifying variants, saturating at `cap` + 1
+__device__ uint64_t count_variants(const SiteVariants& V, uint64_t cap) {
+  uint64_t cnt[kMaxK + 1] = {1};
+  const int K = V.k < 0 ? 0 : V.k;
+  for (int j = 0; j < V.L; ++j) {
+    uint64_t nx[kMaxK + 1] = {0};
+    for (int a = 0; a < V.nch[j]; ++a) {
+      const int inc = V.k >= 0 && V.ch[j][a] != V.s[j];
+      for (int m = 0; m + inc <= K; ++m) nx[m + inc] = min(cap + 1, nx[m + inc] + cnt[m]);
+    }
+    for (int m = 0; m <= K; ++m) cnt[m] = nx[m];
+  }
+  uint64_t t = 0;
+  for (int m = 0; m <= K; ++m) t = min(cap + 1, t + cnt[m]);
+  return t;
+}
+
+// maximum Tm over the qualifying variants by depth-first enumeration (mismatch budget pruned)
+__device__ bool enum_max(const SiteVariants& V, const TmRun& R, double* out) {
+  int8_t idx[32];
+  uint8_t mm[33], v[32];
+  const int L = V.L;
+  double best = -INFINITY;
+  bool any = false;
+  int j = 0;
+  idx[0] = -1;
+  mm[0] = 0;
+  while (j >= 0) {
+    if (++idx[j] >= V.nch[j]) {
+      --j;
+      continue;
+    }
+    const uint8_t b = V.ch[j][idx[j]];
+    const int m = mm[j] + (V.k >= 0 && b != V.s[j]);
+    if (V.k >= 0 && m > V.k) continue;
+    v[j] = b;
+    if (j == L - 1) {
+      double t;
+      if (duplex_tm(v, V.c, L, R, &t)) {
+        any = true;
+        best = fmax(best, t);
+      }
+      continue;
+    }
+    mm[j + 1] = (uint8_t)m;
+    ++j;
+    idx[j] = -1;
+  }
+  *out = best;
+  return any;
+}
+
+enum ChainResult { kChainOk, kChainUndefined, kChainUnbounded };
+
+// Exact maximum of Tm over the qualifying variants for salt methods 0-5 and L >= 3.
 // Tm + 273.15 = N(v) / D(v) with N = 1000 dH and D = dS + S0 < 0, and every term of N and D depends on
 // at most two adjacent variant bases.  Dinkelbach's iteration for fractional programmes: for the
-// current ratio lam, a Viterbi pass over the chain (at most four states per position) finds the
-// variant maximising lam * D - N; its ratio becomes the next lam; at the optimum the maximum is 0.
-// Returns false when no variant is defined or D could reach 0.
-__device__ bool site_tm_chain(const uint8_t* sets, const uint8_t* s, int L, const TmRun& R, double* out) {
-  uint8_t c[32], ch[32][4], nch[32], back[32][4], v[32];
-  for (int j = 0; j < L; ++j) {
-    c[j] = s[j] ^ 2u;
-    nch[j] = 0;
-    for (int code = 0; code < 4; ++code)
-      if ((sets[j] >> code) & 1) ch[j][nch[j]++] = (uint8_t)code;
-  }
+// current ratio lam, a Viterbi pass over the chain finds the variant maximising lam * D - N; its ratio
+// becomes the next lam; at the optimum the maximum is 0.  The chain's states are (position, base,
+// mismatches so far), at most 4 x (k + 1) per position.  kChainUnbounded when some qualifying variant
+// could have D >= 0, where the iteration does not apply.
+__device__ ChainResult site_tm_chain(const SiteVariants& V, const TmRun& R, double* out) {
+  constexpr int M = kMaxK + 1;
+  const int L = V.L, K = V.k < 0 ? 0 : V.k;
+  uint8_t back[32][4][M], v[32];
   // constant part of D: salt (method 5) and R ln(C); methods 1-4 shift Tm by a constant
   const double S0 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
   const double H0 = kInitH + kOneGCH, Sc = kInitS + kOneGCS;  // all-A/T and one-G/C terms are equal here
-  // Viterbi: maximise sum of (lam * ds - 1000 * dh) (lam = 0 with sign -1 on dh .. see callers)
+  auto inc = [&](int j, int a) { return (V.k >= 0 && V.ch[j][a] != V.s[j]) ? 1 : 0; };
+  // Viterbi: maximise the sum of (wl * ds - wn * 1000 * dh) over the qualifying variants; the arg-max is
+  // left in v
   auto viterbi = [&](double wl, double wn, double* best_score) -> bool {
-    double cur[4], nxt[4];
-    for (int a = 0; a < nch[0]; ++a) {
+    double cur[4][M], nxt[4][M];
+    for (int a = 0; a < 4; ++a)
+      for (int m = 0; m <= K; ++m) cur[a][m] = -INFINITY;
+    for (int a = 0; a < V.nch[0]; ++a) {
       double dh, ds;
-      end_sums(0, L, ch[0][a], &dh, &ds);
-      cur[a] = wl * ds - wn * 1000.0 * dh;
+      end_sums(0, L, V.ch[0][a], &dh, &ds);
+      cur[a][inc(0, a)] = wl * ds - wn * 1000.0 * dh;
     }
     for (int i = 0; i + 1 < L; ++i) {
-      for (int b = 0; b < nch[i + 1]; ++b) {
-        double best = -INFINITY;
-        int arg = -1;
-        for (int a = 0; a < nch[i]; ++a) {
-          if (cur[a] == -INFINITY) continue;
+      for (int b = 0; b < V.nch[i + 1]; ++b) {
+        const int ib = inc(i + 1, b);
+        double tail = 0.0;
+        if (i + 1 == L - 1) {
           double dh, ds;
-          if (!edge_sums(i, L, ch[i][a], ch[i + 1][b], c, &dh, &ds)) continue;
-          const double sc = cur[a] + (wl * ds - wn * 1000.0 * dh);
-          if (sc > best) best = sc, arg = a;
+          end_sums(L - 1, L, V.ch[i + 1][b], &dh, &ds);
+          tail = wl * ds - wn * 1000.0 * dh;
         }
-        if (i + 1 == L - 1 && arg >= 0) {
+        for (int m = 0; m <= K; ++m) nxt[b][m] = -INFINITY, back[i + 1][b][m] = 0;
+        for (int a = 0; a < V.nch[i]; ++a) {
           double dh, ds;
-          end_sums(L - 1, L, ch[i + 1][b], &dh, &ds);
-          best += wl * ds - wn * 1000.0 * dh;
+          if (!edge_sums(i, L, V.ch[i][a], V.ch[i + 1][b], V.c, &dh, &ds)) continue;
+          const double w = wl * ds - wn * 1000.0 * dh + tail;
+          for (int m = 0; m + ib <= K; ++m) {
+            if (cur[a][m] == -INFINITY) continue;
+            const double sc = cur[a][m] + w;
+            if (sc > nxt[b][m + ib]) nxt[b][m + ib] = sc, back[i + 1][b][m + ib] = (uint8_t)a;
+          }
         }
-        nxt[b] = best;
-        back[i + 1][b] = (uint8_t)(arg < 0 ? 0 : arg);
       }
-      for (int b = 0; b < nch[i + 1]; ++b) cur[b] = nxt[b];
+      for (int b = 0; b < V.nch[i + 1]; ++b)
+        for (int m = 0; m <= K; ++m) cur[b][m] = nxt[b][m];
     }
     double best = -INFINITY;
-    int arg = -1;
-    for (int b = 0; b < nch[L - 1]; ++b)
-      if (cur[b] > best) best = cur[b], arg = b;
+    int arg = -1, am = 0;
+    for (int b = 0; b < V.nch[L - 1]; ++b)
+      for (int m = 0; m <= K; ++m)
+        if (cur[b][m] > best) best = cur[b][m], arg = b, am = m;
     if (arg < 0) return false;
     for (int j = L - 1; j >= 0; --j) {
-      v[j] = ch[j][arg];
-      if (j) arg = back[j][arg];
+      v[j] = V.ch[j][arg];
+      if (j) {
+        const int pa = back[j][arg][am];
+        am -= inc(j, arg);
+        arg = pa;
+      }
     }
     *best_score = best;
     return true;
   };
-  // D must stay negative for every variant: maximise dS (wl = 1, wn = 0)
+  // D must stay negative for every qualifying variant: maximise dS (wl = 1, wn = 0)
   double maxS;
-  if (!viterbi(1.0, 0.0, &maxS)) return false;
-  if (maxS + Sc + S0 >= 0.0) return false;
+  if (!viterbi(1.0, 0.0, &maxS)) return kChainUndefined;
+  if (maxS + Sc + S0 >= 0.0) return kChainUnbounded;
   // start from the variant that maximises dS - dH / 300 (any defined variant works)
   double sc;
-  if (!viterbi(300.0, 1.0, &sc)) return false;
+  if (!viterbi(300.0, 1.0, &sc)) return kChainUndefined;
   double t;
-  if (!duplex_tm(v, c, L, R, &t)) return false;
-  double lam = t + 273.15 - (R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0);
+  if (!duplex_tm(v, V.c, L, R, &t)) return kChainUndefined;
+  const double shift = R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0;
+  double lam = t + 273.15 - shift;
   double best_t = t;
   for (int it = 0; it < 64; ++it) {
     if (!viterbi(lam, 1.0, &sc)) break;
     // score + lam * (Sc + S0) - 1000 * H0 = lam * D(v) - N(v) for the maximising variant
     const double F = sc + lam * (Sc + S0) - 1000.0 * H0;
     if (F <= 1e-7) break;
-    if (!duplex_tm(v, c, L, R, &t)) break;
-    const double nl = t + 273.15 - (R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0);
+    if (!duplex_tm(v, V.c, L, R, &t)) break;
+    const double nl = t + 273.15 - shift;
     if (!(nl > lam)) break;
     lam = nl;
     best_t = t;
   }
   *out = best_t;
-  return true;
+  return kChainOk;
 }
 
-// maximum over the concrete variants of `sets` (IUPAC sets over codes) paired with site `s`
-__device__ double site_tm(const uint8_t* sets, const uint8_t* s, int L, const TmRun& R) {
-  {
-    uint64_t nv = 1;
-    for (int j = 0; j < L; ++j) nv *= (uint64_t)__popc(sets[j]);
-    if (nv > 64 && L >= 3 && R.saltcorr <= 5) {
-      double t;
-      return site_tm_chain(sets, s, L, R, &t) ? t : __longlong_as_double(0x7ff8000000000000ll);
-    }
+// Tm of a degenerate primer at a site (reading R14): the maximum over the primer's concrete variants
+// with at most k mismatches to the site and none in the last `clamp` positions; NaN when none of them
+// is defined.  Up to kEnumSmall qualifying variants are enumerated; more take the chain method (salt
+// methods 0-5), and where that does not apply they are enumerated up to kEnumLimit.  Beyond that the
+// site gets NaN and ST_TM_LIMIT is raised.
+__device__ double site_tm(const uint8_t* sets, const uint8_t* s, int L, int k, int clamp, const TmRun& R,
+                          uint32_t* status) {
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  SiteVariants V;
+  if (!site_variants(sets, s, L, k, clamp, &V)) return nan;
+  const uint64_t nv = count_variants(V, kEnumLimit);
+  double t;
+  if (nv > kEnumSmall && L >= 3 && R.saltcorr <= 5) {
+    const ChainResult r = site_tm_chain(V, R, &t);
+    if (r == kChainOk) return t;
+    if (r == kChainUndefined) return nan;
   }
-  uint8_t v[32], c[32], choice[32][4], nch[32], idx[32];
-  for (int j = 0; j < L; ++j) {
-    c[j] = s[j] ^ 2u;  // complement code
-    nch[j] = 0;
-    for (int code = 0; code < 4; ++code)
-      if ((sets[j] >> code) & 1) choice[j][nch[j]++] = (uint8_t)code;
-    idx[j] = 0;
+  if (nv > kEnumLimit) {
+    if (status) atomicOr(status, (uint32_t)ST_TM_LIMIT);
+    return nan;
   }
-  double best = -INFINITY;
-  bool any = false;
-  for (;;) {
-    for (int j = 0; j < L; ++j) v[j] = choice[j][idx[j]];
-    double t;
-    if (duplex_tm(v, c, L, R, &t)) {
-      any = true;
-      best = fmax(best, t);
-    }
-    int j = L - 1;
-    while (j >= 0) {
-      if (++idx[j] < nch[j]) break;
-      idx[j] = 0;
-      --j;
-    }
-    if (j < 0) break;
-  }
-  return any ? best : __longlong_as_double(0x7ff8000000000000ll);
+  return enum_max(V, R, &t) ? t : nan;
 }
 
 __device__ __forceinline__ uint8_t base_code(const uint2* planes, uint64_t group0, uint64_t x) {
@@ -430,7 +509,8 @@ __device__ __forceinline__ uint8_t base_code(const uint2* planes, uint64_t group
 
 __global__ void k_tm_hits(const ah_hit* __restrict__ hits, uint64_t n, const uint2* __restrict__ planes,
                           const uint64_t* __restrict__ rec_group, const uint8_t* __restrict__ plen,
-                          const uint8_t* __restrict__ psets, const TmRun R, double* __restrict__ out,
+                          const uint8_t* __restrict__ psets, const uint8_t* __restrict__ pk, int clamp,
+                          const TmRun R, double* __restrict__ out, uint32_t* status,
                           const uint64_t* __restrict__ d_n = nullptr) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || (d_n && i >= *d_n)) return;
@@ -445,7 +525,7 @@ __global__ void k_tm_hits(const ah_hit* __restrict__ hits, uint64_t n, const uin
                           : (uint8_t)(base_code(planes, g0, (uint64_t)h.pos + L - 1 - j) ^ 2u);
     sets[j] = psets[(pair * 2 + primer) * 32 + j];
   }
-  out[i] = site_tm(sets, site, L, R);
+  out[i] = R.variants ? site_tm(sets, site, L, pk[pair], clamp, R, status) : site_tm(sets, site, L, L, 0, R, status);
 }
 
 __global__ void k_tm_amps(ah_amplicon* __restrict__ a, uint64_t n, const double* __restrict__ hit_tm, int filter,
@@ -488,26 +568,34 @@ __global__ void k_tm_duplexes(const uint8_t* __restrict__ v, const uint8_t* __re
 }
 
 __global__ void k_tm_sites(const uint8_t* __restrict__ sets, const uint8_t* __restrict__ site,
-                           const uint32_t* __restrict__ len, uint32_t n, const TmRun R, double* __restrict__ out) {
+                           const uint32_t* __restrict__ len, const uint8_t* __restrict__ kc, uint32_t n,
+                           const TmRun R, double* __restrict__ out, uint32_t* status) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  out[i] = site_tm(sets + 32 * (uint64_t)i, site + 32 * (uint64_t)i, (int)len[i], R);
+  out[i] = site_tm(sets + 32 * (uint64_t)i, site + 32 * (uint64_t)i, (int)len[i], kc[2 * i], kc[2 * i + 1], R,
+                   status);
 }
 
 }  // namespace
 
-ah_status tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const char* const* sites,
-                   const ah_tm_params* params, double* out) {
+ah_status tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const char* const* sites, const uint8_t* k,
+                   const uint8_t* clamp, const ah_tm_params* params, double* out) {
   ah_status st;
   if ((st = load_tables(ctx))) return st;
   TmRun R;
   if ((st = make_run(ctx, params, &R))) return st;
   if (n == 0) return AH_OK;
-  std::vector<uint8_t> sets(32 * (size_t)n, 0), sv(32 * (size_t)n, 0);
+  std::vector<uint8_t> sets(32 * (size_t)n, 0), sv(32 * (size_t)n, 0), kc(2 * (size_t)n);
   std::vector<uint32_t> len(n);
   for (uint32_t i = 0; i < n; ++i) {
     const size_t L = strlen(primers[i]);
     if (L < 2 || L > 32 || strlen(sites[i]) != L) return fail(ctx, AH_EINVAL, "site %u: lengths must match, 2..32", i);
+    const uint32_t ki = k ? k[i] : 255u, ci = clamp ? clamp[i] : 0u;
+    if (ki > (uint32_t)kMaxK && ki < L)
+      return fail(ctx, AH_EINVAL, "site %u: mismatch budget %u above %d and below the length", i, ki, kMaxK);
+    if (ci > L) return fail(ctx, AH_EINVAL, "site %u: clamp %u longer than the primer", i, ci);
+    kc[2 * (size_t)i] = (uint8_t)std::min<uint32_t>(ki, 255u);
+    kc[2 * (size_t)i + 1] = (uint8_t)ci;
     for (size_t j = 0; j < L; ++j) {
       const char x = (char)toupper((unsigned char)sites[i][j]);
       const uint8_t set = iupac_set(primers[i][j]);
@@ -517,25 +605,26 @@ ah_status tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const ch
     }
     len[i] = (uint32_t)L;
   }
-  uint8_t *ds, *dv;
+  uint8_t *ds, *dv, *dk;
   uint32_t* dl;
   double* dout;
   if ((st = dalloc(ctx, &ds, sets.size())) || (st = dalloc(ctx, &dv, sv.size())) || (st = dalloc(ctx, &dl, n)) ||
-      (st = dalloc(ctx, &dout, n)))
+      (st = dalloc(ctx, &dk, kc.size())) || (st = dalloc(ctx, &dout, n)))
     return st;
   AH_CUDA(ctx, cudaMemcpyAsync(ds, sets.data(), sets.size(), cudaMemcpyHostToDevice, ctx->stream));
   AH_CUDA(ctx, cudaMemcpyAsync(dv, sv.data(), sv.size(), cudaMemcpyHostToDevice, ctx->stream));
   AH_CUDA(ctx, cudaMemcpyAsync(dl, len.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
-  k_tm_sites<<<(n + 63) / 64, 64, 0, ctx->stream>>>(ds, dv, dl, n, R, dout);
+  AH_CUDA(ctx, cudaMemcpyAsync(dk, kc.data(), kc.size(), cudaMemcpyHostToDevice, ctx->stream));
+  k_tm_sites<<<(n + 63) / 64, 64, 0, ctx->stream>>>(ds, dv, dl, dk, n, R, dout, ctx->d_status);
   launched(ctx);
   AH_CUDA(ctx, cudaGetLastError());
   AH_CUDA(ctx, cudaMemcpyAsync(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   dfree(ctx, ds);
   dfree(ctx, dv);
   dfree(ctx, dl);
+  dfree(ctx, dk);
   dfree(ctx, dout);
-  return AH_OK;
+  return check_status(ctx);
 }
 
 ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, size_t run_size) {
@@ -546,11 +635,12 @@ ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, siz
 }
 
 void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit_cap, const uint64_t* d_nhits,
-               const uint2* planes, const uint64_t* rec_group, const uint8_t* plen, const uint8_t* psets, double* hit_tm,
+               const uint8_t* pk, int clamp, uint32_t* status, const uint2* planes, const uint64_t* rec_group, const uint8_t* plen, const uint8_t* psets, double* hit_tm,
                ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep) {
   const TmRun R = *(const TmRun*)run;
   k_tm_hits<<<(unsigned)std::max<uint64_t>(1, (hit_cap + 127) / 128), 128, 0, s>>>(hits, hit_cap, planes, rec_group,
-                                                                                  plen, psets, R, hit_tm, d_nhits);
+                                                                                  plen, psets, pk, clamp, R, hit_tm,
+                                                                                  status, d_nhits);
   k_tm_amps<<<(unsigned)std::max<uint64_t>(1, (amp_cap + 255) / 256), 256, 0, s>>>(amps, amp_cap, hit_tm, filter,
                                                                                   min_tm, keep, d_namps);
 }
@@ -571,7 +661,8 @@ ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const a
   if ((st = dalloc(ctx, &hit_tm, h->n))) return st;
   if (h->n)
     k_tm_hits<<<(unsigned)((h->n + 127) / 128), 128, 0, ctx->stream>>>(h->d, h->n, b->planes, b->rec_group, p->d_plen,
-                                                                      p->d_psets, R, hit_tm);
+                                                                      p->d_psets, p->d_pk, p->clamp, R, hit_tm,
+                                                                      ctx->d_status);
   if (h->n) launched(ctx);
   if (params->filter && (st = dalloc(ctx, &keep, a->n))) return st;
   if (a->n)
@@ -598,7 +689,7 @@ ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const a
   }
   dfree(ctx, hit_tm);
   dfree(ctx, keep);
-  return AH_OK;
+  return check_status(ctx);
 }
 
 ah_status tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const char* const* cseqs,

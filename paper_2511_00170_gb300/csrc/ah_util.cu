@@ -37,6 +37,10 @@ ah_status check_status(ah_ctx* ctx) {
     AH_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), ctx->stream));
     if (s & ST_SCAN_MISMATCH)
       return fail(ctx, AH_EINTERNAL, "device self-check: bit-sliced matcher disagreed with the exact re-check");
+    if (s & ST_TM_LIMIT)
+      return fail(ctx, AH_ELIMIT,
+                  "degenerate site Tm: more qualifying primer variants than the enumeration bound, and the chain "
+                  "method does not apply (salt method 6, or a variant whose entropy sum could reach zero)");
     return fail(ctx, AH_EINTERNAL, "device self-check failed (status 0x%x)", s);
   }
   return AH_OK;

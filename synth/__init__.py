@@ -158,6 +158,7 @@ class TmParams:
     dnac2: float = 25.0   # nM
     saltcorr: int = 5
     min_tm: Optional[float] = None   # None: annotate only, no filtering
+    variants: int = 0     # degenerate Tm over 0: every concrete variant, 1: those matching the site
 
 
 @dataclass

@@ -215,47 +215,124 @@ def test_pack_layout(engine):
 
 def _degenerate_sites(seed, n, codes_lo, codes_hi):
     st = synth.Stream(synth.make_key(seed, 77, 1))
-    prims, sites = [], []
+    prims, sites, ks, clamps = [], [], [], []
     for _ in range(n):
         L = st.randint(12, 26)
         p = synth.random_primer(st, L, st.randint(codes_lo, codes_hi), 0, "RYSWKMBDHVNNN")
         v = synth.concrete_variant(st, p)
         sites.append(synth.substitute(st, v, st.randint(0, 4)))
         prims.append(p)
-    return prims, sites
+        ks.append(st.randint(0, 5))
+        clamps.append(st.randint(0, 4))
+    return prims, sites, ks, clamps
+
+
+def _check_sites(got, prims, sites, ks, clamps, prm):
+    for i, (p, s, g) in enumerate(zip(prims, sites, got)):
+        k = None if ks is None else ks[i]
+        c = 0 if clamps is None else clamps[i]
+        r = oracle.tm_site(p, s, prm, k=k, clamp=c)
+        if r is None:
+            assert math.isnan(g), (p, s, k, c, g)
+        else:
+            assert abs(g - r) <= compare.TM_TOL, (p, s, k, c, g, r)
 
 
 @pytest.mark.parametrize("method,na", [(5, 50.0), (0, 50.0), (1, 20.0), (3, 50.0), (4, 10.0), (2, 200.0)])
 def test_degenerate_site_tm_exact_max(engine, method, na):
-    """Sites of primers with 7-9 degenerate codes (128 to 262,144 variants) take the chain method on
-    the GPU; the oracle enumerates every variant."""
+    """Sites of primers with 7-9 degenerate codes (128 to 262,144 variants, many of them within the
+    mismatch budget) take the chain method with mismatch-counting states on the GPU; the oracle
+    enumerates every variant and keeps the qualifying ones."""
     from paper_2511_00170_gb300 import ah
 
-    prims, sites = _degenerate_sites(method, 30, 7, 9)
+    prims, sites, ks, clamps = _degenerate_sites(method, 30, 7, 9)
+    got = ah.ah_tm_sites(engine.ctx, prims, sites, ah.tm_params(Na=na, saltcorr=method), k=ks, clamp=clamps)
+    _check_sites(got, prims, sites, ks, clamps, synth.TmParams(Na=na, saltcorr=method))
+
+
+@pytest.mark.parametrize("method,na", [(4, 10.0), (5, 50.0)])
+def test_degenerate_site_tm_no_mismatch_limit(engine, method, na):
+    """Without a mismatch limit every variant counts; where some variant's entropy sum could reach
+    zero the chain method does not apply and the GPU enumerates (at most 2^20 variants)."""
+    from paper_2511_00170_gb300 import ah
+
+    prims, sites, _, _ = _degenerate_sites(100 + method, 12, 7, 9)
     got = ah.ah_tm_sites(engine.ctx, prims, sites, ah.tm_params(Na=na, saltcorr=method))
-    for p, s, g in zip(prims, sites, got):
-        r = oracle.tm_site(p, s, synth.TmParams(Na=na, saltcorr=method))
-        if r is None:
-            assert math.isnan(g), (p, s)
-        else:
-            assert abs(g - r) <= compare.TM_TOL, (p, s, g, r)
+    _check_sites(got, prims, sites, None, None, synth.TmParams(Na=na, saltcorr=method))
 
 
 def test_degenerate_site_tm_small_sets_and_method6(engine):
-    """Up to 64 variants, and salt method 6 at any count, enumerate on the GPU too."""
+    """Up to 64 qualifying variants, and salt method 6 at any count, enumerate on the GPU too."""
     from paper_2511_00170_gb300 import ah
 
-    prims, sites = _degenerate_sites(11, 40, 0, 6)
+    prims, sites, ks, clamps = _degenerate_sites(11, 40, 0, 6)
     for method in (5, 6):
-        got = ah.ah_tm_sites(engine.ctx, prims, sites, ah.tm_params(saltcorr=method))
-        for p, s, g in zip(prims, sites, got):
-            r = oracle.tm_site(p, s, synth.TmParams(saltcorr=method))
-            assert (r is None and math.isnan(g)) or abs(g - r) <= compare.TM_TOL, (p, s, g, r)
+        got = ah.ah_tm_sites(engine.ctx, prims, sites, ah.tm_params(saltcorr=method), k=ks, clamp=clamps)
+        _check_sites(got, prims, sites, ks, clamps, synth.TmParams(saltcorr=method))
 
 
-def test_dense_workload_small(engine):
-    """Tandem repeats and highly degenerate primers (dense sites, overflowing tiles, chain Tm)."""
+def test_degenerate_site_tm_work_bound(engine):
+    """More than 2^20 qualifying variants under salt method 6 (no chain method) is refused with
+    AH_ELIMIT, and the context stays usable."""
+    from paper_2511_00170_gb300 import ah
+
+    p, s = "N" * 11 + "ACGTTGCAA", "ACGTACGTACGTACGTTGCAA"[1:]
+    with pytest.raises(ah.AhError) as e:
+        ah.ah_tm_sites(engine.ctx, [p], [s], ah.tm_params(saltcorr=6))
+    assert e.value.status == ah.AH_ELIMIT
+    # 4^11 variants with a budget of 3 mismatches: 4,984 qualify; the chain method handles them
+    got = ah.ah_tm_sites(engine.ctx, [p], [s], ah.tm_params(saltcorr=5), k=[3], clamp=[4])
+    r = oracle.tm_site(p, s, synth.TmParams(saltcorr=5), k=3, clamp=4)
+    assert abs(got[0] - r) <= compare.TM_TOL
+
+
+@pytest.mark.parametrize("variants", [0, 1])
+def test_dense_workload_small(engine, variants):
+    """Tandem repeats and highly degenerate primers (dense sites, overflowing tiles, chain Tm), with
+    the site Tm over every variant or over the site-matching ones."""
+    import dataclasses
+
     wl = synth.dense(n_genomes=10, median=2e5, sigma=0.3)
     wl.fwd = ["NNRYTGACCGTAGSAN"[:16]]
     wl.rev = ["NAGYCGATWKSGNACT"[:16]]
+    wl.tm = dataclasses.replace(wl.tm, variants=variants)
     _run_both(engine, wl)
+
+
+def test_pack_paths_agree(engine):
+    """Host records (pipelined copies, 16-byte aligned staging, vector pack kernel) and device records
+    at unaligned offsets (byte pack kernel) give the same planes; so does a streamed range pack."""
+    import torch
+
+    from paper_2511_00170_gb300 import ah
+
+    wl = synth.random_small(21, n_records=40, len_lo=0, len_hi=3000, n_frac=0.03, alphabet="ACGTacgtRYN", plant=0)
+
+    class _Dev:
+        def __init__(self, ptr, shape, typestr):
+            self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3}
+
+    def planes_of(batch):
+        v = ah.ah_batch_view_get(batch)
+        n = v["n_groups"]
+        p = torch.as_tensor(_Dev(v["planes"], (n, 2), "<u4"), device="cuda").cpu().numpy().copy()
+        i = torch.as_tensor(_Dev(v["invalid"], (n,), "<u4"), device="cuda").cpu().numpy().copy()
+        return p, i
+
+    host = engine.pack(wl.seq, wl.offsets)
+    d = torch.from_numpy(np.concatenate([np.zeros(3, np.uint8), wl.seq])).cuda()   # unaligned records
+    dev = engine.pack_device(d.data_ptr() + 3, wl.offsets.astype(np.uint64))
+    ah.ah_ctx_synchronize(engine.ctx)
+    streamed = ah.ah_batch_create(engine.ctx, wl.lengths().astype(np.uint64))
+    half = wl.n_records // 2
+    for a, b_ in ((0, half), (half, wl.n_records)):
+        o = wl.offsets[a:b_ + 1] - wl.offsets[a]
+        ah.ah_batch_pack_range(engine.ctx, streamed, a, d.data_ptr() + 3 + int(wl.offsets[a]), o.astype(np.uint64))
+    try:
+        ph, ih = planes_of(host)
+        for other in (dev, streamed):
+            po, io = planes_of(other)
+            assert np.array_equal(ph, po) and np.array_equal(ih, io)
+    finally:
+        for x in (host, dev, streamed):
+            ah.ah_batch_free(x)

@@ -135,19 +135,91 @@ def test_concentration_term():
     assert oracle.tm_duplex(seq, cseq, synth.TmParams(dnac1=250, dnac2=250)) > a
 
 
-@pytest.mark.parametrize("primer,site", [
-    ("ACGTRYACGTAGG", "ACGTACACGTAGG"),
-    ("NACGTAGCWAGT", "TACGTAGCAAGT"),
-    ("GGCATKMSACGTTA", "GGCATGCCACGTTA"),
-    ("BDHVACGGT", "CATGACGGT"),
-    ("ACGGTTNNAC", "ACGGTTAGAC"),
+def _qualifying(primer, site, k, clamp):
+    """Brute force: concrete variants of `primer` with at most k mismatches to `site` and none in the
+    last `clamp` positions."""
+    L = len(primer)
+    out = []
+    for v in brute.variants(primer):
+        diff = [i for i in range(L) if v[i] != site[i]]
+        if len(diff) <= k and all(i < L - clamp for i in diff):
+            out.append(v)
+    return out
+
+
+@pytest.mark.parametrize("primer,site,k,clamp", [
+    ("ACGTRYACGTAGG", "ACGTACACGTAGG", 13, 0),
+    ("NACGTAGCWAGT", "TACGTAGCAAGT", 12, 0),
+    ("GGCATKMSACGTTA", "GGCATGCCACGTTA", 2, 3),
+    ("BDHVACGGT", "CATGACGGT", 1, 2),
+    ("ACGGTTNNAC", "ACGGTTAGAC", 0, 0),
+    ("ACGGTTNNAC", "ACGGTTAGAC", 2, 4),
+    ("ANCCTRGTCVYHTBN", "ACCCTTGGCACGTTC", 3, 2),
 ])
-def test_degenerate_tm_is_max_over_variants(primer, site):
+def test_degenerate_tm_is_max_over_qualifying_variants(primer, site, k, clamp):
+    """Reading R14: the maximum of the duplex Tm over the variants that match the site within k
+    mismatches and the exact clamp, checked against a brute-force filter of every variant."""
     cseq = "".join(COMP[c] for c in site)
-    vals = [oracle.tm_duplex(v, cseq, synth.TmParams()) for v in brute.variants(primer)]
+    vals = [oracle.tm_duplex(v, cseq, synth.TmParams()) for v in _qualifying(primer, site, k, clamp)]
     vals = [v for v in vals if v is not None]
-    got = oracle.tm_site(primer, site, synth.TmParams())
+    got = oracle.tm_site(primer, site, synth.TmParams(), k=k, clamp=clamp)
     if not vals:
         assert got is None
     else:
         assert got is not None and abs(got - max(vals)) < 1e-12
+
+
+def test_site_tm_concrete_primer():
+    """A primer without degenerate codes has one variant: its own duplex Tm when the site is within k
+    mismatches and the clamp is exact, else undefined."""
+    primer = "AGCTTGACCGTAGGCA"
+    site = "AGCTTGACCATAGGCA"   # one mismatch, 6 positions from the 3' end
+    cseq = "".join(COMP[c] for c in site)
+    t = oracle.tm_duplex(primer, cseq, synth.TmParams())
+    assert t is not None
+    assert oracle.tm_site(primer, site, synth.TmParams(), k=1, clamp=6) == t
+    assert oracle.tm_site(primer, site, synth.TmParams(), k=0, clamp=0) is None
+    assert oracle.tm_site(primer, site, synth.TmParams(), k=1, clamp=7) is None
+
+
+def test_site_tm_excludes_far_variants():
+    """A variant that differs from the site at many positions can reach a larger Biopython value
+    (here the entropy sum comes near -R ln C); it does not count unless it matches the site."""
+    primer, site = "ANCCTRGTCVYHTBN", "ACCCTTGGCACGTTC"
+    prm = synth.TmParams(Na=10.0, saltcorr=4)
+    every = oracle.tm_site(primer, site, prm)
+    near = oracle.tm_site(primer, site, prm, k=3, clamp=2)
+    assert every is not None and near is not None
+    assert every > 200.0 and near < 100.0
+    cseq = "".join(COMP[c] for c in site)
+    vals = [oracle.tm_duplex(v, cseq, prm) for v in _qualifying(primer, site, 3, 2)]
+    assert abs(near - max(v for v in vals if v is not None)) < 1e-12
+
+
+
+
+@pytest.mark.parametrize("variants", [0, 1])
+def test_hit_tm_follows_the_variant_option(variants):
+    """Per-hit Tm: every variant by default, the site-matching ones (the pair's k, the clamp) with
+    variants = 1; checked hit by hit against the site-level function on the site's own bases."""
+    import dataclasses
+
+    wl = synth.random_small(5, n_records=20, len_lo=200, len_hi=800, n_pairs=2, plen_lo=8, plen_hi=12, n_deg=4,
+                            k_max=3, clamp=2, plant=3)
+    wl.tm = dataclasses.replace(wl.tm, variants=variants)
+    hits = oracle.scan(wl)
+    assert len(hits) > 5
+    tm, st = oracle.tm_hits(wl, hits)
+    for h, t, s in zip(hits, tm, st):
+        P = (wl.fwd if h["primer"] == 0 else wl.rev)[h["pair"]]
+        L = len(P)
+        g = wl.seq[wl.offsets[h["record"]]:wl.offsets[h["record"] + 1]].tobytes().decode().upper()
+        site = g[h["pos"]:h["pos"] + L]
+        if h["strand"] == 1:
+            site = "".join(COMP[c] for c in reversed(site))
+        k, c = (wl.k[h["pair"]], wl.clamp) if variants else (None, 0)
+        r = oracle.tm_site(P, site, wl.tm, k=k, clamp=c)
+        if r is None:
+            assert s == 1
+        else:
+            assert s == 0 and t == r
