@@ -244,14 +244,17 @@ def run_engine(args):
     del d_seq
     torch.cuda.empty_cache()
 
+    # the whole step as one autotuned, graph-captured plan (sized by one exact run of the step)
+    plan = eng.plan(batch, params, with_seqs=True, autotune=True, persistent=-1)
+    info = ah.ah_plan_info_get(plan)
+
     def one_step():
-        hits, amps = eng.step(batch, params, with_seqs=True, copy_out=False)
-        ah.ah_hits_free(hits)
-        ah.ah_amplicons_free(amps)
+        ah.ah_plan_launch(plan)
 
     for _ in range(max(3, args.warmup)):
         one_step()
     ah.ah_ctx_synchronize(eng.ctx)
+    ah.ah_plan_check(plan, eng.ctx)
 
     def barrier():
         if world > 1:
@@ -270,6 +273,7 @@ def run_engine(args):
         torch.cuda.synchronize()
     barrier()
     ah.ah_ctx_set_timing(eng.ctx, False)
+    ah.ah_plan_check(plan, eng.ctx)   # every replay fitted its buffers (raises on overflow)
     ms = e0.elapsed_time(e1) / args.steps
     stats = ah.ah_ctx_stats_get(eng.ctx)
     if world > 1:
@@ -284,37 +288,43 @@ def run_engine(args):
     roofline = scan_roofline(stats["scan_ops_per_group"], wl.fwd, wl.rev, wl.clamp, bases_per_launch, scan_ms)
     roofline["step_gbps_frac_of_alu_bound"] = value / world / (ALU_PEAK_TOPS * 1e3 / roofline["ops_per_base"])
 
-    # end to end through the C ABI from pinned host memory
+    # end to end through the C ABI from pinned host memory: every step packs the records from host
+    # ASCII into the plan's batch (the pack kernel reads page-locked memory over the host link),
+    # replays the plan and copies sites, amplicons and sequences back to host memory
     e2e = None
     if not args.no_e2e:
         pinned = torch.empty(wl.total_bp, dtype=torch.uint8, pin_memory=True)
         pinned.numpy()[:] = wl.seq
-        host = pinned.numpy()
+        offs = np.ascontiguousarray(wl.offsets, dtype=np.uint64)
         h2d = d2h = 0
         times = []
         for it in range(1 + args.e2e_steps):
             torch.cuda.synchronize()
             t = time.perf_counter()
-            b = eng.pack(host, wl.offsets, wl.genome_ids)
-            out = eng.step(b, params, with_seqs=True, copy_out=True)
-            ah.ah_batch_free(b)
-            ah.ah_ctx_synchronize(eng.ctx)
+            ah.ah_batch_pack_range(eng.ctx, batch, 0, pinned.data_ptr(), offs)
+            ah.ah_plan_launch(plan, eng.ctx)
+            out = eng.plan_output(plan, with_seqs=True)
             dt = time.perf_counter() - t
             if it > 0:
                 times.append(dt)
-            h2d = wl.total_bp + 16 * wl.n_records
+            h2d = wl.total_bp
             d2h = out.hits.nbytes + out.amps.nbytes + len(out.arena or b"") + out.field_off.nbytes
         e2e = {"value": wl.total_bp / statistics.median(times) / 1e9, "unit": "Gbp/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": len(times), "ms_per_step": statistics.median(times) * 1e3,
-               "path": "pinned host ASCII -> ah_pack_batch (H2D + pack) -> scan/pair/Tm/extract -> D2H results"}
+               "path": "pinned host ASCII -> ah_batch_pack_range (pack kernel reads host memory) -> ah_plan_launch "
+                       "-> ah_plan_results + copies of sites, amplicons and sequences to host"}
         del pinned
 
+    ah.ah_plan_free(plan)
     ah.ah_batch_free(batch)
     eng.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gbp/s", "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "u32+f64", "data": "synthetic", "config": describe(wl),
+                "vs_baseline": None, "dtype": "u32+f64", "data": "synthetic",
+                "config": dict(describe(wl), launch=f"one CUDA-graph replay of the whole step per step; autotuned scan "
+                               f"{info['threads']} threads x {info['groups_per_thread']} groups, shift mode "
+                               f"{info['shift_mode']}, persistent {info['persistent']}"),
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": stats["kernel_launches"],
                 "gpu_launches_per_step": stats["kernel_launches"] / args.steps, "roofline": roofline,
                 "cpu_baseline": base}

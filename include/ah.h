@@ -72,8 +72,9 @@ void* ah_ctx_stream(const ah_ctx* ctx);
  * and, when timing is enabled, the device time of the bit-sliced scan kernel measured with CUDA
  * events recorded on the context's stream around each of its launches. */
 typedef struct {
-  uint64_t kernel_launches; /* kernels launched by this context since the last reset */
-  uint64_t scan_launches;   /* launches of the scan kernel */
+  uint64_t kernel_launches; /* kernels launched by this context since the last reset (a plan replay
+                               counts every kernel node of its graph) */
+  uint64_t scan_launches;   /* launches of the scan kernel (timed ones only, for plan replays) */
   double scan_ms;           /* summed device time of those launches (timing enabled) */
   uint64_t scan_bases;      /* bases covered by those launches */
   uint64_t jit_compiles;    /* scan kernels compiled at run time (NVRTC) */
@@ -83,6 +84,8 @@ typedef struct {
 } ah_ctx_stats;
 ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out);
 ah_status ah_ctx_stats_reset(ah_ctx* ctx);
+/* Time every scan launch with CUDA events on the context's stream (scan_ms).  Synchronises the
+ * stream to collect the timings of plan replays still pending. */
 ah_status ah_ctx_set_timing(ah_ctx* ctx, int enable);
 
 /* Shape of the scan kernel used by ah_scan_primers on this context (a tuning knob; results do not
@@ -120,8 +123,10 @@ typedef struct {
 
 /* Pack host ASCII records.  seqs[i] points at lens[i] characters (no terminator needed);
  * genome_ids may be NULL (then record i has genome id i).  Characters other than ACGTacgt are
- * invalid bases.  Records are copied to the device in chunks of 64 Mi bases (16 MB packed) and
- * packed by a kernel while the next chunk is in flight.  Synchronises the stream before
+ * invalid bases.  Records in page-locked host memory (cudaHostAlloc, cudaHostRegister, pinned
+ * tensors) are read in place by the packing kernel over the host link, at any alignment.  Other
+ * records are copied to the device in chunks of 64 Mi bases (16 MB packed) on a second stream and
+ * packed while the next chunk is in flight.  Synchronises the stream before
  * returning (the host buffers may be reused afterwards).  AH_EINVAL: n_rec == 0, a record longer
  * than 2^32-1 bases, or a NULL pointer with a nonzero length. */
 ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, const uint64_t* lens,
@@ -136,9 +141,11 @@ ah_status ah_pack_batch_device(ah_ctx* ctx, uint32_t n_rec, const uint8_t* d_seq
 /* Streaming: lay out a batch for n_rec records of the given lengths (device memory allocated, nothing
  * packed), then pack consecutive record ranges into it with ah_batch_pack_range.  Synchronises. */
 ah_status ah_batch_create(ah_ctx* ctx, uint32_t n_rec, const uint64_t* lens, const uint32_t* genome_ids, ah_batch** out);
-/* Pack records [first, first + count) of b from device memory: d_seq holds them back to back and
- * h_offsets (host, count + 1 entries, starting at 0) delimits them; their lengths must match the
- * layout.  Synchronises (d_seq may be released afterwards). */
+/* Pack records [first, first + count) of b: d_seq holds them back to back in device memory or in
+ * page-locked host memory (read in place over the host link), at any alignment, and h_offsets
+ * (host, count + 1 entries, starting at 0) delimits them; their lengths must match the layout.
+ * Repacking a batch that a plan was created on refreshes the plan's input.  Synchronises (d_seq
+ * may be released afterwards). */
 ah_status ah_batch_pack_range(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t count, const uint8_t* d_seq,
                               const uint64_t* h_offsets);
 ah_status ah_batch_view_get(const ah_batch* b, ah_batch_view* out);
@@ -344,7 +351,10 @@ typedef struct {
 /* Build (autotune, size, capture).  The batch and primers must outlive the plan.  Synchronises. */
 ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_plan_params* params,
                          ah_plan** out);
-/* One graph launch of the whole step on the context's stream (asynchronous). */
+/* One graph launch of the whole step on the context's stream (asynchronous).  With timing on
+ * (ah_ctx_set_timing), the scan node of each replay is bracketed by its own pair of CUDA events;
+ * their elapsed times are added to the context's scan_ms when the stream is next synchronised by
+ * ah_ctx_synchronize or ah_ctx_set_timing. */
 ah_status ah_plan_launch(ah_plan* plan);
 /* Synchronise and check the last run: AH_EOVERFLOW when a capacity was exceeded (sizes in the info). */
 ah_status ah_plan_check(ah_plan* plan);

@@ -10,12 +10,11 @@
 using namespace ah;
 
 // ------------------------------------------------------------------------------------------
-// packing kernel
+// packing kernels
 //
-// One CTA per item (a piece of one record); each warp turns 32 groups (1024 bases) into plane
-// words at a time: for group i of the block every lane loads one byte (32 consecutive bytes per
-// warp load), three warp ballots assemble the lo, hi and invalid words, and lane i keeps group i's
-// words for one coalesced store at the end.
+// One CTA per item (a piece of one record, at most 2^20 bases); each warp turns 16 groups (512
+// bases) into plane words at a time from 16-byte loads.  The source may be device memory or
+// page-locked host memory, which the kernels then read over the host link.
 namespace {
 
 struct PackItem {
@@ -26,37 +25,6 @@ struct PackItem {
 };
 
 constexpr int kPackThreads = 256;
-
-__global__ void k_pack(const uint8_t* __restrict__ src, const PackItem* __restrict__ items, uint2* __restrict__ planes,
-                       uint32_t* __restrict__ invalid) {
-  const PackItem it = items[blockIdx.x];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (uint32_t blk = warp; blk * 32u < it.n_groups; blk += nwarps) {
-    uint32_t my_lo = 0, my_hi = 0, my_inv = 0;
-    const uint32_t g0 = blk * 32u;
-#pragma unroll 4
-    for (int i = 0; i < 32; ++i) {
-      const uint32_t x = (g0 + (uint32_t)i) * 32u + (uint32_t)lane;  // base index within the item
-      uint32_t c = 'N';
-      if (x < it.n_valid) c = __ldg(src + it.src_off + x);
-      const uint32_t u = c | 0x20u;
-      const bool valid = (u == 'a') | (u == 'c') | (u == 'g') | (u == 't');
-      const uint32_t lo = __ballot_sync(0xffffffffu, valid && ((c >> 1) & 1u));
-      const uint32_t hi = __ballot_sync(0xffffffffu, valid && ((c >> 2) & 1u));
-      const uint32_t inv = __ballot_sync(0xffffffffu, !valid);
-      if (lane == i) {
-        my_lo = lo;
-        my_hi = hi;
-        my_inv = inv;
-      }
-    }
-    const uint32_t g = g0 + (uint32_t)lane;
-    if (g < it.n_groups) {
-      planes[it.dst_group + g] = make_uint2(my_lo, my_hi);
-      invalid[it.dst_group + g] = my_inv;
-    }
-  }
-}
 
 // Items whose source is 16-byte aligned: every lane converts 16 bases fetched with one 16-byte load
 // (a warp covers 512 bases = 16 groups); the code bits of four bytes are gathered with one
@@ -72,15 +40,16 @@ __global__ void k_pack16(const uint8_t* __restrict__ src, const PackItem* __rest
                          uint32_t* __restrict__ invalid) {
   const PackItem it = items[blockIdx.x];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint8_t* base = (const uint8_t*)((uintptr_t)src + it.src_off);  // src may be null: offsets are then addresses
   for (uint32_t blk = warp; blk * 16u < it.n_groups; blk += nwarps) {
     const uint32_t x0 = blk * 512u + (uint32_t)lane * 16u;  // first base of this lane's 16
     uint32_t w[4] = {0x4E4E4E4Eu, 0x4E4E4E4Eu, 0x4E4E4E4Eu, 0x4E4E4E4Eu};  // 'N' past the record
     if (x0 + 16u <= it.n_valid) {
-      const uint4 v = __ldg((const uint4*)(src + it.src_off + x0));
+      const uint4 v = __ldg((const uint4*)(base + x0));
       w[0] = v.x, w[1] = v.y, w[2] = v.z, w[3] = v.w;
     } else if (x0 < it.n_valid) {
       for (uint32_t i = 0; i < it.n_valid - x0; ++i)
-        w[i >> 2] = (w[i >> 2] & ~(0xFFu << (8 * (i & 3)))) | ((uint32_t)__ldg(src + it.src_off + x0 + i) << (8 * (i & 3)));
+        w[i >> 2] = (w[i >> 2] & ~(0xFFu << (8 * (i & 3)))) | ((uint32_t)__ldg(base + x0 + i) << (8 * (i & 3)));
     }
     uint32_t lo = 0, hi = 0, inv = 0;
 #pragma unroll
@@ -101,6 +70,71 @@ __global__ void k_pack16(const uint8_t* __restrict__ src, const PackItem* __rest
     if (!(lane & 1) && g < it.n_groups) {
       planes[it.dst_group + g] = make_uint2(lo | (lo2 << 16), hi | (hi2 << 16));
       invalid[it.dst_group + g] = inv | (inv2 << 16);
+    }
+  }
+}
+
+// the 16 bases of one 16-byte word as bit masks: lo | hi << 16 (code bits) and inv (non-ACGT)
+__device__ __forceinline__ void word_masks(const uint4 v, uint32_t* lohi, uint32_t* inv_out) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  uint32_t lo = 0, hi = 0, inv = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t u = w[q] | 0x20202020u;  // lower case
+    const uint32_t ok = zero_bytes(u ^ 0x61616161u) | zero_bytes(u ^ 0x63636363u) | zero_bytes(u ^ 0x67676767u) |
+                        zero_bytes(u ^ 0x74747474u);
+    lo |= gather4((w[q] >> 1) & 0x01010101u) << (4 * q);
+    hi |= gather4((w[q] >> 2) & 0x01010101u) << (4 * q);
+    inv |= gather4(((~ok) >> 7) & 0x01010101u) << (4 * q);
+  }
+  *lohi = (lo & ~inv) | ((hi & ~inv) << 16);
+  *inv_out = inv;
+}
+
+// Items at any byte alignment.  Word c of an item is the aligned 16 bytes at A + 16c, where A is
+// the item's start rounded down to 16 and r = start - A; it holds item bases 16c - r .. 16c - r + 15.
+// Only words that hold at least one of the item's bases are read (an aligned 16-byte word never
+// crosses a page or an allocation boundary), bytes outside the item count as 'N', and group g is
+// bits r .. r + 31 of words 2g, 2g+1, 2g+2: lane 2j builds group j of the warp's 16 from its own
+// word and its two neighbours' (lane 31 also reads the word after the warp's 32).
+__global__ void k_pack16u(const uint8_t* __restrict__ src, const PackItem* __restrict__ items,
+                          uint2* __restrict__ planes, uint32_t* __restrict__ invalid) {
+  const PackItem it = items[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uintptr_t start = (uintptr_t)src + it.src_off;  // src may be null: offsets are then addresses
+  const uint4* A = (const uint4*)(start & ~(uintptr_t)15);
+  const uint32_t r = (uint32_t)(start & 15);
+  const uint64_t end = (uint64_t)it.n_valid + r;  // item bytes end here, counted from A
+  auto masks = [&](uint64_t c, uint32_t* lohi, uint32_t* inv) {
+    *lohi = 0;
+    *inv = 0xFFFFu;
+    if (16 * c >= end) return;
+    word_masks(__ldg(A + c), lohi, inv);
+    // keep bytes i with 0 <= 16c + i - r < n_valid
+    const int64_t lo_i = (int64_t)r - 16 * (int64_t)c, hi_i = (int64_t)end - 16 * (int64_t)c;
+    uint32_t keep = 0xFFFFu;
+    if (hi_i < 16) keep &= (1u << hi_i) - 1u;
+    if (lo_i > 0) keep &= ~((1u << lo_i) - 1u);
+    *lohi &= keep | (keep << 16);
+    *inv |= ~keep & 0xFFFFu;
+  };
+  for (uint32_t blk = warp; blk * 16u < it.n_groups; blk += nwarps) {
+    const uint64_t c = (uint64_t)blk * 32u + (uint64_t)lane;
+    uint32_t p, v, ph = 0, vh = 0xFFFFu;
+    masks(c, &p, &v);
+    if (lane == 31) masks(c + 1, &ph, &vh);
+    const uint32_t p1 = __shfl_down_sync(0xffffffffu, p, 1), v1 = __shfl_down_sync(0xffffffffu, v, 1);
+    uint32_t p2 = __shfl_down_sync(0xffffffffu, p, 2), v2 = __shfl_down_sync(0xffffffffu, v, 2);
+    const uint32_t hp = __shfl_down_sync(0xffffffffu, ph, 1), hv = __shfl_down_sync(0xffffffffu, vh, 1);
+    if (lane == 30) p2 = hp, v2 = hv;
+    const uint32_t g = blk * 16u + ((uint32_t)lane >> 1);
+    if (!(lane & 1) && g < it.n_groups) {
+      // 48-bit windows (words 2g, 2g+1, 2g+2) of each mask, shifted right by r
+      const uint32_t lo32 = (p & 0xFFFFu) | (p1 << 16), lo_hi = p2 & 0xFFFFu;
+      const uint32_t hi32 = (p >> 16) | (p1 & 0xFFFF0000u), hi_hi = p2 >> 16;
+      const uint32_t in32 = (v & 0xFFFFu) | (v1 << 16), in_hi = v2 & 0xFFFFu;
+      planes[it.dst_group + g] = make_uint2(__funnelshift_r(lo32, lo_hi, r), __funnelshift_r(hi32, hi_hi, r));
+      invalid[it.dst_group + g] = __funnelshift_r(in32, in_hi, r);
     }
   }
 }
@@ -191,7 +225,7 @@ void launch_pack(cudaStream_t s, const uint8_t* d_src, const PackItem* d_items, 
     if (vec)
       k_pack16<<<m, kPackThreads, 0, s>>>(d_src, d_items + i, b->planes, b->invalid);
     else
-      k_pack<<<m, kPackThreads, 0, s>>>(d_src, d_items + i, b->planes, b->invalid);
+      k_pack16u<<<m, kPackThreads, 0, s>>>(d_src, d_items + i, b->planes, b->invalid);
     launched(ctx);
   }
 }
@@ -288,6 +322,8 @@ void ah_ctx_destroy(ah_ctx* ctx) {
   ctx->jit.reset();
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& pr : ctx->ev_pending) ctx->ev_pool.push_back(pr.first), ctx->ev_pool.push_back(pr.second);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -299,7 +335,8 @@ const char* ah_last_error(const ah_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 ah_status ah_ctx_synchronize(ah_ctx* ctx) {
   if (!ctx) return AH_EINVAL;
   AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  return check_status(ctx);
+  ah_status st = drain_timings(ctx);
+  return st ? st : check_status(ctx);
 }
 
 void* ah_ctx_stream(const ah_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
@@ -318,6 +355,8 @@ ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out) {
 
 ah_status ah_ctx_stats_reset(ah_ctx* ctx) {
   if (!ctx) return AH_EINVAL;
+  ah_status st = drain_timings(ctx);  // timings of replays before the reset do not count after it
+  if (st) return st;
   ctx->n_launches = ctx->n_scan_launches = ctx->scan_bases = ctx->jit_compiles = 0;
   ctx->scan_ms = ctx->jit_ms = 0.0;
   return AH_OK;
@@ -340,8 +379,9 @@ ah_status ah_ctx_set_timing(ah_ctx* ctx, int enable) {
   cudaSetDevice(ctx->device);
   for (int i = 0; i < 2 && enable; ++i)
     if (!ctx->ev[i]) AH_CUDA(ctx, cudaEventCreate(&ctx->ev[i]));
+  ah_status st = drain_timings(ctx);
   ctx->timing = enable != 0;
-  return AH_OK;
+  return st;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -359,8 +399,38 @@ ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, co
     delete b;
     return st;
   }
-  // Plan: records (split on group boundaries) fill chunks of up to kChunkBases bases, each piece at a
-  // 16-byte aligned offset of its chunk's staging buffer.
+  // Records in page-locked host memory (or device memory) are read by the pack kernels in place:
+  // one pass over the host link, no staging copies.
+  bool in_place = true;
+  std::vector<uint64_t> dev_addr(n_rec, 0);
+  for (uint32_t r = 0; r < n_rec && in_place; ++r) {
+    if (!lens[r]) continue;
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, seqs[r]) != cudaSuccess) {
+      cudaGetLastError();
+      in_place = false;
+      break;
+    }
+    const bool reachable = (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeDevice ||
+                            pa.type == cudaMemoryTypeManaged) && pa.devicePointer != nullptr &&
+                           (pa.type == cudaMemoryTypeHost || pa.device == ctx->device);
+    if (!reachable) in_place = false;
+    else dev_addr[r] = (uint64_t)(uintptr_t)pa.devicePointer;
+  }
+  if (in_place) {
+    std::vector<PackItem> items;
+    for (uint32_t r = 0; r < n_rec; ++r) add_items(items, b, r, 0, lens[r], dev_addr[r]);
+    st = run_pack(ctx, nullptr, items, b);
+    if (st) {
+      free_batch_arrays(b);
+      delete b;
+      return st;
+    }
+    *out = b;
+    return AH_OK;
+  }
+  // Otherwise records (split on group boundaries) fill chunks of up to kChunkBases bases, each piece
+  // at a 16-byte aligned offset of its chunk's staging buffer, copied on a second stream.
   struct Piece {
     const char* src;
     uint64_t bytes, stage_off;

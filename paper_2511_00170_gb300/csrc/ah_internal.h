@@ -74,6 +74,10 @@ struct ah_ctx {
   int scan_ops_per_group = 0;  // of the last scan kernel launched
   bool timing = false;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  // scan-node timings of graph replays: event pairs recorded by the graph, read when the stream is
+  // next synchronised (ah::drain_timings)
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
 };
 
 struct ah_batch {
@@ -153,6 +157,10 @@ ah_status exclusive_scan_u64(ah_ctx* ctx, const uint64_t* d_in, uint64_t* d_out,
 ah_status read_u64(ah_ctx* ctx, const uint64_t* d, uint64_t* h);
 // read and clear the device status word (synchronises)
 ah_status check_status(ah_ctx* ctx);
+// accumulate the pending scan-node timings of graph replays into the context's counters (syncs)
+ah_status drain_timings(ah_ctx* ctx);
+// an event from the context's pool (created on first use)
+ah_status pool_event(ah_ctx* ctx, cudaEvent_t* ev);
 
 // count a kernel launch of this context (diagnostics)
 inline void launched(ah_ctx* ctx, uint64_t n = 1) { ctx->n_launches += n; }

@@ -49,6 +49,11 @@ struct ah_plan {
   unsigned char tm_run[64];
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // the scan node is bracketed by two event-record nodes; timed replays point them at fresh events
+  cudaEvent_t scan_ev[2] = {nullptr, nullptr};
+  cudaGraphNode_t scan_ev_node[2] = {nullptr, nullptr};
+  bool nodes_own = true;        // the event-record nodes point at scan_ev (not at pool events)
+  uint64_t kernel_nodes = 0;    // kernels one replay launches
   ah_plan_info info{};
 };
 
@@ -98,8 +103,10 @@ void enqueue_step(ah_plan* pl, cudaStream_t s) {
   cudaMemsetAsync(pl->tile_count, 0, pl->n_tiles * sizeof(uint32_t), s);
   cudaMemsetAsync(pl->tpc, 0, pl->n_cells * sizeof(uint32_t), s);
   cudaMemsetAsync(pl->ctr, 0, 4 * sizeof(uint32_t), s);
+  cudaEventRecord(pl->scan_ev[0], s);
   launch_scan_kernel(s, pl->kern, b, pl->slots, pl->tile_count, pl->slot_cap, pl->ctx->d_status,
                      (unsigned long long*)(pl->ctr + 2), pl->n_tiles, pl->grid);
+  cudaEventRecord(pl->scan_ev[1], s);
   launch_tile_max(s, pl->tile_count, pl->n_tiles, pl->ctr + 0);
   launch_tile_sort(s, pl->slots, pl->tile_count, pl->slot_cap, pl->n_tiles, p->n_pairs, pl->tpc);
   exclusive_scan_u32_s(s, pl->tpc, pl->tpc_off, pl->n_cells, pl->scratch);
@@ -143,6 +150,25 @@ ah_status capture(ah_plan* pl) {
   cudaError_t e = cudaStreamEndCapture(s, &g);
   if (e != cudaSuccess) return fail(c, AH_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
   pl->graph = g;
+  // count the kernels of one replay and find the two event-record nodes around the scan
+  size_t n = 0;
+  AH_CUDA(c, cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n) AH_CUDA(c, cudaGraphGetNodes(g, nodes.data(), &n));
+  pl->kernel_nodes = 0;
+  pl->scan_ev_node[0] = pl->scan_ev_node[1] = nullptr;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    AH_CUDA(c, cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel) pl->kernel_nodes++;
+    if (t == cudaGraphNodeTypeEventRecord) {
+      cudaEvent_t e = nullptr;
+      AH_CUDA(c, cudaGraphEventRecordNodeGetEvent(nd, &e));
+      for (int i = 0; i < 2; ++i)
+        if (e == pl->scan_ev[i]) pl->scan_ev_node[i] = nd;
+    }
+  }
+  if (!pl->scan_ev_node[0] || !pl->scan_ev_node[1]) return fail(c, AH_EINTERNAL, "plan: scan timing nodes not captured");
   AH_CUDA(c, cudaGraphInstantiate(&pl->exec, g, 0));
   return AH_OK;
 }
@@ -194,6 +220,8 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
   pl->prm = *prm;
   pl->cfg = ctx->scan_cfg;
   ah_status st = tm_prepare(ctx, &prm->tm, pl->tm_run, sizeof pl->tm_run);
+  for (int i = 0; i < 2 && !st; ++i)
+    if (cudaEventCreate(&pl->scan_ev[i]) != cudaSuccess) st = fail(ctx, AH_ECUDA, "ah_plan_create: event creation failed");
   const auto t0 = std::chrono::steady_clock::now();
   uint64_t n_hits = 0;
   if (!st && prm->autotune) {
@@ -280,8 +308,26 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
 ah_status ah_plan_launch(ah_plan* pl) {
   if (!pl) return AH_EINVAL;
   ah_ctx* c = pl->ctx;
+  if (c->timing) {
+    // a fresh event pair per replay, read back when the stream is next synchronised
+    cudaEvent_t e0, e1;
+    ah_status st;
+    if ((st = pool_event(c, &e0)) || (st = pool_event(c, &e1))) return st;
+    AH_CUDA(c, cudaGraphExecEventRecordNodeSetEvent(pl->exec, pl->scan_ev_node[0], e0));
+    AH_CUDA(c, cudaGraphExecEventRecordNodeSetEvent(pl->exec, pl->scan_ev_node[1], e1));
+    pl->nodes_own = false;
+    c->ev_pending.emplace_back(e0, e1);
+    c->n_scan_launches++;
+    c->scan_bases += pl->b->n_bases;
+  } else if (!pl->nodes_own) {
+    // pool events go back to other users once read: untimed replays record the plan's own pair
+    AH_CUDA(c, cudaGraphExecEventRecordNodeSetEvent(pl->exec, pl->scan_ev_node[0], pl->scan_ev[0]));
+    AH_CUDA(c, cudaGraphExecEventRecordNodeSetEvent(pl->exec, pl->scan_ev_node[1], pl->scan_ev[1]));
+    pl->nodes_own = true;
+  }
   AH_CUDA(c, cudaGraphLaunch(pl->exec, c->stream));
-  launched(c);
+  c->n_launches += pl->kernel_nodes;
+  c->scan_ops_per_group = pl->kern.alu_ops_per_group;
   return AH_OK;
 }
 
@@ -398,6 +444,8 @@ void ah_plan_free(ah_plan* pl) {
     cudaSetDevice(pl->ctx->device);
     free_buffers(pl);
     if (pl->h_out) cudaFreeHost(pl->h_out);
+    for (cudaEvent_t e : pl->scan_ev)
+      if (e) cudaEventDestroy(e);
   }
   delete pl;
 }

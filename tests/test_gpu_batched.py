@@ -106,3 +106,39 @@ def test_per_record_scan_matches(engine):
     finally:
         ah.ah_batch_free(batch)
     assert len(a) > 0 and a.tobytes() == b.tobytes()
+
+
+def test_plan_replays_are_timed_and_counted(engine):
+    """With timing on, each replay's scan node is timed by its own event pair and every kernel node
+    of the graph is counted; untimed replays afterwards leave the counters alone."""
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Params
+
+    wl = synth.batched(n_genomes=20, len_lo=5e3, len_hi=2e5, n_pairs=2)
+    p = Params.from_workload(wl)
+    batch = engine.pack(wl.seq, wl.offsets)
+    try:
+        plan = engine.plan(batch, p, with_seqs=True)
+        try:
+            ah.ah_plan_run(plan, engine.ctx)
+            ah.ah_ctx_stats_reset(engine.ctx)
+            ah.ah_ctx_set_timing(engine.ctx, True)
+            for _ in range(4):
+                ah.ah_plan_launch(plan, engine.ctx)
+            ah.ah_ctx_set_timing(engine.ctx, False)
+            st = ah.ah_ctx_stats_get(engine.ctx)
+            assert st["scan_launches"] == 4 and st["scan_bases"] == 4 * int(wl.total_bp)
+            assert st["scan_ms"] > 0
+            per_replay = st["kernel_launches"] // 4
+            assert st["kernel_launches"] == 4 * per_replay and per_replay >= 10
+            for _ in range(2):
+                ah.ah_plan_launch(plan, engine.ctx)
+            ah.ah_ctx_synchronize(engine.ctx)
+            st2 = ah.ah_ctx_stats_get(engine.ctx)
+            assert st2["scan_launches"] == 4 and st2["scan_ms"] == st["scan_ms"]
+            assert st2["kernel_launches"] == 6 * per_replay
+            ah.ah_plan_check(plan, engine.ctx)
+        finally:
+            ah.ah_plan_free(plan)
+    finally:
+        ah.ah_batch_free(batch)

@@ -299,14 +299,26 @@ def test_dense_workload_small(engine, variants):
     _run_both(engine, wl)
 
 
-def test_pack_paths_agree(engine):
-    """Host records (pipelined copies, 16-byte aligned staging, vector pack kernel) and device records
-    at unaligned offsets (byte pack kernel) give the same planes; so does a streamed range pack."""
+@pytest.mark.parametrize("big", [False, True])
+def test_pack_paths_agree(engine, big):
+    """Every packing path gives the same planes: host records from pageable memory (pipelined copies
+    into 16-byte aligned staging, aligned vector kernel), host records in page-locked memory read in
+    place at odd offsets, device records at odd offsets, and streamed range packs from device and
+    from page-locked host memory.  The large case has records longer than one 2^20-base item."""
     import torch
 
     from paper_2511_00170_gb300 import ah
 
-    wl = synth.random_small(21, n_records=40, len_lo=0, len_hi=3000, n_frac=0.03, alphabet="ACGTacgtRYN", plant=0)
+    if big:
+        wl = synth.plain_small(n_genomes=5, len_lo=1_100_000, len_hi=2_600_000)
+    else:
+        wl = synth.random_small(21, n_records=40, len_lo=0, len_hi=3000, n_frac=0.03, alphabet="ACGTacgtRYN", plant=0)
+        # lengths around the 16-byte word and the 32-base group
+        extra = [b"", b"A", b"ACGTACGTACGTACG", b"ACGTACGTACGTACGT", b"NACGTACGTACGTACGT", b"acgt" * 8 + b"N",
+                 b"ACGT" * 16 + b"TT"]
+        wl.seq = np.concatenate([wl.seq] + [np.frombuffer(x, np.uint8) for x in extra])
+        wl.offsets = np.concatenate([wl.offsets, wl.offsets[-1] + np.cumsum([len(x) for x in extra])]).astype(np.int64)
+        wl.genome_ids = np.arange(len(wl.offsets) - 1, dtype=np.uint32)
 
     class _Dev:
         def __init__(self, ptr, shape, typestr):
@@ -319,20 +331,27 @@ def test_pack_paths_agree(engine):
         i = torch.as_tensor(_Dev(v["invalid"], (n,), "<u4"), device="cuda").cpu().numpy().copy()
         return p, i
 
+    n_rec = len(wl.offsets) - 1
+    lengths = np.diff(wl.offsets).astype(np.uint64)
     host = engine.pack(wl.seq, wl.offsets)
+    pinned = torch.empty(len(wl.seq) + 5, dtype=torch.uint8, pin_memory=True)
+    pinned.numpy()[5:] = wl.seq
+    in_place = engine.pack(pinned.numpy()[5:], wl.offsets)   # odd offsets in page-locked memory
     d = torch.from_numpy(np.concatenate([np.zeros(3, np.uint8), wl.seq])).cuda()   # unaligned records
     dev = engine.pack_device(d.data_ptr() + 3, wl.offsets.astype(np.uint64))
     ah.ah_ctx_synchronize(engine.ctx)
-    streamed = ah.ah_batch_create(engine.ctx, wl.lengths().astype(np.uint64))
-    half = wl.n_records // 2
-    for a, b_ in ((0, half), (half, wl.n_records)):
-        o = wl.offsets[a:b_ + 1] - wl.offsets[a]
-        ah.ah_batch_pack_range(engine.ctx, streamed, a, d.data_ptr() + 3 + int(wl.offsets[a]), o.astype(np.uint64))
+    streamed = ah.ah_batch_create(engine.ctx, lengths)
+    streamed_host = ah.ah_batch_create(engine.ctx, lengths)
+    half = n_rec // 2
+    for a, b_ in ((0, half), (half, n_rec)):
+        o = (wl.offsets[a:b_ + 1] - wl.offsets[a]).astype(np.uint64)
+        ah.ah_batch_pack_range(engine.ctx, streamed, a, d.data_ptr() + 3 + int(wl.offsets[a]), o)
+        ah.ah_batch_pack_range(engine.ctx, streamed_host, a, pinned.data_ptr() + 5 + int(wl.offsets[a]), o)
     try:
         ph, ih = planes_of(host)
-        for other in (dev, streamed):
+        for other in (in_place, dev, streamed, streamed_host):
             po, io = planes_of(other)
             assert np.array_equal(ph, po) and np.array_equal(ih, io)
     finally:
-        for x in (host, dev, streamed):
+        for x in (host, in_place, dev, streamed, streamed_host):
             ah.ah_batch_free(x)
