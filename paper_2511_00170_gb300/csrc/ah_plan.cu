@@ -103,10 +103,11 @@ void enqueue_step(ah_plan* pl, cudaStream_t s) {
   cudaMemsetAsync(pl->tile_count, 0, pl->n_tiles * sizeof(uint32_t), s);
   cudaMemsetAsync(pl->tpc, 0, pl->n_cells * sizeof(uint32_t), s);
   cudaMemsetAsync(pl->ctr, 0, 4 * sizeof(uint32_t), s);
-  cudaEventRecord(pl->scan_ev[0], s);
+  // external records become event-record nodes of the captured graph
+  cudaEventRecordWithFlags(pl->scan_ev[0], s, cudaEventRecordExternal);
   launch_scan_kernel(s, pl->kern, b, pl->slots, pl->tile_count, pl->slot_cap, pl->ctx->d_status,
                      (unsigned long long*)(pl->ctr + 2), pl->n_tiles, pl->grid);
-  cudaEventRecord(pl->scan_ev[1], s);
+  cudaEventRecordWithFlags(pl->scan_ev[1], s, cudaEventRecordExternal);
   launch_tile_max(s, pl->tile_count, pl->n_tiles, pl->ctr + 0);
   launch_tile_sort(s, pl->slots, pl->tile_count, pl->slot_cap, pl->n_tiles, p->n_pairs, pl->tpc);
   exclusive_scan_u32_s(s, pl->tpc, pl->tpc_off, pl->n_cells, pl->scratch);
