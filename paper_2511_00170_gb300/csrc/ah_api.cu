@@ -322,8 +322,6 @@ void ah_ctx_destroy(ah_ctx* ctx) {
   ctx->jit.reset();
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
-  for (auto& pr : ctx->ev_pending) ctx->ev_pool.push_back(pr.first), ctx->ev_pool.push_back(pr.second);
-  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -75,9 +75,9 @@ struct ah_ctx {
   bool timing = false;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   // scan-node timings of graph replays: event pairs recorded by the graph, read when the stream is
-  // next synchronised (ah::drain_timings)
-  std::vector<cudaEvent_t> ev_pool;
+  // next synchronised (ah::drain_timings), which also advances drain_gen
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+  uint64_t drain_gen = 0;
 };
 
 struct ah_batch {
@@ -159,8 +159,6 @@ ah_status read_u64(ah_ctx* ctx, const uint64_t* d, uint64_t* h);
 ah_status check_status(ah_ctx* ctx);
 // accumulate the pending scan-node timings of graph replays into the context's counters (syncs)
 ah_status drain_timings(ah_ctx* ctx);
-// an event from the context's pool (created on first use)
-ah_status pool_event(ah_ctx* ctx, cudaEvent_t* ev);
 
 // count a kernel launch of this context (diagnostics)
 inline void launched(ah_ctx* ctx, uint64_t n = 1) { ctx->n_launches += n; }

@@ -49,10 +49,16 @@ struct ah_plan {
   unsigned char tm_run[64];
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  // the scan node is bracketed by two event-record nodes; timed replays point them at fresh events
+  // The scan node is bracketed by two event-record nodes.  Timed replays use a ring of executable
+  // copies of the graph whose nodes record their own event pairs, so no executable graph is
+  // updated between launches; a slot is reused only after its timing has been read.
+  static constexpr int kRing = 16;
   cudaEvent_t scan_ev[2] = {nullptr, nullptr};
   cudaGraphNode_t scan_ev_node[2] = {nullptr, nullptr};
-  bool nodes_own = true;        // the event-record nodes point at scan_ev (not at pool events)
+  cudaGraphExec_t ring[kRing] = {};
+  cudaEvent_t ring_ev[kRing][2] = {};
+  uint64_t ring_gen[kRing] = {};  // the context's drain generation when the slot was launched (+1)
+  int ring_next = 0;
   uint64_t kernel_nodes = 0;    // kernels one replay launches
   ah_plan_info info{};
 };
@@ -72,6 +78,8 @@ void free_buffers(ah_plan* pl) {
   pl->hit_tm = nullptr, pl->keep = nullptr, pl->koff = nullptr, pl->kept = nullptr, pl->elen = nullptr;
   pl->ebase = nullptr, pl->arena = nullptr, pl->field_off = nullptr, pl->ctr = nullptr;
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  for (auto& x : pl->ring)
+    if (x) cudaGraphExecDestroy(x), x = nullptr;
   if (pl->graph) cudaGraphDestroy(pl->graph);
   pl->exec = nullptr;
   pl->graph = nullptr;
@@ -144,6 +152,8 @@ ah_status capture(ah_plan* pl) {
   ah_ctx* c = pl->ctx;
   cudaStream_t s = c->stream;
   AH_CUDA(c, cudaStreamSynchronize(s));
+  ah_status dst = drain_timings(c);  // the ring's events are recorded afresh from here on
+  if (dst) return dst;
   prepare_tile_sort(pl->slot_cap, nullptr);
   AH_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   enqueue_step(pl, s);
@@ -171,6 +181,16 @@ ah_status capture(ah_plan* pl) {
   }
   if (!pl->scan_ev_node[0] || !pl->scan_ev_node[1]) return fail(c, AH_EINTERNAL, "plan: scan timing nodes not captured");
   AH_CUDA(c, cudaGraphInstantiate(&pl->exec, g, 0));
+  // the timing ring: the same graph with each slot's events in the two record nodes
+  for (int i = 0; i < ah_plan::kRing; ++i) {
+    for (int k = 0; k < 2; ++k) {
+      if (!pl->ring_ev[i][k]) AH_CUDA(c, cudaEventCreate(&pl->ring_ev[i][k]));
+      AH_CUDA(c, cudaGraphEventRecordNodeSetEvent(pl->scan_ev_node[k], pl->ring_ev[i][k]));
+    }
+    AH_CUDA(c, cudaGraphInstantiate(&pl->ring[i], g, 0));
+    pl->ring_gen[i] = 0;
+  }
+  for (int k = 0; k < 2; ++k) AH_CUDA(c, cudaGraphEventRecordNodeSetEvent(pl->scan_ev_node[k], pl->scan_ev[k]));
   return AH_OK;
 }
 
@@ -309,24 +329,22 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
 ah_status ah_plan_launch(ah_plan* pl) {
   if (!pl) return AH_EINVAL;
   ah_ctx* c = pl->ctx;
+  cudaGraphExec_t x = pl->exec;
   if (c->timing) {
-    // a fresh event pair per replay, read back when the stream is next synchronised
-    cudaEvent_t e0, e1;
-    ah_status st;
-    if ((st = pool_event(c, &e0)) || (st = pool_event(c, &e1))) return st;
-    AH_CUDA(c, cudaGraphExecEventRecordNodeSetEvent(pl->exec, pl->scan_ev_node[0], e0));
-    AH_CUDA(c, cudaGraphExecEventRecordNodeSetEvent(pl->exec, pl->scan_ev_node[1], e1));
-    pl->nodes_own = false;
-    c->ev_pending.emplace_back(e0, e1);
+    // the next ring slot; if its previous replay's timing is still unread, read it first
+    const int i = pl->ring_next;
+    pl->ring_next = (i + 1) % ah_plan::kRing;
+    if (pl->ring_gen[i] == c->drain_gen + 1) {
+      ah_status st = drain_timings(c);
+      if (st) return st;
+    }
+    x = pl->ring[i];
+    pl->ring_gen[i] = c->drain_gen + 1;
+    c->ev_pending.emplace_back(pl->ring_ev[i][0], pl->ring_ev[i][1]);
     c->n_scan_launches++;
     c->scan_bases += pl->b->n_bases;
-  } else if (!pl->nodes_own) {
-    // pool events go back to other users once read: untimed replays record the plan's own pair
-    AH_CUDA(c, cudaGraphExecEventRecordNodeSetEvent(pl->exec, pl->scan_ev_node[0], pl->scan_ev[0]));
-    AH_CUDA(c, cudaGraphExecEventRecordNodeSetEvent(pl->exec, pl->scan_ev_node[1], pl->scan_ev[1]));
-    pl->nodes_own = true;
   }
-  AH_CUDA(c, cudaGraphLaunch(pl->exec, c->stream));
+  AH_CUDA(c, cudaGraphLaunch(x, c->stream));
   c->n_launches += pl->kernel_nodes;
   c->scan_ops_per_group = pl->kern.alu_ops_per_group;
   return AH_OK;
@@ -443,10 +461,19 @@ void ah_plan_free(ah_plan* pl) {
   if (!pl) return;
   if (pl->ctx) {
     cudaSetDevice(pl->ctx->device);
+    // timings of this plan's replays that are still unread are read now
+    for (uint64_t g : pl->ring_gen)
+      if (g == pl->ctx->drain_gen + 1) {
+        drain_timings(pl->ctx);
+        break;
+      }
     free_buffers(pl);
     if (pl->h_out) cudaFreeHost(pl->h_out);
     for (cudaEvent_t e : pl->scan_ev)
       if (e) cudaEventDestroy(e);
+    for (auto& pr : pl->ring_ev)
+      for (cudaEvent_t e : pr)
+        if (e) cudaEventDestroy(e);
   }
   delete pl;
 }

@@ -46,16 +46,6 @@ ah_status check_status(ah_ctx* ctx) {
   return AH_OK;
 }
 
-ah_status pool_event(ah_ctx* ctx, cudaEvent_t* ev) {
-  if (!ctx->ev_pool.empty()) {
-    *ev = ctx->ev_pool.back();
-    ctx->ev_pool.pop_back();
-    return AH_OK;
-  }
-  AH_CUDA(ctx, cudaEventCreate(ev));
-  return AH_OK;
-}
-
 ah_status drain_timings(ah_ctx* ctx) {
   if (ctx->ev_pending.empty()) return AH_OK;
   AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -63,10 +53,9 @@ ah_status drain_timings(ah_ctx* ctx) {
     float ms = 0.f;
     AH_CUDA(ctx, cudaEventElapsedTime(&ms, pr.first, pr.second));
     ctx->scan_ms += ms;
-    ctx->ev_pool.push_back(pr.first);
-    ctx->ev_pool.push_back(pr.second);
   }
   ctx->ev_pending.clear();
+  ctx->drain_gen++;
   return AH_OK;
 }
 
