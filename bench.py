@@ -55,18 +55,33 @@ def alg_ops_per_base(fwd, rev, clamp):
     return total / 32.0
 
 
-def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms):
+# DRAM bytes per base of scan kernels captured with ncu (dram__bytes_read.sum + dram__bytes_write.sum
+# of the scan node of a plan replay on the full plain_scale workload, one 1-pass capture), keyed by
+# what identifies the kernel: LOP3/SHF per 32 positions of its circuit, threads, groups per thread,
+# shift mode, persistent.  A kernel not in this table reports traffic null.
+SCAN_TRAFFIC = {
+    (178, 256, 8, 0, 0): 1_892_938_240 / 7_536_412_189,
+}
+
+
+def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms, shape=None):
     """ALU roofline of one scan launch.  `achieved` counts the LOP3 and funnel-shift instructions of
     the generated circuit (the generator's exact count per 32 positions); the normative count
-    (3 lane-ops per non-clamp and 2 per clamp position per oriented pattern) is given beside it."""
+    (3 lane-ops per non-clamp and 2 per clamp position per oriented pattern) is given beside it.
+    `shape` = (threads, groups per thread, shift mode, persistent) of the launch."""
     ops = ops_per_group / 32.0
+    per_base = SCAN_TRAFFIC.get((ops_per_group,) + tuple(shape)) if shape is not None else None
+    traffic = per_base * bases if per_base is not None else None
     achieved = ops * bases / (ms * 1e-3) / 1e12
     norm = alg_ops_per_base(fwd, rev, clamp)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm = 0.25 * bases / (ms * 1e-3) / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tlane-op/s",
-            "frac": achieved / ALU_PEAK_TOPS, "traffic": None, "kernel": "ah_scan_jit (bit-sliced scan)",
+            "frac": achieved / ALU_PEAK_TOPS, "traffic": traffic,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel (same circuit and "
+                               "shape), scaled to the bases of one launch") if traffic is not None else None,
+            "kernel": "ah_scan_jit (bit-sliced scan)",
             "kernel_ms": ms, "ops_per_base": ops, "ops_source": "LOP3 + funnel shifts of the generated circuit",
             "peak_source": "derived: 152 SMs x 64 ALU lanes/clk x 2.07 GHz",
             "normative": {"ops_per_base": norm, "achieved": norm * bases / (ms * 1e-3) / 1e12,
@@ -285,7 +300,8 @@ def run_engine(args):
     # roofline of the dominant kernel (the bit-sliced scan), from its own CUDA-event times
     scan_ms = stats["scan_ms"] / max(1, stats["scan_launches"])
     bases_per_launch = stats["scan_bases"] / max(1, stats["scan_launches"])
-    roofline = scan_roofline(stats["scan_ops_per_group"], wl.fwd, wl.rev, wl.clamp, bases_per_launch, scan_ms)
+    roofline = scan_roofline(stats["scan_ops_per_group"], wl.fwd, wl.rev, wl.clamp, bases_per_launch, scan_ms,
+                             (info["threads"], info["groups_per_thread"], info["shift_mode"], info["persistent"]))
     roofline["step_gbps_frac_of_alu_bound"] = value / world / (ALU_PEAK_TOPS * 1e3 / roofline["ops_per_base"])
 
     # end to end through the C ABI from pinned host memory: every step packs the records from host
