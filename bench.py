@@ -153,7 +153,10 @@ def make_workload(args):
     if args.workload == "batched":
         return synth.batched(n_genomes=args.genomes or 2000)
     if args.workload == "dense":
-        return synth.dense(n_genomes=args.genomes or 500)
+        # 5,000 genomes (17.5 Gbp) drawn on the device, byte-identical to the host drawer
+        import synth.gpu
+
+        return synth.gpu.dense(n_genomes=args.genomes or 5000)
     raise SystemExit(f"unknown workload {args.workload}")
 
 
@@ -252,15 +255,18 @@ def run_engine(args):
     eng = Engine(local)
     stream = torch.cuda.ExternalStream(ah.ah_ctx_stream(eng.ctx))
     params = Params.from_workload(wl)
-    d_seq = torch.from_numpy(wl.seq).to(f"cuda:{local}")
+    on_device = hasattr(wl, "d_seq")   # drawn on the device
+    d_seq = wl.d_seq if on_device else torch.from_numpy(wl.seq).to(f"cuda:{local}")
     torch.cuda.synchronize()
     batch = eng.pack_device(d_seq.data_ptr(), wl.offsets.astype(np.uint64), wl.genome_ids)
     ah.ah_ctx_synchronize(eng.ctx)
-    del d_seq
-    torch.cuda.empty_cache()
+    if not on_device:
+        del d_seq
+        torch.cuda.empty_cache()
 
     # the whole step as one autotuned, graph-captured plan (sized by one exact run of the step)
-    plan = eng.plan(batch, params, with_seqs=True, autotune=True, persistent=-1)
+    with_seqs = getattr(wl, "extract", True)
+    plan = eng.plan(batch, params, with_seqs=with_seqs, autotune=True, persistent=-1)
     info = ah.ah_plan_info_get(plan)
 
     def one_step():
@@ -310,7 +316,10 @@ def run_engine(args):
     e2e = None
     if not args.no_e2e:
         pinned = torch.empty(wl.total_bp, dtype=torch.uint8, pin_memory=True)
-        pinned.numpy()[:] = wl.seq
+        if on_device:
+            pinned.copy_(wl.d_seq)
+        else:
+            pinned.numpy()[:] = wl.seq
         offs = np.ascontiguousarray(wl.offsets, dtype=np.uint64)
         h2d = d2h = 0
         times = []
@@ -319,12 +328,13 @@ def run_engine(args):
             t = time.perf_counter()
             ah.ah_batch_pack_range(eng.ctx, batch, 0, pinned.data_ptr(), offs)
             ah.ah_plan_launch(plan, eng.ctx)
-            out = eng.plan_output(plan, with_seqs=True)
+            out = eng.plan_output(plan, with_seqs=with_seqs)
             dt = time.perf_counter() - t
             if it > 0:
                 times.append(dt)
             h2d = wl.total_bp
-            d2h = out.hits.nbytes + out.amps.nbytes + len(out.arena or b"") + out.field_off.nbytes
+            d2h = out.hits.nbytes + out.amps.nbytes + len(out.arena or b"") + (
+                out.field_off.nbytes if out.field_off is not None else 0)
         e2e = {"value": wl.total_bp / statistics.median(times) / 1e9, "unit": "Gbp/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": len(times), "ms_per_step": statistics.median(times) * 1e3,
                "path": "pinned host ASCII -> ah_batch_pack_range (pack kernel reads host memory) -> ah_plan_launch "
@@ -334,6 +344,9 @@ def run_engine(args):
     ah.ah_plan_free(plan)
     ah.ah_batch_free(batch)
     eng.close()
+    if on_device:
+        wl.d_seq = None
+        torch.cuda.empty_cache()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gbp/s", "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -381,6 +394,8 @@ def run_batched(args):
     for _ in range(max(3, args.warmup)):
         ah.ah_plan_run(plan, eng.ctx)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ah.ah_ctx_stats_reset(eng.ctx)
+    ah.ah_ctx_set_timing(eng.ctx, True)   # each replay's scan node between its own CUDA events
     torch.cuda.synchronize()
     with ClockSampler(0) as clk:
         e0.record(stream)
@@ -388,20 +403,16 @@ def run_batched(args):
             ah.ah_plan_launch(plan, eng.ctx)
         e1.record(stream)
         torch.cuda.synchronize()
+    ah.ah_ctx_set_timing(eng.ctx, False)
     ms = e0.elapsed_time(e1) / args.steps
     ah.ah_plan_check(plan, eng.ctx)
     info = ah.ah_plan_info_get(plan)
-    # the same scan kernel timed alone (regular path, the plan's shape), for the roofline
-    ah.ah_ctx_set_scan_config(eng.ctx, info["threads"], info["groups_per_thread"], 256, info["shift_mode"])
-    pr = eng.primers(p)
-    ah.ah_ctx_stats_reset(eng.ctx)
-    ah.ah_ctx_set_timing(eng.ctx, True)
-    for _ in range(3):
-        h = ah.ah_scan_primers(eng.ctx, batch, pr)
-        ah.ah_hits_free(h)
     st = ah.ah_ctx_stats_get(eng.ctx)
+    launches_per_step = st["kernel_launches"] / args.steps
     scan_ms = st["scan_ms"] / st["scan_launches"]
-    roof = scan_roofline(st["scan_ops_per_group"], wl.fwd, wl.rev, wl.clamp, wl.total_bp, scan_ms)
+    roof = scan_roofline(st["scan_ops_per_group"], wl.fwd, wl.rev, wl.clamp, wl.total_bp, scan_ms,
+                         (info["threads"], info["groups_per_thread"], info["shift_mode"], info["persistent"]))
+    pr = eng.primers(p)
     # the plain form: one launch per genome per pair
     ah.ah_ctx_stats_reset(eng.ctx)
     torch.cuda.synchronize()
@@ -422,7 +433,7 @@ def run_batched(args):
             "plan": {k: info[k] for k in ("threads", "groups_per_thread", "shift_mode", "persistent", "grid",
                                           "n_hits", "n_amps", "arena_bytes")},
             "plan_create_s": plan_s, "autotune_ms": info["autotune_ms"], "generate_and_pack_s": gen_s,
-            "scan_kernel_ms": scan_ms,
+            "scan_kernel_ms": scan_ms, "gpu_launches_per_step": launches_per_step,
             "roofline": roof,
             "plain_per_record": {"launches": st2["scan_launches"], "seconds": per_record_s,
                                  "gbps": wl.total_bp / per_record_s / 1e9, "hits": n_pr,

@@ -191,6 +191,7 @@ class Workload:
     rb_len: int
     planted: List[Planted] = field(default_factory=list)
     seed: int = SEED
+    extract: bool = True            # the path writes amplicon sequences, barcodes and snippets
 
     @property
     def n_records(self) -> int:
@@ -220,7 +221,7 @@ class Workload:
             seq[offs[j]:offs[j + 1]] = self.record(i)
         return Workload(self.name + "-subset", seq, offs, self.genome_ids[recs].copy(), list(self.fwd),
                         list(self.rev), list(self.k), self.clamp, self.min_len, self.max_len,
-                        self.orient_mask, self.tm, self.trim, self.fb_len, self.rb_len, [], self.seed)
+                        self.orient_mask, self.tm, self.trim, self.fb_len, self.rb_len, [], self.seed, self.extract)
 
 
 # ----------------------------------------------------------------------------- primers
@@ -418,29 +419,54 @@ def batched(seed: int = SEED, n_genomes: int = 50_000, len_lo: float = 1e4, len_
 
 def dense(seed: int = SEED, n_genomes: int = 5000, median: float = 3.5e6, sigma: float = 0.4,
           out: Optional[np.ndarray] = None) -> Workload:
-    """Dense-hit stress: tandem repeats in 30 % of genomes, highly degenerate primers, window 50-5000."""
+    """Dense-hit stress: tandem repeats in 30 % of genomes, 18-nt primers with 9 degenerate codes and
+    k=4 (about 2 sites and 1 amplicon per kb of random sequence), window 50-5000, all orientations.
+    Amplicons are counted and annotated with Tm; sequences are not extracted."""
+    lengths, gcs = dense_layout(seed, n_genomes, median, sigma)
+    seq, offsets = _alloc(lengths, out)
+    _fill_genomes(seq, offsets, seed + 3, gcs, 0.005, 50)
+    lib = _get_lib()
+    for g, off, rlen, key, period in dense_repeats(seed, lengths):
+        a = int(offsets[g])
+        lib.synth_fill_tandem(seq.ctypes.data + a + off, rlen, key, period)
+    fwd, rev = dense_primers(seed)
+    return Workload("dense", seq, offsets, np.arange(n_genomes, dtype=np.uint32), fwd, rev, [DENSE_K], 3, 50, 5000,
+                    0b1111, TmParams(min_tm=None), False, 0, 0, [], seed, False)
+
+
+DENSE_K = 4   # mismatch budget of the dense workload: about 1 amplicon per kb of background
+
+
+def dense_layout(seed: int, n_genomes: int, median: float, sigma: float):
+    """Lengths and per-genome GC of the dense workload."""
     st_len = Stream(make_key(seed + 3, T_LEN, 0))
     lengths = [max(1000, int(round(median * math.exp(sigma * st_len.normal())))) for _ in range(n_genomes)]
     st_gc = Stream(make_key(seed + 3, T_GC, 0))
     gcs = [0.30 + 0.40 * st_gc.unit() for _ in range(n_genomes)]
-    seq, offsets = _alloc(lengths, out)
-    _fill_genomes(seq, offsets, seed + 3, gcs, 0.005, 50)
-    lib = _get_lib()
-    for g in range(n_genomes):
+    return lengths, gcs
+
+
+def dense_repeats(seed: int, lengths: Sequence[int]):
+    """The tandem repeats of the dense workload, in the order they are written: (genome, offset in the
+    genome, length, key, period).  30 % of genomes carry 1-5 repeats of period 2-12, 1-20 kbp."""
+    out = []
+    for g, n in enumerate(lengths):
         st = Stream(make_key(seed + 3, T_TANDEM, g))
         if st.unit() >= 0.30:
             continue
-        a, b = int(offsets[g]), int(offsets[g + 1])
         for r in range(st.randint(1, 5)):
             period = st.randint(2, 12)
-            rlen = min(b - a, st.randint(1000, 20000))
-            off = st.randint(0, max(0, b - a - rlen))
-            lib.synth_fill_tandem(seq.ctypes.data + a + off, rlen, make_key(seed + 3, T_TANDEM, g * 64 + r + 1), period)
+            rlen = min(n, st.randint(1000, 20000))
+            off = st.randint(0, max(0, n - rlen))
+            out.append((g, off, rlen, make_key(seed + 3, T_TANDEM, g * 64 + r + 1), period))
+    return out
+
+
+def dense_primers(seed: int):
     pst = Stream(make_key(seed + 3, T_PRIMER, 0))
     fwd = [random_primer(pst, 18, 9, 3, codes="RYMKSWNNN")]
     rev = [random_primer(pst, 18, 9, 3, codes="RYMKSWNNN")]
-    return Workload("dense", seq, offsets, np.arange(n_genomes, dtype=np.uint32), fwd, rev, [2], 3, 50, 5000,
-                    0b1111, TmParams(min_tm=None), False, 0, 0, [], seed)
+    return fwd, rev
 
 
 def random_small(seed: int, n_records: int, len_lo: int, len_hi: int, n_pairs: int = 1, plen_lo: int = 6,

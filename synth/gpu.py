@@ -18,7 +18,7 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 from . import (SEED, T_GC, T_LEN, T_NRUN, T_BASES, Planted, Stream, TmParams, Workload, _get_lib, batched_lengths_and_primers,
-               batched_templates, make_key)
+               DENSE_K, batched_templates, dense_layout, dense_primers, dense_repeats, make_key)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "_synth_gpu.cu")
@@ -74,6 +74,7 @@ class DeviceWorkload:
     rb_len: int
     planted: List[Planted] = field(default_factory=list)
     seed: int = SEED
+    extract: bool = True
 
     @property
     def n_records(self) -> int:
@@ -97,7 +98,9 @@ class DeviceWorkload:
             seq[offs[j]:offs[j + 1]] = self.d_seq[int(self.offsets[i]):int(self.offsets[i + 1])].cpu().numpy()
         return Workload(self.name + "-subset", seq, offs, self.genome_ids[recs].copy(), list(self.fwd), list(self.rev),
                         list(self.k), self.clamp, self.min_len, self.max_len, self.orient_mask, self.tm, self.trim,
-                        self.fb_len, self.rb_len, [], self.seed)
+                        self.fb_len, self.rb_len, [], self.seed, self.extract)
+
+    subset = host_subset
 
 
 def draw_genomes(seed_tag: int, lengths: Sequence[int], gcs: Sequence[float], n_frac: float = 0.005,
@@ -170,6 +173,46 @@ def batched(seed: int = SEED, n_genomes: int = 50_000, len_lo: float = 1e4, len_
     return DeviceWorkload("batched", d, offsets, np.arange(n_genomes, dtype=np.uint32), fwd, rev,
                           [i % 4 for i in range(n_pairs)], 3, 50, 2000, 0b1111, TmParams(min_tm=None), False, 0, 0,
                           planted, seed)
+
+
+def dense(seed: int = SEED, n_genomes: int = 5000, median: float = 3.5e6, sigma: float = 0.4) -> DeviceWorkload:
+    """synth.dense drawn on the device (byte-identical).  The tandem repeats are written on the host
+    in their order; repeats that overlap within a genome are merged into one template first, so the
+    device writes disjoint templates and later repeats win exactly as on the host."""
+    lengths, gcs = dense_layout(seed, n_genomes, median, sigma)
+    d, offsets = draw_genomes(seed + 3, lengths, gcs)
+    lib = _get_lib()
+    by_genome = {}
+    for rep in dense_repeats(seed, lengths):
+        by_genome.setdefault(rep[0], []).append(rep)
+    tmpls = []
+    for g, reps in by_genome.items():
+        # groups of repeats whose spans overlap (transitively), each group written in repeat order
+        spans = sorted(range(len(reps)), key=lambda i: reps[i][1])
+        groups, cur, cur_end = [], [], -1
+        for i in spans:
+            a, n = reps[i][1], reps[i][2]
+            if cur and a < cur_end:
+                cur.append(i)
+                cur_end = max(cur_end, a + n)
+            else:
+                if cur:
+                    groups.append(cur)
+                cur, cur_end = [i], a + n
+        if cur:
+            groups.append(cur)
+        for grp in groups:
+            lo = min(reps[i][1] for i in grp)
+            hi = max(reps[i][1] + reps[i][2] for i in grp)
+            buf = np.zeros(hi - lo, dtype=np.uint8)
+            for i in sorted(grp):
+                _, off, rlen, key, period = reps[i]
+                lib.synth_fill_tandem(buf.ctypes.data + (off - lo), rlen, key, period)
+            tmpls.append((g, lo, buf.tobytes()))
+    scatter(d, offsets, tmpls)
+    fwd, rev = dense_primers(seed)
+    return DeviceWorkload("dense", d, offsets, np.arange(n_genomes, dtype=np.uint32), fwd, rev, [DENSE_K], 3, 50, 5000,
+                          0b1111, TmParams(min_tm=None), False, 0, 0, [], seed, False)
 
 
 def serving_layout(seed: int = SEED, n_genomes: int = 40_000, median: float = 3.5e6, sigma: float = 0.4):

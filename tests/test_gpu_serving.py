@@ -117,3 +117,15 @@ def test_device_drawer_matches_host_drawer():
     assert np.array_equal(host.offsets, dev.offsets)
     assert host.fwd == dev.fwd and host.rev == dev.rev
     assert np.array_equal(host.seq, dev.d_seq.cpu().numpy())
+
+
+def test_device_dense_drawer_matches_host_drawer():
+    """The dense-hit workload drawn on the device (tandem repeats merged where they overlap) equals
+    the host drawer byte for byte."""
+    import synth.gpu as sg
+
+    host = synth.dense(n_genomes=40, median=1.5e5, sigma=0.3)
+    dev = sg.dense(n_genomes=40, median=1.5e5, sigma=0.3)
+    assert np.array_equal(host.offsets, dev.offsets)
+    assert host.fwd == dev.fwd and host.rev == dev.rev
+    assert np.array_equal(host.seq, dev.d_seq.cpu().numpy())
