@@ -348,7 +348,9 @@ typedef struct {
   uint64_t n_hits, n_amps, n_kept, arena_bytes; /* of the last checked run */
   double autotune_ms, best_scan_ms;
 } ah_plan_info;
-/* Build (autotune, size, capture).  The batch and primers must outlive the plan.  Synchronises. */
+/* Build: autotune, size every buffer from one exact run of the regular path, capture, then one
+ * checked replay that grows whatever this batch overflowed (per-tile slot lists included).  The
+ * batch and primers must outlive the plan.  Synchronises. */
 ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_plan_params* params,
                          ah_plan** out);
 /* One graph launch of the whole step on the context's stream (asynchronous).  With timing on

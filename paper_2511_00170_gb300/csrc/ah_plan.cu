@@ -313,6 +313,9 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
     st = fail(ctx, AH_ENOMEM, "ah_plan_create: pinned allocation failed");
   if (!st) st = alloc_buffers(pl);
   if (!st) st = capture(pl);
+  // one checked replay: per-tile slot lists (sized from the context's default) and the other
+  // capacities grow here if this batch needs more, so later replays fit without checks
+  if (!st) st = ah_plan_run(pl);
   if (st) {
     ah_plan_free(pl);
     return st;
