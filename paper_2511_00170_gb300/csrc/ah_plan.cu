@@ -220,6 +220,33 @@ ah_status time_shape(ah_ctx* c, const ah_batch* b, const ah_primers* p, const Sc
   return st;
 }
 
+// After an overflowing run: enlarge the per-tile slot lists and every capacity that overflowed (with
+// `all` false, only those the plan sized itself), free the buffers and capture again.  AH_OK with
+// nothing changed when only caller-given capacities overflowed.
+ah_status grow(ah_plan* pl, bool all) {
+  const ah_plan_info& i = pl->info;
+  const ah_plan_params& q = pl->prm;
+  bool changed = false;
+  if (i.max_tile_sites > pl->slot_cap) {
+    uint32_t need = 1;
+    while (need < i.max_tile_sites) need <<= 1;
+    if (need > 4096) return fail(pl->ctx, AH_EOVERFLOW, "plan: a tile holds more than 4096 sites");
+    pl->slot_cap = need;
+    changed = true;
+  }
+  auto enlarge = [&](uint64_t& cap, uint64_t used, uint64_t given, uint64_t slack) {
+    if (used > cap && (all || !given)) cap = std::max(cap, used + used / 4 + slack), changed = true;
+  };
+  enlarge(pl->hit_cap, i.n_hits, q.hit_capacity, 1024);
+  enlarge(pl->amp_cap, i.n_amps, q.amp_capacity, 1024);
+  if (q.extract) enlarge(pl->arena_cap, i.arena_bytes, q.arena_capacity, 4096);
+  if (!changed) return AH_OK;
+  free_buffers(pl);
+  ah_status st;
+  if ((st = alloc_buffers(pl)) || (st = capture(pl))) return st;
+  return AH_OK;
+}
+
 }  // namespace
 }  // namespace ah
 
@@ -313,9 +340,21 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
     st = fail(ctx, AH_ENOMEM, "ah_plan_create: pinned allocation failed");
   if (!st) st = alloc_buffers(pl);
   if (!st) st = capture(pl);
-  // one checked replay: per-tile slot lists (sized from the context's default) and the other
-  // capacities grow here if this batch needs more, so later replays fit without checks
-  if (!st) st = ah_plan_run(pl);
+  // checked replays: the per-tile slot lists (sized from the context's default) and the capacities
+  // the plan sized itself grow here if this batch needs more, so later replays fit unchecked;
+  // capacities the caller fixed are left as given (ah_plan_check reports them)
+  for (int attempt = 0; attempt < 4 && !st; ++attempt) {
+    if ((st = ah_plan_launch(pl))) break;
+    const ah_status cs = ah_plan_check(pl);
+    if (cs != AH_EOVERFLOW) {
+      st = cs;
+      break;
+    }
+    const uint32_t slots = pl->slot_cap;
+    const uint64_t caps = pl->hit_cap + pl->amp_cap + pl->arena_cap;
+    if ((st = grow(pl, false))) break;  // e.g. a tile with more than 4096 sites
+    if (pl->slot_cap == slots && pl->hit_cap + pl->amp_cap + pl->arena_cap == caps) break;  // only fixed ones
+  }
   if (st) {
     ah_plan_free(pl);
     return st;
@@ -391,19 +430,7 @@ ah_status ah_plan_run(ah_plan* pl) {
     if (st) return st;
     st = ah_plan_check(pl);
     if (st != AH_EOVERFLOW) return st;
-    // grow what overflowed, re-capture
-    const ah_plan_info& i = pl->info;
-    if (i.max_tile_sites > pl->slot_cap) {
-      uint32_t need = 1;
-      while (need < i.max_tile_sites) need <<= 1;
-      if (need > 4096) return fail(pl->ctx, AH_EOVERFLOW, "plan: a tile holds more than 4096 sites");
-      pl->slot_cap = need;
-    }
-    pl->hit_cap = std::max(pl->hit_cap, i.n_hits + i.n_hits / 4 + 1024);
-    pl->amp_cap = std::max(pl->amp_cap, i.n_amps + i.n_amps / 4 + 1024);
-    pl->arena_cap = std::max(pl->arena_cap, i.arena_bytes + i.arena_bytes / 4 + 4096);
-    free_buffers(pl);
-    if ((st = alloc_buffers(pl)) || (st = capture(pl))) return st;
+    if ((st = grow(pl, true)) != AH_OK) return st;
   }
   return fail(pl->ctx, AH_EOVERFLOW, "plan: capacities kept overflowing");
 }
