@@ -106,9 +106,10 @@ ah_status ah_ctx_set_scan_config(ah_ctx* ctx, int threads, int groups_per_thread
  *   - invalid[g] is a uint32: bit b set iff base 32g+b is not one of ACGTacgt (N, other IUPAC
  *     codes, padding); such bases are stored as code 0;
  *   - record r starts at group rec_group[r] (a multiple of 2, so every record starts 16-byte
- *     aligned) and has rec_len[r] bases; the bases after rec_len up to the next record are
- *     padding;
- *   - the plane and invalid arrays extend at least 64 zero groups past the last record.
+ *     aligned) and has rec_len[r] bases; it occupies 2 * (rec_len[r] / 64 + 1) groups, so at
+ *     least one padding base (invalid, code 0) follows every record, the empty record included;
+ *   - the plane and invalid arrays extend at least 64 groups past the last record (code 0,
+ *     invalid).
  */
 typedef struct {
   uint32_t n_records;

@@ -163,7 +163,7 @@ ah_status layout_batch(ah_ctx* ctx, uint32_t n_rec, const uint64_t* lens, const 
     if (lens[r] > 0xffffffffull) return fail(ctx, AH_EINVAL, "record %u is longer than 2^32-1 bases", r);
     b->h_rec_group[r] = cursor;
     b->h_rec_len[r] = (uint32_t)lens[r];
-    cursor += ((lens[r] + 63) / 64) * 2;  // 64-base (16-byte) aligned records
+    cursor += record_groups(lens[r]);
     bases += lens[r];
   }
   b->n_bases = bases;
@@ -182,9 +182,9 @@ ah_status layout_batch(ah_ctx* ctx, uint32_t n_rec, const uint64_t* lens, const 
   AH_CUDA(ctx, cudaMemcpyAsync(b->rec_len, b->h_rec_len.data(), n_rec * sizeof(uint32_t), cudaMemcpyHostToDevice,
                                ctx->stream));
   AH_CUDA(ctx, cudaMemcpyAsync(b->genome_id, gid.data(), n_rec * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
-  // the tail past the last record reads as code 0 and valid; windows there fail the length check
+  // the tail past the last record: code 0, invalid
   AH_CUDA(ctx, cudaMemsetAsync(b->planes + b->n_groups, 0, kTailGroups * sizeof(uint2), ctx->stream));
-  AH_CUDA(ctx, cudaMemsetAsync(b->invalid + b->n_groups, 0, kTailGroups * sizeof(uint32_t), ctx->stream));
+  AH_CUDA(ctx, cudaMemsetAsync(b->invalid + b->n_groups, 0xFF, kTailGroups * sizeof(uint32_t), ctx->stream));
   // host vectors above must outlive the async copies
   AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return AH_OK;
@@ -196,7 +196,7 @@ void add_items(std::vector<PackItem>& items, const ah_batch* b, uint32_t r, uint
                uint64_t src_off) {
   const uint64_t piece = 1ull << 20;  // bases per item (multiple of 32)
   const uint64_t len = b->h_rec_len[r];
-  const uint64_t rec_groups = ((len + 63) / 64) * 2;
+  const uint64_t rec_groups = record_groups(len);
   for (uint64_t a = from; a < to || (a == from && to == from && from == 0 && len == 0); a += piece) {
     uint64_t e = std::min(to, a + piece);
     PackItem it;
@@ -438,6 +438,7 @@ ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, co
   uint64_t fill = 0, stage_max = 0;
   for (uint32_t r = 0; r < n_rec; ++r) {
     uint64_t len = lens[r], done = 0;
+    if (len == 0) add_items(items.back(), b, r, 0, 0, 0);  // its padding groups (nothing is read)
     while (done < len) {
       uint64_t room = kChunkBases - std::min(fill, kChunkBases);
       uint64_t take = std::min(room, len - done);

@@ -24,6 +24,10 @@ constexpr int kGroupBases = 32;            // bases per plane word
 constexpr int kTailGroups = 64;            // zero groups after the last record
 constexpr uint64_t kChunkBases = 64ull << 20;  // host->device streaming chunk (16 MB packed)
 
+// Groups of a record of len bases: whole 64-base blocks (records start 16-byte aligned) with at
+// least one padding base after the record, so a window that leaves its record meets an invalid base.
+inline uint64_t record_groups(uint64_t len) { return (len / 64 + 1) * 2; }
+
 // Device status word bits (set by kernels, read by synchronising calls).
 enum : uint32_t {
   ST_SCAN_MISMATCH = 1u << 0,   // bit-sliced matcher and exact re-check disagree

@@ -228,37 +228,30 @@ struct ScanParams {
 };
 static __device__ __forceinline__ u32 fshr(u32 a, u32 b, u32 s) { return __funnelshift_r(a, b, s); }
 
-// exact re-check of candidate bits, validity, record bounds, and slot append
+// Candidate bits: an exact re-check by a second method (the window's bases against per-position set
+// masks, mismatches counted by popcount), the invalid-base test, and the slot append.  Every record
+// is followed by at least one invalid padding base, so a window that leaves its record holds an
+// invalid base and the one test covers record bounds too.
 static __device__ __noinline__ void emit(u32 h, int q, u64 g, uint2 a, uint2 b, const ScanParams& P) {
   const u64 tile = g / P.tile_groups, tile_pos = tile * P.tile_groups * 32ull;
   const u64 lo64 = (u64)a.x | ((u64)b.x << 32), hi64 = (u64)a.y | ((u64)b.y << 32);
   const u64 inv64 = (u64)P.invalid[g] | ((u64)P.invalid[g + 1] << 32);
   const int L = PLEN[q];
+  const u32 wm = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
+  const u32 mA = MSET[q][0], mC = MSET[q][1], mT = MSET[q][2], mG = MSET[q][3];
   while (h) {
     const int i = __ffs(h) - 1;
     h &= h - 1;
-    int mism = 0, clamp_bad = 0;
-    for (int j = 0; j < L; ++j) {
-      const int code = (int)((lo64 >> (i + j)) & 1) | ((int)((hi64 >> (i + j)) & 1) << 1);
-      if (!((PSET[q][j] >> code) & 1)) {
-        ++mism;
-        if (j >= PCLO[q] && j < PCHI[q]) clamp_bad = 1;
-      }
-    }
-    if (clamp_bad || mism > PK[q]) {
+    const u32 wl = (u32)(lo64 >> i), wh = (u32)(hi64 >> i);  // base j of the window at bit j
+    const u32 match = (~wl & ~wh & mA) | (wl & ~wh & mC) | (~wl & wh & mT) | (wl & wh & mG);
+    const u32 mis = ~match & wm;
+    const int mism = __popc(mis);
+    if ((mis & PCLAMP[q]) || mism > PK[q]) {
       atomicOr(P.status, 1u);
       continue;
     }
-    const u64 wmask = (L == 64) ? ~0ull : ((1ull << L) - 1ull);
-    if ((inv64 >> i) & wmask) continue;
+    if ((u32)(inv64 >> i) & wm) continue;
     const u64 pos = g * 32ull + (u64)i;
-    u32 lo = 0, hi = P.n_rec;
-    while (hi - lo > 1) {
-      const u32 mid = (lo + hi) >> 1;
-      if (P.rec_group[mid] * 32ull <= pos) lo = mid; else hi = mid;
-    }
-    const u64 local = pos - P.rec_group[lo] * 32ull;
-    if (local + (u64)L > (u64)P.rec_len[lo]) continue;
     const u64 key = ((u64)PPAIR[q] << 48) | ((pos - tile_pos) << 16) | ((u64)PORIENT[q] << 8) | (u64)mism;
     const u32 idx = atomicAdd(P.tile_count + tile, 1u);
     if (idx < P.slot_cap) P.slots[tile * (u64)P.slot_cap + idx] = key;
@@ -280,18 +273,27 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg,
     os << "};\n";
   };
   table("unsigned char", "PLEN", [](const Pattern& p) { return p.len; });
-  table("unsigned char", "PCLO", [](const Pattern& p) { return p.clamp_lo; });
-  table("unsigned char", "PCHI", [](const Pattern& p) { return p.clamp_hi; });
   table("unsigned char", "PK", [](const Pattern& p) { return p.k; });
   table("unsigned short", "PPAIR", [](const Pattern& p) { return p.id / 4; });
   table("unsigned char", "PORIENT", [](const Pattern& p) { return p.id % 4; });
-  os << "static __device__ const unsigned char PSET[" << Q << "][32] = {";
+  // per pattern and code c (A, C, T, G): bit j set iff position j's set holds c; and the clamp's bits
+  os << "static __device__ const unsigned int MSET[" << Q << "][4] = {";
   for (int q = 0; q < Q; ++q) {
     os << (q ? "," : "") << "{";
-    for (int j = 0; j < 32; ++j) os << (j ? "," : "") << (unsigned)(j < pats[q].len ? pats[q].set[j] : 15);
+    for (int c = 0; c < 4; ++c) {
+      uint32_t m = 0;
+      for (int j = 0; j < pats[q].len; ++j)
+        if ((pats[q].set[j] >> c) & 1) m |= 1u << j;
+      os << (c ? "," : "") << m << "u";
+    }
     os << "}";
   }
   os << "};\n";
+  table("unsigned int", "PCLAMP", [](const Pattern& p) {
+    uint32_t m = 0;
+    for (int j = p.clamp_lo; j < p.clamp_hi; ++j) m |= 1u << j;
+    return m;
+  });
   os << kPrelude;
 
   // body: per group of 32 positions

@@ -240,8 +240,7 @@ ah_status launch_scan(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const
     if ((st = ctx->jit->get(ctx, pats, cfg, &kern))) return st;
     for (uint32_t r = 0; r < b->n_records; ++r) {
       const uint64_t g0 = b->h_rec_group[r];
-      const uint64_t ng = ((uint64_t)b->h_rec_len[r] + 63) / 64 * 2;
-      if (ng == 0) continue;
+      const uint64_t ng = record_groups(b->h_rec_len[r]);
       ScanParamsHost P{b->planes, b->invalid, b->rec_group, b->rec_len, b->n_records, cap, g0, ng,
                        slots, tile_count, ctx->d_status, tile_groups, nullptr, 0};
       void* args[] = {&P};

@@ -454,11 +454,20 @@ __device__ ChainResult site_tm_chain(const SiteVariants& V, const TmRun& R, doub
   double maxS;
   if (!viterbi(1.0, 0.0, &maxS)) return kChainUndefined;
   if (maxS + Sc + S0 >= 0.0) return kChainUnbounded;
-  // start from the variant that maximises dS - dH / 300 (any defined variant works)
-  double sc;
-  if (!viterbi(300.0, 1.0, &sc)) return kChainUndefined;
-  double t;
-  if (!duplex_tm(v, V.c, L, R, &t)) return kChainUndefined;
+  // Start from the variant that agrees with the site wherever the primer allows (it has the fewest
+  // mismatches, so it qualifies whenever any variant does, and it is usually the maximum: one
+  // Viterbi pass then confirms it); if its duplex is undefined, from the variant that maximises
+  // dS - dH / 300.  Any defined start converges to the same maximum.
+  double sc, t;
+  for (int j = 0; j < L; ++j) {
+    v[j] = V.ch[j][0];
+    for (int a = 0; a < V.nch[j]; ++a)
+      if (V.ch[j][a] == V.s[j]) v[j] = V.s[j];
+  }
+  if (!duplex_tm(v, V.c, L, R, &t)) {
+    if (!viterbi(300.0, 1.0, &sc)) return kChainUndefined;
+    if (!duplex_tm(v, V.c, L, R, &t)) return kChainUndefined;
+  }
   const double shift = R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0;
   double lam = t + 273.15 - shift;
   double best_t = t;
