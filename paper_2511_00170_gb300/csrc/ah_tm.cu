@@ -96,6 +96,12 @@ struct NNTables {
 // global (not constant) memory: threads of a warp look up different steps, which the constant cache
 // would serialise
 __device__ NNTables c_nn;
+// the same values in single precision, for the search passes of the degenerate-site chain method
+struct NNTablesF {
+  float step_h[256], step_s[256];
+  float term_h[256], term_s[256];
+};
+__device__ NNTablesF c_nnf;
 
 int code_of(char c) {  // A=0, C=1, T=2, G=3
   switch (c) {
@@ -162,8 +168,14 @@ ah_status load_tables(ah_ctx* ctx) {
   std::lock_guard<std::mutex> lock(g_tables_mu);
   if (ctx->device < 64 && g_tables_loaded[ctx->device]) return AH_OK;
   static NNTables host;
+  static NNTablesF host_f;
   build_tables(&host);
+  for (int i = 0; i < 256; ++i) {
+    host_f.step_h[i] = (float)host.step_h[i], host_f.step_s[i] = (float)host.step_s[i];
+    host_f.term_h[i] = (float)host.term_h[i], host_f.term_s[i] = (float)host.term_s[i];
+  }
   AH_CUDA(ctx, cudaMemcpyToSymbolAsync(c_nn, &host, sizeof host, 0, cudaMemcpyHostToDevice, ctx->stream));
+  AH_CUDA(ctx, cudaMemcpyToSymbolAsync(c_nnf, &host_f, sizeof host_f, 0, cudaMemcpyHostToDevice, ctx->stream));
   AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->device < 64) g_tables_loaded[ctx->device] = true;
   return AH_OK;
@@ -200,6 +212,24 @@ ah_status make_run(ah_ctx* ctx, const ah_tm_params* p, TmRun* r) {
     default: r->corr_const = 0.0;
   }
   return AH_OK;
+}
+
+// Tm from the duplex sums (dH kcal/mol, dS cal/(K mol), before salt and concentration terms) and the
+// variant's G/C count: salt correction, then Tm = 1000 dH / (dS + R ln C) - 273.15
+__device__ __forceinline__ double tm_of_sums(double dh, double ds, int gc, int L, const TmRun& R) {
+  double corr = 0.0;
+  if (R.saltcorr == 5) {
+    ds += 0.368 * (double)(L - 1) * R.ln_mon;
+  } else if (R.saltcorr == 6) {
+    const double f = (double)gc / (double)L;
+    corr = (4.29 * f - 3.95) * 1e-5 * R.ln_mon + 9.40e-6 * R.ln_mon * R.ln_mon;
+  } else {
+    corr = R.corr_const;
+  }
+  double t = (1000.0 * dh) / (ds + R.rlnk) - 273.15;
+  if (R.saltcorr >= 1 && R.saltcorr <= 4) t += corr;
+  if (R.saltcorr == 6) t = 1.0 / (1.0 / (t + 273.15) + corr) - 273.15;
+  return t;
 }
 
 // Tm of variant v (codes, 5'->3') over c (codes of the opposite strand, 3'->5'); false if undefined
@@ -254,57 +284,57 @@ __device__ bool duplex_tm(const uint8_t* v, const uint8_t* c, int L, const TmRun
     dh += sh;
     ds += __ldg(&c_nn.step_s[k]);
   }
-  double corr = 0.0;
-  if (R.saltcorr == 5) {
-    ds += 0.368 * (double)(L - 1) * R.ln_mon;
-  } else if (R.saltcorr == 6) {
-    const double f = (double)gc / (double)L;
-    corr = (4.29 * f - 3.95) * 1e-5 * R.ln_mon + 9.40e-6 * R.ln_mon * R.ln_mon;
-  } else {
-    corr = R.corr_const;
-  }
-  double t = (1000.0 * dh) / (ds + R.rlnk) - 273.15;
-  if (R.saltcorr >= 1 && R.saltcorr <= 4) t += corr;
-  if (R.saltcorr == 6) t = 1.0 / (1.0 / (t + 273.15) + corr) - 273.15;
-  *tm = t;
+  *tm = tm_of_sums(dh, ds, gc, L, R);
   return true;
 }
 
+// the tables in the arithmetic of a chain pass
+template <class T> struct Tab;
+template <> struct Tab<double> {
+  static __device__ __forceinline__ const NNTables& t() { return c_nn; }
+};
+template <> struct Tab<float> {
+  static __device__ __forceinline__ const NNTablesF& t() { return c_nnf; }
+};
+
 // nearest-neighbour sums of edge (i, i+1) of the variant chain for bases (a, b) at positions i, i+1
 // over the opposite-strand codes c: the terminal-mismatch entry replaces the stack at either end
-__device__ __forceinline__ bool edge_sums(int i, int L, uint8_t a, uint8_t b, const uint8_t* c, double* dh, double* ds) {
+template <class T>
+__device__ __forceinline__ bool edge_sums(int i, int L, uint8_t a, uint8_t b, const uint8_t* c, T* dh, T* ds) {
+  const auto& tb = Tab<T>::t();
   if (i == 0) {
     const int k = c[1] * 64 + c[0] * 16 + b * 4 + a;  // left end read from the opposite strand
-    const double th = __ldg(&c_nn.term_h[k]);
+    const T th = __ldg(&tb.term_h[k]);
     if (!isnan(th)) {
       *dh = th;
-      *ds = __ldg(&c_nn.term_s[k]);
+      *ds = __ldg(&tb.term_s[k]);
       return true;
     }
   }
   if (i == L - 2) {
     const int k = a * 64 + b * 16 + c[L - 2] * 4 + c[L - 1];
-    const double th = __ldg(&c_nn.term_h[k]);
+    const T th = __ldg(&tb.term_h[k]);
     if (!isnan(th)) {
       *dh = th;
-      *ds = __ldg(&c_nn.term_s[k]);
+      *ds = __ldg(&tb.term_s[k]);
       return true;
     }
   }
   const int k = a * 64 + b * 16 + c[i] * 4 + c[i + 1];
-  const double sh = __ldg(&c_nn.step_h[k]);
+  const T sh = __ldg(&tb.step_h[k]);
   if (isnan(sh)) return false;
   *dh = sh;
-  *ds = __ldg(&c_nn.step_s[k]);
+  *ds = __ldg(&tb.step_s[k]);
   return true;
 }
 
 // initiation terms that depend on the variant's end bases
-__device__ __forceinline__ void end_sums(int j, int L, uint8_t v, double* dh, double* ds) {
-  *dh = (v & 1) ? kTermGCH : kTermATH;
-  *ds = (v & 1) ? kTermGCS : kTermATS;
-  if (j == 0 && v == 2) *dh += k5TAH, *ds += k5TAS;       // 5' T
-  if (j == L - 1 && v == 0) *dh += k5TAH, *ds += k5TAS;   // 3' A
+template <class T>
+__device__ __forceinline__ void end_sums(int j, int L, uint8_t v, T* dh, T* ds) {
+  *dh = (T)((v & 1) ? kTermGCH : kTermATH);
+  *ds = (T)((v & 1) ? kTermGCS : kTermATS);
+  if (j == 0 && v == 2) *dh += (T)k5TAH, *ds += (T)k5TAS;       // 5' T
+  if (j == L - 1 && v == 0) *dh += (T)k5TAH, *ds += (T)k5TAS;   // 3' A
 }
 
 // The variants that count at a site (reading R14): per position the primer's codes, only the site's
@@ -346,16 +376,21 @@ __device__ uint64_t count_variants(const SiteVariants& V, uint64_t cap) {
   return t;
 }
 
-// maximum Tm over the qualifying variants by depth-first enumeration (mismatch budget pruned)
+// Maximum Tm over the qualifying variants by depth-first enumeration.  The walk adds one position's
+// terms per step (the end terms at both ends, the edge to the previous base in between), so variants
+// share the sums of their common prefix; a prefix whose last edge has no parameter is undefined for
+// every variant below it and is cut, and so is one over the mismatch budget.
 __device__ bool enum_max(const SiteVariants& V, const TmRun& R, double* out) {
   int8_t idx[32];
-  uint8_t mm[33], v[32];
+  uint8_t mm[33], gcs[33], v[32];
+  double sh[33], ss[33];  // sums of the terms of positions < j
   const int L = V.L;
   double best = -INFINITY;
   bool any = false;
   int j = 0;
   idx[0] = -1;
-  mm[0] = 0;
+  mm[0] = gcs[0] = 0;
+  sh[0] = ss[0] = 0.0;
   while (j >= 0) {
     if (++idx[j] >= V.nch[j]) {
       --j;
@@ -364,15 +399,27 @@ __device__ bool enum_max(const SiteVariants& V, const TmRun& R, double* out) {
     const uint8_t b = V.ch[j][idx[j]];
     const int m = mm[j] + (V.k >= 0 && b != V.s[j]);
     if (V.k >= 0 && m > V.k) continue;
-    v[j] = b;
-    if (j == L - 1) {
-      double t;
-      if (duplex_tm(v, V.c, L, R, &t)) {
-        any = true;
-        best = fmax(best, t);
-      }
+    double dh = sh[j], ds = ss[j], eh, es;
+    if (j == 0) {
+      end_sums<double>(0, L, b, &eh, &es);
+    } else if (!edge_sums<double>(j - 1, L, v[j - 1], b, V.c, &eh, &es)) {
       continue;
     }
+    dh += eh;
+    ds += es;
+    v[j] = b;
+    const int gc = gcs[j] + (b & 1);
+    if (j == L - 1) {
+      end_sums<double>(L - 1, L, b, &eh, &es);
+      dh += eh + kInitH + (gc ? kOneGCH : kAllATH);
+      ds += es + kInitS + (gc ? kOneGCS : kAllATS);
+      any = true;
+      best = fmax(best, tm_of_sums(dh, ds, gc, L, R));
+      continue;
+    }
+    sh[j + 1] = dh;
+    ss[j + 1] = ds;
+    gcs[j + 1] = (uint8_t)gc;
     mm[j + 1] = (uint8_t)m;
     ++j;
     idx[j] = -1;
@@ -383,104 +430,131 @@ __device__ bool enum_max(const SiteVariants& V, const TmRun& R, double* out) {
 
 enum ChainResult { kChainOk, kChainUndefined, kChainUnbounded };
 
+// One Viterbi pass over the chain of qualifying variants, in arithmetic T: the variant maximising
+// the sum of (wl * dS - wn * 1000 * dH) over its terms that depend on its bases (arg-max left in v).
+// States are (position, base, mismatches so far), at most 4 x (k + 1) per position.
+template <class T>
+__device__ bool chain_viterbi_k(const SiteVariants& V, T wl, T wn, uint8_t (*back)[4][kMaxK + 1], uint8_t* v,
+                                T* best_score) {
+  constexpr int M = kMaxK + 1;
+  const int L = V.L, K = V.k < 0 ? 0 : V.k;
+  auto inc = [&](int j, int a) { return (V.k >= 0 && V.ch[j][a] != V.s[j]) ? 1 : 0; };
+  const T ninf = -(T)INFINITY;
+  T cur[4][M], nxt[4][M];
+  for (int a = 0; a < 4; ++a)
+    for (int m = 0; m <= K; ++m) cur[a][m] = ninf;
+  for (int a = 0; a < V.nch[0]; ++a) {
+    T dh, ds;
+    end_sums<T>(0, L, V.ch[0][a], &dh, &ds);
+    cur[a][inc(0, a)] = wl * ds - wn * (T)1000 * dh;
+  }
+  for (int i = 0; i + 1 < L; ++i) {
+    for (int b = 0; b < V.nch[i + 1]; ++b) {
+      const int ib = inc(i + 1, b);
+      T tail = 0;
+      if (i + 1 == L - 1) {
+        T dh, ds;
+        end_sums<T>(L - 1, L, V.ch[i + 1][b], &dh, &ds);
+        tail = wl * ds - wn * (T)1000 * dh;
+      }
+      for (int m = 0; m <= K; ++m) nxt[b][m] = ninf, back[i + 1][b][m] = 0;
+      for (int a = 0; a < V.nch[i]; ++a) {
+        T dh, ds;
+        if (!edge_sums<T>(i, L, V.ch[i][a], V.ch[i + 1][b], V.c, &dh, &ds)) continue;
+        const T w = wl * ds - wn * (T)1000 * dh + tail;
+        for (int m = 0; m + ib <= K; ++m) {
+          if (cur[a][m] == ninf) continue;
+          const T sc = cur[a][m] + w;
+          if (sc > nxt[b][m + ib]) nxt[b][m + ib] = sc, back[i + 1][b][m + ib] = (uint8_t)a;
+        }
+      }
+    }
+    for (int b = 0; b < V.nch[i + 1]; ++b)
+      for (int m = 0; m <= K; ++m) cur[b][m] = nxt[b][m];
+  }
+  T best = ninf;
+  int arg = -1, am = 0;
+  for (int b = 0; b < V.nch[L - 1]; ++b)
+    for (int m = 0; m <= K; ++m)
+      if (cur[b][m] > best) best = cur[b][m], arg = b, am = m;
+  if (arg < 0) return false;
+  for (int j = L - 1; j >= 0; --j) {
+    v[j] = V.ch[j][arg];
+    if (j) {
+      const int pa = back[j][arg][am];
+      am -= inc(j, arg);
+      arg = pa;
+    }
+  }
+  *best_score = best;
+  return true;
+}
+
+template <class T>
+__device__ __forceinline__ bool chain_viterbi(const SiteVariants& V, T wl, T wn, uint8_t (*back)[4][kMaxK + 1],
+                                              uint8_t* v, T* best_score) {
+  return chain_viterbi_k<T>(V, wl, wn, back, v, best_score);
+}
+
 // Exact maximum of Tm over the qualifying variants for salt methods 0-5 and L >= 3.
 // Tm + 273.15 = N(v) / D(v) with N = 1000 dH and D = dS + S0 < 0, and every term of N and D depends on
 // at most two adjacent variant bases.  Dinkelbach's iteration for fractional programmes: for the
 // current ratio lam, a Viterbi pass over the chain finds the variant maximising lam * D - N; its ratio
-// becomes the next lam; at the optimum the maximum is 0.  The chain's states are (position, base,
-// mismatches so far), at most 4 x (k + 1) per position.  kChainUnbounded when some qualifying variant
-// could have D >= 0, where the iteration does not apply.
+// becomes the next lam; at the optimum the maximum is 0.  The search passes run in single precision
+// (GB300 runs FP32 at many times its FP64 rate); every candidate's Tm is evaluated exactly, and the
+// optimum is confirmed by a double-precision pass, which continues the iteration if single
+// precision stopped short.  kChainUnbounded when some qualifying variant could have D >= 0, where
+// the iteration does not apply.
 __device__ ChainResult site_tm_chain(const SiteVariants& V, const TmRun& R, double* out) {
-  constexpr int M = kMaxK + 1;
-  const int L = V.L, K = V.k < 0 ? 0 : V.k;
-  uint8_t back[32][4][M], v[32];
+  const int L = V.L;
+  uint8_t back[32][4][kMaxK + 1], v[32];
   // constant part of D: salt (method 5) and R ln(C); methods 1-4 shift Tm by a constant
   const double S0 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
   const double H0 = kInitH + kOneGCH, Sc = kInitS + kOneGCS;  // all-A/T and one-G/C terms are equal here
-  auto inc = [&](int j, int a) { return (V.k >= 0 && V.ch[j][a] != V.s[j]) ? 1 : 0; };
-  // Viterbi: maximise the sum of (wl * ds - wn * 1000 * dh) over the qualifying variants; the arg-max is
-  // left in v
-  auto viterbi = [&](double wl, double wn, double* best_score) -> bool {
-    double cur[4][M], nxt[4][M];
-    for (int a = 0; a < 4; ++a)
-      for (int m = 0; m <= K; ++m) cur[a][m] = -INFINITY;
-    for (int a = 0; a < V.nch[0]; ++a) {
-      double dh, ds;
-      end_sums(0, L, V.ch[0][a], &dh, &ds);
-      cur[a][inc(0, a)] = wl * ds - wn * 1000.0 * dh;
-    }
-    for (int i = 0; i + 1 < L; ++i) {
-      for (int b = 0; b < V.nch[i + 1]; ++b) {
-        const int ib = inc(i + 1, b);
-        double tail = 0.0;
-        if (i + 1 == L - 1) {
-          double dh, ds;
-          end_sums(L - 1, L, V.ch[i + 1][b], &dh, &ds);
-          tail = wl * ds - wn * 1000.0 * dh;
-        }
-        for (int m = 0; m <= K; ++m) nxt[b][m] = -INFINITY, back[i + 1][b][m] = 0;
-        for (int a = 0; a < V.nch[i]; ++a) {
-          double dh, ds;
-          if (!edge_sums(i, L, V.ch[i][a], V.ch[i + 1][b], V.c, &dh, &ds)) continue;
-          const double w = wl * ds - wn * 1000.0 * dh + tail;
-          for (int m = 0; m + ib <= K; ++m) {
-            if (cur[a][m] == -INFINITY) continue;
-            const double sc = cur[a][m] + w;
-            if (sc > nxt[b][m + ib]) nxt[b][m + ib] = sc, back[i + 1][b][m + ib] = (uint8_t)a;
-          }
-        }
-      }
-      for (int b = 0; b < V.nch[i + 1]; ++b)
-        for (int m = 0; m <= K; ++m) cur[b][m] = nxt[b][m];
-    }
-    double best = -INFINITY;
-    int arg = -1, am = 0;
-    for (int b = 0; b < V.nch[L - 1]; ++b)
-      for (int m = 0; m <= K; ++m)
-        if (cur[b][m] > best) best = cur[b][m], arg = b, am = m;
-    if (arg < 0) return false;
-    for (int j = L - 1; j >= 0; --j) {
-      v[j] = V.ch[j][arg];
-      if (j) {
-        const int pa = back[j][arg][am];
-        am -= inc(j, arg);
-        arg = pa;
-      }
-    }
-    *best_score = best;
-    return true;
-  };
-  // D must stay negative for every qualifying variant: maximise dS (wl = 1, wn = 0)
-  double maxS;
-  if (!viterbi(1.0, 0.0, &maxS)) return kChainUndefined;
-  if (maxS + Sc + S0 >= 0.0) return kChainUnbounded;
-  // Start from the variant that agrees with the site wherever the primer allows (it has the fewest
-  // mismatches, so it qualifies whenever any variant does, and it is usually the maximum: one
-  // Viterbi pass then confirms it); if its duplex is undefined, from the variant that maximises
-  // dS - dH / 300.  Any defined start converges to the same maximum.
-  double sc, t;
-  for (int j = 0; j < L; ++j) {
-    v[j] = V.ch[j][0];
-    for (int a = 0; a < V.nch[j]; ++a)
-      if (V.ch[j][a] == V.s[j]) v[j] = V.s[j];
-  }
-  if (!duplex_tm(v, V.c, L, R, &t)) {
-    if (!viterbi(300.0, 1.0, &sc)) return kChainUndefined;
-    if (!duplex_tm(v, V.c, L, R, &t)) return kChainUndefined;
-  }
   const double shift = R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0;
-  double lam = t + 273.15 - shift;
-  double best_t = t;
+  // D must stay negative for every qualifying variant: the largest dS, in single precision when it is
+  // clearly below the bound (rounding there is far below 0.01), else in double precision
+  {
+    float maxS_f;
+    if (!chain_viterbi<float>(V, 1.f, 0.f, back, v, &maxS_f)) return kChainUndefined;
+    if (!((double)maxS_f + Sc + S0 < -0.01)) {
+      double maxS;
+      if (!chain_viterbi<double>(V, 1.0, 0.0, back, v, &maxS)) return kChainUndefined;
+      if (maxS + Sc + S0 >= 0.0) return kChainUnbounded;
+    }
+  }
+  // start from the variant that maximises dS - dH / 300 (any defined variant works)
+  float scf;
+  if (!chain_viterbi<float>(V, 300.f, 1.f, back, v, &scf)) return kChainUndefined;
+  double t;
+  if (!duplex_tm(v, V.c, L, R, &t)) {
+    double sc;
+    if (!chain_viterbi<double>(V, 300.0, 1.0, back, v, &sc) || !duplex_tm(v, V.c, L, R, &t)) return kChainUndefined;
+  }
+  double lam = t + 273.15 - shift, best_t = t;
+  // single-precision search: stop when the pass proposes no variant with a larger exact Tm
   for (int it = 0; it < 64; ++it) {
-    if (!viterbi(lam, 1.0, &sc)) break;
+    if (!chain_viterbi<float>(V, (float)lam, 1.f, back, v, &scf)) break;
+    double tn;
+    if (!duplex_tm(v, V.c, L, R, &tn)) break;
+    const double nl = tn + 273.15 - shift;
+    if (!(nl > lam)) break;
+    lam = nl;
+    best_t = tn;
+  }
+  // double-precision confirmation (and continuation, should single precision have stopped short)
+  for (int it = 0; it < 64; ++it) {
+    double sc;
+    if (!chain_viterbi<double>(V, lam, 1.0, back, v, &sc)) break;
     // score + lam * (Sc + S0) - 1000 * H0 = lam * D(v) - N(v) for the maximising variant
     const double F = sc + lam * (Sc + S0) - 1000.0 * H0;
     if (F <= 1e-7) break;
-    if (!duplex_tm(v, V.c, L, R, &t)) break;
-    const double nl = t + 273.15 - shift;
+    double tn;
+    if (!duplex_tm(v, V.c, L, R, &tn)) break;
+    const double nl = tn + 273.15 - shift;
     if (!(nl > lam)) break;
     lam = nl;
-    best_t = t;
+    best_t = tn;
   }
   *out = best_t;
   return kChainOk;
@@ -516,13 +590,41 @@ __device__ __forceinline__ uint8_t base_code(const uint2* planes, uint64_t group
   return (uint8_t)(((w.x >> bit) & 1u) | (((w.y >> bit) & 1u) << 1));
 }
 
-__global__ void k_tm_hits(const ah_hit* __restrict__ hits, uint64_t n, const uint2* __restrict__ planes,
+// Sites arrive in (pair, record, pos, orient) order, so neighbouring sites alternate between the
+// pair's two primers, whose chains differ in shape.  Each block first sorts its sites by primer in
+// shared memory (bitonic, kTmBlock keys), so that a warp walks one primer's chain in step.
+constexpr int kTmBlock = 128;
+
+__global__ void __launch_bounds__(kTmBlock) k_tm_hits(const ah_hit* __restrict__ hits, uint64_t n,
+                          const uint2* __restrict__ planes,
                           const uint64_t* __restrict__ rec_group, const uint8_t* __restrict__ plen,
                           const uint8_t* __restrict__ psets, const uint8_t* __restrict__ pk, int clamp,
                           const TmRun R, double* __restrict__ out, uint32_t* status,
                           const uint64_t* __restrict__ d_n = nullptr) {
-  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || (d_n && i >= *d_n)) return;
+  __shared__ uint32_t keys[kTmBlock];
+  const uint64_t base = (uint64_t)blockIdx.x * kTmBlock;
+  const uint64_t n_here = d_n ? min(n, *d_n) : n;
+  {
+    const uint64_t i = base + threadIdx.x;
+    // key: primer (pair * 2 + primer, < 512), then the site's slot in the block; empty slots last
+    keys[threadIdx.x] = i < n_here ? (((uint32_t)(hits[i].pattern >> 2) * 2u + (hits[i].pattern & 1u)) << 16) |
+                                         threadIdx.x
+                                   : 0xFFFFFFFFu;
+  }
+  __syncthreads();
+  for (int size = 2; size <= kTmBlock; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const int t = threadIdx.x, o = t ^ stride;
+      if (o > t) {
+        const uint32_t x = keys[t], y = keys[o];
+        const bool up = (t & size) == 0;
+        if ((x > y) == up) keys[t] = y, keys[o] = x;
+      }
+      __syncthreads();
+    }
+  const uint32_t key = keys[threadIdx.x];
+  if (key == 0xFFFFFFFFu) return;
+  const uint64_t i = base + (key & 0xFFFFu);
   const ah_hit h = hits[i];
   const int L = plen[h.pattern];
   const uint32_t pair = h.pattern >> 2, primer = h.pattern & 1u, strand = (h.pattern >> 1) & 1u;
@@ -647,7 +749,7 @@ void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit
                const uint8_t* pk, int clamp, uint32_t* status, const uint2* planes, const uint64_t* rec_group, const uint8_t* plen, const uint8_t* psets, double* hit_tm,
                ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep) {
   const TmRun R = *(const TmRun*)run;
-  k_tm_hits<<<(unsigned)std::max<uint64_t>(1, (hit_cap + 127) / 128), 128, 0, s>>>(hits, hit_cap, planes, rec_group,
+  k_tm_hits<<<(unsigned)std::max<uint64_t>(1, (hit_cap + kTmBlock - 1) / kTmBlock), kTmBlock, 0, s>>>(hits, hit_cap, planes, rec_group,
                                                                                   plen, psets, pk, clamp, R, hit_tm,
                                                                                   status, d_nhits);
   k_tm_amps<<<(unsigned)std::max<uint64_t>(1, (amp_cap + 255) / 256), 256, 0, s>>>(amps, amp_cap, hit_tm, filter,
@@ -669,7 +771,7 @@ ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const a
   uint32_t* keep = nullptr;
   if ((st = dalloc(ctx, &hit_tm, h->n))) return st;
   if (h->n)
-    k_tm_hits<<<(unsigned)((h->n + 127) / 128), 128, 0, ctx->stream>>>(h->d, h->n, b->planes, b->rec_group, p->d_plen,
+    k_tm_hits<<<(unsigned)((h->n + kTmBlock - 1) / kTmBlock), kTmBlock, 0, ctx->stream>>>(h->d, h->n, b->planes, b->rec_group, p->d_plen,
                                                                       p->d_psets, p->d_pk, p->clamp, R, hit_tm,
                                                                       ctx->d_status);
   if (h->n) launched(ctx);
