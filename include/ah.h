@@ -74,7 +74,8 @@ void* ah_ctx_stream(const ah_ctx* ctx);
 typedef struct {
   uint64_t kernel_launches; /* kernels launched by this context since the last reset (a plan replay
                                counts every kernel node of its graph) */
-  uint64_t scan_launches;   /* launches of the scan kernel (timed ones only, for plan replays) */
+  uint64_t scan_launches;   /* scans of a batch (a scan may launch one kernel per pair group;
+                               timed ones only, for plan replays) */
   double scan_ms;           /* summed device time of those launches (timing enabled) */
   uint64_t scan_bases;      /* bases covered by those launches */
   uint64_t jit_compiles;    /* scan kernels compiled at run time (NVRTC) */
@@ -84,6 +85,13 @@ typedef struct {
 } ah_ctx_stats;
 ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out);
 ah_status ah_ctx_stats_reset(ah_ctx* ctx);
+/* Regular scans (ah_scan_primers) of this context generate kernels of at most `pairs` primer pairs
+ * each (0, the default: one kernel for every pair).  Smaller kernels compile faster and in parallel
+ * on the host's cores, which bounds the latency of a new primer set; one kernel for every pair
+ * shares more work between patterns and scans fastest.  Plans always use one kernel.  Generated
+ * kernels are cached process-wide, keyed by their source.  AH_EINVAL outside 0..256. */
+ah_status ah_ctx_set_pairs_per_kernel(ah_ctx* ctx, int pairs);
+
 /* Time every scan launch with CUDA events on the context's stream (scan_ms).  Synchronises the
  * stream to collect the timings of plan replays still pending. */
 ah_status ah_ctx_set_timing(ah_ctx* ctx, int enable);

@@ -96,6 +96,7 @@ SIGNATURES = {
     "ah_ctx_stream": (_VP, [_VP]),
     "ah_ctx_stats_get": (_I32, [_VP, ctypes.POINTER(ah_ctx_stats)]),
     "ah_ctx_stats_reset": (_I32, [_VP]),
+    "ah_ctx_set_pairs_per_kernel": (_I32, [_VP, ctypes.c_int]),
     "ah_ctx_set_timing": (_I32, [_VP, _I32]),
     "ah_ctx_set_scan_config": (_I32, [_VP, _I32, _I32, _I32, _I32]),
     "ah_pack_batch": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
@@ -196,6 +197,10 @@ def ah_ctx_stats_get(ctx) -> dict:
 
 def ah_ctx_stats_reset(ctx) -> None:
     _check(load().ah_ctx_stats_reset(ctx), ctx)
+
+
+def ah_ctx_set_pairs_per_kernel(ctx, pairs: int) -> None:
+    _check(load().ah_ctx_set_pairs_per_kernel(ctx, int(pairs)), ctx)
 
 
 def ah_ctx_set_timing(ctx, enable: bool) -> None:

@@ -310,7 +310,7 @@ ah_status ah_ctx_create(ah_ctx** out, int device, void* cuda_stream) {
     uint64_t threshold = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
   }
-  ctx->jit.reset(new JitCache());
+  ctx->jit = &JitCache::global();
   *out = ctx;
   return AH_OK;
 }
@@ -319,7 +319,7 @@ void ah_ctx_destroy(ah_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  ctx->jit.reset();
+  ctx->jit = nullptr;
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->d_status) cudaFree(ctx->d_status);
@@ -369,6 +369,13 @@ ah_status ah_ctx_set_scan_config(ah_ctx* ctx, int threads, int groups_per_thread
   ctx->scan_cfg.groups_per_thread = groups_per_thread;
   ctx->scan_cfg.slot_cap = slot_cap;
   ctx->scan_cfg.shift_mode = shift_mode;
+  return AH_OK;
+}
+
+ah_status ah_ctx_set_pairs_per_kernel(ah_ctx* ctx, int pairs) {
+  if (!ctx) return AH_EINVAL;
+  if (pairs < 0 || pairs > 256) return fail(ctx, AH_EINVAL, "ah_ctx_set_pairs_per_kernel: 0..256");
+  ctx->scan_cfg.pairs_per_kernel = pairs;
   return AH_OK;
 }
 

@@ -52,6 +52,8 @@ struct ScanConfig {
   int shift_mode = 0;       // pattern-position alignment: 0 funnel shifts (ALU pipe), 1 multiply pairs
                             // (FMA pipe), 2 alternate the two
   int persistent = 0;       // 1: CTAs loop over tiles taken from a device counter
+  int pairs_per_kernel = 0; // regular scans: kernels of at most this many pairs, compiled in parallel
+                            // and launched one after another (0: one kernel for every pair)
 };
 
 class JitCache;
@@ -65,7 +67,8 @@ struct ah_ctx {
   std::string err;
   uint32_t* d_status = nullptr;      // device status word
   uint32_t* h_status = nullptr;      // pinned mirror
-  std::unique_ptr<ah::JitCache> jit;
+  ah::JitCache* jit = nullptr;       // the process-wide kernel cache
+  std::mutex stats_mu;               // compile counters are updated from compile threads
   ah::ScanConfig scan_cfg;
   int sm_count = 0;
   // diagnostics
@@ -222,13 +225,25 @@ struct ScanKernel {
   int alu_ops_per_group = 0;  // LOP3 + funnel-shift instructions of the generated circuit per 32 positions
 };
 std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg, int* alu_ops_per_group = nullptr);
+// Generated scan kernels, one process-wide cache keyed by source text: a kernel is compiled once,
+// callers that ask for it while it compiles wait for that compile.  Kernels stay loaded for the
+// life of the process.
 class JitCache {
  public:
+  static JitCache& global();
   ah_status get(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out);
-  ~JitCache();
+  // several pattern sets, the missing kernels compiled on parallel host threads
+  ah_status get_many(ah_ctx* ctx, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg,
+                     std::vector<ScanKernel>* out);
  private:
+  struct Entry;
+  ah_status get_impl(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out,
+                     std::string* err);
   std::mutex mu_;
-  std::unordered_map<std::string, std::pair<cudaLibrary_t, ScanKernel>> cache_;
+  std::unordered_map<std::string, std::shared_ptr<Entry>> cache_;
 };
+
+// the pattern sets a scan with cfg.pairs_per_kernel launches, in pair order
+std::vector<std::vector<Pattern>> scan_groups(const std::vector<Pattern>& pats, const ScanConfig& cfg);
 
 }  // namespace ah

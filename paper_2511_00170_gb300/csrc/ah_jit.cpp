@@ -20,7 +20,10 @@
 #include <chrono>
 #include <cstdarg>
 #include <cstring>
+#include <atomic>
+#include <condition_variable>
 #include <map>
+#include <thread>
 #include <sstream>
 
 #include "ah_internal.h"
@@ -377,22 +380,34 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg,
   return os.str();
 }
 
-ah_status JitCache::get(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out) {
-  int ops = 0;
-  std::string src = scan_source(pats, cfg, &ops);
-  std::lock_guard<std::mutex> lock(mu_);
-  auto it = cache_.find(src);
-  if (it != cache_.end()) {
-    *out = it->second.second;
-    return AH_OK;
-  }
-  const auto t0 = std::chrono::steady_clock::now();
+struct JitCache::Entry {
+  std::mutex m;
+  std::condition_variable cv;
+  bool done = false;
+  ah_status st = AH_OK;
+  std::string err;
+  ScanKernel k{};
+};
+
+JitCache& JitCache::global() {
+  static JitCache* cache = new JitCache();  // never destroyed: kernels stay loaded until exit
+  return *cache;
+}
+
+namespace {
+
+// NVRTC for this device's architecture, then the runtime's library API (no link-time driver
+// dependency); fills k or returns a message
+ah_status compile(int device, const std::string& src, int ops, const ScanConfig& cfg, ScanKernel* k,
+                  std::string* err) {
   nvrtcProgram prog;
-  if (nvrtcCreateProgram(&prog, src.c_str(), "ah_scan_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
-    return fail(ctx, AH_EJIT, "nvrtcCreateProgram failed");
+  if (nvrtcCreateProgram(&prog, src.c_str(), "ah_scan_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+    *err = "nvrtcCreateProgram failed";
+    return AH_EJIT;
+  }
   int major = 0, minor = 0;
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, ctx->device);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, ctx->device);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
   std::string arch = "-arch=sm_" + std::to_string(major * 10 + minor) + (major >= 9 ? "a" : "");
   const char* opts[] = {arch.c_str(), "-default-device", "-lineinfo"};
   nvrtcResult r = nvrtcCompileProgram(prog, 3, opts);
@@ -402,32 +417,120 @@ ah_status JitCache::get(ah_ctx* ctx, const std::vector<Pattern>& pats, const Sca
     std::string log(n, '\0');
     nvrtcGetProgramLog(prog, &log[0]);
     nvrtcDestroyProgram(&prog);
-    return fail(ctx, AH_EJIT, "scan kernel compilation failed: %s", log.substr(0, 2000).c_str());
+    *err = "scan kernel compilation failed: " + log.substr(0, 2000);
+    return AH_EJIT;
   }
   size_t cubin_size = 0;
   nvrtcGetCUBINSize(prog, &cubin_size);
   std::vector<char> cubin(cubin_size);
   nvrtcGetCUBIN(prog, cubin.data());
   nvrtcDestroyProgram(&prog);
-  // the runtime's library API keeps the engine free of a link-time driver dependency
+  cudaSetDevice(device);
   cudaLibrary_t lib;
   cudaError_t ce = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-  if (ce != cudaSuccess) return fail(ctx, AH_EJIT, "cudaLibraryLoadData failed: %s", cudaGetErrorString(ce));
-  ScanKernel k;
-  ce = cudaLibraryGetKernel(&k.fn, lib, "ah_scan_jit");
-  if (ce != cudaSuccess) return fail(ctx, AH_EJIT, "cudaLibraryGetKernel failed: %s", cudaGetErrorString(ce));
-  k.threads = cfg.threads;
-  k.groups_per_thread = cfg.groups_per_thread;
-  k.alu_ops_per_group = ops;
-  ctx->jit_compiles++;
-  ctx->jit_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  cache_.emplace(src, std::make_pair(lib, k));
-  *out = k;
+  if (ce != cudaSuccess) {
+    *err = std::string("cudaLibraryLoadData failed: ") + cudaGetErrorString(ce);
+    return AH_EJIT;
+  }
+  ce = cudaLibraryGetKernel(&k->fn, lib, "ah_scan_jit");
+  if (ce != cudaSuccess) {
+    *err = std::string("cudaLibraryGetKernel failed: ") + cudaGetErrorString(ce);
+    return AH_EJIT;
+  }
+  k->threads = cfg.threads;
+  k->groups_per_thread = cfg.groups_per_thread;
+  k->alu_ops_per_group = ops;
   return AH_OK;
 }
 
-JitCache::~JitCache() {
-  for (auto& kv : cache_) cudaLibraryUnload(kv.second.first);
+}  // namespace
+
+ah_status JitCache::get(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out) {
+  std::string err;
+  const ah_status st = get_impl(ctx, pats, cfg, out, &err);
+  return st ? fail(ctx, st, "%s", err.c_str()) : AH_OK;
+}
+
+ah_status JitCache::get_impl(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out,
+                             std::string* err_out) {
+  int ops = 0;
+  std::string src = scan_source(pats, cfg, &ops);
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, ctx->device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, ctx->device);
+  const std::string key = std::to_string(major * 10 + minor) + "\n" + src;
+  std::shared_ptr<Entry> e;
+  bool mine = false;
+  {
+    std::lock_guard<std::mutex> lock(mu_);
+    auto it = cache_.find(key);
+    if (it == cache_.end()) {
+      e = std::make_shared<Entry>();
+      cache_.emplace(key, e);
+      mine = true;
+    } else {
+      e = it->second;
+    }
+  }
+  if (mine) {
+    const auto t0 = std::chrono::steady_clock::now();
+    ScanKernel k;
+    std::string err;
+    const ah_status st = compile(ctx->device, src, ops, cfg, &k, &err);
+    {
+      std::lock_guard<std::mutex> lock(e->m);
+      e->st = st;
+      e->err = err;
+      e->k = k;
+      e->done = true;
+    }
+    e->cv.notify_all();
+    if (st) {
+      std::lock_guard<std::mutex> lock(mu_);
+      cache_.erase(key);  // a later call may try again
+    } else {
+      std::lock_guard<std::mutex> lock(ctx->stats_mu);
+      ctx->jit_compiles++;
+      ctx->jit_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+  }
+  std::unique_lock<std::mutex> lock(e->m);
+  e->cv.wait(lock, [&] { return e->done; });
+  if (e->st) {
+    *err_out = e->err;
+    return e->st;
+  }
+  *out = e->k;
+  return AH_OK;
+}
+
+ah_status JitCache::get_many(ah_ctx* ctx, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg,
+                             std::vector<ScanKernel>* out) {
+  out->assign(sets.size(), ScanKernel{});
+  if (sets.size() == 1) return get(ctx, sets[0], cfg, &(*out)[0]);
+  std::vector<ah_status> st(sets.size(), AH_OK);
+  std::vector<std::string> err(sets.size());
+  const size_t width = std::max<size_t>(1, std::min<size_t>(sets.size(), std::thread::hardware_concurrency()));
+  std::atomic<size_t> next{0};
+  std::vector<std::thread> pool;
+  for (size_t w = 0; w < width; ++w)
+    pool.emplace_back([&] {
+      cudaSetDevice(ctx->device);
+      for (size_t i = next++; i < sets.size(); i = next++) st[i] = get_impl(ctx, sets[i], cfg, &(*out)[i], &err[i]);
+    });
+  for (auto& t : pool) t.join();
+  for (size_t i = 0; i < sets.size(); ++i)
+    if (st[i]) return fail(ctx, st[i], "%s", err[i].c_str());
+  return AH_OK;
+}
+
+std::vector<std::vector<Pattern>> scan_groups(const std::vector<Pattern>& pats, const ScanConfig& cfg) {
+  std::vector<std::vector<Pattern>> out;
+  const size_t per = cfg.pairs_per_kernel > 0 ? 4 * (size_t)cfg.pairs_per_kernel : pats.size();
+  for (size_t i = 0; i < pats.size(); i += per)
+    out.emplace_back(pats.begin() + i, pats.begin() + std::min(pats.size(), i + per));
+  if (out.empty()) out.emplace_back();
+  return out;
 }
 
 }  // namespace ah

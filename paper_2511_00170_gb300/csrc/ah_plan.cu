@@ -267,6 +267,7 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
   pl->p = p;
   pl->prm = *prm;
   pl->cfg = ctx->scan_cfg;
+  pl->cfg.pairs_per_kernel = 0;  // a plan captures one scan kernel over every pair
   ah_status st = tm_prepare(ctx, &prm->tm, pl->tm_run, sizeof pl->tm_run);
   for (int i = 0; i < 2 && !st; ++i)
     if (cudaEventCreate(&pl->scan_ev[i]) != cudaSuccess) st = fail(ctx, AH_ECUDA, "ah_plan_create: event creation failed");

@@ -202,31 +202,35 @@ ah_status launch_scan(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const
                       uint64_t tile_groups, uint64_t n_tiles, uint64_t* slots, uint32_t* tile_count, uint32_t cap) {
   ah_status st;
   if (!per_record) {
-    ScanKernel kern;
-    if ((st = ctx->jit->get(ctx, p->pats, cfg, &kern))) return st;
+    // one kernel for every pair, or (cfg.pairs_per_kernel) kernels of a few pairs each, compiled in
+    // parallel and launched one after another into the same tile slot lists
+    std::vector<ScanKernel> kerns;
+    if ((st = ctx->jit->get_many(ctx, scan_groups(p->pats, cfg), cfg, &kerns))) return st;
     unsigned long long* work = nullptr;
-    if (cfg.persistent) {
-      if ((st = dalloc(ctx, &work, 1))) return st;
-      AH_CUDA(ctx, cudaMemsetAsync(work, 0, sizeof *work, ctx->stream));
-    }
+    if (cfg.persistent && (st = dalloc(ctx, &work, 1))) return st;
     if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
-    for (uint64_t t0 = 0; t0 < n_tiles; t0 += 0x7fffffffull) {
-      const uint64_t nt = std::min<uint64_t>(0x7fffffffull, n_tiles - t0);
-      const uint64_t g0 = t0 * tile_groups;
-      ScanParamsHost P{b->planes, b->invalid, b->rec_group, b->rec_len, b->n_records, cap, g0,
-                       std::min<uint64_t>(b->n_groups - std::min(b->n_groups, g0), nt * tile_groups),
-                       slots, tile_count, ctx->d_status, tile_groups, work, nt};
-      void* args[] = {&P};
-      const unsigned grid = cfg.persistent ? (unsigned)std::min<uint64_t>(nt, persistent_grid(ctx, kern)) : (unsigned)nt;
-      cudaError_t le = cudaLaunchKernel((const void*)kern.fn, dim3(grid), dim3((unsigned)cfg.threads), args, 0,
-                                        ctx->stream);
-      if (le != cudaSuccess) return fail(ctx, AH_ECUDA, "scan kernel launch failed: %s", cudaGetErrorString(le));
-      launched(ctx);
-      ctx->n_scan_launches++;
-      ctx->scan_ops_per_group = kern.alu_ops_per_group;
-      if (cfg.persistent && t0 + nt < n_tiles) AH_CUDA(ctx, cudaMemsetAsync(work, 0, sizeof *work, ctx->stream));
+    int ops = 0;
+    for (const ScanKernel& kern : kerns) {
+      for (uint64_t t0 = 0; t0 < n_tiles; t0 += 0x7fffffffull) {
+        const uint64_t nt = std::min<uint64_t>(0x7fffffffull, n_tiles - t0);
+        const uint64_t g0 = t0 * tile_groups;
+        if (cfg.persistent) AH_CUDA(ctx, cudaMemsetAsync(work, 0, sizeof *work, ctx->stream));
+        ScanParamsHost P{b->planes, b->invalid, b->rec_group, b->rec_len, b->n_records, cap, g0,
+                         std::min<uint64_t>(b->n_groups - std::min(b->n_groups, g0), nt * tile_groups),
+                         slots, tile_count, ctx->d_status, tile_groups, work, nt};
+        void* args[] = {&P};
+        const unsigned grid =
+            cfg.persistent ? (unsigned)std::min<uint64_t>(nt, persistent_grid(ctx, kern)) : (unsigned)nt;
+        cudaError_t le = cudaLaunchKernel((const void*)kern.fn, dim3(grid), dim3((unsigned)cfg.threads), args, 0,
+                                          ctx->stream);
+        if (le != cudaSuccess) return fail(ctx, AH_ECUDA, "scan kernel launch failed: %s", cudaGetErrorString(le));
+        launched(ctx);
+      }
+      ops += kern.alu_ops_per_group;
     }
     if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
+    ctx->n_scan_launches++;          // passes over the batch
+    ctx->scan_ops_per_group = ops;   // all patterns, per 32 positions
     dfree(ctx, work);
     ctx->scan_bases += b->n_bases;
     return AH_OK;

@@ -178,6 +178,9 @@ ah_status ah_server_create(const ah_batch* db, int n_slots, uint64_t memory_budg
       return st;
     }
     c->scan_cfg.slot_cap = 64;  // requests are sparse; dense tiles are re-run with room
+    // a request's primer set is compiled as kernels of 4 pairs on parallel host threads: a cold
+    // 32-pair set compiles in about the time of one 4-pair kernel instead of 8x longer
+    c->scan_cfg.pairs_per_kernel = 4;
     s->ctxs.push_back(c);
   }
   for (int i = 0; i < n_slots; ++i) s->workers.emplace_back(worker, s, i);

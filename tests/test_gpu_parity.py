@@ -355,3 +355,17 @@ def test_pack_paths_agree(engine, big):
     finally:
         for x in (host, in_place, dev, streamed, streamed_host):
             ah.ah_batch_free(x)
+
+
+@pytest.mark.parametrize("pairs_per_kernel", [1, 3])
+def test_pairs_per_kernel(engine, pairs_per_kernel):
+    """Scans split into kernels of a few pairs each (compiled in parallel, launched in turn into the
+    same tile slot lists) give the oracle's outputs, as one kernel for every pair does."""
+    from paper_2511_00170_gb300 import ah
+
+    wl = synth.batched(n_genomes=24, len_lo=2e3, len_hi=2e5, n_pairs=7)
+    ah.ah_ctx_set_pairs_per_kernel(engine.ctx, pairs_per_kernel)
+    try:
+        _run_both(engine, wl)
+    finally:
+        ah.ah_ctx_set_pairs_per_kernel(engine.ctx, 0)
