@@ -274,8 +274,9 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
   const auto t0 = std::chrono::steady_clock::now();
   uint64_t n_hits = 0;
   if (!st && prm->autotune) {
-    // candidate shapes x alignment modes, then the persistent form of the best
-    const int shapes[][2] = {{128, 8}, {256, 4}, {128, 4}, {256, 8}};
+    // candidate shapes x alignment modes, then the persistent form of the best; a candidate replaces
+    // the incumbent only when it is at least 3 % faster, so near-equal shapes do not flip between runs
+    const int shapes[][2] = {{256, 8}, {128, 8}, {256, 4}, {128, 4}};
     double best = 1e30;
     ScanConfig win = pl->cfg;
     for (int mode = 0; mode < 2 && !st; ++mode) {
@@ -287,14 +288,15 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
         c.persistent = 0;
         double ms = 0;
         if ((st = time_shape(ctx, b, p, c, 2, &ms, &n_hits))) break;
-        if (ms < best) best = ms, win = c;
+        if (ms < best * 0.97) best = ms, win = c;
       }
     }
     if (!st && prm->persistent != 0) {
       ScanConfig c = win;
       c.persistent = 1;
       double ms = 0;
-      if (!(st = time_shape(ctx, b, p, c, 2, &ms, &n_hits)) && (ms < best || prm->persistent > 0)) best = ms, win = c;
+      if (!(st = time_shape(ctx, b, p, c, 2, &ms, &n_hits)) && (ms < best * 0.97 || prm->persistent > 0))
+        best = ms, win = c;
     }
     pl->cfg = win;
     pl->info.best_scan_ms = best;
