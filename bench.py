@@ -60,7 +60,7 @@ def alg_ops_per_base(fwd, rev, clamp):
 # what identifies the kernel: LOP3/SHF per 32 positions of its circuit, threads, groups per thread,
 # shift mode, persistent.  A kernel not in this table reports traffic null.
 SCAN_TRAFFIC = {
-    (178, 256, 8, 0, 0): 1_892_938_240 / 7_536_412_189,
+    (178, 256, 8, 0, 0): 1_910_984_960 / 7_536_412_189,
 }
 
 
