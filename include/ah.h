@@ -132,10 +132,11 @@ typedef struct {
 
 /* Pack host ASCII records.  seqs[i] points at lens[i] characters (no terminator needed);
  * genome_ids may be NULL (then record i has genome id i).  Characters other than ACGTacgt are
- * invalid bases.  Records in page-locked host memory (cudaHostAlloc, cudaHostRegister, pinned
- * tensors) are read in place by the packing kernel over the host link, at any alignment.  Other
- * records are copied to the device in chunks of 64 Mi bases (16 MB packed) on a second stream and
- * packed while the next chunk is in flight.  Synchronises the stream before
+ * invalid bases.  Records are copied to the device by the copy engines in chunks of up to 64 Mi
+ * bases (16 MB packed), one copy per run of records contiguous in host memory, on a second stream,
+ * and each chunk is packed from device memory while the next one is in flight; page-locked host
+ * memory (cudaHostAlloc, cudaHostRegister, pinned tensors) moves at the full host-link rate.
+ * Records already in device memory are packed in place.  Synchronises the stream before
  * returning (the host buffers may be reused afterwards).  AH_EINVAL: n_rec == 0, a record longer
  * than 2^32-1 bases, or a NULL pointer with a nonzero length. */
 ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, const uint64_t* lens,
@@ -150,8 +151,8 @@ ah_status ah_pack_batch_device(ah_ctx* ctx, uint32_t n_rec, const uint8_t* d_seq
 /* Streaming: lay out a batch for n_rec records of the given lengths (device memory allocated, nothing
  * packed), then pack consecutive record ranges into it with ah_batch_pack_range.  Synchronises. */
 ah_status ah_batch_create(ah_ctx* ctx, uint32_t n_rec, const uint64_t* lens, const uint32_t* genome_ids, ah_batch** out);
-/* Pack records [first, first + count) of b: d_seq holds them back to back in device memory or in
- * page-locked host memory (read in place over the host link), at any alignment, and h_offsets
+/* Pack records [first, first + count) of b: d_seq holds them back to back, at any alignment, in
+ * device memory (packed in place) or host memory (copied in chunks as ah_pack_batch does), and h_offsets
  * (host, count + 1 entries, starting at 0) delimits them; their lengths must match the layout.
  * Repacking a batch that a plan was created on refreshes the plan's input.  Synchronises (d_seq
  * may be released afterwards). */
@@ -372,6 +373,13 @@ ah_status ah_plan_check(ah_plan* plan);
 /* Launch and check, growing capacities and re-capturing on overflow. */
 ah_status ah_plan_run(ah_plan* plan);
 ah_status ah_plan_info_get(const ah_plan* plan, ah_plan_info* out);
+/* Copy the last run's sites, amplicons (the kept ones when the Tm filter is on) and, with
+ * extraction, the sequence arena and its 5n+1 field offsets straight from the plan's buffers into
+ * caller memory (any host memory; page-locked is fastest).  Capacities are in elements (bytes for
+ * the arena); a NULL buffer skips that output.  Checks the run like ah_plan_check first, then
+ * AH_EOVERFLOW if a buffer is too small (ah_plan_info_get then gives the counts).  Synchronises. */
+ah_status ah_plan_copy_results(ah_plan* plan, ah_hit* hits, uint64_t hits_cap, ah_amplicon* amps, uint64_t amps_cap,
+                               char* arena, uint64_t arena_cap, uint64_t* field_off, uint64_t field_off_cap);
 /* Copies of the last run's sites and (kept) amplicons, with sequences when extraction is on. */
 ah_status ah_plan_results(ah_plan* plan, ah_hits** hits, ah_amplicons** amps);
 void ah_plan_free(ah_plan* plan);

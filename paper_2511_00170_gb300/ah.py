@@ -131,6 +131,7 @@ SIGNATURES = {
     "ah_plan_check": (_I32, [_VP]),
     "ah_plan_run": (_I32, [_VP]),
     "ah_plan_info_get": (_I32, [_VP, ctypes.POINTER(ah_plan_info)]),
+    "ah_plan_copy_results": (_I32, [_VP, _VP, _U64, _VP, _U64, _VP, _U64, _VP, _U64]),
     "ah_plan_results": (_I32, [_VP, _PVP, _PVP]),
     "ah_plan_free": (None, [_VP]),
     "ah_server_create": (_I32, [_VP, _I32, _U64, _PVP]),
@@ -448,6 +449,16 @@ def ah_plan_info_get(plan) -> dict:
     i = ah_plan_info()
     _check(load().ah_plan_info_get(plan, ctypes.byref(i)))
     return {f: getattr(i, f) for f, _ in ah_plan_info._fields_}
+
+
+def ah_plan_copy_results(plan, ctx, hits: Optional[np.ndarray], amps: Optional[np.ndarray],
+                         arena: Optional[np.ndarray], field_off: Optional[np.ndarray]) -> None:
+    """Copy the last run's results into caller arrays (HIT_DTYPE, AMP_DTYPE, uint8, uint64; any may be
+    None); the counts are in ah_plan_info_get afterwards."""
+    def buf(a):
+        return (None, 0) if a is None else (a.ctypes.data, len(a))
+    h, a, r, f = buf(hits), buf(amps), buf(arena), buf(field_off)
+    _check(load().ah_plan_copy_results(plan, h[0], h[1], a[0], a[1], r[0], r[1], f[0], f[1]), ctx)
 
 
 def ah_plan_results(plan, ctx=None):

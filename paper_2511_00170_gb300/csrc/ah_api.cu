@@ -390,6 +390,125 @@ ah_status ah_ctx_set_timing(ah_ctx* ctx, int enable) {
 }
 
 // ------------------------------------------------------------------------------------------
+namespace {
+
+// Pack records first .. first + n - 1 of b, record first + i read from src[i] (b's layout gives the
+// lengths).  Records in device memory are read in place by the packing kernel.  Host records (page-
+// locked or not) go through the copy engines: consecutive pieces that are contiguous in host memory
+// become one copy per chunk of up to kChunkBases bases, into one of two staging buffers on a second
+// stream, while the context's stream packs the previous chunk from HBM.  Synchronises.
+ah_status pack_records(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t n, const char* const* src) {
+  bool on_device = true;
+  std::vector<uint64_t> dev_addr(n, 0);
+  for (uint32_t i = 0; i < n && on_device; ++i) {
+    if (!b->h_rec_len[first + i]) continue;
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, src[i]) != cudaSuccess) {
+      cudaGetLastError();
+      on_device = false;
+      break;
+    }
+    if ((pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) && pa.devicePointer &&
+        pa.device == ctx->device)
+      dev_addr[i] = (uint64_t)(uintptr_t)pa.devicePointer;
+    else
+      on_device = false;
+  }
+  if (on_device) {
+    std::vector<PackItem> items;
+    for (uint32_t i = 0; i < n; ++i) add_items(items, b, first + i, 0, b->h_rec_len[first + i], dev_addr[i]);
+    return run_pack(ctx, nullptr, items, b);
+  }
+  // chunks of host pieces (records split on group boundaries), each piece at the staging offset that
+  // continues the previous one, so a run of pieces contiguous in host memory is one copy
+  struct Run {
+    const char* src;
+    uint64_t bytes, stage_off;
+  };
+  std::vector<std::vector<Run>> runs(1);
+  std::vector<std::vector<PackItem>> items(1);
+  uint64_t fill = 0, stage_max = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t r = first + i;
+    const uint64_t len = b->h_rec_len[r];
+    uint64_t done = 0;
+    if (len == 0) add_items(items.back(), b, r, 0, 0, 0);  // its padding groups (nothing is read)
+    while (done < len) {
+      uint64_t take = std::min(kChunkBases - std::min(fill, kChunkBases), len - done);
+      if (take < len - done) take &= ~uint64_t(31);  // split records on group boundaries
+      if (take == 0) {
+        runs.emplace_back();
+        items.emplace_back();
+        fill = 0;
+        continue;
+      }
+      const char* sp = src[i] + done;
+      std::vector<Run>& rv = runs.back();
+      if (!rv.empty() && rv.back().src + rv.back().bytes == sp && rv.back().stage_off + rv.back().bytes == fill)
+        rv.back().bytes += take;
+      else
+        rv.push_back({sp, take, fill});
+      add_items(items.back(), b, r, done, done + take, fill);
+      fill += take;
+      stage_max = std::max(stage_max, fill);
+      done += take;
+    }
+  }
+  std::vector<PackItem> all;
+  std::vector<size_t> at;
+  for (auto& v : items) {
+    at.push_back(all.size());
+    all.insert(all.end(), v.begin(), v.end());
+  }
+  if (all.empty()) return AH_OK;
+  ah_status st = AH_OK;
+  uint8_t* staging[2] = {nullptr, nullptr};
+  PackItem* d_items = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, packed[2] = {nullptr, nullptr};
+  // 16 bytes of slack: the packing kernel reads whole aligned 16-byte words around its bytes
+  if (!st) st = dalloc(ctx, &staging[0], stage_max + 16);
+  if (!st && runs.size() > 1) st = dalloc(ctx, &staging[1], stage_max + 16);
+  if (!st) st = dalloc(ctx, &d_items, all.size());
+  cudaError_t e = cudaSuccess;
+  if (!st) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess && !st; ++k) {
+    e = cudaEventCreateWithFlags(&copied[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&packed[k], cudaEventDisableTiming);
+  }
+  if (!st && e == cudaSuccess)
+    e = cudaMemcpyAsync(d_items, all.data(), all.size() * sizeof(PackItem), cudaMemcpyHostToDevice, ctx->stream);
+  for (size_t c = 0; c < runs.size() && !st && e == cudaSuccess; ++c) {
+    const int w = (int)(c & 1);
+    if (c >= 2) e = cudaStreamWaitEvent(cs, packed[w], 0);  // the buffer's previous chunk is packed
+    for (const Run& rn : runs[c]) {
+      if (e != cudaSuccess) break;
+      e = cudaMemcpyAsync(staging[w] + rn.stage_off, rn.src, rn.bytes, cudaMemcpyHostToDevice, cs);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(copied[w], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, copied[w], 0);
+    if (e == cudaSuccess && !items[c].empty())
+      launch_pack(ctx->stream, staging[w], d_items + at[c], items[c].data(), items[c].size(), b, ctx);
+    if (e == cudaSuccess) e = cudaEventRecord(packed[w], ctx->stream);
+  }
+  if (!st && e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (!st && e != cudaSuccess) st = fail(ctx, AH_ECUDA, "packing failed: %s", cudaGetErrorString(e));
+  if (cs) {
+    cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
+  }
+  for (int k = 0; k < 2; ++k) {
+    if (copied[k]) cudaEventDestroy(copied[k]);
+    if (packed[k]) cudaEventDestroy(packed[k]);
+  }
+  dfree(ctx, staging[0]);
+  dfree(ctx, staging[1]);
+  dfree(ctx, d_items);
+  return st;
+}
+
+}  // namespace
+
 ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, const uint64_t* lens,
                         const uint32_t* genome_ids, ah_batch** out) {
   if (!ctx || !out || !lens || (n_rec && !seqs) || n_rec == 0) return fail(ctx, AH_EINVAL, "ah_pack_batch: bad arguments");
@@ -399,120 +518,7 @@ ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, co
   cudaSetDevice(ctx->device);
   ah_batch* b = new ah_batch();
   ah_status st = layout_batch(ctx, n_rec, lens, genome_ids, b);
-  if (st) {
-    free_batch_arrays(b);
-    delete b;
-    return st;
-  }
-  // Records in page-locked host memory (or device memory) are read by the pack kernels in place:
-  // one pass over the host link, no staging copies.
-  bool in_place = true;
-  std::vector<uint64_t> dev_addr(n_rec, 0);
-  for (uint32_t r = 0; r < n_rec && in_place; ++r) {
-    if (!lens[r]) continue;
-    cudaPointerAttributes pa;
-    if (cudaPointerGetAttributes(&pa, seqs[r]) != cudaSuccess) {
-      cudaGetLastError();
-      in_place = false;
-      break;
-    }
-    const bool reachable = (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeDevice ||
-                            pa.type == cudaMemoryTypeManaged) && pa.devicePointer != nullptr &&
-                           (pa.type == cudaMemoryTypeHost || pa.device == ctx->device);
-    if (!reachable) in_place = false;
-    else dev_addr[r] = (uint64_t)(uintptr_t)pa.devicePointer;
-  }
-  if (in_place) {
-    std::vector<PackItem> items;
-    for (uint32_t r = 0; r < n_rec; ++r) add_items(items, b, r, 0, lens[r], dev_addr[r]);
-    st = run_pack(ctx, nullptr, items, b);
-    if (st) {
-      free_batch_arrays(b);
-      delete b;
-      return st;
-    }
-    *out = b;
-    return AH_OK;
-  }
-  // Otherwise records (split on group boundaries) fill chunks of up to kChunkBases bases, each piece
-  // at a 16-byte aligned offset of its chunk's staging buffer, copied on a second stream.
-  struct Piece {
-    const char* src;
-    uint64_t bytes, stage_off;
-  };
-  std::vector<std::vector<Piece>> pieces(1);
-  std::vector<std::vector<PackItem>> items(1);
-  uint64_t fill = 0, stage_max = 0;
-  for (uint32_t r = 0; r < n_rec; ++r) {
-    uint64_t len = lens[r], done = 0;
-    if (len == 0) add_items(items.back(), b, r, 0, 0, 0);  // its padding groups (nothing is read)
-    while (done < len) {
-      uint64_t room = kChunkBases - std::min(fill, kChunkBases);
-      uint64_t take = std::min(room, len - done);
-      if (take < len - done) take &= ~uint64_t(31);  // split records on group boundaries
-      if (take == 0) {
-        pieces.emplace_back();
-        items.emplace_back();
-        fill = 0;
-        continue;
-      }
-      const uint64_t off = (fill + 15) & ~uint64_t(15);
-      pieces.back().push_back({seqs[r] + done, take, off});
-      add_items(items.back(), b, r, done, done + take, off);
-      fill = off + take;
-      stage_max = std::max(stage_max, fill);
-      done += take;
-    }
-  }
-  // all items uploaded once; the chunks then alternate between two staging buffers: copies on a
-  // second stream, packing on the context's stream, ordered by events
-  std::vector<PackItem> all;
-  std::vector<size_t> first;
-  for (auto& v : items) {
-    first.push_back(all.size());
-    all.insert(all.end(), v.begin(), v.end());
-  }
-  uint8_t* staging[2] = {nullptr, nullptr};
-  PackItem* d_items = nullptr;
-  cudaStream_t cs = nullptr;
-  cudaEvent_t copied[2] = {nullptr, nullptr}, packed[2] = {nullptr, nullptr};
-  if (!st) st = dalloc(ctx, &staging[0], std::max<uint64_t>(stage_max, 16));
-  if (!st && pieces.size() > 1) st = dalloc(ctx, &staging[1], std::max<uint64_t>(stage_max, 16));
-  if (!st) st = dalloc(ctx, &d_items, std::max<size_t>(all.size(), 1));
-  cudaError_t e = cudaSuccess;
-  if (!st) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-  for (int i = 0; i < 2 && e == cudaSuccess && !st; ++i) {
-    e = cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&packed[i], cudaEventDisableTiming);
-  }
-  if (!st && e == cudaSuccess && !all.empty())
-    e = cudaMemcpyAsync(d_items, all.data(), all.size() * sizeof(PackItem), cudaMemcpyHostToDevice, ctx->stream);
-  for (size_t c = 0; c < pieces.size() && !st && e == cudaSuccess; ++c) {
-    const int w = (int)(c & 1);
-    if (c >= 2) e = cudaStreamWaitEvent(cs, packed[w], 0);  // the buffer's previous chunk is packed
-    for (const Piece& pc : pieces[c]) {
-      if (e != cudaSuccess) break;
-      e = cudaMemcpyAsync(staging[w] + pc.stage_off, pc.src, pc.bytes, cudaMemcpyHostToDevice, cs);
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(copied[w], cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, copied[w], 0);
-    if (e == cudaSuccess && !items[c].empty())
-      launch_pack(ctx->stream, staging[w], d_items + first[c], items[c].data(), items[c].size(), b, ctx);
-    if (e == cudaSuccess) e = cudaEventRecord(packed[w], ctx->stream);
-  }
-  if (!st && e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (!st && e != cudaSuccess) st = fail(ctx, AH_ECUDA, "packing failed: %s", cudaGetErrorString(e));
-  if (cs) {
-    cudaStreamSynchronize(cs);
-    cudaStreamDestroy(cs);
-  }
-  for (int i = 0; i < 2; ++i) {
-    if (copied[i]) cudaEventDestroy(copied[i]);
-    if (packed[i]) cudaEventDestroy(packed[i]);
-  }
-  dfree(ctx, staging[0]);
-  dfree(ctx, staging[1]);
-  dfree(ctx, d_items);
+  if (!st) st = pack_records(ctx, b, 0, n_rec, seqs);
   if (st) {
     free_batch_arrays(b);
     delete b;
@@ -609,13 +615,13 @@ ah_status ah_batch_pack_range(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t
   if (!usable(ctx, b) || count == 0 || (uint64_t)first + count > b->n_records)
     return fail(ctx, AH_EINVAL, "ah_batch_pack_range: bad record range");
   cudaSetDevice(ctx->device);
-  std::vector<PackItem> items;
+  std::vector<const char*> src(count);
   for (uint32_t i = 0; i < count; ++i) {
     if (h_offsets[i + 1] < h_offsets[i] || h_offsets[i + 1] - h_offsets[i] != b->h_rec_len[first + i])
       return fail(ctx, AH_EINVAL, "ah_batch_pack_range: record %u length differs from the layout", first + i);
-    add_items(items, b, first + i, 0, b->h_rec_len[first + i], h_offsets[i]);
+    src[i] = (const char*)d_seq + h_offsets[i];
   }
-  return run_pack(ctx, d_seq, items, b);
+  return pack_records(ctx, b, first, count, src.data());
 }
 
 ah_status ah_batch_view_get(const ah_batch* b, ah_batch_view* out) {

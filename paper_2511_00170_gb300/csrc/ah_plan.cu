@@ -448,6 +448,31 @@ ah_status ah_plan_info_get(const ah_plan* pl, ah_plan_info* out) {
   return AH_OK;
 }
 
+ah_status ah_plan_copy_results(ah_plan* pl, ah_hit* hits, uint64_t hits_cap, ah_amplicon* amps, uint64_t amps_cap,
+                               char* arena, uint64_t arena_cap, uint64_t* field_off, uint64_t field_off_cap) {
+  if (!pl) return AH_EINVAL;
+  ah_status st = ah_plan_check(pl);
+  if (st) return st;
+  ah_ctx* c = pl->ctx;
+  const ah_plan_info& i = pl->info;
+  const uint64_t nf = pl->prm.extract ? 5 * i.n_kept + 1 : 0;
+  if ((hits && hits_cap < i.n_hits) || (amps && amps_cap < i.n_kept) ||
+      (arena && pl->prm.extract && arena_cap < i.arena_bytes) || (field_off && field_off_cap < nf))
+    return fail(c, AH_EOVERFLOW, "ah_plan_copy_results: buffers smaller than the results (%llu sites, %llu amplicons, "
+                "%llu arena bytes)", (unsigned long long)i.n_hits, (unsigned long long)i.n_kept,
+                (unsigned long long)i.arena_bytes);
+  cudaStream_t s = c->stream;
+  if (hits && i.n_hits) AH_CUDA(c, cudaMemcpyAsync(hits, pl->hits, i.n_hits * sizeof(ah_hit), cudaMemcpyDeviceToHost, s));
+  if (amps && i.n_kept)
+    AH_CUDA(c, cudaMemcpyAsync(amps, pl->prm.tm.filter ? pl->kept : pl->amps, i.n_kept * sizeof(ah_amplicon),
+                               cudaMemcpyDeviceToHost, s));
+  if (arena && pl->prm.extract && i.arena_bytes)
+    AH_CUDA(c, cudaMemcpyAsync(arena, pl->arena, i.arena_bytes, cudaMemcpyDeviceToHost, s));
+  if (field_off && nf) AH_CUDA(c, cudaMemcpyAsync(field_off, pl->field_off, nf * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  AH_CUDA(c, cudaStreamSynchronize(s));
+  return AH_OK;
+}
+
 ah_status ah_plan_results(ah_plan* pl, ah_hits** hits_out, ah_amplicons** amps_out) {
   if (!pl || !hits_out || !amps_out) return AH_EINVAL;
   *hits_out = nullptr;

@@ -144,3 +144,37 @@ def test_plan_replays_are_timed_and_counted(engine):
             ah.ah_plan_free(plan)
     finally:
         ah.ah_batch_free(batch)
+
+
+def test_plan_copy_results(engine):
+    """The direct copy of a run's results into caller buffers equals the results objects, and buffers
+    that are too small are refused with AH_EOVERFLOW."""
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Params
+
+    wl = synth.batched(n_genomes=20, len_lo=5e3, len_hi=2e5, n_pairs=3)
+    wl.trim, wl.fb_len, wl.rb_len = True, 10, 7
+    p = Params.from_workload(wl)
+    batch = engine.pack(wl.seq, wl.offsets)
+    try:
+        plan = engine.plan(batch, p, with_seqs=True)
+        try:
+            ah.ah_plan_run(plan, engine.ctx)
+            ref = engine.plan_output(plan)
+            i = ah.ah_plan_info_get(plan)
+            hits = np.zeros(i["n_hits"] + 3, ah.HIT_DTYPE)
+            amps = np.zeros(i["n_kept"] + 3, ah.AMP_DTYPE)
+            arena = np.zeros(i["arena_bytes"] + 3, np.uint8)
+            fo = np.zeros(5 * i["n_kept"] + 1, np.uint64)
+            ah.ah_plan_copy_results(plan, engine.ctx, hits, amps, arena, fo)
+            assert hits[:i["n_hits"]].tobytes() == ref.hits.tobytes()
+            assert amps[:i["n_kept"]].tobytes() == ref.amps.tobytes()
+            assert arena[:i["arena_bytes"]].tobytes() == (ref.arena or b"")
+            assert np.array_equal(fo, ref.field_off)
+            with pytest.raises(ah.AhError) as e:
+                ah.ah_plan_copy_results(plan, engine.ctx, hits[:max(0, i["n_hits"] - 1)], None, None, None)
+            assert e.value.status == ah.AH_EOVERFLOW or i["n_hits"] == 0
+        finally:
+            ah.ah_plan_free(plan)
+    finally:
+        ah.ah_batch_free(batch)
