@@ -311,7 +311,7 @@ def run_engine(args):
     roofline["step_gbps_frac_of_alu_bound"] = value / world / (ALU_PEAK_TOPS * 1e3 / roofline["ops_per_base"])
 
     # end to end through the C ABI from pinned host memory: every step packs the records from host
-    # ASCII into the plan's batch (copy engines in 64 Mi-base chunks, packed from HBM as they land),
+    # ASCII into the plan's batch (copy engines in 256 Mi-base chunks, packed from HBM as they land),
     # replays the plan and copies sites, amplicons and sequences into pinned host buffers
     e2e = None
     if not args.no_e2e:

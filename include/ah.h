@@ -132,8 +132,8 @@ typedef struct {
 
 /* Pack host ASCII records.  seqs[i] points at lens[i] characters (no terminator needed);
  * genome_ids may be NULL (then record i has genome id i).  Characters other than ACGTacgt are
- * invalid bases.  Records are copied to the device by the copy engines in chunks of up to 64 Mi
- * bases (16 MB packed), one copy per run of records contiguous in host memory, on a second stream,
+ * invalid bases.  Records are copied to the device by the copy engines in chunks of up to 256 Mi
+ * bases (64 MB packed), one copy per run of records contiguous in host memory, on a second stream,
  * and each chunk is packed from device memory while the next one is in flight; page-locked host
  * memory (cudaHostAlloc, cudaHostRegister, pinned tensors) moves at the full host-link rate.
  * Records already in device memory are packed in place.  Synchronises the stream before

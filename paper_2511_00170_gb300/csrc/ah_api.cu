@@ -465,7 +465,7 @@ ah_status pack_records(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t n, con
   uint8_t* staging[2] = {nullptr, nullptr};
   PackItem* d_items = nullptr;
   cudaStream_t cs = nullptr;
-  cudaEvent_t copied[2] = {nullptr, nullptr}, packed[2] = {nullptr, nullptr};
+  cudaEvent_t copied[2] = {nullptr, nullptr}, packed[2] = {nullptr, nullptr}, ready = nullptr;
   // 16 bytes of slack: the packing kernel reads whole aligned 16-byte words around its bytes
   if (!st) st = dalloc(ctx, &staging[0], stage_max + 16);
   if (!st && runs.size() > 1) st = dalloc(ctx, &staging[1], stage_max + 16);
@@ -476,8 +476,12 @@ ah_status pack_records(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t n, con
     e = cudaEventCreateWithFlags(&copied[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&packed[k], cudaEventDisableTiming);
   }
+  if (!st && e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
   if (!st && e == cudaSuccess)
     e = cudaMemcpyAsync(d_items, all.data(), all.size() * sizeof(PackItem), cudaMemcpyHostToDevice, ctx->stream);
+  // the staging buffers were allocated in the context stream's order: the copy stream starts after that
+  if (!st && e == cudaSuccess) e = cudaEventRecord(ready, ctx->stream);
+  if (!st && e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
   for (size_t c = 0; c < runs.size() && !st && e == cudaSuccess; ++c) {
     const int w = (int)(c & 1);
     if (c >= 2) e = cudaStreamWaitEvent(cs, packed[w], 0);  // the buffer's previous chunk is packed
@@ -501,6 +505,7 @@ ah_status pack_records(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t n, con
     if (copied[k]) cudaEventDestroy(copied[k]);
     if (packed[k]) cudaEventDestroy(packed[k]);
   }
+  if (ready) cudaEventDestroy(ready);
   dfree(ctx, staging[0]);
   dfree(ctx, staging[1]);
   dfree(ctx, d_items);
