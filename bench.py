@@ -229,6 +229,21 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------------------ engine arm
+def job_time_and_value(ms_local, bases_per_rank, world):
+    """Replicas (one process per GPU, each scanning its own copy of the workload): the job's step time
+    is the slowest rank's, and the job's throughput counts every rank's bases.  Needs an initialised
+    process group when world > 1."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * bases_per_rank / (ms * 1e-3) / 1e9
+
+
 def run_engine(args):
     import numpy as np
     import torch
@@ -297,11 +312,7 @@ def run_engine(args):
     ah.ah_plan_check(plan, eng.ctx)   # every replay fitted its buffers (raises on overflow)
     ms = e0.elapsed_time(e1) / args.steps
     stats = ah.ah_ctx_stats_get(eng.ctx)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * wl.total_bp / (ms * 1e-3) / 1e9
+    ms, value = job_time_and_value(ms, wl.total_bp, world)
 
     # roofline of the dominant kernel (the bit-sliced scan), from its own CUDA-event times
     scan_ms = stats["scan_ms"] / max(1, stats["scan_launches"])
