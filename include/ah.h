@@ -19,10 +19,12 @@
  *     back from the device and therefore synchronise that stream; this is stated per call.
  *   - Objects (ah_batch, ah_primers, ah_hits, ah_amplicons) are owned by the library and released
  *     only by their ah_*_free call, which enqueues the release on the owning context's stream.
- *     Freeing NULL is a no-op.  An object may only be used with the context that made it.
+ *     Freeing NULL is a no-op.  A packed batch may be read by any context on the same device (the
+ *     serving loop's workers share one); other objects are used with the context that made them.
  *   - Host pointers are plain host memory (pinned memory makes copies asynchronous and fast).
  *   - Device-side checks never trap: a kernel that detects an inconsistency sets a status word
- *     that the next synchronising call turns into AH_EINTERNAL.
+ *     that the next synchronising call turns into AH_EINTERNAL (AH_ELIMIT for a degenerate-site Tm
+ *     over its work bound).  No kernel waits on another, so no call waits on the device unbounded.
  *   - All sizes are in bases unless stated otherwise.
  */
 #ifndef AH_H
@@ -80,8 +82,8 @@ typedef struct {
   uint64_t scan_bases;      /* bases covered by those launches */
   uint64_t jit_compiles;    /* scan kernels compiled at run time (NVRTC) */
   double jit_ms;            /* host time spent compiling them */
-  int32_t scan_ops_per_group; /* ALU instructions (LOP3 and funnel shifts) of the last one-launch scan
-                                 kernel's generated circuit per 32 positions */
+  int32_t scan_ops_per_group; /* ALU instructions (LOP3 and funnel shifts) of the last scan's
+                                 generated circuits (all its kernels) per 32 positions */
 } ah_ctx_stats;
 ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out);
 ah_status ah_ctx_stats_reset(ah_ctx* ctx);
