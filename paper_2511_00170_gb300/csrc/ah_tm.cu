@@ -96,12 +96,14 @@ struct NNTables {
 // global (not constant) memory: threads of a warp look up different steps, which the constant cache
 // would serialise
 __device__ NNTables c_nn;
-// the same values in single precision, for the search passes of the degenerate-site chain method
-struct NNTablesF {
-  float step_h[256], step_s[256];
-  float term_h[256], term_s[256];
+// The same values as integers in units of 0.1 (every published value has one decimal), for the
+// degenerate-site search: sums of them are exact in any arithmetic.  kNoParam marks a missing entry.
+constexpr int16_t kNoParam = INT16_MIN;
+struct NNTablesI {
+  int16_t step_h[256], step_s[256];
+  int16_t term_h[256], term_s[256];
 };
-__device__ NNTablesF c_nnf;
+__device__ NNTablesI c_nni;
 
 int code_of(char c) {  // A=0, C=1, T=2, G=3
   switch (c) {
@@ -168,14 +170,19 @@ ah_status load_tables(ah_ctx* ctx) {
   std::lock_guard<std::mutex> lock(g_tables_mu);
   if (ctx->device < 64 && g_tables_loaded[ctx->device]) return AH_OK;
   static NNTables host;
-  static NNTablesF host_f;
+  static NNTablesI host_i;
   build_tables(&host);
+  auto tenths = [](double x) -> int16_t {
+    if (std::isnan(x)) return kNoParam;
+    const double t = std::round(x * 10.0);
+    return (int16_t)t;
+  };
   for (int i = 0; i < 256; ++i) {
-    host_f.step_h[i] = (float)host.step_h[i], host_f.step_s[i] = (float)host.step_s[i];
-    host_f.term_h[i] = (float)host.term_h[i], host_f.term_s[i] = (float)host.term_s[i];
+    host_i.step_h[i] = tenths(host.step_h[i]), host_i.step_s[i] = tenths(host.step_s[i]);
+    host_i.term_h[i] = tenths(host.term_h[i]), host_i.term_s[i] = tenths(host.term_s[i]);
   }
   AH_CUDA(ctx, cudaMemcpyToSymbolAsync(c_nn, &host, sizeof host, 0, cudaMemcpyHostToDevice, ctx->stream));
-  AH_CUDA(ctx, cudaMemcpyToSymbolAsync(c_nnf, &host_f, sizeof host_f, 0, cudaMemcpyHostToDevice, ctx->stream));
+  AH_CUDA(ctx, cudaMemcpyToSymbolAsync(c_nni, &host_i, sizeof host_i, 0, cudaMemcpyHostToDevice, ctx->stream));
   AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->device < 64) g_tables_loaded[ctx->device] = true;
   return AH_OK;
@@ -288,53 +295,48 @@ __device__ bool duplex_tm(const uint8_t* v, const uint8_t* c, int L, const TmRun
   return true;
 }
 
-// the tables in the arithmetic of a chain pass
-template <class T> struct Tab;
-template <> struct Tab<double> {
-  static __device__ __forceinline__ const NNTables& t() { return c_nn; }
-};
-template <> struct Tab<float> {
-  static __device__ __forceinline__ const NNTablesF& t() { return c_nnf; }
-};
+// the end-dependent initiation terms in tenths
+constexpr int tenths_of(double x) { return (int)(x * 10.0 + (x >= 0 ? 0.5 : -0.5)); }
+constexpr int kTermATH10 = tenths_of(kTermATH), kTermATS10 = tenths_of(kTermATS);
+constexpr int kTermGCH10 = tenths_of(kTermGCH), kTermGCS10 = tenths_of(kTermGCS);
+constexpr int k5TAH10 = tenths_of(k5TAH), k5TAS10 = tenths_of(k5TAS);
 
-// nearest-neighbour sums of edge (i, i+1) of the variant chain for bases (a, b) at positions i, i+1
-// over the opposite-strand codes c: the terminal-mismatch entry replaces the stack at either end
-template <class T>
-__device__ __forceinline__ bool edge_sums(int i, int L, uint8_t a, uint8_t b, const uint8_t* c, T* dh, T* ds) {
-  const auto& tb = Tab<T>::t();
+// nearest-neighbour sums (tenths) of edge (i, i+1) of the variant chain for bases (a, b) at
+// positions i, i+1 over the opposite-strand codes c: the terminal-mismatch entry replaces the stack
+// at either end; false when the step has no parameter
+__device__ __forceinline__ bool edge_sums(int i, int L, uint8_t a, uint8_t b, const uint8_t* c, int* dh, int* ds) {
   if (i == 0) {
     const int k = c[1] * 64 + c[0] * 16 + b * 4 + a;  // left end read from the opposite strand
-    const T th = __ldg(&tb.term_h[k]);
-    if (!isnan(th)) {
+    const int th = __ldg(&c_nni.term_h[k]);
+    if (th != kNoParam) {
       *dh = th;
-      *ds = __ldg(&tb.term_s[k]);
+      *ds = __ldg(&c_nni.term_s[k]);
       return true;
     }
   }
   if (i == L - 2) {
     const int k = a * 64 + b * 16 + c[L - 2] * 4 + c[L - 1];
-    const T th = __ldg(&tb.term_h[k]);
-    if (!isnan(th)) {
+    const int th = __ldg(&c_nni.term_h[k]);
+    if (th != kNoParam) {
       *dh = th;
-      *ds = __ldg(&tb.term_s[k]);
+      *ds = __ldg(&c_nni.term_s[k]);
       return true;
     }
   }
   const int k = a * 64 + b * 16 + c[i] * 4 + c[i + 1];
-  const T sh = __ldg(&tb.step_h[k]);
-  if (isnan(sh)) return false;
+  const int sh = __ldg(&c_nni.step_h[k]);
+  if (sh == kNoParam) return false;
   *dh = sh;
-  *ds = __ldg(&tb.step_s[k]);
+  *ds = __ldg(&c_nni.step_s[k]);
   return true;
 }
 
-// initiation terms that depend on the variant's end bases
-template <class T>
-__device__ __forceinline__ void end_sums(int j, int L, uint8_t v, T* dh, T* ds) {
-  *dh = (T)((v & 1) ? kTermGCH : kTermATH);
-  *ds = (T)((v & 1) ? kTermGCS : kTermATS);
-  if (j == 0 && v == 2) *dh += (T)k5TAH, *ds += (T)k5TAS;       // 5' T
-  if (j == L - 1 && v == 0) *dh += (T)k5TAH, *ds += (T)k5TAS;   // 3' A
+// initiation terms (tenths) that depend on the variant's end bases
+__device__ __forceinline__ void end_sums(int j, int L, uint8_t v, int* dh, int* ds) {
+  *dh = (v & 1) ? kTermGCH10 : kTermATH10;
+  *ds = (v & 1) ? kTermGCS10 : kTermATS10;
+  if (j == 0 && v == 2) *dh += k5TAH10, *ds += k5TAS10;       // 5' T
+  if (j == L - 1 && v == 0) *dh += k5TAH10, *ds += k5TAS10;   // 3' A
 }
 
 // The variants that count at a site (reading R14): per position the primer's codes, only the site's
@@ -376,21 +378,29 @@ __device__ uint64_t count_variants(const SiteVariants& V, uint64_t cap) {
   return t;
 }
 
+// Tm of a variant from its exact sums (tenths) and G/C count
+__device__ __forceinline__ double tm_of_tenths(int dh10, int ds10, int gc, int L, const TmRun& R) {
+  const double dh = 0.1 * dh10 + kInitH + (gc ? kOneGCH : kAllATH);
+  const double ds = 0.1 * ds10 + kInitS + (gc ? kOneGCS : kAllATS);
+  return tm_of_sums(dh, ds, gc, L, R);
+}
+
 // Maximum Tm over the qualifying variants by depth-first enumeration.  The walk adds one position's
 // terms per step (the end terms at both ends, the edge to the previous base in between), so variants
 // share the sums of their common prefix; a prefix whose last edge has no parameter is undefined for
-// every variant below it and is cut, and so is one over the mismatch budget.
+// every variant below it and is cut, and so is one over the mismatch budget.  Sums are exact
+// integers (tenths); each variant's Tm is one division.
 __device__ bool enum_max(const SiteVariants& V, const TmRun& R, double* out) {
   int8_t idx[32];
   uint8_t mm[33], gcs[33], v[32];
-  double sh[33], ss[33];  // sums of the terms of positions < j
+  int sh[33], ss[33];  // sums of the terms of positions < j
   const int L = V.L;
   double best = -INFINITY;
   bool any = false;
   int j = 0;
   idx[0] = -1;
   mm[0] = gcs[0] = 0;
-  sh[0] = ss[0] = 0.0;
+  sh[0] = ss[0] = 0;
   while (j >= 0) {
     if (++idx[j] >= V.nch[j]) {
       --j;
@@ -399,22 +409,19 @@ __device__ bool enum_max(const SiteVariants& V, const TmRun& R, double* out) {
     const uint8_t b = V.ch[j][idx[j]];
     const int m = mm[j] + (V.k >= 0 && b != V.s[j]);
     if (V.k >= 0 && m > V.k) continue;
-    double dh = sh[j], ds = ss[j], eh, es;
+    int eh, es;
     if (j == 0) {
-      end_sums<double>(0, L, b, &eh, &es);
-    } else if (!edge_sums<double>(j - 1, L, v[j - 1], b, V.c, &eh, &es)) {
+      end_sums(0, L, b, &eh, &es);
+    } else if (!edge_sums(j - 1, L, v[j - 1], b, V.c, &eh, &es)) {
       continue;
     }
-    dh += eh;
-    ds += es;
+    const int dh = sh[j] + eh, ds = ss[j] + es;
     v[j] = b;
     const int gc = gcs[j] + (b & 1);
     if (j == L - 1) {
-      end_sums<double>(L - 1, L, b, &eh, &es);
-      dh += eh + kInitH + (gc ? kOneGCH : kAllATH);
-      ds += es + kInitS + (gc ? kOneGCS : kAllATS);
+      end_sums(L - 1, L, b, &eh, &es);
       any = true;
-      best = fmax(best, tm_of_sums(dh, ds, gc, L, R));
+      best = fmax(best, tm_of_tenths(dh + eh, ds + es, gc, L, R));
       continue;
     }
     sh[j + 1] = dh;
@@ -430,54 +437,67 @@ __device__ bool enum_max(const SiteVariants& V, const TmRun& R, double* out) {
 
 enum ChainResult { kChainOk, kChainUndefined, kChainUnbounded };
 
-// One Viterbi pass over the chain of qualifying variants, in arithmetic T: the variant maximising
-// the sum of (wl * dS - wn * 1000 * dH) over its terms that depend on its bases (arg-max left in v).
-// States are (position, base, mismatches so far), at most 4 x (k + 1) per position.
+// One Viterbi pass over the chain of qualifying variants: the variant maximising A * dS10 - B * dH10
+// (sums in tenths) in score arithmetic T, its bases left in v and its exact sums in dh10/ds10.  T is
+// float for the search passes and int64 (fixed point) for the confirming pass.  States are
+// (position, base, mismatches so far), at most 4 x (k + 1) per position.
 template <class T>
-__device__ bool chain_viterbi_k(const SiteVariants& V, T wl, T wn, uint8_t (*back)[4][kMaxK + 1], uint8_t* v,
-                                T* best_score) {
+__device__ bool chain_viterbi(const SiteVariants& V, T A, T B, uint8_t (*back)[4][kMaxK + 1], uint8_t* v,
+                              T* best_score, int* dh10, int* ds10) {
   constexpr int M = kMaxK + 1;
   const int L = V.L, K = V.k < 0 ? 0 : V.k;
   auto inc = [&](int j, int a) { return (V.k >= 0 && V.ch[j][a] != V.s[j]) ? 1 : 0; };
-  const T ninf = -(T)INFINITY;
+  bool live[4][M], nlive[4][M];
   T cur[4][M], nxt[4][M];
+  int ch_[4][M], cs_[4][M], nh_[4][M], ns_[4][M];
   for (int a = 0; a < 4; ++a)
-    for (int m = 0; m <= K; ++m) cur[a][m] = ninf;
+    for (int m = 0; m <= K; ++m) live[a][m] = false;
   for (int a = 0; a < V.nch[0]; ++a) {
-    T dh, ds;
-    end_sums<T>(0, L, V.ch[0][a], &dh, &ds);
-    cur[a][inc(0, a)] = wl * ds - wn * (T)1000 * dh;
+    int dh, ds;
+    end_sums(0, L, V.ch[0][a], &dh, &ds);
+    const int m = inc(0, a);
+    live[a][m] = true;
+    cur[a][m] = A * (T)ds - B * (T)dh;
+    ch_[a][m] = dh, cs_[a][m] = ds;
   }
   for (int i = 0; i + 1 < L; ++i) {
     for (int b = 0; b < V.nch[i + 1]; ++b) {
       const int ib = inc(i + 1, b);
-      T tail = 0;
-      if (i + 1 == L - 1) {
-        T dh, ds;
-        end_sums<T>(L - 1, L, V.ch[i + 1][b], &dh, &ds);
-        tail = wl * ds - wn * (T)1000 * dh;
-      }
-      for (int m = 0; m <= K; ++m) nxt[b][m] = ninf, back[i + 1][b][m] = 0;
+      int th = 0, ts = 0;
+      if (i + 1 == L - 1) end_sums(L - 1, L, V.ch[i + 1][b], &th, &ts);
+      for (int m = 0; m <= K; ++m) nlive[b][m] = false, back[i + 1][b][m] = 0;
       for (int a = 0; a < V.nch[i]; ++a) {
-        T dh, ds;
-        if (!edge_sums<T>(i, L, V.ch[i][a], V.ch[i + 1][b], V.c, &dh, &ds)) continue;
-        const T w = wl * ds - wn * (T)1000 * dh + tail;
+        int dh, ds;
+        if (!edge_sums(i, L, V.ch[i][a], V.ch[i + 1][b], V.c, &dh, &ds)) continue;
+        dh += th, ds += ts;
+        const T w = A * (T)ds - B * (T)dh;
         for (int m = 0; m + ib <= K; ++m) {
-          if (cur[a][m] == ninf) continue;
+          if (!live[a][m]) continue;
           const T sc = cur[a][m] + w;
-          if (sc > nxt[b][m + ib]) nxt[b][m + ib] = sc, back[i + 1][b][m + ib] = (uint8_t)a;
+          const int n = m + ib;
+          if (!nlive[b][n] || sc > nxt[b][n]) {
+            nlive[b][n] = true;
+            nxt[b][n] = sc;
+            nh_[b][n] = ch_[a][m] + dh, ns_[b][n] = cs_[a][m] + ds;
+            back[i + 1][b][n] = (uint8_t)a;
+          }
         }
       }
     }
     for (int b = 0; b < V.nch[i + 1]; ++b)
-      for (int m = 0; m <= K; ++m) cur[b][m] = nxt[b][m];
+      for (int m = 0; m <= K; ++m) {
+        live[b][m] = nlive[b][m];
+        if (nlive[b][m]) cur[b][m] = nxt[b][m], ch_[b][m] = nh_[b][m], cs_[b][m] = ns_[b][m];
+      }
   }
-  T best = ninf;
   int arg = -1, am = 0;
   for (int b = 0; b < V.nch[L - 1]; ++b)
     for (int m = 0; m <= K; ++m)
-      if (cur[b][m] > best) best = cur[b][m], arg = b, am = m;
+      if (live[b][m] && (arg < 0 || cur[b][m] > cur[arg][am])) arg = b, am = m;
   if (arg < 0) return false;
+  *best_score = cur[arg][am];
+  *dh10 = ch_[arg][am];
+  *ds10 = cs_[arg][am];
   for (int j = L - 1; j >= 0; --j) {
     v[j] = V.ch[j][arg];
     if (j) {
@@ -486,25 +506,20 @@ __device__ bool chain_viterbi_k(const SiteVariants& V, T wl, T wn, uint8_t (*bac
       arg = pa;
     }
   }
-  *best_score = best;
   return true;
-}
-
-template <class T>
-__device__ __forceinline__ bool chain_viterbi(const SiteVariants& V, T wl, T wn, uint8_t (*back)[4][kMaxK + 1],
-                                              uint8_t* v, T* best_score) {
-  return chain_viterbi_k<T>(V, wl, wn, back, v, best_score);
 }
 
 // Exact maximum of Tm over the qualifying variants for salt methods 0-5 and L >= 3.
 // Tm + 273.15 = N(v) / D(v) with N = 1000 dH and D = dS + S0 < 0, and every term of N and D depends on
 // at most two adjacent variant bases.  Dinkelbach's iteration for fractional programmes: for the
-// current ratio lam, a Viterbi pass over the chain finds the variant maximising lam * D - N; its ratio
-// becomes the next lam; at the optimum the maximum is 0.  The search passes run in single precision
-// (GB300 runs FP32 at many times its FP64 rate); every candidate's Tm is evaluated exactly, and the
-// optimum is confirmed by a double-precision pass, which continues the iteration if single
-// precision stopped short.  kChainUnbounded when some qualifying variant could have D >= 0, where
-// the iteration does not apply.
+// current ratio lam, a Viterbi pass over the chain finds the variant maximising lam * D - N; its
+// ratio becomes the next lam; at the optimum the maximum is 0.  Every published parameter has one
+// decimal, so the passes carry exact integer sums (tenths) and each candidate's ratio is one exact
+// division.  The search passes score in single precision; the optimum is confirmed by a pass in
+// 64-bit fixed point (lam scaled by 2^36, products of integers exact), which continues the
+// iteration should single precision have stopped short.  The sign check (the largest dS) is exact in
+// single precision: its scores are integer sums far below 2^24.  kChainUnbounded when some
+// qualifying variant could have D >= 0, where the iteration does not apply.
 __device__ ChainResult site_tm_chain(const SiteVariants& V, const TmRun& R, double* out) {
   const int L = V.L;
   uint8_t back[32][4][kMaxK + 1], v[32];
@@ -512,51 +527,46 @@ __device__ ChainResult site_tm_chain(const SiteVariants& V, const TmRun& R, doub
   const double S0 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
   const double H0 = kInitH + kOneGCH, Sc = kInitS + kOneGCS;  // all-A/T and one-G/C terms are equal here
   const double shift = R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0;
-  // D must stay negative for every qualifying variant: the largest dS, in single precision when it is
-  // clearly below the bound (rounding there is far below 0.01), else in double precision
-  {
-    float maxS_f;
-    if (!chain_viterbi<float>(V, 1.f, 0.f, back, v, &maxS_f)) return kChainUndefined;
-    if (!((double)maxS_f + Sc + S0 < -0.01)) {
-      double maxS;
-      if (!chain_viterbi<double>(V, 1.0, 0.0, back, v, &maxS)) return kChainUndefined;
-      if (maxS + Sc + S0 >= 0.0) return kChainUnbounded;
-    }
-  }
-  // start from the variant that maximises dS - dH / 300 (any defined variant works)
+  auto ratio = [&](int dh10, int ds10) { return 1000.0 * (0.1 * dh10 + H0) / (0.1 * ds10 + Sc + S0); };
+  int dh10, ds10;
   float scf;
-  if (!chain_viterbi<float>(V, 300.f, 1.f, back, v, &scf)) return kChainUndefined;
-  double t;
-  if (!duplex_tm(v, V.c, L, R, &t)) {
-    double sc;
-    if (!chain_viterbi<double>(V, 300.0, 1.0, back, v, &sc) || !duplex_tm(v, V.c, L, R, &t)) return kChainUndefined;
-  }
-  double lam = t + 273.15 - shift, best_t = t;
-  // single-precision search: stop when the pass proposes no variant with a larger exact Tm
+  // D must stay negative for every qualifying variant
+  if (!chain_viterbi<float>(V, 1.f, 0.f, back, v, &scf, &dh10, &ds10)) return kChainUndefined;
+  if (0.1 * ds10 + Sc + S0 >= 0.0) return kChainUnbounded;
+  // start from the variant that maximises dS - dH / 300 (any defined variant works)
+  if (!chain_viterbi<float>(V, 300.f, 1000.f, back, v, &scf, &dh10, &ds10)) return kChainUndefined;
+  double lam = ratio(dh10, ds10);
+  int best_h = dh10, best_s = ds10;
+  // single-precision search: stop when a pass proposes no variant with a larger exact ratio
   for (int it = 0; it < 64; ++it) {
-    if (!chain_viterbi<float>(V, (float)lam, 1.f, back, v, &scf)) break;
-    double tn;
-    if (!duplex_tm(v, V.c, L, R, &tn)) break;
-    const double nl = tn + 273.15 - shift;
-    if (!(nl > lam)) break;
-    lam = nl;
-    best_t = tn;
+    if (!chain_viterbi<float>(V, (float)lam, 1000.f, back, v, &scf, &dh10, &ds10)) break;
+    const double r = ratio(dh10, ds10);
+    if (!(r > lam)) break;
+    lam = r, best_h = dh10, best_s = ds10;
   }
-  // double-precision confirmation (and continuation, should single precision have stopped short)
+  // Confirmation: no variant scores above the incumbent at lam (else continue from the better one).
+  // Fixed point while |lam| < 4000 K keeps every path score below 2^62 (|sums| < 10^4 tenths);
+  // beyond that, which only variants with D near 0 reach, double precision.
+  constexpr double kScale = 68719476736.0;  // 2^36
   for (int it = 0; it < 64; ++it) {
-    double sc;
-    if (!chain_viterbi<double>(V, lam, 1.0, back, v, &sc)) break;
-    // score + lam * (Sc + S0) - 1000 * H0 = lam * D(v) - N(v) for the maximising variant
-    const double F = sc + lam * (Sc + S0) - 1000.0 * H0;
-    if (F <= 1e-7) break;
-    double tn;
-    if (!duplex_tm(v, V.c, L, R, &tn)) break;
-    const double nl = tn + 273.15 - shift;
-    if (!(nl > lam)) break;
-    lam = nl;
-    best_t = tn;
+    bool better;
+    if (fabs(lam) < 4000.0) {
+      const long long Lq = llrint(lam * kScale), Bq = (long long)(1000.0 * kScale);
+      long long sc;
+      if (!chain_viterbi<long long>(V, Lq, Bq, back, v, &sc, &dh10, &ds10)) break;
+      better = sc > Lq * best_s - Bq * best_h;
+    } else {
+      double sc;
+      if (!chain_viterbi<double>(V, lam, 1000.0, back, v, &sc, &dh10, &ds10)) break;
+      const double inc = lam * best_s - 1000.0 * best_h;
+      better = sc > inc + 1e-12 * fabs(inc);
+    }
+    if (!better) break;
+    const double r = ratio(dh10, ds10);
+    if (!(r > lam)) break;
+    lam = r, best_h = dh10, best_s = ds10;
   }
-  *out = best_t;
+  *out = lam + shift - 273.15;
   return kChainOk;
 }
 
