@@ -198,8 +198,10 @@ void launch_scan_kernel(cudaStream_t s, const ScanKernel& k, const ah_batch* b, 
                         uint32_t cap, uint32_t* status, unsigned long long* work, uint64_t n_tiles, int grid);
 void launch_tile_max(cudaStream_t s, const uint32_t* tile_count, uint64_t n_tiles, uint32_t* out);
 size_t prepare_tile_sort(uint32_t cap, int* warps_out);
-void launch_tile_sort(cudaStream_t s, uint64_t* slots, const uint32_t* tile_count, uint32_t cap, uint64_t n_tiles,
-                      uint32_t n_pairs, uint32_t* tpc);
+// sorts every tile's keys and counts them per pair; big: n_tiles + 1 words of device scratch, used
+// when cap exceeds 256; returns the kernels launched
+int launch_tile_sort(cudaStream_t s, uint64_t* slots, const uint32_t* tile_count, uint32_t cap, uint64_t n_tiles,
+                     uint32_t n_pairs, uint32_t* tpc, uint32_t* big, int sm_count);
 void launch_emit_hits(cudaStream_t s, const uint64_t* slots, const uint32_t* tile_count, uint32_t cap, uint64_t n_tiles,
                       uint64_t tile_groups, const uint64_t* off, const ah_batch* b, ah_hit* hits,
                       const uint64_t* tile_base, uint64_t hit_cap, uint32_t* overflow, uint64_t* pair_off,

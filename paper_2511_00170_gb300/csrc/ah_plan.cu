@@ -29,6 +29,7 @@ struct ah_plan {
   uint64_t* slots = nullptr;
   uint32_t* tile_count = nullptr;
   uint32_t* tpc = nullptr;
+  uint32_t* big = nullptr;      // n_tiles + 1: tiles with more than 256 keys (count first)
   uint64_t* tpc_off = nullptr;  // n_cells + 1; [n_cells] = sites found
   uint64_t* scratch = nullptr;  // prefix-sum block sums
   ah_hit* hits = nullptr;
@@ -68,12 +69,12 @@ namespace {
 
 void free_buffers(ah_plan* pl) {
   ah_ctx* c = pl->ctx;
-  for (void* q : {(void*)pl->slots, (void*)pl->tile_count, (void*)pl->tpc, (void*)pl->tpc_off, (void*)pl->scratch,
+  for (void* q : {(void*)pl->slots, (void*)pl->tile_count, (void*)pl->tpc, (void*)pl->big, (void*)pl->tpc_off, (void*)pl->scratch,
                   (void*)pl->hits, (void*)pl->pair_off, (void*)pl->pcount, (void*)pl->poff, (void*)pl->amps,
                   (void*)pl->hit_tm, (void*)pl->keep, (void*)pl->koff, (void*)pl->kept, (void*)pl->elen,
                   (void*)pl->ebase, (void*)pl->arena, (void*)pl->field_off, (void*)pl->ctr})
     dfree(c, q);
-  pl->slots = nullptr, pl->tile_count = nullptr, pl->tpc = nullptr, pl->tpc_off = nullptr, pl->scratch = nullptr;
+  pl->slots = nullptr, pl->tile_count = nullptr, pl->tpc = nullptr, pl->big = nullptr, pl->tpc_off = nullptr, pl->scratch = nullptr;
   pl->hits = nullptr, pl->pair_off = nullptr, pl->pcount = nullptr, pl->poff = nullptr, pl->amps = nullptr;
   pl->hit_tm = nullptr, pl->keep = nullptr, pl->koff = nullptr, pl->kept = nullptr, pl->elen = nullptr;
   pl->ebase = nullptr, pl->arena = nullptr, pl->field_off = nullptr, pl->ctr = nullptr;
@@ -90,7 +91,7 @@ ah_status alloc_buffers(ah_plan* pl) {
   ah_status st;
   const uint64_t scan_n = std::max({pl->n_cells, pl->hit_cap, pl->amp_cap});
   if ((st = dalloc(c, &pl->slots, pl->n_tiles * pl->slot_cap)) || (st = dalloc(c, &pl->tile_count, pl->n_tiles)) ||
-      (st = dalloc(c, &pl->tpc, pl->n_cells)) || (st = dalloc(c, &pl->tpc_off, pl->n_cells + 1)) ||
+      (st = dalloc(c, &pl->tpc, pl->n_cells)) || (st = dalloc(c, &pl->big, pl->n_tiles + 1)) || (st = dalloc(c, &pl->tpc_off, pl->n_cells + 1)) ||
       (st = dalloc(c, &pl->scratch, scan_scratch_elems(scan_n))) || (st = dalloc(c, &pl->hits, pl->hit_cap)) ||
       (st = dalloc(c, &pl->pair_off, pl->p->n_pairs + 1)) || (st = dalloc(c, &pl->pcount, pl->hit_cap)) ||
       (st = dalloc(c, &pl->poff, pl->hit_cap + 1)) || (st = dalloc(c, &pl->amps, pl->amp_cap)) ||
@@ -117,7 +118,8 @@ void enqueue_step(ah_plan* pl, cudaStream_t s) {
                      (unsigned long long*)(pl->ctr + 2), pl->n_tiles, pl->grid);
   cudaEventRecordWithFlags(pl->scan_ev[1], s, cudaEventRecordExternal);
   launch_tile_max(s, pl->tile_count, pl->n_tiles, pl->ctr + 0);
-  launch_tile_sort(s, pl->slots, pl->tile_count, pl->slot_cap, pl->n_tiles, p->n_pairs, pl->tpc);
+  launch_tile_sort(s, pl->slots, pl->tile_count, pl->slot_cap, pl->n_tiles, p->n_pairs, pl->tpc, pl->big,
+                   pl->ctx->sm_count);
   exclusive_scan_u32_s(s, pl->tpc, pl->tpc_off, pl->n_cells, pl->scratch);
   launch_emit_hits(s, pl->slots, pl->tile_count, pl->slot_cap, pl->n_tiles, pl->tile_groups, pl->tpc_off, b, pl->hits,
                    nullptr, pl->hit_cap, pl->ctr + 1, pl->pair_off, p->n_pairs);

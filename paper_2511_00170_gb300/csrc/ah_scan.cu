@@ -48,21 +48,13 @@ __device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* a, uint32_t 
   return lo;
 }
 
-// one warp per tile: sort the tile's keys in shared memory, write them back, count per pair
-__global__ void k_tile_sort(uint64_t* __restrict__ slots, const uint32_t* __restrict__ tile_count, uint32_t cap,
-                            uint32_t cap_pow2, uint64_t n_tiles, uint32_t n_pairs,
-                            uint32_t* __restrict__ tile_pair_count) {
-  extern __shared__ uint64_t sm[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (t >= n_tiles) return;
-  const uint32_t n = min(tile_count[t], cap);
-  if (n == 0) return;
-  uint64_t* tk = slots + t * cap;
+// Sort one tile's keys (one warp, bitonic in the warp's shared-memory buffer), write them back and
+// count them per pair (pair in the top 16 bits).
+__device__ __forceinline__ void sort_tile(uint64_t* tk, uint32_t n, uint64_t* buf, uint64_t t, uint64_t n_tiles,
+                                          uint32_t n_pairs, uint32_t* tile_pair_count, int lane) {
   if (n > 1) {
     uint32_t m = 2;
     while (m < n) m <<= 1;
-    uint64_t* buf = sm + (uint64_t)warp * cap_pow2;
     for (uint32_t i = lane; i < m; i += 32) buf[i] = i < n ? tk[i] : ~0ull;
     __syncwarp();
     for (uint32_t k = 2; k <= m; k <<= 1) {
@@ -84,12 +76,45 @@ __global__ void k_tile_sort(uint64_t* __restrict__ slots, const uint32_t* __rest
     for (uint32_t i = lane; i < n; i += 32) tk[i] = buf[i];
     __syncwarp();
   }
-  // per-pair counts from the sorted keys (pair in the top 16 bits)
   const uint32_t p_first = (uint32_t)(tk[0] >> 48), p_last = (uint32_t)(tk[n - 1] >> 48);
   for (uint32_t p = p_first + lane; p <= p_last && p < n_pairs; p += 32) {
     const uint32_t a = lower_bound_u64(tk, n, (uint64_t)p << 48);
     const uint32_t b = lower_bound_u64(tk, n, (uint64_t)(p + 1) << 48);
     if (b > a) tile_pair_count[(uint64_t)p * n_tiles + t] = b - a;
+  }
+}
+
+constexpr uint32_t kSmallTile = 256;  // keys a tile may hold to be sorted by the small-buffer kernel
+
+// One warp per tile with a kSmallTile-key buffer per warp (high occupancy).  Tiles holding more
+// keys are appended to big[1..] (count in big[0]) for k_tile_sort_big.
+__global__ void k_tile_sort(uint64_t* __restrict__ slots, const uint32_t* __restrict__ tile_count, uint32_t cap,
+                            uint64_t n_tiles, uint32_t n_pairs, uint32_t* __restrict__ tile_pair_count,
+                            uint32_t* __restrict__ big) {
+  __shared__ uint64_t sm[8 * kSmallTile];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (t >= n_tiles) return;
+  const uint32_t n = min(tile_count[t], cap);
+  if (n == 0) return;
+  if (n > kSmallTile) {
+    if (lane == 0) big[1 + atomicAdd(big, 1u)] = (uint32_t)t;
+    return;
+  }
+  sort_tile(slots + t * cap, n, sm + warp * kSmallTile, t, n_tiles, n_pairs, tile_pair_count, lane);
+}
+
+// The listed tiles, one warp each with a buffer of cap_pow2 keys, over a fixed grid.
+__global__ void k_tile_sort_big(uint64_t* __restrict__ slots, const uint32_t* __restrict__ tile_count, uint32_t cap,
+                                uint32_t cap_pow2, uint64_t n_tiles, uint32_t n_pairs,
+                                uint32_t* __restrict__ tile_pair_count, const uint32_t* __restrict__ big) {
+  extern __shared__ uint64_t sm_big[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+  const uint32_t n_big = big[0];
+  for (uint32_t i = blockIdx.x * warps + warp; i < n_big; i += gridDim.x * warps) {
+    const uint64_t t = big[1 + i];
+    sort_tile(slots + t * cap, min(tile_count[t], cap), sm_big + (uint64_t)warp * cap_pow2, t, n_tiles, n_pairs,
+              tile_pair_count, lane);
   }
 }
 
@@ -154,26 +179,38 @@ void launch_tile_max(cudaStream_t s, const uint32_t* tile_count, uint64_t n_tile
                                                                                                      out);
 }
 
-// shared memory the tile sort needs for slot lists of `cap` keys; sets the kernel attribute when that
-// exceeds the default (call before any stream capture)
-size_t prepare_tile_sort(uint32_t cap, int* warps_out) {
+// warps per block and shared memory of the large-tile sort for slot lists of `cap` keys
+size_t big_sort_shape(uint32_t cap, int* warps_out, uint32_t* cap_pow2_out) {
   uint32_t cap_pow2 = 2;
   while (cap_pow2 < cap) cap_pow2 <<= 1;
   const int warps = (int)std::max<uint32_t>(1, std::min<uint32_t>(8, 16384 / cap_pow2));
-  const size_t smem = (size_t)warps * cap_pow2 * sizeof(uint64_t);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (warps_out) *warps_out = warps;
+  if (cap_pow2_out) *cap_pow2_out = cap_pow2;
+  return (size_t)warps * cap_pow2 * sizeof(uint64_t);
+}
+
+// sets the large-tile sort's shared-memory attribute when it exceeds the default (call before any
+// stream capture, which does not allow it)
+size_t prepare_tile_sort(uint32_t cap, int* warps_out) {
+  const size_t smem = big_sort_shape(cap, warps_out, nullptr);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_tile_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return smem;
 }
 
-void launch_tile_sort(cudaStream_t s, uint64_t* slots, const uint32_t* tile_count, uint32_t cap, uint64_t n_tiles,
-                      uint32_t n_pairs, uint32_t* tpc) {
+// sort every tile's keys and count them per pair; `big` (n_tiles + 1 words) is needed only when
+// cap > kSmallTile
+int launch_tile_sort(cudaStream_t s, uint64_t* slots, const uint32_t* tile_count, uint32_t cap, uint64_t n_tiles,
+                     uint32_t n_pairs, uint32_t* tpc, uint32_t* big, int sm_count) {
+  if (cap > kSmallTile) cudaMemsetAsync(big, 0, sizeof(uint32_t), s);
+  k_tile_sort<<<(unsigned)((n_tiles + 7) / 8), 256, 0, s>>>(slots, tile_count, cap, n_tiles, n_pairs, tpc, big);
+  if (cap <= kSmallTile) return 1;
+  int warps = 1;
   uint32_t cap_pow2 = 2;
-  while (cap_pow2 < cap) cap_pow2 <<= 1;
-  const int warps = (int)std::max<uint32_t>(1, std::min<uint32_t>(8, 16384 / cap_pow2));
-  const size_t smem = (size_t)warps * cap_pow2 * sizeof(uint64_t);
-  k_tile_sort<<<(unsigned)((n_tiles + warps - 1) / warps), warps * 32, smem, s>>>(slots, tile_count, cap, cap_pow2,
-                                                                                  n_tiles, n_pairs, tpc);
+  const size_t smem = big_sort_shape(cap, &warps, &cap_pow2);
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n_tiles + warps - 1) / warps,
+                                                                           4ull * (uint64_t)std::max(1, sm_count)));
+  k_tile_sort_big<<<grid, warps * 32, smem, s>>>(slots, tile_count, cap, cap_pow2, n_tiles, n_pairs, tpc, big);
+  return 2;
 }
 
 void launch_emit_hits(cudaStream_t s, const uint64_t* slots, const uint32_t* tile_count, uint32_t cap, uint64_t n_tiles,
@@ -321,10 +358,13 @@ ah_status scan_sites(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, bool p
   if ((st = dalloc(ctx, &tpc, n_cells))) return st;
   if ((st = dalloc(ctx, &off, n_cells + 1))) return st;
   AH_CUDA(ctx, cudaMemsetAsync(tpc, 0, n_cells * sizeof(uint32_t), ctx->stream));
+  uint32_t* big = nullptr;  // tiles with more than 256 keys, sorted by the large-buffer kernel
+  if (cap > 256 && (st = dalloc(ctx, &big, n_tiles + 1))) return st;
   prepare_tile_sort(cap, nullptr);
-  launch_tile_sort(ctx->stream, slots, tile_count, cap, n_tiles, n_pairs, tpc);
-  launched(ctx);
+  const int sorts = launch_tile_sort(ctx->stream, slots, tile_count, cap, n_tiles, n_pairs, tpc, big, ctx->sm_count);
+  for (int i = 0; i < sorts; ++i) launched(ctx);
   AH_CUDA(ctx, cudaGetLastError());
+  dfree(ctx, big);
   if ((st = exclusive_scan_u32(ctx, tpc, off, n_cells))) return st;
   uint64_t total = 0;
   if ((st = read_u64(ctx, off + n_cells, &total))) return st;
