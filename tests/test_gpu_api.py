@@ -111,17 +111,17 @@ def test_server_requests_refused(env):
     srv = ah.ah_server_create(batch, n_slots=1)
     try:
         with pytest.raises(ah.AhError) as e:
-            ah.ah_server_submit(srv, wl.fwd, wl.rev, wl.k, wl.clamp, wl.n_records - 1, 2)   # past the end
+            ah.ah_server_submit(srv, wl.fwd, wl.rev, wl.k, wl.clamp, wl.n_records - 1, 2, 10, 500)   # past the end
         assert e.value.status == ah.AH_EINVAL
         with pytest.raises(ah.AhError) as e:
-            ah.ah_server_submit(srv, [], [], [], wl.clamp, 0, 1)                             # no pairs
+            ah.ah_server_submit(srv, [], [], [], wl.clamp, 0, 1, 10, 500)                     # no pairs
         assert e.value.status == ah.AH_EINVAL
         # a request whose primers are invalid is admitted and fails alone, with its message
-        t = ah.ah_server_submit(srv, ["ACGTXACGT"], wl.rev, wl.k, wl.clamp, 0, 1)
+        t = ah.ah_server_submit(srv, ["ACGTXACGT"], wl.rev, wl.k, wl.clamp, 0, 1, 10, 500)
         with pytest.raises(ah.AhError) as e:
             ah.ah_server_wait(srv, t)
         assert e.value.status == ah.AH_EINVAL
-        ok = ah.ah_server_wait(srv, ah.ah_server_submit(srv, wl.fwd, wl.rev, wl.k, wl.clamp, 0, wl.n_records))
+        ok = ah.ah_server_wait(srv, ah.ah_server_submit(srv, wl.fwd, wl.rev, wl.k, wl.clamp, 0, wl.n_records, 10, 500))
         assert len(ok["hits"]) >= 0
     finally:
         ah.ah_server_destroy(srv)
