@@ -84,3 +84,27 @@ def assert_same_sequences(out, ref):
     assert len(gk) == len(ok)
     for m, k in enumerate(gk):
         assert out.fields(m) == ref_seq[k], f"sequence fields differ at {k}"
+
+
+class Restricted:
+    """The plan's output restricted to some records, renumbered as the oracle numbers a subset."""
+
+    def __init__(self, out, records):
+        records = np.asarray(records, dtype=np.int64)
+        remap = {int(r): i for i, r in enumerate(records)}
+        hm = np.isin(out.hits["record"], records)
+        new_index = -np.ones(len(out.hits), dtype=np.int64)
+        new_index[np.nonzero(hm)[0]] = np.arange(int(hm.sum()))
+        self.hits = out.hits[hm].copy()
+        self.hits["record"] = [remap[int(r)] for r in self.hits["record"]]
+        am = np.isin(out.amps["record"], records)
+        self._src = np.nonzero(am)[0]
+        self.amps = out.amps[am].copy()
+        self.amps["record"] = [remap[int(r)] for r in self.amps["record"]]
+        self.amps["hit_i"] = new_index[self.amps["hit_i"]]
+        self.amps["hit_j"] = new_index[self.amps["hit_j"]]
+        assert (self.amps["hit_i"] >= 0).all() and (self.amps["hit_j"] >= 0).all()
+        self._out = out
+
+    def fields(self, m):
+        return self._out.fields(int(self._src[m]))

@@ -29,30 +29,6 @@ def engine():
     e.close()
 
 
-class _Restricted:
-    """The plan's output restricted to some records, renumbered as the oracle numbers a subset."""
-
-    def __init__(self, out, records):
-        records = np.asarray(records, dtype=np.int64)
-        remap = {int(r): i for i, r in enumerate(records)}
-        hm = np.isin(out.hits["record"], records)
-        new_index = -np.ones(len(out.hits), dtype=np.int64)
-        new_index[np.nonzero(hm)[0]] = np.arange(int(hm.sum()))
-        self.hits = out.hits[hm].copy()
-        self.hits["record"] = [remap[int(r)] for r in self.hits["record"]]
-        am = np.isin(out.amps["record"], records)
-        self._src = np.nonzero(am)[0]
-        self.amps = out.amps[am].copy()
-        self.amps["record"] = [remap[int(r)] for r in self.amps["record"]]
-        self.amps["hit_i"] = new_index[self.amps["hit_i"]]
-        self.amps["hit_j"] = new_index[self.amps["hit_j"]]
-        assert (self.amps["hit_i"] >= 0).all() and (self.amps["hit_j"] >= 0).all()
-        self._out = out
-
-    def fields(self, m):
-        return self._out.fields(int(self._src[m]))
-
-
 def _plan_output(engine, batch, p, with_seqs=True):
     """Plan exactly as the bench builds it, one checked run, the results on the host."""
     from paper_2511_00170_gb300 import ah
@@ -139,7 +115,7 @@ def test_plain_scale_full(engine):
     _check_properties(out, wl, wl.lengths().astype(np.int64))
     recs = _sample(wl.n_records, 12, 1)
     ref = oracle.run(wl.subset(recs))
-    sub = _Restricted(out, recs)
+    sub = compare.Restricted(out, recs)
     compare.assert_same_hits(sub, ref)
     compare.assert_same_amplicons(sub, ref, filtered=False)
     compare.assert_same_sequences(sub, ref)
@@ -171,7 +147,7 @@ def test_dense_full(engine):
     lengths = np.diff(wl.offsets).astype(np.int64)
     assert len(out.hits) > wl.total_bp // 1000 and len(out.amps) > wl.total_bp // 2000   # ~2 sites, ~1 amplicon per kb
     _check_properties(out, wl, lengths)
-    sub = _Restricted(out, recs)
+    sub = compare.Restricted(out, recs)
     ref_hits = oracle.scan(host)
     assert compare.gpu_hit_tuples(sub.hits) == compare.oracle_hit_tuples(ref_hits)
     ref_amps = oracle.pair(host, ref_hits)
@@ -221,7 +197,60 @@ def test_batched_full(engine):
         ah.ah_batch_free(batch)
     _check_properties(out, wl, np.diff(wl.offsets).astype(np.int64))
     ref = oracle.run(host)
-    sub = _Restricted(out, recs)
+    sub = compare.Restricted(out, recs)
     compare.assert_same_hits(sub, ref)
     compare.assert_same_amplicons(sub, ref, filtered=False)
     compare.assert_same_sequences(sub, ref)
+
+
+def test_serving_full():
+    """The serving database at full size (40,000 genomes, 151.5 Gbp resident, drawn and packed in
+    ranges as the bench does), 8 slots, the first requests of the Poisson trace with at most 12
+    pairs submitted together: each result, restricted to two sampled records of its range, equals
+    the oracle on those records (sites, amplicons, Tm, sequences)."""
+    import torch
+
+    import synth.gpu as sg
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Engine, Output
+
+    n_db = 40_000
+    lengths, _ = sg.serving_layout(n_genomes=n_db)
+    trace = [r for r in synth.serving_trace(synth.SEED, 60, 200.0, n_db) if len(r["fwd"]) <= 12][:6]
+    st = synth.Stream(synth.make_key(7, 4244, 0))
+    picks = {i: sorted({r["first_record"] + st.randint(0, r["n_records"] - 1) for _ in range(2)})
+             for i, r in enumerate(trace)}
+    wanted = sorted({g for v in picks.values() for g in v})
+    host = {}
+    eng = Engine(0)
+    db = ah.ah_batch_create(eng.ctx, np.asarray(lengths, dtype=np.uint64))
+    try:
+        for first, d, offs in sg.serving_db_chunks(n_genomes=n_db):
+            for g in wanted:
+                if first <= g < first + len(offs) - 1:
+                    host[g] = d[int(offs[g - first]):int(offs[g - first + 1])].cpu().numpy().copy()
+            ah.ah_batch_pack_range(eng.ctx, db, first, d.data_ptr(), offs.astype(np.uint64))
+            del d
+            torch.cuda.empty_cache()
+        srv = ah.ah_server_create(db, n_slots=8)
+        try:
+            keys = ("fwd", "rev", "k", "clamp", "first_record", "n_records", "min_len", "max_len", "orient_mask")
+            tickets = [ah.ah_server_submit(srv, **{k: r[k] for k in keys}) for r in trace]
+            results = [ah.ah_server_wait(srv, t) for t in tickets]
+        finally:
+            ah.ah_server_destroy(srv)
+    finally:
+        ah.ah_batch_free(db)
+        eng.close()
+    for i, (r, got) in enumerate(zip(trace, results)):
+        recs = picks[i]
+        seq = np.concatenate([host[g] for g in recs])
+        offs = np.concatenate([[0], np.cumsum([len(host[g]) for g in recs])]).astype(np.int64)
+        wl = synth.Workload("serving-sample", seq, offs, np.asarray(recs, dtype=np.uint32), list(r["fwd"]),
+                            list(r["rev"]), list(r["k"]), r["clamp"], r["min_len"], r["max_len"], r["orient_mask"],
+                            synth.TmParams(min_tm=None), False, 0, 0)
+        ref = oracle.run(wl)
+        sub = compare.Restricted(Output(got["hits"], got["amps"], got["arena"], got["field_off"]), recs)
+        compare.assert_same_hits(sub, ref)
+        compare.assert_same_amplicons(sub, ref, filtered=False)
+        compare.assert_same_sequences(sub, ref)
