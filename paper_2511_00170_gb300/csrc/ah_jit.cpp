@@ -140,74 +140,173 @@ Val or_reduce(Emitter& E, std::vector<Val> v) {
   return v[0];
 }
 
-// failure word of one pattern: bit set iff clamp mismatch or (#non-clamp mismatches >= k+1)
-Val gen_pattern(Emitter& E, const Pattern& P, std::map<std::pair<int, int>, bool>& used) {
-  std::vector<Val> fail_terms, x1;
+// carry-save reduction of the bits at each weight below wsat to at most one bit per weight; carries
+// at weight wsat or above are failures (the count has reached wsat > k)
+void reduce_bits(Emitter& E, std::map<int, std::vector<Val>>& bits, int wsat, std::vector<Val>& fail_terms) {
+  auto carry = [&](int w, const Val& c) {
+    if (w >= wsat)
+      fail_terms.push_back(c);
+    else
+      bits[w].push_back(c);
+  };
+  for (int w = 1; w < wsat; w *= 2) {
+    std::vector<Val> list = bits[w];
+    while (list.size() >= 3) {
+      std::vector<Val> nl;
+      size_t i = 0;
+      for (; i + 2 < list.size(); i += 3) {
+        nl.push_back(E.xor3(list[i], list[i + 1], list[i + 2]));
+        carry(2 * w, E.maj(list[i], list[i + 1], list[i + 2]));
+      }
+      for (; i < list.size(); ++i) nl.push_back(list[i]);
+      list.swap(nl);
+    }
+    if (list.size() == 2) {
+      const Val a = list[0], b = list[1];
+      list = {E.xor2(a, b)};
+      carry(2 * w, E.and2(a, b));
+    }
+    bits[w] = list;
+  }
+}
+
+// count >= T over the reduced bits (weights 1 .. wsat/2, at most one bit each), or nothing when the
+// count cannot reach T below wsat (T == wsat: the carries already say it)
+void count_ge(Emitter& E, std::map<int, std::vector<Val>>& bits, int wsat, int T, std::vector<Val>& fail_terms) {
+  if (T == wsat) return;
+  Val ge = ones();
+  for (int w = 1, i = 0; w < wsat; w *= 2, ++i) {
+    const Val b = bits[w].empty() ? Val{"", true, true} : bits[w][0];
+    const bool tbit = (T >> i) & 1;
+    if (ge.is_const && !ge.inv) {
+      ge = tbit ? b : ones();  // b & 1 = b ; b | 1 = 1
+    } else if (b.is_const) {
+      ge = tbit ? Val{"", true, true} : ge;  // 0 & ge = 0 ; 0 | ge = ge
+    } else {
+      ge = tbit ? E.and2(b, ge) : E.or2(b, ge);
+    }
+  }
+  if (!(ge.is_const && ge.inv)) fail_terms.push_back(ge);
+}
+
+// Failure word of one pattern: bit set iff a clamp position mismatches or the non-clamp mismatches
+// reach k+1.  Phase A (emitted with every pattern's, sharing shifted planes) covers the clamp and the
+// counted positions most likely to mismatch, until a window survives them with probability below
+// kSurvive; phase B adds the rest to the same carry-save sums.  The kernel runs phase B only when
+// some window of the warp survived phase A (a warp vote): for the others the answer is already
+// "fail", so the result is exact either way.
+struct PatternCode {
+  Val fail_a;                               // failure word after phase A (final without phase B)
+  bool has_b = false;
+  std::vector<std::pair<int, int>> planes_b;  // shifted planes phase B reads
+  std::string code_b;                       // phase B statements
+  Val fail_b;                               // final failure word, defined in code_b
+  int ops_b = 0;
+};
+
+constexpr double kSurvive = 1.5e-4;
+
+PatternCode gen_pattern(Emitter& EA, int* tmp, const Pattern& P, std::map<std::pair<int, int>, bool>& used_a) {
+  struct In {
+    Val x;
+    int kind, j;
+    double p_mis;
+  };
+  std::vector<In> clamp, counted;
   for (int j = 0; j < P.len; ++j) {
     int kind;
     bool inv;
     if (!set_plane(P.set[j], &kind, &inv)) continue;  // N never mismatches
-    used[{kind, j}] = true;
-    // mismatch bit: the complement of the match plane
-    const Val x{plane_name(kind, j), !inv, false};
-    if (j >= P.clamp_lo && j < P.clamp_hi)
-      fail_terms.push_back(x);
-    else
-      x1.push_back(x);
+    // mismatch bit: the complement of the match plane; its probability on uniform bases
+    const int n_bases = __builtin_popcount(P.set[j]);
+    In in{Val{plane_name(kind, j), !inv, false}, kind, j, (4 - n_bases) / 4.0};
+    (j >= P.clamp_lo && j < P.clamp_hi ? clamp : counted).push_back(in);
   }
   const int T = P.k + 1;  // failing count
-  if ((int)x1.size() >= T) {
-    int wsat = 1;
-    while (wsat < T) wsat *= 2;
-    if (wsat == 1) {
-      for (auto& x : x1) fail_terms.push_back(x);
-    } else {
-      std::map<int, std::vector<Val>> bits;
-      bits[1] = x1;
-      auto carry = [&](int w, const Val& c) {
-        if (w >= wsat)
-          fail_terms.push_back(c);
-        else
-          bits[w].push_back(c);
-      };
-      for (int w = 1; w < wsat; w *= 2) {
-        std::vector<Val> list = bits[w];
-        while (list.size() >= 3) {
-          std::vector<Val> nl;
-          size_t i = 0;
-          for (; i + 2 < list.size(); i += 3) {
-            nl.push_back(E.xor3(list[i], list[i + 1], list[i + 2]));
-            carry(2 * w, E.maj(list[i], list[i + 1], list[i + 2]));
-          }
-          for (; i < list.size(); ++i) nl.push_back(list[i]);
-          list.swap(nl);
-        }
-        if (list.size() == 2) {
-          const Val a = list[0], b = list[1];
-          list = {E.xor2(a, b)};
-          carry(2 * w, E.and2(a, b));
-        }
-        bits[w] = list;
+  int wsat = 1;
+  while (wsat < T) wsat *= 2;
+  // phase A: the clamp and the most mismatch-prone counted positions, until survival < kSurvive
+  std::stable_sort(counted.begin(), counted.end(), [](const In& a, const In& b) { return a.p_mis > b.p_mis; });
+  double p_clamp = 1.0;
+  for (const In& c : clamp) p_clamp *= 1.0 - c.p_mis;
+  size_t h = counted.size();
+  {
+    std::vector<double> dist(T + 1, 0.0);  // P(count = c) for c < T, dist[T]: count >= T
+    dist[0] = 1.0;
+    for (size_t i = 0; i < counted.size(); ++i) {
+      std::vector<double> nd(T + 1, 0.0);
+      for (int c = 0; c <= T; ++c) {
+        nd[std::min(T, c + 1)] += dist[c] * counted[i].p_mis;
+        nd[c] += dist[c] * (1.0 - counted[i].p_mis);
       }
-      if (T != wsat) {
-        // count >= T over the reduced low bits (weights 1 .. wsat/2), least significant first
-        Val ge = ones();
-        for (int w = 1, i = 0; w < wsat; w *= 2, ++i) {
-          const Val b = bits[w].empty() ? Val{"", true, true} : bits[w][0];
-          const bool tbit = (T >> i) & 1;
-          if (ge.is_const && !ge.inv) {
-            ge = tbit ? b : ones();  // b & 1 = b ; b | 1 = 1
-          } else if (b.is_const) {
-            ge = tbit ? Val{"", true, true} : ge;  // 0 & ge = 0 ; 0 | ge = ge
-          } else {
-            ge = tbit ? E.and2(b, ge) : E.or2(b, ge);
-          }
-        }
-        if (!(ge.is_const && ge.inv)) fail_terms.push_back(ge);
+      dist.swap(nd);
+      const double survive = p_clamp * (1.0 - dist[T]);
+      if (survive < kSurvive && counted.size() - (i + 1) >= 3) {
+        h = i + 1;
+        break;
       }
     }
   }
-  return or_reduce(E, fail_terms);
+  PatternCode out;
+  std::vector<Val> fail_terms;
+  for (const In& c : clamp) {
+    used_a[{c.kind, c.j}] = true;
+    fail_terms.push_back(c.x);
+  }
+  std::map<int, std::vector<Val>> bits;
+  for (size_t i = 0; i < h; ++i) {
+    used_a[{counted[i].kind, counted[i].j}] = true;
+    bits[1].push_back(counted[i].x);
+  }
+  if ((int)counted.size() < T) {  // the count can never fail: only the clamp decides
+    out.fail_a = or_reduce(EA, fail_terms);
+    return out;
+  }
+  if (wsat == 1) {  // k = 0: every counted mismatch fails
+    for (size_t i = 0; i < h; ++i) fail_terms.push_back(counted[i].x);
+  } else {
+    reduce_bits(EA, bits, wsat, fail_terms);
+  }
+  if (h == counted.size()) {
+    if (wsat > 1) count_ge(EA, bits, wsat, T, fail_terms);
+    out.fail_a = or_reduce(EA, fail_terms);
+    return out;
+  }
+  // phase A's failure word: the failures so far and the partial count reaching T
+  {
+    std::vector<Val> fa = fail_terms;
+    if (wsat > 1) {
+      std::map<int, std::vector<Val>> partial = bits;
+      count_ge(EA, partial, wsat, T, fa);
+    }
+    out.fail_a = or_reduce(EA, fa);
+  }
+  // phase B: the remaining positions join the same sums.  A count that reached T in phase A only
+  // grows, so phase A's failure word is part of the final one; phase B adds its own carries past
+  // wsat and the final comparison.
+  Emitter EB;
+  EB.tmp = *tmp > EA.tmp ? *tmp : EA.tmp;
+  std::map<std::pair<int, int>, bool> seen;
+  std::vector<Val> fail_b{out.fail_a};
+  for (size_t i = h; i < counted.size(); ++i) {
+    const std::pair<int, int> pl{counted[i].kind, counted[i].j};
+    if (!seen.count(pl)) out.planes_b.push_back(pl), seen[pl] = true;
+    if (wsat == 1)
+      fail_b.push_back(counted[i].x);
+    else
+      bits[1].push_back(counted[i].x);
+  }
+  if (wsat > 1) {
+    reduce_bits(EB, bits, wsat, fail_b);
+    count_ge(EB, bits, wsat, T, fail_b);
+  }
+  out.fail_b = or_reduce(EB, fail_b);
+  out.has_b = true;
+  out.code_b = EB.os.str();
+  out.ops_b = EB.ops;
+  EA.tmp = EB.tmp;  // temporaries stay unique across phases
+  *tmp = EB.tmp;
+  return out;
 }
 
 const char* kPrelude = R"(
@@ -302,18 +401,25 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg,
   // body: per group of 32 positions
   Emitter E;
   std::map<std::pair<int, int>, bool> used;
-  std::vector<std::string> fails(Q);
-  for (int q = 0; q < Q; ++q) fails[q] = expr_of(gen_pattern(E, pats[q], used));
+  std::vector<PatternCode> pc(Q);
+  int tmpc = 0;
+  for (int q = 0; q < Q; ++q) pc[q] = gen_pattern(E, &tmpc, pats[q], used);
   bool kind_used[K_COUNT] = {};
   for (auto& u : used) kind_used[u.first.first] = true;
+  for (auto& c : pc)
+    for (auto& pl : c.planes_b) kind_used[pl.first] = true;
   if (alu_ops_per_group) {
-    // the circuit's ALU instructions per group of 32 positions: LOP3 of the trees, one funnel
-    // shift per (plane, offset) used, plane derivations (one per derived kind and word), and the
-    // AND-reduction of failure words per block of four patterns
-    int shifts = 0, derived = 0;
+    // the circuit's ALU instructions per group of 32 positions when every phase runs: LOP3 of the
+    // trees, one funnel shift per (plane, offset), plane derivations (one per derived kind and
+    // word), and the AND-reduction of failure words per block of four patterns
+    int shifts = 0, derived = 0, ops_b = 0;
     for (auto& u : used) shifts += u.first.second > 0;
+    for (auto& c : pc) {
+      ops_b += c.ops_b;
+      for (auto& pl : c.planes_b) shifts += pl.second > 0 && !used.count(pl);
+    }
     for (int k = 0; k < K_COUNT; ++k) derived += kind_used[k] && k != K_LO && k != K_HI ? 2 : 0;
-    *alu_ops_per_group = E.ops + shifts + derived + 2 * ((Q + 3) / 4);
+    *alu_ops_per_group = E.ops + ops_b + shifts + derived + 2 * ((Q + 3) / 4);
   }
 
   // one block of the launch: NT threads x GPT groups of 32 positions, from group_begin
@@ -335,35 +441,44 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg,
     for (int w = 0; w < 2; ++w) os << "    const u32 " << kKindName[k] << w << " = " << kind_expr(k, w) << ";\n";
   }
   int nshift = 0;
-  for (auto& u : used) {
-    int kind = u.first.first, j = u.first.second;
+  auto emit_shift = [&](int kind, int j, const char* indent) {
     const std::string name = plane_name(kind, j), w0 = std::string(kKindName[kind]) + "0",
                       w1 = std::string(kKindName[kind]) + "1";
     if (j == 0) {
-      os << "    const u32 " << name << " = " << w0 << ";\n";
-      continue;
+      os << indent << "const u32 " << name << " = " << w0 << ";\n";
+      return;
     }
     const bool by_multiply = cfg.shift_mode == 1 || (cfg.shift_mode == 2 && (nshift++ & 1));
     if (!by_multiply) {
-      os << "    const u32 " << name << " = fshr(" << w0 << ", " << w1 << ", " << j << "u);\n";
+      os << indent << "const u32 " << name << " = fshr(" << w0 << ", " << w1 << ", " << j << "u);\n";
     } else {
       // (w0 >> j) | (w1 << (32 - j)) as hi(w0 * 2^(32-j)) + lo(w1 * 2^(32-j)): two integer
       // multiply-adds on the FMA pipe instead of one funnel shift on the ALU pipe
       const unsigned long long m = 1ull << (32 - j);
-      os << "    u32 " << name << ";\n    { u32 t_; asm(\"mul.lo.u32 %0, %1, " << m << ";\" : \"=r\"(t_) : \"r\"(" << w1
-         << ")); asm(\"mad.hi.u32 %0, %1, " << m << ", %2;\" : \"=r\"(" << name << ") : \"r\"(" << w0
-         << "), \"r\"(t_)); }\n";
+      os << indent << "u32 " << name << ";\n" << indent << "{ u32 t_; asm(\"mul.lo.u32 %0, %1, " << m
+         << ";\" : \"=r\"(t_) : \"r\"(" << w1 << ")); asm(\"mad.hi.u32 %0, %1, " << m << ", %2;\" : \"=r\"(" << name
+         << ") : \"r\"(" << w0 << "), \"r\"(t_)); }\n";
     }
-  }
+  };
+  for (auto& u : used) emit_shift(u.first.first, u.first.second, "    ");
   os << "    {\n" << E.os.str();
+  // phase B of each pattern, only for warps with a window that survived phase A
+  for (int q = 0; q < Q; ++q) {
+    os << "      u32 f" << q << " = " << expr_of(pc[q].fail_a) << ";\n";
+    if (!pc[q].has_b) continue;
+    os << "      if (__any_sync(__activemask(), ~f" << q << ")) {\n";
+    for (auto& pl : pc[q].planes_b)
+      if (!used.count(pl)) emit_shift(pl.first, pl.second, "        ");
+    os << pc[q].code_b;
+    os << "        f" << q << " = " << expr_of(pc[q].fail_b) << ";\n      }\n";
+  }
   // hit words and the rare emission path, in blocks of four patterns
   for (int q0 = 0; q0 < Q; q0 += 4) {
     int q1 = std::min(Q, q0 + 4);
     os << "      if (__builtin_expect((";
-    for (int q = q0; q < q1; ++q) os << (q > q0 ? " & " : "") << fails[q];
+    for (int q = q0; q < q1; ++q) os << (q > q0 ? " & " : "") << "f" << q;
     os << ") != 0xffffffffu, 0)) {\n";
-    for (int q = q0; q < q1; ++q)
-      os << "        if (~" << fails[q] << ") emit(~" << fails[q] << ", " << q << ", g, a, b, P);\n";
+    for (int q = q0; q < q1; ++q) os << "        if (~f" << q << ") emit(~f" << q << ", " << q << ", g, a, b, P);\n";
     os << "      }\n";
   }
   os << "    }\n  }\n}\n";

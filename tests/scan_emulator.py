@@ -29,8 +29,9 @@ def _expr(e, env):
     return np.asarray(eval(e, {"np": np, "M": M, "fshr": fshr}, env), dtype=np.uint32)
 
 
-def failure_words(src, lo0, hi0, lo1, hi1):
-    """Run the generated body; returns the failure word of every pattern."""
+def failure_words(src, lo0, hi0, lo1, hi1, phase_a=None):
+    """Run the generated body; returns the failure word of every pattern.  With phase_a (a list),
+    also appends each pattern's phase-A word (the word before the warp-vote branch) to it."""
     body = src[src.index("const u32 lo0 = a.x"):src.index("if (__builtin_expect")]
     env = {"lo0": lo0, "hi0": hi0, "lo1": lo1, "hi1": hi1}
     zero = np.zeros_like(lo0)
@@ -39,6 +40,15 @@ def failure_words(src, lo0, hi0, lo1, hi1):
         if m:
             if m.group(1) not in env:
                 env[m.group(1)] = _expr(m.group(2), env)
+            continue
+        # a pattern's failure word: phase A's value, then (inside the warp-vote branch, which every
+        # emulated lane takes) the final value after phase B; lanes whose windows all failed phase A
+        # are left with phase A's word, which is already all ones
+        m = re.match(r"\s*(u32 )?(f\d+) = (.*?);$", line)
+        if m:
+            env[m.group(2)] = zero | _expr(m.group(3), env)   # constants become one word per lane
+            if m.group(1):
+                env["phase_a_" + m.group(2)] = env[m.group(2)]
             continue
         m = re.match(r'\s*u32 (\w+); asm\("lop3.b32 %0, %1, %2, %3, (0x[0-9a-f]+);" : "=r"\(\w+\) : '
                      r'"r"\((\w+)\), "r"\((\w+)\), "r"\((\w+)\)\);', line)
@@ -51,6 +61,9 @@ def failure_words(src, lo0, hi0, lo1, hi1):
                     r |= (a if idx & 4 else M ^ a) & (b if idx & 2 else M ^ b) & (c if idx & 1 else M ^ c)
             env[m.group(1)] = r
     out = []
+    if phase_a is not None:
+        for f in re.findall(r"if \(~(\(~\w+\)|\w+)\) emit", src):
+            phase_a.append(env.get("phase_a_" + f, env.get(f)))
     for f in re.findall(r"if \(~(\(~\w+\)|\w+)\) emit", src):
         if f.startswith("(~"):
             out.append(M ^ env[f[2:-1]])

@@ -1,7 +1,8 @@
 """The bit-sliced scan logic generated for a primer set (IUPAC plane selection, funnel shifts, the
 carry-save counter tree and clamp terms as LOP3 truth tables), run on the CPU, equals an exact
-per-position mismatch count and clamp check on random data.  No GPU is needed: the generated
-statements are executed with numpy."""
+per-position mismatch count and clamp check on random data, and every window its first phase
+(clamp and most selective positions, after which a warp may skip the rest) fails does fail.  No
+GPU is needed: the generated statements are executed with numpy."""
 import os
 import subprocess
 
@@ -39,11 +40,16 @@ def _check(dump, k, clamp, primers, seed, n=2000):
     src = dump(k, clamp, primers)
     rng = np.random.default_rng(seed)
     planes = [rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32) for _ in range(4)]
-    got = scan_emulator.failure_words(src, *planes)
+    phase_a = []
+    got = scan_emulator.failure_words(src, *planes, phase_a=phase_a)
     want = scan_emulator.exact_failure_words(primers, k, clamp, *planes)
     assert len(got) == len(want) == 2 * len(primers)
     for q, (g, w) in enumerate(zip(got, want)):
         assert np.array_equal(g, w), f"pattern {q}: {int(np.count_nonzero(g != w))} words differ"
+    # the warp vote may skip phase B only where phase A already says "fail": every window phase A
+    # fails must fail in the end
+    for q, (a, w) in enumerate(zip(phase_a, want)):
+        assert not np.any(a & ~w), f"pattern {q}: phase A fails a window that matches"
 
 
 @pytest.mark.parametrize("k,clamp,primers", CASES)
