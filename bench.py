@@ -60,7 +60,7 @@ def alg_ops_per_base(fwd, rev, clamp):
 # what identifies the kernel: LOP3/SHF per 32 positions of its circuit, threads, groups per thread,
 # shift mode, persistent.  A kernel not in this table reports traffic null.
 SCAN_TRAFFIC = {
-    (178, 256, 8, 0, 0): 1_910_984_960 / 7_536_412_189,
+    (188, 256, 8, 0, 0): 1_910_472_704 / 7_536_412_189,
 }
 
 
@@ -70,9 +70,10 @@ def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms, shape=None):
     positions per lane-op) times the bases of the launch, over its CUDA-event time.  The generated
     circuit needs fewer instructions than that count (it shares plane derivations and shifts across
     patterns, reads two-base IUPAC sets straight from the code planes and folds the counter tree),
-    so the algorithmic fraction can exceed 1; the circuit's own instruction count and the fraction of
-    the ALU pipe it keeps busy are under `circuit`.  `shape` = (threads, groups per thread, shift
-    mode, persistent) of the launch."""
+    and a warp skips a pattern's second phase when every one of its windows already failed the
+    first, so the algorithmic fraction can exceed 1.  `circuit` gives the generator's instruction
+    count with every phase run (an upper bound on what executes).  `shape` = (threads, groups per
+    thread, shift mode, persistent) of the launch."""
     ops = ops_per_group / 32.0
     per_base = SCAN_TRAFFIC.get((ops_per_group,) + tuple(shape)) if shape is not None else None
     traffic = per_base * bases if per_base is not None else None
@@ -90,7 +91,8 @@ def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms, shape=None):
             "ops_per_base": norm, "ops_source": "algorithmic: sum over oriented patterns of (3 (L - c) + 2 c) / 32",
             "peak_source": "derived: 152 SMs x 64 ALU lanes/clk x 2.07 GHz",
             "circuit": {"ops_per_base": ops, "achieved": circuit, "frac": circuit / ALU_PEAK_TOPS,
-                        "source": "LOP3 + funnel shifts of the generated circuit (the generator's exact count)"},
+                        "source": "LOP3 + funnel shifts of the generated circuit with every phase run "
+                                  "(warps skip phase two when all their windows failed phase one)"},
             "hbm": {"achieved_gbs": hbm, "peak_gbs": hbm_peak,
                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "frac": hbm / hbm_peak,
                     "algorithmic_bytes_per_base": 0.25}}
