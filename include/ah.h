@@ -153,6 +153,20 @@ ah_status ah_pack_batch_device(ah_ctx* ctx, uint32_t n_rec, const uint8_t* d_seq
 /* Streaming: lay out a batch for n_rec records of the given lengths (device memory allocated, nothing
  * packed), then pack consecutive record ranges into it with ah_batch_pack_range.  Synchronises. */
 ah_status ah_batch_create(ah_ctx* ctx, uint32_t n_rec, const uint64_t* lens, const uint32_t* genome_ids, ah_batch** out);
+/* Store and reload a packed batch (Section "Implementations": AHv2 keeps genomes as 2-bit batches
+ * on disk and streams those).  ah_batch_export copies the bases out in the device layout: planes
+ * (uint2[n_groups], 0.25 bytes per base; n_groups from ah_batch_view_get) and, sparsely, the
+ * nonzero invalid words (group index and word; about 1 % of groups at 0.5 % N, plus padding).
+ * *n_invalid: capacity in, count out; with NULL lists only the count.  AH_EOVERFLOW when the lists
+ * are too short.  Synchronises.
+ * ah_batch_import copies them into a batch laid out for the same record lengths (ah_batch_create),
+ * clearing the other invalid words: 4x fewer bytes over the host link than ASCII.  Page-locked
+ * buffers move at the full link rate.  AH_EINVAL for a group index past the batch.  Synchronises. */
+ah_status ah_batch_export(const ah_batch* b, void* planes_out, uint64_t* n_invalid, uint64_t* inv_groups,
+                          uint32_t* inv_words);
+ah_status ah_batch_import(ah_ctx* ctx, ah_batch* b, const void* planes, uint64_t n_invalid, const uint64_t* inv_groups,
+                          const uint32_t* inv_words);
+
 /* Pack records [first, first + count) of b: d_seq holds them back to back, at any alignment, in
  * device memory (packed in place) or host memory (copied in chunks as ah_pack_batch does), and h_offsets
  * (host, count + 1 entries, starting at 0) delimits them; their lengths must match the layout.

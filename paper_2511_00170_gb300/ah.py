@@ -101,6 +101,8 @@ SIGNATURES = {
     "ah_ctx_set_scan_config": (_I32, [_VP, _I32, _I32, _I32, _I32]),
     "ah_pack_batch": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
     "ah_pack_batch_device": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
+    "ah_batch_export": (_I32, [_VP, _VP, ctypes.POINTER(ctypes.c_uint64), _VP, _VP]),
+    "ah_batch_import": (_I32, [_VP, _VP, _VP, _U64, _VP, _VP]),
     "ah_batch_view_get": (_I32, [_VP, ctypes.POINTER(ah_batch_view)]),
     "ah_batch_slice": (_I32, [_VP, _VP, _U32, _U32, _PVP]),
     "ah_batch_create": (_I32, [_VP, _U32, _VP, _VP, _PVP]),
@@ -236,6 +238,30 @@ def ah_pack_batch_device(ctx, d_seq: int, offsets: np.ndarray, genome_ids: Optio
     _check(load().ah_pack_batch_device(ctx, len(offsets) - 1, d_seq, offsets.ctypes.data,
                                        None if gid is None else gid.ctypes.data, ctypes.byref(out)), ctx)
     return out
+
+
+def ah_batch_export(batch, planes: Optional[np.ndarray] = None, groups: Optional[np.ndarray] = None,
+                    words: Optional[np.ndarray] = None):
+    """Packed bases of a batch for storage: (planes uint32[n_groups, 2], invalid group indices uint64,
+    invalid words uint32).  Caller arrays (e.g. page-locked) may be passed in; the lists are sized by
+    a first counting call."""
+    v = ah_batch_view_get(batch)
+    if planes is None:
+        planes = np.empty((v["n_groups"], 2), dtype=np.uint32)
+    n = ctypes.c_uint64(0)
+    _check(load().ah_batch_export(batch, None, ctypes.byref(n), None, None))
+    if groups is None:
+        groups = np.empty(n.value, dtype=np.uint64)
+    if words is None:
+        words = np.empty(n.value, dtype=np.uint32)
+    n2 = ctypes.c_uint64(len(groups))
+    _check(load().ah_batch_export(batch, planes.ctypes.data, ctypes.byref(n2), groups.ctypes.data, words.ctypes.data))
+    return planes, groups[:n2.value], words[:n2.value]
+
+
+def ah_batch_import(ctx, batch, planes: np.ndarray, groups: np.ndarray, words: np.ndarray) -> None:
+    _check(load().ah_batch_import(ctx, batch, planes.ctypes.data, len(groups), groups.ctypes.data if len(groups) else None,
+                                  words.ctypes.data if len(words) else None), ctx)
 
 
 def ah_batch_view_get(batch) -> dict:

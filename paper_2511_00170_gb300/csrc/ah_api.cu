@@ -139,6 +139,18 @@ __global__ void k_pack16u(const uint8_t* __restrict__ src, const PackItem* __res
   }
 }
 
+// sparse invalid words back into a batch's bitmap; an index past the batch is refused (status bit)
+__global__ void k_scatter_invalid(const uint64_t* __restrict__ groups, const uint32_t* __restrict__ words, uint64_t n,
+                                  uint32_t* __restrict__ invalid, uint64_t n_groups, uint32_t* status) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t g = groups[i];
+    if (g < n_groups)
+      invalid[g] = words[i];
+    else
+      atomicOr(status, (uint32_t)ST_BAD_INPUT);
+  }
+}
+
 void free_batch_arrays(ah_batch* b) {
   if (!b || !b->ctx) return;
   dfree(b->ctx, b->rec_group);
@@ -627,6 +639,60 @@ ah_status ah_batch_pack_range(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t
     src[i] = (const char*)d_seq + h_offsets[i];
   }
   return pack_records(ctx, b, first, count, src.data());
+}
+
+ah_status ah_batch_export(const ah_batch* b, void* planes_out, uint64_t* n_invalid, uint64_t* inv_groups,
+                          uint32_t* inv_words) {
+  if (!b || !b->ctx || !n_invalid) return AH_EINVAL;
+  ah_ctx* ctx = b->ctx;
+  cudaSetDevice(ctx->device);
+  std::vector<uint32_t> inv(b->n_groups);
+  AH_CUDA(ctx, cudaMemcpyAsync(inv.data(), b->invalid, b->n_groups * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  if (planes_out)
+    AH_CUDA(ctx, cudaMemcpyAsync(planes_out, b->planes, b->n_groups * sizeof(uint2), cudaMemcpyDeviceToHost, ctx->stream));
+  AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  uint64_t n = 0;
+  for (uint64_t g = 0; g < b->n_groups; ++g) n += inv[g] != 0;
+  const uint64_t cap = *n_invalid;
+  *n_invalid = n;
+  if (!inv_groups || !inv_words) return AH_OK;
+  if (cap < n) return fail(ctx, AH_EOVERFLOW, "ah_batch_export: %llu invalid words, room for %llu", (unsigned long long)n,
+                           (unsigned long long)cap);
+  uint64_t j = 0;
+  for (uint64_t g = 0; g < b->n_groups; ++g)
+    if (inv[g]) inv_groups[j] = g, inv_words[j] = inv[g], ++j;
+  return AH_OK;
+}
+
+ah_status ah_batch_import(ah_ctx* ctx, ah_batch* b, const void* planes, uint64_t n_invalid, const uint64_t* inv_groups,
+                          const uint32_t* inv_words) {
+  if (!ctx || !b || !planes || (n_invalid && (!inv_groups || !inv_words)) || b->view)
+    return fail(ctx, AH_EINVAL, "ah_batch_import: bad arguments");
+  if (!usable(ctx, b)) return fail(ctx, AH_EINVAL, "ah_batch_import: batch of another device");
+  for (uint64_t i = 0; i < n_invalid; ++i)
+    if (inv_groups[i] >= b->n_groups)
+      return fail(ctx, AH_EINVAL, "ah_batch_import: invalid word %llu at group %llu, past the batch's %llu groups",
+                  (unsigned long long)i, (unsigned long long)inv_groups[i], (unsigned long long)b->n_groups);
+  cudaSetDevice(ctx->device);
+  AH_CUDA(ctx, cudaMemcpyAsync(b->planes, planes, b->n_groups * sizeof(uint2), cudaMemcpyHostToDevice, ctx->stream));
+  AH_CUDA(ctx, cudaMemsetAsync(b->invalid, 0, b->n_groups * sizeof(uint32_t), ctx->stream));
+  if (n_invalid) {
+    uint64_t* dg = nullptr;
+    uint32_t* dw = nullptr;
+    ah_status st;
+    if ((st = dalloc(ctx, &dg, n_invalid)) || (st = dalloc(ctx, &dw, n_invalid))) return st;
+    AH_CUDA(ctx, cudaMemcpyAsync(dg, inv_groups, n_invalid * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
+    AH_CUDA(ctx, cudaMemcpyAsync(dw, inv_words, n_invalid * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+    k_scatter_invalid<<<(unsigned)std::min<uint64_t>((n_invalid + 255) / 256, 65535), 256, 0, ctx->stream>>>(
+        dg, dw, n_invalid, b->invalid, b->n_groups, ctx->d_status);
+    launched(ctx);
+    AH_CUDA(ctx, cudaGetLastError());
+    dfree(ctx, dg);
+    dfree(ctx, dw);
+  }
+  AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx);
 }
 
 ah_status ah_batch_view_get(const ah_batch* b, ah_batch_view* out) {

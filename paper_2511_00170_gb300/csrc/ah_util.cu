@@ -37,6 +37,7 @@ ah_status check_status(ah_ctx* ctx) {
     AH_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), ctx->stream));
     if (s & ST_SCAN_MISMATCH)
       return fail(ctx, AH_EINTERNAL, "device self-check: bit-sliced matcher disagreed with the exact re-check");
+    if (s & ST_BAD_INPUT) return fail(ctx, AH_EINVAL, "device input check: an index past the batch");
     if (s & ST_TM_LIMIT)
       return fail(ctx, AH_ELIMIT,
                   "degenerate site Tm: more qualifying primer variants than the enumeration bound, and the chain "

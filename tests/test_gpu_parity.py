@@ -369,3 +369,36 @@ def test_pairs_per_kernel(engine, pairs_per_kernel):
         _run_both(engine, wl)
     finally:
         ah.ah_ctx_set_pairs_per_kernel(engine.ctx, 0)
+
+
+def test_batch_export_import(engine):
+    """A packed batch exported (dense planes, sparse invalid words) and imported into a fresh layout
+    gives the same planes, invalid words and outputs; an index past the batch is refused."""
+    import torch
+
+    from paper_2511_00170_gb300 import ah
+
+    wl = synth.random_small(23, n_records=30, len_lo=0, len_hi=4000, n_frac=0.03, alphabet="ACGTacgtRYN", plant=2)
+    a = engine.pack(wl.seq, wl.offsets)
+    b = ah.ah_batch_create(engine.ctx, wl.lengths().astype(np.uint64))
+    try:
+        planes, groups, words = ah.ah_batch_export(a)
+        v = ah.ah_batch_view_get(a)
+        assert planes.shape == (v["n_groups"], 2) and len(groups) == len(words) > 0
+        ah.ah_batch_import(engine.ctx, b, planes, groups, words)
+        p2, g2, w2 = ah.ah_batch_export(b)
+        assert np.array_equal(planes, p2) and np.array_equal(groups, g2) and np.array_equal(words, w2)
+        from paper_2511_00170_gb300.pipeline import Params
+
+        p = Params.from_workload(wl)
+        o1, o2 = engine.step(a, p), engine.step(b, p)
+        assert o1.hits.tobytes() == o2.hits.tobytes() and o1.amps.tobytes() == o2.amps.tobytes()
+        assert o1.arena == o2.arena
+        bad = groups.copy()
+        bad[0] = v["n_groups"]
+        with pytest.raises(ah.AhError) as e:
+            ah.ah_batch_import(engine.ctx, b, planes, bad, words)
+        assert e.value.status == ah.AH_EINVAL
+    finally:
+        ah.ah_batch_free(a)
+        ah.ah_batch_free(b)
