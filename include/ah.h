@@ -83,7 +83,9 @@ typedef struct {
   uint64_t jit_compiles;    /* scan kernels compiled at run time (NVRTC) */
   double jit_ms;            /* host time spent compiling them */
   int32_t scan_ops_per_group; /* ALU instructions (LOP3 and funnel shifts) of the last scan's
-                                 generated circuits (all its kernels) per 32 positions */
+                                 generated circuits (all its kernels) per 32 positions; 0 after a
+                                 scan by the generic kernel */
+  uint64_t generic_scans;   /* scans run by the generic (compile-free) kernel */
 } ah_ctx_stats;
 ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out);
 ah_status ah_ctx_stats_reset(ah_ctx* ctx);
@@ -93,6 +95,22 @@ ah_status ah_ctx_stats_reset(ah_ctx* ctx);
  * shares more work between patterns and scans fastest.  Plans always use one kernel.  Generated
  * kernels are cached process-wide, keyed by their source.  AH_EINVAL outside 0..256. */
 ah_status ah_ctx_set_pairs_per_kernel(ah_ctx* ctx, int pairs);
+
+/* Which scan kernel regular scans (ah_scan_primers) use; all find the same sites (Supplementary,
+ * "Primer matching and clamp logic").
+ *   0 (the default): kernels generated and compiled for the primer set (on first use, then cached
+ *     process-wide).
+ *   1: the generic kernel built into the library, which reads the primer set from a table and needs
+ *     no compile, but scans several times slower.
+ *   2: the generated kernels when they are compiled already.  Otherwise a scan of at most 2^34
+ *     base-patterns (bases x 4 x pairs) runs on the generic kernel alone; a larger one runs the
+ *     generic kernel over leading tiles while a host thread compiles the generated kernels, and
+ *     those over the rest once they are ready.  Server contexts always take the second way and do
+ *     not wait for a compile that the generic kernel outlasted.
+ *   3: the generic kernel over the first half of the tiles and the generated kernels over the rest
+ *     (a fixed hand-over point, for tests).
+ * Plans always use a generated kernel.  AH_EINVAL for another mode. */
+ah_status ah_ctx_set_generic_scan(ah_ctx* ctx, int mode);
 
 /* Time every scan launch with CUDA events on the context's stream (scan_ms).  Synchronises the
  * stream to collect the timings of plan replays still pending. */

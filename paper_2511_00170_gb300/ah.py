@@ -76,7 +76,7 @@ class ah_result(ctypes.Structure):
 class ah_ctx_stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("scan_launches", ctypes.c_uint64), ("scan_ms", ctypes.c_double),
                 ("scan_bases", ctypes.c_uint64), ("jit_compiles", ctypes.c_uint64), ("jit_ms", ctypes.c_double),
-                ("scan_ops_per_group", ctypes.c_int32)]
+                ("scan_ops_per_group", ctypes.c_int32), ("generic_scans", ctypes.c_uint64)]
 
 
 class ah_batch_view(ctypes.Structure):
@@ -97,6 +97,7 @@ SIGNATURES = {
     "ah_ctx_stats_get": (_I32, [_VP, ctypes.POINTER(ah_ctx_stats)]),
     "ah_ctx_stats_reset": (_I32, [_VP]),
     "ah_ctx_set_pairs_per_kernel": (_I32, [_VP, ctypes.c_int]),
+    "ah_ctx_set_generic_scan": (_I32, [_VP, ctypes.c_int]),
     "ah_ctx_set_timing": (_I32, [_VP, _I32]),
     "ah_ctx_set_scan_config": (_I32, [_VP, _I32, _I32, _I32, _I32]),
     "ah_pack_batch": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
@@ -204,6 +205,12 @@ def ah_ctx_stats_reset(ctx) -> None:
 
 def ah_ctx_set_pairs_per_kernel(ctx, pairs: int) -> None:
     _check(load().ah_ctx_set_pairs_per_kernel(ctx, int(pairs)), ctx)
+
+
+def ah_ctx_set_generic_scan(ctx, mode: int) -> None:
+    """0: generated scan kernels; 1: the generic (compile-free) kernel; 2: the generic kernel while the
+    primer set's kernels compile; 3: generic on the first half of the tiles, generated on the rest."""
+    _check(load().ah_ctx_set_generic_scan(ctx, int(mode)), ctx)
 
 
 def ah_ctx_set_timing(ctx, enable: bool) -> None:

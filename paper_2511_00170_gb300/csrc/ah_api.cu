@@ -360,6 +360,7 @@ ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out) {
   out->jit_compiles = ctx->jit_compiles;
   out->jit_ms = ctx->jit_ms;
   out->scan_ops_per_group = ctx->scan_ops_per_group;
+  out->generic_scans = ctx->n_generic_scans;
   return AH_OK;
 }
 
@@ -367,7 +368,7 @@ ah_status ah_ctx_stats_reset(ah_ctx* ctx) {
   if (!ctx) return AH_EINVAL;
   ah_status st = drain_timings(ctx);  // timings of replays before the reset do not count after it
   if (st) return st;
-  ctx->n_launches = ctx->n_scan_launches = ctx->scan_bases = ctx->jit_compiles = 0;
+  ctx->n_launches = ctx->n_scan_launches = ctx->scan_bases = ctx->jit_compiles = ctx->n_generic_scans = 0;
   ctx->scan_ms = ctx->jit_ms = 0.0;
   return AH_OK;
 }
@@ -388,6 +389,13 @@ ah_status ah_ctx_set_pairs_per_kernel(ah_ctx* ctx, int pairs) {
   if (!ctx) return AH_EINVAL;
   if (pairs < 0 || pairs > 256) return fail(ctx, AH_EINVAL, "ah_ctx_set_pairs_per_kernel: 0..256");
   ctx->scan_cfg.pairs_per_kernel = pairs;
+  return AH_OK;
+}
+
+ah_status ah_ctx_set_generic_scan(ah_ctx* ctx, int mode) {
+  if (!ctx) return AH_EINVAL;
+  if (mode < 0 || mode > 3) return fail(ctx, AH_EINVAL, "ah_ctx_set_generic_scan: mode 0 to 3");
+  ctx->generic_scan = mode;
   return AH_OK;
 }
 
@@ -779,7 +787,10 @@ ah_status ah_primers_create(ah_ctx* ctx, uint32_t n_pairs, const char* const* fw
   ah_status st = dalloc(ctx, &p->d_plen, plen.size());
   if (!st) st = dalloc(ctx, &p->d_psets, psets.size());
   if (!st) st = dalloc(ctx, &p->d_pk, p->k.size());
+  const std::vector<GenPattern> gen = gen_table(p->pats);
+  if (!st) st = dalloc(ctx, &p->d_gen, gen.size());
   if (!st) {
+    cudaMemcpyAsync(p->d_gen, gen.data(), gen.size() * sizeof(GenPattern), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemcpyAsync(p->d_plen, plen.data(), plen.size(), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemcpyAsync(p->d_psets, psets.data(), psets.size(), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemcpyAsync(p->d_pk, p->k.data(), p->k.size(), cudaMemcpyHostToDevice, ctx->stream);
@@ -799,6 +810,7 @@ void ah_primers_free(ah_primers* p) {
     dfree(p->ctx, p->d_plen);
     dfree(p->ctx, p->d_psets);
     dfree(p->ctx, p->d_pk);
+    dfree(p->ctx, p->d_gen);
   }
   delete p;
 }

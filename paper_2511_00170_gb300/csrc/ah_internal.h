@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <atomic>
 #include <cstdio>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -47,6 +49,23 @@ struct Pattern {
   uint16_t id;         // 4 * pair + orient
 };
 
+// One oriented pattern as the generic (compile-free) scan kernel reads it.  The evaluated positions
+// (N excluded) come clamp first, then the counted ones most likely to mismatch first; position e
+// has offset j[e] in the window and mismatch bit c0 ^ (lo & c1) ^ (hi & c2) ^ (lo & hi & c3) of
+// the base's code bits, x[e] = (c0, c1, c2, c3), each 0 or ~0.
+struct alignas(16) GenPattern {
+  uint4 x[32];
+  uint8_t j[32];
+  uint32_t mset[4];     // bit j of mset[c]: position j's set holds code c (A, C, T, G)
+  uint32_t clamp_mask;  // bits of the clamp positions
+  uint8_t len, k, n_eval, n_clamp;
+  uint16_t pair;
+  uint8_t orient;
+  uint8_t width;        // counter bits: the least w with 2^w >= k + 1
+};
+std::vector<GenPattern> gen_table(const std::vector<Pattern>& pats);
+constexpr int kGenMaxPatterns = 64;  // patterns per generic launch (the table sits in shared memory)
+
 struct ScanConfig {
   int threads = 128;        // threads per CTA (128 x 8 was fastest for a single pair in a sweep on GB300)
   int groups_per_thread = 8;
@@ -81,6 +100,16 @@ struct ah_ctx {
   uint64_t jit_compiles = 0;
   double jit_ms = 0.0;
   int scan_ops_per_group = 0;  // of the last scan kernel launched
+  // scan kernel choice: 0 generated kernels, 1 the generic kernel, 2 the generic kernel while a
+  // primer set's generated kernels compile (see launch_scan)
+  int generic_scan = 0;
+  uint64_t n_generic_scans = 0;
+  // mode 2 with this set: starts compiling the kernels of these pattern groups on a thread the
+  // caller owns and returns a flag the compile sets (1 done, 2 failed); the scan does not wait for
+  // it once the generic kernel has covered the batch (a server joins the thread later)
+  std::function<std::shared_ptr<std::atomic<int>>(const std::vector<std::vector<ah::Pattern>>&,
+                                                  const ah::ScanConfig&)>
+      compile_behind;
   bool timing = false;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   // scan-node timings of graph replays: event pairs recorded by the graph, read when the stream is
@@ -116,6 +145,7 @@ struct ah_primers {
   uint8_t* d_plen = nullptr;           // per pattern length
   uint8_t* d_psets = nullptr;          // [n_pairs][2 primers][32] IUPAC sets of the primers as written
   uint8_t* d_pk = nullptr;             // [n_pairs] mismatch budget
+  ah::GenPattern* d_gen = nullptr;     // the patterns as the generic scan kernel reads them
 };
 
 struct ah_hits {
@@ -239,10 +269,18 @@ class JitCache {
   // several pattern sets, the missing kernels compiled on parallel host threads
   ah_status get_many(ah_ctx* ctx, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg,
                      std::vector<ScanKernel>* out);
+  // every set's kernel compiled and loaded for this device (starts no compile)
+  bool ready(int device, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg);
+  // compiles the sets' missing kernels for this device (parallel host threads) and returns the
+  // first failure's status; for a background thread (no context, no compile counters)
+  ah_status prefetch(int device, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg);
  private:
   struct Entry;
-  ah_status get_impl(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out,
-                     std::string* err);
+  // stats: the context whose compile counters a compile adds to (may be null)
+  ah_status get_impl(int device, ah_ctx* stats, const std::vector<Pattern>& pats, const ScanConfig& cfg,
+                     ScanKernel* out, std::string* err);
+  void many_impl(int device, ah_ctx* stats, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg,
+                 std::vector<ScanKernel>* out, std::vector<ah_status>* st, std::vector<std::string>* err);
   std::mutex mu_;
   std::unordered_map<std::string, std::shared_ptr<Entry>> cache_;
 };

@@ -562,17 +562,17 @@ ah_status compile(int device, const std::string& src, int ops, const ScanConfig&
 
 ah_status JitCache::get(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out) {
   std::string err;
-  const ah_status st = get_impl(ctx, pats, cfg, out, &err);
+  const ah_status st = get_impl(ctx->device, ctx, pats, cfg, out, &err);
   return st ? fail(ctx, st, "%s", err.c_str()) : AH_OK;
 }
 
-ah_status JitCache::get_impl(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out,
-                             std::string* err_out) {
+ah_status JitCache::get_impl(int device, ah_ctx* stats, const std::vector<Pattern>& pats, const ScanConfig& cfg,
+                             ScanKernel* out, std::string* err_out) {
   int ops = 0;
   std::string src = scan_source(pats, cfg, &ops);
   int major = 0, minor = 0;
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, ctx->device);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, ctx->device);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
   const std::string key = std::to_string(major * 10 + minor) + "\n" + src;
   std::shared_ptr<Entry> e;
   bool mine = false;
@@ -591,7 +591,7 @@ ah_status JitCache::get_impl(ah_ctx* ctx, const std::vector<Pattern>& pats, cons
     const auto t0 = std::chrono::steady_clock::now();
     ScanKernel k;
     std::string err;
-    const ah_status st = compile(ctx->device, src, ops, cfg, &k, &err);
+    const ah_status st = compile(device, src, ops, cfg, &k, &err);
     {
       std::lock_guard<std::mutex> lock(e->m);
       e->st = st;
@@ -603,10 +603,10 @@ ah_status JitCache::get_impl(ah_ctx* ctx, const std::vector<Pattern>& pats, cons
     if (st) {
       std::lock_guard<std::mutex> lock(mu_);
       cache_.erase(key);  // a later call may try again
-    } else {
-      std::lock_guard<std::mutex> lock(ctx->stats_mu);
-      ctx->jit_compiles++;
-      ctx->jit_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    } else if (stats) {
+      std::lock_guard<std::mutex> lock(stats->stats_mu);
+      stats->jit_compiles++;
+      stats->jit_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
   }
   std::unique_lock<std::mutex> lock(e->m);
@@ -619,24 +619,67 @@ ah_status JitCache::get_impl(ah_ctx* ctx, const std::vector<Pattern>& pats, cons
   return AH_OK;
 }
 
-ah_status JitCache::get_many(ah_ctx* ctx, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg,
-                             std::vector<ScanKernel>* out) {
+void JitCache::many_impl(int device, ah_ctx* stats, const std::vector<std::vector<Pattern>>& sets,
+                         const ScanConfig& cfg, std::vector<ScanKernel>* out, std::vector<ah_status>* st,
+                         std::vector<std::string>* err) {
   out->assign(sets.size(), ScanKernel{});
-  if (sets.size() == 1) return get(ctx, sets[0], cfg, &(*out)[0]);
-  std::vector<ah_status> st(sets.size(), AH_OK);
-  std::vector<std::string> err(sets.size());
+  st->assign(sets.size(), AH_OK);
+  err->assign(sets.size(), std::string());
+  if (sets.size() == 1) {
+    (*st)[0] = get_impl(device, stats, sets[0], cfg, &(*out)[0], &(*err)[0]);
+    return;
+  }
   const size_t width = std::max<size_t>(1, std::min<size_t>(sets.size(), std::thread::hardware_concurrency()));
   std::atomic<size_t> next{0};
   std::vector<std::thread> pool;
   for (size_t w = 0; w < width; ++w)
     pool.emplace_back([&] {
-      cudaSetDevice(ctx->device);
-      for (size_t i = next++; i < sets.size(); i = next++) st[i] = get_impl(ctx, sets[i], cfg, &(*out)[i], &err[i]);
+      cudaSetDevice(device);
+      for (size_t i = next++; i < sets.size(); i = next++)
+        (*st)[i] = get_impl(device, stats, sets[i], cfg, &(*out)[i], &(*err)[i]);
     });
   for (auto& t : pool) t.join();
+}
+
+ah_status JitCache::get_many(ah_ctx* ctx, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg,
+                             std::vector<ScanKernel>* out) {
+  std::vector<ah_status> st;
+  std::vector<std::string> err;
+  many_impl(ctx->device, ctx, sets, cfg, out, &st, &err);
   for (size_t i = 0; i < sets.size(); ++i)
     if (st[i]) return fail(ctx, st[i], "%s", err[i].c_str());
   return AH_OK;
+}
+
+ah_status JitCache::prefetch(int device, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg) {
+  cudaSetDevice(device);
+  std::vector<ScanKernel> out;
+  std::vector<ah_status> st;
+  std::vector<std::string> err;
+  many_impl(device, nullptr, sets, cfg, &out, &st, &err);
+  for (ah_status s : st)
+    if (s) return s;
+  return AH_OK;
+}
+
+bool JitCache::ready(int device, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg) {
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+  for (const auto& pats : sets) {
+    int ops = 0;
+    const std::string key = std::to_string(major * 10 + minor) + "\n" + scan_source(pats, cfg, &ops);
+    std::shared_ptr<Entry> e;
+    {
+      std::lock_guard<std::mutex> lock(mu_);
+      auto it = cache_.find(key);
+      if (it == cache_.end()) return false;
+      e = it->second;
+    }
+    std::lock_guard<std::mutex> lock(e->m);
+    if (!e->done || e->st) return false;
+  }
+  return true;
 }
 
 std::vector<std::vector<Pattern>> scan_groups(const std::vector<Pattern>& pats, const ScanConfig& cfg) {

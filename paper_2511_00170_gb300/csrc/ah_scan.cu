@@ -6,6 +6,7 @@
 //   4. keys become ah_hit records (record lookup by binary search) in (pair, record, pos, orient)
 //      order, so pairing needs no global sort.
 #include <algorithm>
+#include <thread>
 
 #include "ah_internal.h"
 
@@ -162,7 +163,164 @@ __global__ void k_pair_offsets(const uint64_t* __restrict__ off, uint64_t n_tile
   if (p <= n_pairs) pair_off[p] = off[(uint64_t)p * n_tiles];
 }
 
+// ------------------------------------------------------------------------------------------
+// Generic scan: the same bit-sliced test with the primer set read from a table (GenPattern) at run
+// time, so a new primer set needs no compile.  Each position's mismatch bit is the two-variable
+// boolean function x(lo, hi) = c0 ^ (lo & c1) ^ (hi & c2) ^ (lo & hi & c3) of the shifted code
+// planes, with the set's coefficients as 0 / ~0 words (three LOP3); the count is a saturating
+// ripple counter of `width` bits.  A warp whose windows have all failed stops the pattern early.
+
+// mismatch bits of the 32 windows at offset j of one evaluated position
+__device__ __forceinline__ uint32_t gen_mismatch(const uint4& c, int j, uint2 a, uint2 b) {
+  const uint32_t lo = __funnelshift_r(a.x, b.x, j), hi = __funnelshift_r(a.y, b.y, j);
+  return ((lo & ((hi & c.w) ^ c.y)) ^ (hi & c.z)) ^ c.x;
+}
+
+// bits of the windows starting in group (a, b) that pass P: no clamp mismatch, fewer than k + 1
+// counted mismatches
+template <int W>
+__device__ __forceinline__ uint32_t gen_pass(const GenPattern& P, uint2 a, uint2 b) {
+  uint32_t fail = 0;
+  int e = 0;
+  for (; e < P.n_clamp; ++e) fail |= gen_mismatch(P.x[e], P.j[e], a, b);
+  if (!__any_sync(__activemask(), ~fail)) return 0;
+  uint32_t c[W > 0 ? W : 1] = {};
+  for (int n = 0; e < P.n_eval; ++e) {
+    const uint32_t x = gen_mismatch(P.x[e], P.j[e], a, b);
+    if (W == 0) {
+      fail |= x;
+    } else {
+      uint32_t carry = x;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const uint32_t nc = c[w] & carry;
+        c[w] ^= carry;
+        carry = nc;
+      }
+      fail |= carry;  // the count passed 2^W - 1 >= k
+    }
+    if ((++n & 3) == 0 && !__any_sync(__activemask(), ~fail)) return 0;
+  }
+  if (W > 0) {
+    // count >= k + 1 on the W counter bits (needed when k + 1 < 2^W), least significant bit first
+    const uint32_t T = P.k + 1u;
+    if (T < (1u << W)) {
+      uint32_t ge = ~0u;
+#pragma unroll
+      for (int w = 0; w < W; ++w) ge = ((T >> w) & 1u) ? (c[w] & ge) : (c[w] | ge);
+      fail |= ge;
+    }
+  }
+  return ~fail;
+}
+
+// candidate windows of P: the exact re-check by set masks (a disagreement sets the status word),
+// the invalid-base test (which also rejects windows leaving their record: every record ends in a
+// padding base) and the slot append; the same keys as the generated kernels
+__device__ __noinline__ void gen_emit(uint32_t h, const GenPattern& P, uint64_t g, uint2 a, uint2 b,
+                                      const uint32_t* __restrict__ invalid, uint64_t tile_groups,
+                                      uint64_t* __restrict__ slots, uint32_t* __restrict__ tile_count, uint32_t cap,
+                                      uint32_t* status) {
+  const uint64_t tile = g / tile_groups, tile_pos = tile * tile_groups * 32ull;
+  const uint64_t lo64 = (uint64_t)a.x | ((uint64_t)b.x << 32), hi64 = (uint64_t)a.y | ((uint64_t)b.y << 32);
+  const uint64_t inv64 = (uint64_t)invalid[g] | ((uint64_t)invalid[g + 1] << 32);
+  const uint32_t wm = P.len == 32 ? 0xffffffffu : ((1u << P.len) - 1u);
+  while (h) {
+    const int i = __ffs(h) - 1;
+    h &= h - 1;
+    const uint32_t wl = (uint32_t)(lo64 >> i), wh = (uint32_t)(hi64 >> i);
+    const uint32_t match = (~wl & ~wh & P.mset[0]) | (wl & ~wh & P.mset[1]) | (~wl & wh & P.mset[2]) |
+                           (wl & wh & P.mset[3]);
+    const uint32_t mis = ~match & wm;
+    const int mism = __popc(mis);
+    if ((mis & P.clamp_mask) || mism > P.k) {
+      atomicOr(status, (uint32_t)ST_SCAN_MISMATCH);
+      continue;
+    }
+    if ((uint32_t)(inv64 >> i) & wm) continue;
+    const uint64_t pos = g * 32ull + (uint64_t)i;
+    const uint64_t key =
+        ((uint64_t)P.pair << 48) | ((pos - tile_pos) << 16) | ((uint64_t)P.orient << 8) | (uint64_t)mism;
+    const uint32_t idx = atomicAdd(tile_count + tile, 1u);
+    if (idx < cap) slots[tile * (uint64_t)cap + idx] = key;
+  }
+}
+
+// one CTA per tile of blockDim.x * gpt groups (the tiles of the slot lists); the pattern table is
+// staged in shared memory; every thread takes gpt groups and tests each against every pattern
+__global__ void k_scan_generic(const uint2* __restrict__ planes, const uint32_t* __restrict__ invalid,
+                               uint64_t group_begin, uint64_t n_groups, const GenPattern* __restrict__ pats,
+                               int n_pats, int gpt, uint64_t tile_groups, uint64_t* __restrict__ slots,
+                               uint32_t* __restrict__ tile_count, uint32_t cap, uint32_t* status) {
+  extern __shared__ uint4 gen_sm[];
+  const GenPattern* sp = reinterpret_cast<const GenPattern*>(gen_sm);
+  const uint4* src = reinterpret_cast<const uint4*>(pats);
+  const int words = n_pats * (int)(sizeof(GenPattern) / sizeof(uint4));
+  for (int i = threadIdx.x; i < words; i += blockDim.x) gen_sm[i] = src[i];
+  __syncthreads();
+  const uint64_t first = (uint64_t)blockIdx.x * blockDim.x * gpt;
+  for (int it = 0; it < gpt; ++it) {
+    const uint64_t gl = first + (uint64_t)it * blockDim.x + threadIdx.x;
+    if (gl >= n_groups) return;
+    const uint64_t g = group_begin + gl;
+    const uint2 a = __ldg(planes + g), b = __ldg(planes + g + 1);
+    for (int q = 0; q < n_pats; ++q) {
+      const GenPattern& P = sp[q];
+      uint32_t h;
+      switch (P.width) {
+        case 0: h = gen_pass<0>(P, a, b); break;
+        case 1: h = gen_pass<1>(P, a, b); break;
+        case 2: h = gen_pass<2>(P, a, b); break;
+        case 3: h = gen_pass<3>(P, a, b); break;
+        default: h = gen_pass<4>(P, a, b);
+      }
+      if (h) gen_emit(h, P, g, a, b, invalid, tile_groups, slots, tile_count, cap, status);
+    }
+  }
+}
+
 }  // namespace
+
+std::vector<GenPattern> gen_table(const std::vector<Pattern>& pats) {
+  std::vector<GenPattern> out(pats.size());
+  for (size_t q = 0; q < pats.size(); ++q) {
+    const Pattern& P = pats[q];
+    GenPattern& G = out[q];
+    G = GenPattern{};
+    G.len = P.len;
+    G.k = P.k;
+    G.pair = (uint16_t)(P.id / 4);
+    G.orient = (uint8_t)(P.id % 4);
+    G.width = 0;
+    while ((1u << G.width) < P.k + 1u) G.width++;
+    for (int j = 0; j < P.len; ++j) {
+      for (int c = 0; c < 4; ++c)
+        if ((P.set[j] >> c) & 1) G.mset[c] |= 1u << j;
+      if (j >= P.clamp_lo && j < P.clamp_hi) G.clamp_mask |= 1u << j;
+    }
+    // evaluated positions: the clamp, then the counted ones by falling mismatch probability on
+    // uniform bases (fewer bases in the set first); N never mismatches and is left out
+    std::vector<int> clamp, counted;
+    for (int j = 0; j < P.len; ++j) {
+      if (P.set[j] == 0xF) continue;
+      (j >= P.clamp_lo && j < P.clamp_hi ? clamp : counted).push_back(j);
+    }
+    std::stable_sort(counted.begin(), counted.end(),
+                     [&](int a, int b) { return __builtin_popcount(P.set[a]) < __builtin_popcount(P.set[b]); });
+    G.n_clamp = (uint8_t)clamp.size();
+    clamp.insert(clamp.end(), counted.begin(), counted.end());
+    G.n_eval = (uint8_t)clamp.size();
+    for (size_t e = 0; e < clamp.size(); ++e) {
+      const int j = clamp[e];
+      const uint8_t S = P.set[j];
+      // mismatch bit at codes A (lo 0, hi 0), C (1, 0), T (0, 1), G (1, 1) and its algebraic normal form
+      const uint32_t fA = (S & 1) ? 0u : ~0u, fC = (S & 2) ? 0u : ~0u, fT = (S & 4) ? 0u : ~0u, fG = (S & 8) ? 0u : ~0u;
+      G.x[e] = make_uint4(fA, fA ^ fC, fA ^ fT, fA ^ fC ^ fT ^ fG);
+      G.j[e] = (uint8_t)j;
+    }
+  }
+  return out;
+}
 
 void launch_scan_kernel(cudaStream_t s, const ScanKernel& k, const ah_batch* b, uint64_t* slots, uint32_t* tile_count,
                         uint32_t cap, uint32_t* status, unsigned long long* work, uint64_t n_tiles, int grid) {
@@ -224,6 +382,36 @@ void launch_emit_hits(cudaStream_t s, const uint64_t* slots, const uint32_t* til
 
 namespace {
 
+// Generic-scan mode 2 without a compile_behind hook: base-patterns (bases x patterns) up to which
+// the generic kernel scans alone (no compile); above it, it scans while a local thread compiles.
+constexpr double kGenericAutoWork = 17179869184.0;  // 2^34
+// generic-kernel chunks while a compile runs: about this many base-patterns each (a few ms), so
+// the switch to the generated kernels comes soon after the compile ends
+constexpr double kGenericChunkWork = 4.0e9;
+
+// the generic kernel over tiles [t_begin, t_end), at most kGenMaxPatterns patterns per launch
+ah_status enqueue_generic(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ScanConfig& cfg,
+                          uint64_t tile_groups, uint64_t t_begin, uint64_t t_end, uint64_t* slots,
+                          uint32_t* tile_count, uint32_t cap) {
+  const size_t Q = p->pats.size();
+  for (size_t q0 = 0; q0 < Q; q0 += kGenMaxPatterns) {
+    const int nq = (int)std::min<size_t>(kGenMaxPatterns, Q - q0);
+    for (uint64_t t0 = t_begin; t0 < t_end; t0 += 0x7fffffffull) {
+      const uint64_t nt = std::min<uint64_t>(0x7fffffffull, t_end - t0);
+      const uint64_t g0 = t0 * tile_groups;
+      const uint64_t ng = std::min<uint64_t>(b->n_groups - std::min(b->n_groups, g0), nt * tile_groups);
+      if (ng == 0) continue;
+      k_scan_generic<<<(unsigned)nt, cfg.threads, nq * sizeof(GenPattern), ctx->stream>>>(
+          b->planes, b->invalid, g0, ng, p->d_gen + q0, nq, cfg.groups_per_thread, tile_groups, slots, tile_count, cap,
+          ctx->d_status);
+      const cudaError_t le = cudaGetLastError();
+      if (le != cudaSuccess) return fail(ctx, AH_ECUDA, "generic scan launch failed: %s", cudaGetErrorString(le));
+      launched(ctx);
+    }
+  }
+  return AH_OK;
+}
+
 // persistent grid: resident CTAs per SM x SMs
 int persistent_grid(ah_ctx* ctx, const ScanKernel& k) {
   int per_sm = 0;
@@ -233,41 +421,118 @@ int persistent_grid(ah_ctx* ctx, const ScanKernel& k) {
   return per_sm * ctx->sm_count;
 }
 
+// the generated kernels over tiles [t_begin, t_end), one after another
+ah_status enqueue_jit(ah_ctx* ctx, const ah_batch* b, const std::vector<ScanKernel>& kerns, const ScanConfig& cfg,
+                      uint64_t tile_groups, uint64_t t_begin, uint64_t t_end, uint64_t* slots, uint32_t* tile_count,
+                      uint32_t cap, unsigned long long* work) {
+  for (const ScanKernel& kern : kerns) {
+    for (uint64_t t0 = t_begin; t0 < t_end; t0 += 0x7fffffffull) {
+      const uint64_t nt = std::min<uint64_t>(0x7fffffffull, t_end - t0);
+      const uint64_t g0 = t0 * tile_groups;
+      if (cfg.persistent) AH_CUDA(ctx, cudaMemsetAsync(work, 0, sizeof *work, ctx->stream));
+      ScanParamsHost P{b->planes, b->invalid, b->rec_group, b->rec_len, b->n_records, cap, g0,
+                       std::min<uint64_t>(b->n_groups - std::min(b->n_groups, g0), nt * tile_groups),
+                       slots, tile_count, ctx->d_status, tile_groups, work, nt};
+      void* args[] = {&P};
+      const unsigned grid =
+          cfg.persistent ? (unsigned)std::min<uint64_t>(nt, persistent_grid(ctx, kern)) : (unsigned)nt;
+      cudaError_t le = cudaLaunchKernel((const void*)kern.fn, dim3(grid), dim3((unsigned)cfg.threads), args, 0,
+                                        ctx->stream);
+      if (le != cudaSuccess) return fail(ctx, AH_ECUDA, "scan kernel launch failed: %s", cudaGetErrorString(le));
+      launched(ctx);
+    }
+  }
+  return AH_OK;
+}
+
+// generic-kernel chunks over the leading tiles until *flag turns nonzero (at most two chunks in
+// flight; the flag is read as each completes); returns the first tile left
+ah_status generic_until(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ScanConfig& cfg,
+                        uint64_t tile_groups, uint64_t n_tiles, uint64_t* slots, uint32_t* tile_count, uint32_t cap,
+                        const std::atomic<int>& flag, uint64_t* t_out) {
+  const double per_tile = (double)tile_groups * 32.0 * (double)std::max<size_t>(1, p->pats.size());
+  const uint64_t chunk = std::max<uint64_t>(2ull * std::max(1, ctx->sm_count), (uint64_t)(kGenericChunkWork / per_tile));
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  ah_status st = AH_OK;
+  for (auto& e : done)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      st = fail(ctx, AH_ECUDA, "cudaEventCreate failed");
+  uint64_t t = 0;
+  int issued = 0;
+  while (!st && t < n_tiles && flag.load() == 0) {
+    if (issued >= 2) {
+      cudaEventSynchronize(done[issued % 2]);
+      if (flag.load() != 0) break;
+    }
+    const uint64_t nt = std::min<uint64_t>(chunk, n_tiles - t);
+    if ((st = enqueue_generic(ctx, b, p, cfg, tile_groups, t, t + nt, slots, tile_count, cap))) break;
+    cudaEventRecord(done[issued % 2], ctx->stream);
+    issued++;
+    t += nt;
+  }
+  for (auto& e : done)
+    if (e) cudaEventDestroy(e);
+  *t_out = t;
+  return st;
+}
+
 // Launch the scan over the batch.  per_record: one launch per record and pair (the plain form),
 // otherwise one launch over everything (grid of tiles, or persistent CTAs).
 ah_status launch_scan(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ScanConfig& cfg, bool per_record,
                       uint64_t tile_groups, uint64_t n_tiles, uint64_t* slots, uint32_t* tile_count, uint32_t cap) {
-  ah_status st;
+  ah_status st = AH_OK;
   if (!per_record) {
     // one kernel for every pair, or (cfg.pairs_per_kernel) kernels of a few pairs each, compiled in
     // parallel and launched one after another into the same tile slot lists
-    std::vector<ScanKernel> kerns;
-    if ((st = ctx->jit->get_many(ctx, scan_groups(p->pats, cfg), cfg, &kerns))) return st;
-    unsigned long long* work = nullptr;
-    if (cfg.persistent && (st = dalloc(ctx, &work, 1))) return st;
-    if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
-    int ops = 0;
-    for (const ScanKernel& kern : kerns) {
-      for (uint64_t t0 = 0; t0 < n_tiles; t0 += 0x7fffffffull) {
-        const uint64_t nt = std::min<uint64_t>(0x7fffffffull, n_tiles - t0);
-        const uint64_t g0 = t0 * tile_groups;
-        if (cfg.persistent) AH_CUDA(ctx, cudaMemsetAsync(work, 0, sizeof *work, ctx->stream));
-        ScanParamsHost P{b->planes, b->invalid, b->rec_group, b->rec_len, b->n_records, cap, g0,
-                         std::min<uint64_t>(b->n_groups - std::min(b->n_groups, g0), nt * tile_groups),
-                         slots, tile_count, ctx->d_status, tile_groups, work, nt};
-        void* args[] = {&P};
-        const unsigned grid =
-            cfg.persistent ? (unsigned)std::min<uint64_t>(nt, persistent_grid(ctx, kern)) : (unsigned)nt;
-        cudaError_t le = cudaLaunchKernel((const void*)kern.fn, dim3(grid), dim3((unsigned)cfg.threads), args, 0,
-                                          ctx->stream);
-        if (le != cudaSuccess) return fail(ctx, AH_ECUDA, "scan kernel launch failed: %s", cudaGetErrorString(le));
-        launched(ctx);
+    const std::vector<std::vector<Pattern>> sets = scan_groups(p->pats, cfg);
+    // generic-kernel choice: the whole batch (mode 1, or mode 2 on a small batch without a
+    // compile_behind hook), or leading tiles while the generated kernels compile (mode 2)
+    bool generic_all = ctx->generic_scan == 1;
+    std::shared_ptr<std::atomic<int>> flag;
+    std::thread local;
+    if (ctx->generic_scan == 2 && !ctx->jit->ready(ctx->device, sets, cfg)) {
+      if (ctx->compile_behind) {
+        flag = ctx->compile_behind(sets, cfg);
+      } else if ((double)b->n_bases * (double)p->pats.size() <= kGenericAutoWork) {
+        generic_all = true;
+      } else {
+        flag = std::make_shared<std::atomic<int>>(0);
+        const int device = ctx->device;
+        local = std::thread([device, sets, cfg, flag] {
+          flag->store(JitCache::global().prefetch(device, sets, cfg) ? 2 : 1);
+        });
       }
-      ops += kern.alu_ops_per_group;
+    }
+    if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
+    uint64_t t = 0;
+    if (generic_all) {
+      st = enqueue_generic(ctx, b, p, cfg, tile_groups, 0, n_tiles, slots, tile_count, cap);
+      t = n_tiles;
+    } else if (ctx->generic_scan == 3) {  // the hand-over at a fixed tile
+      t = n_tiles / 2;
+      if (t) st = enqueue_generic(ctx, b, p, cfg, tile_groups, 0, t, slots, tile_count, cap);
+    } else if (flag) {
+      st = generic_until(ctx, b, p, cfg, tile_groups, n_tiles, slots, tile_count, cap, *flag, &t);
+    }
+    if (t > 0) ctx->n_generic_scans++;
+    int ops = 0;
+    unsigned long long* work = nullptr;
+    if (!st && t < n_tiles) {
+      if (local.joinable()) local.join();
+      std::vector<ScanKernel> kerns;
+      st = ctx->jit->get_many(ctx, sets, cfg, &kerns);
+      if (!st && cfg.persistent) st = dalloc(ctx, &work, 1);
+      if (!st) st = enqueue_jit(ctx, b, kerns, cfg, tile_groups, t, n_tiles, slots, tile_count, cap, work);
+      for (const ScanKernel& kern : kerns) ops += kern.alu_ops_per_group;
+    }
+    if (local.joinable()) local.join();
+    if (st) {
+      dfree(ctx, work);
+      return st;
     }
     if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
     ctx->n_scan_launches++;          // passes over the batch
-    ctx->scan_ops_per_group = ops;   // all patterns, per 32 positions
+    ctx->scan_ops_per_group = ops;   // generated circuits of all patterns per 32 positions (0: generic only)
     dfree(ctx, work);
     ctx->scan_bases += b->n_bases;
     return AH_OK;

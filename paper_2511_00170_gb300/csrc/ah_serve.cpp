@@ -8,6 +8,11 @@
 // others are on the GPU join as slots and memory free up, and their kernels overlap on the device.
 // Each admitted request runs the whole path on a slice of the database (no copy of the genomes)
 // and its results are copied to host memory owned by the request's result.
+//
+// A request whose primer set has no compiled scan kernels yet starts scanning with the generic
+// kernel while a thread compiles the generated kernels; the rest of the scan uses them once they
+// are ready.  A small request may finish before its compile does; the server joins that thread
+// later, and requests with the same primers find the kernels cached.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -51,6 +56,9 @@ struct ah_server {
   uint64_t next_ticket = 1;
   bool stop = false;
   int running = 0;
+  // compiles started for requests' primer sets, each with the flag it sets when done
+  std::mutex cmu;
+  std::vector<std::pair<std::thread, std::shared_ptr<std::atomic<int>>>> compiles;
 };
 
 namespace ah {
@@ -149,6 +157,27 @@ void worker(ah_server* s, int slot) {
   }
 }
 
+// start compiling a request's kernels on a thread the server owns (joined once done)
+std::shared_ptr<std::atomic<int>> compile_behind(ah_server* s, const std::vector<std::vector<Pattern>>& sets,
+                                                 const ScanConfig& cfg) {
+  auto flag = std::make_shared<std::atomic<int>>(0);
+  const int device = s->device;
+  std::lock_guard<std::mutex> lock(s->cmu);
+  for (auto it = s->compiles.begin(); it != s->compiles.end();) {
+    if (it->second->load() != 0) {
+      it->first.join();
+      it = s->compiles.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  // a failure is reported by the request's own scan, which then compiles (and fails) itself
+  s->compiles.emplace_back(
+      std::thread([device, sets, cfg, flag] { flag->store(JitCache::global().prefetch(device, sets, cfg) ? 2 : 1); }),
+      flag);
+  return flag;
+}
+
 }  // namespace
 }  // namespace ah
 
@@ -181,6 +210,11 @@ ah_status ah_server_create(const ah_batch* db, int n_slots, uint64_t memory_budg
     // a request's primer set is compiled as kernels of 4 pairs on parallel host threads: a cold
     // 32-pair set compiles in about the time of one 4-pair kernel instead of 8x longer
     c->scan_cfg.pairs_per_kernel = 4;
+    // a primer set without compiled kernels starts on the generic kernel while it compiles
+    c->generic_scan = 2;
+    c->compile_behind = [s](const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg) {
+      return compile_behind(s, sets, cfg);
+    };
     s->ctxs.push_back(c);
   }
   for (int i = 0; i < n_slots; ++i) s->workers.emplace_back(worker, s, i);
@@ -255,6 +289,7 @@ void ah_server_destroy(ah_server* s) {
   }
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
+  for (auto& c : s->compiles) c.first.join();
   for (auto& kv : s->jobs) {
     ah_result_free(kv.second->result);
     delete kv.second;

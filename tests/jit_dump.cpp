@@ -1,5 +1,8 @@
-// Test helper: print the scan kernel source the engine generates for a primer set.
-// usage: jit_dump k clamp primer [primer ...]   (each primer gives its + and - strand patterns)
+// Test helper: print the scan kernel source the engine generates for a primer set, or (first
+// argument "gen") the pattern table of the generic scan kernel, one pattern per block:
+//   len k n_eval n_clamp width clamp_mask mset0 mset1 mset2 mset3
+//   then n_eval lines "j c0 c1 c2 c3" (coefficients as 0 / 4294967295)
+// usage: jit_dump [gen] k clamp primer [primer ...]   (each primer gives its + and - strand patterns)
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -18,6 +21,8 @@ static uint8_t set_of(char c) {
 static uint8_t comp(uint8_t s) { return (uint8_t)(((s & 1) << 2) | ((s & 4) >> 2) | ((s & 2) << 2) | ((s & 8) >> 2)); }
 
 int main(int argc, char** argv) {
+  const bool gen = argc > 1 && !strcmp(argv[1], "gen");
+  if (gen) ++argv, --argc;
   const int k = atoi(argv[1]), clamp = atoi(argv[2]);
   std::vector<ah::Pattern> pats;
   for (int a = 3; a < argc; ++a)
@@ -34,6 +39,14 @@ int main(int argc, char** argv) {
       P.clamp_hi = (uint8_t)(strand == 0 ? L : clamp);
       pats.push_back(P);
     }
+  if (gen) {
+    for (const ah::GenPattern& G : ah::gen_table(pats)) {
+      printf("%d %d %d %d %d %u %u %u %u %u\n", G.len, G.k, G.n_eval, G.n_clamp, G.width, G.clamp_mask, G.mset[0],
+             G.mset[1], G.mset[2], G.mset[3]);
+      for (int e = 0; e < G.n_eval; ++e) printf("%d %u %u %u %u\n", G.j[e], G.x[e].x, G.x[e].y, G.x[e].z, G.x[e].w);
+    }
+    return 0;
+  }
   ah::ScanConfig cfg;
   puts(ah::scan_source(pats, cfg).c_str());
   return 0;

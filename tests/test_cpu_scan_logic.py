@@ -1,8 +1,10 @@
 """The bit-sliced scan logic generated for a primer set (IUPAC plane selection, funnel shifts, the
 carry-save counter tree and clamp terms as LOP3 truth tables), run on the CPU, equals an exact
 per-position mismatch count and clamp check on random data, and every window its first phase
-(clamp and most selective positions, after which a warp may skip the rest) fails does fail.  No
-GPU is needed: the generated statements are executed with numpy."""
+(clamp and most selective positions, after which a warp may skip the rest) fails does fail.  The
+generic kernel's pattern table (per-position mismatch functions in algebraic normal form, the
+evaluation order, the counter width), run through the generic kernel's equations with its warp
+early exit, gives the same words.  No GPU is needed: everything is executed with numpy."""
 import os
 import subprocess
 
@@ -27,7 +29,8 @@ def dump():
         cuda_inc = "/usr/local/cuda/include"
         subprocess.check_call(["g++", "-std=c++17", "-O1", "-I", cuda_inc, src, "-o", exe, "-L", lib, "-lah",
                                f"-Wl,-rpath,{lib}"])
-    return lambda k, c, prims: subprocess.check_output([exe, str(k), str(c)] + prims, text=True)
+    return lambda k, c, prims, gen=False: subprocess.check_output([exe] + (["gen"] if gen else []) +
+                                                                [str(k), str(c)] + prims, text=True)
 
 
 CASES = [(2, 3, ["AGATACCKWCAACAACTGC", "CTCCTCGTATAWTMTCRACC"]), (0, 0, ["ACGTACGT"]),
@@ -40,6 +43,11 @@ def _check(dump, k, clamp, primers, seed, n=2000):
     src = dump(k, clamp, primers)
     rng = np.random.default_rng(seed)
     planes = [rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32) for _ in range(4)]
+    _check_planes(src, k, clamp, primers, planes)
+    _check_planes(src, k, clamp, primers, _planted_planes(primers, k, clamp, n // 2, seed))
+
+
+def _check_planes(src, k, clamp, primers, planes):
     phase_a = []
     got = scan_emulator.failure_words(src, *planes, phase_a=phase_a)
     want = scan_emulator.exact_failure_words(primers, k, clamp, *planes)
@@ -66,3 +74,117 @@ def test_generated_logic_random_primer_sets(dump, seed):
     prims = [synth.random_primer(st, st.randint(max(2, clamp), 32) if i else L, st.randint(0, 8), clamp,
                                  "RYSWKMBDHVN") for i in range(st.randint(1, 3))]
     _check(dump, k, clamp, prims, seed, n=600)
+
+
+def _generic_failure_words(table, lo0, hi0, lo1, hi1):
+    """The generic kernel's pass test per pattern, lanes of 32 words as warps (early exit after the
+    clamp and every fourth counted position when no window of the warp is left)."""
+    lines = table.strip().splitlines()
+    out, i = [], 0
+    ones = np.uint32(0xFFFFFFFF)
+    while i < len(lines):
+        L, k, n_eval, n_clamp, width, *_ = (int(v) for v in lines[i].split())
+        pos = [tuple(int(v) for v in ln.split()) for ln in lines[i + 1:i + 1 + n_eval]]
+        i += 1 + n_eval
+        res = np.zeros(len(lo0), dtype=np.uint32)
+        for w0 in range(0, len(lo0), 32):
+            sl = slice(w0, w0 + 32)
+            a_lo, a_hi = lo0[sl].astype(np.uint64), hi0[sl].astype(np.uint64)
+            b_lo, b_hi = lo1[sl].astype(np.uint64), hi1[sl].astype(np.uint64)
+            lo64, hi64 = a_lo | (b_lo << np.uint64(32)), a_hi | (b_hi << np.uint64(32))
+
+            def mismatch(p):
+                j, c0, c1, c2, c3 = p
+                lo = ((lo64 >> np.uint64(j)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+                hi = ((hi64 >> np.uint64(j)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+                c0, c1, c2, c3 = (np.uint32(c) for c in (c0, c1, c2, c3))
+                return ((lo & ((hi & c3) ^ c1)) ^ (hi & c2)) ^ c0
+
+            fail = np.zeros(len(lo64), dtype=np.uint32)
+            for p in pos[:n_clamp]:
+                fail |= mismatch(p)
+            if not np.any(~fail):
+                continue
+            c = [np.zeros(len(lo64), dtype=np.uint32) for _ in range(max(width, 1))]
+            stopped = False
+            for n, p in enumerate(pos[n_clamp:], start=1):
+                x = mismatch(p)
+                if width == 0:
+                    fail |= x
+                else:
+                    carry = x
+                    for w in range(width):
+                        nc = c[w] & carry
+                        c[w] ^= carry
+                        carry = nc
+                    fail |= carry
+                if n % 4 == 0 and not np.any(~fail):
+                    stopped = True
+                    break
+            if stopped:
+                continue
+            T = k + 1
+            if width > 0 and T < (1 << width):
+                ge = np.full(len(lo64), ones, dtype=np.uint32)
+                for w in range(width):
+                    ge = (c[w] & ge) if (T >> w) & 1 else (c[w] | ge)
+                fail |= ge
+            res[sl] = ~fail
+        out.append(~res)  # failure words
+    return out
+
+
+def _planted_planes(primers, k, clamp, n, seed):
+    """Planes (lo, hi of group g; lo, hi of group g + 1) of a random sequence holding many planted
+    instances of the patterns with about k mismatches (k - 1 to k + 2, now and then one in the
+    clamp), so that the count comparison decides many windows."""
+    rng = np.random.default_rng(seed)
+    seq = rng.integers(0, 4, 32 * (n + 1))
+    pats = []
+    for p in primers:
+        rc = "".join(scan_emulator.COMP[c] for c in reversed(p))
+        pats += [(p, set(range(len(p) - clamp, len(p)))), (rc, set(range(clamp)))]
+    for _ in range(n // 2):
+        pat, cl = pats[rng.integers(len(pats))]
+        at = int(rng.integers(0, len(seq) - len(pat)))
+        bases = [scan_emulator.SETS[ch][rng.integers(len(scan_emulator.SETS[ch]))] for ch in pat]
+        free = [j for j, ch in enumerate(pat) if ch != "N" and j not in cl]
+        m = min(len(free), max(0, k - 1 + int(rng.integers(0, 4))))
+        mis = list(rng.choice(free, m, replace=False)) if m else []
+        if cl and rng.random() < 0.1:
+            mis.append(int(rng.choice(sorted(cl))))
+        for j in mis:
+            others = [b for b in "ACGT" if b not in scan_emulator.SETS[pat[j]]]
+            if others:
+                bases[j] = others[rng.integers(len(others))]
+        seq[at:at + len(pat)] = [scan_emulator.CODE[b] for b in bases]
+    bits = lambda b: np.packbits(((seq >> b) & 1).astype(np.uint8).reshape(-1, 32)[:, ::-1], axis=1) \
+        .view(">u4").ravel().astype(np.uint32)
+    lo, hi = bits(0), bits(1)
+    return [lo[:-1].copy(), hi[:-1].copy(), lo[1:].copy(), hi[1:].copy()]
+
+
+def _check_generic(dump, k, clamp, primers, seed, n=1024):
+    table = dump(k, clamp, primers, gen=True)
+    planes = _planted_planes(primers, k, clamp, n, seed)
+    got = _generic_failure_words(table, *planes)
+    want = scan_emulator.exact_failure_words(primers, k, clamp, *planes)
+    assert len(got) == len(want) == 2 * len(primers)
+    for q, (g, w) in enumerate(zip(got, want)):
+        assert np.array_equal(g, w), f"pattern {q}: {int(np.count_nonzero(g != w))} words differ"
+
+
+@pytest.mark.parametrize("k,clamp,primers", CASES)
+def test_generic_table_fixed_cases(dump, k, clamp, primers):
+    _check_generic(dump, k, clamp, primers, 3)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_generic_table_random_primer_sets(dump, seed):
+    st = synth.Stream(synth.make_key(seed, 4243, 0))
+    L = st.randint(2, 32)
+    clamp = st.randint(0, min(L, 6))
+    k = st.randint(0, min(L, 15))
+    prims = [synth.random_primer(st, st.randint(max(2, clamp), 32) if i else L, st.randint(0, 8), clamp,
+                                 "RYSWKMBDHVN") for i in range(st.randint(1, 3))]
+    _check_generic(dump, k, clamp, prims, seed, n=512)

@@ -402,3 +402,70 @@ def test_batch_export_import(engine):
     finally:
         ah.ah_batch_free(a)
         ah.ah_batch_free(b)
+
+
+@pytest.fixture(params=[1, 3], ids=["generic", "handover"])
+def generic(engine, request):
+    """The engine's context with the generic (compile-free) scan kernel forced over every tile, or
+    over the first half of the tiles with the generated kernels on the rest."""
+    from paper_2511_00170_gb300 import ah
+
+    ah.ah_ctx_set_generic_scan(engine.ctx, request.param)
+    ah.ah_ctx_stats_reset(engine.ctx)
+    try:
+        yield engine
+        if request.param == 1:
+            assert ah.ah_ctx_stats_get(engine.ctx)["generic_scans"] > 0
+    finally:
+        ah.ah_ctx_set_generic_scan(engine.ctx, 0)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_generic_scan_random_small(generic, seed):
+    """The generic kernel (primer set read from a table at run time) finds the oracle's sites."""
+    _run_both(generic, _random_case(seed))
+
+
+def test_generic_scan_edges_and_overflow(generic):
+    """Edge records, degenerate primers up to 32 bases with k = 15, and the dense-tile re-run, through
+    the generic kernel."""
+    test_edge_records(generic)
+    test_dense_sites_overflow_retry(generic)
+
+
+@pytest.mark.parametrize("threads,gpt,slots", [(128, 8, 256), (256, 4, 64), (64, 16, 16)])
+def test_generic_scan_many_pairs(generic, threads, gpt, slots):
+    """Twenty pairs: more patterns than one generic launch holds (64), so two launches append to the
+    same tile slot lists; every tile shape."""
+    from paper_2511_00170_gb300 import ah
+
+    ah.ah_ctx_set_scan_config(generic.ctx, threads, gpt, slots, 0)
+    try:
+        _run_both(generic, synth.batched(n_genomes=16, len_lo=2e3, len_hi=2e5, n_pairs=20))
+    finally:
+        ah.ah_ctx_set_scan_config(generic.ctx, 256, 4, 256, 0)
+
+
+def test_generic_scan_auto(engine):
+    """Mode 2 scans a primer set whose kernels are not compiled with the generic kernel (no compile),
+    and once they are compiled, with the generated kernels."""
+    from paper_2511_00170_gb300 import ah
+
+    wl = synth.random_small(7_770_001, n_records=3, len_lo=500, len_hi=3000, n_pairs=2, plen_lo=17, plen_hi=23,
+                            n_deg=3, k_max=3, clamp=2, plant=3)
+    ctx = engine.ctx
+    ah.ah_ctx_set_generic_scan(ctx, 2)
+    try:
+        ah.ah_ctx_stats_reset(ctx)
+        _run_both(engine, wl)
+        s = ah.ah_ctx_stats_get(ctx)
+        assert s["generic_scans"] == 2 and s["jit_compiles"] == 0   # two steps (filtered, unfiltered)
+        ah.ah_ctx_set_generic_scan(ctx, 0)
+        _run_both(engine, wl)                                        # compiles
+        ah.ah_ctx_set_generic_scan(ctx, 2)
+        ah.ah_ctx_stats_reset(ctx)
+        _run_both(engine, wl)
+        s = ah.ah_ctx_stats_get(ctx)
+        assert s["generic_scans"] == 0 and s["jit_compiles"] == 0
+    finally:
+        ah.ah_ctx_set_generic_scan(ctx, 0)
