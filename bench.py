@@ -532,6 +532,7 @@ def run_serving(args):
     db_bp = int(sum(lengths))
     trace = synth.serving_trace(synth.SEED, args.requests, args.rate, n_db)
     srv = ah.ah_server_create(db, n_slots=args.slots)
+    ah.ah_server_set_scan_mode(srv, args.scan_mode)
     keys = ("fwd", "rev", "k", "clamp", "first_record", "n_records", "min_len", "max_len", "orient_mask")
     t_start = time.perf_counter()
     tickets = []
@@ -553,13 +554,21 @@ def run_serving(args):
             "config": {"workload": f"serving: {n_db} genomes ({db_bp / 1e9:.1f} Gbp, "
                                    f"{db_bp / 4e9:.1f} GB packed) resident; Poisson {args.rate} req/s, "
                                    f"{args.requests} requests of 1-32 pairs (17-26 nt, k 0-3) over contiguous "
-                                   "subsets of 1-100 % of the database", "slots": args.slots},
+                                   "subsets of 1-100 % of the database", "slots": args.slots,
+                       "scan_mode": {0: "generated kernels (compiled per primer set)", 1: "generic kernel (no compile)",
+                                     2: "generic kernel while the generated kernels compile"}[args.scan_mode]},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "mean": float(lat.mean()), "max": float(lat.max())},
             "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
             "completed": len(res), "makespan_s": span, "offered_rate": args.rate,
             "served_rate": len(res) / span, "pattern_gbp_per_s": pattern_bases / span / 1e9,
             "db_build_s": gen_s, "clocks": clk.summary()}
+    if args.dump_requests:
+        with open(args.dump_requests, "w") as f:
+            json.dump([{"submit": x["t_submit"], "admit": x["t_admit"], "done": x["t_done"], "stages": x["t_stage"],
+                        "bases": x["bases"],
+                        "pairs": len(r["fwd"]), "hits": len(x["hits"]), "amps": len(x["amps"])}
+                       for x, r in zip(res, trace)], f)
     ah.ah_batch_free(db)
     eng.close()
     print(json.dumps(line), flush=True)
@@ -580,6 +589,9 @@ def main():
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--dump-requests", default="", help="serving: write per-request times to this JSON file")
+    ap.add_argument("--scan-mode", type=int, default=2,
+                    help="serving: 0 generated scan kernels, 1 generic kernel, 2 generic while compiling")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -80,12 +80,14 @@ typedef struct {
                                timed ones only, for plan replays) */
   double scan_ms;           /* summed device time of those launches (timing enabled) */
   uint64_t scan_bases;      /* bases covered by those launches */
-  uint64_t jit_compiles;    /* scan kernels compiled at run time (NVRTC) */
+  uint64_t jit_compiles;    /* scan kernels compiled at run time (NVRTC), background compiles of
+                               generic-scan mode 2 included (counted when they finish) */
   double jit_ms;            /* host time spent compiling them */
   int32_t scan_ops_per_group; /* ALU instructions (LOP3 and funnel shifts) of the last scan's
                                  generated circuits (all its kernels) per 32 positions; 0 after a
                                  scan by the generic kernel */
-  uint64_t generic_scans;   /* scans run by the generic (compile-free) kernel */
+  uint64_t generic_scans;   /* scans run by the generic (compile-free) kernel, wholly or in part */
+  uint64_t generic_bases;   /* bases of those scans the generic kernel covered (whole tiles) */
 } ah_ctx_stats;
 ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out);
 ah_status ah_ctx_stats_reset(ah_ctx* ctx);
@@ -102,11 +104,11 @@ ah_status ah_ctx_set_pairs_per_kernel(ah_ctx* ctx, int pairs);
  *     process-wide).
  *   1: the generic kernel built into the library, which reads the primer set from a table and needs
  *     no compile, but scans several times slower.
- *   2: the generated kernels when they are compiled already.  Otherwise a scan of at most 2^34
- *     base-patterns (bases x 4 x pairs) runs on the generic kernel alone; a larger one runs the
- *     generic kernel over leading tiles while a host thread compiles the generated kernels, and
- *     those over the rest once they are ready.  Server contexts always take the second way and do
- *     not wait for a compile that the generic kernel outlasted.
+ *   2: the generated kernels when they are compiled already.  Otherwise the generic kernel scans
+ *     leading tiles while a host thread of the context compiles the generated kernels, which scan
+ *     the rest once they are ready; a scan the generic kernel finishes first does not wait for the
+ *     compile (the context joins that thread later, at the latest in ah_ctx_destroy).  Server
+ *     contexts use this mode.
  *   3: the generic kernel over the first half of the tiles and the generated kernels over the rest
  *     (a fixed hand-over point, for tests).
  * Plans always use a generated kernel.  AH_EINVAL for another mode. */
@@ -427,6 +429,11 @@ void ah_plan_free(ah_plan* plan);
  * budget beside the requests already running (a request alone on the device is always admitted),
  * so requests that arrive while others run join as slots and memory free up and their kernels
  * overlap on the GPU.  A request runs the whole path on a slice of the database (no genome copy).
+ * Each worker has a CUDA stream per priority class (up to three of the device's priorities); a
+ * request runs at the priority of its scan work, bases x 4 x pairs (below 1e11, below 1e12,
+ * above), so small requests are scheduled ahead of large ones running beside them.  By default
+ * the scan of a primer set whose generated kernels are not compiled starts on the generic kernel
+ * while they compile (ah_ctx_set_generic_scan mode 2); ah_server_set_scan_mode changes that.
  */
 typedef struct ah_server ah_server;
 typedef struct {
@@ -450,6 +457,8 @@ typedef struct {
   uint64_t* field_off;   /* 5 * n_amps + 1 */
   double t_submit, t_admit, t_done; /* seconds on the server's clock */
   char error[256];
+  double t_stage[5];     /* when each stage ended: slice and primers, scan, pairing, Tm, sequences
+                            and host copies (t_done) */
 } ah_result;
 /* memory_budget: device bytes requests may reserve (0: 60 % of the free memory now).  The database
  * must outlive the server. */
@@ -459,6 +468,9 @@ ah_status ah_server_submit(ah_server* s, const ah_request* r, uint64_t* ticket);
 /* Block until the request is done; the result is the caller's (ah_result_free).  Returns the
  * request's status. */
 ah_status ah_server_wait(ah_server* s, uint64_t ticket, ah_result** out);
+/* Generic-scan mode (ah_ctx_set_generic_scan: 0, 1 or 2; default 2) of requests admitted from now
+ * on.  Mode 1 serves without any run-time compilation.  AH_EINVAL for another mode. */
+ah_status ah_server_set_scan_mode(ah_server* s, int mode);
 ah_status ah_server_now(const ah_server* s, double* seconds);
 void ah_result_free(ah_result* r);
 /* Finish queued requests, stop the workers and release the server. */

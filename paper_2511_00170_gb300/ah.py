@@ -70,13 +70,14 @@ class ah_result(ctypes.Structure):
                 ("arena_bytes", ctypes.c_uint64), ("bases", ctypes.c_uint64), ("hits", ctypes.c_void_p),
                 ("amps", ctypes.c_void_p), ("arena", ctypes.c_void_p), ("field_off", ctypes.c_void_p),
                 ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
-                ("error", ctypes.c_char * 256)]
+                ("error", ctypes.c_char * 256), ("t_stage", ctypes.c_double * 5)]
 
 
 class ah_ctx_stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("scan_launches", ctypes.c_uint64), ("scan_ms", ctypes.c_double),
                 ("scan_bases", ctypes.c_uint64), ("jit_compiles", ctypes.c_uint64), ("jit_ms", ctypes.c_double),
-                ("scan_ops_per_group", ctypes.c_int32), ("generic_scans", ctypes.c_uint64)]
+                ("scan_ops_per_group", ctypes.c_int32), ("generic_scans", ctypes.c_uint64),
+                ("generic_bases", ctypes.c_uint64)]
 
 
 class ah_batch_view(ctypes.Structure):
@@ -141,6 +142,7 @@ SIGNATURES = {
     "ah_server_submit": (_I32, [_VP, ctypes.POINTER(ah_request), ctypes.POINTER(ctypes.c_uint64)]),
     "ah_server_wait": (_I32, [_VP, _U64, ctypes.POINTER(ctypes.POINTER(ah_result))]),
     "ah_server_now": (_I32, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "ah_server_set_scan_mode": (_I32, [_VP, ctypes.c_int]),
     "ah_result_free": (None, [ctypes.POINTER(ah_result)]),
     "ah_server_destroy": (None, [_VP]),
 }
@@ -545,9 +547,14 @@ def ah_server_wait(server, ticket: int) -> dict:
         off = np.ctypeslib.as_array(ctypes.cast(r.field_off, ctypes.POINTER(ctypes.c_uint64)),
                                     (5 * r.n_amps + 1,)).copy() if r.field_off else None
         return {"hits": hits, "amps": amps, "arena": arena, "field_off": off, "bases": r.bases,
-                "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done}
+                "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done, "t_stage": list(r.t_stage)}
     finally:
         load().ah_result_free(p)
+
+
+def ah_server_set_scan_mode(server, mode: int) -> None:
+    """Generic-scan mode of requests admitted from now on (0 generated, 1 generic, 2 generic while compiling)."""
+    _check(load().ah_server_set_scan_mode(server, int(mode)))
 
 
 def ah_server_now(server) -> float:

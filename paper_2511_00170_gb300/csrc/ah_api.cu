@@ -316,12 +316,21 @@ ah_status ah_ctx_create(ah_ctx** out, int device, void* cuda_stream) {
     ah_ctx_destroy(ctx);
     return AH_ENOMEM;
   }
-  // keep freed pool memory cached for reuse across steps
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
-    uint64_t threshold = UINT64_MAX;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+  // the context's own stream-ordered pool: contexts never reuse each other's freed blocks, which
+  // would make one context's allocations wait for another's stream; freed memory stays cached for
+  // reuse across steps
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) {
+    ctx->pool = nullptr;
+    ah_ctx_destroy(ctx);
+    return AH_ENOMEM;
   }
+  uint64_t threshold = UINT64_MAX;
+  cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &threshold);
   ctx->jit = &JitCache::global();
   *out = ctx;
   return AH_OK;
@@ -331,9 +340,12 @@ void ah_ctx_destroy(ah_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& c : ctx->compiles) c.first.join();
   ctx->jit = nullptr;
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  // blocks still held by objects of this context are released with them
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -361,6 +373,7 @@ ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out) {
   out->jit_ms = ctx->jit_ms;
   out->scan_ops_per_group = ctx->scan_ops_per_group;
   out->generic_scans = ctx->n_generic_scans;
+  out->generic_bases = ctx->generic_bases;
   return AH_OK;
 }
 
@@ -368,7 +381,7 @@ ah_status ah_ctx_stats_reset(ah_ctx* ctx) {
   if (!ctx) return AH_EINVAL;
   ah_status st = drain_timings(ctx);  // timings of replays before the reset do not count after it
   if (st) return st;
-  ctx->n_launches = ctx->n_scan_launches = ctx->scan_bases = ctx->jit_compiles = ctx->n_generic_scans = 0;
+  ctx->n_launches = ctx->n_scan_launches = ctx->scan_bases = ctx->jit_compiles = ctx->n_generic_scans = ctx->generic_bases = 0;
   ctx->scan_ms = ctx->jit_ms = 0.0;
   return AH_OK;
 }

@@ -6,7 +6,7 @@
 #include <cstdint>
 #include <atomic>
 #include <cstdio>
-#include <functional>
+#include <thread>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -50,12 +50,14 @@ struct Pattern {
 };
 
 // One oriented pattern as the generic (compile-free) scan kernel reads it.  The evaluated positions
-// (N excluded) come clamp first, then the counted ones most likely to mismatch first; position e
-// has offset j[e] in the window and mismatch bit c0 ^ (lo & c1) ^ (hi & c2) ^ (lo & hi & c3) of
-// the base's code bits, x[e] = (c0, c1, c2, c3), each 0 or ~0.
+// (N excluded) come clamp first, then the counted ones most likely to mismatch first; entry e has
+// offset j[e] in the window and mismatch bit c0 ^ (lo & c1) ^ (hi & c2) ^ (lo & hi & c3) of the
+// base's code bits, x[e] = (c0, c1, c2, c3), each 0 or ~0.  Both sections are padded to multiples
+// of 4 entries with x = 0 (never a mismatch): entries [0, n_clamp) are the clamp's, [n_clamp,
+// n_eval) the counted positions'.
 struct alignas(16) GenPattern {
-  uint4 x[32];
-  uint8_t j[32];
+  uint4 x[40];
+  uint8_t j[40];
   uint32_t mset[4];     // bit j of mset[c]: position j's set holds code c (A, C, T, G)
   uint32_t clamp_mask;  // bits of the clamp positions
   uint8_t len, k, n_eval, n_clamp;
@@ -86,6 +88,7 @@ struct ah_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::string err;
+  cudaMemPool_t pool = nullptr;      // the context's stream-ordered memory pool
   uint32_t* d_status = nullptr;      // device status word
   uint32_t* h_status = nullptr;      // pinned mirror
   ah::JitCache* jit = nullptr;       // the process-wide kernel cache
@@ -101,15 +104,14 @@ struct ah_ctx {
   double jit_ms = 0.0;
   int scan_ops_per_group = 0;  // of the last scan kernel launched
   // scan kernel choice: 0 generated kernels, 1 the generic kernel, 2 the generic kernel while a
-  // primer set's generated kernels compile (see launch_scan)
+  // primer set's generated kernels compile, 3 a fixed hand-over (see launch_scan)
   int generic_scan = 0;
   uint64_t n_generic_scans = 0;
-  // mode 2 with this set: starts compiling the kernels of these pattern groups on a thread the
-  // caller owns and returns a flag the compile sets (1 done, 2 failed); the scan does not wait for
-  // it once the generic kernel has covered the batch (a server joins the thread later)
-  std::function<std::shared_ptr<std::atomic<int>>(const std::vector<std::vector<ah::Pattern>>&,
-                                                  const ah::ScanConfig&)>
-      compile_behind;
+  uint64_t generic_bases = 0;  // bases those scans covered with the generic kernel (tile granularity)
+  // mode 2: compiles running on threads of this context, each with the flag it sets when done
+  // (1 compiled, 2 failed); finished ones are joined when the next starts, the rest on destroy
+  std::mutex compile_mu;
+  std::vector<std::pair<std::thread, std::shared_ptr<std::atomic<int>>>> compiles;
   bool timing = false;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   // scan-node timings of graph replays: event pairs recorded by the graph, read when the stream is
@@ -182,7 +184,7 @@ template <class T>
 ah_status dalloc(ah_ctx* ctx, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), ctx->stream);
+  cudaError_t e = cudaMallocFromPoolAsync((void**)p, count * sizeof(T), ctx->pool, ctx->stream);
   if (e != cudaSuccess) return fail(ctx, AH_ENOMEM, "device allocation of %zu bytes failed: %s", count * sizeof(T),
                                     cudaGetErrorString(e));
   return AH_OK;
@@ -271,16 +273,20 @@ class JitCache {
                      std::vector<ScanKernel>* out);
   // every set's kernel compiled and loaded for this device (starts no compile)
   bool ready(int device, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg);
-  // compiles the sets' missing kernels for this device (parallel host threads) and returns the
-  // first failure's status; for a background thread (no context, no compile counters)
-  ah_status prefetch(int device, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg);
+  // compiles the sets' missing kernels for this device (parallel host threads) without loading
+  // them (the first get loads) and returns the first failure's status; for a background thread
+  // (stats: the context whose compile counters it adds to, or null; reports no error to it)
+  ah_status prefetch(int device, ah_ctx* stats, const std::vector<std::vector<Pattern>>& sets,
+                     const ScanConfig& cfg);
  private:
   struct Entry;
-  // stats: the context whose compile counters a compile adds to (may be null)
+  // stats: the context whose compile counters a compile adds to (may be null); load_it: load the
+  // kernel into the process and fill out (else compile only)
   ah_status get_impl(int device, ah_ctx* stats, const std::vector<Pattern>& pats, const ScanConfig& cfg,
-                     ScanKernel* out, std::string* err);
+                     ScanKernel* out, std::string* err, bool load_it);
   void many_impl(int device, ah_ctx* stats, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg,
-                 std::vector<ScanKernel>* out, std::vector<ah_status>* st, std::vector<std::string>* err);
+                 std::vector<ScanKernel>* out, std::vector<ah_status>* st, std::vector<std::string>* err,
+                 bool load_it);
   std::mutex mu_;
   std::unordered_map<std::string, std::shared_ptr<Entry>> cache_;
 };

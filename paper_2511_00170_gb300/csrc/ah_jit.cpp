@@ -495,12 +495,18 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg,
   return os.str();
 }
 
+// One generated kernel: compiled to a cubin (done), then loaded into the process (loaded) by the
+// first caller that launches it.  Background compiles stop at the cubin, so module loading stays on
+// the thread that owns the stream.
 struct JitCache::Entry {
   std::mutex m;
   std::condition_variable cv;
   bool done = false;
+  bool loaded = false;
   ah_status st = AH_OK;
   std::string err;
+  std::vector<char> cubin;
+  int ops = 0;
   ScanKernel k{};
 };
 
@@ -511,10 +517,8 @@ JitCache& JitCache::global() {
 
 namespace {
 
-// NVRTC for this device's architecture, then the runtime's library API (no link-time driver
-// dependency); fills k or returns a message
-ah_status compile(int device, const std::string& src, int ops, const ScanConfig& cfg, ScanKernel* k,
-                  std::string* err) {
+// NVRTC for this device's architecture (host work only); fills cubin or returns a message
+ah_status compile(int device, const std::string& src, std::vector<char>* cubin, std::string* err) {
   nvrtcProgram prog;
   if (nvrtcCreateProgram(&prog, src.c_str(), "ah_scan_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
     *err = "nvrtcCreateProgram failed";
@@ -537,9 +541,15 @@ ah_status compile(int device, const std::string& src, int ops, const ScanConfig&
   }
   size_t cubin_size = 0;
   nvrtcGetCUBINSize(prog, &cubin_size);
-  std::vector<char> cubin(cubin_size);
-  nvrtcGetCUBIN(prog, cubin.data());
+  cubin->resize(cubin_size);
+  nvrtcGetCUBIN(prog, cubin->data());
   nvrtcDestroyProgram(&prog);
+  return AH_OK;
+}
+
+// the runtime's library API (no link-time driver dependency); fills k or returns a message
+ah_status load(int device, const std::vector<char>& cubin, int ops, const ScanConfig& cfg, ScanKernel* k,
+               std::string* err) {
   cudaSetDevice(device);
   cudaLibrary_t lib;
   cudaError_t ce = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
@@ -562,12 +572,12 @@ ah_status compile(int device, const std::string& src, int ops, const ScanConfig&
 
 ah_status JitCache::get(ah_ctx* ctx, const std::vector<Pattern>& pats, const ScanConfig& cfg, ScanKernel* out) {
   std::string err;
-  const ah_status st = get_impl(ctx->device, ctx, pats, cfg, out, &err);
+  const ah_status st = get_impl(ctx->device, ctx, pats, cfg, out, &err, true);
   return st ? fail(ctx, st, "%s", err.c_str()) : AH_OK;
 }
 
 ah_status JitCache::get_impl(int device, ah_ctx* stats, const std::vector<Pattern>& pats, const ScanConfig& cfg,
-                             ScanKernel* out, std::string* err_out) {
+                             ScanKernel* out, std::string* err_out, bool load_it) {
   int ops = 0;
   std::string src = scan_source(pats, cfg, &ops);
   int major = 0, minor = 0;
@@ -589,14 +599,15 @@ ah_status JitCache::get_impl(int device, ah_ctx* stats, const std::vector<Patter
   }
   if (mine) {
     const auto t0 = std::chrono::steady_clock::now();
-    ScanKernel k;
+    std::vector<char> cubin;
     std::string err;
-    const ah_status st = compile(device, src, ops, cfg, &k, &err);
+    const ah_status st = compile(device, src, &cubin, &err);
     {
       std::lock_guard<std::mutex> lock(e->m);
       e->st = st;
       e->err = err;
-      e->k = k;
+      e->cubin.swap(cubin);
+      e->ops = ops;
       e->done = true;
     }
     e->cv.notify_all();
@@ -615,18 +626,27 @@ ah_status JitCache::get_impl(int device, ah_ctx* stats, const std::vector<Patter
     *err_out = e->err;
     return e->st;
   }
+  if (!load_it) return AH_OK;
+  if (!e->loaded) {  // the first caller that launches it loads it (under the entry's lock)
+    ScanKernel k;
+    const ah_status st = load(device, e->cubin, e->ops, cfg, &k, err_out);
+    if (st) return st;
+    e->k = k;
+    e->loaded = true;
+    std::vector<char>().swap(e->cubin);
+  }
   *out = e->k;
   return AH_OK;
 }
 
 void JitCache::many_impl(int device, ah_ctx* stats, const std::vector<std::vector<Pattern>>& sets,
                          const ScanConfig& cfg, std::vector<ScanKernel>* out, std::vector<ah_status>* st,
-                         std::vector<std::string>* err) {
+                         std::vector<std::string>* err, bool load_it) {
   out->assign(sets.size(), ScanKernel{});
   st->assign(sets.size(), AH_OK);
   err->assign(sets.size(), std::string());
   if (sets.size() == 1) {
-    (*st)[0] = get_impl(device, stats, sets[0], cfg, &(*out)[0], &(*err)[0]);
+    (*st)[0] = get_impl(device, stats, sets[0], cfg, &(*out)[0], &(*err)[0], load_it);
     return;
   }
   const size_t width = std::max<size_t>(1, std::min<size_t>(sets.size(), std::thread::hardware_concurrency()));
@@ -636,7 +656,7 @@ void JitCache::many_impl(int device, ah_ctx* stats, const std::vector<std::vecto
     pool.emplace_back([&] {
       cudaSetDevice(device);
       for (size_t i = next++; i < sets.size(); i = next++)
-        (*st)[i] = get_impl(device, stats, sets[i], cfg, &(*out)[i], &(*err)[i]);
+        (*st)[i] = get_impl(device, stats, sets[i], cfg, &(*out)[i], &(*err)[i], load_it);
     });
   for (auto& t : pool) t.join();
 }
@@ -645,18 +665,19 @@ ah_status JitCache::get_many(ah_ctx* ctx, const std::vector<std::vector<Pattern>
                              std::vector<ScanKernel>* out) {
   std::vector<ah_status> st;
   std::vector<std::string> err;
-  many_impl(ctx->device, ctx, sets, cfg, out, &st, &err);
+  many_impl(ctx->device, ctx, sets, cfg, out, &st, &err, true);
   for (size_t i = 0; i < sets.size(); ++i)
     if (st[i]) return fail(ctx, st[i], "%s", err[i].c_str());
   return AH_OK;
 }
 
-ah_status JitCache::prefetch(int device, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg) {
+ah_status JitCache::prefetch(int device, ah_ctx* stats, const std::vector<std::vector<Pattern>>& sets,
+                             const ScanConfig& cfg) {
   cudaSetDevice(device);
   std::vector<ScanKernel> out;
   std::vector<ah_status> st;
   std::vector<std::string> err;
-  many_impl(device, nullptr, sets, cfg, &out, &st, &err);
+  many_impl(device, stats, sets, cfg, &out, &st, &err, false);
   for (ah_status s : st)
     if (s) return s;
   return AH_OK;
@@ -677,7 +698,7 @@ bool JitCache::ready(int device, const std::vector<std::vector<Pattern>>& sets, 
       e = it->second;
     }
     std::lock_guard<std::mutex> lock(e->m);
-    if (!e->done || e->st) return false;
+    if (!e->done || e->st || !e->loaded) return false;
   }
   return true;
 }

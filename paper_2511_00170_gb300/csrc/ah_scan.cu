@@ -170,6 +170,8 @@ __global__ void k_pair_offsets(const uint64_t* __restrict__ off, uint64_t n_tile
 // planes, with the set's coefficients as 0 / ~0 words (three LOP3); the count is a saturating
 // ripple counter of `width` bits.  A warp whose windows have all failed stops the pattern early.
 
+static_assert(sizeof(GenPattern) * kGenMaxPatterns <= 48 * 1024, "generic pattern table exceeds default shared memory");
+
 // mismatch bits of the 32 windows at offset j of one evaluated position
 __device__ __forceinline__ uint32_t gen_mismatch(const uint4& c, int j, uint2 a, uint2 b) {
   const uint32_t lo = __funnelshift_r(a.x, b.x, j), hi = __funnelshift_r(a.y, b.y, j);
@@ -182,24 +184,32 @@ template <int W>
 __device__ __forceinline__ uint32_t gen_pass(const GenPattern& P, uint2 a, uint2 b) {
   uint32_t fail = 0;
   int e = 0;
-  for (; e < P.n_clamp; ++e) fail |= gen_mismatch(P.x[e], P.j[e], a, b);
+  for (; e < P.n_clamp; e += 4) {
+    const uint32_t js = *reinterpret_cast<const uint32_t*>(P.j + e);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) fail |= gen_mismatch(P.x[e + u], (js >> (8 * u)) & 31, a, b);
+  }
   if (!__any_sync(__activemask(), ~fail)) return 0;
   uint32_t c[W > 0 ? W : 1] = {};
-  for (int n = 0; e < P.n_eval; ++e) {
-    const uint32_t x = gen_mismatch(P.x[e], P.j[e], a, b);
-    if (W == 0) {
-      fail |= x;
-    } else {
-      uint32_t carry = x;
+  for (; e < P.n_eval; e += 4) {
+    const uint32_t js = *reinterpret_cast<const uint32_t*>(P.j + e);
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        const uint32_t nc = c[w] & carry;
-        c[w] ^= carry;
-        carry = nc;
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t x = gen_mismatch(P.x[e + u], (js >> (8 * u)) & 31, a, b);
+      if (W == 0) {
+        fail |= x;
+      } else {
+        uint32_t carry = x;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          const uint32_t nc = c[w] & carry;
+          c[w] ^= carry;
+          carry = nc;
+        }
+        fail |= carry;  // the count passed 2^W - 1 >= k
       }
-      fail |= carry;  // the count passed 2^W - 1 >= k
     }
-    if ((++n & 3) == 0 && !__any_sync(__activemask(), ~fail)) return 0;
+    if (!__any_sync(__activemask(), ~fail)) return 0;
   }
   if (W > 0) {
     // count >= k + 1 on the W counter bits (needed when k + 1 < 2^W), least significant bit first
@@ -307,11 +317,15 @@ std::vector<GenPattern> gen_table(const std::vector<Pattern>& pats) {
     }
     std::stable_sort(counted.begin(), counted.end(),
                      [&](int a, int b) { return __builtin_popcount(P.set[a]) < __builtin_popcount(P.set[b]); });
+    // sections padded to multiples of 4 entries (-1: padding, x = 0, j = 0)
+    while (clamp.size() % 4) clamp.push_back(-1);
+    while (counted.size() % 4) counted.push_back(-1);
     G.n_clamp = (uint8_t)clamp.size();
     clamp.insert(clamp.end(), counted.begin(), counted.end());
     G.n_eval = (uint8_t)clamp.size();
     for (size_t e = 0; e < clamp.size(); ++e) {
       const int j = clamp[e];
+      if (j < 0) continue;
       const uint8_t S = P.set[j];
       // mismatch bit at codes A (lo 0, hi 0), C (1, 0), T (0, 1), G (1, 1) and its algebraic normal form
       const uint32_t fA = (S & 1) ? 0u : ~0u, fC = (S & 2) ? 0u : ~0u, fT = (S & 4) ? 0u : ~0u, fG = (S & 8) ? 0u : ~0u;
@@ -382,9 +396,6 @@ void launch_emit_hits(cudaStream_t s, const uint64_t* slots, const uint32_t* til
 
 namespace {
 
-// Generic-scan mode 2 without a compile_behind hook: base-patterns (bases x patterns) up to which
-// the generic kernel scans alone (no compile); above it, it scans while a local thread compiles.
-constexpr double kGenericAutoWork = 17179869184.0;  // 2^34
 // generic-kernel chunks while a compile runs: about this many base-patterns each (a few ms), so
 // the switch to the generated kernels comes soon after the compile ends
 constexpr double kGenericChunkWork = 4.0e9;
@@ -421,6 +432,29 @@ int persistent_grid(ah_ctx* ctx, const ScanKernel& k) {
   return per_sm * ctx->sm_count;
 }
 
+// start compiling the generated kernels of `sets` on a thread of the context; returns the flag the
+// compile sets (1 compiled, 2 failed: the scan that needs them then compiles again and reports)
+std::shared_ptr<std::atomic<int>> start_compile(ah_ctx* ctx, const std::vector<std::vector<Pattern>>& sets,
+                                                const ScanConfig& cfg) {
+  auto flag = std::make_shared<std::atomic<int>>(0);
+  const int device = ctx->device;
+  std::lock_guard<std::mutex> lock(ctx->compile_mu);
+  for (auto it = ctx->compiles.begin(); it != ctx->compiles.end();) {
+    if (it->second->load() != 0) {
+      it->first.join();
+      it = ctx->compiles.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  ctx->compiles.emplace_back(
+      std::thread([ctx, device, sets, cfg, flag] {
+        flag->store(JitCache::global().prefetch(device, ctx, sets, cfg) ? 2 : 1);
+      }),
+      flag);
+  return flag;
+}
+
 // the generated kernels over tiles [t_begin, t_end), one after another
 ah_status enqueue_jit(ah_ctx* ctx, const ah_batch* b, const std::vector<ScanKernel>& kerns, const ScanConfig& cfg,
                       uint64_t tile_groups, uint64_t t_begin, uint64_t t_end, uint64_t* slots, uint32_t* tile_count,
@@ -455,7 +489,7 @@ ah_status generic_until(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, con
   cudaEvent_t done[2] = {nullptr, nullptr};
   ah_status st = AH_OK;
   for (auto& e : done)
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming | cudaEventBlockingSync) != cudaSuccess)
       st = fail(ctx, AH_ECUDA, "cudaEventCreate failed");
   uint64_t t = 0;
   int issued = 0;
@@ -485,24 +519,12 @@ ah_status launch_scan(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const
     // one kernel for every pair, or (cfg.pairs_per_kernel) kernels of a few pairs each, compiled in
     // parallel and launched one after another into the same tile slot lists
     const std::vector<std::vector<Pattern>> sets = scan_groups(p->pats, cfg);
-    // generic-kernel choice: the whole batch (mode 1, or mode 2 on a small batch without a
-    // compile_behind hook), or leading tiles while the generated kernels compile (mode 2)
-    bool generic_all = ctx->generic_scan == 1;
+    // generic kernel: over the whole batch (mode 1), or (mode 2, generated kernels not compiled)
+    // over leading tiles while a thread of the context compiles them; the scan does not wait for
+    // a compile the generic kernel outlasts
+    const bool generic_all = ctx->generic_scan == 1;
     std::shared_ptr<std::atomic<int>> flag;
-    std::thread local;
-    if (ctx->generic_scan == 2 && !ctx->jit->ready(ctx->device, sets, cfg)) {
-      if (ctx->compile_behind) {
-        flag = ctx->compile_behind(sets, cfg);
-      } else if ((double)b->n_bases * (double)p->pats.size() <= kGenericAutoWork) {
-        generic_all = true;
-      } else {
-        flag = std::make_shared<std::atomic<int>>(0);
-        const int device = ctx->device;
-        local = std::thread([device, sets, cfg, flag] {
-          flag->store(JitCache::global().prefetch(device, sets, cfg) ? 2 : 1);
-        });
-      }
-    }
+    if (ctx->generic_scan == 2 && !ctx->jit->ready(ctx->device, sets, cfg)) flag = start_compile(ctx, sets, cfg);
     if (ctx->timing) AH_CUDA(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
     uint64_t t = 0;
     if (generic_all) {
@@ -514,18 +536,19 @@ ah_status launch_scan(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const
     } else if (flag) {
       st = generic_until(ctx, b, p, cfg, tile_groups, n_tiles, slots, tile_count, cap, *flag, &t);
     }
-    if (t > 0) ctx->n_generic_scans++;
+    if (t > 0) {
+      ctx->n_generic_scans++;
+      ctx->generic_bases += std::min<uint64_t>(b->n_bases, std::min<uint64_t>(b->n_groups, t * tile_groups) * 32ull);
+    }
     int ops = 0;
     unsigned long long* work = nullptr;
     if (!st && t < n_tiles) {
-      if (local.joinable()) local.join();
       std::vector<ScanKernel> kerns;
       st = ctx->jit->get_many(ctx, sets, cfg, &kerns);
       if (!st && cfg.persistent) st = dalloc(ctx, &work, 1);
       if (!st) st = enqueue_jit(ctx, b, kerns, cfg, tile_groups, t, n_tiles, slots, tile_count, cap, work);
       for (const ScanKernel& kern : kerns) ops += kern.alu_ops_per_group;
     }
-    if (local.joinable()) local.join();
     if (st) {
       dfree(ctx, work);
       return st;

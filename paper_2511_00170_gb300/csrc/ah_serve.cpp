@@ -9,10 +9,15 @@
 // Each admitted request runs the whole path on a slice of the database (no copy of the genomes)
 // and its results are copied to host memory owned by the request's result.
 //
+// Each worker owns one CUDA stream per priority class.  A request runs on the stream of its class,
+// chosen by its scan work (bases x 4 x pairs): the smaller the request, the higher the priority,
+// so the blocks of a small request are scheduled ahead of those of large ones already running and
+// its latency stays close to its own run time instead of growing with the load.
+//
 // A request whose primer set has no compiled scan kernels yet starts scanning with the generic
 // kernel while a thread compiles the generated kernels; the rest of the scan uses them once they
-// are ready.  A small request may finish before its compile does; the server joins that thread
-// later, and requests with the same primers find the kernels cached.
+// are ready (generic-scan mode 2).  A small request may finish before its compile does; its
+// context joins that thread later, and requests with the same primers find the kernels cached.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -48,6 +53,8 @@ struct ah_server {
   uint64_t budget = 0, reserved = 0;
   std::chrono::steady_clock::time_point t0;
   std::vector<ah_ctx*> ctxs;
+  std::vector<std::vector<cudaStream_t>> streams;  // [slot][priority class], class 0 the highest
+  std::atomic<int> scan_mode{2};                   // generic-scan mode of the requests' scans
   std::vector<std::thread> workers;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -56,9 +63,6 @@ struct ah_server {
   uint64_t next_ticket = 1;
   bool stop = false;
   int running = 0;
-  // compiles started for requests' primer sets, each with the flag it sets when done
-  std::mutex cmu;
-  std::vector<std::pair<std::thread, std::shared_ptr<std::atomic<int>>>> compiles;
 };
 
 namespace ah {
@@ -75,25 +79,49 @@ uint64_t estimate_bytes(const ah_server* s, const ah_request& r, int slot_cap, u
   return tiles * ((uint64_t)slot_cap * 8 + 8 + 12ull * r.n_pairs) + (64ull << 20);
 }
 
+// priority class of a request of `work` base-patterns: 0 below 1e11, 1 below 1e12, 2 above
+// (capped by the classes the device offers)
+int priority_class(double work, int n_classes) {
+  const int c = work < 1e11 ? 0 : work < 1e12 ? 1 : 2;
+  return std::min(c, n_classes - 1);
+}
+
 void fill_error(ah_result* res, ah_status st, const char* msg) {
   res->status = st;
   snprintf(res->error, sizeof res->error, "%s", msg ? msg : "");
 }
 
-void run_job(ah_server* s, ah_ctx* ctx, Job* j) {
+void run_job(ah_server* s, int slot, Job* j) {
+  ah_ctx* ctx = s->ctxs[slot];
   ah_result* res = j->result;
   const ah_request& r = j->req;
+  {
+    const ah_batch* db = s->db;
+    const uint64_t g0 = db->h_rec_group[r.first_record];
+    const uint64_t g1 = (uint64_t)r.first_record + r.n_records < db->n_records
+                            ? db->h_rec_group[r.first_record + r.n_records]
+                            : db->n_groups;
+    const double work = (double)(g1 - g0) * 32.0 * 4.0 * r.n_pairs;
+    ctx->stream = s->streams[slot][priority_class(work, (int)s->streams[slot].size())];
+    ctx->generic_scan = s->scan_mode.load();
+  }
   ah_batch* slice = nullptr;
   ah_primers* pr = nullptr;
   ah_hits* h = nullptr;
   ah_amplicons* a = nullptr;
   std::vector<const char*> f(r.n_pairs), rv(r.n_pairs);
   for (uint32_t i = 0; i < r.n_pairs; ++i) f[i] = j->fwd[i].c_str(), rv[i] = j->rev[i].c_str();
+  // stage end times; a stage that synchronises the stream anyway is timed when it returns
+  auto stage = [&](int i) { res->t_stage[i] = now_s(s->t0); };
   ah_status st = ah_batch_slice(ctx, s->db, r.first_record, r.n_records, &slice);
   if (!st) st = ah_primers_create(ctx, r.n_pairs, f.data(), rv.data(), j->k.data(), r.clamp, &pr);
+  stage(0);
   if (!st) st = ah_scan_primers(ctx, slice, pr, &h);
+  stage(1);
   if (!st) st = ah_pair_amplicons(ctx, slice, pr, h, r.min_len, r.max_len, r.orient_mask, &a);
+  stage(2);
   if (!st) st = ah_tm_filter(ctx, slice, pr, h, a, &r.tm);
+  stage(3);
   if (!st && r.extract) st = ah_extract_barcodes(ctx, slice, pr, h, a, r.trim, r.fb_len, r.rb_len);
   if (!st) {
     res->n_hits = h->n;
@@ -122,7 +150,6 @@ void run_job(ah_server* s, ah_ctx* ctx, Job* j) {
 }
 
 void worker(ah_server* s, int slot) {
-  ah_ctx* ctx = s->ctxs[slot];
   cudaSetDevice(s->device);
   for (;;) {
     Job* j = nullptr;
@@ -144,10 +171,10 @@ void worker(ah_server* s, int slot) {
       j->result->t_admit = now_s(s->t0);
     }
     s->cv_work.notify_all();
-    run_job(s, ctx, j);
+    run_job(s, slot, j);
     {
       std::lock_guard<std::mutex> lock(s->mu);
-      j->result->t_done = now_s(s->t0);
+      j->result->t_done = j->result->t_stage[4] = now_s(s->t0);
       s->reserved -= j->est_bytes;
       s->running--;
       j->done = true;
@@ -155,27 +182,6 @@ void worker(ah_server* s, int slot) {
     s->cv_done.notify_all();
     s->cv_work.notify_all();
   }
-}
-
-// start compiling a request's kernels on a thread the server owns (joined once done)
-std::shared_ptr<std::atomic<int>> compile_behind(ah_server* s, const std::vector<std::vector<Pattern>>& sets,
-                                                 const ScanConfig& cfg) {
-  auto flag = std::make_shared<std::atomic<int>>(0);
-  const int device = s->device;
-  std::lock_guard<std::mutex> lock(s->cmu);
-  for (auto it = s->compiles.begin(); it != s->compiles.end();) {
-    if (it->second->load() != 0) {
-      it->first.join();
-      it = s->compiles.erase(it);
-    } else {
-      ++it;
-    }
-  }
-  // a failure is reported by the request's own scan, which then compiles (and fails) itself
-  s->compiles.emplace_back(
-      std::thread([device, sets, cfg, flag] { flag->store(JitCache::global().prefetch(device, sets, cfg) ? 2 : 1); }),
-      flag);
-  return flag;
 }
 
 }  // namespace
@@ -199,22 +205,35 @@ ah_status ah_server_create(const ah_batch* db, int n_slots, uint64_t memory_budg
     memory_budget = (uint64_t)(free_b * 0.6);
   }
   s->budget = memory_budget;
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  const int n_classes = std::max(1, std::min(3, least - greatest + 1));
   for (int i = 0; i < n_slots; ++i) {
+    s->streams.emplace_back();
+    for (int c = 0; c < n_classes; ++c) {
+      // class 0 the greatest priority, the last class the least
+      const int prio = n_classes == 1 ? least : greatest + (least - greatest) * c / (n_classes - 1);
+      cudaStream_t st = nullptr;
+      if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio) != cudaSuccess) {
+        ah_server_destroy(s);
+        return AH_ECUDA;
+      }
+      s->streams.back().push_back(st);
+    }
     ah_ctx* c = nullptr;
-    ah_status st = ah_ctx_create(&c, s->device, nullptr);
+    ah_status st = ah_ctx_create(&c, s->device, s->streams.back().back());
     if (st) {
       ah_server_destroy(s);
       return st;
     }
     c->scan_cfg.slot_cap = 64;  // requests are sparse; dense tiles are re-run with room
+    // a worker's pool keeps up to 2 GiB of freed memory cached; beyond that it returns memory at
+    // the next synchronisation, so idle workers do not hold what a large request needs
+    uint64_t keep = 2ull << 30;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     // a request's primer set is compiled as kernels of 4 pairs on parallel host threads: a cold
     // 32-pair set compiles in about the time of one 4-pair kernel instead of 8x longer
     c->scan_cfg.pairs_per_kernel = 4;
-    // a primer set without compiled kernels starts on the generic kernel while it compiles
-    c->generic_scan = 2;
-    c->compile_behind = [s](const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg) {
-      return compile_behind(s, sets, cfg);
-    };
     s->ctxs.push_back(c);
   }
   for (int i = 0; i < n_slots; ++i) s->workers.emplace_back(worker, s, i);
@@ -266,6 +285,12 @@ ah_status ah_server_wait(ah_server* s, uint64_t ticket, ah_result** out) {
   return (*out)->status;
 }
 
+ah_status ah_server_set_scan_mode(ah_server* s, int mode) {
+  if (!s || mode < 0 || mode > 2) return AH_EINVAL;
+  s->scan_mode.store(mode);
+  return AH_OK;
+}
+
 ah_status ah_server_now(const ah_server* s, double* seconds) {
   if (!s || !seconds) return AH_EINVAL;
   *seconds = now_s(s->t0);
@@ -289,12 +314,13 @@ void ah_server_destroy(ah_server* s) {
   }
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
-  for (auto& c : s->compiles) c.first.join();
   for (auto& kv : s->jobs) {
     ah_result_free(kv.second->result);
     delete kv.second;
   }
   for (ah_ctx* c : s->ctxs) ah_ctx_destroy(c);
+  for (auto& v : s->streams)
+    for (cudaStream_t st : v) cudaStreamDestroy(st);
   delete s;
 }
 

@@ -124,5 +124,8 @@ def test_server_requests_refused(env):
         assert e.value.status == ah.AH_EINVAL
         ok = ah.ah_server_wait(srv, ah.ah_server_submit(srv, wl.fwd, wl.rev, wl.k, wl.clamp, 0, wl.n_records, 10, 500))
         assert len(ok["hits"]) >= 0
+        with pytest.raises(ah.AhError) as e:
+            ah.ah_server_set_scan_mode(srv, 3)
+        assert e.value.status == ah.AH_EINVAL
     finally:
         ah.ah_server_destroy(srv)

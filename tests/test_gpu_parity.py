@@ -447,8 +447,9 @@ def test_generic_scan_many_pairs(generic, threads, gpt, slots):
 
 
 def test_generic_scan_auto(engine):
-    """Mode 2 scans a primer set whose kernels are not compiled with the generic kernel (no compile),
-    and once they are compiled, with the generated kernels."""
+    """Mode 2 starts a primer set whose kernels are not compiled on the generic kernel, compiling them
+    on a thread of the context (not waited for by a scan the generic kernel finishes first); once
+    they are compiled, it scans with them."""
     from paper_2511_00170_gb300 import ah
 
     wl = synth.random_small(7_770_001, n_records=3, len_lo=500, len_hi=3000, n_pairs=2, plen_lo=17, plen_hi=23,
@@ -459,13 +460,13 @@ def test_generic_scan_auto(engine):
         ah.ah_ctx_stats_reset(ctx)
         _run_both(engine, wl)
         s = ah.ah_ctx_stats_get(ctx)
-        assert s["generic_scans"] == 2 and s["jit_compiles"] == 0   # two steps (filtered, unfiltered)
+        assert s["generic_scans"] >= 1   # the second step may find them compiled
         ah.ah_ctx_set_generic_scan(ctx, 0)
-        _run_both(engine, wl)                                        # compiles
+        _run_both(engine, wl)                                        # waits for the compile if still running
         ah.ah_ctx_set_generic_scan(ctx, 2)
         ah.ah_ctx_stats_reset(ctx)
         _run_both(engine, wl)
         s = ah.ah_ctx_stats_get(ctx)
-        assert s["generic_scans"] == 0 and s["jit_compiles"] == 0
+        assert s["generic_scans"] == 0 and s["generic_bases"] == 0 and s["jit_compiles"] == 0
     finally:
         ah.ah_ctx_set_generic_scan(ctx, 0)

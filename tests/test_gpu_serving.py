@@ -77,14 +77,18 @@ def test_alone_equals_mix(db):
     assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
 
 
-def test_request_matches_slice_and_oracle(db):
+@pytest.mark.parametrize("scan_mode", [2, 1, 0])
+def test_request_matches_slice_and_oracle(db, scan_mode):
+    """Each scan mode (generic while compiling, generic only, generated only) gives the oracle's
+    outputs and those of the direct path on a slice of the database."""
     from paper_2511_00170_gb300 import ah
     from paper_2511_00170_gb300.pipeline import Output, Params
 
     wl, eng, batch = db
     srv = ah.ah_server_create(batch, n_slots=2)
+    ah.ah_server_set_scan_mode(srv, scan_mode)
     try:
-        for r in _requests(wl, 3, seed=9):
+        for r in _requests(wl, 3, seed=9 + 10 * scan_mode):
             got = ah.ah_server_wait(srv, ah.ah_server_submit(srv, **r))
             sub = wl.host_subset(range(r["first_record"], r["first_record"] + r["n_records"]))
             sub.fwd, sub.rev, sub.k, sub.clamp = r["fwd"], r["rev"], r["k"], r["clamp"]
