@@ -305,11 +305,13 @@ ah_status ah_pair_amplicons_noalloc(void* cuda_stream, const ah_hit* d_hits, uin
 typedef struct {
   double Na, K, Tris, Mg, dNTPs; /* mM */
   double dnac1, dnac2;           /* nM, the two strand concentrations */
-  int32_t saltcorr;              /* 0 none; 1-6 as in Biopython's salt_correction; default 5 */
+  int32_t saltcorr;              /* 0 none; 1-7 as in Biopython's salt_correction (7: Owczarzy et
+                                    al. 2008, Mg2+ and dNTPs modelled directly); default 5 */
   int32_t filter;                /* nonzero: drop amplicons with Tm < min_tm or undefined Tm */
   double min_tm;                 /* degrees C */
   int32_t variants;              /* degenerate primers: 0 every concrete variant (default);
                                     1 only variants matching the site within k and the clamp */
+  int32_t selfcomp;              /* 1: self-complementary duplexes (symmetry term, C = dnac1) */
 } ah_tm_params;
 
 /* Fill tm and flags of every amplicon (Section "Implementations": Biopython's Tm_NN in C; Section

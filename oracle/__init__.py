@@ -83,6 +83,8 @@ def _get():
             L.or_extract.restype = i64
             L.or_free.argtypes = [vp]
             L.or_free.restype = None
+            L.or_free_mg.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.or_free_mg.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -154,6 +156,11 @@ def tm_duplex(seq: str, cseq: str, tm) -> Optional[float]:
     p = _params(tm)
     t = _get().or_tm_duplex(seq.encode(), cseq.encode(), len(seq), ctypes.byref(p), ctypes.byref(d))
     return t if d.value else None
+
+
+def free_mg(mg_mM: float, dntps_mM: float) -> float:
+    """Free Mg2+ (mM) beside dNTPs that bind it one to one (salt method 7's input)."""
+    return _get().or_free_mg(float(mg_mM), float(dntps_mM))
 
 
 def tm_site(primer: str, site: str, tm, k: Optional[int] = None, clamp: int = 0) -> Optional[float]:

@@ -437,7 +437,7 @@ static int find_param(const nn_param* t, int n, const char* key, double* dh, dou
 typedef struct {
   double Na, K, Tris, Mg, dNTPs; /* mM */
   double dnac1, dnac2;           /* nM */
-  int saltcorr;                  /* 0 none, 1..6 */
+  int saltcorr;                  /* 0 none, 1..7 */
   int selfcomp;
   int variants;                  /* 0: every concrete variant (R14); 1: only those matching the site */
 } or_tm_params;
@@ -452,12 +452,56 @@ static double gc_fraction(const char* s, int L) {
   return n ? (double)gc / n : 0.0;
 }
 
+/* Free Mg2+ (mM) when dNTPs bind Mg2+ one to one with association constant Ka = 3e4 per M
+ * (Owczarzy et al. 2008): with x the free Mg2+, the bound amount Mg - x and the free dNTP
+ * dNTP - (Mg - x) satisfy Ka x (dNTP - Mg + x) = Mg - x, whose positive root is taken (in M). */
+double or_free_mg(double mg_mM, double dntps_mM) {
+  const double ka = 3e4, mg = mg_mM * 1e-3, dn = dntps_mM * 1e-3;
+  if (dn <= 0.0) return mg_mM;
+  const double b = ka * (dn - mg) + 1.0;
+  return 1e3 * (-b + sqrt(b * b + 4.0 * ka * mg)) / (2.0 * ka);
+}
+
+/* Salt method 7 (Owczarzy et al. 2008, Mg2+ with monovalent ions): a correction to 1/Tm.  [Mon+]
+ * = Na + K + Tris/2 (no Na-equivalent for Mg2+), [Mg2+] free of dNTPs, both in M, f the G/C
+ * fraction, N the duplex length:
+ *   [Mon+] > 0 and sqrt([Mg2+]) / [Mon+] < 0.22: monovalent ions dominate and the correction is
+ *     Owczarzy et al. 2004's (method 6) at [Mon+];
+ *   otherwise a + b ln[Mg2+] + f (c + d ln[Mg2+]) + (e + f' ln[Mg2+] + g ln^2[Mg2+]) / (2 (N - 1))
+ *     with a = 3.92e-5, b = -9.11e-6, c = 6.26e-5, d = 1.42e-5, e = -4.82e-4, f' = 5.25e-4,
+ *     g = 8.31e-5, where for a ratio below 6 the monovalent ions modify three of them:
+ *     a *= 0.843 - 0.352 sqrt([Mon+]) ln[Mon+], d *= 1.279 - 4.03e-3 ln[Mon+] - 8.03e-3 ln^2[Mon+],
+ *     g *= 0.486 - 0.258 ln[Mon+] + 5.25e-3 ln^3[Mon+].
+ * Undefined (*ok = 0) without any cation. */
+static double salt_owczarzy2008(const or_tm_params* p, const char* seq, int L, int* ok) {
+  const double mon = (p->Na + p->K + p->Tris / 2.0) * 1e-3;
+  const double mg = or_free_mg(p->Mg, p->dNTPs) * 1e-3;
+  const double f = gc_fraction(seq, L);
+  double a = 3.92e-5, b = -9.11e-6, c = 6.26e-5, d = 1.42e-5, e = -4.82e-4, f2 = 5.25e-4, g = 8.31e-5;
+  if (mon > 0.0) {
+    const double ratio = sqrt(mg) / mon, lm = log(mon);
+    if (ratio < 0.22) return (4.29 * f - 3.95) * 1e-5 * lm + 9.40e-6 * lm * lm;
+    if (ratio < 6.0) {
+      a *= 0.843 - 0.352 * sqrt(mon) * lm;
+      d *= 1.279 - 4.03e-3 * lm - 8.03e-3 * lm * lm;
+      g *= 0.486 - 0.258 * lm + 5.25e-3 * lm * lm * lm;
+    }
+  }
+  if (!(mg > 0.0)) {
+    *ok = 0;
+    return 0.0;
+  }
+  const double lg = log(mg);
+  return a + b * lg + f * (c + d * lg) + (e + f2 * lg + g * lg * lg) / (2.0 * (L - 1));
+}
+
 /* Salt correction (von Ahsen et al. 2001 Na-equivalent for Mg/dNTPs; methods: 1 Schildkraut &
  * Lifson 1965, 2 Wetmur 1991, 3 SantaLucia et al. 1996, 4 and 5 SantaLucia 1998, 6 Owczarzy et
- * al. 2004).  Returns 0 with *ok = 0 when the method is not covered. */
+ * al. 2004, 7 Owczarzy et al. 2008).  Returns 0 with *ok = 0 when the method is not covered. */
 static double salt_correction(const or_tm_params* p, const char* seq, int L, int* ok) {
   *ok = 1;
   if (p->saltcorr == 0) return 0.0;
+  if (p->saltcorr == 7) return salt_owczarzy2008(p, seq, L, ok);
   double Mon = p->Na + p->K + p->Tris / 2.0;
   if ((p->K + p->Mg + p->Tris + p->dNTPs) > 0 && p->dNTPs < p->Mg) Mon += 120.0 * sqrt(p->Mg - p->dNTPs);
   double mon = Mon * 1e-3;
@@ -581,7 +625,7 @@ double or_tm_duplex(const char* seq, const char* cseq, int L, const or_tm_params
   if (p->saltcorr == 5) ds += corr;
   double tm = (1000.0 * dh) / (ds + R * log(k)) - 273.15;
   if (p->saltcorr >= 1 && p->saltcorr <= 4) tm += corr;
-  if (p->saltcorr == 6) tm = 1.0 / (1.0 / (tm + 273.15) + corr) - 273.15;
+  if (p->saltcorr == 6 || p->saltcorr == 7) tm = 1.0 / (1.0 / (tm + 273.15) + corr) - 273.15;
   return tm;
 }
 

@@ -884,8 +884,8 @@ ah_status ah_pair_amplicons(ah_ctx* ctx, const ah_batch* b, const ah_primers* p,
 ah_status ah_tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a,
                        const ah_tm_params* params) {
   if (!ctx || !b || !p || !h || !a || !params) return fail(ctx, AH_EINVAL, "ah_tm_filter: NULL argument");
-  if (params->saltcorr < 0 || params->saltcorr > 6)
-    return fail(ctx, AH_EINVAL, "ah_tm_filter: salt correction method %d is not supported (0-6)", params->saltcorr);
+  if (params->saltcorr < 0 || params->saltcorr > 7)
+    return fail(ctx, AH_EINVAL, "ah_tm_filter: salt correction method %d is not supported (0-7)", params->saltcorr);
   cudaSetDevice(ctx->device);
   return tm_filter(ctx, b, p, h, a, params);
 }
@@ -893,8 +893,8 @@ ah_status ah_tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, cons
 ah_status ah_tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const char* const* cseqs,
                          const ah_tm_params* params, double* tm_out) {
   if (!ctx || (n && (!seqs || !cseqs || !tm_out)) || !params) return fail(ctx, AH_EINVAL, "ah_tm_duplexes: NULL argument");
-  if (params->saltcorr < 0 || params->saltcorr > 6)
-    return fail(ctx, AH_EINVAL, "ah_tm_duplexes: salt correction method %d is not supported (0-6)", params->saltcorr);
+  if (params->saltcorr < 0 || params->saltcorr > 7)
+    return fail(ctx, AH_EINVAL, "ah_tm_duplexes: salt correction method %d is not supported (0-7)", params->saltcorr);
   cudaSetDevice(ctx->device);
   return tm_duplexes(ctx, n, seqs, cseqs, params, tm_out);
 }
@@ -903,8 +903,8 @@ ah_status ah_tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const
                       const uint8_t* clamp,
                       const ah_tm_params* params, double* tm_out) {
   if (!ctx || (n && (!primers || !sites || !tm_out)) || !params) return fail(ctx, AH_EINVAL, "ah_tm_sites: NULL argument");
-  if (params->saltcorr < 0 || params->saltcorr > 6)
-    return fail(ctx, AH_EINVAL, "ah_tm_sites: salt correction method %d is not supported (0-6)", params->saltcorr);
+  if (params->saltcorr < 0 || params->saltcorr > 7)
+    return fail(ctx, AH_EINVAL, "ah_tm_sites: salt correction method %d is not supported (0-7)", params->saltcorr);
   cudaSetDevice(ctx->device);
   return tm_sites(ctx, n, primers, sites, k, clamp, params, tm_out);
 }

@@ -260,7 +260,7 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
                          ah_plan** out) {
   if (!ctx || !b || !p || !prm || !out) return fail(ctx, AH_EINVAL, "ah_plan_create: NULL argument");
   if (prm->min_len > prm->max_len) return fail(ctx, AH_EINVAL, "ah_plan_create: min_len > max_len");
-  if (prm->tm.saltcorr < 0 || prm->tm.saltcorr > 6) return fail(ctx, AH_EINVAL, "ah_plan_create: bad salt method");
+  if (prm->tm.saltcorr < 0 || prm->tm.saltcorr > 7) return fail(ctx, AH_EINVAL, "ah_plan_create: bad salt method");
   *out = nullptr;
   cudaSetDevice(ctx->device);
   ah_plan* pl = new ah_plan();

@@ -84,6 +84,8 @@ constexpr double kInitH = 0.0, kInitS = 0.0;
 constexpr double kTermATH = 2.3, kTermATS = 4.1;
 constexpr double kTermGCH = 0.1, kTermGCS = -2.8;
 constexpr double kOneGCH = 0.0, kOneGCS = 0.0, kAllATH = 0.0, kAllATS = 0.0, k5TAH = 0.0, k5TAS = 0.0;
+// symmetry correction of a self-complementary duplex
+constexpr double kSymH = 0.0, kSymS = -1.4;
 
 // degenerate site Tm: largest mismatch budget, and the enumeration bounds
 constexpr int kMaxK = 15;
@@ -190,52 +192,91 @@ ah_status load_tables(ah_ctx* ctx) {
 
 // run constants computed once on the host
 struct TmRun {
-  double rlnk;       // R ln(C)
-  double ln_mon;     // ln of the monovalent-equivalent concentration (M)
-  double corr_const; // methods 1-4: Tm correction
+  double rlnk;        // R ln(C)
+  double ln_mon;      // ln of the monovalent-equivalent concentration (M)
+  double corr_const;  // methods 1-4: Tm correction
+  // methods 6 and 7: correction to 1/Tm, rc0 + rc1 f + rc2 / (2 (L - 1)) with f the G/C fraction
+  double rc0, rc1, rc2;
+  double sym_h, sym_s;  // self-complementary duplexes: the symmetry terms (else 0)
   int saltcorr;
-  int selfcomp;
-  int variants;      // 1: degenerate site Tm over the variants matching the site only
+  int variants;       // 1: degenerate site Tm over the variants matching the site only
 };
 
+// Free Mg2+ (M) beside dNTPs binding it one to one, association constant 3e4 per M (Owczarzy et al.
+// 2008): the positive root of Ka x^2 + (Ka (dNTP - Mg) + 1) x - Mg = 0.
+double free_magnesium(double mg, double dntps) {
+  if (!(dntps > 0.0)) return mg;
+  const double ka = 3e4, b = ka * (dntps - mg) + 1.0;
+  return (-b + std::sqrt(b * b + 4.0 * ka * mg)) / (2.0 * ka);
+}
+
 ah_status make_run(ah_ctx* ctx, const ah_tm_params* p, TmRun* r) {
+  if (p->variants != 0 && p->variants != 1) return fail(ctx, AH_EINVAL, "Tm: variants must be 0 or 1");
+  if (p->selfcomp != 0 && p->selfcomp != 1) return fail(ctx, AH_EINVAL, "Tm: selfcomp must be 0 or 1");
   double mon_mM = p->Na + p->K + p->Tris / 2.0;
-  if ((p->K + p->Mg + p->Tris + p->dNTPs) > 0 && p->dNTPs < p->Mg) mon_mM += 120.0 * std::sqrt(p->Mg - p->dNTPs);
+  // Na+-equivalent of Mg2+ (von Ahsen et al. 2001) for methods 1-6; method 7 models Mg2+ itself
+  if (p->saltcorr != 7 && (p->K + p->Mg + p->Tris + p->dNTPs) > 0 && p->dNTPs < p->Mg)
+    mon_mM += 120.0 * std::sqrt(p->Mg - p->dNTPs);
   const double mon = mon_mM * 1e-3;
-  if (p->saltcorr != 0 && !(mon > 0)) return fail(ctx, AH_EINVAL, "Tm: salt correction needs a positive cation concentration");
-  const double conc = (p->dnac1 - p->dnac2 / 2.0) * 1e-9;
+  const double mg = free_magnesium(p->Mg * 1e-3, p->dNTPs * 1e-3);
+  if (p->saltcorr >= 1 && p->saltcorr <= 6 && !(mon > 0))
+    return fail(ctx, AH_EINVAL, "Tm: salt correction needs a positive cation concentration");
+  if (p->saltcorr == 7 && !(mon > 0) && !(mg > 0))
+    return fail(ctx, AH_EINVAL, "Tm: salt method 7 needs monovalent ions or free Mg2+");
+  const double conc = (p->selfcomp ? p->dnac1 : p->dnac1 - p->dnac2 / 2.0) * 1e-9;
   if (!(conc > 0)) return fail(ctx, AH_EINVAL, "Tm: strand concentrations give C <= 0");
   r->rlnk = 1.987 * std::log(conc);
-  r->ln_mon = p->saltcorr ? std::log(mon) : 0.0;
-  if (p->variants != 0 && p->variants != 1) return fail(ctx, AH_EINVAL, "Tm: variants must be 0 or 1");
+  r->ln_mon = mon > 0 ? std::log(mon) : 0.0;
   r->saltcorr = p->saltcorr;
-  r->selfcomp = 0;
   r->variants = p->variants;
+  r->sym_h = p->selfcomp ? kSymH : 0.0;
+  r->sym_s = p->selfcomp ? kSymS : 0.0;
+  r->corr_const = r->rc0 = r->rc1 = r->rc2 = 0.0;
+  const double lm = r->ln_mon;
   switch (p->saltcorr) {
     case 1: r->corr_const = 16.6 * std::log10(mon); break;
     case 2: r->corr_const = 16.6 * std::log10(mon / (1.0 + 0.7 * mon)); break;
     case 3: r->corr_const = 12.5 * std::log10(mon); break;
     case 4: r->corr_const = 11.7 * std::log10(mon); break;
-    default: r->corr_const = 0.0;
+    case 6:  // Owczarzy et al. 2004
+      r->rc0 = -3.95e-5 * lm + 9.40e-6 * lm * lm;
+      r->rc1 = 4.29e-5 * lm;
+      break;
+    case 7: {  // Owczarzy et al. 2008: by the ratio sqrt([Mg2+]) / [Mon+]
+      if (mon > 0 && std::sqrt(mg) / mon < 0.22) {  // monovalent ions dominate: the 2004 form
+        r->rc0 = -3.95e-5 * lm + 9.40e-6 * lm * lm;
+        r->rc1 = 4.29e-5 * lm;
+        break;
+      }
+      double a = 3.92e-5, d = 1.42e-5, g = 8.31e-5;
+      if (mon > 0 && std::sqrt(mg) / mon < 6.0) {  // mixed: monovalent ions modify a, d, g
+        a *= 0.843 - 0.352 * std::sqrt(mon) * lm;
+        d *= 1.279 - 4.03e-3 * lm - 8.03e-3 * lm * lm;
+        g *= 0.486 - 0.258 * lm + 5.25e-3 * lm * lm * lm;
+      }
+      const double lg = std::log(mg);
+      r->rc0 = a - 9.11e-6 * lg;
+      r->rc1 = 6.26e-5 + d * lg;
+      r->rc2 = -4.82e-4 + 5.25e-4 * lg + g * lg * lg;
+      break;
+    }
+    default: break;
   }
   return AH_OK;
 }
 
 // Tm from the duplex sums (dH kcal/mol, dS cal/(K mol), before salt and concentration terms) and the
-// variant's G/C count: salt correction, then Tm = 1000 dH / (dS + R ln C) - 273.15
+// variant's G/C count: symmetry terms, salt correction, Tm = 1000 dH / (dS + R ln C) - 273.15
 __device__ __forceinline__ double tm_of_sums(double dh, double ds, int gc, int L, const TmRun& R) {
-  double corr = 0.0;
-  if (R.saltcorr == 5) {
-    ds += 0.368 * (double)(L - 1) * R.ln_mon;
-  } else if (R.saltcorr == 6) {
-    const double f = (double)gc / (double)L;
-    corr = (4.29 * f - 3.95) * 1e-5 * R.ln_mon + 9.40e-6 * R.ln_mon * R.ln_mon;
-  } else {
-    corr = R.corr_const;
-  }
+  dh += R.sym_h;
+  ds += R.sym_s;
+  if (R.saltcorr == 5) ds += 0.368 * (double)(L - 1) * R.ln_mon;
   double t = (1000.0 * dh) / (ds + R.rlnk) - 273.15;
-  if (R.saltcorr >= 1 && R.saltcorr <= 4) t += corr;
-  if (R.saltcorr == 6) t = 1.0 / (1.0 / (t + 273.15) + corr) - 273.15;
+  if (R.saltcorr >= 1 && R.saltcorr <= 4) t += R.corr_const;
+  if (R.saltcorr >= 6) {
+    const double corr = R.rc0 + R.rc1 * ((double)gc / (double)L) + R.rc2 / (2.0 * (double)(L - 1));
+    t = 1.0 / (1.0 / (t + 273.15) + corr) - 273.15;
+  }
   return t;
 }
 
@@ -525,7 +566,8 @@ __device__ ChainResult site_tm_chain(const SiteVariants& V, const TmRun& R, doub
   uint8_t back[32][4][kMaxK + 1], v[32];
   // constant part of D: salt (method 5) and R ln(C); methods 1-4 shift Tm by a constant
   const double S0 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
-  const double H0 = kInitH + kOneGCH, Sc = kInitS + kOneGCS;  // all-A/T and one-G/C terms are equal here
+  // all-A/T and one-G/C terms are equal here
+  const double H0 = kInitH + kOneGCH + R.sym_h, Sc = kInitS + kOneGCS + R.sym_s;
   const double shift = R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0;
   auto ratio = [&](int dh10, int ds10) { return 1000.0 * (0.1 * dh10 + H0) / (0.1 * ds10 + Sc + S0); };
   int dh10, ds10;

@@ -159,6 +159,7 @@ class TmParams:
     saltcorr: int = 5
     min_tm: Optional[float] = None   # None: annotate only, no filtering
     variants: int = 0     # degenerate Tm over 0: every concrete variant, 1: those matching the site
+    selfcomp: int = 0     # 1: the duplexes are self-complementary (symmetry term, C = dnac1)
 
 
 @dataclass

@@ -56,7 +56,9 @@ def test_primers_refused(env, fwd, rev, k, clamp):
 
 def test_tm_parameters_refused(env):
     ah, ctx, wl, batch = env
-    _refused(ah, ctx, ah.AH_EINVAL, ah.ah_tm_duplexes, ctx, ["ACGT"], ["TGCA"], ah.tm_params(saltcorr=7))
+    _refused(ah, ctx, ah.AH_EINVAL, ah.ah_tm_duplexes, ctx, ["ACGT"], ["TGCA"], ah.tm_params(saltcorr=8))
+    _refused(ah, ctx, ah.AH_EINVAL, ah.ah_tm_duplexes, ctx, ["ACGT"], ["TGCA"], ah.tm_params(Na=0, saltcorr=7))
+    _refused(ah, ctx, ah.AH_EINVAL, ah.ah_tm_duplexes, ctx, ["ACGT"], ["TGCA"], ah.tm_params(selfcomp=2))
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_tm_duplexes, ctx, ["ACGT"], ["TGCA"], ah.tm_params(dnac1=1, dnac2=4))
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_tm_duplexes, ctx, ["ACGT"], ["TGCA"], ah.tm_params(variants=2))
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_tm_duplexes, ctx, ["ACGT"], ["TGC"], ah.tm_params())   # lengths differ

@@ -61,8 +61,10 @@ def _random_case(seed):
                             fb=st.randint(0, 20), rb=st.randint(0, 20), trim=bool(st.randint(0, 1)))
     if st.randint(0, 1):
         wl.tm.min_tm = float(st.randint(-20, 40))
-    wl.tm.saltcorr = st.choice([5, 5, 5, 0, 1, 2, 3, 4, 6])
+    wl.tm.saltcorr = st.choice([5, 5, 5, 0, 1, 2, 3, 4, 6, 7, 7])
     wl.tm.Na = float(st.choice([50, 10, 200]))
+    wl.tm.Mg = float(st.choice([0, 0, 1.5, 3]))
+    wl.tm.dNTPs = float(st.choice([0, 0.8]))
     return wl
 
 
@@ -170,6 +172,49 @@ def test_tm_duplexes(engine):
     assert worst <= compare.TM_TOL
 
 
+# every salt method with the other cations and dNTPs; method 7 in its three regimes (monovalent
+# ions dominating, mixed, Mg2+ dominating) and with Mg2+ alone; self-complementary mode
+_TM_OPTION_CASES = [
+    dict(Na=50.0, Mg=1.5, dNTPs=0.8, K=10.0, Tris=20.0, saltcorr=5),
+    dict(Na=50.0, Mg=2.0, dNTPs=0.2, saltcorr=6),
+    dict(Na=100.0, K=50.0, Tris=10.0, saltcorr=1),
+    dict(Na=30.0, Mg=1.0, saltcorr=2),
+    dict(Na=200.0, Mg=0.0, saltcorr=7),
+    dict(Na=50.0, Mg=2.0, dNTPs=0.8, saltcorr=7),
+    dict(Na=10.0, Mg=3.0, saltcorr=7),
+    dict(Na=0.0, Mg=4.0, dNTPs=1.0, saltcorr=7),
+    dict(Na=50.0, saltcorr=5, selfcomp=1, dnac1=250.0),
+    dict(Na=50.0, Mg=2.0, saltcorr=7, selfcomp=1, dnac1=100.0),
+]
+
+
+@pytest.mark.parametrize("case", _TM_OPTION_CASES)
+def test_tm_duplex_options(engine, case):
+    """Duplex Tm under the remaining Tm_NN options: K+, Tris, Mg2+ and dNTPs with every salt method,
+    salt method 7 (Owczarzy et al. 2008) in each of its regimes, and self-complementary duplexes."""
+    from paper_2511_00170_gb300 import ah
+
+    st = synth.Stream(synth.make_key(4, 902, 0))
+    seqs, cseqs = [], []
+    for _ in range(3000):
+        L = st.randint(2, 32)
+        s = "".join(st.choice("ACGT") for _ in range(L))
+        c = [COMP[x] for x in s]
+        for _ in range(st.randint(0, 3)):
+            p = st.randint(0, L - 1)
+            c[p] = st.choice([b for b in "ACGT" if b != COMP[s[p]]])
+        seqs.append(s)
+        cseqs.append("".join(c))
+    got = ah.ah_tm_duplexes(engine.ctx, seqs, cseqs, ah.tm_params(**case))
+    tmp = synth.TmParams(**case)
+    for s, c, g in zip(seqs, cseqs, got):
+        r = oracle.tm_duplex(s, c, tmp)
+        if r is None:
+            assert math.isnan(g), (s, c)
+        else:
+            assert abs(g - r) <= compare.TM_TOL, (s, c, g, r)
+
+
 def test_pack_layout(engine):
     """Planes and invalid words against the layout in include/ah.h, read back from the device."""
     import torch
@@ -269,6 +314,18 @@ def test_degenerate_site_tm_small_sets_and_method6(engine):
     for method in (5, 6):
         got = ah.ah_tm_sites(engine.ctx, prims, sites, ah.tm_params(saltcorr=method), k=ks, clamp=clamps)
         _check_sites(got, prims, sites, ks, clamps, synth.TmParams(saltcorr=method))
+
+
+@pytest.mark.parametrize("case", [dict(Na=50.0, Mg=2.0, dNTPs=0.8, saltcorr=7), dict(Na=10.0, Mg=3.0, saltcorr=7),
+                                  dict(Na=50.0, saltcorr=5, selfcomp=1), dict(Na=50.0, Mg=1.5, saltcorr=4, selfcomp=1)])
+def test_degenerate_site_tm_options(engine, case):
+    """Degenerate sites under salt method 7 (enumerated: the correction depends on each variant's G/C
+    content) and in self-complementary mode (the chain method carries the symmetry term)."""
+    from paper_2511_00170_gb300 import ah
+
+    prims, sites, ks, clamps = _degenerate_sites(21 + case["saltcorr"], 24, 0, 8)
+    got = ah.ah_tm_sites(engine.ctx, prims, sites, ah.tm_params(**case), k=ks, clamp=clamps)
+    _check_sites(got, prims, sites, ks, clamps, synth.TmParams(**case))
 
 
 def test_degenerate_site_tm_work_bound(engine):

@@ -125,6 +125,64 @@ def test_salt_method5():
     assert all(a < b for a, b in zip(ts, ts[1:]))
 
 
+@pytest.mark.parametrize("seq", ["AGCTTGACCGTAGGCATTA", "GCGCGGCCGCATGC", "ATATTAAATTTATATAATAT"])
+@pytest.mark.parametrize("na", [10.0, 50.0, 200.0])
+def test_salt_method7_without_magnesium_is_method6(seq, na):
+    """Owczarzy et al. 2008 reduces to Owczarzy et al. 2004 (method 6) when no Mg2+ is present: the
+    Mg2+ / monovalent ratio is 0, below the 0.22 bound where monovalent ions dominate."""
+    cseq = "".join(COMP[c] for c in seq)
+    m6 = oracle.tm_duplex(seq, cseq, synth.TmParams(Na=na, saltcorr=6))
+    m7 = oracle.tm_duplex(seq, cseq, synth.TmParams(Na=na, saltcorr=7))
+    assert m6 is not None and abs(m6 - m7) < 1e-12
+
+
+@pytest.mark.parametrize("seq", ["AGCTTGACCGTAGGCATTA", "GCGCGGCCGCATGC"])
+def test_salt_method7_magnesium_dominated_ignores_monovalent(seq):
+    """At sqrt([Mg2+]) / [Mon+] >= 6 (Owczarzy et al. 2008) the correction depends on Mg2+ alone:
+    10 mM Mg2+ (sqrt 0.1 M^1/2) with 0 to 16 mM monovalent ions gives one Tm; 20 mM Na+ (ratio
+    5) falls in the mixed regime and differs."""
+    cseq = "".join(COMP[c] for c in seq)
+    ts = [oracle.tm_duplex(seq, cseq, synth.TmParams(Na=na, Mg=10.0, saltcorr=7)) for na in (0.0, 5.0, 10.0, 16.0)]
+    assert ts[0] is not None and max(ts) - min(ts) < 1e-12
+    mixed = oracle.tm_duplex(seq, cseq, synth.TmParams(Na=20.0, Mg=10.0, saltcorr=7))
+    assert abs(mixed - ts[0]) > 1e-6
+
+
+def test_salt_method7_tm_rises_with_magnesium():
+    """Tm of a 19-mer rises with Mg2+ over the PCR range 0.5-10 mM at 50 mM Na+ (Owczarzy et al. 2008)."""
+    seq = "AGCTTGACCGTAGGCATTA"
+    cseq = "".join(COMP[c] for c in seq)
+    ts = [oracle.tm_duplex(seq, cseq, synth.TmParams(Na=50.0, Mg=mg, saltcorr=7)) for mg in (0.5, 1.0, 2.0, 5.0, 10.0)]
+    assert all(a < b for a, b in zip(ts, ts[1:])), ts
+    # and without any cation the method is undefined
+    assert oracle.tm_duplex(seq, cseq, synth.TmParams(Na=0.0, Mg=0.0, saltcorr=7)) is None
+
+
+@pytest.mark.parametrize("mg,dntp", [(1.5, 0.8), (3.0, 0.2), (2.0, 2.0), (0.5, 4.0), (10.0, 1.0)])
+def test_free_magnesium_satisfies_mass_action(mg, dntp):
+    """Free Mg2+ beside dNTPs (Ka = 3e4 per M, one to one): Ka [Mg]free [dNTP]free = [Mg.dNTP], with
+    both free amounts non-negative and the bound amount at most the smaller total."""
+    x = oracle.free_mg(mg, dntp) * 1e-3
+    bound = mg * 1e-3 - x
+    dfree = dntp * 1e-3 - bound
+    assert 0.0 < x <= mg * 1e-3 and 0.0 <= bound <= min(mg, dntp) * 1e-3 + 1e-15 and dfree >= -1e-15
+    assert abs(3e4 * x * dfree - bound) <= 1e-9 * max(bound, 1e-12)
+    assert oracle.free_mg(mg, 0.0) == mg
+
+
+@pytest.mark.parametrize("seq", ["GCGCAATTGCGC", "ACGTACGT", "AGCTTAAGCT"])
+def test_self_complementary_duplex(seq):
+    """A self-complementary duplex (selfcomp) takes C = c1 and the symmetry entropy: its Tm equals the
+    ordinary Tm at strand concentration c1 exp(dS_sym / R), c2 = 0, with dS_sym = -1.4 cal/(K mol)."""
+    cseq = "".join(COMP[c] for c in seq)
+    assert "".join(COMP[c] for c in reversed(seq)) == seq
+    for salt in (0, 5, 6):
+        sc = oracle.tm_duplex(seq, cseq, synth.TmParams(dnac1=250.0, dnac2=0.0, saltcorr=salt, selfcomp=1))
+        eq = oracle.tm_duplex(seq, cseq, synth.TmParams(dnac1=250.0 * math.exp(-1.4 / 1.987), dnac2=0.0,
+                                                        saltcorr=salt))
+        assert abs(sc - eq) < 1e-9, (salt, sc, eq)
+
+
 def test_concentration_term():
     seq = "AGCTTGACCGTAGGCATTA"
     cseq = "".join(COMP[c] for c in seq)
