@@ -242,6 +242,7 @@ void launch_pair_walk(cudaStream_t s, bool emit, const ah_hit* hits, uint64_t ca
                       const uint64_t* pair_off, const uint8_t* plen, uint32_t min_len, uint32_t max_len, uint32_t mask,
                       uint32_t* counts, const uint64_t* out_off, ah_amplicon* out, uint64_t out_cap,
                       uint32_t* overflow);
+constexpr size_t kTmRunBytes = 128;  // room for the Tm run constants a plan keeps
 ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, size_t run_size);
 void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit_cap, const uint64_t* d_nhits,
                const uint8_t* pk, int clamp, uint32_t* status,

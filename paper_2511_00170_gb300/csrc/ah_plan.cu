@@ -47,7 +47,7 @@ struct ah_plan {
   uint64_t* field_off = nullptr;
   uint32_t* ctr = nullptr;      // [0] fullest tile, [1] overflow bits, [2..3] persistent work counter
   uint64_t* h_out = nullptr;    // pinned: counters read back after a run
-  unsigned char tm_run[64];
+  alignas(8) unsigned char tm_run[ah::kTmRunBytes];
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   // The scan node is bracketed by two event-record nodes.  Timed replays use a ring of executable

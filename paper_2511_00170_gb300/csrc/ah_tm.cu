@@ -790,6 +790,8 @@ ah_status tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const ch
   return check_status(ctx);
 }
 
+static_assert(sizeof(TmRun) <= kTmRunBytes, "Tm run constants exceed a plan's buffer");
+
 ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, size_t run_size) {
   ah_status st;
   if ((st = load_tables(ctx))) return st;
