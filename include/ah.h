@@ -164,6 +164,22 @@ typedef struct {
 ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, const uint64_t* lens,
                         const uint32_t* genome_ids, ah_batch** out);
 
+/* FASTA input (Abstract: the pipeline packs FASTA into 2-bit batches).  `text` holds n_bytes of
+ * FASTA, in host or device memory: each record is a header line starting with '>' and the sequence
+ * lines up to the next header.  It is parsed on the device (host text is copied there first): line
+ * breaks and '\r', ' ', '\t' in sequence lines are dropped, every other byte is a base (non-ACGT
+ * bytes become invalid bases as in ah_pack_batch), bytes before the first header are ignored, and a
+ * record may be empty.  Returns the packed batch (genome_ids as in ah_pack_batch, may be NULL) and,
+ * if names_out is not NULL, the records' header lines (without '>' and a trailing '\r').
+ * AH_EINVAL when no line starts with '>'.  Synchronises the stream. */
+typedef struct ah_fasta ah_fasta;
+ah_status ah_fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint32_t* genome_ids,
+                        ah_batch** batch_out, ah_fasta** names_out);
+uint32_t ah_fasta_count(const ah_fasta* f);
+/* header line of record i (owned by f), NULL past the end */
+const char* ah_fasta_name(const ah_fasta* f, uint32_t i);
+void ah_fasta_free(ah_fasta* f);
+
 /* Pack records that are already in device memory: d_seq holds all records back to back and
  * h_offsets (host, n_rec+1 entries) gives record r as d_seq[h_offsets[r], h_offsets[r+1]).
  * Asynchronous; d_seq must stay valid until the stream reaches this work. */

@@ -158,6 +158,20 @@ def tm_duplex(seq: str, cseq: str, tm) -> Optional[float]:
     return t if d.value else None
 
 
+def parse_fasta(text: bytes) -> Tuple[List[str], List[bytes]]:
+    """FASTA records, line by line (Abstract: the input is FASTA): a line starting with '>' opens a
+    record named by the rest of the line (a trailing '\\r' dropped); every other line adds its bytes
+    except '\\r', ' ' and '\\t' to the open record; lines before the first header are ignored."""
+    names, seqs = [], []
+    for line in text.split(b"\n"):
+        if line.startswith(b">"):
+            names.append(line[1:].rstrip(b"\r").decode("latin-1"))
+            seqs.append(bytearray())
+        elif seqs:
+            seqs[-1] += bytes(c for c in line if c not in b"\r \t")
+    return names, [bytes(s) for s in seqs]
+
+
 def free_mg(mg_mM: float, dntps_mM: float) -> float:
     """Free Mg2+ (mM) beside dNTPs that bind it one to one (salt method 7's input)."""
     return _get().or_free_mg(float(mg_mM), float(dntps_mM))

@@ -103,6 +103,10 @@ SIGNATURES = {
     "ah_ctx_set_scan_config": (_I32, [_VP, _I32, _I32, _I32, _I32]),
     "ah_pack_batch": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
     "ah_pack_batch_device": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
+    "ah_fasta_pack": (_I32, [_VP, _VP, _U64, _VP, _PVP, _PVP]),
+    "ah_fasta_count": (_U32, [_VP]),
+    "ah_fasta_name": (ctypes.c_char_p, [_VP, _U32]),
+    "ah_fasta_free": (None, [_VP]),
     "ah_batch_export": (_I32, [_VP, _VP, ctypes.POINTER(ctypes.c_uint64), _VP, _VP]),
     "ah_batch_import": (_I32, [_VP, _VP, _VP, _U64, _VP, _VP]),
     "ah_batch_view_get": (_I32, [_VP, ctypes.POINTER(ah_batch_view)]),
@@ -247,6 +251,28 @@ def ah_pack_batch_device(ctx, d_seq: int, offsets: np.ndarray, genome_ids: Optio
     _check(load().ah_pack_batch_device(ctx, len(offsets) - 1, d_seq, offsets.ctypes.data,
                                        None if gid is None else gid.ctypes.data, ctypes.byref(out)), ctx)
     return out
+
+
+def ah_fasta_pack(ctx, text, genome_ids: Optional[np.ndarray] = None, n_bytes: Optional[int] = None):
+    """FASTA text (bytes / numpy uint8 on the host, or a device address with n_bytes) parsed and packed
+    on the device.  Returns (batch, names)."""
+    keep = None
+    if isinstance(text, int):
+        addr, n = text, int(n_bytes)
+    else:
+        keep = np.frombuffer(text, dtype=np.uint8) if isinstance(text, (bytes, bytearray)) else \
+            np.ascontiguousarray(text, dtype=np.uint8)
+        addr, n = keep.ctypes.data, len(keep)
+    gid = None if genome_ids is None else np.ascontiguousarray(genome_ids, dtype=np.uint32)
+    out, names = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().ah_fasta_pack(ctx, addr, n, None if gid is None else gid.ctypes.data, ctypes.byref(out),
+                                ctypes.byref(names)), ctx)
+    L = load()
+    try:
+        nm = [L.ah_fasta_name(names, i).decode("latin-1") for i in range(L.ah_fasta_count(names))]
+    finally:
+        L.ah_fasta_free(names)
+    return out, nm
 
 
 def ah_batch_export(batch, planes: Optional[np.ndarray] = None, groups: Optional[np.ndarray] = None,

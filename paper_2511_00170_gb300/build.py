@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libah.so")
-SOURCES = ["ah_api.cu", "ah_util.cu", "ah_scan.cu", "ah_pair.cu", "ah_tm.cu", "ah_extract.cu", "ah_plan.cu", "ah_jit.cpp", "ah_serve.cpp"]
+SOURCES = ["ah_api.cu", "ah_util.cu", "ah_scan.cu", "ah_pair.cu", "ah_tm.cu", "ah_extract.cu", "ah_plan.cu", "ah_fasta.cu", "ah_jit.cpp",
+           "ah_serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

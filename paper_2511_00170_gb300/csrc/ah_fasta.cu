@@ -1,0 +1,316 @@
+// FASTA input on the device (Abstract and Section "Implementations": the pipeline packs FASTA into
+// 2-bit batches).  Raw FASTA text, a '>' header line per record followed by sequence lines, is
+// parsed where it lies in HBM: a line-state pass per 4 KiB tile, the tiles' entry states chained on
+// the host, then a counting pass and an emitting pass that compact the sequence bytes (line breaks
+// and blanks dropped) and record every header.  The compacted sequences are packed like any other
+// device source.
+//
+// Line state: LS at the start of a line, H inside a header line, S inside a sequence line.  A line
+// whose first byte is '>' is a header and starts a record; '\n' ends a line; '\r', ' ' and '\t' in a
+// sequence line are not bases.  Bytes before the first header belong to no record.
+#include <algorithm>
+#include <cstring>
+
+#include "ah_internal.h"
+
+struct ah_fasta {
+  std::vector<std::string> names;  // header lines without '>' and trailing '\r'
+};
+
+namespace ah {
+namespace {
+
+constexpr int kFaThreads = 256, kFaBytes = 16, kFaTile = kFaThreads * kFaBytes;
+enum : uint32_t { FS_LS = 0, FS_H = 1, FS_S = 2 };
+// a transfer function over the three states: bits 2s..2s+1 hold the state after, from state s
+constexpr uint32_t kIdentity = FS_LS | (FS_H << 2) | (FS_S << 4);
+
+__device__ __forceinline__ uint32_t apply(uint32_t f, uint32_t s) { return (f >> (2 * s)) & 3u; }
+// first a, then b
+__device__ __forceinline__ uint32_t compose(uint32_t a, uint32_t b) {
+  return apply(b, apply(a, FS_LS)) | (apply(b, apply(a, FS_H)) << 2) | (apply(b, apply(a, FS_S)) << 4);
+}
+__device__ __forceinline__ uint32_t step(uint32_t s, uint8_t c) {
+  if (c == '\n') return FS_LS;
+  if (s == FS_LS) return c == '>' ? FS_H : FS_S;
+  return s;
+}
+__device__ __forceinline__ bool is_blank(uint8_t c) { return c == '\r' || c == ' ' || c == '\t'; }
+
+// this thread's bytes [p0, p1)
+__device__ __forceinline__ void thread_span(uint64_t n, uint64_t* p0, uint64_t* p1) {
+  *p0 = (uint64_t)blockIdx.x * kFaTile + (uint64_t)threadIdx.x * kFaBytes;
+  *p1 = min(n, *p0 + kFaBytes);
+  if (*p0 > n) *p0 = n;
+}
+
+__device__ uint32_t thread_function(const uint8_t* __restrict__ t, uint64_t p0, uint64_t p1) {
+  uint32_t a = FS_LS, b = FS_H, c = FS_S;
+  for (uint64_t p = p0; p < p1; ++p) {
+    const uint8_t x = t[p];
+    a = step(a, x), b = step(b, x), c = step(c, x);
+  }
+  return a | (b << 2) | (c << 4);
+}
+
+// exclusive composition of the block's thread functions (thread order) and the block's total
+__device__ uint32_t block_exclusive_function(uint32_t f, uint32_t* total) {
+  __shared__ uint32_t warp_f[kFaThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = f;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t other = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc = compose(other, inc);
+  }
+  uint32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane == 0) exc = kIdentity;
+  if (lane == 31) warp_f[warp] = inc;
+  __syncthreads();
+  uint32_t before = kIdentity;
+  for (int w = 0; w < warp; ++w) before = compose(before, warp_f[w]);
+  if (total) {
+    uint32_t all = kIdentity;
+    for (int w = 0; w < kFaThreads / 32; ++w) all = compose(all, warp_f[w]);
+    *total = all;
+  }
+  __syncthreads();
+  return compose(before, exc);
+}
+
+// exclusive sums of two per-thread counts over the block, and their totals
+__device__ void block_exclusive_sums(uint32_t a, uint32_t b, uint32_t* ea, uint32_t* eb, uint32_t* ta, uint32_t* tb) {
+  __shared__ uint32_t wa[kFaThreads / 32], wb[kFaThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t xa = __shfl_up_sync(0xffffffffu, ia, o), xb = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) ia += xa, ib += xb;
+  }
+  if (lane == 31) wa[warp] = ia, wb[warp] = ib;
+  __syncthreads();
+  uint32_t ba = 0, bb = 0, sa = 0, sb = 0;
+  for (int w = 0; w < kFaThreads / 32; ++w) {
+    if (w < warp) ba += wa[w], bb += wb[w];
+    sa += wa[w], sb += wb[w];
+  }
+  __syncthreads();
+  *ea = ba + ia - a;
+  *eb = bb + ib - b;
+  *ta = sa;
+  *tb = sb;
+}
+
+// pass 1: each tile's transfer function
+__global__ void __launch_bounds__(kFaThreads) k_fa_tiles(const uint8_t* __restrict__ t, uint64_t n,
+                                                         uint8_t* __restrict__ tile_f) {
+  uint64_t p0, p1;
+  thread_span(n, &p0, &p1);
+  uint32_t total;
+  block_exclusive_function(thread_function(t, p0, p1), &total);
+  if (threadIdx.x == 0) tile_f[blockIdx.x] = (uint8_t)total;
+}
+
+// passes 2 and 3: classify the tile's bytes from its entry state.  emit = false: per-tile counts of
+// sequence bytes and headers.  emit = true: sequence bytes to out[rank], and per header (record r)
+// hdr_pos[r] (first byte after '>'), seq_rank[r] (sequence bytes before it) and hdr_end[r] (its '\n').
+template <bool emit>
+__global__ void __launch_bounds__(kFaThreads) k_fa_pass(const uint8_t* __restrict__ t, uint64_t n,
+                                                        const uint8_t* __restrict__ tile_entry,
+                                                        uint32_t* __restrict__ tile_seq, uint32_t* __restrict__ tile_hdr,
+                                                        const uint64_t* __restrict__ seq_base,
+                                                        const uint64_t* __restrict__ hdr_base, uint8_t* __restrict__ out,
+                                                        uint64_t* __restrict__ hdr_pos, uint64_t* __restrict__ hdr_end,
+                                                        uint64_t* __restrict__ seq_rank) {
+  uint64_t p0, p1;
+  thread_span(n, &p0, &p1);
+  const uint32_t before = block_exclusive_function(thread_function(t, p0, p1), nullptr);
+  const uint32_t s0 = apply(before, tile_entry[blockIdx.x]);
+  uint32_t n_seq = 0, n_hdr = 0, s = s0;
+  for (uint64_t p = p0; p < p1; ++p) {
+    const uint8_t x = t[p];
+    if (s == FS_LS && x == '>') ++n_hdr;
+    else if ((s == FS_S || s == FS_LS) && x != '\n' && !is_blank(x)) ++n_seq;
+    s = step(s, x);
+  }
+  uint32_t e_seq, e_hdr, t_seq, t_hdr;
+  block_exclusive_sums(n_seq, n_hdr, &e_seq, &e_hdr, &t_seq, &t_hdr);
+  if (!emit) {
+    if (threadIdx.x == 0) tile_seq[blockIdx.x] = t_seq, tile_hdr[blockIdx.x] = t_hdr;
+    return;
+  }
+  uint64_t rank = seq_base[blockIdx.x] + e_seq;
+  uint64_t rec = hdr_base[blockIdx.x] + e_hdr;  // headers started before this byte
+  s = s0;
+  for (uint64_t p = p0; p < p1; ++p) {
+    const uint8_t x = t[p];
+    if (s == FS_LS && x == '>') {
+      hdr_pos[rec] = p + 1;
+      seq_rank[rec] = rank;
+      ++rec;
+    } else if (s == FS_H && x == '\n') {
+      hdr_end[rec - 1] = p;  // rec >= 1: a header line is open
+    } else if ((s == FS_S || s == FS_LS) && x != '\n' && !is_blank(x)) {
+      out[rank++] = x;
+    }
+    s = step(s, x);
+  }
+}
+
+// names of records [0, n_rec) into one buffer: name r is text[hdr_pos[r], hdr_pos[r] + len[r])
+__global__ void k_fa_names(const uint8_t* __restrict__ t, const uint64_t* __restrict__ hdr_pos,
+                           const uint64_t* __restrict__ name_off, uint32_t n_rec, uint8_t* __restrict__ names) {
+  const uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= n_rec) return;
+  const uint64_t len = name_off[r + 1] - name_off[r];
+  for (uint64_t i = threadIdx.x & 31; i < len; i += 32) names[name_off[r] + i] = t[hdr_pos[r] + i];
+}
+
+uint32_t host_apply(uint32_t f, uint32_t s) { return (f >> (2 * s)) & 3u; }
+
+}  // namespace
+}  // namespace ah
+
+using namespace ah;
+
+extern "C" {
+
+ah_status ah_fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint32_t* genome_ids,
+                        ah_batch** batch_out, ah_fasta** names_out) {
+  if (!ctx || !text || !batch_out || n_bytes == 0) return fail(ctx, AH_EINVAL, "ah_fasta_pack: bad arguments");
+  *batch_out = nullptr;
+  if (names_out) *names_out = nullptr;
+  cudaSetDevice(ctx->device);
+  cudaPointerAttributes pa;
+  const bool on_device = cudaPointerGetAttributes(&pa, text) == cudaSuccess &&
+                         (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  ah_status st = AH_OK;
+  const uint8_t* t = (const uint8_t*)text;
+  uint8_t* staged = nullptr;
+  if (!on_device) {
+    if ((st = dalloc(ctx, &staged, n_bytes))) return st;
+    AH_CUDA(ctx, cudaMemcpyAsync(staged, text, n_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    t = staged;
+  }
+  const uint64_t n_tiles = (n_bytes + kFaTile - 1) / kFaTile;
+  uint8_t *tile_f = nullptr, *tile_entry = nullptr, *compact = nullptr;
+  uint32_t *tile_seq = nullptr, *tile_hdr = nullptr;
+  uint64_t *seq_base = nullptr, *hdr_base = nullptr, *hdr_pos = nullptr, *hdr_end = nullptr, *seq_rank = nullptr;
+  std::vector<uint8_t> h_f(n_tiles), h_entry(n_tiles);
+  uint64_t total_seq = 0, total_hdr = 0;
+  auto cleanup = [&] {
+    for (void* p : {(void*)staged, (void*)tile_f, (void*)tile_entry, (void*)compact, (void*)tile_seq,
+                    (void*)tile_hdr, (void*)seq_base, (void*)hdr_base, (void*)hdr_pos, (void*)hdr_end, (void*)seq_rank})
+      dfree(ctx, p);
+  };
+  do {
+    if ((st = dalloc(ctx, &tile_f, n_tiles)) || (st = dalloc(ctx, &tile_entry, n_tiles)) ||
+        (st = dalloc(ctx, &tile_seq, n_tiles)) || (st = dalloc(ctx, &tile_hdr, n_tiles)) ||
+        (st = dalloc(ctx, &seq_base, n_tiles + 1)) || (st = dalloc(ctx, &hdr_base, n_tiles + 1)))
+      break;
+    // pass 1, then the tiles' entry states chained on the host (one byte per 4 KiB)
+    k_fa_tiles<<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, tile_f);
+    launched(ctx);
+    if (cudaMemcpyAsync(h_f.data(), tile_f, n_tiles, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+      st = fail(ctx, AH_ECUDA, "ah_fasta_pack: tile pass failed");
+      break;
+    }
+    uint32_t s = FS_LS;
+    for (uint64_t i = 0; i < n_tiles; ++i) h_entry[i] = (uint8_t)s, s = host_apply(h_f[i], s);
+    if (cudaMemcpyAsync(tile_entry, h_entry.data(), n_tiles, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+      st = fail(ctx, AH_ECUDA, "ah_fasta_pack: entry upload failed");
+      break;
+    }
+    // pass 2: counts per tile, then their exclusive sums
+    k_fa_pass<false><<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, tile_entry, tile_seq, tile_hdr,
+                                                                        nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                        nullptr);
+    launched(ctx);
+    if ((st = exclusive_scan_u32(ctx, tile_seq, seq_base, n_tiles)) ||
+        (st = exclusive_scan_u32(ctx, tile_hdr, hdr_base, n_tiles)) || (st = read_u64(ctx, seq_base + n_tiles, &total_seq)) ||
+        (st = read_u64(ctx, hdr_base + n_tiles, &total_hdr)))
+      break;
+    if (total_hdr == 0) {
+      st = fail(ctx, AH_EINVAL, "ah_fasta_pack: no record (no line starts with '>')");
+      break;
+    }
+    if (total_hdr > 0xffffffffull) {
+      st = fail(ctx, AH_EINVAL, "ah_fasta_pack: more than 2^32 - 1 records");
+      break;
+    }
+    if ((st = dalloc(ctx, &compact, total_seq + 16)) || (st = dalloc(ctx, &hdr_pos, total_hdr)) ||
+        (st = dalloc(ctx, &hdr_end, total_hdr)) || (st = dalloc(ctx, &seq_rank, total_hdr + 1)))
+      break;
+    // a header line that runs to the end of the text ends there
+    std::vector<uint64_t> fill(total_hdr, n_bytes);
+    AH_CUDA(ctx, cudaMemcpyAsync(hdr_end, fill.data(), total_hdr * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
+    // pass 3: compacted sequence bytes and the headers
+    k_fa_pass<true><<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, tile_entry, nullptr, nullptr,
+                                                                       seq_base, hdr_base, compact, hdr_pos, hdr_end,
+                                                                       seq_rank);
+    launched(ctx);
+    std::vector<uint64_t> h_pos(total_hdr), h_end(total_hdr), h_rank(total_hdr + 1);
+    AH_CUDA(ctx, cudaMemcpyAsync(h_pos.data(), hdr_pos, total_hdr * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    AH_CUDA(ctx, cudaMemcpyAsync(h_end.data(), hdr_end, total_hdr * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    AH_CUDA(ctx, cudaMemcpyAsync(h_rank.data(), seq_rank, total_hdr * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    h_rank[total_hdr] = total_seq;
+    const uint32_t n_rec = (uint32_t)total_hdr;
+    // records: sequence offsets relative to the first record's first base
+    std::vector<uint64_t> offs(n_rec + 1);
+    for (uint32_t r = 0; r <= n_rec; ++r) offs[r] = h_rank[r] - h_rank[0];
+    st = ah_pack_batch_device(ctx, n_rec, compact + h_rank[0], offs.data(), genome_ids, batch_out);
+    if (st) break;
+    if (names_out) {
+      ah_fasta* f = new ah_fasta();
+      f->names.resize(n_rec);
+      std::vector<uint64_t> name_off(n_rec + 1, 0);
+      for (uint32_t r = 0; r < n_rec; ++r) name_off[r + 1] = name_off[r] + (h_end[r] - h_pos[r]);
+      std::vector<char> all(name_off[n_rec] + 1);
+      if (on_device) {
+        uint64_t* d_off = nullptr;
+        uint8_t* d_names = nullptr;
+        st = dalloc(ctx, &d_off, n_rec + 1);
+        if (!st) st = dalloc(ctx, &d_names, name_off[n_rec] + 1);
+        if (!st) {
+          cudaMemcpyAsync(d_off, name_off.data(), (n_rec + 1) * 8, cudaMemcpyHostToDevice, ctx->stream);
+          k_fa_names<<<(n_rec + 7) / 8, 256, 0, ctx->stream>>>(t, hdr_pos, d_off, n_rec, d_names);
+          launched(ctx);
+          cudaMemcpyAsync(all.data(), d_names, name_off[n_rec], cudaMemcpyDeviceToHost, ctx->stream);
+          if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = fail(ctx, AH_ECUDA, "ah_fasta_pack: names");
+        }
+        dfree(ctx, d_off);
+        dfree(ctx, d_names);
+      } else {
+        for (uint32_t r = 0; r < n_rec; ++r) memcpy(all.data() + name_off[r], text + h_pos[r], h_end[r] - h_pos[r]);
+      }
+      for (uint32_t r = 0; r < n_rec && !st; ++r) {
+        std::string nm(all.data() + name_off[r], name_off[r + 1] - name_off[r]);
+        while (!nm.empty() && nm.back() == '\r') nm.pop_back();
+        f->names[r] = std::move(nm);
+      }
+      if (st) {
+        delete f;
+        ah_batch_free(*batch_out);
+        *batch_out = nullptr;
+        break;
+      }
+      *names_out = f;
+    }
+  } while (false);
+  cleanup();
+  return st;
+}
+
+uint32_t ah_fasta_count(const ah_fasta* f) { return f ? (uint32_t)f->names.size() : 0; }
+
+const char* ah_fasta_name(const ah_fasta* f, uint32_t i) {
+  return f && i < f->names.size() ? f->names[i].c_str() : nullptr;
+}
+
+void ah_fasta_free(ah_fasta* f) { delete f; }
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+"""FASTA input parsed and packed on the device (ah_fasta_pack) against the oracle's line-by-line
+parser: record names, and packed planes and invalid words identical to packing the oracle's record
+sequences (needs a GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ah_ctx():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2511_00170_gb300 import ah
+
+    ctx = ah.ah_ctx_create(0)
+    yield ah, ctx
+    ah.ah_ctx_destroy(ctx)
+
+
+def _random_fasta(seed: int, n_records: int, crlf: bool, junk: bool) -> bytes:
+    st = synth.Stream(synth.make_key(seed, 4321, 0))
+    nl = b"\r\n" if crlf else b"\n"
+    out = bytearray()
+    if junk:
+        out += b"; a comment line before the first record" + nl + b"ACGT" + nl
+    for r in range(n_records):
+        name_len = st.choice([5, 30, 200, 5000])   # 5000: a header longer than a 4 KiB tile
+        name = "rec%d " % r + "".join(st.choice("abcXYZ0123 _|=.") for _ in range(name_len))
+        out += b">" + name.encode() + nl
+        L = st.choice([0, 1, 50, 999, 10000, 70000])
+        seq = "".join(st.choice("ACGTACGTACGTacgtNnRY") for _ in range(L))
+        width = st.choice([60, 61, 80, 10 ** 9])   # 10**9: one line per record
+        for i in range(0, L, width):
+            line = seq[i:i + width]
+            if st.randint(0, 20) == 0:
+                line = line[: len(line) // 2] + " \t" + line[len(line) // 2:]
+            out += line.encode() + nl
+        if st.randint(0, 5) == 0:
+            out += nl   # an empty line
+    if out.endswith(nl) and st.randint(0, 1):
+        out = out[: -len(nl)]   # no final line break
+    return bytes(out)
+
+
+def _batch_bytes(ah, batch):
+    planes, groups, words = ah.ah_batch_export(batch)
+    v = ah.ah_batch_view_get(batch)
+    return planes.tobytes(), groups.tobytes(), words.tobytes(), v["n_records"], v["n_bases"]
+
+
+@pytest.mark.parametrize("seed,n_records,crlf,junk,on_device",
+                         [(1, 1, False, False, False), (2, 7, False, True, False), (3, 40, True, False, False),
+                          (4, 25, False, False, True), (5, 60, True, True, True), (6, 3, False, False, True)])
+def test_fasta_pack_matches_oracle(ah_ctx, seed, n_records, crlf, junk, on_device):
+    import torch
+
+    ah, ctx = ah_ctx
+    text = _random_fasta(seed, n_records, crlf, junk)
+    names, seqs = oracle.parse_fasta(text)
+    assert len(names) == n_records
+    if on_device:
+        d = torch.frombuffer(bytearray(text), dtype=torch.uint8).cuda()
+        batch, got_names = ah.ah_fasta_pack(ctx, d.data_ptr(), n_bytes=len(text))
+    else:
+        batch, got_names = ah.ah_fasta_pack(ctx, text)
+    lens = np.array([len(s) for s in seqs], dtype=np.uint64)
+    ref = ah.ah_pack_batch(ctx, np.frombuffer(b"".join(seqs) or b"\0", dtype=np.uint8),
+                           np.concatenate([[0], np.cumsum(lens)]).astype(np.int64))
+    try:
+        assert got_names == names
+        assert _batch_bytes(ah, batch) == _batch_bytes(ah, ref)
+    finally:
+        ah.ah_batch_free(batch)
+        ah.ah_batch_free(ref)
+
+
+def test_fasta_pack_refuses_text_without_records(ah_ctx):
+    ah, ctx = ah_ctx
+    with pytest.raises(ah.AhError) as e:
+        ah.ah_fasta_pack(ctx, b"ACGT\nACGT\n")
+    assert e.value.status == ah.AH_EINVAL
+    batch, names = ah.ah_fasta_pack(ctx, b">only a header")   # one empty record
+    try:
+        assert names == ["only a header"] and ah.ah_batch_view_get(batch)["n_bases"] == 0
+    finally:
+        ah.ah_batch_free(batch)
+
+
+def test_fasta_pipeline_equals_direct_packing(ah_ctx):
+    """The whole path on a batch packed from FASTA gives the oracle's sites and amplicons."""
+    from paper_2511_00170_gb300.pipeline import Engine, Params
+    from tests import compare
+
+    wl = synth.random_small(31, n_records=6, len_lo=500, len_hi=20000, n_pairs=2, plant=3)
+    lines = []
+    for r in range(wl.n_records):
+        s = wl.seq[wl.offsets[r]:wl.offsets[r + 1]].tobytes()
+        lines.append(b">genome_%d some description" % r)
+        lines += [s[i:i + 60] for i in range(0, len(s), 60)]
+    text = b"\n".join(lines) + b"\n"
+    eng = Engine(0)
+    try:
+        from paper_2511_00170_gb300 import ah
+
+        batch, names = ah.ah_fasta_pack(eng.ctx, text)
+        assert names == ["genome_%d some description" % r for r in range(wl.n_records)]
+        out = eng.step(batch, Params.from_workload(wl))
+        ah.ah_batch_free(batch)
+    finally:
+        eng.close()
+    ref = oracle.run(wl)
+    compare.assert_same_hits(out, ref)
+    compare.assert_same_amplicons(out, ref, filtered=wl.tm.min_tm is not None)
+    compare.assert_same_sequences(out, ref)
