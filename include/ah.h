@@ -373,6 +373,21 @@ ah_status ah_tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const
 ah_status ah_extract_barcodes(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h,
                               ah_amplicons* a, int trim, uint32_t fb_len, uint32_t rb_len);
 
+/* FASTA output (Supplementary "Headers and outputs"), host code over host copies of the results
+ * (ah_amplicons_copy, ah_amplicons_seq_copy): per amplicon a header line
+ *   >{id}.source={source}.coordinates={start+1}-{end}.Tm={tm}.orientation={FR|RF|FF|RR}
+ *    .fprimer={forward primer's site}.rprimer={reverse primer's site}[.fb={fb}.rb={rb}]
+ * (one line, fields joined by '.') and the amplicon sequence on the next.  id is the record's header
+ * line up to its first blank (record_names[record], e.g. from ah_fasta_name); .source= is omitted
+ * when record_sources is NULL or its entry is; coordinates are 1-based and inclusive on the top
+ * strand, primer sites included; Tm has two decimals, NA when undefined; for RF the forward
+ * primer's site is site j; .fb/.rb only when barcodes is nonzero.  Writes the text to out when it
+ * fits out_cap (AH_EOVERFLOW otherwise) and its length to *out_len; out = NULL only measures.
+ * AH_EINVAL for a record index >= n_records. */
+ah_status ah_amplicons_fasta(uint64_t n_amps, const ah_amplicon* amps, const char* arena, const uint64_t* field_off,
+                             uint32_t n_records, const char* const* record_names, const char* const* record_sources,
+                             int barcodes, char* out, uint64_t out_cap, uint64_t* out_len);
+
 ah_status ah_amplicons_count(const ah_amplicons* a, uint64_t* n);
 ah_status ah_amplicons_copy(const ah_amplicons* a, ah_amplicon* host_out, uint64_t cap);
 /* Bytes in the arena written by ah_extract_barcodes (0 before). */

@@ -172,6 +172,32 @@ def parse_fasta(text: bytes) -> Tuple[List[str], List[bytes]]:
     return names, [bytes(s) for s in seqs]
 
 
+def amplicon_fasta(records, names: Sequence[str], sources: Optional[Sequence[str]], barcodes: bool) -> bytes:
+    """FASTA text of amplicons with the headers of Supplementary "Headers and outputs": records are
+    (record, start, end, orient, tm, (amplicon, fb, rb, site i, site j)); the id is the record name
+    up to its first blank; coordinates 1-based inclusive; Tm to two decimals (NA if undefined); the
+    forward primer's site is site j for RF, site i otherwise; barcodes only when requested."""
+    out = []
+    for rec, start, end, orient, tm, f in records:
+        name = names[rec]
+        for i, ch in enumerate(name):
+            if ch in " \t":
+                name = name[:i]
+                break
+        h = ">" + name
+        if sources is not None and sources[rec] is not None:
+            h += ".source=" + sources[rec]
+        h += ".coordinates=%d-%d" % (start + 1, end)
+        h += ".Tm=" + ("NA" if tm != tm else "%.2f" % tm)
+        h += ".orientation=" + ORIENT_NAMES[orient]
+        fp, rp = (f[4], f[3]) if orient == 1 else (f[3], f[4])
+        h += ".fprimer=" + fp.decode("latin-1") + ".rprimer=" + rp.decode("latin-1")
+        if barcodes:
+            h += ".fb=" + f[1].decode("latin-1") + ".rb=" + f[2].decode("latin-1")
+        out.append(h.encode("latin-1") + b"\n" + f[0] + b"\n")
+    return b"".join(out)
+
+
 def free_mg(mg_mM: float, dntps_mM: float) -> float:
     """Free Mg2+ (mM) beside dNTPs that bind it one to one (salt method 7's input)."""
     return _get().or_free_mg(float(mg_mM), float(dntps_mM))

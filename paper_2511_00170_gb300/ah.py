@@ -107,6 +107,8 @@ SIGNATURES = {
     "ah_fasta_count": (_U32, [_VP]),
     "ah_fasta_name": (ctypes.c_char_p, [_VP, _U32]),
     "ah_fasta_free": (None, [_VP]),
+    "ah_amplicons_fasta": (_I32, [_U64, _VP, _VP, _VP, _U32, _VP, _VP, ctypes.c_int, _VP, _U64,
+                                  ctypes.POINTER(ctypes.c_uint64)]),
     "ah_batch_export": (_I32, [_VP, _VP, ctypes.POINTER(ctypes.c_uint64), _VP, _VP]),
     "ah_batch_import": (_I32, [_VP, _VP, _VP, _U64, _VP, _VP]),
     "ah_batch_view_get": (_I32, [_VP, ctypes.POINTER(ah_batch_view)]),
@@ -273,6 +275,38 @@ def ah_fasta_pack(ctx, text, genome_ids: Optional[np.ndarray] = None, n_bytes: O
     finally:
         L.ah_fasta_free(names)
     return out, nm
+
+
+def ah_fasta_count(names) -> int:
+    """Records of an ah_fasta handle (ah_fasta_pack's wrapper returns the names as a list)."""
+    return int(load().ah_fasta_count(names))
+
+
+def ah_fasta_name(names, i: int) -> Optional[str]:
+    v = load().ah_fasta_name(names, int(i))
+    return None if v is None else v.decode("latin-1")
+
+
+def ah_fasta_free(names) -> None:
+    load().ah_fasta_free(names)
+
+
+def ah_amplicons_fasta(amps: np.ndarray, arena: bytes, field_off: np.ndarray, record_names: Sequence[str],
+                       record_sources: Optional[Sequence[str]] = None, barcodes: bool = False) -> bytes:
+    """FASTA records with the headers of the paper's output (host formatting of copied results)."""
+    amps = np.ascontiguousarray(amps, dtype=AMP_DTYPE)
+    off = np.ascontiguousarray(field_off, dtype=np.uint64)
+    arena = arena or b"\0"
+    names = (ctypes.c_char_p * max(1, len(record_names)))(*[x.encode("latin-1") for x in record_names])
+    srcs = None if record_sources is None else \
+        (ctypes.c_char_p * max(1, len(record_sources)))(*[x.encode("latin-1") for x in record_sources])
+    n = ctypes.c_uint64()
+    L = load()
+    args = (len(amps), amps.ctypes.data, arena, off.ctypes.data, len(record_names), names, srcs, int(bool(barcodes)))
+    _check(L.ah_amplicons_fasta(*args, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(max(1, n.value))
+    _check(L.ah_amplicons_fasta(*args, buf, n.value, ctypes.byref(n)))
+    return buf.raw[:n.value]
 
 
 def ah_batch_export(batch, planes: Optional[np.ndarray] = None, groups: Optional[np.ndarray] = None,
