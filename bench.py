@@ -251,6 +251,62 @@ def job_time_and_value(ms_local, bases_per_rank, world):
     return ms, world * bases_per_rank / (ms * 1e-3) / 1e9
 
 
+def fasta_into(dst, seq, offsets, width=80):
+    """Write the records as FASTA (">genome_<r> synthetic" headers, `width`-column lines) into the
+    uint8 array dst; returns the length.  With dst None, only the length."""
+    import numpy as np
+
+    pos = 0
+    for r in range(len(offsets) - 1):
+        head = b">genome_%d synthetic\n" % r
+        L = int(offsets[r + 1] - offsets[r])
+        rows = (L + width - 1) // width
+        n = len(head) + L + rows
+        if dst is not None:
+            dst[pos:pos + len(head)] = np.frombuffer(head, dtype=np.uint8)
+            body = dst[pos + len(head):pos + n]
+            s = seq[int(offsets[r]):int(offsets[r + 1])]
+            full = (L // width) * (width + 1)
+            if full:
+                grid = body[:full].reshape(-1, width + 1)
+                grid[:, :width] = s[:(L // width) * width].reshape(-1, width)
+                grid[:, width] = 10
+            tail = L - (L // width) * width
+            if tail:
+                body[full:full + tail] = s[L - tail:]
+                body[full + tail] = 10
+        pos += n
+    return pos
+
+
+def e2e_from_fasta(ah, eng, wl, batch, plan, bufs, on_device, steps):
+    """End to end from FASTA text in pinned host memory: ah_fasta_pack_into (copy, parse and pack on
+    the device) -> plan replay -> results into pinned host buffers."""
+    import numpy as np
+    import torch
+
+    seq = wl.d_seq.cpu().numpy() if on_device else wl.seq
+    n = fasta_into(None, seq, wl.offsets)
+    t_text = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    fasta_into(t_text.numpy(), seq, wl.offsets)
+    del seq
+    times = []
+    for it in range(1 + steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ah.ah_fasta_pack_into(eng.ctx, t_text.data_ptr(), batch, n_bytes=n)
+        ah.ah_plan_launch(plan, eng.ctx)
+        ah.ah_plan_copy_results(plan, eng.ctx, *bufs)
+        dt = time.perf_counter() - t
+        if it > 0:
+            times.append(dt)
+    del t_text
+    return {"value": wl.total_bp / statistics.median(times) / 1e9, "unit": "Gbp/s", "h2d_bytes_per_step": n,
+            "ms_per_step": statistics.median(times) * 1e3,
+            "path": "pinned FASTA text (80-column lines) -> ah_fasta_pack_into (one copy, parsed and packed on "
+                    "the device) -> ah_plan_launch -> ah_plan_copy_results into pinned host buffers"}
+
+
 def run_engine(args):
     import numpy as np
     import torch
@@ -398,6 +454,8 @@ def run_engine(args):
             "path": "pinned 2-bit planes + sparse invalid words -> ah_batch_import -> ah_plan_launch -> "
                     "ah_plan_copy_results into pinned host buffers"}
         del pl_t, g_t, w_t
+        if args.e2e_fasta:
+            e2e["from_fasta"] = e2e_from_fasta(ah, eng, wl, batch, plan, bufs, on_device, args.e2e_steps)
 
     ah.ah_plan_free(plan)
     ah.ah_batch_free(batch)
@@ -584,6 +642,8 @@ def main():
     ap.add_argument("--genomes", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-fasta", action="store_true",
+                    help="also time end to end from FASTA text (80-column lines) parsed and packed on the device")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--requests", type=int, default=200)

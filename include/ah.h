@@ -175,6 +175,10 @@ ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, co
 typedef struct ah_fasta ah_fasta;
 ah_status ah_fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint32_t* genome_ids,
                         ah_batch** batch_out, ah_fasta** names_out);
+/* The same into an existing batch (not a slice) whose records have the text's number and lengths
+ * (AH_EINVAL otherwise), e.g. the batch of a plan: FASTA text in, packed bases where the plan reads
+ * them. */
+ah_status ah_fasta_pack_into(ah_ctx* ctx, const char* text, uint64_t n_bytes, ah_batch* batch, ah_fasta** names_out);
 uint32_t ah_fasta_count(const ah_fasta* f);
 /* header line of record i (owned by f), NULL past the end */
 const char* ah_fasta_name(const ah_fasta* f, uint32_t i);

@@ -104,6 +104,7 @@ SIGNATURES = {
     "ah_pack_batch": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
     "ah_pack_batch_device": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
     "ah_fasta_pack": (_I32, [_VP, _VP, _U64, _VP, _PVP, _PVP]),
+    "ah_fasta_pack_into": (_I32, [_VP, _VP, _U64, _VP, _PVP]),
     "ah_fasta_count": (_U32, [_VP]),
     "ah_fasta_name": (ctypes.c_char_p, [_VP, _U32]),
     "ah_fasta_free": (None, [_VP]),
@@ -275,6 +276,26 @@ def ah_fasta_pack(ctx, text, genome_ids: Optional[np.ndarray] = None, n_bytes: O
     finally:
         L.ah_fasta_free(names)
     return out, nm
+
+
+def ah_fasta_pack_into(ctx, text, batch, n_bytes: Optional[int] = None, names: bool = False):
+    """FASTA text packed into an existing batch of the same record lengths; returns the names if asked."""
+    keep = None
+    if isinstance(text, int):
+        addr, n = text, int(n_bytes)
+    else:
+        keep = np.frombuffer(text, dtype=np.uint8) if isinstance(text, (bytes, bytearray)) else \
+            np.ascontiguousarray(text, dtype=np.uint8)
+        addr, n = keep.ctypes.data, len(keep)
+    h = ctypes.c_void_p()
+    _check(load().ah_fasta_pack_into(ctx, addr, n, batch, ctypes.byref(h) if names else None), ctx)
+    if not names:
+        return None
+    L = load()
+    try:
+        return [L.ah_fasta_name(h, i).decode("latin-1") for i in range(L.ah_fasta_count(h))]
+    finally:
+        L.ah_fasta_free(h)
 
 
 def ah_fasta_count(names) -> int:

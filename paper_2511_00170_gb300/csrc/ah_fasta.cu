@@ -20,7 +20,8 @@ struct ah_fasta {
 namespace ah {
 namespace {
 
-constexpr int kFaThreads = 256, kFaBytes = 16, kFaTile = kFaThreads * kFaBytes;
+constexpr int kFaThreads = 256, kFaBytes = 16, kFaSegs = 4, kFaTile = kFaThreads * kFaBytes * kFaSegs;
+// a thread takes kFaSegs consecutive 16-byte segments (64 bytes); a tile (one CTA) 16 KiB
 enum : uint32_t { FS_LS = 0, FS_H = 1, FS_S = 2 };
 // a transfer function over the three states: bits 2s..2s+1 hold the state after, from state s
 constexpr uint32_t kIdentity = FS_LS | (FS_H << 2) | (FS_S << 4);
@@ -37,20 +38,105 @@ __device__ __forceinline__ uint32_t step(uint32_t s, uint8_t c) {
 }
 __device__ __forceinline__ bool is_blank(uint8_t c) { return c == '\r' || c == ' ' || c == '\t'; }
 
-// this thread's bytes [p0, p1)
-__device__ __forceinline__ void thread_span(uint64_t n, uint64_t* p0, uint64_t* p1) {
-  *p0 = (uint64_t)blockIdx.x * kFaTile + (uint64_t)threadIdx.x * kFaBytes;
+// segment q of this thread: bytes [p0, p1)
+__device__ __forceinline__ void seg_span(uint64_t n, int q, uint64_t* p0, uint64_t* p1) {
+  *p0 = (uint64_t)blockIdx.x * kFaTile + ((uint64_t)threadIdx.x * kFaSegs + q) * kFaBytes;
   *p1 = min(n, *p0 + kFaBytes);
   if (*p0 > n) *p0 = n;
 }
 
-__device__ uint32_t thread_function(const uint8_t* __restrict__ t, uint64_t p0, uint64_t p1) {
-  uint32_t a = FS_LS, b = FS_H, c = FS_S;
-  for (uint64_t p = p0; p < p1; ++p) {
-    const uint8_t x = t[p];
-    a = step(a, x), b = step(b, x), c = step(c, x);
+// A thread's segment: up to 16 bytes and per-byte class masks (bit j for byte j).
+struct Seg {
+  uint32_t w0, w1, w2, w3;  // the bytes, little-endian (registers: no indexed array)
+  int len;
+  uint32_t nl, gt, blank;
+  __device__ __forceinline__ uint8_t at(int j) const {
+    const uint32_t w = j < 8 ? (j < 4 ? w0 : w1) : (j < 12 ? w2 : w3);
+    return (uint8_t)(w >> (8 * (j & 3)));
   }
-  return a | (b << 2) | (c << 4);
+};
+
+// bits 7, 15, 23, 31 of m to bits 0-3 (the four partial products land on distinct bits below 28)
+__device__ __forceinline__ uint32_t bit7_mask(uint32_t m) { return ((m & 0x80808080u) * 0x00204081u) >> 28; }
+
+// bit j: byte j of w equals the byte in ch4 (exact per byte: no borrow crosses bytes)
+__device__ __forceinline__ uint32_t bytes_eq(uint32_t w, uint32_t ch4) {
+  const uint32_t y = w ^ ch4;
+  return bit7_mask(~(((y & 0x7f7f7f7fu) + 0x7f7f7f7fu) | y));
+}
+
+__device__ __forceinline__ void classify_seg(const uint32_t* w, int len, Seg* g) {
+  g->len = len;
+  g->nl = g->gt = g->blank = 0;
+  g->w0 = w[0], g->w1 = w[1], g->w2 = w[2], g->w3 = w[3];
+  // bases and other letters have bit 7 clear and bit 6 set; line breaks, '>' and blanks do not,
+  // so most segments skip the exact classification
+  uint32_t other = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) other |= ~(~w[q] & (w[q] << 1)) & 0x80808080u;
+  if (other == 0 && len == kFaBytes) return;
+  // line breaks exactly; '>' and blanks only when some other non-letter byte is present
+  uint32_t other16 = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    other16 |= bit7_mask(~(~w[q] & (w[q] << 1))) << (4 * q);
+    g->nl |= bytes_eq(w[q], 0x0a0a0a0au) << (4 * q);
+  }
+  if (other16 != g->nl || len != kFaBytes) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      g->gt |= bytes_eq(w[q], 0x3e3e3e3eu) << (4 * q);
+      g->blank |= (bytes_eq(w[q], 0x0d0d0d0du) | bytes_eq(w[q], 0x20202020u) | bytes_eq(w[q], 0x09090909u)) << (4 * q);
+    }
+  }
+  const uint32_t valid = len >= 32 ? 0xffffffffu : ((1u << len) - 1u);
+  g->nl &= valid, g->gt &= valid, g->blank &= valid;
+}
+
+// the thread's kFaSegs segments: whole and 16-byte aligned, four vector loads issued together;
+// otherwise byte loads up to the end of the text
+__device__ __forceinline__ void load_segs(const uint8_t* __restrict__ t, uint64_t n, Seg* g) {
+  const uint64_t p = (uint64_t)blockIdx.x * kFaTile + (uint64_t)threadIdx.x * (kFaSegs * kFaBytes);
+  uint32_t w[kFaSegs][4];
+  if (p + kFaSegs * kFaBytes <= n && (((uint64_t)(uintptr_t)t) & 15) == 0) {
+    const uint4* v = reinterpret_cast<const uint4*>(t + p);
+    uint4 x[kFaSegs];
+#pragma unroll
+    for (int q = 0; q < kFaSegs; ++q) x[q] = __ldg(v + q);
+#pragma unroll
+    for (int q = 0; q < kFaSegs; ++q) {
+      w[q][0] = x[q].x, w[q][1] = x[q].y, w[q][2] = x[q].z, w[q][3] = x[q].w;
+      classify_seg(w[q], kFaBytes, &g[q]);
+    }
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < kFaSegs; ++q) {
+    const uint64_t p0 = min(n, p + (uint64_t)q * kFaBytes), p1 = min(n, p0 + kFaBytes);
+    const int len = (int)(p1 - p0);
+    w[q][0] = w[q][1] = w[q][2] = w[q][3] = 0;
+#pragma unroll
+    for (int j = 0; j < kFaBytes; ++j)
+      if (j < len) w[q][j >> 2] |= (uint32_t)t[p0 + j] << (8 * (j & 3));
+    classify_seg(w[q], len, &g[q]);
+  }
+}
+
+// the segment's transfer function
+__device__ __forceinline__ uint32_t seg_function(const Seg& g) {
+  if (g.len == 0) return kIdentity;
+  if (g.nl) {
+    const int last = 31 - __clz(g.nl);
+    const uint32_t e = last == g.len - 1 ? FS_LS : (g.at(last + 1) == '>' ? FS_H : FS_S);
+    return e | (e << 2) | (e << 4);
+  }
+  return (g.at(0) == '>' ? FS_H : FS_S) | (FS_H << 2) | (FS_S << 4);
+}
+
+// the segment needs the byte walk: a header starts in it or it starts inside a header line
+__device__ __forceinline__ bool seg_has_header(const Seg& g, uint32_t s0) {
+  const uint32_t line_start = (g.nl << 1) | (s0 == FS_LS ? 1u : 0u);
+  return s0 == FS_H || (g.gt & line_start) != 0;
 }
 
 // exclusive composition of the block's thread functions (thread order) and the block's total
@@ -105,16 +191,54 @@ __device__ void block_exclusive_sums(uint32_t a, uint32_t b, uint32_t* ea, uint3
 // pass 1: each tile's transfer function
 __global__ void __launch_bounds__(kFaThreads) k_fa_tiles(const uint8_t* __restrict__ t, uint64_t n,
                                                          uint8_t* __restrict__ tile_f) {
-  uint64_t p0, p1;
-  thread_span(n, &p0, &p1);
+  Seg g[kFaSegs];
+  load_segs(t, n, g);
+  uint32_t f = kIdentity;
+#pragma unroll
+  for (int q = 0; q < kFaSegs; ++q) f = compose(f, seg_function(g[q]));
   uint32_t total;
-  block_exclusive_function(thread_function(t, p0, p1), &total);
+  block_exclusive_function(f, &total);
   if (threadIdx.x == 0) tile_f[blockIdx.x] = (uint8_t)total;
 }
 
 // passes 2 and 3: classify the tile's bytes from its entry state.  emit = false: per-tile counts of
 // sequence bytes and headers.  emit = true: sequence bytes to out[rank], and per header (record r)
 // hdr_pos[r] (first byte after '>'), seq_rank[r] (sequence bytes before it) and hdr_end[r] (its '\n').
+// one segment from entry state s: counts (or, emitting, the bytes and header records); returns the
+// state after it
+template <bool emit>
+__device__ __forceinline__ uint32_t seg_pass(const Seg& g, uint64_t p0, uint32_t s, uint32_t* n_seq, uint32_t* n_hdr,
+                                             uint8_t* staged, uint32_t* local, uint64_t* rec, uint64_t seq_base0,
+                                             uint64_t* __restrict__ hdr_pos, uint64_t* __restrict__ hdr_end,
+                                             uint64_t* __restrict__ seq_rank) {
+  if (!seg_has_header(g, s)) {  // no header: every byte that is not a line break or a blank
+    const uint32_t valid = g.len >= 32 ? 0xffffffffu : ((1u << g.len) - 1u);
+    const uint32_t seq_mask = ~(g.nl | g.blank) & valid;
+    *n_seq += __popc(seq_mask);
+    if (emit)
+      for (uint32_t m = seq_mask; m; m &= m - 1) staged[(*local)++] = g.at(__ffs(m) - 1);
+    return apply(seg_function(g), s);
+  }
+  for (int j = 0; j < g.len; ++j) {
+    const uint8_t x = g.at(j);
+    if (s == FS_LS && x == '>') {
+      ++*n_hdr;
+      if (emit) {
+        hdr_pos[*rec] = p0 + j + 1;
+        seq_rank[*rec] = seq_base0 + *local;
+        ++*rec;
+      }
+    } else if (s == FS_H && x == '\n') {
+      if (emit) hdr_end[*rec - 1] = p0 + j;  // a header line is open: *rec >= 1
+    } else if ((s == FS_S || s == FS_LS) && x != '\n' && !is_blank(x)) {
+      ++*n_seq;
+      if (emit) staged[(*local)++] = x;
+    }
+    s = step(s, x);
+  }
+  return s;
+}
+
 template <bool emit>
 __global__ void __launch_bounds__(kFaThreads) k_fa_pass(const uint8_t* __restrict__ t, uint64_t n,
                                                         const uint8_t* __restrict__ tile_entry,
@@ -123,16 +247,20 @@ __global__ void __launch_bounds__(kFaThreads) k_fa_pass(const uint8_t* __restric
                                                         const uint64_t* __restrict__ hdr_base, uint8_t* __restrict__ out,
                                                         uint64_t* __restrict__ hdr_pos, uint64_t* __restrict__ hdr_end,
                                                         uint64_t* __restrict__ seq_rank) {
-  uint64_t p0, p1;
-  thread_span(n, &p0, &p1);
-  const uint32_t before = block_exclusive_function(thread_function(t, p0, p1), nullptr);
+  __shared__ __align__(16) uint8_t staged[emit ? kFaTile + 32 : 16];  // the tile's sequence bytes, compacted
+  Seg g[kFaSegs];
+  load_segs(t, n, g);
+  uint32_t f = kIdentity;
+#pragma unroll
+  for (int q = 0; q < kFaSegs; ++q) f = compose(f, seg_function(g[q]));
+  const uint32_t before = block_exclusive_function(f, nullptr);
   const uint32_t s0 = apply(before, tile_entry[blockIdx.x]);
   uint32_t n_seq = 0, n_hdr = 0, s = s0;
-  for (uint64_t p = p0; p < p1; ++p) {
-    const uint8_t x = t[p];
-    if (s == FS_LS && x == '>') ++n_hdr;
-    else if ((s == FS_S || s == FS_LS) && x != '\n' && !is_blank(x)) ++n_seq;
-    s = step(s, x);
+#pragma unroll
+  for (int q = 0; q < kFaSegs; ++q) {
+    uint64_t p0, p1;
+    seg_span(n, q, &p0, &p1);
+    s = seg_pass<false>(g[q], p0, s, &n_seq, &n_hdr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr);
   }
   uint32_t e_seq, e_hdr, t_seq, t_hdr;
   block_exclusive_sums(n_seq, n_hdr, &e_seq, &e_hdr, &t_seq, &t_hdr);
@@ -140,21 +268,29 @@ __global__ void __launch_bounds__(kFaThreads) k_fa_pass(const uint8_t* __restric
     if (threadIdx.x == 0) tile_seq[blockIdx.x] = t_seq, tile_hdr[blockIdx.x] = t_hdr;
     return;
   }
-  uint64_t rank = seq_base[blockIdx.x] + e_seq;
-  uint64_t rec = hdr_base[blockIdx.x] + e_hdr;  // headers started before this byte
+  const uint64_t base = seq_base[blockIdx.x];
+  const uint32_t lead = (uint32_t)(base & 15);  // staged[lead + i] goes to out[base + i]
+  uint32_t local = lead + e_seq;                // this thread's first sequence byte, staged
+  uint64_t rec = hdr_base[blockIdx.x] + e_hdr;  // headers started before this thread's bytes
+  uint32_t cs = 0, ch = 0;
   s = s0;
-  for (uint64_t p = p0; p < p1; ++p) {
-    const uint8_t x = t[p];
-    if (s == FS_LS && x == '>') {
-      hdr_pos[rec] = p + 1;
-      seq_rank[rec] = rank;
-      ++rec;
-    } else if (s == FS_H && x == '\n') {
-      hdr_end[rec - 1] = p;  // rec >= 1: a header line is open
-    } else if ((s == FS_S || s == FS_LS) && x != '\n' && !is_blank(x)) {
-      out[rank++] = x;
-    }
-    s = step(s, x);
+#pragma unroll
+  for (int q = 0; q < kFaSegs; ++q) {
+    uint64_t p0, p1;
+    seg_span(n, q, &p0, &p1);
+    s = seg_pass<true>(g[q], p0, s, &cs, &ch, staged, &local, &rec, base - lead, hdr_pos, hdr_end, seq_rank);
+  }
+  __syncthreads();
+  // out[base, base + t_seq) from staged[lead, lead + t_seq): whole aligned 16-byte units as uint4,
+  // the partial first and last units byte by byte (their other bytes belong to the next tiles)
+  uint8_t* dst = out + (base - lead);
+  const uint32_t end = lead + t_seq;
+  const uint32_t full_lo = lead ? 16u : 0u, full_hi = end & ~15u;
+  for (uint32_t u = full_lo + 16u * threadIdx.x; u < full_hi; u += 16u * kFaThreads)
+    *reinterpret_cast<uint4*>(dst + u) = *reinterpret_cast<const uint4*>(staged + u);
+  if (threadIdx.x < 32) {
+    for (uint32_t i = lead + threadIdx.x; i < min(full_lo, end); i += 32) dst[i] = staged[i];
+    for (uint32_t i = max(full_hi, full_lo) + threadIdx.x; i < end; i += 32) dst[i] = staged[i];
   }
 }
 
@@ -174,13 +310,13 @@ uint32_t host_apply(uint32_t f, uint32_t s) { return (f >> (2 * s)) & 3u; }
 
 using namespace ah;
 
-extern "C" {
+namespace ah {
+namespace {
 
-ah_status ah_fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint32_t* genome_ids,
-                        ah_batch** batch_out, ah_fasta** names_out) {
-  if (!ctx || !text || !batch_out || n_bytes == 0) return fail(ctx, AH_EINVAL, "ah_fasta_pack: bad arguments");
-  *batch_out = nullptr;
-  if (names_out) *names_out = nullptr;
+// Parse and pack: into a new batch (*batch_out) or, with `into`, into an existing batch whose record
+// lengths must equal the text's.
+ah_status fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint32_t* genome_ids, ah_batch* into,
+                     ah_batch** batch_out, ah_fasta** names_out) {
   cudaSetDevice(ctx->device);
   cudaPointerAttributes pa;
   const bool on_device = cudaPointerGetAttributes(&pa, text) == cudaSuccess &&
@@ -262,7 +398,17 @@ ah_status ah_fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
     // records: sequence offsets relative to the first record's first base
     std::vector<uint64_t> offs(n_rec + 1);
     for (uint32_t r = 0; r <= n_rec; ++r) offs[r] = h_rank[r] - h_rank[0];
-    st = ah_pack_batch_device(ctx, n_rec, compact + h_rank[0], offs.data(), genome_ids, batch_out);
+    if (into) {
+      bool same = into->n_records == n_rec;
+      for (uint32_t r = 0; same && r < n_rec; ++r) same = into->h_rec_len[r] == offs[r + 1] - offs[r];
+      if (!same) {
+        st = fail(ctx, AH_EINVAL, "ah_fasta_pack_into: the text's records differ from the batch's in number or length");
+        break;
+      }
+      st = ah_batch_pack_range(ctx, into, 0, n_rec, compact + h_rank[0], offs.data());
+    } else {
+      st = ah_pack_batch_device(ctx, n_rec, compact + h_rank[0], offs.data(), genome_ids, batch_out);
+    }
     if (st) break;
     if (names_out) {
       ah_fasta* f = new ah_fasta();
@@ -294,8 +440,10 @@ ah_status ah_fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
       }
       if (st) {
         delete f;
-        ah_batch_free(*batch_out);
-        *batch_out = nullptr;
+        if (!into) {
+          ah_batch_free(*batch_out);
+          *batch_out = nullptr;
+        }
         break;
       }
       *names_out = f;
@@ -303,6 +451,26 @@ ah_status ah_fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
   } while (false);
   cleanup();
   return st;
+}
+
+}  // namespace
+}  // namespace ah
+
+extern "C" {
+
+ah_status ah_fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint32_t* genome_ids,
+                        ah_batch** batch_out, ah_fasta** names_out) {
+  if (!ctx || !text || !batch_out || n_bytes == 0) return fail(ctx, AH_EINVAL, "ah_fasta_pack: bad arguments");
+  *batch_out = nullptr;
+  if (names_out) *names_out = nullptr;
+  return fasta_pack(ctx, text, n_bytes, genome_ids, nullptr, batch_out, names_out);
+}
+
+ah_status ah_fasta_pack_into(ah_ctx* ctx, const char* text, uint64_t n_bytes, ah_batch* batch, ah_fasta** names_out) {
+  if (!ctx || !text || !batch || n_bytes == 0 || batch->view)
+    return fail(ctx, AH_EINVAL, "ah_fasta_pack_into: bad arguments");
+  if (names_out) *names_out = nullptr;
+  return fasta_pack(ctx, text, n_bytes, nullptr, batch, nullptr, names_out);
 }
 
 uint32_t ah_fasta_count(const ah_fasta* f) { return f ? (uint32_t)f->names.size() : 0; }

@@ -79,6 +79,26 @@ def test_fasta_pack_matches_oracle(ah_ctx, seed, n_records, crlf, junk, on_devic
         ah.ah_batch_free(ref)
 
 
+def test_fasta_pack_into_existing_batch(ah_ctx):
+    """Packing FASTA into an existing batch of the same record lengths gives the same bases as a new
+    batch; other lengths are refused."""
+    ah, ctx = ah_ctx
+    text = _random_fasta(7, 12, False, False)
+    names, seqs = oracle.parse_fasta(text)
+    fresh, _ = ah.ah_fasta_pack(ctx, text)
+    into = ah.ah_batch_create(ctx, np.array([len(s) for s in seqs], dtype=np.uint64))
+    wrong = ah.ah_batch_create(ctx, np.array([len(s) + 1 for s in seqs], dtype=np.uint64))
+    try:
+        assert ah.ah_fasta_pack_into(ctx, text, into, names=True) == names
+        assert _batch_bytes(ah, into) == _batch_bytes(ah, fresh)
+        with pytest.raises(ah.AhError) as e:
+            ah.ah_fasta_pack_into(ctx, text, wrong)
+        assert e.value.status == ah.AH_EINVAL
+    finally:
+        for b in (fresh, into, wrong):
+            ah.ah_batch_free(b)
+
+
 def test_fasta_pack_refuses_text_without_records(ah_ctx):
     ah, ctx = ah_ctx
     with pytest.raises(ah.AhError) as e:
