@@ -346,6 +346,10 @@ void ah_ctx_destroy(ah_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   // blocks still held by objects of this context are released with them
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  for (int b = 0; b < 2; ++b) {
+    if (ctx->bounce[b]) cudaFreeHost(ctx->bounce[b]);
+    if (ctx->bounce_ev[b]) cudaEventDestroy(ctx->bounce_ev[b]);
+  }
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -860,9 +864,7 @@ ah_status ah_hits_device(const ah_hits* h, const ah_hit** d_hits, const uint64_t
 ah_status ah_hits_copy(const ah_hits* h, ah_hit* host_out, uint64_t cap) {
   if (!h || (!host_out && cap)) return AH_EINVAL;
   uint64_t n = std::min(cap, h->n);
-  if (n) AH_CUDA(h->ctx, cudaMemcpyAsync(host_out, h->d, n * sizeof(ah_hit), cudaMemcpyDeviceToHost, h->ctx->stream));
-  AH_CUDA(h->ctx, cudaStreamSynchronize(h->ctx->stream));
-  return AH_OK;
+  return copy_to_host(h->ctx, host_out, h->d, n * sizeof(ah_hit));
 }
 
 void ah_hits_free(ah_hits* h) {
@@ -925,9 +927,7 @@ ah_status ah_amplicons_count(const ah_amplicons* a, uint64_t* n) {
 ah_status ah_amplicons_copy(const ah_amplicons* a, ah_amplicon* host_out, uint64_t cap) {
   if (!a || (!host_out && cap)) return AH_EINVAL;
   uint64_t n = std::min(cap, a->n);
-  if (n) AH_CUDA(a->ctx, cudaMemcpyAsync(host_out, a->d, n * sizeof(ah_amplicon), cudaMemcpyDeviceToHost, a->ctx->stream));
-  AH_CUDA(a->ctx, cudaStreamSynchronize(a->ctx->stream));
-  return AH_OK;
+  return copy_to_host(a->ctx, host_out, a->d, n * sizeof(ah_amplicon));
 }
 
 ah_status ah_amplicons_arena_size(const ah_amplicons* a, uint64_t* bytes) {
@@ -943,12 +943,8 @@ ah_status ah_amplicons_seq_copy(const ah_amplicons* a, char* arena_out, uint64_t
   if (arena_cap < a->arena_bytes || offsets_cap < 5 * a->n + 1)
     return fail(a->ctx, AH_EOVERFLOW, "ah_amplicons_seq_copy: need %llu arena bytes and %llu offsets",
                 (unsigned long long)a->arena_bytes, (unsigned long long)(5 * a->n + 1));
-  if (a->arena_bytes)
-    AH_CUDA(a->ctx, cudaMemcpyAsync(arena_out, a->d_arena, a->arena_bytes, cudaMemcpyDeviceToHost, a->ctx->stream));
-  AH_CUDA(a->ctx, cudaMemcpyAsync(offsets_out, a->d_field_off, (5 * a->n + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                                  a->ctx->stream));
-  AH_CUDA(a->ctx, cudaStreamSynchronize(a->ctx->stream));
-  return AH_OK;
+  ah_status st = copy_to_host(a->ctx, arena_out, a->d_arena, a->arena_bytes);
+  return st ? st : copy_to_host(a->ctx, offsets_out, a->d_field_off, (5 * a->n + 1) * sizeof(uint64_t));
 }
 
 void ah_amplicons_free(ah_amplicons* a) {

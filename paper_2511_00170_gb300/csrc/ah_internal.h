@@ -89,6 +89,8 @@ struct ah_ctx {
   bool own_stream = false;
   std::string err;
   cudaMemPool_t pool = nullptr;      // the context's stream-ordered memory pool
+  uint8_t* bounce[2] = {nullptr, nullptr};       // page-locked buffers for copies into pageable memory
+  cudaEvent_t bounce_ev[2] = {nullptr, nullptr};
   uint32_t* d_status = nullptr;      // device status word
   uint32_t* h_status = nullptr;      // pinned mirror
   ah::JitCache* jit = nullptr;       // the process-wide kernel cache
@@ -194,6 +196,10 @@ void dfree(ah_ctx* ctx, void* p);
 // ---- exclusive scan over counts: out[i] = sum(in[0..i)), out[n] = total ------------------------
 ah_status exclusive_scan_u32(ah_ctx* ctx, const uint32_t* d_in, uint64_t* d_out, uint64_t n);
 ah_status exclusive_scan_u64(ah_ctx* ctx, const uint64_t* d_in, uint64_t* d_out, uint64_t n);
+// device -> host copy into caller memory, synchronous: page-locked destinations directly, pageable
+// ones through the context's two page-locked bounce buffers, so that no copy takes the driver's
+// pageable path (one staging pipeline for every stream of the process)
+ah_status copy_to_host(ah_ctx* ctx, void* dst, const void* src, uint64_t bytes);
 // read one uint64 from device memory (synchronises the stream)
 ah_status read_u64(ah_ctx* ctx, const uint64_t* d, uint64_t* h);
 // read and clear the device status word (synchronises)

@@ -23,6 +23,46 @@ void dfree(ah_ctx* ctx, void* p) {
   if (p) cudaFreeAsync(p, ctx->stream);
 }
 
+ah_status copy_to_host(ah_ctx* ctx, void* dst, const void* src, uint64_t bytes) {
+  constexpr uint64_t kBounce = 8ull << 20;
+  if (bytes) {
+    cudaPointerAttributes pa;
+    const bool locked = cudaPointerGetAttributes(&pa, dst) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    if (locked || bytes <= (64u << 10)) {
+      AH_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    } else {
+      for (int b = 0; b < 2; ++b) {
+        if (!ctx->bounce[b]) AH_CUDA(ctx, cudaMallocHost(&ctx->bounce[b], kBounce));
+        if (!ctx->bounce_ev[b]) AH_CUDA(ctx, cudaEventCreateWithFlags(&ctx->bounce_ev[b], cudaEventDisableTiming));
+      }
+      // chunk i lands in buffer i % 2 while the host copies chunk i - 1 out of the other
+      uint64_t off[2] = {0, 0}, len[2] = {0, 0};
+      int i = 0;
+      for (uint64_t o = 0; o < bytes; o += kBounce, ++i) {
+        const int b = i & 1;
+        if (len[b]) {
+          AH_CUDA(ctx, cudaEventSynchronize(ctx->bounce_ev[b]));
+          memcpy((char*)dst + off[b], ctx->bounce[b], len[b]);
+        }
+        off[b] = o;
+        len[b] = std::min<uint64_t>(kBounce, bytes - o);
+        AH_CUDA(ctx, cudaMemcpyAsync(ctx->bounce[b], (const char*)src + o, len[b], cudaMemcpyDeviceToHost, ctx->stream));
+        AH_CUDA(ctx, cudaEventRecord(ctx->bounce_ev[b], ctx->stream));
+      }
+      for (int k = 0; k < 2; ++k) {
+        const int b = (i + k) & 1;  // the older chunk first
+        if (!len[b]) continue;
+        AH_CUDA(ctx, cudaEventSynchronize(ctx->bounce_ev[b]));
+        memcpy((char*)dst + off[b], ctx->bounce[b], len[b]);
+        len[b] = 0;
+      }
+    }
+  }
+  AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return AH_OK;
+}
+
 ah_status read_u64(ah_ctx* ctx, const uint64_t* d, uint64_t* h) {
   AH_CUDA(ctx, cudaMemcpyAsync(h, d, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
   AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
