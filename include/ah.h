@@ -179,6 +179,21 @@ ah_status ah_fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
  * (AH_EINVAL otherwise), e.g. the batch of a plan: FASTA text in, packed bases where the plan reads
  * them. */
 ah_status ah_fasta_pack_into(ah_ctx* ctx, const char* text, uint64_t n_bytes, ah_batch* batch, ah_fasta** names_out);
+/* FASTQ input with qualities (future work the paper names: FASTQ input with quality
+ * propagation).  Records are four lines: '@' and the name, the bases, a '+' line, the qualities (one
+ * byte per base); '\r' is dropped and empty lines after the last record are ignored.  Parsed on the
+ * device like ah_fasta_pack.  Returns the packed bases, the qualities (*quals_out, one byte per base
+ * of every record, kept on the device for ah_extract_qualities) and optionally the names.
+ * AH_EINVAL when the text is not such records or a record's qualities differ in length from its
+ * bases.  Synchronises the stream. */
+typedef struct ah_quals ah_quals;
+ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint32_t* genome_ids,
+                        ah_batch** batch_out, ah_quals** quals_out, ah_fasta** names_out);
+uint32_t ah_quals_count(const ah_quals* q);
+/* The record offsets (n + 1 entries; the last is the total) and, when out is not NULL, all
+ * qualities back to back (cap >= the total, else AH_EOVERFLOW) into host memory. */
+ah_status ah_quals_copy(const ah_quals* q, char* out, uint64_t cap, uint64_t* offsets_out);
+void ah_quals_free(ah_quals* q);
 uint32_t ah_fasta_count(const ah_fasta* f);
 /* header line of record i (owned by f), NULL past the end */
 const char* ah_fasta_name(const ah_fasta* f, uint32_t i);
@@ -391,6 +406,22 @@ ah_status ah_extract_barcodes(ah_ctx* ctx, const ah_batch* b, const ah_primers* 
 ah_status ah_amplicons_fasta(uint64_t n_amps, const ah_amplicon* amps, const char* arena, const uint64_t* field_off,
                              uint32_t n_records, const char* const* record_names, const char* const* record_sources,
                              int barcodes, char* out, uint64_t out_cap, uint64_t* out_len);
+/* The same as FASTQ: '@' instead of '>', then after the sequence a '+' line and the qualities
+ * (qual_arena: ah_amplicons_qual_copy's output, field 0 of each amplicon). */
+ah_status ah_amplicons_fastq(uint64_t n_amps, const ah_amplicon* amps, const char* arena, const char* qual_arena,
+                             const uint64_t* field_off, uint32_t n_records, const char* const* record_names,
+                             const char* const* record_sources, int barcodes, char* out, uint64_t out_cap,
+                             uint64_t* out_len);
+
+/* Qualities of the amplicon sequences (field 0 of ah_extract_barcodes: the amplicon or its trimmed
+ * interior), taken from the qualities q of batch b's records and reversed for RF as the bases are
+ * (not complemented).  Run after ah_extract_barcodes on the same objects; AH_EINVAL when q does not
+ * match b's records.  ah_amplicons_qual_copy copies them out in the layout of the sequence arena:
+ * amplicon m's qualities at the offsets of its field 0, other bytes unspecified (cap >= the arena's
+ * size). */
+ah_status ah_extract_qualities(ah_ctx* ctx, const ah_quals* q, const ah_batch* b, const ah_primers* p,
+                               const ah_hits* h, ah_amplicons* a);
+ah_status ah_amplicons_qual_copy(const ah_amplicons* a, char* out, uint64_t cap);
 
 ah_status ah_amplicons_count(const ah_amplicons* a, uint64_t* n);
 ah_status ah_amplicons_copy(const ah_amplicons* a, ah_amplicon* host_out, uint64_t cap);

@@ -198,6 +198,51 @@ def amplicon_fasta(records, names: Sequence[str], sources: Optional[Sequence[str
     return b"".join(out)
 
 
+def parse_fastq(text: bytes) -> Tuple[List[str], List[bytes], List[bytes]]:
+    """FASTQ records of four lines ('@' name, bases, '+', qualities; '\\r' dropped; empty lines after
+    the last record ignored): names, bases, qualities."""
+    lines = [ln.replace(b"\r", b"") for ln in text.split(b"\n")]
+    while lines and lines[-1] == b"":
+        lines.pop()
+    names, seqs, quals = [], [], []
+    for r in range(0, len(lines), 4):
+        head = lines[r]
+        assert head.startswith(b"@"), "not FASTQ"
+        names.append(head[1:].decode("latin-1"))
+        seqs.append(lines[r + 1] if r + 1 < len(lines) else b"")
+        quals.append(lines[r + 3] if r + 3 < len(lines) else b"")
+        assert len(seqs[-1]) == len(quals[-1]), "qualities differ in length from the bases"
+    return names, seqs, quals
+
+
+def amplicon_qualities(wl, hits: np.ndarray, amps: np.ndarray, quals: Sequence[bytes]) -> List[bytes]:
+    """Per amplicon the qualities of its sequence field (Supplementary "Primer trimming and barcode
+    extraction"): the bases from site i's start to site j's end, or with trimming from site i's end
+    to site j's start (empty if they overlap), reversed for RF as the bases are (qualities are not
+    complemented)."""
+    lf, lr = primer_lengths(wl)
+    out = []
+    for a in amps:
+        hi, hj = hits[a["hit_i"]], hits[a["hit_j"]]
+        li = (lf if hi["primer"] == 0 else lr)[hi["pair"]]
+        lj = (lf if hj["primer"] == 0 else lr)[hj["pair"]]
+        s_i, e_i, s_j, e_j = int(hi["pos"]), int(hi["pos"]) + int(li), int(hj["pos"]), int(hj["pos"]) + int(lj)
+        lo, hi_ = (e_i, max(e_i, s_j)) if wl.trim else (s_i, e_j)
+        q = quals[int(a["record"])][lo:hi_]
+        out.append(q[::-1] if int(a["orient"]) == 1 else q)
+    return out
+
+
+def amplicon_fastq(records, names: Sequence[str], sources: Optional[Sequence[str]], barcodes: bool) -> bytes:
+    """FASTQ text: records are (record, start, end, orient, tm, fields, qualities); the header as in
+    amplicon_fasta with '@', then the sequence, '+' and the qualities."""
+    out = []
+    for rec in records:
+        fa = amplicon_fasta([rec[:6]], names, sources, barcodes)
+        out.append(b"@" + fa[1:] + b"+\n" + rec[6] + b"\n")
+    return b"".join(out)
+
+
 def free_mg(mg_mM: float, dntps_mM: float) -> float:
     """Free Mg2+ (mM) beside dNTPs that bind it one to one (salt method 7's input)."""
     return _get().or_free_mg(float(mg_mM), float(dntps_mM))

@@ -106,6 +106,14 @@ SIGNATURES = {
     "ah_fasta_pack": (_I32, [_VP, _VP, _U64, _VP, _PVP, _PVP]),
     "ah_fasta_pack_into": (_I32, [_VP, _VP, _U64, _VP, _PVP]),
     "ah_fasta_count": (_U32, [_VP]),
+    "ah_fastq_pack": (_I32, [_VP, _VP, _U64, _VP, _PVP, _PVP, _PVP]),
+    "ah_quals_count": (_U32, [_VP]),
+    "ah_quals_copy": (_I32, [_VP, _VP, _U64, _VP]),
+    "ah_quals_free": (None, [_VP]),
+    "ah_extract_qualities": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "ah_amplicons_qual_copy": (_I32, [_VP, _VP, _U64]),
+    "ah_amplicons_fastq": (_I32, [_U64, _VP, _VP, _VP, _VP, _U32, _VP, _VP, ctypes.c_int, _VP, _U64,
+                                  ctypes.POINTER(ctypes.c_uint64)]),
     "ah_fasta_name": (ctypes.c_char_p, [_VP, _U32]),
     "ah_fasta_free": (None, [_VP]),
     "ah_amplicons_fasta": (_I32, [_U64, _VP, _VP, _VP, _U32, _VP, _VP, ctypes.c_int, _VP, _U64,
@@ -298,6 +306,58 @@ def ah_fasta_pack_into(ctx, text, batch, n_bytes: Optional[int] = None, names: b
         L.ah_fasta_free(h)
 
 
+def ah_fastq_pack(ctx, text, genome_ids: Optional[np.ndarray] = None, n_bytes: Optional[int] = None):
+    """FASTQ text (host bytes/array, or a device address with n_bytes) parsed on the device.  Returns
+    (batch, quals, names); free quals with ah_quals_free."""
+    keep = None
+    if isinstance(text, int):
+        addr, n = text, int(n_bytes)
+    else:
+        keep = np.frombuffer(text, dtype=np.uint8) if isinstance(text, (bytes, bytearray)) else \
+            np.ascontiguousarray(text, dtype=np.uint8)
+        addr, n = keep.ctypes.data, len(keep)
+    gid = None if genome_ids is None else np.ascontiguousarray(genome_ids, dtype=np.uint32)
+    out, q, names = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().ah_fastq_pack(ctx, addr, n, None if gid is None else gid.ctypes.data, ctypes.byref(out),
+                                ctypes.byref(q), ctypes.byref(names)), ctx)
+    L = load()
+    try:
+        nm = [L.ah_fasta_name(names, i).decode("latin-1") for i in range(L.ah_fasta_count(names))]
+    finally:
+        L.ah_fasta_free(names)
+    return out, q, nm
+
+
+def ah_quals_count(quals) -> int:
+    return int(load().ah_quals_count(quals))
+
+
+def ah_quals_copy(quals) -> Tuple[bytes, np.ndarray]:
+    """(all qualities back to back, record offsets)."""
+    n = ah_quals_count(quals)
+    off = np.zeros(n + 1, dtype=np.uint64)
+    L = load()
+    _check(L.ah_quals_copy(quals, None, 0, off.ctypes.data))
+    total = int(off[-1])
+    buf = ctypes.create_string_buffer(max(1, total))
+    _check(L.ah_quals_copy(quals, buf, total, off.ctypes.data))
+    return buf.raw[:total], off
+
+
+def ah_quals_free(quals) -> None:
+    load().ah_quals_free(quals)
+
+
+def ah_extract_qualities(ctx, quals, batch, primers, hits, amps) -> None:
+    _check(load().ah_extract_qualities(ctx, quals, batch, primers, hits, amps), ctx)
+
+
+def ah_amplicons_qual_copy(amps, arena_bytes: int) -> bytes:
+    buf = ctypes.create_string_buffer(max(1, arena_bytes))
+    _check(load().ah_amplicons_qual_copy(amps, buf, arena_bytes))
+    return buf.raw[:arena_bytes]
+
+
 def ah_fasta_count(names) -> int:
     """Records of an ah_fasta handle (ah_fasta_pack's wrapper returns the names as a list)."""
     return int(load().ah_fasta_count(names))
@@ -327,6 +387,26 @@ def ah_amplicons_fasta(amps: np.ndarray, arena: bytes, field_off: np.ndarray, re
     _check(L.ah_amplicons_fasta(*args, None, 0, ctypes.byref(n)))
     buf = ctypes.create_string_buffer(max(1, n.value))
     _check(L.ah_amplicons_fasta(*args, buf, n.value, ctypes.byref(n)))
+    return buf.raw[:n.value]
+
+
+def ah_amplicons_fastq(amps: np.ndarray, arena: bytes, qual_arena: bytes, field_off: np.ndarray,
+                       record_names: Sequence[str], record_sources: Optional[Sequence[str]] = None,
+                       barcodes: bool = False) -> bytes:
+    """FASTQ records: the FASTA headers with '@', the sequence, '+', the qualities."""
+    amps = np.ascontiguousarray(amps, dtype=AMP_DTYPE)
+    off = np.ascontiguousarray(field_off, dtype=np.uint64)
+    arena, qual_arena = arena or b"\0", qual_arena or b"\0"
+    names = (ctypes.c_char_p * max(1, len(record_names)))(*[x.encode("latin-1") for x in record_names])
+    srcs = None if record_sources is None else \
+        (ctypes.c_char_p * max(1, len(record_sources)))(*[x.encode("latin-1") for x in record_sources])
+    n = ctypes.c_uint64()
+    L = load()
+    args = (len(amps), amps.ctypes.data, arena, qual_arena, off.ctypes.data, len(record_names), names, srcs,
+            int(bool(barcodes)))
+    _check(L.ah_amplicons_fastq(*args, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(max(1, n.value))
+    _check(L.ah_amplicons_fastq(*args, buf, n.value, ctypes.byref(n)))
     return buf.raw[:n.value]
 
 

@@ -952,6 +952,7 @@ void ah_amplicons_free(ah_amplicons* a) {
   dfree(a->ctx, a->d);
   dfree(a->ctx, a->d_arena);
   dfree(a->ctx, a->d_field_off);
+  dfree(a->ctx, a->d_qarena);
   delete a;
 }
 

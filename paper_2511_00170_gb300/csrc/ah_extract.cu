@@ -106,6 +106,23 @@ __global__ void k_extract_write(const ah_amplicon* __restrict__ amps, uint64_t n
   if (m == n - 1 && lane == 0) field_off[5 * n] = w;
 }
 
+// qualities of field 0 (the amplicon or its trimmed interior) at the field's arena offset, reversed
+// for RF like the bases (qualities are not complemented); one warp per amplicon
+__global__ void k_extract_qual(const ah_amplicon* __restrict__ amps, uint64_t n, const ah_hit* __restrict__ hits,
+                               const uint32_t* __restrict__ rec_len, const uint8_t* __restrict__ plen, int trim,
+                               const uint8_t* __restrict__ qual, const uint64_t* __restrict__ qoff,
+                               const uint64_t* __restrict__ field_off, char* __restrict__ qarena) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t m = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (m >= n) return;
+  const ah_amplicon A = amps[m];
+  const Fields f = fields_of(A, hits[A.hit_i], hits[A.hit_j], plen, rec_len[A.record], trim, 0, 0);
+  const uint8_t* q = qual + qoff[A.record];
+  const uint64_t w = field_off[5 * m];
+  const int64_t len = f.b[0] - f.a[0];
+  for (int64_t i = lane; i < len; i += 32) qarena[w + i] = (char)(f.rc[0] ? q[f.b[0] - 1 - i] : q[f.a[0] + i]);
+}
+
 }  // namespace
 
 void launch_extract(cudaStream_t s, bool write, const ah_amplicon* amps, uint64_t cap, const uint64_t* d_n,
@@ -151,9 +168,47 @@ ah_status extract(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_
   }
   AH_CUDA(ctx, cudaGetLastError());
   a->arena_bytes = bytes;
+  a->trim = trim;
+  dfree(ctx, a->d_qarena);
+  a->d_qarena = nullptr;
   dfree(ctx, tot);
   dfree(ctx, base);
   return AH_OK;
 }
 
 }  // namespace ah
+
+using namespace ah;
+
+extern "C" {
+
+ah_status ah_extract_qualities(ah_ctx* ctx, const ah_quals* q, const ah_batch* b, const ah_primers* p,
+                               const ah_hits* h, ah_amplicons* a) {
+  if (!ctx || !q || !b || !p || !h || !a) return fail(ctx, AH_EINVAL, "ah_extract_qualities: NULL argument");
+  if (!a->d_field_off) return fail(ctx, AH_EINVAL, "ah_extract_qualities: run ah_extract_barcodes first");
+  bool same = q->n_records == b->n_records;
+  for (uint32_t r = 0; same && r < b->n_records; ++r) same = q->h_off[r + 1] - q->h_off[r] == b->h_rec_len[r];
+  if (!same) return fail(ctx, AH_EINVAL, "ah_extract_qualities: the qualities do not belong to this batch");
+  cudaSetDevice(ctx->device);
+  dfree(ctx, a->d_qarena);
+  a->d_qarena = nullptr;
+  ah_status st = dalloc(ctx, &a->d_qarena, a->arena_bytes + 1);
+  if (st) return st;
+  if (a->n) {
+    k_extract_qual<<<(unsigned)((a->n + 7) / 8), 256, 0, ctx->stream>>>(a->d, a->n, h->d, b->rec_len, p->d_plen, a->trim,
+                                                                        q->d_qual, q->d_off, a->d_field_off, a->d_qarena);
+    launched(ctx);
+  }
+  AH_CUDA(ctx, cudaGetLastError());
+  return AH_OK;
+}
+
+ah_status ah_amplicons_qual_copy(const ah_amplicons* a, char* out, uint64_t cap) {
+  if (!a) return AH_EINVAL;
+  if (!a->d_qarena) return fail(a->ctx, AH_EINVAL, "ah_amplicons_qual_copy: no qualities extracted");
+  if (cap < a->arena_bytes) return fail(a->ctx, AH_EOVERFLOW, "ah_amplicons_qual_copy: need %llu bytes",
+                                        (unsigned long long)a->arena_bytes);
+  return copy_to_host(a->ctx, out, a->d_qarena, a->arena_bytes);
+}
+
+}  // extern "C"

@@ -14,7 +14,7 @@
 #include "ah_internal.h"
 
 struct ah_fasta {
-  std::vector<std::string> names;  // header lines without '>' and trailing '\r'
+  std::vector<std::string> names;  // header lines without '>' (or '@') and trailing '\r'
 };
 
 namespace ah {
@@ -303,6 +303,172 @@ __global__ void k_fa_names(const uint8_t* __restrict__ t, const uint64_t* __rest
   for (uint64_t i = threadIdx.x & 31; i < len; i += 32) names[name_off[r] + i] = t[hdr_pos[r] + i];
 }
 
+// ------------------------------------------------------------------------------------------
+// FASTQ (four lines per record: '@' header, bases, '+' line, qualities).  The line of a byte is the
+// number of line breaks before it, so a tile needs only the line breaks before it (an exclusive
+// sum) and no state machine; line 4r is record r's header, 4r + 1 its bases, 4r + 3 its qualities
+// ('\r' dropped from all three).
+
+// the thread's 64 bytes as four segments with their line-break and '\r' masks
+__device__ __forceinline__ void fq_load(const uint8_t* __restrict__ t, uint64_t n, Seg* g) {
+  const uint64_t p = (uint64_t)blockIdx.x * kFaTile + (uint64_t)threadIdx.x * (kFaSegs * kFaBytes);
+  const bool whole = p + kFaSegs * kFaBytes <= n && (((uint64_t)(uintptr_t)t) & 15) == 0;
+  uint4 x[kFaSegs];
+  if (whole) {
+    const uint4* v = reinterpret_cast<const uint4*>(t + p);
+#pragma unroll
+    for (int q = 0; q < kFaSegs; ++q) x[q] = __ldg(v + q);
+  }
+#pragma unroll
+  for (int q = 0; q < kFaSegs; ++q) {
+    uint32_t w[4];
+    int len = kFaBytes;
+    if (whole) {
+      w[0] = x[q].x, w[1] = x[q].y, w[2] = x[q].z, w[3] = x[q].w;
+    } else {
+      const uint64_t p0 = min(n, p + (uint64_t)q * kFaBytes), p1 = min(n, p0 + kFaBytes);
+      len = (int)(p1 - p0);
+      w[0] = w[1] = w[2] = w[3] = 0;
+#pragma unroll
+      for (int j = 0; j < kFaBytes; ++j)
+        if (j < len) w[j >> 2] |= (uint32_t)t[p0 + j] << (8 * (j & 3));
+    }
+    Seg& s = g[q];
+    s.len = len;
+    s.w0 = w[0], s.w1 = w[1], s.w2 = w[2], s.w3 = w[3];
+    s.nl = s.blank = s.gt = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      s.nl |= bytes_eq(w[k], 0x0a0a0a0au) << (4 * k);
+      s.blank |= bytes_eq(w[k], 0x0d0d0d0du) << (4 * k);
+    }
+    const uint32_t valid = len >= 32 ? 0xffffffffu : ((1u << len) - 1u);
+    s.nl &= valid, s.blank &= valid;
+  }
+}
+
+// pass 1: line breaks per tile
+__global__ void __launch_bounds__(kFaThreads) k_fq_lines(const uint8_t* __restrict__ t, uint64_t n,
+                                                         uint32_t* __restrict__ tile_nl) {
+  Seg g[kFaSegs];
+  fq_load(t, n, g);
+  uint32_t c = 0;
+#pragma unroll
+  for (int q = 0; q < kFaSegs; ++q) c += __popc(g[q].nl);
+  uint32_t e0, e1, t0, t1;
+  block_exclusive_sums(c, 0, &e0, &e1, &t0, &t1);
+  if (threadIdx.x == 0) tile_nl[blockIdx.x] = t0;
+}
+
+// passes 2 and 3 from each tile's line number: counts of bases, qualities and headers per tile, or
+// (emit) the bases and qualities compacted and per record r: hdr_pos[r] (after '@'), hdr_end[r] (its
+// line break), seq_rank[r] and qual_rank[r] (bases and qualities before the record)
+template <bool emit>
+__global__ void __launch_bounds__(kFaThreads) k_fq_pass(const uint8_t* __restrict__ t, uint64_t n,
+                                                        const uint64_t* __restrict__ line_base,
+                                                        uint32_t* __restrict__ tile_seq, uint32_t* __restrict__ tile_qual,
+                                                        uint32_t* __restrict__ tile_hdr, uint32_t* __restrict__ bad,
+                                                        const uint64_t* __restrict__ seq_base,
+                                                        const uint64_t* __restrict__ qual_base, uint8_t* __restrict__ seq_out,
+                                                        uint8_t* __restrict__ qual_out, uint64_t* __restrict__ hdr_pos,
+                                                        uint64_t* __restrict__ hdr_end, uint64_t* __restrict__ seq_rank,
+                                                        uint64_t* __restrict__ qual_rank, uint64_t n_rec) {
+  __shared__ __align__(16) uint8_t st_seq[emit ? kFaTile + 32 : 16], st_qual[emit ? kFaTile + 32 : 16];
+  Seg g[kFaSegs];
+  fq_load(t, n, g);
+  const uint64_t p = (uint64_t)blockIdx.x * kFaTile + (uint64_t)threadIdx.x * (kFaSegs * kFaBytes);
+  uint32_t c = 0;
+#pragma unroll
+  for (int q = 0; q < kFaSegs; ++q) c += __popc(g[q].nl);
+  uint32_t e_nl, e_x, t_nl, t_x;
+  block_exclusive_sums(c, 0, &e_nl, &e_x, &t_nl, &t_x);
+  const uint64_t line0 = line_base[blockIdx.x] + e_nl;
+  const bool start0 = p == 0 || (p < n && t[p - 1] == '\n');  // the thread's first byte starts a line
+  // one walk over the runs between line breaks; emit = false counts, emit = true writes
+  auto walk = [&](bool write, uint32_t* ns, uint32_t* nq, uint32_t* nh, uint32_t* nbad, uint32_t ls, uint32_t lq,
+                  uint64_t sb, uint64_t qb) {
+    uint64_t line = line0;
+    bool at_start = start0;
+    for (int q = 0; q < kFaSegs; ++q) {
+      const Seg& s = g[q];
+      const uint64_t p0 = p + (uint64_t)q * kFaBytes;
+      uint32_t rest = s.nl;
+      int a = 0;
+      for (;;) {
+        const int stop = rest ? __ffs(rest) - 1 : s.len;  // run [a, stop), then a line break at stop
+        if (stop > a || (rest && stop == a)) {
+          const uint32_t run = (stop >= 32 ? 0xffffffffu : ((1u << stop) - 1u)) & ~((1u << a) - 1u);
+          const uint32_t kind = (uint32_t)(line & 3);
+          if (kind == 1 || kind == 3) {
+            const uint32_t m = run & ~s.blank;
+            if (kind == 1) {
+              *ns += __popc(m);
+              if (write)
+                for (uint32_t x = m; x; x &= x - 1) st_seq[ls++] = s.at(__ffs(x) - 1);
+            } else {
+              *nq += __popc(m);
+              if (write)
+                for (uint32_t x = m; x; x &= x - 1) st_qual[lq++] = s.at(__ffs(x) - 1);
+            }
+          } else if (kind == 0 && at_start && stop > a) {  // a non-empty header line starts here
+            if (s.at(a) == '@') {
+              ++*nh;
+              if (write && (line >> 2) < n_rec) {  // records past n_rec are malformed text: caught on the host
+                hdr_pos[line >> 2] = p0 + a + 1;
+                seq_rank[line >> 2] = sb + ls;
+                qual_rank[line >> 2] = qb + lq;
+              }
+            } else {
+              ++*nbad;
+            }
+          }
+          if (kind == 0 && rest && write && (line >> 2) < n_rec) hdr_end[line >> 2] = p0 + stop;
+        }
+        if (!rest) {
+          if (stop > a) at_start = false;
+          break;
+        }
+        rest &= rest - 1;
+        a = stop + 1;
+        ++line;
+        at_start = true;
+      }
+    }
+    return make_uint2(ls, lq);
+  };
+  uint32_t ns = 0, nq = 0, nh = 0, nb = 0;
+  walk(false, &ns, &nq, &nh, &nb, 0, 0, 0, 0);
+  uint32_t e_seq, e_qual, t_seq, t_qual;
+  block_exclusive_sums(ns, nq, &e_seq, &e_qual, &t_seq, &t_qual);
+  if (!emit) {
+    uint32_t e_h, e_b, t_h, t_b;
+    block_exclusive_sums(nh, nb, &e_h, &e_b, &t_h, &t_b);
+    if (threadIdx.x == 0) {
+      tile_seq[blockIdx.x] = t_seq, tile_qual[blockIdx.x] = t_qual, tile_hdr[blockIdx.x] = t_h;
+      if (t_b) atomicAdd(bad, t_b);
+    }
+    return;
+  }
+  const uint64_t sbase = seq_base[blockIdx.x], qbase = qual_base[blockIdx.x];
+  const uint32_t slead = (uint32_t)(sbase & 15), qlead = (uint32_t)(qbase & 15);
+  uint32_t d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+  walk(true, &d0, &d1, &d2, &d3, slead + e_seq, qlead + e_qual, sbase - slead, qbase - qlead);
+  __syncthreads();
+  // out[base, base + count) from staged[lead, lead + count) in aligned 16-byte units
+  auto copy_out = [&](uint8_t* out, const uint8_t* st, uint64_t base, uint32_t lead, uint32_t cnt) {
+    uint8_t* dst = out + (base - lead);
+    const uint32_t end = lead + cnt, full_lo = lead ? 16u : 0u, full_hi = end & ~15u;
+    for (uint32_t u = full_lo + 16u * threadIdx.x; u < full_hi; u += 16u * kFaThreads)
+      *reinterpret_cast<uint4*>(dst + u) = *reinterpret_cast<const uint4*>(st + u);
+    if (threadIdx.x < 32) {
+      for (uint32_t i = lead + threadIdx.x; i < min(full_lo, end); i += 32) dst[i] = st[i];
+      for (uint32_t i = max(full_hi, full_lo) + threadIdx.x; i < end; i += 32) dst[i] = st[i];
+    }
+  };
+  copy_out(seq_out, st_seq, sbase, slead, t_seq);
+  copy_out(qual_out, st_qual, qbase, qlead, t_qual);
+}
+
 uint32_t host_apply(uint32_t f, uint32_t s) { return (f >> (2 * s)) & 3u; }
 
 }  // namespace
@@ -471,6 +637,182 @@ ah_status ah_fasta_pack_into(ah_ctx* ctx, const char* text, uint64_t n_bytes, ah
     return fail(ctx, AH_EINVAL, "ah_fasta_pack_into: bad arguments");
   if (names_out) *names_out = nullptr;
   return fasta_pack(ctx, text, n_bytes, nullptr, batch, nullptr, names_out);
+}
+
+ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint32_t* genome_ids,
+                        ah_batch** batch_out, ah_quals** quals_out, ah_fasta** names_out) {
+  if (!ctx || !text || !batch_out || !quals_out || n_bytes == 0) return fail(ctx, AH_EINVAL, "ah_fastq_pack: bad arguments");
+  *batch_out = nullptr;
+  *quals_out = nullptr;
+  if (names_out) *names_out = nullptr;
+  cudaSetDevice(ctx->device);
+  cudaPointerAttributes pa;
+  const bool on_device = cudaPointerGetAttributes(&pa, text) == cudaSuccess &&
+                         (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  ah_status st = AH_OK;
+  const uint8_t* t = (const uint8_t*)text;
+  uint8_t *staged = nullptr, *seq = nullptr, *qual = nullptr;
+  const uint64_t n_tiles = (n_bytes + kFaTile - 1) / kFaTile;
+  uint32_t *tile_nl = nullptr, *tile_seq = nullptr, *tile_qual = nullptr, *tile_hdr = nullptr, *bad = nullptr;
+  uint64_t *line_base = nullptr, *seq_base = nullptr, *qual_base = nullptr, *hdr_base = nullptr;
+  uint64_t *hdr_pos = nullptr, *hdr_end = nullptr, *seq_rank = nullptr, *qual_rank = nullptr;
+  ah_quals* q = nullptr;
+  auto cleanup = [&] {
+    for (void* x : {(void*)staged, (void*)seq, (void*)tile_nl, (void*)tile_seq, (void*)tile_qual, (void*)tile_hdr,
+                    (void*)bad, (void*)line_base, (void*)seq_base, (void*)qual_base, (void*)hdr_base, (void*)hdr_pos,
+                    (void*)hdr_end, (void*)seq_rank, (void*)qual_rank})
+      dfree(ctx, x);
+  };
+  do {
+    if (!on_device) {
+      if ((st = dalloc(ctx, &staged, n_bytes))) break;
+      if (cudaMemcpyAsync(staged, text, n_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+        st = fail(ctx, AH_ECUDA, "ah_fastq_pack: copy failed");
+        break;
+      }
+      t = staged;
+    }
+    if ((st = dalloc(ctx, &tile_nl, n_tiles)) || (st = dalloc(ctx, &tile_seq, n_tiles)) ||
+        (st = dalloc(ctx, &tile_qual, n_tiles)) || (st = dalloc(ctx, &tile_hdr, n_tiles)) || (st = dalloc(ctx, &bad, 1)) ||
+        (st = dalloc(ctx, &line_base, n_tiles + 1)) || (st = dalloc(ctx, &seq_base, n_tiles + 1)) ||
+        (st = dalloc(ctx, &qual_base, n_tiles + 1)) || (st = dalloc(ctx, &hdr_base, n_tiles + 1)))
+      break;
+    if (cudaMemsetAsync(bad, 0, 4, ctx->stream) != cudaSuccess) {
+      st = fail(ctx, AH_ECUDA, "ah_fastq_pack: memset failed");
+      break;
+    }
+    k_fq_lines<<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, tile_nl);
+    launched(ctx);
+    if ((st = exclusive_scan_u32(ctx, tile_nl, line_base, n_tiles))) break;
+    k_fq_pass<false><<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, line_base, tile_seq, tile_qual,
+                                                                        tile_hdr, bad, nullptr, nullptr, nullptr, nullptr,
+                                                                        nullptr, nullptr, nullptr, nullptr, 0);
+    launched(ctx);
+    uint64_t total_seq = 0, total_qual = 0, n_rec = 0;
+    uint32_t h_bad = 0;
+    if ((st = exclusive_scan_u32(ctx, tile_seq, seq_base, n_tiles)) ||
+        (st = exclusive_scan_u32(ctx, tile_qual, qual_base, n_tiles)) ||
+        (st = exclusive_scan_u32(ctx, tile_hdr, hdr_base, n_tiles)) || (st = read_u64(ctx, seq_base + n_tiles, &total_seq)) ||
+        (st = read_u64(ctx, qual_base + n_tiles, &total_qual)) || (st = read_u64(ctx, hdr_base + n_tiles, &n_rec)))
+      break;
+    if (cudaMemcpy(&h_bad, bad, 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      st = fail(ctx, AH_ECUDA, "ah_fastq_pack: status read failed");
+      break;
+    }
+    if (n_rec == 0 || h_bad || n_rec > 0xffffffffull) {
+      st = fail(ctx, AH_EINVAL, "ah_fastq_pack: not FASTQ (every record is four lines, the first starting with '@')");
+      break;
+    }
+    if ((st = dalloc(ctx, &seq, total_seq + 16)) || (st = dalloc(ctx, &qual, total_qual + 16)) ||
+        (st = dalloc(ctx, &hdr_pos, n_rec)) || (st = dalloc(ctx, &hdr_end, n_rec)) ||
+        (st = dalloc(ctx, &seq_rank, n_rec)) || (st = dalloc(ctx, &qual_rank, n_rec)))
+      break;
+    std::vector<uint64_t> fill(n_rec, n_bytes), none(n_rec, ~0ull);
+    AH_CUDA(ctx, cudaMemcpyAsync(hdr_end, fill.data(), n_rec * 8, cudaMemcpyHostToDevice, ctx->stream));
+    AH_CUDA(ctx, cudaMemcpyAsync(hdr_pos, none.data(), n_rec * 8, cudaMemcpyHostToDevice, ctx->stream));
+    k_fq_pass<true><<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, line_base, nullptr, nullptr, nullptr,
+                                                                       nullptr, seq_base, qual_base, seq, qual, hdr_pos,
+                                                                       hdr_end, seq_rank, qual_rank, n_rec);
+    launched(ctx);
+    std::vector<uint64_t> h_pos(n_rec), h_end(n_rec), h_srank(n_rec + 1), h_qrank(n_rec + 1);
+    AH_CUDA(ctx, cudaMemcpyAsync(h_pos.data(), hdr_pos, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    AH_CUDA(ctx, cudaMemcpyAsync(h_end.data(), hdr_end, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    AH_CUDA(ctx, cudaMemcpyAsync(h_srank.data(), seq_rank, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    AH_CUDA(ctx, cudaMemcpyAsync(h_qrank.data(), qual_rank, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    h_srank[n_rec] = total_seq;
+    h_qrank[n_rec] = total_qual;
+    const uint32_t R = (uint32_t)n_rec;
+    bool ok = true;
+    for (uint32_t r = 0; r < R && ok; ++r)
+      ok = h_pos[r] != ~0ull && h_srank[r + 1] - h_srank[r] == h_qrank[r + 1] - h_qrank[r];
+    if (!ok) {
+      st = fail(ctx, AH_EINVAL, "ah_fastq_pack: a record lacks its header line or its qualities differ in length from its bases");
+      break;
+    }
+    std::vector<uint64_t> offs(R + 1);
+    for (uint32_t r = 0; r <= R; ++r) offs[r] = h_srank[r] - h_srank[0];
+    if ((st = ah_pack_batch_device(ctx, R, seq + h_srank[0], offs.data(), genome_ids, batch_out))) break;
+    q = new ah_quals();
+    q->ctx = ctx;
+    q->n_records = R;
+    q->h_off.resize(R + 1);
+    for (uint32_t r = 0; r <= R; ++r) q->h_off[r] = h_qrank[r] - h_qrank[0];
+    if ((st = dalloc(ctx, &q->d_off, R + 1))) break;
+    AH_CUDA(ctx, cudaMemcpyAsync(q->d_off, q->h_off.data(), (R + 1) * 8, cudaMemcpyHostToDevice, ctx->stream));
+    if (h_qrank[0] == 0) {  // keep the buffer itself
+      q->d_qual = qual;
+      qual = nullptr;
+    } else {
+      if ((st = dalloc(ctx, &q->d_qual, q->h_off[R] + 16))) break;
+      AH_CUDA(ctx, cudaMemcpyAsync(q->d_qual, qual + h_qrank[0], q->h_off[R], cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    if (names_out) {
+      ah_fasta* f = new ah_fasta();
+      f->names.resize(R);
+      std::vector<uint64_t> name_off(R + 1, 0);
+      for (uint32_t r = 0; r < R; ++r) name_off[r + 1] = name_off[r] + (h_end[r] - h_pos[r]);
+      std::vector<char> all(name_off[R] + 1);
+      if (on_device) {
+        uint64_t* d_off = nullptr;
+        uint8_t* d_names = nullptr;
+        st = dalloc(ctx, &d_off, R + 1);
+        if (!st) st = dalloc(ctx, &d_names, name_off[R] + 1);
+        if (!st) {
+          cudaMemcpyAsync(d_off, name_off.data(), (R + 1) * 8, cudaMemcpyHostToDevice, ctx->stream);
+          k_fa_names<<<(R + 7) / 8, 256, 0, ctx->stream>>>(t, hdr_pos, d_off, R, d_names);
+          launched(ctx);
+          cudaMemcpyAsync(all.data(), d_names, name_off[R], cudaMemcpyDeviceToHost, ctx->stream);
+          if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = fail(ctx, AH_ECUDA, "ah_fastq_pack: names");
+        }
+        dfree(ctx, d_off);
+        dfree(ctx, d_names);
+      } else {
+        for (uint32_t r = 0; r < R; ++r) memcpy(all.data() + name_off[r], text + h_pos[r], h_end[r] - h_pos[r]);
+      }
+      for (uint32_t r = 0; r < R; ++r) {
+        std::string nm(all.data() + name_off[r], name_off[r + 1] - name_off[r]);
+        while (!nm.empty() && nm.back() == '\r') nm.pop_back();
+        f->names[r] = std::move(nm);
+      }
+      if (st) {
+        delete f;
+        break;
+      }
+      *names_out = f;
+    }
+  } while (false);
+  if (qual) dfree(ctx, qual);
+  cleanup();
+  if (st) {
+    if (*batch_out) ah_batch_free(*batch_out);
+    *batch_out = nullptr;
+    ah_quals_free(q);
+    return st;
+  }
+  *quals_out = q;
+  return AH_OK;
+}
+
+uint32_t ah_quals_count(const ah_quals* q) { return q ? q->n_records : 0; }
+
+ah_status ah_quals_copy(const ah_quals* q, char* out, uint64_t cap, uint64_t* offsets_out) {
+  if (!q || !offsets_out) return AH_EINVAL;
+  memcpy(offsets_out, q->h_off.data(), q->h_off.size() * sizeof(uint64_t));
+  if (!out) return AH_OK;
+  if (cap < q->h_off.back()) return fail(q->ctx, AH_EOVERFLOW, "ah_quals_copy: need %llu bytes",
+                                         (unsigned long long)q->h_off.back());
+  return copy_to_host(q->ctx, out, q->d_qual, q->h_off.back());
+}
+
+void ah_quals_free(ah_quals* q) {
+  if (!q) return;
+  if (q->ctx) {
+    dfree(q->ctx, q->d_qual);
+    dfree(q->ctx, q->d_off);
+  }
+  delete q;
 }
 
 uint32_t ah_fasta_count(const ah_fasta* f) { return f ? (uint32_t)f->names.size() : 0; }

@@ -152,6 +152,14 @@ struct ah_primers {
   ah::GenPattern* d_gen = nullptr;     // the patterns as the generic scan kernel reads them
 };
 
+struct ah_quals {
+  ah_ctx* ctx = nullptr;
+  uint32_t n_records = 0;
+  uint8_t* d_qual = nullptr;      // every record's qualities back to back
+  uint64_t* d_off = nullptr;      // n_records + 1
+  std::vector<uint64_t> h_off;
+};
+
 struct ah_hits {
   ah_ctx* ctx = nullptr;
   uint64_t n = 0;
@@ -168,6 +176,8 @@ struct ah_amplicons {
   char* d_arena = nullptr;
   uint64_t arena_bytes = 0;
   uint64_t* d_field_off = nullptr;     // 5 n + 1 when extracted
+  int trim = 0;                        // of the last extraction
+  char* d_qarena = nullptr;            // qualities of field 0 at its arena offsets (ah_extract_qualities)
 };
 
 namespace ah {

@@ -83,3 +83,27 @@ def test_amplicon_fasta_paper_example_shape(ah):
                    b".fprimer=CAG.rprimer=TTA.fb=.rb=\nCC\n")
     recs = [(0, 12344, 13567, 0, 60.4249, tuple(fields[0:5])), (0, 99, 150, 1, float("nan"), tuple(fields[5:10]))]
     assert oracle.amplicon_fasta(recs, ["seqid some text"], ["GCF_XXXX.fa"], True) == got
+
+
+@pytest.mark.parametrize("seed", [3, 8])
+def test_amplicon_fastq_matches_reference(ah, seed):
+    """FASTQ output: the FASTA header with '@', the sequence, '+' and the qualities of field 0."""
+    wl, amps, tms, fields = _inputs(seed)
+    abi = np.zeros(len(amps), dtype=ah.AMP_DTYPE)
+    for k in ("record", "start", "end", "orient", "hit_i", "hit_j"):
+        abi[k] = amps[k]
+    abi["tm"] = tms
+    arena = b"".join(b"".join(f) for f in fields)
+    off = np.cumsum([0] + [len(x) for f in fields for x in f]).astype(np.uint64)
+    # qualities: any printable bytes of the amplicon's length, at field 0's offsets
+    rng = np.random.default_rng(seed)
+    q = [bytes(rng.integers(33, 74, len(f[0]), dtype=np.uint8)) for f in fields]
+    qarena = bytearray(len(arena))
+    for m, f in enumerate(fields):
+        qarena[int(off[5 * m]):int(off[5 * m]) + len(f[0])] = q[m]
+    names = ["rec%d x" % r for r in range(wl.n_records)]
+    got = ah.ah_amplicons_fastq(abi, arena, bytes(qarena), off, names, None, True)
+    recs = [(int(a["record"]), int(a["start"]), int(a["end"]), int(a["orient"]), float(t), f, qq)
+            for a, t, f, qq in zip(amps, tms, fields, q)]
+    assert got == oracle.amplicon_fastq(recs, names, None, True)
+    assert got.count(b"\n+\n") == len(amps)

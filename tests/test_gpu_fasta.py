@@ -137,3 +137,114 @@ def test_fasta_pipeline_equals_direct_packing(ah_ctx):
     compare.assert_same_hits(out, ref)
     compare.assert_same_amplicons(out, ref, filtered=wl.tm.min_tm is not None)
     compare.assert_same_sequences(out, ref)
+
+
+def _random_fastq(seed: int, n_records: int, crlf: bool) -> bytes:
+    st = synth.Stream(synth.make_key(seed, 4322, 0))
+    nl = b"\r\n" if crlf else b"\n"
+    out = bytearray()
+    for r in range(n_records):
+        name = "read%d " % r + "".join(st.choice("abc XYZ:0123/") for _ in range(st.choice([3, 40, 6000])))
+        L = st.choice([0, 1, 100, 150, 5000, 40000])
+        seq = "".join(st.choice("ACGTACGTNacgt") for _ in range(L))
+        qual = "".join(chr(st.randint(33, 74)) for _ in range(L))   # may start with '@' or '+'
+        out += b"@" + name.encode() + nl + seq.encode() + nl + (b"+" if st.randint(0, 1) else b"+" + name.encode()) + nl
+        out += qual.encode() + nl
+    if st.randint(0, 1):
+        out += nl + nl   # empty lines after the last record
+    elif out.endswith(nl):
+        out = out[: -len(nl)]
+    return bytes(out)
+
+
+@pytest.mark.parametrize("seed,n_records,crlf,on_device", [(1, 1, False, False), (2, 30, True, False),
+                                                           (3, 50, False, True), (4, 9, True, True)])
+def test_fastq_pack_matches_oracle(ah_ctx, seed, n_records, crlf, on_device):
+    import torch
+
+    ah, ctx = ah_ctx
+    text = _random_fastq(seed, n_records, crlf)
+    names, seqs, quals = oracle.parse_fastq(text)
+    assert len(names) == n_records
+    if on_device:
+        d = torch.frombuffer(bytearray(text), dtype=torch.uint8).cuda()
+        batch, q, got_names = ah.ah_fastq_pack(ctx, d.data_ptr(), n_bytes=len(text))
+    else:
+        batch, q, got_names = ah.ah_fastq_pack(ctx, text)
+    lens = np.array([len(s) for s in seqs], dtype=np.uint64)
+    ref = ah.ah_pack_batch(ctx, np.frombuffer(b"".join(seqs) or b"\0", dtype=np.uint8),
+                           np.concatenate([[0], np.cumsum(lens)]).astype(np.int64))
+    try:
+        assert got_names == names
+        assert _batch_bytes(ah, batch) == _batch_bytes(ah, ref)
+        got_q, off = ah.ah_quals_copy(q)
+        assert got_q == b"".join(quals)
+        assert list(off) == list(np.concatenate([[0], np.cumsum([len(x) for x in quals])]))
+    finally:
+        ah.ah_batch_free(batch)
+        ah.ah_batch_free(ref)
+        ah.ah_quals_free(q)
+
+
+@pytest.mark.parametrize("text", [b"ACGT\nACGT\n+\nIIII\n", b"@r\nACGT\n+\nIII\n",
+                                  b"@r\nACGT\n+\nIIII\nnot a header\nAC\n+\nII\n"])
+def test_fastq_pack_refuses_malformed(ah_ctx, text):
+    ah, ctx = ah_ctx
+    with pytest.raises(ah.AhError) as e:
+        ah.ah_fastq_pack(ctx, text)
+    assert e.value.status == ah.AH_EINVAL
+
+
+@pytest.mark.parametrize("trim", [False, True])
+def test_fastq_qualities_follow_the_amplicons(ah_ctx, trim):
+    """The whole path on FASTQ input: the sites and amplicons of the oracle, and every kept amplicon's
+    qualities those of its sequence field (reversed for RF); then the FASTQ writer's records."""
+    from paper_2511_00170_gb300.pipeline import Engine, Params
+    from tests import compare
+
+    wl = synth.random_small(41 + trim, n_records=5, len_lo=500, len_hi=20000, n_pairs=2, plant=3, trim=trim)
+    wl.orient_mask = 15
+    st = synth.Stream(synth.make_key(7, 4323, 0))
+    quals = []
+    lines = []
+    for r in range(wl.n_records):
+        s = wl.seq[wl.offsets[r]:wl.offsets[r + 1]].tobytes()
+        qv = bytes(st.randint(33, 74) for _ in range(len(s)))
+        quals.append(qv)
+        lines += [b"@genome_%d" % r, s, b"+", qv]
+    text = b"\n".join(lines) + b"\n"
+    eng = Engine(0)
+    try:
+        from paper_2511_00170_gb300 import ah
+
+        batch, q, names = ah.ah_fastq_pack(eng.ctx, text)
+        p = Params.from_workload(wl)
+        hits, amps = eng.step(batch, p, copy_out=False)
+        try:
+            ah.ah_extract_qualities(eng.ctx, q, batch, eng.primers(p), hits, amps)
+            ah.ah_ctx_synchronize(eng.ctx)
+            from paper_2511_00170_gb300.pipeline import Output
+
+            h = ah.ah_hits_copy(hits)
+            a = ah.ah_amplicons_copy(amps)
+            arena, off = ah.ah_amplicons_seq_copy(amps)
+            qarena = ah.ah_amplicons_qual_copy(amps, len(arena))
+            out = Output(h, a, arena, off)
+        finally:
+            ah.ah_hits_free(hits)
+            ah.ah_amplicons_free(amps)
+            ah.ah_quals_free(q)
+            ah.ah_batch_free(batch)
+    finally:
+        eng.close()
+    ref = oracle.run(wl)
+    compare.assert_same_hits(out, ref)
+    compare.assert_same_sequences(out, ref)
+    kept = ref.amps[ref.keep]
+    ref_q = dict(zip(compare.oracle_amp_keys(ref.hits, kept), oracle.amplicon_qualities(wl, ref.hits, kept, quals)))
+    keys = compare.gpu_amp_keys(out)
+    assert len(keys) == len(kept) > 0
+    for m, k in enumerate(keys):
+        assert qarena[int(off[5 * m]):int(off[5 * m + 1])] == ref_q[k], k
+    fq = ah.ah_amplicons_fastq(a, arena, qarena, off, names)
+    assert fq.count(b"\n+\n") == len(a)

@@ -20,3 +20,23 @@ def test_parse_fasta_hand_example():
 
 def test_parse_fasta_no_records():
     assert oracle.parse_fasta(b"ACGT\nACGT\n") == ([], [])
+
+
+def test_parse_fastq_hand_example():
+    text = (b"@read1 first\r\n"
+            b"ACGTN\r\n"
+            b"+\r\n"
+            b"IIII#\r\n"
+            b"@read2\n"
+            b"\n"
+            b"+read2\n"
+            b"\n"
+            b"@read3\n"
+            b"GG\n"
+            b"+\n"
+            b"@I\n"
+            b"\n\n")
+    names, seqs, quals = oracle.parse_fastq(text)
+    assert names == ["read1 first", "read2", "read3"]
+    assert seqs == [b"ACGTN", b"", b"GG"]
+    assert quals == [b"IIII#", b"", b"@I"]   # a quality line may start with '@'
