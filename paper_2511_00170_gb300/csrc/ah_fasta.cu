@@ -246,7 +246,9 @@ __global__ void __launch_bounds__(kFaThreads) k_fa_pass(const uint8_t* __restric
                                                         const uint64_t* __restrict__ seq_base,
                                                         const uint64_t* __restrict__ hdr_base, uint8_t* __restrict__ out,
                                                         uint64_t* __restrict__ hdr_pos, uint64_t* __restrict__ hdr_end,
-                                                        uint64_t* __restrict__ seq_rank) {
+                                                        uint64_t* __restrict__ seq_rank, uint64_t pos_off, uint64_t seq_off,
+                                                        uint64_t hdr_off) {
+  // (a chunk of the text: positions, bases and records before it are pos_off, seq_off, hdr_off)
   __shared__ __align__(16) uint8_t staged[emit ? kFaTile + 32 : 16];  // the tile's sequence bytes, compacted
   Seg g[kFaSegs];
   load_segs(t, n, g);
@@ -268,17 +270,17 @@ __global__ void __launch_bounds__(kFaThreads) k_fa_pass(const uint8_t* __restric
     if (threadIdx.x == 0) tile_seq[blockIdx.x] = t_seq, tile_hdr[blockIdx.x] = t_hdr;
     return;
   }
-  const uint64_t base = seq_base[blockIdx.x];
+  const uint64_t base = seq_off + seq_base[blockIdx.x];
   const uint32_t lead = (uint32_t)(base & 15);  // staged[lead + i] goes to out[base + i]
   uint32_t local = lead + e_seq;                // this thread's first sequence byte, staged
-  uint64_t rec = hdr_base[blockIdx.x] + e_hdr;  // headers started before this thread's bytes
+  uint64_t rec = hdr_off + hdr_base[blockIdx.x] + e_hdr;  // headers started before this thread's bytes
   uint32_t cs = 0, ch = 0;
   s = s0;
 #pragma unroll
   for (int q = 0; q < kFaSegs; ++q) {
     uint64_t p0, p1;
     seg_span(n, q, &p0, &p1);
-    s = seg_pass<true>(g[q], p0, s, &cs, &ch, staged, &local, &rec, base - lead, hdr_pos, hdr_end, seq_rank);
+    s = seg_pass<true>(g[q], pos_off + p0, s, &cs, &ch, staged, &local, &rec, base - lead, hdr_pos, hdr_end, seq_rank);
   }
   __syncthreads();
   // out[base, base + t_seq) from staged[lead, lead + t_seq): whole aligned 16-byte units as uint4,
@@ -491,50 +493,123 @@ ah_status fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint
   ah_status st = AH_OK;
   const uint8_t* t = (const uint8_t*)text;
   uint8_t* staged = nullptr;
-  if (!on_device) {
-    if ((st = dalloc(ctx, &staged, n_bytes))) return st;
-    AH_CUDA(ctx, cudaMemcpyAsync(staged, text, n_bytes, cudaMemcpyHostToDevice, ctx->stream));
-    t = staged;
-  }
   const uint64_t n_tiles = (n_bytes + kFaTile - 1) / kFaTile;
-  uint8_t *tile_f = nullptr, *tile_entry = nullptr, *compact = nullptr;
+  // host text is parsed in chunks as it lands: a copy stream moves chunk c + 1 while the passes run
+  // on chunk c (each chunk's passes need only the entry state and totals of the chunks before it)
+  const uint64_t chunk_tiles = on_device ? std::max<uint64_t>(1, n_tiles) : (kChunkBases / kFaTile);
+  const uint64_t n_chunks = (n_tiles + chunk_tiles - 1) / chunk_tiles;
+  uint8_t *tile_f = nullptr, *tile_entry = nullptr, *compact = nullptr, *h_f = nullptr, *h_entry = nullptr;
   uint32_t *tile_seq = nullptr, *tile_hdr = nullptr;
   uint64_t *seq_base = nullptr, *hdr_base = nullptr, *hdr_pos = nullptr, *hdr_end = nullptr, *seq_rank = nullptr;
-  std::vector<uint8_t> h_f(n_tiles), h_entry(n_tiles);
+  uint64_t hdr_cap = 0;
+  cudaStream_t cs = nullptr;
+  std::vector<cudaEvent_t> landed;
   uint64_t total_seq = 0, total_hdr = 0;
   auto cleanup = [&] {
+    if (cs) {
+      cudaStreamSynchronize(cs);
+      cudaStreamDestroy(cs);
+    }
+    for (cudaEvent_t e : landed) cudaEventDestroy(e);
+    if (h_f) cudaFreeHost(h_f);
+    if (h_entry) cudaFreeHost(h_entry);
     for (void* p : {(void*)staged, (void*)tile_f, (void*)tile_entry, (void*)compact, (void*)tile_seq,
                     (void*)tile_hdr, (void*)seq_base, (void*)hdr_base, (void*)hdr_pos, (void*)hdr_end, (void*)seq_rank})
       dfree(ctx, p);
   };
+  // record arrays with room for `need` records, contents kept, a missing header end read as the end
+  // of the text
+  auto grow = [&](uint64_t need) -> ah_status {
+    if (need <= hdr_cap) return AH_OK;
+    const uint64_t cap = std::max<uint64_t>(need, std::max<uint64_t>(4096, 2 * hdr_cap));
+    uint64_t *np = nullptr, *ne = nullptr, *nr = nullptr;
+    ah_status e = AH_OK;
+    if ((e = dalloc(ctx, &np, cap)) || (e = dalloc(ctx, &ne, cap)) || (e = dalloc(ctx, &nr, cap + 1))) {
+      dfree(ctx, np), dfree(ctx, ne), dfree(ctx, nr);
+      return e;
+    }
+    std::vector<uint64_t> fill(cap - hdr_cap, n_bytes);
+    cudaMemcpyAsync(ne + hdr_cap, fill.data(), fill.size() * 8, cudaMemcpyHostToDevice, ctx->stream);
+    if (hdr_cap) {
+      cudaMemcpyAsync(np, hdr_pos, hdr_cap * 8, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaMemcpyAsync(ne, hdr_end, hdr_cap * 8, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaMemcpyAsync(nr, seq_rank, hdr_cap * 8, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    dfree(ctx, hdr_pos), dfree(ctx, hdr_end), dfree(ctx, seq_rank);
+    hdr_pos = np, hdr_end = ne, seq_rank = nr, hdr_cap = cap;
+    return cudaStreamSynchronize(ctx->stream) == cudaSuccess ? AH_OK : fail(ctx, AH_ECUDA, "ah_fasta_pack: grow");
+  };
   do {
     if ((st = dalloc(ctx, &tile_f, n_tiles)) || (st = dalloc(ctx, &tile_entry, n_tiles)) ||
         (st = dalloc(ctx, &tile_seq, n_tiles)) || (st = dalloc(ctx, &tile_hdr, n_tiles)) ||
-        (st = dalloc(ctx, &seq_base, n_tiles + 1)) || (st = dalloc(ctx, &hdr_base, n_tiles + 1)))
+        (st = dalloc(ctx, &seq_base, n_tiles + 1)) || (st = dalloc(ctx, &hdr_base, n_tiles + 1)) ||
+        (st = dalloc(ctx, &compact, n_bytes + 16)))
       break;
-    // pass 1, then the tiles' entry states chained on the host (one byte per 4 KiB)
-    k_fa_tiles<<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, tile_f);
-    launched(ctx);
-    if (cudaMemcpyAsync(h_f.data(), tile_f, n_tiles, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-      st = fail(ctx, AH_ECUDA, "ah_fasta_pack: tile pass failed");
+    if (cudaMallocHost(&h_f, chunk_tiles) != cudaSuccess || cudaMallocHost(&h_entry, chunk_tiles) != cudaSuccess) {
+      st = fail(ctx, AH_ENOMEM, "ah_fasta_pack: page-locked buffers");
       break;
     }
-    uint32_t s = FS_LS;
-    for (uint64_t i = 0; i < n_tiles; ++i) h_entry[i] = (uint8_t)s, s = host_apply(h_f[i], s);
-    if (cudaMemcpyAsync(tile_entry, h_entry.data(), n_tiles, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
-      st = fail(ctx, AH_ECUDA, "ah_fasta_pack: entry upload failed");
-      break;
+    if (!on_device) {
+      if ((st = dalloc(ctx, &staged, n_bytes + 16))) break;
+      cudaEvent_t ready;
+      if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) {
+        st = fail(ctx, AH_ECUDA, "ah_fasta_pack: copy stream");
+        break;
+      }
+      landed.push_back(ready);  // the buffer was allocated in the context stream's order
+      cudaEventRecord(ready, ctx->stream);
+      cudaStreamWaitEvent(cs, ready, 0);
+      for (uint64_t c = 0; c < n_chunks && !st; ++c) {
+        const uint64_t b0 = c * chunk_tiles * kFaTile, b1 = std::min(n_bytes, b0 + chunk_tiles * kFaTile);
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMemcpyAsync(staged + b0, text + b0, b1 - b0, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+            cudaEventRecord(e, cs) != cudaSuccess)
+          st = fail(ctx, AH_ECUDA, "ah_fasta_pack: copy");
+        landed.push_back(e);
+      }
+      if (st) break;
+      t = staged;
     }
-    // pass 2: counts per tile, then their exclusive sums
-    k_fa_pass<false><<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, tile_entry, tile_seq, tile_hdr,
-                                                                        nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                                        nullptr);
-    launched(ctx);
-    if ((st = exclusive_scan_u32(ctx, tile_seq, seq_base, n_tiles)) ||
-        (st = exclusive_scan_u32(ctx, tile_hdr, hdr_base, n_tiles)) || (st = read_u64(ctx, seq_base + n_tiles, &total_seq)) ||
-        (st = read_u64(ctx, hdr_base + n_tiles, &total_hdr)))
-      break;
+    uint32_t state = FS_LS;
+    for (uint64_t c = 0; c < n_chunks && !st; ++c) {
+      const uint64_t t0 = c * chunk_tiles, nt = std::min(chunk_tiles, n_tiles - t0);
+      const uint64_t b0 = t0 * kFaTile, nb = std::min(n_bytes, b0 + nt * kFaTile) - b0;
+      if (!on_device) cudaStreamWaitEvent(ctx->stream, landed[1 + c], 0);
+      // pass 1 on the chunk; its tiles' entry states chained on the host
+      k_fa_tiles<<<(unsigned)nt, kFaThreads, 0, ctx->stream>>>(t + b0, nb, tile_f + t0);
+      launched(ctx);
+      if (cudaMemcpyAsync(h_f, tile_f + t0, nt, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+          cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        st = fail(ctx, AH_ECUDA, "ah_fasta_pack: tile pass failed");
+        break;
+      }
+      for (uint64_t i = 0; i < nt; ++i) h_entry[i] = (uint8_t)state, state = host_apply(h_f[i], state);
+      if (cudaMemcpyAsync(tile_entry + t0, h_entry, nt, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+        st = fail(ctx, AH_ECUDA, "ah_fasta_pack: entry upload failed");
+        break;
+      }
+      // pass 2: counts per tile, their sums within the chunk, the chunk's totals
+      k_fa_pass<false><<<(unsigned)nt, kFaThreads, 0, ctx->stream>>>(t + b0, nb, tile_entry + t0, tile_seq + t0,
+                                                                      tile_hdr + t0, nullptr, nullptr, nullptr, nullptr,
+                                                                      nullptr, nullptr, 0, 0, 0);
+      launched(ctx);
+      uint64_t c_seq = 0, c_hdr = 0;
+      if ((st = exclusive_scan_u32(ctx, tile_seq + t0, seq_base + t0, nt)) ||
+          (st = exclusive_scan_u32(ctx, tile_hdr + t0, hdr_base + t0, nt)) ||
+          (st = read_u64(ctx, seq_base + t0 + nt, &c_seq)) || (st = read_u64(ctx, hdr_base + t0 + nt, &c_hdr)))
+        break;
+      if (c_hdr && (st = grow(total_hdr + c_hdr))) break;
+      // pass 3: the chunk's bases and headers at their places in the whole text
+      k_fa_pass<true><<<(unsigned)nt, kFaThreads, 0, ctx->stream>>>(t + b0, nb, tile_entry + t0, nullptr, nullptr,
+                                                                     seq_base + t0, hdr_base + t0, compact, hdr_pos,
+                                                                     hdr_end, seq_rank, b0, total_seq, total_hdr);
+      launched(ctx);
+      total_seq += c_seq;
+      total_hdr += c_hdr;
+    }
+    if (st) break;
     if (total_hdr == 0) {
       st = fail(ctx, AH_EINVAL, "ah_fasta_pack: no record (no line starts with '>')");
       break;
@@ -543,17 +618,6 @@ ah_status fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint
       st = fail(ctx, AH_EINVAL, "ah_fasta_pack: more than 2^32 - 1 records");
       break;
     }
-    if ((st = dalloc(ctx, &compact, total_seq + 16)) || (st = dalloc(ctx, &hdr_pos, total_hdr)) ||
-        (st = dalloc(ctx, &hdr_end, total_hdr)) || (st = dalloc(ctx, &seq_rank, total_hdr + 1)))
-      break;
-    // a header line that runs to the end of the text ends there
-    std::vector<uint64_t> fill(total_hdr, n_bytes);
-    AH_CUDA(ctx, cudaMemcpyAsync(hdr_end, fill.data(), total_hdr * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
-    // pass 3: compacted sequence bytes and the headers
-    k_fa_pass<true><<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, tile_entry, nullptr, nullptr,
-                                                                       seq_base, hdr_base, compact, hdr_pos, hdr_end,
-                                                                       seq_rank);
-    launched(ctx);
     std::vector<uint64_t> h_pos(total_hdr), h_end(total_hdr), h_rank(total_hdr + 1);
     AH_CUDA(ctx, cudaMemcpyAsync(h_pos.data(), hdr_pos, total_hdr * 8, cudaMemcpyDeviceToHost, ctx->stream));
     AH_CUDA(ctx, cudaMemcpyAsync(h_end.data(), hdr_end, total_hdr * 8, cudaMemcpyDeviceToHost, ctx->stream));

@@ -248,3 +248,43 @@ def test_fastq_qualities_follow_the_amplicons(ah_ctx, trim):
         assert qarena[int(off[5 * m]):int(off[5 * m + 1])] == ref_q[k], k
     fq = ah.ah_amplicons_fastq(a, arena, qarena, off, names)
     assert fq.count(b"\n+\n") == len(a)
+
+
+def test_fasta_pack_host_text_in_several_chunks(ah_ctx):
+    """Host text longer than one 256 MiB copy chunk is parsed chunk by chunk as it lands; records,
+    a header line and a sequence line that cross chunk boundaries come out as from the oracle."""
+    ah, ctx = ah_ctx
+    rng = np.random.default_rng(11)
+    chunk = 256 << 20
+    parts, pos, r = [], 0, 0
+
+    def record(name: bytes, L: int, width: int):
+        nonlocal pos, r
+        seq = rng.choice(np.frombuffer(b"ACGTACGTN", dtype=np.uint8), L)
+        rows = [seq[i:i + width].tobytes() for i in range(0, L, width)] if width else [seq.tobytes()]
+        txt = b">" + name + b"\n" + b"\n".join(rows) + b"\n"
+        parts.append(txt)
+        pos += len(txt)
+        r += 1
+
+    while pos < chunk - 30000:                       # ordinary records up to just before the first boundary
+        record(b"rec%d" % r, int(rng.integers(1000, 3_000_000)), 80)
+    parts.append(b"\n" * (chunk - 10000 - pos))      # empty lines: the next header starts 10,000 bytes before it
+    pos = chunk - 10000
+    record(b"long header " + b"x" * 20000, 5000, 60)  # its header crosses the boundary
+    while pos < 2 * chunk - 50:
+        record(b"rec%d" % r, int(rng.integers(1000, 3_000_000)), 0)   # one-line records cross the second
+    record(b"last", 777, 70)
+    text = b"".join(parts)
+    assert len(text) > 2 * chunk
+    names, seqs = oracle.parse_fasta(text)
+    batch, got_names = ah.ah_fasta_pack(ctx, text)
+    lens = np.array([len(s) for s in seqs], dtype=np.uint64)
+    ref = ah.ah_pack_batch(ctx, np.frombuffer(b"".join(seqs), dtype=np.uint8),
+                           np.concatenate([[0], np.cumsum(lens)]).astype(np.int64))
+    try:
+        assert got_names == names
+        assert _batch_bytes(ah, batch) == _batch_bytes(ah, ref)
+    finally:
+        ah.ah_batch_free(batch)
+        ah.ah_batch_free(ref)
