@@ -478,75 +478,69 @@ __device__ bool enum_max(const SiteVariants& V, const TmRun& R, double* out) {
 
 enum ChainResult { kChainOk, kChainUndefined, kChainUnbounded };
 
-// One Viterbi pass over the chain of qualifying variants: the variant maximising A * dS10 - B * dH10
-// (sums in tenths) in score arithmetic T, its bases left in v and its exact sums in dh10/ds10.  T is
-// float for the search passes and int64 (fixed point) for the confirming pass.  States are
-// (position, base, mismatches so far), at most 4 x (k + 1) per position.
-template <class T>
-__device__ bool chain_viterbi(const SiteVariants& V, T A, T B, uint8_t (*back)[4][kMaxK + 1], uint8_t* v,
-                              T* best_score, int* dh10, int* ds10) {
+// One Viterbi pass over the chain of qualifying variants: the best score A * dS10 - B * dH10 (sums in
+// tenths) in score arithmetic T over the variants, and that variant's exact sums in dh10/ds10, carried
+// forward with each state (no backtracking).  T is float for the search passes and int64 (fixed
+// point) for the confirming pass.  States are (position, base, mismatches so far), at most
+// 4 x (k + 1) per position.
+template <typename T>
+__device__ __forceinline__ T no_score();
+template <>
+__device__ __forceinline__ float no_score<float>() { return -INFINITY; }
+template <>
+__device__ __forceinline__ double no_score<double>() { return -INFINITY; }
+template <>
+__device__ __forceinline__ long long no_score<long long>() { return LLONG_MIN; }
+
+template <typename T>
+__device__ bool chain_viterbi(const SiteVariants& V, T A, T B, T* best_score, int* dh10, int* ds10) {
   constexpr int M = kMaxK + 1;
-  const int L = V.L, K = V.k < 0 ? 0 : V.k;
+  const int L = V.L, K = V.k < 0 ? 0 : V.k, W = K + 1;  // a base's states: mismatch counts 0..K
   auto inc = [&](int j, int a) { return (V.k >= 0 && V.ch[j][a] != V.s[j]) ? 1 : 0; };
-  bool live[4][M], nlive[4][M];
-  T cur[4][M], nxt[4][M];
-  int ch_[4][M], cs_[4][M], nh_[4][M], ns_[4][M];
-  for (int a = 0; a < 4; ++a)
-    for (int m = 0; m <= K; ++m) live[a][m] = false;
+  // state (base a, count m) at a * W + m: the best score (no_score: unreachable) and that path's
+  // sums packed as dh10 * 65536 + ds10 (|sums| < 2^15 tenths, so packed sums add exactly)
+  const T none = no_score<T>();
+  T cur[4 * M], nxt[4 * M];
+  int32_t cs[4 * M], ns[4 * M];
+  for (int x = 0; x < 4 * W; ++x) cur[x] = none;
   for (int a = 0; a < V.nch[0]; ++a) {
     int dh, ds;
     end_sums(0, L, V.ch[0][a], &dh, &ds);
-    const int m = inc(0, a);
-    live[a][m] = true;
-    cur[a][m] = A * (T)ds - B * (T)dh;
-    ch_[a][m] = dh, cs_[a][m] = ds;
+    const int x = a * W + inc(0, a);
+    cur[x] = A * (T)ds - B * (T)dh;
+    cs[x] = dh * 65536 + ds;
   }
   for (int i = 0; i + 1 < L; ++i) {
+    for (int x = 0; x < 4 * W; ++x) nxt[x] = none;
     for (int b = 0; b < V.nch[i + 1]; ++b) {
       const int ib = inc(i + 1, b);
       int th = 0, ts = 0;
       if (i + 1 == L - 1) end_sums(L - 1, L, V.ch[i + 1][b], &th, &ts);
-      for (int m = 0; m <= K; ++m) nlive[b][m] = false, back[i + 1][b][m] = 0;
       for (int a = 0; a < V.nch[i]; ++a) {
         int dh, ds;
         if (!edge_sums(i, L, V.ch[i][a], V.ch[i + 1][b], V.c, &dh, &ds)) continue;
         dh += th, ds += ts;
         const T w = A * (T)ds - B * (T)dh;
+        const int32_t pw = dh * 65536 + ds;
         for (int m = 0; m + ib <= K; ++m) {
-          if (!live[a][m]) continue;
-          const T sc = cur[a][m] + w;
-          const int n = m + ib;
-          if (!nlive[b][n] || sc > nxt[b][n]) {
-            nlive[b][n] = true;
-            nxt[b][n] = sc;
-            nh_[b][n] = ch_[a][m] + dh, ns_[b][n] = cs_[a][m] + ds;
-            back[i + 1][b][n] = (uint8_t)a;
-          }
+          const T c = cur[a * W + m];
+          if (c == none) continue;
+          const T sc = c + w;
+          const int y = b * W + m + ib;
+          if (sc > nxt[y]) nxt[y] = sc, ns[y] = cs[a * W + m] + pw;
         }
       }
     }
-    for (int b = 0; b < V.nch[i + 1]; ++b)
-      for (int m = 0; m <= K; ++m) {
-        live[b][m] = nlive[b][m];
-        if (nlive[b][m]) cur[b][m] = nxt[b][m], ch_[b][m] = nh_[b][m], cs_[b][m] = ns_[b][m];
-      }
+    for (int x = 0; x < 4 * W; ++x) cur[x] = nxt[x], cs[x] = ns[x];
   }
-  int arg = -1, am = 0;
-  for (int b = 0; b < V.nch[L - 1]; ++b)
-    for (int m = 0; m <= K; ++m)
-      if (live[b][m] && (arg < 0 || cur[b][m] > cur[arg][am])) arg = b, am = m;
+  int arg = -1;
+  for (int x = 0; x < 4 * W; ++x)
+    if (cur[x] != none && (arg < 0 || cur[x] > cur[arg])) arg = x;
   if (arg < 0) return false;
-  *best_score = cur[arg][am];
-  *dh10 = ch_[arg][am];
-  *ds10 = cs_[arg][am];
-  for (int j = L - 1; j >= 0; --j) {
-    v[j] = V.ch[j][arg];
-    if (j) {
-      const int pa = back[j][arg][am];
-      am -= inc(j, arg);
-      arg = pa;
-    }
-  }
+  *best_score = cur[arg];
+  const int32_t p = cs[arg];
+  *ds10 = (int16_t)(p & 0xffff);
+  *dh10 = (p - *ds10) / 65536;
   return true;
 }
 
@@ -563,8 +557,7 @@ __device__ bool chain_viterbi(const SiteVariants& V, T A, T B, uint8_t (*back)[4
 // qualifying variant could have D >= 0, where the iteration does not apply.
 __device__ ChainResult site_tm_chain(const SiteVariants& V, const TmRun& R, double* out) {
   const int L = V.L;
-  uint8_t back[32][4][kMaxK + 1], v[32];
-  // constant part of D: salt (method 5) and R ln(C); methods 1-4 shift Tm by a constant
+    // constant part of D: salt (method 5) and R ln(C); methods 1-4 shift Tm by a constant
   const double S0 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
   // all-A/T and one-G/C terms are equal here
   const double H0 = kInitH + kOneGCH + R.sym_h, Sc = kInitS + kOneGCS + R.sym_s;
@@ -573,15 +566,15 @@ __device__ ChainResult site_tm_chain(const SiteVariants& V, const TmRun& R, doub
   int dh10, ds10;
   float scf;
   // D must stay negative for every qualifying variant
-  if (!chain_viterbi<float>(V, 1.f, 0.f, back, v, &scf, &dh10, &ds10)) return kChainUndefined;
+  if (!chain_viterbi<float>(V, 1.f, 0.f, &scf, &dh10, &ds10)) return kChainUndefined;
   if (0.1 * ds10 + Sc + S0 >= 0.0) return kChainUnbounded;
   // start from the variant that maximises dS - dH / 300 (any defined variant works)
-  if (!chain_viterbi<float>(V, 300.f, 1000.f, back, v, &scf, &dh10, &ds10)) return kChainUndefined;
+  if (!chain_viterbi<float>(V, 300.f, 1000.f, &scf, &dh10, &ds10)) return kChainUndefined;
   double lam = ratio(dh10, ds10);
   int best_h = dh10, best_s = ds10;
   // single-precision search: stop when a pass proposes no variant with a larger exact ratio
   for (int it = 0; it < 64; ++it) {
-    if (!chain_viterbi<float>(V, (float)lam, 1000.f, back, v, &scf, &dh10, &ds10)) break;
+    if (!chain_viterbi<float>(V, (float)lam, 1000.f, &scf, &dh10, &ds10)) break;
     const double r = ratio(dh10, ds10);
     if (!(r > lam)) break;
     lam = r, best_h = dh10, best_s = ds10;
@@ -595,11 +588,11 @@ __device__ ChainResult site_tm_chain(const SiteVariants& V, const TmRun& R, doub
     if (fabs(lam) < 4000.0) {
       const long long Lq = llrint(lam * kScale), Bq = (long long)(1000.0 * kScale);
       long long sc;
-      if (!chain_viterbi<long long>(V, Lq, Bq, back, v, &sc, &dh10, &ds10)) break;
+      if (!chain_viterbi<long long>(V, Lq, Bq, &sc, &dh10, &ds10)) break;
       better = sc > Lq * best_s - Bq * best_h;
     } else {
       double sc;
-      if (!chain_viterbi<double>(V, lam, 1000.0, back, v, &sc, &dh10, &ds10)) break;
+      if (!chain_viterbi<double>(V, lam, 1000.0, &sc, &dh10, &ds10)) break;
       const double inc = lam * best_s - 1000.0 * best_h;
       better = sc > inc + 1e-12 * fabs(inc);
     }
