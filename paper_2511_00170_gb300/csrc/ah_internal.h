@@ -210,6 +210,7 @@ ah_status exclusive_scan_u64(ah_ctx* ctx, const uint64_t* d_in, uint64_t* d_out,
 // ones through the context's two page-locked bounce buffers, so that no copy takes the driver's
 // pageable path (one staging pipeline for every stream of the process)
 ah_status copy_to_host(ah_ctx* ctx, void* dst, const void* src, uint64_t bytes);
+constexpr uint64_t kBounceBytes = 8ull << 20;  // each of a context's two bounce buffers
 // read one uint64 from device memory (synchronises the stream)
 ah_status read_u64(ah_ctx* ctx, const uint64_t* d, uint64_t* h);
 // read and clear the device status word (synchronises)

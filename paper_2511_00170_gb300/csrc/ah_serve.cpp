@@ -227,14 +227,20 @@ ah_status ah_server_create(const ah_batch* db, int n_slots, uint64_t memory_budg
       return st;
     }
     c->scan_cfg.slot_cap = 64;  // requests are sparse; dense tiles are re-run with room
-    // a worker's pool keeps up to 2 GiB of freed memory cached; beyond that it returns memory at
-    // the next synchronisation, so idle workers do not hold what a large request needs
-    uint64_t keep = 2ull << 30;
-    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    // a worker's pool keeps its freed memory (the default of ah_ctx_create): returning memory at a
+    // synchronisation and mapping it again for the next large request would stall the other
+    // workers' streams
     // a request's primer set is compiled as kernels of 4 pairs on parallel host threads: a cold
     // 32-pair set compiles in about the time of one 4-pair kernel instead of 8x longer
     c->scan_cfg.pairs_per_kernel = 4;
     s->ctxs.push_back(c);
+    // the page-locked bounce buffers for result copies exist before the first request
+    for (int b = 0; b < 2; ++b)
+      if (cudaMallocHost(&c->bounce[b], kBounceBytes) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->bounce_ev[b], cudaEventDisableTiming) != cudaSuccess) {
+        ah_server_destroy(s);
+        return AH_ENOMEM;
+      }
   }
   for (int i = 0; i < n_slots; ++i) s->workers.emplace_back(worker, s, i);
   *out = s;

@@ -24,7 +24,6 @@ void dfree(ah_ctx* ctx, void* p) {
 }
 
 ah_status copy_to_host(ah_ctx* ctx, void* dst, const void* src, uint64_t bytes) {
-  constexpr uint64_t kBounce = 8ull << 20;
   if (bytes) {
     cudaPointerAttributes pa;
     const bool locked = cudaPointerGetAttributes(&pa, dst) == cudaSuccess && pa.type == cudaMemoryTypeHost;
@@ -33,20 +32,20 @@ ah_status copy_to_host(ah_ctx* ctx, void* dst, const void* src, uint64_t bytes) 
       AH_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     } else {
       for (int b = 0; b < 2; ++b) {
-        if (!ctx->bounce[b]) AH_CUDA(ctx, cudaMallocHost(&ctx->bounce[b], kBounce));
+        if (!ctx->bounce[b]) AH_CUDA(ctx, cudaMallocHost(&ctx->bounce[b], kBounceBytes));
         if (!ctx->bounce_ev[b]) AH_CUDA(ctx, cudaEventCreateWithFlags(&ctx->bounce_ev[b], cudaEventDisableTiming));
       }
       // chunk i lands in buffer i % 2 while the host copies chunk i - 1 out of the other
       uint64_t off[2] = {0, 0}, len[2] = {0, 0};
       int i = 0;
-      for (uint64_t o = 0; o < bytes; o += kBounce, ++i) {
+      for (uint64_t o = 0; o < bytes; o += kBounceBytes, ++i) {
         const int b = i & 1;
         if (len[b]) {
           AH_CUDA(ctx, cudaEventSynchronize(ctx->bounce_ev[b]));
           memcpy((char*)dst + off[b], ctx->bounce[b], len[b]);
         }
         off[b] = o;
-        len[b] = std::min<uint64_t>(kBounce, bytes - o);
+        len[b] = std::min<uint64_t>(kBounceBytes, bytes - o);
         AH_CUDA(ctx, cudaMemcpyAsync(ctx->bounce[b], (const char*)src + o, len[b], cudaMemcpyDeviceToHost, ctx->stream));
         AH_CUDA(ctx, cudaEventRecord(ctx->bounce_ev[b], ctx->stream));
       }
