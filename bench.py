@@ -632,6 +632,84 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------------ FASTQ reads arm
+def run_reads(args):
+    """Amplicon-sequencing reads end to end from FASTQ text in pinned host memory: ah_fastq_pack
+    (copy, parse and pack on the device, qualities kept there), the whole step, the amplicons'
+    qualities, and sites, amplicons, sequences and qualities copied to the host, every step."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+
+    __graft_entry__.build()
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Engine, Params
+
+    torch.cuda.set_device(0)
+    n_reads = args.genomes or 2_000_000
+    text_np, wl = synth.amplicon_reads(n_reads=n_reads)
+    text = torch.empty(text_np.nbytes, dtype=torch.uint8, pin_memory=True)
+    text.numpy()[:] = text_np
+    del text_np
+    eng = Engine(0)
+    p = Params.from_workload(wl)
+    L = ah.load()
+    pinned = {}
+
+    def pinned_buf(name, nbytes):   # page-locked result buffers, grown when a step needs more
+        if name not in pinned or pinned[name].numel() < nbytes:
+            pinned[name] = torch.empty(int(nbytes * 1.25) + 4096, dtype=torch.uint8, pin_memory=True)
+        return pinned[name]
+
+    stages = {"fastq_ms": [], "step_ms": [], "qual_ms": [], "copy_ms": []}
+    totals, counts = [], None
+    with ClockSampler(0) as clk:
+        for it in range(max(3, args.warmup) + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            batch, q, _ = ah.ah_fastq_pack(eng.ctx, text.data_ptr(), n_bytes=text.numel(), names=False)
+            t1 = time.perf_counter()
+            hits, amps = eng.step(batch, p, with_seqs=True, copy_out=False)
+            ah.ah_ctx_synchronize(eng.ctx)
+            t2 = time.perf_counter()
+            ah.ah_extract_qualities(eng.ctx, q, batch, eng.primers(p), hits, amps)
+            ah.ah_ctx_synchronize(eng.ctx)
+            t3 = time.perf_counter()
+            # sites, amplicons, sequences and qualities into page-locked host buffers
+            nh, na, nb = ah.ah_hits_count(hits), ah.ah_amplicons_count(amps), ah.ah_amplicons_arena_size(amps)
+            bh, ba = pinned_buf("hits", nh * 12 + 1), pinned_buf("amps", na * 32 + 1)
+            bs, bo, bq = pinned_buf("seq", nb + 1), pinned_buf("off", (5 * na + 1) * 8), pinned_buf("qual", nb + 1)
+            for st in (L.ah_hits_copy(hits, bh.data_ptr(), nh), L.ah_amplicons_copy(amps, ba.data_ptr(), na),
+                       L.ah_amplicons_seq_copy(amps, bs.data_ptr(), nb, bo.data_ptr(), 5 * na + 1),
+                       L.ah_amplicons_qual_copy(amps, bq.data_ptr(), nb)):
+                if st:
+                    raise RuntimeError(f"copy failed: {st}")
+            t4 = time.perf_counter()
+            ah.ah_hits_free(hits), ah.ah_amplicons_free(amps), ah.ah_quals_free(q), ah.ah_batch_free(batch)
+            if it >= max(3, args.warmup):
+                for k, v in zip(stages, (t1 - t0, t2 - t1, t3 - t2, t4 - t3)):
+                    stages[k].append(v * 1e3)
+                totals.append(t4 - t0)
+                counts = (nh, na, 2 * nb)
+    eng.close()
+    ms = statistics.median(totals) * 1e3
+    line = {"metric": METRIC, "workload": "amplicon_reads", "value": wl.total_bp / (ms * 1e-3) / 1e9, "unit": "Gbp/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "data": "synthetic", "dtype": "u32+f64",
+            "config": {"workload": f"amplicon_reads: {n_reads} FASTQ reads of 300 bp ({wl.total_bp / 1e9:.2f} Gbp, "
+                                   f"{text.numel() / 1e9:.2f} GB of text), the plain primer pair, k=2, trim, "
+                                   "qualities propagated", "reads": n_reads},
+            "e2e": {"value": wl.total_bp / (ms * 1e-3) / 1e9, "unit": "Gbp/s", "h2d_bytes_per_step": int(text.numel()),
+                    "d2h_bytes_per_step": counts[0] * 12 + counts[1] * 32 + counts[2] if counts else 0,
+                    "path": "pinned FASTQ text -> ah_fastq_pack -> scan, pairing, Tm, extraction -> "
+                            "ah_extract_qualities -> sites, amplicons, sequences and qualities into pinned host buffers"},
+            "stages_ms": {k: statistics.median(v) for k, v in stages.items()},
+            "sites": counts[0] if counts else 0, "amplicons": counts[1] if counts else 0, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -659,6 +737,8 @@ def main():
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "amplicon_reads":
+        run_reads(args)
     else:
         run_engine(args)
 

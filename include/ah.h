@@ -197,6 +197,9 @@ void ah_quals_free(ah_quals* q);
 uint32_t ah_fasta_count(const ah_fasta* f);
 /* header line of record i (owned by f), NULL past the end */
 const char* ah_fasta_name(const ah_fasta* f, uint32_t i);
+/* All names back to back and their offsets (count + 1 entries; the last is the total); out = NULL
+ * only fills the offsets.  AH_EOVERFLOW when cap is short. */
+ah_status ah_fasta_names_copy(const ah_fasta* f, char* out, uint64_t cap, uint64_t* offsets_out);
 void ah_fasta_free(ah_fasta* f);
 
 /* Pack records that are already in device memory: d_seq holds all records back to back and

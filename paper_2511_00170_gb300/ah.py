@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from typing import Optional, Sequence
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -116,6 +116,7 @@ SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_uint64)]),
     "ah_fasta_name": (ctypes.c_char_p, [_VP, _U32]),
     "ah_fasta_free": (None, [_VP]),
+    "ah_fasta_names_copy": (_I32, [_VP, _VP, _U64, _VP]),
     "ah_amplicons_fasta": (_I32, [_U64, _VP, _VP, _VP, _U32, _VP, _VP, ctypes.c_int, _VP, _U64,
                                   ctypes.POINTER(ctypes.c_uint64)]),
     "ah_batch_export": (_I32, [_VP, _VP, ctypes.POINTER(ctypes.c_uint64), _VP, _VP]),
@@ -264,6 +265,32 @@ def ah_pack_batch_device(ctx, d_seq: int, offsets: np.ndarray, genome_ids: Optio
     return out
 
 
+def _names_of(h) -> List[str]:
+    """The names held by an ah_fasta handle (bulk copy), then the handle freed."""
+    L = load()
+    try:
+        n = L.ah_fasta_count(h)
+        off = np.zeros(n + 1, dtype=np.uint64)
+        _check(L.ah_fasta_names_copy(h, None, 0, off.ctypes.data))
+        buf = ctypes.create_string_buffer(max(1, int(off[-1])))
+        _check(L.ah_fasta_names_copy(h, buf, int(off[-1]), off.ctypes.data))
+        raw = buf.raw[:int(off[-1])].decode("latin-1")
+        return [raw[int(off[i]):int(off[i + 1])] for i in range(n)]
+    finally:
+        L.ah_fasta_free(h)
+
+
+def ah_fasta_names_copy(names) -> Tuple[bytes, np.ndarray]:
+    """(all names back to back, offsets) of an ah_fasta handle."""
+    L = load()
+    n = L.ah_fasta_count(names)
+    off = np.zeros(n + 1, dtype=np.uint64)
+    _check(L.ah_fasta_names_copy(names, None, 0, off.ctypes.data))
+    buf = ctypes.create_string_buffer(max(1, int(off[-1])))
+    _check(L.ah_fasta_names_copy(names, buf, int(off[-1]), off.ctypes.data))
+    return buf.raw[:int(off[-1])], off
+
+
 def ah_fasta_pack(ctx, text, genome_ids: Optional[np.ndarray] = None, n_bytes: Optional[int] = None):
     """FASTA text (bytes / numpy uint8 on the host, or a device address with n_bytes) parsed and packed
     on the device.  Returns (batch, names)."""
@@ -278,12 +305,7 @@ def ah_fasta_pack(ctx, text, genome_ids: Optional[np.ndarray] = None, n_bytes: O
     out, names = ctypes.c_void_p(), ctypes.c_void_p()
     _check(load().ah_fasta_pack(ctx, addr, n, None if gid is None else gid.ctypes.data, ctypes.byref(out),
                                 ctypes.byref(names)), ctx)
-    L = load()
-    try:
-        nm = [L.ah_fasta_name(names, i).decode("latin-1") for i in range(L.ah_fasta_count(names))]
-    finally:
-        L.ah_fasta_free(names)
-    return out, nm
+    return out, _names_of(names)
 
 
 def ah_fasta_pack_into(ctx, text, batch, n_bytes: Optional[int] = None, names: bool = False):
@@ -297,18 +319,13 @@ def ah_fasta_pack_into(ctx, text, batch, n_bytes: Optional[int] = None, names: b
         addr, n = keep.ctypes.data, len(keep)
     h = ctypes.c_void_p()
     _check(load().ah_fasta_pack_into(ctx, addr, n, batch, ctypes.byref(h) if names else None), ctx)
-    if not names:
-        return None
-    L = load()
-    try:
-        return [L.ah_fasta_name(h, i).decode("latin-1") for i in range(L.ah_fasta_count(h))]
-    finally:
-        L.ah_fasta_free(h)
+    return _names_of(h) if names else None
 
 
-def ah_fastq_pack(ctx, text, genome_ids: Optional[np.ndarray] = None, n_bytes: Optional[int] = None):
+def ah_fastq_pack(ctx, text, genome_ids: Optional[np.ndarray] = None, n_bytes: Optional[int] = None,
+                  names: bool = True):
     """FASTQ text (host bytes/array, or a device address with n_bytes) parsed on the device.  Returns
-    (batch, quals, names); free quals with ah_quals_free."""
+    (batch, quals, names or None); free quals with ah_quals_free."""
     keep = None
     if isinstance(text, int):
         addr, n = text, int(n_bytes)
@@ -317,15 +334,10 @@ def ah_fastq_pack(ctx, text, genome_ids: Optional[np.ndarray] = None, n_bytes: O
             np.ascontiguousarray(text, dtype=np.uint8)
         addr, n = keep.ctypes.data, len(keep)
     gid = None if genome_ids is None else np.ascontiguousarray(genome_ids, dtype=np.uint32)
-    out, q, names = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    out, q, h = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     _check(load().ah_fastq_pack(ctx, addr, n, None if gid is None else gid.ctypes.data, ctypes.byref(out),
-                                ctypes.byref(q), ctypes.byref(names)), ctx)
-    L = load()
-    try:
-        nm = [L.ah_fasta_name(names, i).decode("latin-1") for i in range(L.ah_fasta_count(names))]
-    finally:
-        L.ah_fasta_free(names)
-    return out, q, nm
+                                ctypes.byref(q), ctypes.byref(h) if names else None), ctx)
+    return out, q, (_names_of(h) if names else None)
 
 
 def ah_quals_count(quals) -> int:

@@ -434,11 +434,19 @@ namespace {
 // locked or not) go through the copy engines: consecutive pieces that are contiguous in host memory
 // become one copy per chunk of up to kChunkBases bases, into one of two staging buffers on a second
 // stream, while the context's stream packs the previous chunk from HBM.  Synchronises.
-ah_status pack_records(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t n, const char* const* src) {
+// src[i]: record first + i.  one_buffer: every src lies in one allocation (its kind is checked once)
+ah_status pack_records(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t n, const char* const* src,
+                       bool one_buffer = false) {
   bool on_device = true;
   std::vector<uint64_t> dev_addr(n, 0);
+  bool checked = false;
   for (uint32_t i = 0; i < n && on_device; ++i) {
     if (!b->h_rec_len[first + i]) continue;
+    if (one_buffer && checked) {
+      dev_addr[i] = (uint64_t)(uintptr_t)src[i];  // device memory of this device: the first check
+      continue;
+    }
+    checked = true;
     cudaPointerAttributes pa;
     if (cudaPointerGetAttributes(&pa, src[i]) != cudaSuccess) {
       cudaGetLastError();
@@ -446,7 +454,7 @@ ah_status pack_records(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t n, con
       break;
     }
     if ((pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) && pa.devicePointer &&
-        pa.device == ctx->device)
+        pa.device == ctx->device && pa.devicePointer == (const void*)src[i])
       dev_addr[i] = (uint64_t)(uintptr_t)pa.devicePointer;
     else
       on_device = false;
@@ -663,7 +671,7 @@ ah_status ah_batch_pack_range(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t
       return fail(ctx, AH_EINVAL, "ah_batch_pack_range: record %u length differs from the layout", first + i);
     src[i] = (const char*)d_seq + h_offsets[i];
   }
-  return pack_records(ctx, b, first, count, src.data());
+  return pack_records(ctx, b, first, count, src.data(), true);
 }
 
 ah_status ah_batch_export(const ah_batch* b, void* planes_out, uint64_t* n_invalid, uint64_t* inv_groups,

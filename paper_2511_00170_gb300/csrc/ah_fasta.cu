@@ -885,6 +885,17 @@ const char* ah_fasta_name(const ah_fasta* f, uint32_t i) {
   return f && i < f->names.size() ? f->names[i].c_str() : nullptr;
 }
 
+ah_status ah_fasta_names_copy(const ah_fasta* f, char* out, uint64_t cap, uint64_t* offsets_out) {
+  if (!f || !offsets_out) return AH_EINVAL;
+  uint64_t total = 0;
+  offsets_out[0] = 0;
+  for (size_t i = 0; i < f->names.size(); ++i) offsets_out[i + 1] = total += f->names[i].size();
+  if (!out) return AH_OK;
+  if (cap < total) return AH_EOVERFLOW;
+  for (size_t i = 0; i < f->names.size(); ++i) memcpy(out + offsets_out[i], f->names[i].data(), f->names[i].size());
+  return AH_OK;
+}
+
 void ah_fasta_free(ah_fasta* f) { delete f; }
 
 }  // extern "C"

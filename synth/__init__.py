@@ -522,3 +522,58 @@ def serving_trace(seed: int, n_requests: int, rate_per_s: float, n_db_records: i
         out.append(dict(arrival=t, fwd=fwd, rev=rev, k=k, clamp=3, first_record=first, n_records=count, min_len=50,
                         max_len=2000, orient_mask=15))
     return out
+
+
+def amplicon_reads(seed: int = SEED, n_reads: int = 2_000_000, read_len: int = 300, err: float = 0.01):
+    """Amplicon-sequencing reads as FASTQ text (the input the paper's future-work FASTQ support is
+    for): each read holds a concrete variant of the plain pair's forward primer 0-10 bases in, a
+    random interior and the reverse complement of a variant of its reverse primer 0-10 bases before
+    the end; a tenth of the reads are random; substitutions at rate `err`; qualities uniform on
+    '!'..'J'.  Returns (FASTQ bytes as a uint8 array, the Workload of the same reads)."""
+    pst = Stream(make_key(seed, T_PRIMER, 0))        # the plain pair
+    fwd = random_primer(pst, 19, 2, 3)
+    rev = random_primer(pst, 20, 3, 3)
+    rng = np.random.default_rng(seed + 17)
+    codes = np.frombuffer(b"ACGT", dtype=np.uint8)
+    seqs = codes[rng.integers(0, 4, (n_reads, read_len))]
+    vst = Stream(make_key(seed, T_PLANT, 0x5eed))
+    fv = [np.frombuffer(concrete_variant(vst, fwd).encode(), dtype=np.uint8) for _ in range(32)]
+    comp = bytes.maketrans(b"ACGT", b"TGCA")
+    rv = [np.frombuffer(concrete_variant(vst, rev).encode().translate(comp)[::-1], dtype=np.uint8) for _ in range(32)]
+    a = rng.integers(0, 11, n_reads)
+    b = rng.integers(0, 11, n_reads)
+    fi = rng.integers(0, 32, n_reads)
+    ri = rng.integers(0, 32, n_reads)
+    planted = rng.random(n_reads) >= 0.1
+    gf = np.where(planted, a * 32 + fi, -1)
+    gr = np.where(planted, b * 32 + ri, -1)
+    for g in range(11 * 32):
+        aa, k = divmod(g, 32)
+        sel = np.nonzero(gf == g)[0]
+        if len(sel):
+            seqs[sel, aa:aa + len(fwd)] = fv[k]
+        sel = np.nonzero(gr == g)[0]
+        if len(sel):
+            e = read_len - aa
+            seqs[sel, e - len(rev):e] = rv[k]
+    errs = rng.random((n_reads, read_len)) < err
+    seqs[errs] = codes[rng.integers(0, 4, int(errs.sum()))]
+    quals = rng.integers(33, 75, (n_reads, read_len), dtype=np.uint8)
+    name_len = 10
+    rec = 1 + name_len + 1 + read_len + 3 + read_len + 1
+    text = np.empty((n_reads, rec), dtype=np.uint8)
+    text[:, 0] = ord("@")
+    idx = np.arange(n_reads)
+    for d in range(name_len):
+        text[:, 1 + d] = 48 + (idx // 10 ** (name_len - 1 - d)) % 10
+    c = 1 + name_len
+    text[:, c] = 10
+    text[:, c + 1:c + 1 + read_len] = seqs
+    c += 1 + read_len
+    text[:, c:c + 3] = np.frombuffer(b"\n+\n", dtype=np.uint8)
+    text[:, c + 3:c + 3 + read_len] = quals
+    text[:, -1] = 10
+    offsets = np.arange(n_reads + 1, dtype=np.int64) * read_len
+    wl = Workload("amplicon_reads", seqs.reshape(-1), offsets, np.arange(n_reads, dtype=np.uint32), [fwd], [rev], [2],
+                  3, 50, 2000, 0b1111, TmParams(min_tm=None), True, 0, 0, [], seed)
+    return text.reshape(-1), wl
