@@ -5,7 +5,10 @@
 
 #include <cstdint>
 #include <atomic>
+#include <condition_variable>
 #include <cstdio>
+#include <deque>
+#include <functional>
 #include <thread>
 #include <memory>
 #include <mutex>
@@ -307,6 +310,13 @@ class JitCache {
                  bool load_it);
   std::mutex mu_;
   std::unordered_map<std::string, std::shared_ptr<Entry>> cache_;
+  // fn(0..n-1) on the compile workers and the calling thread.  The workers start on first use and
+  // live for the process, so a compile does not pay for starting a thread.
+  void run_parallel(size_t n, const std::function<void(size_t)>& fn);
+  std::mutex pool_mu_;
+  std::condition_variable pool_cv_;
+  std::deque<std::function<void()>> tasks_;
+  std::vector<std::thread> workers_;
 };
 
 // the pattern sets a scan with cfg.pairs_per_kernel launches, in pair order

@@ -649,16 +649,62 @@ void JitCache::many_impl(int device, ah_ctx* stats, const std::vector<std::vecto
     (*st)[0] = get_impl(device, stats, sets[0], cfg, &(*out)[0], &(*err)[0], load_it);
     return;
   }
-  const size_t width = std::max<size_t>(1, std::min<size_t>(sets.size(), std::thread::hardware_concurrency()));
-  std::atomic<size_t> next{0};
-  std::vector<std::thread> pool;
-  for (size_t w = 0; w < width; ++w)
-    pool.emplace_back([&] {
-      cudaSetDevice(device);
-      for (size_t i = next++; i < sets.size(); i = next++)
-        (*st)[i] = get_impl(device, stats, sets[i], cfg, &(*out)[i], &(*err)[i], load_it);
-    });
-  for (auto& t : pool) t.join();
+  run_parallel(sets.size(), [&](size_t i) {
+    cudaSetDevice(device);
+    (*st)[i] = get_impl(device, stats, sets[i], cfg, &(*out)[i], &(*err)[i], load_it);
+  });
+}
+
+void JitCache::run_parallel(size_t n, const std::function<void(size_t)>& fn) {
+  if (n == 0) return;
+  if (n == 1) {
+    fn(0);
+    return;
+  }
+  // items are taken from a shared counter by the caller and by helper tasks on the workers; the
+  // caller returns once every item is done.  A helper that starts after the last item was taken
+  // finds none and leaves without touching fn.
+  struct Job {
+    std::function<void(size_t)> fn;
+    size_t n = 0;
+    std::atomic<size_t> next{0}, done{0};
+    std::mutex m;
+    std::condition_variable cv;
+  };
+  auto job = std::make_shared<Job>();
+  job->fn = fn;
+  job->n = n;
+  auto loop = [](const std::shared_ptr<Job>& j) {
+    for (size_t i = j->next++; i < j->n; i = j->next++) {
+      j->fn(i);
+      if (++j->done == j->n) {
+        std::lock_guard<std::mutex> l(j->m);
+        j->cv.notify_all();
+      }
+    }
+  };
+  {
+    std::lock_guard<std::mutex> lock(pool_mu_);
+    const size_t want = std::max<size_t>(1, std::min<size_t>(16, std::thread::hardware_concurrency()));
+    while (workers_.size() < want)
+      workers_.emplace_back([this] {
+        for (;;) {
+          std::function<void()> t;
+          {
+            std::unique_lock<std::mutex> l(pool_mu_);
+            pool_cv_.wait(l, [this] { return !tasks_.empty(); });
+            t = std::move(tasks_.front());
+            tasks_.pop_front();
+          }
+          t();
+        }
+      });
+    for (size_t h = 0; h + 1 < std::min(n, workers_.size() + 1); ++h) tasks_.emplace_back([job, loop] { loop(job); });
+  }
+  pool_cv_.notify_all();
+  loop(job);
+  std::unique_lock<std::mutex> l(job->m);
+  job->cv.wait(l, [&] { return job->done.load() == job->n; });
 }
 
 ah_status JitCache::get_many(ah_ctx* ctx, const std::vector<std::vector<Pattern>>& sets, const ScanConfig& cfg,
