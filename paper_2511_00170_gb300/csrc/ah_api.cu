@@ -36,10 +36,17 @@ __device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {  // 0x80 in each ze
   return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
 }
 
-__global__ void k_pack16(const uint8_t* __restrict__ src, const PackItem* __restrict__ items, uint2* __restrict__ planes,
-                         uint32_t* __restrict__ invalid) {
-  const PackItem it = items[blockIdx.x];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+// Items to warps: per_warp = false, a block per item (its warps split the item; long records);
+// per_warp = true, a warp per item over a grid-stride loop (many short records).
+template <bool per_warp>
+__global__ void k_pack16(const uint8_t* __restrict__ src, const PackItem* __restrict__ items, uint64_t n_items,
+                         uint2* __restrict__ planes, uint32_t* __restrict__ invalid) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t w0 = per_warp ? ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5 : blockIdx.x;
+  const uint64_t wstep = per_warp ? ((uint64_t)gridDim.x * blockDim.x) >> 5 : n_items;
+  const uint32_t warp = per_warp ? 0u : (threadIdx.x >> 5), nwarps = per_warp ? 1u : (blockDim.x >> 5);
+  for (uint64_t ix = w0; ix < n_items; ix += wstep) {
+  const PackItem it = items[ix];
   const uint8_t* base = (const uint8_t*)((uintptr_t)src + it.src_off);  // src may be null: offsets are then addresses
   for (uint32_t blk = warp; blk * 16u < it.n_groups; blk += nwarps) {
     const uint32_t x0 = blk * 512u + (uint32_t)lane * 16u;  // first base of this lane's 16
@@ -72,6 +79,7 @@ __global__ void k_pack16(const uint8_t* __restrict__ src, const PackItem* __rest
       invalid[it.dst_group + g] = inv | (inv2 << 16);
     }
   }
+  }
 }
 
 // the 16 bases of one 16-byte word as bit masks: lo | hi << 16 (code bits) and inv (non-ACGT)
@@ -97,10 +105,15 @@ __device__ __forceinline__ void word_masks(const uint4 v, uint32_t* lohi, uint32
 // crosses a page or an allocation boundary), bytes outside the item count as 'N', and group g is
 // bits r .. r + 31 of words 2g, 2g+1, 2g+2: lane 2j builds group j of the warp's 16 from its own
 // word and its two neighbours' (lane 31 also reads the word after the warp's 32).
-__global__ void k_pack16u(const uint8_t* __restrict__ src, const PackItem* __restrict__ items,
+template <bool per_warp>
+__global__ void k_pack16u(const uint8_t* __restrict__ src, const PackItem* __restrict__ items, uint64_t n_items,
                           uint2* __restrict__ planes, uint32_t* __restrict__ invalid) {
-  const PackItem it = items[blockIdx.x];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint64_t w0 = per_warp ? ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5 : blockIdx.x;
+  const uint64_t wstep = per_warp ? ((uint64_t)gridDim.x * blockDim.x) >> 5 : n_items;
+  const uint32_t warp = per_warp ? 0u : (threadIdx.x >> 5), nwarps = per_warp ? 1u : (blockDim.x >> 5);
+  for (uint64_t ix = w0; ix < n_items; ix += wstep) {
+  const PackItem it = items[ix];
   const uintptr_t start = (uintptr_t)src + it.src_off;  // src may be null: offsets are then addresses
   const uint4* A = (const uint4*)(start & ~(uintptr_t)15);
   const uint32_t r = (uint32_t)(start & 15);
@@ -136,6 +149,7 @@ __global__ void k_pack16u(const uint8_t* __restrict__ src, const PackItem* __res
       planes[it.dst_group + g] = make_uint2(__funnelshift_r(lo32, lo_hi, r), __funnelshift_r(hi32, hi_hi, r));
       invalid[it.dst_group + g] = __funnelshift_r(in32, in_hi, r);
     }
+  }
   }
 }
 
@@ -232,12 +246,24 @@ bool aligned16(const uint8_t* base, const PackItem* items, size_t n) {
 void launch_pack(cudaStream_t s, const uint8_t* d_src, const PackItem* d_items, const PackItem* h_items, size_t n,
                  ah_batch* b, ah_ctx* ctx) {
   const bool vec = aligned16(d_src, h_items, n);
+  uint64_t groups = 0;
+  for (size_t i = 0; i < n; ++i) groups += h_items[i].n_groups;
+  if (n > 4096 && groups < 128ull * n) {
+    // many short items (fewer than 128 groups, 4 Ki bases, on average): a warp per item
+    const unsigned grid = (unsigned)std::min<uint64_t>((n + 7) / 8, 32ull * std::max(1, ctx->sm_count));
+    if (vec)
+      k_pack16<true><<<grid, kPackThreads, 0, s>>>(d_src, d_items, n, b->planes, b->invalid);
+    else
+      k_pack16u<true><<<grid, kPackThreads, 0, s>>>(d_src, d_items, n, b->planes, b->invalid);
+    launched(ctx);
+    return;
+  }
   for (size_t i = 0; i < n; i += 65535) {
     const unsigned m = (unsigned)std::min<size_t>(65535, n - i);
     if (vec)
-      k_pack16<<<m, kPackThreads, 0, s>>>(d_src, d_items + i, b->planes, b->invalid);
+      k_pack16<false><<<m, kPackThreads, 0, s>>>(d_src, d_items + i, m, b->planes, b->invalid);
     else
-      k_pack16u<<<m, kPackThreads, 0, s>>>(d_src, d_items + i, b->planes, b->invalid);
+      k_pack16u<false><<<m, kPackThreads, 0, s>>>(d_src, d_items + i, m, b->planes, b->invalid);
     launched(ctx);
   }
 }

@@ -772,16 +772,21 @@ ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
         (st = dalloc(ctx, &hdr_pos, n_rec)) || (st = dalloc(ctx, &hdr_end, n_rec)) ||
         (st = dalloc(ctx, &seq_rank, n_rec)) || (st = dalloc(ctx, &qual_rank, n_rec)))
       break;
-    std::vector<uint64_t> fill(n_rec, n_bytes), none(n_rec, ~0ull);
+    std::vector<uint64_t> fill(n_rec, n_bytes);
     AH_CUDA(ctx, cudaMemcpyAsync(hdr_end, fill.data(), n_rec * 8, cudaMemcpyHostToDevice, ctx->stream));
-    AH_CUDA(ctx, cudaMemcpyAsync(hdr_pos, none.data(), n_rec * 8, cudaMemcpyHostToDevice, ctx->stream));
+    // a record whose header line was never seen keeps the ~0 rank and is refused below
+    AH_CUDA(ctx, cudaMemsetAsync(seq_rank, 0xff, n_rec * 8, ctx->stream));
     k_fq_pass<true><<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, line_base, nullptr, nullptr, nullptr,
                                                                        nullptr, seq_base, qual_base, seq, qual, hdr_pos,
                                                                        hdr_end, seq_rank, qual_rank, n_rec);
     launched(ctx);
-    std::vector<uint64_t> h_pos(n_rec), h_end(n_rec), h_srank(n_rec + 1), h_qrank(n_rec + 1);
-    AH_CUDA(ctx, cudaMemcpyAsync(h_pos.data(), hdr_pos, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    AH_CUDA(ctx, cudaMemcpyAsync(h_end.data(), hdr_end, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    // header positions come back only for the names; a missing header shows as a missing rank
+    std::vector<uint64_t> h_pos(names_out ? n_rec : 0), h_end(names_out ? n_rec : 0), h_srank(n_rec + 1),
+        h_qrank(n_rec + 1);
+    if (names_out) {
+      AH_CUDA(ctx, cudaMemcpyAsync(h_pos.data(), hdr_pos, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
+      AH_CUDA(ctx, cudaMemcpyAsync(h_end.data(), hdr_end, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    }
     AH_CUDA(ctx, cudaMemcpyAsync(h_srank.data(), seq_rank, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
     AH_CUDA(ctx, cudaMemcpyAsync(h_qrank.data(), qual_rank, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
     AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -790,7 +795,7 @@ ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
     const uint32_t R = (uint32_t)n_rec;
     bool ok = true;
     for (uint32_t r = 0; r < R && ok; ++r)
-      ok = h_pos[r] != ~0ull && h_srank[r + 1] - h_srank[r] == h_qrank[r + 1] - h_qrank[r];
+      ok = h_srank[r] != ~0ull && h_srank[r + 1] >= h_srank[r] && h_srank[r + 1] - h_srank[r] == h_qrank[r + 1] - h_qrank[r];
     if (!ok) {
       st = fail(ctx, AH_EINVAL, "ah_fastq_pack: a record lacks its header line or its qualities differ in length from its bases");
       break;
