@@ -167,6 +167,9 @@ def make_workload(args):
     raise SystemExit(f"unknown workload {args.workload}")
 
 
+L2_FLUSH_BELOW = 256 << 20   # packed bytes below which timed steps are separated by an L2 flush
+
+
 def describe(wl):
     return {"workload": f"{wl.name}: {wl.n_records} synthetic genomes, {wl.total_bp / 1e9:.3f} Gbp, "
                         f"{len(wl.fwd)} degenerate primer pair(s), k={wl.k}, clamp {wl.clamp}, "
@@ -174,7 +177,10 @@ def describe(wl):
                         f"trim={wl.trim}, barcodes {wl.fb_len}/{wl.rb_len}, "
                         f"Tm filter {wl.tm.min_tm}",
             "genomes": wl.n_records, "bases": wl.total_bp, "pairs": len(wl.fwd),
-            "l2": "inputs larger than L2 (packed genomes %.2f GB >> 129 MB)" % (wl.total_bp / 4e9)}
+            "l2": ("inputs larger than L2 (packed genomes %.2f GB >> 129 MB)" % (wl.total_bp / 4e9)
+                   if wl.total_bp / 4 > L2_FLUSH_BELOW else
+                   "inputs smaller than L2 (packed genomes %.1f MB): a 512 MB buffer is written between timed "
+                   "steps, outside the timed intervals" % (wl.total_bp / 4e6))}
 
 
 # ------------------------------------------------------------------------------------------ oracle arm
@@ -361,19 +367,31 @@ def run_engine(args):
 
     ah.ah_ctx_stats_reset(eng.ctx)
     ah.ah_ctx_set_timing(eng.ctx, True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush = wl.total_bp / 4 <= L2_FLUSH_BELOW   # inputs that fit in L2: flush it between timed steps
+    scratch = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}") if flush else None
+    marks = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.steps if flush else 1)]
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            one_step()
-        e1.record(stream)
+        if flush:
+            for a, z in marks:
+                with torch.cuda.stream(stream):
+                    scratch.fill_(1)
+                a.record(stream)
+                one_step()
+                z.record(stream)
+        else:
+            marks[0][0].record(stream)
+            for _ in range(args.steps):
+                one_step()
+            marks[0][1].record(stream)
         torch.cuda.synchronize()
     barrier()
     ah.ah_ctx_set_timing(eng.ctx, False)
     ah.ah_plan_check(plan, eng.ctx)   # every replay fitted its buffers (raises on overflow)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = sum(a.elapsed_time(z) for a, z in marks) / args.steps
+    del scratch
     stats = ah.ah_ctx_stats_get(eng.ctx)
     ms, value = job_time_and_value(ms, wl.total_bp, world)
 
