@@ -635,6 +635,20 @@ __device__ __forceinline__ uint8_t base_code(const uint2* planes, uint64_t group
   return (uint8_t)(((w.x >> bit) & 1u) | (((w.y >> bit) & 1u) << 1));
 }
 
+// Only the sites that some amplicon pairs need a Tm (an amplicon's Tm is the lower of its two
+// sites'): the amplicons first write this word (a NaN no Tm computation returns) into hit_tm at
+// their two sites, over an array cleared to zero, and the Tm kernel takes only the marked sites.
+constexpr unsigned long long kSiteWanted = 0xFFFFFFFFFFFFFFFFull;
+
+__global__ void k_mark_sites(const ah_amplicon* __restrict__ a, uint64_t n, double* __restrict__ hit_tm,
+                             const uint64_t* __restrict__ d_n = nullptr) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (d_n ? min(n, *d_n) : n)) return;
+  const uint2 hij = *reinterpret_cast<const uint2*>(&a[i]);  // hit_i, hit_j
+  reinterpret_cast<unsigned long long*>(hit_tm)[hij.x] = kSiteWanted;
+  reinterpret_cast<unsigned long long*>(hit_tm)[hij.y] = kSiteWanted;
+}
+
 // Sites arrive in (pair, record, pos, orient) order, so neighbouring sites alternate between the
 // pair's two primers, whose chains differ in shape.  Each block first sorts its sites by primer in
 // shared memory (bitonic, kTmBlock keys), so that a warp walks one primer's chain in step.
@@ -651,10 +665,12 @@ __global__ void __launch_bounds__(kTmBlock) k_tm_hits(const ah_hit* __restrict__
   const uint64_t n_here = d_n ? min(n, *d_n) : n;
   {
     const uint64_t i = base + threadIdx.x;
-    // key: primer (pair * 2 + primer, < 512), then the site's slot in the block; empty slots last
-    keys[threadIdx.x] = i < n_here ? (((uint32_t)(hits[i].pattern >> 2) * 2u + (hits[i].pattern & 1u)) << 16) |
-                                         threadIdx.x
-                                   : 0xFFFFFFFFu;
+    // key: primer (pair * 2 + primer, < 512), then the site's slot in the block; empty slots and
+    // sites no amplicon pairs last
+    const bool wanted = i < n_here && (unsigned long long)__double_as_longlong(out[i]) == kSiteWanted;
+    keys[threadIdx.x] = wanted ? (((uint32_t)(hits[i].pattern >> 2) * 2u + (hits[i].pattern & 1u)) << 16) |
+                                     threadIdx.x
+                               : 0xFFFFFFFFu;
   }
   __syncthreads();
   for (int size = 2; size <= kTmBlock; size <<= 1)
@@ -796,6 +812,8 @@ void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit
                const uint8_t* pk, int clamp, uint32_t* status, const uint2* planes, const uint64_t* rec_group, const uint8_t* plen, const uint8_t* psets, double* hit_tm,
                ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep) {
   const TmRun R = *(const TmRun*)run;
+  cudaMemsetAsync(hit_tm, 0, std::max<uint64_t>(1, hit_cap) * sizeof(double), s);
+  k_mark_sites<<<(unsigned)std::max<uint64_t>(1, (amp_cap + 255) / 256), 256, 0, s>>>(amps, amp_cap, hit_tm, d_namps);
   k_tm_hits<<<(unsigned)std::max<uint64_t>(1, (hit_cap + kTmBlock - 1) / kTmBlock), kTmBlock, 0, s>>>(hits, hit_cap, planes, rec_group,
                                                                                   plen, psets, pk, clamp, R, hit_tm,
                                                                                   status, d_nhits);
@@ -817,11 +835,16 @@ ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const a
   double* hit_tm = nullptr;
   uint32_t* keep = nullptr;
   if ((st = dalloc(ctx, &hit_tm, h->n))) return st;
-  if (h->n)
+  if (h->n && a->n) {
+    AH_CUDA(ctx, cudaMemsetAsync(hit_tm, 0, h->n * sizeof(double), ctx->stream));
+    k_mark_sites<<<(unsigned)((a->n + 255) / 256), 256, 0, ctx->stream>>>(a->d, a->n, hit_tm);
+    launched(ctx);
+  }
+  if (h->n && a->n)
     k_tm_hits<<<(unsigned)((h->n + kTmBlock - 1) / kTmBlock), kTmBlock, 0, ctx->stream>>>(h->d, h->n, b->planes, b->rec_group, p->d_plen,
                                                                       p->d_psets, p->d_pk, p->clamp, R, hit_tm,
                                                                       ctx->d_status);
-  if (h->n) launched(ctx);
+  if (h->n && a->n) launched(ctx);
   if (params->filter && (st = dalloc(ctx, &keep, a->n))) return st;
   if (a->n)
     k_tm_amps<<<(unsigned)((a->n + 255) / 256), 256, 0, ctx->stream>>>(a->d, a->n, hit_tm, params->filter,

@@ -295,6 +295,19 @@ def test_degenerate_site_tm_exact_max(engine, method, na):
     _check_sites(got, prims, sites, ks, clamps, synth.TmParams(Na=na, saltcorr=method))
 
 
+def test_degenerate_site_tm_wide_mismatch_budget(engine):
+    """Mismatch budgets of 6 to 12 (7 to 13 states per base) on primers with 8-10 degenerate codes:
+    beyond the widths whose Viterbi states stay in registers, the chain method keeps them in
+    per-thread arrays; both forms must give the oracle's exact maximum."""
+    from paper_2511_00170_gb300 import ah
+
+    prims, sites, _, clamps = _degenerate_sites(31, 24, 8, 10)
+    st = synth.Stream(synth.make_key(31, 78, 1))
+    ks = [st.randint(6, 12) for _ in prims]
+    got = ah.ah_tm_sites(engine.ctx, prims, sites, ah.tm_params(), k=ks, clamp=clamps)
+    _check_sites(got, prims, sites, ks, clamps, synth.TmParams())
+
+
 @pytest.mark.parametrize("method,na", [(4, 10.0), (5, 50.0)])
 def test_degenerate_site_tm_no_mismatch_limit(engine, method, na):
     """Without a mismatch limit every variant counts; where some variant's entropy sum could reach
