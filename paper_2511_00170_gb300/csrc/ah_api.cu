@@ -165,6 +165,27 @@ __global__ void k_scatter_invalid(const uint64_t* __restrict__ groups, const uin
   }
 }
 
+// Layout from device-resident record ranks (record r: source bytes [rank[r], rank[r + 1]), rank[n]
+// = total): each record's length and group count; then, from the group offsets, its packing item
+// and (without caller ids) its genome id.
+__global__ void k_ranked_lengths(const uint64_t* __restrict__ rank, uint64_t total, uint32_t n,
+                                 uint32_t* __restrict__ rec_len, uint32_t* __restrict__ groups) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint64_t len = (r + 1 < n ? rank[r + 1] : total) - rank[r];
+  rec_len[r] = (uint32_t)len;
+  groups[r] = (uint32_t)record_groups(len);
+}
+
+__global__ void k_ranked_items(const uint64_t* __restrict__ rank, const uint32_t* __restrict__ rec_len,
+                               const uint32_t* __restrict__ groups, const uint64_t* __restrict__ rec_group, uint32_t n,
+                               PackItem* __restrict__ items, uint32_t* __restrict__ genome_id) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  items[r] = PackItem{rank[r], rec_group[r], rec_len[r], groups[r]};
+  if (genome_id) genome_id[r] = r;
+}
+
 void free_batch_arrays(ah_batch* b) {
   if (!b || !b->ctx) return;
   dfree(b->ctx, b->rec_group);
@@ -313,6 +334,73 @@ uint8_t set_complement(uint8_t s) {
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
+namespace ah {
+
+ah_status pack_batch_ranked(ah_ctx* ctx, uint32_t n, const uint8_t* d_seq, const uint64_t* d_rank,
+                            const uint64_t* h_rank, const uint32_t* genome_ids, ah_batch** out) {
+  *out = nullptr;
+  if (n == 0) return fail(ctx, AH_EINVAL, "a batch needs at least one record");
+  ah_batch* b = new ah_batch();
+  b->ctx = ctx;
+  b->n_records = n;
+  b->h_rec_group.resize(n);
+  b->h_rec_len.resize(n);
+  uint64_t cursor = 0;
+  ah_status st = AH_OK;
+  for (uint32_t r = 0; r < n && !st; ++r) {
+    const uint64_t len = h_rank[r + 1] - h_rank[r];
+    if (h_rank[r + 1] < h_rank[r] || len > 0xffffffffull) st = fail(ctx, AH_EINVAL, "record %u: bad length", r);
+    b->h_rec_group[r] = cursor;
+    b->h_rec_len[r] = (uint32_t)len;
+    cursor += record_groups(len);
+  }
+  b->n_bases = h_rank[n] - h_rank[0];
+  b->n_groups = cursor;
+  b->alloc_groups = cursor + kTailGroups;
+  uint32_t* groups = nullptr;
+  PackItem* items = nullptr;
+  const unsigned grid = (n + 255) / 256;
+  if (!st) st = dalloc(ctx, &b->planes, b->alloc_groups);
+  if (!st) st = dalloc(ctx, &b->invalid, b->alloc_groups);
+  if (!st) st = dalloc(ctx, &b->rec_group, (uint64_t)n + 1);  // the scan also writes the total
+  if (!st) st = dalloc(ctx, &b->rec_len, n);
+  if (!st) st = dalloc(ctx, &b->genome_id, n);
+  if (!st) st = dalloc(ctx, &groups, n);
+  if (!st) st = dalloc(ctx, &items, n);
+  if (!st && genome_ids &&
+      cudaMemcpyAsync(b->genome_id, genome_ids, n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    st = fail(ctx, AH_ECUDA, "genome id copy failed");
+  if (!st) {
+    k_ranked_lengths<<<grid, 256, 0, ctx->stream>>>(d_rank, h_rank[n], n, b->rec_len, groups);
+    launched(ctx);
+    st = exclusive_scan_u32(ctx, groups, b->rec_group, n);
+  }
+  if (!st) {
+    k_ranked_items<<<grid, 256, 0, ctx->stream>>>(d_rank, b->rec_len, groups, b->rec_group, n, items,
+                                                   genome_ids ? nullptr : b->genome_id);
+    launched(ctx);
+    // a warp per record (any alignment), as launch_pack does for many short items
+    const unsigned pgrid = (unsigned)std::min<uint64_t>((n + 7) / 8, 32ull * std::max(1, ctx->sm_count));
+    k_pack16u<true><<<pgrid, kPackThreads, 0, ctx->stream>>>(d_seq, items, n, b->planes, b->invalid);
+    launched(ctx);
+    cudaMemsetAsync(b->planes + b->n_groups, 0, kTailGroups * sizeof(uint2), ctx->stream);
+    cudaMemsetAsync(b->invalid + b->n_groups, 0xFF, kTailGroups * sizeof(uint32_t), ctx->stream);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+      st = fail(ctx, AH_ECUDA, "ranked packing failed");
+  }
+  dfree(ctx, groups);
+  dfree(ctx, items);
+  if (st) {
+    free_batch_arrays(b);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return AH_OK;
+}
+
+}  // namespace ah
+
 extern "C" {
 
 ah_status ah_ctx_create(ah_ctx** out, int device, void* cuda_stream) {

@@ -471,6 +471,28 @@ __global__ void __launch_bounds__(kFaThreads) k_fq_pass(const uint8_t* __restric
   copy_out(qual_out, st_qual, qbase, qlead, t_qual);
 }
 
+// hdr_end[r] = the text's end before the emitting pass (a record whose header line ends the text)
+__global__ void k_fill_u64(uint64_t* __restrict__ p, uint64_t n, uint64_t v) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// every record has its header (its rank was written) and as many qualities as bases; bad = 1 if not
+__global__ void k_fq_check(const uint64_t* __restrict__ seq_rank, const uint64_t* __restrict__ qual_rank, uint64_t n,
+                           uint64_t total_seq, uint64_t total_qual, uint32_t* bad) {
+  const uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint64_t s0 = seq_rank[r], s1 = r + 1 < n ? seq_rank[r + 1] : total_seq;
+  const uint64_t q0 = qual_rank[r], q1 = r + 1 < n ? qual_rank[r + 1] : total_qual;
+  if (s0 == ~0ull || s1 < s0 || q1 < q0 || s1 - s0 != q1 - q0) atomicOr(bad, 1u);
+}
+
+// off[r] = rank[r] - rank[0] for r < n, off[n] = total - rank[0]
+__global__ void k_rank_offsets(const uint64_t* __restrict__ rank, uint64_t n, uint64_t total, uint64_t* __restrict__ off) {
+  const uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (r <= n) off[r] = (r < n ? rank[r] : total) - rank[0];
+}
+
 uint32_t host_apply(uint32_t f, uint32_t s) { return (f >> (2 * s)) & 3u; }
 
 }  // namespace
@@ -772,50 +794,54 @@ ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
         (st = dalloc(ctx, &hdr_pos, n_rec)) || (st = dalloc(ctx, &hdr_end, n_rec)) ||
         (st = dalloc(ctx, &seq_rank, n_rec)) || (st = dalloc(ctx, &qual_rank, n_rec)))
       break;
-    std::vector<uint64_t> fill(n_rec, n_bytes);
-    AH_CUDA(ctx, cudaMemcpyAsync(hdr_end, fill.data(), n_rec * 8, cudaMemcpyHostToDevice, ctx->stream));
+    k_fill_u64<<<(unsigned)std::min<uint64_t>((n_rec + 255) / 256, 4096), 256, 0, ctx->stream>>>(hdr_end, n_rec,
+                                                                                                n_bytes);
+    launched(ctx);
     // a record whose header line was never seen keeps the ~0 rank and is refused below
     AH_CUDA(ctx, cudaMemsetAsync(seq_rank, 0xff, n_rec * 8, ctx->stream));
     k_fq_pass<true><<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, line_base, nullptr, nullptr, nullptr,
                                                                        nullptr, seq_base, qual_base, seq, qual, hdr_pos,
                                                                        hdr_end, seq_rank, qual_rank, n_rec);
     launched(ctx);
-    // header positions come back only for the names; a missing header shows as a missing rank
-    std::vector<uint64_t> h_pos(names_out ? n_rec : 0), h_end(names_out ? n_rec : 0), h_srank(n_rec + 1),
-        h_qrank(n_rec + 1);
-    if (names_out) {
-      AH_CUDA(ctx, cudaMemcpyAsync(h_pos.data(), hdr_pos, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
-      AH_CUDA(ctx, cudaMemcpyAsync(h_end.data(), hdr_end, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    // records checked on the device; the sequence ranks come back for the batch's host record
+    // table (the quality offsets equal the sequence offsets once the lengths match), header
+    // positions only for the names
+    AH_CUDA(ctx, cudaMemsetAsync(bad, 0, 4, ctx->stream));
+    k_fq_check<<<(unsigned)((n_rec + 255) / 256), 256, 0, ctx->stream>>>(seq_rank, qual_rank, n_rec, total_seq,
+                                                                         total_qual, bad);
+    launched(ctx);
+    std::vector<uint64_t> h_pos(names_out ? n_rec : 0), h_end(names_out ? n_rec : 0), h_srank(n_rec + 1);
+    if ((st = copy_to_host(ctx, h_srank.data(), seq_rank, n_rec * 8))) break;
+    if (names_out && ((st = copy_to_host(ctx, h_pos.data(), hdr_pos, n_rec * 8)) ||
+                      (st = copy_to_host(ctx, h_end.data(), hdr_end, n_rec * 8))))
+      break;
+    if (cudaMemcpy(&h_bad, bad, 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      st = fail(ctx, AH_ECUDA, "ah_fastq_pack: status read failed");
+      break;
     }
-    AH_CUDA(ctx, cudaMemcpyAsync(h_srank.data(), seq_rank, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    AH_CUDA(ctx, cudaMemcpyAsync(h_qrank.data(), qual_rank, n_rec * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     h_srank[n_rec] = total_seq;
-    h_qrank[n_rec] = total_qual;
     const uint32_t R = (uint32_t)n_rec;
-    bool ok = true;
-    for (uint32_t r = 0; r < R && ok; ++r)
-      ok = h_srank[r] != ~0ull && h_srank[r + 1] >= h_srank[r] && h_srank[r + 1] - h_srank[r] == h_qrank[r + 1] - h_qrank[r];
-    if (!ok) {
+    if (h_bad) {
       st = fail(ctx, AH_EINVAL, "ah_fastq_pack: a record lacks its header line or its qualities differ in length from its bases");
       break;
     }
-    std::vector<uint64_t> offs(R + 1);
-    for (uint32_t r = 0; r <= R; ++r) offs[r] = h_srank[r] - h_srank[0];
-    if ((st = ah_pack_batch_device(ctx, R, seq + h_srank[0], offs.data(), genome_ids, batch_out))) break;
+    if ((st = pack_batch_ranked(ctx, R, seq, seq_rank, h_srank.data(), genome_ids, batch_out))) break;
     q = new ah_quals();
     q->ctx = ctx;
     q->n_records = R;
     q->h_off.resize(R + 1);
-    for (uint32_t r = 0; r <= R; ++r) q->h_off[r] = h_qrank[r] - h_qrank[0];
+    for (uint32_t r = 0; r <= R; ++r) q->h_off[r] = h_srank[r] - h_srank[0];
     if ((st = dalloc(ctx, &q->d_off, R + 1))) break;
-    AH_CUDA(ctx, cudaMemcpyAsync(q->d_off, q->h_off.data(), (R + 1) * 8, cudaMemcpyHostToDevice, ctx->stream));
-    if (h_qrank[0] == 0) {  // keep the buffer itself
+    k_rank_offsets<<<(unsigned)((R + 256) / 256), 256, 0, ctx->stream>>>(qual_rank, R, total_qual, q->d_off);
+    launched(ctx);
+    uint64_t q0 = 0;
+    if ((st = read_u64(ctx, qual_rank, &q0))) break;
+    if (q0 == 0) {  // keep the buffer itself
       q->d_qual = qual;
       qual = nullptr;
     } else {
       if ((st = dalloc(ctx, &q->d_qual, q->h_off[R] + 16))) break;
-      AH_CUDA(ctx, cudaMemcpyAsync(q->d_qual, qual + h_qrank[0], q->h_off[R], cudaMemcpyDeviceToDevice, ctx->stream));
+      AH_CUDA(ctx, cudaMemcpyAsync(q->d_qual, qual + q0, q->h_off[R], cudaMemcpyDeviceToDevice, ctx->stream));
     }
     if (names_out) {
       ah_fasta* f = new ah_fasta();

@@ -33,7 +33,7 @@ constexpr uint64_t kChunkBases = 256ull << 20;
 
 // Groups of a record of len bases: whole 64-base blocks (records start 16-byte aligned) with at
 // least one padding base after the record, so a window that leaves its record meets an invalid base.
-inline uint64_t record_groups(uint64_t len) { return (len / 64 + 1) * 2; }
+__host__ __device__ inline uint64_t record_groups(uint64_t len) { return (len / 64 + 1) * 2; }
 
 // Device status word bits (set by kernels, read by synchronising calls).
 enum : uint32_t {
@@ -216,6 +216,12 @@ ah_status copy_to_host(ah_ctx* ctx, void* dst, const void* src, uint64_t bytes);
 constexpr uint64_t kBounceBytes = 8ull << 20;  // each of a context's two bounce buffers
 // read one uint64 from device memory (synchronises the stream)
 ah_status read_u64(ah_ctx* ctx, const uint64_t* d, uint64_t* h);
+// A batch of n records whose bases lie in device memory at d_seq[rank[r], rank[r + 1]) (rank[n] =
+// total), with the ranks both on the device (d_rank, n values) and on the host (h_rank, n + 1
+// values).  Lengths, group offsets and packing items are computed on the device; the batch's host
+// record table from h_rank; no per-record array crosses the host link.  Synchronises.
+ah_status pack_batch_ranked(ah_ctx* ctx, uint32_t n, const uint8_t* d_seq, const uint64_t* d_rank,
+                            const uint64_t* h_rank, const uint32_t* genome_ids, ah_batch** out);
 // read and clear the device status word (synchronises)
 ah_status check_status(ah_ctx* ctx);
 // accumulate the pending scan-node timings of graph replays into the context's counters (syncs)
