@@ -311,9 +311,9 @@ __global__ void k_fa_names(const uint8_t* __restrict__ t, const uint64_t* __rest
 // sum) and no state machine; line 4r is record r's header, 4r + 1 its bases, 4r + 3 its qualities
 // ('\r' dropped from all three).
 
-// the thread's 64 bytes as four segments with their line-break and '\r' masks
-__device__ __forceinline__ void fq_load(const uint8_t* __restrict__ t, uint64_t n, Seg* g) {
-  const uint64_t p = (uint64_t)blockIdx.x * kFaTile + (uint64_t)threadIdx.x * (kFaSegs * kFaBytes);
+// the thread's 64 bytes of tile `tile` as four segments with their line-break and '\r' masks
+__device__ __forceinline__ void fq_load(const uint8_t* __restrict__ t, uint64_t n, uint64_t tile, Seg* g) {
+  const uint64_t p = tile * kFaTile + (uint64_t)threadIdx.x * (kFaSegs * kFaBytes);
   const bool whole = p + kFaSegs * kFaBytes <= n && (((uint64_t)(uintptr_t)t) & 15) == 0;
   uint4 x[kFaSegs];
   if (whole) {
@@ -349,25 +349,29 @@ __device__ __forceinline__ void fq_load(const uint8_t* __restrict__ t, uint64_t 
   }
 }
 
-// pass 1: line breaks per tile
-__global__ void __launch_bounds__(kFaThreads) k_fq_lines(const uint8_t* __restrict__ t, uint64_t n,
+// pass 1: line breaks per tile, over tiles tile0 .. tile0 + gridDim.x - 1 of the text
+__global__ void __launch_bounds__(kFaThreads) k_fq_lines(const uint8_t* __restrict__ t, uint64_t n, uint64_t tile0,
                                                          uint32_t* __restrict__ tile_nl) {
+  const uint64_t tile = tile0 + blockIdx.x;
   Seg g[kFaSegs];
-  fq_load(t, n, g);
+  fq_load(t, n, tile, g);
   uint32_t c = 0;
 #pragma unroll
   for (int q = 0; q < kFaSegs; ++q) c += __popc(g[q].nl);
   uint32_t e0, e1, t0, t1;
   block_exclusive_sums(c, 0, &e0, &e1, &t0, &t1);
-  if (threadIdx.x == 0) tile_nl[blockIdx.x] = t0;
+  if (threadIdx.x == 0) tile_nl[tile] = t0;
 }
 
 // passes 2 and 3 from each tile's line number: counts of bases, qualities and headers per tile, or
 // (emit) the bases and qualities compacted and per record r: hdr_pos[r] (after '@'), hdr_end[r] (its
-// line break), seq_rank[r] and qual_rank[r] (bases and qualities before the record)
+// line break), seq_rank[r] and qual_rank[r] (bases and qualities before the record).  Tiles tile0 ..
+// tile0 + gridDim.x - 1 of the text; line_base, seq_base and qual_base count from the first of them,
+// the lines, bases and qualities of the tiles before it are line_off, seq_off and qual_off.
 template <bool emit>
-__global__ void __launch_bounds__(kFaThreads) k_fq_pass(const uint8_t* __restrict__ t, uint64_t n,
-                                                        const uint64_t* __restrict__ line_base,
+__global__ void __launch_bounds__(kFaThreads) k_fq_pass(const uint8_t* __restrict__ t, uint64_t n, uint64_t tile0,
+                                                        const uint64_t* __restrict__ line_base, uint64_t line_off,
+                                                        uint64_t seq_off, uint64_t qual_off,
                                                         uint32_t* __restrict__ tile_seq, uint32_t* __restrict__ tile_qual,
                                                         uint32_t* __restrict__ tile_hdr, uint32_t* __restrict__ bad,
                                                         const uint64_t* __restrict__ seq_base,
@@ -376,15 +380,16 @@ __global__ void __launch_bounds__(kFaThreads) k_fq_pass(const uint8_t* __restric
                                                         uint64_t* __restrict__ hdr_end, uint64_t* __restrict__ seq_rank,
                                                         uint64_t* __restrict__ qual_rank, uint64_t n_rec) {
   __shared__ __align__(16) uint8_t st_seq[emit ? kFaTile + 32 : 16], st_qual[emit ? kFaTile + 32 : 16];
+  const uint64_t tile = tile0 + blockIdx.x;
   Seg g[kFaSegs];
-  fq_load(t, n, g);
-  const uint64_t p = (uint64_t)blockIdx.x * kFaTile + (uint64_t)threadIdx.x * (kFaSegs * kFaBytes);
+  fq_load(t, n, tile, g);
+  const uint64_t p = tile * kFaTile + (uint64_t)threadIdx.x * (kFaSegs * kFaBytes);
   uint32_t c = 0;
 #pragma unroll
   for (int q = 0; q < kFaSegs; ++q) c += __popc(g[q].nl);
   uint32_t e_nl, e_x, t_nl, t_x;
   block_exclusive_sums(c, 0, &e_nl, &e_x, &t_nl, &t_x);
-  const uint64_t line0 = line_base[blockIdx.x] + e_nl;
+  const uint64_t line0 = line_off + line_base[tile] + e_nl;
   const bool start0 = p == 0 || (p < n && t[p - 1] == '\n');  // the thread's first byte starts a line
   // one walk over the runs between line breaks; emit = false counts, emit = true writes
   auto walk = [&](bool write, uint32_t* ns, uint32_t* nq, uint32_t* nh, uint32_t* nbad, uint32_t ls, uint32_t lq,
@@ -446,12 +451,12 @@ __global__ void __launch_bounds__(kFaThreads) k_fq_pass(const uint8_t* __restric
     uint32_t e_h, e_b, t_h, t_b;
     block_exclusive_sums(nh, nb, &e_h, &e_b, &t_h, &t_b);
     if (threadIdx.x == 0) {
-      tile_seq[blockIdx.x] = t_seq, tile_qual[blockIdx.x] = t_qual, tile_hdr[blockIdx.x] = t_h;
+      tile_seq[tile] = t_seq, tile_qual[tile] = t_qual, tile_hdr[tile] = t_h;
       if (t_b) atomicAdd(bad, t_b);
     }
     return;
   }
-  const uint64_t sbase = seq_base[blockIdx.x], qbase = qual_base[blockIdx.x];
+  const uint64_t sbase = seq_off + seq_base[tile], qbase = qual_off + qual_base[tile];
   const uint32_t slead = (uint32_t)(sbase & 15), qlead = (uint32_t)(qbase & 15);
   uint32_t d0 = 0, d1 = 0, d2 = 0, d3 = 0;
   walk(true, &d0, &d1, &d2, &d3, slead + e_seq, qlead + e_qual, sbase - slead, qbase - qlead);
@@ -740,48 +745,119 @@ ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
   const uint8_t* t = (const uint8_t*)text;
   uint8_t *staged = nullptr, *seq = nullptr, *qual = nullptr;
   const uint64_t n_tiles = (n_bytes + kFaTile - 1) / kFaTile;
+  // host text is parsed in chunks as it lands, as FASTA is: a copy stream moves chunk c + 1 while the
+  // passes run on chunk c, which need only the lines, bases and qualities of the chunks before it
+  const uint64_t chunk_tiles = on_device ? std::max<uint64_t>(1, n_tiles) : (kChunkBases / kFaTile);
+  const uint64_t n_chunks = (n_tiles + chunk_tiles - 1) / chunk_tiles;
   uint32_t *tile_nl = nullptr, *tile_seq = nullptr, *tile_qual = nullptr, *tile_hdr = nullptr, *bad = nullptr;
   uint64_t *line_base = nullptr, *seq_base = nullptr, *qual_base = nullptr, *hdr_base = nullptr;
   uint64_t *hdr_pos = nullptr, *hdr_end = nullptr, *seq_rank = nullptr, *qual_rank = nullptr;
+  uint64_t rec_cap = 0;
   ah_quals* q = nullptr;
+  cudaStream_t cs = nullptr;
+  std::vector<cudaEvent_t> landed;
   auto cleanup = [&] {
+    if (cs) {
+      cudaStreamSynchronize(cs);
+      cudaStreamDestroy(cs);
+    }
+    for (cudaEvent_t e : landed) cudaEventDestroy(e);
     for (void* x : {(void*)staged, (void*)seq, (void*)tile_nl, (void*)tile_seq, (void*)tile_qual, (void*)tile_hdr,
                     (void*)bad, (void*)line_base, (void*)seq_base, (void*)qual_base, (void*)hdr_base, (void*)hdr_pos,
                     (void*)hdr_end, (void*)seq_rank, (void*)qual_rank})
       dfree(ctx, x);
   };
-  do {
-    if (!on_device) {
-      if ((st = dalloc(ctx, &staged, n_bytes))) break;
-      if (cudaMemcpyAsync(staged, text, n_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
-        st = fail(ctx, AH_ECUDA, "ah_fastq_pack: copy failed");
-        break;
-      }
-      t = staged;
+  auto fill = [&](uint64_t* p, uint64_t n, uint64_t v) {
+    k_fill_u64<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 4096), 256, 0, ctx->stream>>>(p, n, v);
+    launched(ctx);
+  };
+  // record arrays with room for `need` records, contents kept; a new record's header end reads as
+  // the end of the text and its rank as missing (~0) until its header is seen
+  auto grow = [&](uint64_t need) -> ah_status {
+    if (need <= rec_cap) return AH_OK;
+    const uint64_t cap = std::max<uint64_t>(need, std::max<uint64_t>(4096, 2 * rec_cap));
+    uint64_t* nw[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint64_t** old[4] = {&hdr_pos, &hdr_end, &seq_rank, &qual_rank};
+    ah_status e = AH_OK;
+    for (int k = 0; k < 4 && !e; ++k) e = dalloc(ctx, &nw[k], cap);
+    if (e) {
+      for (uint64_t* x : nw) dfree(ctx, x);
+      return e;
     }
+    for (int k = 0; k < 4; ++k) {
+      if (rec_cap) cudaMemcpyAsync(nw[k], *old[k], rec_cap * 8, cudaMemcpyDeviceToDevice, ctx->stream);
+      dfree(ctx, *old[k]);
+      *old[k] = nw[k];
+    }
+    fill(hdr_end + rec_cap, cap - rec_cap, n_bytes);
+    fill(seq_rank + rec_cap, cap - rec_cap, ~0ull);
+    rec_cap = cap;
+    return cudaGetLastError() == cudaSuccess ? AH_OK : fail(ctx, AH_ECUDA, "ah_fastq_pack: record arrays");
+  };
+  do {
     if ((st = dalloc(ctx, &tile_nl, n_tiles)) || (st = dalloc(ctx, &tile_seq, n_tiles)) ||
         (st = dalloc(ctx, &tile_qual, n_tiles)) || (st = dalloc(ctx, &tile_hdr, n_tiles)) || (st = dalloc(ctx, &bad, 1)) ||
         (st = dalloc(ctx, &line_base, n_tiles + 1)) || (st = dalloc(ctx, &seq_base, n_tiles + 1)) ||
-        (st = dalloc(ctx, &qual_base, n_tiles + 1)) || (st = dalloc(ctx, &hdr_base, n_tiles + 1)))
+        (st = dalloc(ctx, &qual_base, n_tiles + 1)) || (st = dalloc(ctx, &hdr_base, n_tiles + 1)) ||
+        (st = dalloc(ctx, &seq, n_bytes + 16)) || (st = dalloc(ctx, &qual, n_bytes + 16)))
       break;
     if (cudaMemsetAsync(bad, 0, 4, ctx->stream) != cudaSuccess) {
       st = fail(ctx, AH_ECUDA, "ah_fastq_pack: memset failed");
       break;
     }
-    k_fq_lines<<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, tile_nl);
-    launched(ctx);
-    if ((st = exclusive_scan_u32(ctx, tile_nl, line_base, n_tiles))) break;
-    k_fq_pass<false><<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, line_base, tile_seq, tile_qual,
-                                                                        tile_hdr, bad, nullptr, nullptr, nullptr, nullptr,
-                                                                        nullptr, nullptr, nullptr, nullptr, 0);
-    launched(ctx);
-    uint64_t total_seq = 0, total_qual = 0, n_rec = 0;
+    if (!on_device) {
+      if ((st = dalloc(ctx, &staged, n_bytes + 16))) break;
+      cudaEvent_t ready;
+      if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) {
+        st = fail(ctx, AH_ECUDA, "ah_fastq_pack: copy stream");
+        break;
+      }
+      landed.push_back(ready);  // the buffer was allocated in the context stream's order
+      cudaEventRecord(ready, ctx->stream);
+      cudaStreamWaitEvent(cs, ready, 0);
+      for (uint64_t c = 0; c < n_chunks && !st; ++c) {
+        const uint64_t b0 = c * chunk_tiles * kFaTile, b1 = std::min(n_bytes, b0 + chunk_tiles * kFaTile);
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMemcpyAsync(staged + b0, text + b0, b1 - b0, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+            cudaEventRecord(e, cs) != cudaSuccess)
+          st = fail(ctx, AH_ECUDA, "ah_fastq_pack: copy");
+        landed.push_back(e);
+      }
+      if (st) break;
+      t = staged;
+    }
+    uint64_t total_lines = 0, total_seq = 0, total_qual = 0, n_rec = 0;
+    for (uint64_t c = 0; c < n_chunks && !st; ++c) {
+      const uint64_t t0 = c * chunk_tiles, nt = std::min(chunk_tiles, n_tiles - t0);
+      if (!on_device) cudaStreamWaitEvent(ctx->stream, landed[1 + c], 0);
+      k_fq_lines<<<(unsigned)nt, kFaThreads, 0, ctx->stream>>>(t, n_bytes, t0, tile_nl);
+      launched(ctx);
+      if ((st = exclusive_scan_u32(ctx, tile_nl + t0, line_base + t0, nt))) break;
+      k_fq_pass<false><<<(unsigned)nt, kFaThreads, 0, ctx->stream>>>(
+          t, n_bytes, t0, line_base, total_lines, 0, 0, tile_seq, tile_qual, tile_hdr, bad, nullptr, nullptr, nullptr,
+          nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+      launched(ctx);
+      uint64_t c_lines = 0, c_seq = 0, c_qual = 0, c_hdr = 0;
+      if ((st = exclusive_scan_u32(ctx, tile_seq + t0, seq_base + t0, nt)) ||
+          (st = exclusive_scan_u32(ctx, tile_qual + t0, qual_base + t0, nt)) ||
+          (st = exclusive_scan_u32(ctx, tile_hdr + t0, hdr_base + t0, nt)) ||
+          (st = read_u64(ctx, line_base + t0 + nt, &c_lines)) || (st = read_u64(ctx, seq_base + t0 + nt, &c_seq)) ||
+          (st = read_u64(ctx, qual_base + t0 + nt, &c_qual)) || (st = read_u64(ctx, hdr_base + t0 + nt, &c_hdr)))
+        break;
+      if ((st = grow(n_rec + c_hdr))) break;
+      k_fq_pass<true><<<(unsigned)nt, kFaThreads, 0, ctx->stream>>>(
+          t, n_bytes, t0, line_base, total_lines, total_seq, total_qual, nullptr, nullptr, nullptr, nullptr, seq_base,
+          qual_base, seq, qual, hdr_pos, hdr_end, seq_rank, qual_rank, rec_cap);
+      launched(ctx);
+      total_lines += c_lines;
+      total_seq += c_seq;
+      total_qual += c_qual;
+      n_rec += c_hdr;
+    }
+    if (st) break;
     uint32_t h_bad = 0;
-    if ((st = exclusive_scan_u32(ctx, tile_seq, seq_base, n_tiles)) ||
-        (st = exclusive_scan_u32(ctx, tile_qual, qual_base, n_tiles)) ||
-        (st = exclusive_scan_u32(ctx, tile_hdr, hdr_base, n_tiles)) || (st = read_u64(ctx, seq_base + n_tiles, &total_seq)) ||
-        (st = read_u64(ctx, qual_base + n_tiles, &total_qual)) || (st = read_u64(ctx, hdr_base + n_tiles, &n_rec)))
-      break;
     if (cudaMemcpy(&h_bad, bad, 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
       st = fail(ctx, AH_ECUDA, "ah_fastq_pack: status read failed");
       break;
@@ -790,19 +866,6 @@ ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
       st = fail(ctx, AH_EINVAL, "ah_fastq_pack: not FASTQ (every record is four lines, the first starting with '@')");
       break;
     }
-    if ((st = dalloc(ctx, &seq, total_seq + 16)) || (st = dalloc(ctx, &qual, total_qual + 16)) ||
-        (st = dalloc(ctx, &hdr_pos, n_rec)) || (st = dalloc(ctx, &hdr_end, n_rec)) ||
-        (st = dalloc(ctx, &seq_rank, n_rec)) || (st = dalloc(ctx, &qual_rank, n_rec)))
-      break;
-    k_fill_u64<<<(unsigned)std::min<uint64_t>((n_rec + 255) / 256, 4096), 256, 0, ctx->stream>>>(hdr_end, n_rec,
-                                                                                                n_bytes);
-    launched(ctx);
-    // a record whose header line was never seen keeps the ~0 rank and is refused below
-    AH_CUDA(ctx, cudaMemsetAsync(seq_rank, 0xff, n_rec * 8, ctx->stream));
-    k_fq_pass<true><<<(unsigned)n_tiles, kFaThreads, 0, ctx->stream>>>(t, n_bytes, line_base, nullptr, nullptr, nullptr,
-                                                                       nullptr, seq_base, qual_base, seq, qual, hdr_pos,
-                                                                       hdr_end, seq_rank, qual_rank, n_rec);
-    launched(ctx);
     // records checked on the device; the sequence ranks come back for the batch's host record
     // table (the quality offsets equal the sequence offsets once the lengths match), header
     // positions only for the names
@@ -834,15 +897,11 @@ ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
     if ((st = dalloc(ctx, &q->d_off, R + 1))) break;
     k_rank_offsets<<<(unsigned)((R + 256) / 256), 256, 0, ctx->stream>>>(qual_rank, R, total_qual, q->d_off);
     launched(ctx);
+    // the qualities into a buffer of their own size (the staging one is sized by the text)
     uint64_t q0 = 0;
     if ((st = read_u64(ctx, qual_rank, &q0))) break;
-    if (q0 == 0) {  // keep the buffer itself
-      q->d_qual = qual;
-      qual = nullptr;
-    } else {
-      if ((st = dalloc(ctx, &q->d_qual, q->h_off[R] + 16))) break;
-      AH_CUDA(ctx, cudaMemcpyAsync(q->d_qual, qual + q0, q->h_off[R], cudaMemcpyDeviceToDevice, ctx->stream));
-    }
+    if ((st = dalloc(ctx, &q->d_qual, q->h_off[R] + 16))) break;
+    AH_CUDA(ctx, cudaMemcpyAsync(q->d_qual, qual + q0, q->h_off[R], cudaMemcpyDeviceToDevice, ctx->stream));
     if (names_out) {
       ah_fasta* f = new ah_fasta();
       f->names.resize(R);

@@ -288,3 +288,50 @@ def test_fasta_pack_host_text_in_several_chunks(ah_ctx):
     finally:
         ah.ah_batch_free(batch)
         ah.ah_batch_free(ref)
+
+
+def test_fastq_pack_host_text_in_several_chunks(ah_ctx):
+    """FASTQ host text longer than two 256 MiB copy chunks is parsed chunk by chunk as it lands; a
+    header line that crosses the first boundary and a sequence line that crosses the second come
+    out as from the oracle, with every record's qualities."""
+    ah, ctx = ah_ctx
+    rng = np.random.default_rng(12)
+    chunk = 256 << 20
+    parts, pos = [], 0
+    letters = np.frombuffer(b"ACGTACGTNacgt", dtype=np.uint8)
+
+    def record(name: bytes, L: int):  # 2 L + len(name) + 6 bytes
+        nonlocal pos
+        txt = (b"@" + name + b"\n" + rng.choice(letters, L).tobytes() + b"\n+\n" +
+               rng.integers(33, 75, L, dtype=np.uint8).tobytes() + b"\n")
+        parts.append(txt)
+        pos += len(txt)
+
+    while pos < chunk - 5_000_000:
+        record(b"read%d" % len(parts), int(rng.integers(100, 2_000_000)))
+    rem = chunk - 10000 - pos                       # a filler record ends 10,000 bytes before the boundary
+    name = b"f" if (rem - 7) % 2 == 0 else b"fg"
+    record(name, (rem - 6 - len(name)) // 2)
+    assert pos == chunk - 10000
+    record(b"long header " + b"x" * 20000, 5000)    # its header line crosses the first boundary
+    while pos < 2 * chunk - 5_000_000:
+        record(b"read%d" % len(parts), int(rng.integers(100, 2_000_000)))
+    record(b"s", 2 * chunk - pos - 3 + 1000)          # its sequence line crosses the second by 1,000 bytes
+    record(b"last", 777)
+    text = b"".join(parts)
+    assert len(text) > 2 * chunk
+    names, seqs, quals = oracle.parse_fastq(text)
+    batch, q, got_names = ah.ah_fastq_pack(ctx, text)
+    lens = np.array([len(s) for s in seqs], dtype=np.uint64)
+    ref = ah.ah_pack_batch(ctx, np.frombuffer(b"".join(seqs), dtype=np.uint8),
+                           np.concatenate([[0], np.cumsum(lens)]).astype(np.int64))
+    try:
+        assert got_names == names
+        assert _batch_bytes(ah, batch) == _batch_bytes(ah, ref)
+        got_q, off = ah.ah_quals_copy(q)
+        assert got_q == b"".join(quals)
+        assert list(off) == list(np.concatenate([[0], np.cumsum([len(x) for x in quals])]))
+    finally:
+        ah.ah_batch_free(batch)
+        ah.ah_batch_free(ref)
+        ah.ah_quals_free(q)
