@@ -354,12 +354,14 @@ typedef struct {
 
 /* Fill tm and flags of every amplicon (Section "Implementations": Biopython's Tm_NN in C; Section
  * "Primer degeneracy": Tm over the primer's variants).  The nearest-neighbour Tm (FP64) of each site
- * is the maximum of Tm(variant, site) over every concrete variant of its primer, or with
+ * that some amplicon pairs (no other site needs one) is the maximum of Tm(variant, site) over every
+ * concrete variant of its primer, or with
  * params->variants = 1 over those that match the site under the scan's rule (at most the pair's k
  * differing positions, none in the 3' clamp).  The amplicon's Tm is the lower of its two sites'.  With filter set, the amplicon list is compacted to
  * the kept ones (order preserved).  Synchronises the stream.  AH_ELIMIT when a site has more than
- * 2^20 qualifying variants and the exact chain method does not apply (salt method 6, or a variant
- * whose entropy sum could reach zero); that site's Tm is then NaN. */
+ * 2^20 qualifying variants and the exact chain method does not apply (salt methods 6 and 7, whose
+ * corrections depend on each variant's G/C content, or a variant whose entropy sum could reach
+ * zero); that site's Tm is then NaN. */
 ah_status ah_tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a,
                        const ah_tm_params* params);
 
@@ -374,7 +376,7 @@ ah_status ah_tm_duplexes(ah_ctx* ctx, uint32_t n, const char* const* seqs, const
  * maximum over the primer's concrete variants with at most k[i] positions differing from the site
  * and none among its last clamp[i] positions, as ah_tm_filter computes per site: enumerated for at
  * most 64 such variants, otherwise exact by Dinkelbach iterations over a chain Viterbi whose states
- * count mismatches, falling back to enumeration (up to 2^20 variants) for salt method 6.  k == NULL
+ * count mismatches, falling back to enumeration (up to 2^20 variants) for salt methods 6 and 7.  k == NULL
  * or k[i] >= the primer length: no mismatch limit; otherwise k[i] <= 15.  clamp == NULL: no clamp;
  * clamp[i] <= length (params->variants is not read: k and clamp say which variants count).
  * tm_out[i] is NaN when no qualifying variant has a defined Tm.  Synchronises; AH_ELIMIT as for
