@@ -794,12 +794,28 @@ ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
     rec_cap = cap;
     return cudaGetLastError() == cudaSuccess ? AH_OK : fail(ctx, AH_ECUDA, "ah_fastq_pack: record arrays");
   };
+  // bases and qualities compacted: room for `need` bytes (and the packer's 16 of slack), the first
+  // `used` kept.  Valid FASTQ has as many qualities as bases, at most half the text each, which is
+  // the first size; other text may need more before it is refused.
+  uint64_t seq_cap = 0, qual_cap = 0;
+  auto grow_bytes = [&](uint8_t** buf, uint64_t* cap, uint64_t used, uint64_t need) -> ah_status {
+    if (need + 16 <= *cap) return AH_OK;
+    const uint64_t nc = std::max(need + 16, std::min(n_bytes + 16, 2 * *cap));
+    uint8_t* nb = nullptr;
+    ah_status e = dalloc(ctx, &nb, nc);
+    if (e) return e;
+    if (used) cudaMemcpyAsync(nb, *buf, used, cudaMemcpyDeviceToDevice, ctx->stream);
+    dfree(ctx, *buf);
+    *buf = nb;
+    *cap = nc;
+    return AH_OK;
+  };
   do {
     if ((st = dalloc(ctx, &tile_nl, n_tiles)) || (st = dalloc(ctx, &tile_seq, n_tiles)) ||
         (st = dalloc(ctx, &tile_qual, n_tiles)) || (st = dalloc(ctx, &tile_hdr, n_tiles)) || (st = dalloc(ctx, &bad, 1)) ||
         (st = dalloc(ctx, &line_base, n_tiles + 1)) || (st = dalloc(ctx, &seq_base, n_tiles + 1)) ||
         (st = dalloc(ctx, &qual_base, n_tiles + 1)) || (st = dalloc(ctx, &hdr_base, n_tiles + 1)) ||
-        (st = dalloc(ctx, &seq, n_bytes + 16)) || (st = dalloc(ctx, &qual, n_bytes + 16)))
+        (st = grow_bytes(&seq, &seq_cap, 0, n_bytes / 2)) || (st = grow_bytes(&qual, &qual_cap, 0, n_bytes / 2)))
       break;
     if (cudaMemsetAsync(bad, 0, 4, ctx->stream) != cudaSuccess) {
       st = fail(ctx, AH_ECUDA, "ah_fastq_pack: memset failed");
@@ -846,7 +862,9 @@ ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
           (st = read_u64(ctx, line_base + t0 + nt, &c_lines)) || (st = read_u64(ctx, seq_base + t0 + nt, &c_seq)) ||
           (st = read_u64(ctx, qual_base + t0 + nt, &c_qual)) || (st = read_u64(ctx, hdr_base + t0 + nt, &c_hdr)))
         break;
-      if ((st = grow(n_rec + c_hdr))) break;
+      if ((st = grow(n_rec + c_hdr)) || (st = grow_bytes(&seq, &seq_cap, total_seq, total_seq + c_seq)) ||
+          (st = grow_bytes(&qual, &qual_cap, total_qual, total_qual + c_qual)))
+        break;
       k_fq_pass<true><<<(unsigned)nt, kFaThreads, 0, ctx->stream>>>(
           t, n_bytes, t0, line_base, total_lines, total_seq, total_qual, nullptr, nullptr, nullptr, nullptr, seq_base,
           qual_base, seq, qual, hdr_pos, hdr_end, seq_rank, qual_rank, rec_cap);
@@ -897,7 +915,7 @@ ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
     if ((st = dalloc(ctx, &q->d_off, R + 1))) break;
     k_rank_offsets<<<(unsigned)((R + 256) / 256), 256, 0, ctx->stream>>>(qual_rank, R, total_qual, q->d_off);
     launched(ctx);
-    // the qualities into a buffer of their own size (the staging one is sized by the text)
+    // the qualities into a buffer of their own size
     uint64_t q0 = 0;
     if ((st = read_u64(ctx, qual_rank, &q0))) break;
     if ((st = dalloc(ctx, &q->d_qual, q->h_off[R] + 16))) break;

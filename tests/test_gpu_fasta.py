@@ -187,7 +187,8 @@ def test_fastq_pack_matches_oracle(ah_ctx, seed, n_records, crlf, on_device):
 
 
 @pytest.mark.parametrize("text", [b"ACGT\nACGT\n+\nIIII\n", b"@r\nACGT\n+\nIII\n",
-                                  b"@r\nACGT\n+\nIIII\nnot a header\nAC\n+\nII\n"])
+                                  b"@r\nACGT\n+\nIIII\nnot a header\nAC\n+\nII\n",
+                                  b"@r\n" + b"A" * 100000 + b"\n+\n\n"])   # bases over half the text
 def test_fastq_pack_refuses_malformed(ah_ctx, text):
     ah, ctx = ah_ctx
     with pytest.raises(ah.AhError) as e:
