@@ -343,26 +343,12 @@ ah_status pack_batch_ranked(ah_ctx* ctx, uint32_t n, const uint8_t* d_seq, const
   ah_batch* b = new ah_batch();
   b->ctx = ctx;
   b->n_records = n;
-  b->h_rec_group.resize(n);
-  b->h_rec_len.resize(n);
-  uint64_t cursor = 0;
-  ah_status st = AH_OK;
-  for (uint32_t r = 0; r < n && !st; ++r) {
-    const uint64_t len = h_rank[r + 1] - h_rank[r];
-    if (h_rank[r + 1] < h_rank[r] || len > 0xffffffffull) st = fail(ctx, AH_EINVAL, "record %u: bad length", r);
-    b->h_rec_group[r] = cursor;
-    b->h_rec_len[r] = (uint32_t)len;
-    cursor += record_groups(len);
-  }
-  b->n_bases = h_rank[n] - h_rank[0];
-  b->n_groups = cursor;
-  b->alloc_groups = cursor + kTailGroups;
   uint32_t* groups = nullptr;
   PackItem* items = nullptr;
   const unsigned grid = (n + 255) / 256;
-  if (!st) st = dalloc(ctx, &b->planes, b->alloc_groups);
-  if (!st) st = dalloc(ctx, &b->invalid, b->alloc_groups);
-  if (!st) st = dalloc(ctx, &b->rec_group, (uint64_t)n + 1);  // the scan also writes the total
+  // the device first: lengths, group offsets (their total sizes the planes), items, packing; the
+  // host record table is filled while the device packs
+  ah_status st = dalloc(ctx, &b->rec_group, (uint64_t)n + 1);  // the scan also writes the total
   if (!st) st = dalloc(ctx, &b->rec_len, n);
   if (!st) st = dalloc(ctx, &b->genome_id, n);
   if (!st) st = dalloc(ctx, &groups, n);
@@ -375,6 +361,12 @@ ah_status pack_batch_ranked(ah_ctx* ctx, uint32_t n, const uint8_t* d_seq, const
     launched(ctx);
     st = exclusive_scan_u32(ctx, groups, b->rec_group, n);
   }
+  uint64_t dev_groups = 0;
+  if (!st) st = read_u64(ctx, b->rec_group + n, &dev_groups);
+  b->n_groups = dev_groups;
+  b->alloc_groups = dev_groups + kTailGroups;
+  if (!st) st = dalloc(ctx, &b->planes, b->alloc_groups);
+  if (!st) st = dalloc(ctx, &b->invalid, b->alloc_groups);
   if (!st) {
     k_ranked_items<<<grid, 256, 0, ctx->stream>>>(d_rank, b->rec_len, groups, b->rec_group, n, items,
                                                    genome_ids ? nullptr : b->genome_id);
@@ -385,9 +377,22 @@ ah_status pack_batch_ranked(ah_ctx* ctx, uint32_t n, const uint8_t* d_seq, const
     launched(ctx);
     cudaMemsetAsync(b->planes + b->n_groups, 0, kTailGroups * sizeof(uint2), ctx->stream);
     cudaMemsetAsync(b->invalid + b->n_groups, 0xFF, kTailGroups * sizeof(uint32_t), ctx->stream);
-    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess)
-      st = fail(ctx, AH_ECUDA, "ranked packing failed");
+    if (cudaGetLastError() != cudaSuccess) st = fail(ctx, AH_ECUDA, "ranked packing failed");
   }
+  b->h_rec_group.resize(n);
+  b->h_rec_len.resize(n);
+  uint64_t cursor = 0;
+  bool bad = false;
+  for (uint32_t r = 0; r < n; ++r) {
+    const uint64_t len = h_rank[r + 1] - h_rank[r];
+    bad |= h_rank[r + 1] < h_rank[r] || len > 0xffffffffull;
+    b->h_rec_group[r] = cursor;
+    b->h_rec_len[r] = (uint32_t)len;
+    cursor += record_groups(len);
+  }
+  b->n_bases = h_rank[n] - h_rank[0];
+  if (!st && (bad || cursor != dev_groups)) st = fail(ctx, AH_EINTERNAL, "pack_batch_ranked: bad record ranks");
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && !st) st = fail(ctx, AH_ECUDA, "ranked packing failed");
   dfree(ctx, groups);
   dfree(ctx, items);
   if (st) {

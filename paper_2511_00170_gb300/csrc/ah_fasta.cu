@@ -482,14 +482,15 @@ __global__ void k_fill_u64(uint64_t* __restrict__ p, uint64_t n, uint64_t v) {
     p[i] = v;
 }
 
-// every record has its header (its rank was written) and as many qualities as bases; bad = 1 if not
+// every record has its header (its rank was written), fewer than 2^32 bases and as many qualities
+// as bases; bad = 1 if not
 __global__ void k_fq_check(const uint64_t* __restrict__ seq_rank, const uint64_t* __restrict__ qual_rank, uint64_t n,
                            uint64_t total_seq, uint64_t total_qual, uint32_t* bad) {
   const uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (r >= n) return;
   const uint64_t s0 = seq_rank[r], s1 = r + 1 < n ? seq_rank[r + 1] : total_seq;
   const uint64_t q0 = qual_rank[r], q1 = r + 1 < n ? qual_rank[r + 1] : total_qual;
-  if (s0 == ~0ull || s1 < s0 || q1 < q0 || s1 - s0 != q1 - q0) atomicOr(bad, 1u);
+  if (s0 == ~0ull || s1 < s0 || q1 < q0 || s1 - s0 != q1 - q0 || s1 - s0 > 0xffffffffull) atomicOr(bad, 1u);
 }
 
 // off[r] = rank[r] - rank[0] for r < n, off[n] = total - rank[0]
@@ -910,16 +911,15 @@ ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
     q = new ah_quals();
     q->ctx = ctx;
     q->n_records = R;
-    q->h_off.resize(R + 1);
-    for (uint32_t r = 0; r <= R; ++r) q->h_off[r] = h_srank[r] - h_srank[0];
     if ((st = dalloc(ctx, &q->d_off, R + 1))) break;
     k_rank_offsets<<<(unsigned)((R + 256) / 256), 256, 0, ctx->stream>>>(qual_rank, R, total_qual, q->d_off);
     launched(ctx);
-    // the qualities into a buffer of their own size
-    uint64_t q0 = 0;
-    if ((st = read_u64(ctx, qual_rank, &q0))) break;
-    if ((st = dalloc(ctx, &q->d_qual, q->h_off[R] + 16))) break;
-    AH_CUDA(ctx, cudaMemcpyAsync(q->d_qual, qual + q0, q->h_off[R], cudaMemcpyDeviceToDevice, ctx->stream));
+    // the qualities into a buffer of their own size: none come before the first record (line 0 is its
+    // header), and their offsets are the bases' (the lengths match)
+    if ((st = dalloc(ctx, &q->d_qual, total_qual + 16))) break;
+    AH_CUDA(ctx, cudaMemcpyAsync(q->d_qual, qual, total_qual, cudaMemcpyDeviceToDevice, ctx->stream));
+    q->h_off.resize(R + 1);
+    for (uint32_t r = 0; r <= R; ++r) q->h_off[r] = h_srank[r] - h_srank[0];
     if (names_out) {
       ah_fasta* f = new ah_fasta();
       f->names.resize(R);
@@ -955,6 +955,7 @@ ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const u
       *names_out = f;
     }
   } while (false);
+  if (!st && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = fail(ctx, AH_ECUDA, "ah_fastq_pack: copies failed");
   if (qual) dfree(ctx, qual);
   cleanup();
   if (st) {

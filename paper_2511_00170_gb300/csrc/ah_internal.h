@@ -219,7 +219,9 @@ ah_status read_u64(ah_ctx* ctx, const uint64_t* d, uint64_t* h);
 // A batch of n records whose bases lie in device memory at d_seq[rank[r], rank[r + 1]) (rank[n] =
 // total), with the ranks both on the device (d_rank, n values) and on the host (h_rank, n + 1
 // values).  Lengths, group offsets and packing items are computed on the device; the batch's host
-// record table from h_rank; no per-record array crosses the host link.  Synchronises.
+// record table from h_rank; no per-record array crosses the host link.  The caller has checked that
+// the ranks do not decrease and that every record is shorter than 2^32 bases (the device reads each
+// record's bytes by them).  Synchronises.
 ah_status pack_batch_ranked(ah_ctx* ctx, uint32_t n, const uint8_t* d_seq, const uint64_t* d_rank,
                             const uint64_t* h_rank, const uint32_t* genome_ids, ah_batch** out);
 // read and clear the device status word (synchronises)
