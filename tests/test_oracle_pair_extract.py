@@ -195,3 +195,24 @@ def test_trim_overlapping_sites_is_empty():
     assert len(a) == 1
     (x,) = oracle.extract(wl2, hits, a, trim=True, fb=0, rb=0)
     assert x[0] == ""
+
+
+@pytest.mark.parametrize("seed", [21, 22, 23])
+def test_amplicon_qualities_follow_the_sequences(seed):
+    """Given each record's own bases as its qualities, an amplicon's quality field is its sequence
+    field for FR, FF and RR, and the complement of it for RF (qualities are reversed with the bases
+    but not complemented), trimmed or not."""
+    wl = synth.random_small(seed, n_records=3, len_lo=150, len_hi=400, n_pairs=2, plen_lo=6, plen_hi=9, n_deg=2,
+                            k_max=2, clamp=2, n_frac=0.0, plant=3, min_len=10, max_len=150, fb=0, rb=0)
+    hits = oracle.scan(wl)
+    amps = oracle.pair(wl, hits)
+    assert len(amps) > 0 and 1 in set(int(o) for o in amps["orient"])
+    quals = [wl.record_str(r).upper().encode() for r in range(wl.n_records)]
+    comp = bytes.maketrans(b"ACGT", b"TGCA")
+    for trim in (False, True):
+        wl.trim = trim
+        got = oracle.amplicon_qualities(wl, hits, amps, quals)
+        ex = oracle.extract(wl, hits, amps, trim=trim)
+        for a, q, x in zip(amps, got, ex):
+            s = x[0].upper().encode()
+            assert q == (s.translate(comp) if int(a["orient"]) == 1 else s), (int(a["orient"]), trim)
