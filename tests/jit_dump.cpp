@@ -2,7 +2,8 @@
 // argument "gen") the pattern table of the generic scan kernel, one pattern per block:
 //   len k n_eval n_clamp width clamp_mask mset0 mset1 mset2 mset3
 //   then n_eval lines "j c0 c1 c2 c3" (coefficients as 0 / 4294967295)
-// usage: jit_dump [gen] k clamp primer [primer ...]   (each primer gives its + and - strand patterns)
+// usage: jit_dump [gen] [shift=N] k clamp primer [primer ...]   (each primer gives its + and -
+// strand patterns; shift=N sets the scan source's shift mode, 0 by default)
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -23,6 +24,8 @@ static uint8_t comp(uint8_t s) { return (uint8_t)(((s & 1) << 2) | ((s & 4) >> 2
 int main(int argc, char** argv) {
   const bool gen = argc > 1 && !strcmp(argv[1], "gen");
   if (gen) ++argv, --argc;
+  int shift_mode = 0;
+  if (argc > 1 && !strncmp(argv[1], "shift=", 6)) shift_mode = atoi(argv[1] + 6), ++argv, --argc;
   const int k = atoi(argv[1]), clamp = atoi(argv[2]);
   std::vector<ah::Pattern> pats;
   for (int a = 3; a < argc; ++a)
@@ -48,6 +51,7 @@ int main(int argc, char** argv) {
     return 0;
   }
   ah::ScanConfig cfg;
+  cfg.shift_mode = shift_mode;
   puts(ah::scan_source(pats, cfg).c_str());
   return 0;
 }

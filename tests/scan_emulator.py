@@ -2,7 +2,8 @@
 
 The generated kernel computes, for 32 positions at once, a failure word per pattern from the two
 code-bit planes of two consecutive groups.  This module runs exactly those statements with numpy:
-plane definitions, funnel shifts and LOP3 instructions (evaluated from their truth tables), and
+plane definitions, funnel shifts (or their multiply-add form), LOP3 instructions (evaluated from
+their truth tables), and
 compares each failure word with an exact per-position mismatch count and clamp check.
 """
 import re
@@ -49,6 +50,15 @@ def failure_words(src, lo0, hi0, lo1, hi1, phase_a=None):
             env[m.group(2)] = zero | _expr(m.group(3), env)   # constants become one word per lane
             if m.group(1):
                 env["phase_a_" + m.group(2)] = env[m.group(2)]
+            continue
+        # a shift by two multiply-adds: t = lo(w1 * m), then hi(w0 * m) + t (m = 2^(32 - j))
+        m = re.match(r'\s*\{ u32 t_; asm\("mul.lo.u32 %0, %1, (\d+);" : "=r"\(t_\) : "r"\((\w+)\)\); '
+                     r'asm\("mad.hi.u32 %0, %1, (\d+), %2;" : "=r"\((\w+)\) : "r"\((\w+)\), "r"\(t_\)\); \}', line)
+        if m:
+            m1, w1, m2, name, w0 = m.group(1, 2, 3, 4, 5)
+            t = (env[w1].astype(np.uint64) * np.uint64(int(m1))) & np.uint64(0xFFFFFFFF)
+            h = (env[w0].astype(np.uint64) * np.uint64(int(m2))) >> np.uint64(32)
+            env[name] = ((h + t) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
             continue
         m = re.match(r'\s*u32 (\w+); asm\("lop3.b32 %0, %1, %2, %3, (0x[0-9a-f]+);" : "=r"\(\w+\) : '
                      r'"r"\((\w+)\), "r"\((\w+)\), "r"\((\w+)\)\);', line)

@@ -25,12 +25,13 @@ def dump():
     exe = os.path.join(ROOT, "paper_2511_00170_gb300", "_build", "jit_dump")
     src = os.path.join(ROOT, "tests", "jit_dump.cpp")
     lib = os.path.join(ROOT, "paper_2511_00170_gb300")
-    if not os.path.exists(exe) or os.path.getmtime(exe) < os.path.getmtime(os.path.join(lib, "libah.so")):
+    if not os.path.exists(exe) or os.path.getmtime(exe) < max(os.path.getmtime(os.path.join(lib, "libah.so")),
+                                                              os.path.getmtime(src)):
         cuda_inc = "/usr/local/cuda/include"
         subprocess.check_call(["g++", "-std=c++17", "-O1", "-I", cuda_inc, src, "-o", exe, "-L", lib, "-lah",
                                f"-Wl,-rpath,{lib}"])
-    return lambda k, c, prims, gen=False: subprocess.check_output([exe] + (["gen"] if gen else []) +
-                                                                [str(k), str(c)] + prims, text=True)
+    return lambda k, c, prims, gen=False, shift=0: subprocess.check_output(
+        [exe] + (["gen"] if gen else []) + [f"shift={shift}", str(k), str(c)] + prims, text=True)
 
 
 CASES = [(2, 3, ["AGATACCKWCAACAACTGC", "CTCCTCGTATAWTMTCRACC"]), (0, 0, ["ACGTACGT"]),
@@ -39,8 +40,8 @@ CASES = [(2, 3, ["AGATACCKWCAACAACTGC", "CTCCTCGTATAWTMTCRACC"]), (0, 0, ["ACGTA
          (4, 4, ["ACGTNACGTNACGTNACGTN"]), (6, 3, ["RRRRRRRRRRYYYYYYYYYY"]), (0, 2, ["AC"]), (1, 0, ["NN"])]
 
 
-def _check(dump, k, clamp, primers, seed, n=2000):
-    src = dump(k, clamp, primers)
+def _check(dump, k, clamp, primers, seed, n=2000, shift=0):
+    src = dump(k, clamp, primers, shift=shift)
     rng = np.random.default_rng(seed)
     planes = [rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32) for _ in range(4)]
     _check_planes(src, k, clamp, primers, planes)
@@ -63,6 +64,16 @@ def _check_planes(src, k, clamp, primers, planes):
 @pytest.mark.parametrize("k,clamp,primers", CASES)
 def test_generated_logic_fixed_cases(dump, k, clamp, primers):
     _check(dump, k, clamp, primers, 1)
+
+
+@pytest.mark.parametrize("shift", [1, 2])
+@pytest.mark.parametrize("k,clamp,primers", CASES[:6])
+def test_generated_logic_multiply_shifts(dump, k, clamp, primers, shift):
+    """Shift modes 1 and 2 align the planes with multiply-adds (all of them, or every other one)
+    instead of funnel shifts; the words are the same."""
+    src = dump(k, clamp, primers, shift=shift)
+    assert "mad.hi.u32" in src or "fshr(" not in src
+    _check(dump, k, clamp, primers, 2, shift=shift)
 
 
 @pytest.mark.parametrize("seed", range(8))
