@@ -107,3 +107,22 @@ def test_amplicon_fastq_matches_reference(ah, seed):
             for a, t, f, qq in zip(amps, tms, fields, q)]
     assert got == oracle.amplicon_fastq(recs, names, None, True)
     assert got.count(b"\n+\n") == len(amps)
+
+
+def test_amplicon_fasta_into_caller_buffer(ah):
+    """With `out`, the text goes into the caller's array and its length comes back; an array too
+    small for it is refused before anything is written."""
+    wl, amps, tms, fields = _inputs(8)
+    abi = np.zeros(len(amps), dtype=ah.AMP_DTYPE)
+    for k in ("record", "start", "end", "orient", "hit_i", "hit_j"):
+        abi[k] = amps[k]
+    abi["tm"] = tms
+    arena = b"".join(b"".join(f) for f in fields)
+    off = np.cumsum([0] + [len(x) for f in fields for x in f]).astype(np.uint64)
+    names = ["rec%d x" % r for r in range(wl.n_records)]
+    want = ah.ah_amplicons_fasta(abi, arena, off, names, None, True)
+    buf = np.full(len(want) + 10, 0xAB, dtype=np.uint8)
+    n = ah.ah_amplicons_fasta(abi, arena, off, names, None, True, out=buf)
+    assert n == len(want) and buf[:n].tobytes() == want and np.all(buf[n:] == 0xAB)
+    with pytest.raises(ValueError):
+        ah.ah_amplicons_fasta(abi, arena, off, names, None, True, out=np.zeros(len(want) - 1, dtype=np.uint8))
