@@ -124,3 +124,15 @@ def test_check_primer_validation():
     assert oracle.check_primer("A" * 33, 1, 0) == 2
     assert oracle.check_primer("ACGT", 5, 0) == 3
     assert oracle.check_primer("ACGT", 1, 5) == 4
+
+
+@pytest.mark.parametrize("seed", [40, 41])
+def test_scan_output_does_not_depend_on_threads(seed):
+    """The oracle splits records across threads for speed; its sites, in canonical order, are the
+    same for any number of threads."""
+    wl = synth.random_small(seed, n_records=23, len_lo=0, len_hi=3000, n_pairs=3, plen_lo=6, plen_hi=12, n_deg=3,
+                            k_max=3, clamp=2, n_frac=0.01, plant=2)
+    one = oracle.scan(wl, threads=1)
+    assert len(one) > 0
+    for t in (3, 7):
+        assert np.array_equal(oracle.scan(wl, threads=t), one)
