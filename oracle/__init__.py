@@ -83,6 +83,9 @@ def _get():
             L.or_extract.restype = i64
             L.or_free.argtypes = [vp]
             L.or_free.restype = None
+            L.or_nn_entry.argtypes = [ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]
+            L.or_nn_entry.restype = ctypes.c_int
             L.or_free_mg.argtypes = [ctypes.c_double, ctypes.c_double]
             L.or_free_mg.restype = ctypes.c_double
             _lib = L
@@ -148,6 +151,16 @@ def duplex_sums(seq: str, cseq: str) -> Optional[Tuple[float, float]]:
     """(dH kcal/mol, dS cal/(K mol)) before salt and concentration terms, or None if undefined."""
     dh, ds = ctypes.c_double(), ctypes.c_double()
     ok = _get().or_duplex_sums(seq.encode(), cseq.encode(), len(seq), ctypes.byref(dh), ctypes.byref(ds))
+    return (dh.value, ds.value) if ok else None
+
+
+NN_WC, NN_INTERNAL, NN_TERMINAL, NN_SCALAR = range(4)
+
+
+def nn_entry(table: int, key: str) -> Optional[Tuple[float, float]]:
+    """One stored parameter (dH, dS) as written in the oracle's tables, or None (for pins only)."""
+    dh, ds = ctypes.c_double(), ctypes.c_double()
+    ok = _get().or_nn_entry(table, key.encode(), ctypes.byref(dh), ctypes.byref(ds))
     return (dh.value, ds.value) if ok else None
 
 
@@ -295,6 +308,21 @@ def tm_keep(tm: np.ndarray, status: np.ndarray, min_tm: Optional[float]) -> np.n
         return (status == 0) & (tm >= min_tm)
 
 
+# Two FP64 evaluations of the same Tm may differ in their last digits (summation order, libm), and
+# the engine's Tm is held to within this distance of the oracle's; a decision closer to the
+# threshold than this is flagged rather than trusted (reading R16: the filter compares unrounded
+# values).
+NEAR_TOL = 1e-9
+
+
+def tm_near(tm: np.ndarray, status: np.ndarray, min_tm: Optional[float]) -> np.ndarray:
+    """Near-threshold flag: Tm defined and within NEAR_TOL degrees of min_tm (never without one)."""
+    if min_tm is None:
+        return np.zeros(len(tm), dtype=bool)
+    with np.errstate(invalid="ignore"):
+        return (status == 0) & (np.abs(tm - min_tm) <= NEAR_TOL)
+
+
 # ------------------------------------------------------------------------------------------ extract
 def extract(wl, hits: np.ndarray, amps: np.ndarray, trim: Optional[bool] = None, fb: Optional[int] = None,
             rb: Optional[int] = None) -> List[Tuple[str, str, str, str, str]]:
@@ -333,6 +361,8 @@ class Result:
     amp_status: np.ndarray
     keep: np.ndarray
     seqs: Optional[List[Tuple[str, str, str, str, str]]]   # for the kept amplicons, in order
+    near: Optional[np.ndarray] = None    # Tm within NEAR_TOL of min_tm
+    min_tm: Optional[float] = None       # the threshold the filter used (None: no filter)
 
 
 def run(wl, threads: int = 0, with_seqs: bool = True) -> Result:
@@ -342,4 +372,4 @@ def run(wl, threads: int = 0, with_seqs: bool = True) -> Result:
     atm, ast = amplicon_tm(amps, htm, hst)
     keep = tm_keep(atm, ast, wl.tm.min_tm)
     seqs = extract(wl, hits, amps[keep]) if with_seqs else None
-    return Result(hits, amps, htm, hst, atm, ast, keep, seqs)
+    return Result(hits, amps, htm, hst, atm, ast, keep, seqs, tm_near(atm, ast, wl.tm.min_tm), wl.tm.min_tm)

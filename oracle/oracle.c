@@ -434,6 +434,33 @@ static int find_param(const nn_param* t, int n, const char* key, double* dh, dou
   return 0;
 }
 
+/* Read access to one parameter entry, exactly as stored (no lookup rules, no arithmetic), so that
+ * tests can hold the tables against published values: table 0 the Watson-Crick stacks, 1 the
+ * internal mismatches, 2 the terminal mismatches, 3 the scalar terms ("init", "init_A/T",
+ * "init_G/C", "init_oneG/C", "init_allA/T", "init_5T/A", "sym").  Returns 1 if the key exists. */
+int or_nn_entry(int table, const char* key, double* dh, double* ds) {
+  *dh = *ds = 0.0;
+  switch (table) {
+    case 0: return find_param(WC_STACK, NELEM(WC_STACK), key, dh, ds);
+    case 1: return find_param(INTERNAL_MM, NELEM(INTERNAL_MM), key, dh, ds);
+    case 2: return find_param(TERMINAL_MM, NELEM(TERMINAL_MM), key, dh, ds);
+    default: break;
+  }
+  static const struct { const char* key; const double *dh, *ds; } scalars[] = {
+      {"init", &INIT_DH, &INIT_DS},           {"init_A/T", &INIT_AT_DH, &INIT_AT_DS},
+      {"init_G/C", &INIT_GC_DH, &INIT_GC_DS}, {"init_oneG/C", &INIT_ONEGC_DH, &INIT_ONEGC_DS},
+      {"init_allA/T", &INIT_ALLAT_DH, &INIT_ALLAT_DS}, {"init_5T/A", &INIT_5TA_DH, &INIT_5TA_DS},
+      {"sym", &SYM_DH, &SYM_DS},
+  };
+  for (int i = 0; i < NELEM(scalars); ++i)
+    if (strcmp(scalars[i].key, key) == 0) {
+      *dh = *scalars[i].dh;
+      *ds = *scalars[i].ds;
+      return 1;
+    }
+  return 0;
+}
+
 typedef struct {
   double Na, K, Tris, Mg, dNTPs; /* mM */
   double dnac1, dnac2;           /* nM */
