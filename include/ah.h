@@ -292,8 +292,11 @@ void ah_hits_free(ah_hits* h);
 #define AH_RR 8u
 
 /* Amplicon record.  [start, end) on the top strand; orient 0 FR, 1 RF, 2 FF, 3 RR.
- * tm is filled by ah_tm_filter (NaN before).  flags: bit0 kept by the Tm filter, bit1 Tm within
- * 1e-9 C of the threshold, bit2 Tm undefined (a site with no parameterised variant). */
+ * tm is filled by ah_tm_filter (NaN before).  flags: bit0 the threshold decision (Tm defined and
+ * >= min_tm), bit1 Tm within 1e-9 C of min_tm (the decision then rests on the last digits of an
+ * FP64 value: a caller who needs it stable re-checks these), bit2 Tm undefined (a site with no
+ * parameterised variant).  With the filter on, only amplicons with bit0 remain; with it off the
+ * bits annotate every amplicon against min_tm (pass -infinity for no threshold). */
 typedef struct {
   uint32_t hit_i, hit_j; /* indices into the hits: the + anchor site and the - site */
   uint32_t record;
@@ -325,12 +328,17 @@ ah_status ah_pair_amplicons(ah_ctx* ctx, const ah_batch* b, const ah_primers* p,
  * Returns AH_EINVAL when n_hits exceeds AH_PAIR_NOALLOC_MAX_SITES (1,048,576) or an argument is
  * missing, AH_EOVERFLOW (with *n_out set, nothing written) when the amplicons exceed out_capacity.
  * Scratch memory is one file-scope device array of about 12 MiB (partner counts, prefix sums and
- * block sums for up to AH_PAIR_NOALLOC_MAX_SITES sites); every GPU that loads the library holds it
- * until the process exits.  The first call on a device looks up that array's device address, so
- * make it before any stream capture.  All calls share the array: calls whose work overlaps on the
- * GPU (other streams, other threads) race and must be serialised by the caller.  The call works on
- * the current device and enqueues on `cuda_stream`; it waits for the count pass, then returns with
- * the emit pass enqueued. */
+ * block sums for up to AH_PAIR_NOALLOC_MAX_SITES sites).  CUDA loads the library's device code onto a
+ * device lazily, and the array is allocated with it, on the first ah_ctx_create on that device or
+ * the first call of this entry point there, whichever comes first; it then stays until the process
+ * exits.  A caller that will hand the rest of the GPU's memory to its own pool must therefore make
+ * one of those calls first (a call with n_hits = 0 only does this set-up), and make it before any
+ * stream capture.  All calls share the array: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  The call works on the current device
+ * and enqueues on `cuda_stream`; it waits for the count pass, then returns with the emit pass
+ * enqueued.  AH_ECUDA without enqueuing anything when an error from earlier work is pending on the
+ * calling thread (left in place for its owner); AH_ECUDA after a failed launch, with the passes
+ * before it still enqueued. */
 #define AH_PAIR_NOALLOC_MAX_SITES (1u << 20)
 ah_status ah_pair_amplicons_noalloc(void* cuda_stream, const ah_hit* d_hits, uint64_t n_hits,
                                     const uint64_t* d_pair_offsets, const uint8_t* d_pattern_len, uint32_t min_len,
@@ -345,8 +353,9 @@ typedef struct {
   double dnac1, dnac2;           /* nM, the two strand concentrations */
   int32_t saltcorr;              /* 0 none; 1-7 as in Biopython's salt_correction (7: Owczarzy et
                                     al. 2008, Mg2+ and dNTPs modelled directly); default 5 */
-  int32_t filter;                /* nonzero: drop amplicons with Tm < min_tm or undefined Tm */
-  double min_tm;                 /* degrees C */
+  int32_t filter;                /* nonzero: drop amplicons with Tm < min_tm or undefined Tm;
+                                    zero: keep all, flags still report the decision */
+  double min_tm;                 /* degrees C (flags bits 0 and 1 are taken against it) */
   int32_t variants;              /* degenerate primers: 0 every concrete variant (default);
                                     1 only variants matching the site within k and the clamp */
   int32_t selfcomp;              /* 1: self-complementary duplexes (symmetry term, C = dnac1) */

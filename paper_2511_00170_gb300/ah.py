@@ -573,9 +573,14 @@ def ah_pair_amplicons_noalloc(stream: int, d_hits: int, n_hits: int, d_pair_offs
 
 # ------------------------------------------------------------------------------------------ Tm
 def tm_params(Na=50.0, K=0.0, Tris=0.0, Mg=0.0, dNTPs=0.0, dnac1=25.0, dnac2=25.0, saltcorr=5, min_tm=None,
-              variants=0, selfcomp=0) -> ah_tm_params:
-    return ah_tm_params(Na, K, Tris, Mg, dNTPs, dnac1, dnac2, saltcorr, 0 if min_tm is None else 1,
-                        0.0 if min_tm is None else float(min_tm), int(variants), int(selfcomp))
+              variants=0, selfcomp=0, filter=None) -> ah_tm_params:
+    """min_tm None: no threshold (flags bit0 then marks a defined Tm).  filter None: filter iff a
+    threshold is given; False with a threshold only annotates the decision in the flags."""
+    flt = (min_tm is not None) if filter is None else bool(filter)
+    if flt and min_tm is None:
+        raise ValueError("filtering needs min_tm")
+    return ah_tm_params(Na, K, Tris, Mg, dNTPs, dnac1, dnac2, saltcorr, int(flt),
+                        float("-inf") if min_tm is None else float(min_tm), int(variants), int(selfcomp))
 
 
 def ah_tm_filter(ctx, batch, primers, hits, amps, params: ah_tm_params) -> None:

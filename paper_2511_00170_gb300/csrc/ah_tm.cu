@@ -712,15 +712,18 @@ __global__ void k_tm_amps(ah_amplicon* __restrict__ a, uint64_t n, const double*
   const double ti = hit_tm[m.hit_i], tj = hit_tm[m.hit_j];
   const bool undefined = isnan(ti) || isnan(tj);
   const double t = undefined ? __longlong_as_double(0x7ff8000000000000ll) : fmin(ti, tj);
+  // bit0: the threshold decision (defined and Tm >= min_tm), bit1: Tm within 1e-9 C of min_tm, so
+  // that the decision rests on the last digits of a double, bit2: undefined.  Without the filter
+  // the list is not compacted and the bits only annotate.
+  const bool pass = !undefined && t >= min_tm;
   uint8_t flags = 0;
-  bool k = !filter || (!undefined && t >= min_tm);
-  if (k) flags |= 1;
+  if (pass) flags |= 1;
   if (!undefined && fabs(t - min_tm) <= 1e-9) flags |= 2;
   if (undefined) flags |= 4;
   m.tm = t;
   m.flags = flags;
   a[i] = m;
-  if (keep) keep[i] = k ? 1u : 0u;
+  if (keep) keep[i] = (!filter || pass) ? 1u : 0u;
 }
 
 __global__ void k_compact_amps(const ah_amplicon* __restrict__ in, uint64_t n, const uint32_t* __restrict__ keep,

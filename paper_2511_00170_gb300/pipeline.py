@@ -35,6 +35,7 @@ class Params:
     rb_len: int = 0
     variants: int = 0
     selfcomp: int = 0
+    filter: Optional[bool] = None   # None: filter iff min_tm is set; False: annotate the decision only
 
     @classmethod
     def from_workload(cls, wl) -> "Params":
@@ -45,7 +46,7 @@ class Params:
 
     def tm_params(self) -> ah.ah_tm_params:
         return ah.tm_params(self.Na, self.K, self.Tris, self.Mg, self.dNTPs, self.dnac1, self.dnac2, self.saltcorr,
-                            self.min_tm, self.variants, self.selfcomp)
+                            self.min_tm, self.variants, self.selfcomp, self.filter)
 
 
 @dataclass

@@ -53,26 +53,68 @@ def assert_same_hits(out, ref):
         assert a == b, f"hit {a} vs oracle {b}"
 
 
-def assert_same_amplicons(out, ref, filtered: bool):
-    """filtered: the CUDA output went through the Tm filter (compare with the oracle's kept set)."""
-    ref_amps = ref.amps[ref.keep] if filtered else ref.amps
-    ref_tm = ref.amp_tm[ref.keep] if filtered else ref.amp_tm
-    ref_st = ref.amp_status[ref.keep] if filtered else ref.amp_status
+NEAR_TOL = 1e-9   # the near-threshold flag's distance (flags bit1)
+# |Tm - min_tm| this close to NEAR_TOL: the two sides' Tms (equal within ~1e-13) may fall on either
+# side of the flag's edge, so bit1 is not compared there
+_EDGE_BAND = 1e-11
+
+
+def _flag_bits(tm: float, undefined: bool, min_tm):
+    """(decision, near, undefined) as the oracle's Tm implies them, and whether `near` is decidable."""
+    if undefined:
+        return False, False, True, True
+    if min_tm is None:
+        return True, False, False, True
+    d = abs(tm - min_tm)
+    return tm >= min_tm, d <= NEAR_TOL, False, abs(d - NEAR_TOL) > _EDGE_BAND
+
+
+def assert_same_amplicons(out, ref, filtered: bool, min_tm="from_ref"):
+    """Amplicons, Tm and the three flag bits, amplicon by amplicon.
+
+    filtered: the CUDA output went through the Tm filter (compare with the oracle's kept set).
+    min_tm: the threshold the CUDA run used; by default the oracle's when filtered, none otherwise
+    (bit0 then means a defined Tm).  Amplicons within NEAR_TOL of the threshold must carry bit1; their
+    decision (bit0, and with it membership of a filtered list) may differ from the oracle's, since it
+    rests on the last digits of a double, but must agree with the CUDA path's own Tm.
+    """
+    if min_tm == "from_ref":
+        min_tm = ref.min_tm if filtered else None
+    assert not filtered or min_tm is not None
+    ok_all = oracle_amp_keys(ref.hits, ref.amps)
+    exp = {k: _flag_bits(float(t), bool(s), min_tm) + (float(t),)
+           for k, t, s in zip(ok_all, ref.amp_tm, ref.amp_status)}
     gk = gpu_amp_keys(out)
-    ok = oracle_amp_keys(ref.hits, ref_amps)
-    assert sorted(gk) == sorted(ok), f"amplicon sets differ: {len(gk)} vs oracle {len(ok)}"
-    ref_by: Dict[Tuple, Tuple[float, int]] = {k: (float(t), int(s)) for k, t, s in zip(ok, ref_tm, ref_st)}
+    assert len(set(gk)) == len(gk), "duplicate amplicons"
+    if filtered:
+        must = {k for k, e in exp.items() if e[0] and not e[1]}
+        may = {k for k, e in exp.items() if e[0] or e[1]}
+        got = set(gk)
+        assert must <= got, f"amplicons the oracle keeps are missing: {len(must - got)} of {len(must)}"
+        assert got <= may, f"amplicons the oracle drops were kept: {len(got - may)}"
+    else:
+        assert sorted(gk) == sorted(ok_all), f"amplicon sets differ: {len(gk)} vs oracle {len(ok_all)}"
     worst = 0.0
     for k, a in zip(gk, out.amps):
-        t, s = ref_by[k]
-        undefined = bool(a["flags"] & 4)
-        assert undefined == bool(s), f"Tm definedness differs at {k}"
+        dec, near, undef, decidable, t = exp[k]
+        flags = int(a["flags"])
+        undefined = bool(flags & 4)
+        assert undefined == undef, f"Tm definedness differs at {k}"
         if not undefined:
-            d = abs(float(a["tm"]) - t)
+            g = float(a["tm"])
+            d = abs(g - t)
             worst = max(worst, d)
             assert d <= TM_TOL, f"Tm {a['tm']!r} vs oracle {t!r} at {k}"
         else:
             assert math.isnan(float(a["tm"]))
+        if decidable:
+            assert bool(flags & 2) == near, f"near-threshold flag {bool(flags & 2)} vs oracle {near} at {k}"
+        if near:
+            assert bool(flags & 1) == (float(a["tm"]) >= min_tm), f"decision contradicts the CUDA Tm at {k}"
+        else:
+            assert bool(flags & 1) == dec, f"threshold decision {bool(flags & 1)} vs oracle {dec} at {k}"
+        if filtered:
+            assert flags & 1, f"filtered list holds an amplicon that fails the threshold at {k}"
     return worst
 
 

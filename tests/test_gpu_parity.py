@@ -540,3 +540,53 @@ def test_generic_scan_auto(engine):
         assert s["generic_scans"] == 0 and s["generic_bases"] == 0 and s["jit_compiles"] == 0
     finally:
         ah.ah_ctx_set_generic_scan(ctx, 0)
+
+
+@pytest.fixture(scope="module")
+def near_case():
+    """A small planted workload and the oracle's unfiltered result (Tm does not depend on min_tm)."""
+    wl = synth.plain_small(n_genomes=4, len_lo=200_000, len_hi=400_000)
+    wl.tm.min_tm = None
+    ref = oracle.run(wl, with_seqs=False)
+    defined = np.nonzero(ref.amp_status == 0)[0]
+    assert len(defined) > 0
+    return wl, ref, float(ref.amp_tm[defined[0]])
+
+
+@pytest.mark.parametrize("offset", [0.0, 5e-10, -5e-10, 2e-9, -2e-9])
+def test_near_threshold_flags(engine, near_case, offset):
+    """min_tm at an amplicon's exact oracle Tm, then 5e-10 and 2e-9 C to either side.  Flags bit1 must
+    mark exactly the amplicons within 1e-9 C of min_tm, bit0 the threshold decision; both with the
+    filter on (kept list) and off (every amplicon annotated)."""
+    import dataclasses
+
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Params
+
+    wl, ref_u, t0 = near_case
+    thr = t0 + offset
+    ref = dataclasses.replace(ref_u, keep=oracle.tm_keep(ref_u.amp_tm, ref_u.amp_status, thr),
+                              near=oracle.tm_near(ref_u.amp_tm, ref_u.amp_status, thr), min_tm=thr)
+    near_expected = abs(offset) <= 1e-9
+    assert ref.near.any() == near_expected
+    batch = engine.pack(wl.seq, wl.offsets, wl.genome_ids)
+    try:
+        p = Params.from_workload(wl)
+        p.min_tm = thr
+        out_f = engine.step(batch, p, with_seqs=False)
+        p.filter = False
+        out_a = engine.step(batch, p, with_seqs=False)
+    finally:
+        ah.ah_batch_free(batch)
+    compare.assert_same_amplicons(out_f, ref, filtered=True, min_tm=thr)
+    compare.assert_same_amplicons(out_a, ref, filtered=False, min_tm=thr)
+    # the annotated list holds every amplicon: the flagged ones are exactly the oracle's near ones,
+    # and away from the exact Tm the decision is the oracle's
+    flagged = (out_a.amps["flags"] & 2) != 0
+    assert int(flagged.sum()) == int(ref.near.sum())
+    t_gpu = out_a.amps["tm"][flagged]
+    assert np.all(np.abs(t_gpu - thr) <= 1e-9)
+    if offset != 0.0:
+        dec = (out_a.amps["flags"] & 1) != 0
+        assert int(dec.sum()) == int(ref.keep.sum())
+        assert len(out_f.amps) == int(ref.keep.sum())
