@@ -429,6 +429,10 @@ ah_status ah_ctx_create(ah_ctx** out, int device, void* cuda_stream) {
     ctx->own_stream = true;
   }
   cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (ah::noalloc_prepare() != cudaSuccess) {
+    ah_ctx_destroy(ctx);
+    return AH_ECUDA;
+  }
   if (cudaMalloc(&ctx->d_status, sizeof(uint32_t)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_status, sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {

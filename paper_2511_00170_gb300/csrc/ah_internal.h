@@ -238,6 +238,8 @@ ah_status scan_primers_per_record(ah_ctx* ctx, const ah_batch* b, const ah_prime
 // pairing (ah_pair.cu)
 ah_status pair_amplicons(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, uint32_t min_len,
                          uint32_t max_len, uint32_t orient_mask, ah_amplicons** out);
+// the allocation-free pairing's device array, loaded on the current device (ah_pair.cu)
+cudaError_t noalloc_prepare();
 // melting temperature (ah_tm.cu)
 ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const ah_hits* h, ah_amplicons* a,
                     const ah_tm_params* params);

@@ -151,21 +151,15 @@ constexpr size_t kNaScratchBytes = kNaSumsOff + kNaBlocks * sizeof(uint64_t);
 
 static __device__ __align__(256) unsigned char g_pair_scratch[kNaScratchBytes];
 
-// device address of g_pair_scratch per device, resolved once with that device current
-std::mutex g_na_mu;
-unsigned char* g_na_addr[64] = {};
-
-cudaError_t na_scratch(int device, unsigned char** out) {
-  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_na_mu);
-  if (!g_na_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_pair_scratch);
-    if (e != cudaSuccess) return e;
-    g_na_addr[device] = (unsigned char*)p;
-  }
-  *out = g_na_addr[device];
-  return cudaSuccess;
+// The device address of g_pair_scratch on the current device.  The first lookup on a device loads
+// this file's device code there (CUDA loads modules lazily), which also allocates the array; later
+// lookups only read the runtime's symbol table, so the address is looked up on every call rather
+// than cached, and a call after a device reset sees the new one.
+cudaError_t na_scratch(unsigned char** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_pair_scratch);
+  *out = (unsigned char*)p;
+  return e;
 }
 
 __device__ __forceinline__ uint64_t na_block_exclusive(uint64_t v, uint64_t* total) {
@@ -234,6 +228,15 @@ __global__ void k_na_apply(const uint32_t* __restrict__ counts, uint64_t n, cons
 }
 
 }  // namespace
+
+// Loads this file's device code, and with it the allocation-free pairing's scratch array, on the
+// current device (called when a context is created, so that a caller who creates a context before
+// handing the rest of the GPU's memory to its own pool never pays for it later).
+cudaError_t noalloc_prepare() {
+  unsigned char* p = nullptr;
+  return na_scratch(&p);
+}
+
 }  // namespace ah
 
 extern "C" ah_status ah_pair_amplicons_noalloc(void* cuda_stream, const ah_hit* d_hits, uint64_t n_hits,
@@ -245,10 +248,11 @@ extern "C" ah_status ah_pair_amplicons_noalloc(void* cuda_stream, const ah_hit* 
   *n_out = 0;
   if (n_hits > kNoAllocMaxSites) return AH_EINVAL;
   if (n_hits && (!d_hits || !d_pair_offsets || !d_pattern_len)) return AH_EINVAL;
-  int device = 0;
-  if (cudaGetDevice(&device) != cudaSuccess) return AH_ECUDA;
+  // an error left on this thread by earlier, unrelated work is not ours to report or to clear:
+  // refuse before enqueuing anything, and leave it in place
+  if (cudaPeekAtLastError() != cudaSuccess) return AH_ECUDA;
   unsigned char* scratch = nullptr;
-  if (na_scratch(device, &scratch) != cudaSuccess) return AH_ECUDA;
+  if (na_scratch(&scratch) != cudaSuccess) return AH_ECUDA;
   if (n_hits == 0) return AH_OK;
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   uint32_t* counts = (uint32_t*)(scratch + kNaCountsOff);
@@ -258,10 +262,15 @@ extern "C" ah_status ah_pair_amplicons_noalloc(void* cuda_stream, const ah_hit* 
   const unsigned nb = (unsigned)((n_hits + kNaTile - 1) / kNaTile);
   // every count, offset and block sum for the n_hits sites is written before it is read, so the
   // previous call's contents need no clearing
+  // each launch is checked as it is made (the thread had no pending error on entry, so an error
+  // now is this launch's); a failure returns with the passes before it still enqueued
   k_pair_walk<false><<<blocks, 256, 0, stream>>>(d_hits, n_hits, d_pair_offsets, d_pattern_len, min_len, max_len,
                                                  orient_mask & 15u, counts, nullptr, nullptr);
+  if (cudaGetLastError() != cudaSuccess) return AH_ECUDA;
   k_na_sums<<<nb, kNaThreads, 0, stream>>>(counts, n_hits, sums);
+  if (cudaGetLastError() != cudaSuccess) return AH_ECUDA;
   k_na_scan_sums<<<1, kNaThreads, 0, stream>>>(sums, nb, offsets + n_hits);
+  if (cudaGetLastError() != cudaSuccess) return AH_ECUDA;
   k_na_apply<<<nb, kNaThreads, 0, stream>>>(counts, n_hits, sums, offsets);
   if (cudaGetLastError() != cudaSuccess) return AH_ECUDA;
   uint64_t total = 0;

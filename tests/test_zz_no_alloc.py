@@ -102,3 +102,103 @@ def test_noalloc_pairing_reports_limits(engine):
     finally:
         ah.ah_hits_free(hits)
         ah.ah_batch_free(batch)
+
+
+def _periodic(periods, tail):
+    """One record of (30 A, 30 T) periods and a final run of `tail` A: with the all-A primers below
+    and k = 0 every period holds exactly 80 sites (F+ 21, R+ 19, F- 21, R- 19) and 40 amplicons (the
+    last + site of each A run pairs with every - site of the next T run), and the tail 2 * tail - 20
+    sites and no amplicon.  Partner counts are spread over every block of the prefix sums."""
+    g = ("A" * 30 + "T" * 30) * periods + "A" * tail
+    wl = synth.random_small(2, n_records=1, len_lo=10, len_hi=10, n_pairs=1, plant=0)
+    wl.seq = np.frombuffer(g.encode(), dtype=np.uint8).copy()
+    wl.offsets = np.array([0, len(g)], dtype=np.int64)
+    wl.genome_ids = np.zeros(1, dtype=np.uint32)
+    wl.fwd, wl.rev, wl.k, wl.clamp = ["A" * 10], ["A" * 12], [0], 2
+    wl.min_len, wl.max_len, wl.orient_mask = 20, 200, 15
+    return wl
+
+
+@pytest.mark.parametrize("periods,tail", [(12_500, 0), (13_107, 18)])
+def test_noalloc_pairing_many_blocks(engine, periods, tail):
+    """About a million sites (489 blocks of partial sums) and exactly AH_PAIR_NOALLOC_MAX_SITES
+    (all 512), so that the carry between blocks of the prefix sums is exercised."""
+    from paper_2511_00170_gb300 import ah
+
+    wl = _periodic(periods, tail)
+    p, batch, hits, ref = _sites_and_reference(engine, wl)
+    try:
+        n_hits = ah.ah_hits_count(hits)
+        assert n_hits == 80 * periods + (2 * tail - 20 if tail else 0)
+        assert n_hits > 2 * 2048
+        if tail:
+            assert n_hits == ah.AH_PAIR_NOALLOC_MAX_SITES
+        assert len(ref) == 40 * periods
+        for _ in range(2):   # two calls in a row over the same shared scratch
+            got = _noalloc(engine, p, hits, len(ref))
+            assert len(got) == len(ref)
+            assert got.tobytes() == ref.tobytes()
+    finally:
+        ah.ah_hits_free(hits)
+        ah.ah_batch_free(batch)
+
+
+_FIRST_CALL = r'''
+import sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import torch
+import oracle
+import synth
+from paper_2511_00170_gb300 import ah
+
+wl = synth.plain_small(n_genomes=3, len_lo=100_000, len_hi=200_000)
+o = oracle.scan(wl)
+orient = 2 * o["strand"].astype(np.int64) + o["primer"]
+order = np.lexsort((orient, o["pos"], o["record"], o["pair"]))   # the library's site order
+hits = np.zeros(len(o), dtype=ah.HIT_DTYPE)
+hits["record"], hits["pos"], hits["mism"] = o["record"][order], o["pos"][order], o["mism"][order]
+hits["pattern"] = 4 * o["pair"][order].astype(np.int64) + orient[order]
+n_pairs = len(wl.fwd)
+pair_off = np.searchsorted(o["pair"][order], np.arange(n_pairs + 1)).astype(np.uint64)
+plen = []
+for f, r in zip(wl.fwd, wl.rev):
+    plen += [len(f), len(r), len(f), len(r)]
+d_hits = torch.from_numpy(hits.view(np.uint8).copy()).cuda()
+d_off = torch.from_numpy(pair_off.view(np.uint8).copy()).cuda()
+d_plen = torch.tensor(plen, dtype=torch.uint8, device="cuda")
+cap = 4096
+d_out = torch.empty(cap * ah.AMP_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+torch.cuda.synchronize()
+# the first call of the library in this process
+n = ah.ah_pair_amplicons_noalloc(0, d_hits.data_ptr(), len(hits), d_off.data_ptr(), d_plen.data_ptr(), wl.min_len,
+                                 wl.max_len, wl.orient_mask, d_out.data_ptr(), cap)
+torch.cuda.synchronize()
+got = d_out[:n * ah.AMP_DTYPE.itemsize].cpu().numpy().view(ah.AMP_DTYPE)
+
+from paper_2511_00170_gb300.pipeline import Engine, Params
+e = Engine(0)
+p = Params.from_workload(wl)
+batch = e.pack(wl.seq, wl.offsets)
+h = ah.ah_scan_primers(e.ctx, batch, e.primers(p))
+assert ah.ah_hits_copy(h).tobytes() == hits.tobytes(), "oracle sites differ from the scan's"
+a = ah.ah_pair_amplicons(e.ctx, batch, e.primers(p), h, p.min_len, p.max_len, p.orient_mask)
+ref = ah.ah_amplicons_copy(a)
+assert n > 0 and len(got) == len(ref), (n, len(ref))
+assert got.tobytes() == ref.tobytes()
+print("first-call ok", n)
+'''
+
+
+def test_noalloc_pairing_as_first_call_of_a_process(engine):
+    """In a fresh process whose first library call is the allocation-free pairing (its device code and
+    scratch array are set up by that call), the result equals the allocating entry point's.  (The
+    engine fixture only makes sure the library is built; it lives in this test process.)"""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FIRST_CALL, root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    assert "first-call ok" in r.stdout
