@@ -46,7 +46,8 @@ typedef enum {
   AH_ETIMEOUT = 5,   /* a bounded device wait ran out */
   AH_EJIT = 6,       /* run-time compilation of a specialised kernel failed */
   AH_EINTERNAL = 7,  /* a device self-check failed */
-  AH_ELIMIT = 8      /* an exact computation would exceed its work bound (degenerate site Tm) */
+  AH_ELIMIT = 8,     /* an exact computation would exceed its work bound (degenerate site Tm) */
+  AH_ECANCELED = 9   /* a served request was cancelled (ah_server_cancel) */
 } ah_status;
 
 typedef struct ah_ctx ah_ctx;
@@ -117,6 +118,10 @@ ah_status ah_ctx_set_generic_scan(ah_ctx* ctx, int mode);
 /* Time every scan launch with CUDA events on the context's stream (scan_ms).  Synchronises the
  * stream to collect the timings of plan replays still pending. */
 ah_status ah_ctx_set_timing(ah_ctx* ctx, int enable);
+/* Fault injection on the host (no GPU fault): the context's next n device allocations fail with
+ * AH_ENOMEM, as when the device is out of memory.  The call that meets one fails cleanly and the
+ * context stays usable. */
+ah_status ah_ctx_inject_alloc_failures(ah_ctx* ctx, int n);
 
 /* Shape of the scan kernel used by ah_scan_primers on this context (a tuning knob; results do not
  * depend on it): threads per CTA (32..1024, a multiple of 32), groups of 32 positions per thread
@@ -189,6 +194,14 @@ ah_status ah_fasta_pack_into(ah_ctx* ctx, const char* text, uint64_t n_bytes, ah
 typedef struct ah_quals ah_quals;
 ah_status ah_fastq_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint32_t* genome_ids,
                         ah_batch** batch_out, ah_quals** quals_out, ah_fasta** names_out);
+/* File front end (Abstract: FASTA files in): the whole file at `path` is read into page-locked host
+ * memory by parallel reads, then parsed and packed as ah_fasta_pack / ah_fastq_pack do.  AH_EINVAL
+ * when the file cannot be opened or read (the message names it), AH_ENOMEM when the page-locked
+ * buffer cannot be had.  Synchronises. */
+ah_status ah_fasta_pack_file(ah_ctx* ctx, const char* path, const uint32_t* genome_ids, ah_batch** batch_out,
+                             ah_fasta** names_out);
+ah_status ah_fastq_pack_file(ah_ctx* ctx, const char* path, const uint32_t* genome_ids, ah_batch** batch_out,
+                             ah_quals** quals_out, ah_fasta** names_out);
 uint32_t ah_quals_count(const ah_quals* q);
 /* The record offsets (n + 1 entries; the last is the total) and, when out is not NULL, all
  * qualities back to back (cap >= the total, else AH_EOVERFLOW) into host memory. */
@@ -486,6 +499,15 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
  * their elapsed times are added to the context's scan_ms when the stream is next synchronised by
  * ah_ctx_synchronize or ah_ctx_set_timing. */
 ah_status ah_plan_launch(ah_plan* plan);
+/* The step on genomes in host memory: every record of the plan's batch is packed again from
+ * h_seq[h_offsets[r], h_offsets[r + 1]) (the lengths must be the batch's), the text crossing the link
+ * in staged chunks as ah_batch_pack_range does, and each range of scan tiles whose bases (and the
+ * group after them) have landed is scanned while the next chunk is copied; the rest of the step
+ * follows the last chunk as one graph launch.  Results as after ah_plan_launch (ah_plan_check,
+ * ah_plan_copy_results).  Returns with the work enqueued on the context's stream; h_seq must stay
+ * valid until the stream is synchronised (page-locked memory is fastest).  The plan's batch is
+ * overwritten. */
+ah_status ah_plan_launch_host(ah_plan* plan, const uint8_t* h_seq, const uint64_t* h_offsets);
 /* Synchronise and check the last run: AH_EOVERFLOW when a capacity was exceeded (sizes in the info). */
 ah_status ah_plan_check(ah_plan* plan);
 /* Launch and check, growing capacities and re-capturing on overflow. */
@@ -510,7 +532,11 @@ void ah_plan_free(ah_plan* plan);
  * oldest is admitted as soon as a worker is free and its estimated device memory fits under the
  * budget beside the requests already running (a request alone on the device is always admitted),
  * so requests that arrive while others run join as slots and memory free up and their kernels
- * overlap on the GPU.  A request runs the whole path on a slice of the database (no genome copy).
+ * overlap on the GPU.  Any queued request that fits is admitted, not only the oldest: a small
+ * request does not wait behind a large one that waits for memory, and a request passed over 8
+ * times is then waited for (no starvation).  A running request holds its estimate
+ * (ah_server_request_bytes) against the budget, grown to the memory its context actually holds
+ * after each stage.  A request runs the whole path on a slice of the database (no genome copy).
  * Each worker has a CUDA stream per priority class (up to three of the device's priorities); a
  * request runs at the priority of its scan work, bases x 4 x pairs (below 1e11, below 1e12,
  * above), so small requests are scheduled ahead of large ones running beside them.  By default
@@ -554,6 +580,16 @@ ah_status ah_server_wait(ah_server* s, uint64_t ticket, ah_result** out);
  * on.  Mode 1 serves without any run-time compilation.  AH_EINVAL for another mode. */
 ah_status ah_server_set_scan_mode(ah_server* s, int mode);
 ah_status ah_server_now(const ah_server* s, double* seconds);
+/* Cancel a request: a queued one finishes at once, a running one at its next stage boundary; its
+ * result (ah_server_wait) has status AH_ECANCELED.  AH_EINVAL for an unknown or collected ticket. */
+ah_status ah_server_cancel(ah_server* s, uint64_t ticket);
+/* Device bytes the server reserves for a request when admitting it (its estimate). */
+ah_status ah_server_request_bytes(const ah_server* s, const ah_request* r, uint64_t* bytes);
+/* The budget, the bytes reserved now and the most ever reserved at once (any may be NULL). */
+ah_status ah_server_memory(const ah_server* s, uint64_t* budget, uint64_t* reserved, uint64_t* reserved_peak);
+/* Fault injection on the host (no GPU fault): the next n admitted requests find their first
+ * device allocation failing; each fails with AH_ENOMEM and the server goes on serving. */
+ah_status ah_server_inject_alloc_failures(ah_server* s, int n);
 void ah_result_free(ah_result* r);
 /* Finish queued requests, stop the workers and release the server. */
 void ah_server_destroy(ah_server* s);

@@ -16,9 +16,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libah.so")
 
-AH_OK, AH_EINVAL, AH_ENOMEM, AH_ECUDA, AH_EOVERFLOW, AH_ETIMEOUT, AH_EJIT, AH_EINTERNAL, AH_ELIMIT = range(9)
+AH_OK, AH_EINVAL, AH_ENOMEM, AH_ECUDA, AH_EOVERFLOW, AH_ETIMEOUT, AH_EJIT, AH_EINTERNAL, AH_ELIMIT, AH_ECANCELED = range(10)
 STATUS_NAMES = {0: "AH_OK", 1: "AH_EINVAL", 2: "AH_ENOMEM", 3: "AH_ECUDA", 4: "AH_EOVERFLOW", 5: "AH_ETIMEOUT",
-                6: "AH_EJIT", 7: "AH_EINTERNAL", 8: "AH_ELIMIT"}
+                6: "AH_EJIT", 7: "AH_EINTERNAL", 8: "AH_ELIMIT", 9: "AH_ECANCELED"}
 AH_FR, AH_RF, AH_FF, AH_RR = 1, 2, 4, 8
 
 HIT_DTYPE = np.dtype([("record", "<u4"), ("pos", "<u4"), ("pattern", "<u2"), ("mism", "u1"), ("flags", "u1")])
@@ -159,6 +159,15 @@ SIGNATURES = {
     "ah_server_wait": (_I32, [_VP, _U64, ctypes.POINTER(ctypes.POINTER(ah_result))]),
     "ah_server_now": (_I32, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "ah_server_set_scan_mode": (_I32, [_VP, ctypes.c_int]),
+    "ah_server_cancel": (_I32, [_VP, _U64]),
+    "ah_server_request_bytes": (_I32, [_VP, ctypes.POINTER(ah_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "ah_server_memory": (_I32, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                ctypes.POINTER(ctypes.c_uint64)]),
+    "ah_server_inject_alloc_failures": (_I32, [_VP, ctypes.c_int]),
+    "ah_ctx_inject_alloc_failures": (_I32, [_VP, ctypes.c_int]),
+    "ah_plan_launch_host": (_I32, [_VP, _VP, _VP]),
+    "ah_fasta_pack_file": (_I32, [_VP, ctypes.c_char_p, _VP, _PVP, _PVP]),
+    "ah_fastq_pack_file": (_I32, [_VP, ctypes.c_char_p, _VP, _PVP, _PVP, _PVP]),
     "ah_result_free": (None, [ctypes.POINTER(ah_result)]),
     "ah_server_destroy": (None, [_VP]),
 }
@@ -337,6 +346,24 @@ def ah_fastq_pack(ctx, text, genome_ids: Optional[np.ndarray] = None, n_bytes: O
     out, q, h = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     _check(load().ah_fastq_pack(ctx, addr, n, None if gid is None else gid.ctypes.data, ctypes.byref(out),
                                 ctypes.byref(q), ctypes.byref(h) if names else None), ctx)
+    return out, q, (_names_of(h) if names else None)
+
+
+def ah_fasta_pack_file(ctx, path: str, genome_ids: Optional[np.ndarray] = None):
+    """A FASTA file read, parsed and packed; returns (batch, names)."""
+    gid = None if genome_ids is None else np.ascontiguousarray(genome_ids, dtype=np.uint32)
+    out, names = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().ah_fasta_pack_file(ctx, os.fsencode(path), None if gid is None else gid.ctypes.data,
+                                     ctypes.byref(out), ctypes.byref(names)), ctx)
+    return out, _names_of(names)
+
+
+def ah_fastq_pack_file(ctx, path: str, genome_ids: Optional[np.ndarray] = None, names: bool = True):
+    """A FASTQ file read, parsed and packed; returns (batch, quals, names or None)."""
+    gid = None if genome_ids is None else np.ascontiguousarray(genome_ids, dtype=np.uint32)
+    out, q, h = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().ah_fastq_pack_file(ctx, os.fsencode(path), None if gid is None else gid.ctypes.data,
+                                     ctypes.byref(out), ctypes.byref(q), ctypes.byref(h) if names else None), ctx)
     return out, q, (_names_of(h) if names else None)
 
 
@@ -711,10 +738,9 @@ def ah_server_create(db, n_slots: int = 4, memory_budget: int = 0):
     return out
 
 
-def ah_server_submit(server, fwd: Sequence[str], rev: Sequence[str], k: Sequence[int], clamp: int, first_record: int,
-                     n_records: int, min_len: int, max_len: int, orient_mask: int = 15,
-                     tm: Optional[ah_tm_params] = None, extract: bool = True, trim: bool = False, fb_len: int = 0,
-                     rb_len: int = 0) -> int:
+def _request(fwd, rev, k, clamp, first_record, n_records, min_len, max_len, orient_mask=15, tm=None, extract=True,
+             trim=False, fb_len=0, rb_len=0):
+    """An ah_request and the buffers it points to (kept alive with it)."""
     n = len(fwd)
     fa = (ctypes.c_char_p * n)(*[x.encode("ascii") for x in fwd])
     ra = (ctypes.c_char_p * n)(*[x.encode("ascii") for x in rev])
@@ -722,9 +748,51 @@ def ah_server_submit(server, fwd: Sequence[str], rev: Sequence[str], k: Sequence
     r = ah_request(n, ctypes.cast(fa, ctypes.c_void_p), ctypes.cast(ra, ctypes.c_void_p), ka.ctypes.data, clamp,
                    first_record, n_records, min_len, max_len, orient_mask, tm if tm is not None else tm_params(),
                    int(bool(extract)), int(bool(trim)), fb_len, rb_len)
+    return r, (fa, ra, ka)
+
+
+def ah_server_submit(server, fwd: Sequence[str], rev: Sequence[str], k: Sequence[int], clamp: int, first_record: int,
+                     n_records: int, min_len: int, max_len: int, orient_mask: int = 15,
+                     tm: Optional[ah_tm_params] = None, extract: bool = True, trim: bool = False, fb_len: int = 0,
+                     rb_len: int = 0) -> int:
+    r, keep = _request(fwd, rev, k, clamp, first_record, n_records, min_len, max_len, orient_mask, tm, extract, trim,
+                       fb_len, rb_len)
     t = ctypes.c_uint64()
     _check(load().ah_server_submit(server, ctypes.byref(r), ctypes.byref(t)))
     return t.value
+
+
+def ah_server_request_bytes(server, **req) -> int:
+    """Device bytes the server reserves when it admits this request (same keywords as ah_server_submit)."""
+    r, keep = _request(**req)
+    b = ctypes.c_uint64()
+    _check(load().ah_server_request_bytes(server, ctypes.byref(r), ctypes.byref(b)))
+    return b.value
+
+
+def ah_server_cancel(server, ticket: int) -> None:
+    _check(load().ah_server_cancel(server, ticket))
+
+
+def ah_server_memory(server) -> dict:
+    b, r, p = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().ah_server_memory(server, ctypes.byref(b), ctypes.byref(r), ctypes.byref(p)))
+    return {"budget": b.value, "reserved": r.value, "reserved_peak": p.value}
+
+
+def ah_server_inject_alloc_failures(server, n: int) -> None:
+    _check(load().ah_server_inject_alloc_failures(server, int(n)))
+
+
+def ah_plan_launch_host(plan, h_seq: int, offsets: np.ndarray, ctx=None) -> None:
+    """The plan's step on genomes in host memory at address h_seq (records at offsets, uint64,
+    n_records + 1 entries), the scan overlapping the upload."""
+    offs = np.ascontiguousarray(offsets, dtype=np.uint64)
+    _check(load().ah_plan_launch_host(plan, h_seq, offs.ctypes.data), ctx)
+
+
+def ah_ctx_inject_alloc_failures(ctx, n: int) -> None:
+    _check(load().ah_ctx_inject_alloc_failures(ctx, int(n)), ctx)
 
 
 def ah_server_wait(server, ticket: int) -> dict:

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libah.so")
 SOURCES = ["ah_api.cu", "ah_util.cu", "ah_scan.cu", "ah_pair.cu", "ah_tm.cu", "ah_extract.cu", "ah_plan.cu", "ah_fasta.cu", "ah_jit.cpp",
-           "ah_serve.cpp", "ah_output.cpp"]
+           "ah_serve.cpp", "ah_output.cpp", "ah_files.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -539,6 +539,12 @@ ah_status ah_ctx_set_generic_scan(ah_ctx* ctx, int mode) {
   return AH_OK;
 }
 
+ah_status ah_ctx_inject_alloc_failures(ah_ctx* ctx, int n) {
+  if (!ctx || n < 0) return AH_EINVAL;
+  ctx->fail_allocs = n;
+  return AH_OK;
+}
+
 ah_status ah_ctx_set_timing(ah_ctx* ctx, int enable) {
   if (!ctx) return AH_EINVAL;
   cudaSetDevice(ctx->device);
@@ -558,8 +564,12 @@ namespace {
 // become one copy per chunk of up to kChunkBases bases, into one of two staging buffers on a second
 // stream, while the context's stream packs the previous chunk from HBM.  Synchronises.
 // src[i]: record first + i.  one_buffer: every src lies in one allocation (its kind is checked once)
+// on_chunk (may be empty): called after each staged chunk's packing is enqueued on ctx->stream with
+// the end of the groups it completes (the pieces come in batch order, so with first == 0 every group
+// below it holds its final contents once the stream reaches that point); with it set, the call
+// returns without waiting for the context's stream.
 ah_status pack_records(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t n, const char* const* src,
-                       bool one_buffer = false) {
+                       bool one_buffer = false, const std::function<void(uint64_t)>& on_chunk = {}) {
   bool on_device = true;
   std::vector<uint64_t> dev_addr(n, 0);
   bool checked = false;
@@ -585,7 +595,9 @@ ah_status pack_records(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t n, con
   if (on_device) {
     std::vector<PackItem> items;
     for (uint32_t i = 0; i < n; ++i) add_items(items, b, first + i, 0, b->h_rec_len[first + i], dev_addr[i]);
-    return run_pack(ctx, nullptr, items, b);
+    ah_status st = run_pack(ctx, nullptr, items, b);
+    if (!st && on_chunk) on_chunk(b->n_groups);
+    return st;
   }
   // chunks of host pieces (records split on group boundaries), each piece at the staging offset that
   // continues the previous one, so a run of pieces contiguous in host memory is one copy
@@ -662,8 +674,13 @@ ah_status pack_records(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t n, con
     if (e == cudaSuccess && !items[c].empty())
       launch_pack(ctx->stream, staging[w], d_items + at[c], items[c].data(), items[c].size(), b, ctx);
     if (e == cudaSuccess) e = cudaEventRecord(packed[w], ctx->stream);
+    if (e == cudaSuccess && on_chunk) {
+      uint64_t done = 0;
+      for (const PackItem& it : items[c]) done = std::max(done, it.dst_group + it.n_groups);
+      on_chunk(c + 1 == runs.size() ? b->n_groups : done);
+    }
   }
-  if (!st && e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (!st && e == cudaSuccess && !on_chunk) e = cudaStreamSynchronize(ctx->stream);
   if (!st && e != cudaSuccess) st = fail(ctx, AH_ECUDA, "packing failed: %s", cudaGetErrorString(e));
   if (cs) {
     cudaStreamSynchronize(cs);
@@ -681,6 +698,23 @@ ah_status pack_records(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t n, con
 }
 
 }  // namespace
+
+}  // extern "C"
+
+namespace ah {
+ah_status pack_host_staged(ah_ctx* ctx, ah_batch* b, const uint8_t* h_seq, const uint64_t* h_offsets,
+                           const std::function<void(uint64_t)>& on_chunk) {
+  std::vector<const char*> src(b->n_records);
+  for (uint32_t i = 0; i < b->n_records; ++i) {
+    if (h_offsets[i + 1] < h_offsets[i] || h_offsets[i + 1] - h_offsets[i] != b->h_rec_len[i])
+      return fail(ctx, AH_EINVAL, "record %u length differs from the batch layout", i);
+    src[i] = (const char*)h_seq + h_offsets[i];
+  }
+  return pack_records(ctx, b, 0, b->n_records, src.data(), true, on_chunk);
+}
+}  // namespace ah
+
+extern "C" {
 
 ah_status ah_pack_batch(ah_ctx* ctx, uint32_t n_rec, const char* const* seqs, const uint64_t* lens,
                         const uint32_t* genome_ids, ah_batch** out) {
@@ -796,6 +830,7 @@ ah_status ah_batch_pack_range(ah_ctx* ctx, ah_batch* b, uint32_t first, uint32_t
   }
   return pack_records(ctx, b, first, count, src.data(), true);
 }
+
 
 ah_status ah_batch_export(const ah_batch* b, void* planes_out, uint64_t* n_invalid, uint64_t* inv_groups,
                           uint32_t* inv_words) {
@@ -932,9 +967,18 @@ ah_status ah_primers_create(ah_ctx* ctx, uint32_t n_pairs, const char* const* fw
       }
     }
   }
+  // each primer as four position masks, bit j of mask c: position j allows base code c
+  std::vector<uint4> pmask(2 * (size_t)n_pairs);
+  for (size_t q = 0; q < pmask.size(); ++q) {
+    uint32_t m[4] = {0, 0, 0, 0};
+    for (int j = 0; j < 32; ++j)
+      for (int c = 0; c < 4; ++c) m[c] |= (uint32_t)((psets[q * 32 + j] >> c) & 1u) << j;
+    pmask[q] = make_uint4(m[0], m[1], m[2], m[3]);
+  }
   ah_status st = dalloc(ctx, &p->d_plen, plen.size());
   if (!st) st = dalloc(ctx, &p->d_psets, psets.size());
   if (!st) st = dalloc(ctx, &p->d_pk, p->k.size());
+  if (!st) st = dalloc(ctx, &p->d_pmask, pmask.size());
   const std::vector<GenPattern> gen = gen_table(p->pats);
   if (!st) st = dalloc(ctx, &p->d_gen, gen.size());
   if (!st) {
@@ -942,6 +986,7 @@ ah_status ah_primers_create(ah_ctx* ctx, uint32_t n_pairs, const char* const* fw
     cudaMemcpyAsync(p->d_plen, plen.data(), plen.size(), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemcpyAsync(p->d_psets, psets.data(), psets.size(), cudaMemcpyHostToDevice, ctx->stream);
     cudaMemcpyAsync(p->d_pk, p->k.data(), p->k.size(), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(p->d_pmask, pmask.data(), pmask.size() * sizeof(uint4), cudaMemcpyHostToDevice, ctx->stream);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = fail(ctx, AH_ECUDA, "primer upload failed");
   }
   if (st) {
@@ -958,6 +1003,7 @@ void ah_primers_free(ah_primers* p) {
     dfree(p->ctx, p->d_plen);
     dfree(p->ctx, p->d_psets);
     dfree(p->ctx, p->d_pk);
+    dfree(p->ctx, p->d_pmask);
     dfree(p->ctx, p->d_gen);
   }
   delete p;

@@ -123,6 +123,8 @@ struct ah_ctx {
   // next synchronised (ah::drain_timings), which also advances drain_gen
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
   uint64_t drain_gen = 0;
+  // fault injection on the host: this many of the next device allocations fail with AH_ENOMEM
+  int fail_allocs = 0;
 };
 
 struct ah_batch {
@@ -152,6 +154,7 @@ struct ah_primers {
   uint8_t* d_plen = nullptr;           // per pattern length
   uint8_t* d_psets = nullptr;          // [n_pairs][2 primers][32] IUPAC sets of the primers as written
   uint8_t* d_pk = nullptr;             // [n_pairs] mismatch budget
+  uint4* d_pmask = nullptr;            // [n_pairs][2 primers] position masks per base code (A, C, T, G)
   ah::GenPattern* d_gen = nullptr;     // the patterns as the generic scan kernel reads them
 };
 
@@ -199,6 +202,10 @@ template <class T>
 ah_status dalloc(ah_ctx* ctx, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
+  if (ctx->fail_allocs > 0) {
+    ctx->fail_allocs--;
+    return fail(ctx, AH_ENOMEM, "device allocation of %zu bytes failed: injected failure", count * sizeof(T));
+  }
   cudaError_t e = cudaMallocFromPoolAsync((void**)p, count * sizeof(T), ctx->pool, ctx->stream);
   if (e != cudaSuccess) return fail(ctx, AH_ENOMEM, "device allocation of %zu bytes failed: %s", count * sizeof(T),
                                     cudaGetErrorString(e));
@@ -224,6 +231,12 @@ ah_status read_u64(ah_ctx* ctx, const uint64_t* d, uint64_t* h);
 // record's bytes by them).  Synchronises.
 ah_status pack_batch_ranked(ah_ctx* ctx, uint32_t n, const uint8_t* d_seq, const uint64_t* d_rank,
                             const uint64_t* h_rank, const uint32_t* genome_ids, ah_batch** out);
+// Repack every record of b from host (or device) memory at h_seq[h_offsets[r], h_offsets[r + 1]) in
+// staged chunks, calling on_chunk after each chunk's packing is enqueued on ctx->stream with the
+// number of leading groups it completes (b->n_groups for the last).  Returns without waiting for
+// the stream.
+ah_status pack_host_staged(ah_ctx* ctx, ah_batch* b, const uint8_t* h_seq, const uint64_t* h_offsets,
+                           const std::function<void(uint64_t)>& on_chunk);
 // read and clear the device status word (synchronises)
 ah_status check_status(ah_ctx* ctx);
 // accumulate the pending scan-node timings of graph replays into the context's counters (syncs)
@@ -258,6 +271,9 @@ void exclusive_scan_u32_s(cudaStream_t s, const uint32_t* d_in, uint64_t* d_out,
 void exclusive_scan_u64_s(cudaStream_t s, const uint64_t* d_in, uint64_t* d_out, uint64_t n, uint64_t* scratch);
 void launch_scan_kernel(cudaStream_t s, const ScanKernel& k, const ah_batch* b, uint64_t* slots, uint32_t* tile_count,
                         uint32_t cap, uint32_t* status, unsigned long long* work, uint64_t n_tiles, int grid);
+// a one-CTA-per-tile kernel over groups [g0, g1) of b (g0 a multiple of the tile, g1 of it or the end)
+void launch_scan_range(cudaStream_t s, const ScanKernel& k, const ah_batch* b, uint64_t* slots, uint32_t* tile_count,
+                       uint32_t cap, uint32_t* status, uint64_t g0, uint64_t g1);
 void launch_tile_max(cudaStream_t s, const uint32_t* tile_count, uint64_t n_tiles, uint32_t* out);
 size_t prepare_tile_sort(uint32_t cap, int* warps_out);
 // sorts every tile's keys and counts them per pair; big: n_tiles + 1 words of device scratch, used
@@ -275,8 +291,7 @@ void launch_pair_walk(cudaStream_t s, bool emit, const ah_hit* hits, uint64_t ca
 constexpr size_t kTmRunBytes = 128;  // room for the Tm run constants a plan keeps
 ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, size_t run_size);
 void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit_cap, const uint64_t* d_nhits,
-               const uint8_t* pk, int clamp, uint32_t* status,
-               const uint2* planes, const uint64_t* rec_group, const uint8_t* plen, const uint8_t* psets, double* hit_tm,
+               const ah_primers* p, uint32_t* status, const uint2* planes, const uint64_t* rec_group, double* hit_tm,
                ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep);
 void launch_compact_amps(cudaStream_t s, const ah_amplicon* in, uint64_t cap, const uint32_t* keep, const uint64_t* off,
                          ah_amplicon* out);

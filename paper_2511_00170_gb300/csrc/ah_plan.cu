@@ -62,6 +62,11 @@ struct ah_plan {
   int ring_next = 0;
   uint64_t kernel_nodes = 0;    // kernels one replay launches
   ah_plan_info info{};
+  // the step after the scan as a graph of its own, and a one-CTA-per-tile scan kernel, for runs
+  // whose scan is launched range by range as the input lands (ah_plan_launch_host)
+  cudaGraphExec_t post_exec = nullptr;
+  uint64_t post_kernel_nodes = 0;
+  ah::ScanKernel range_kern;
 };
 
 namespace ah {
@@ -79,6 +84,8 @@ void free_buffers(ah_plan* pl) {
   pl->hit_tm = nullptr, pl->keep = nullptr, pl->koff = nullptr, pl->kept = nullptr, pl->elen = nullptr;
   pl->ebase = nullptr, pl->arena = nullptr, pl->field_off = nullptr, pl->ctr = nullptr;
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->post_exec) cudaGraphExecDestroy(pl->post_exec);
+  pl->post_exec = nullptr;
   for (auto& x : pl->ring)
     if (x) cudaGraphExecDestroy(x), x = nullptr;
   if (pl->graph) cudaGraphDestroy(pl->graph);
@@ -104,19 +111,30 @@ ah_status alloc_buffers(ah_plan* pl) {
   return AH_OK;
 }
 
-// the step, enqueued on stream s (captured into the graph)
-void enqueue_step(ah_plan* pl, cudaStream_t s) {
-  const ah_batch* b = pl->b;
-  const ah_primers* p = pl->p;
-  const ah_plan_params& q = pl->prm;
+// the step, enqueued on stream s (captured into the graph): the counters' reset, the scan, and
+// everything after the scan
+void enqueue_pre(ah_plan* pl, cudaStream_t s) {
   cudaMemsetAsync(pl->tile_count, 0, pl->n_tiles * sizeof(uint32_t), s);
   cudaMemsetAsync(pl->tpc, 0, pl->n_cells * sizeof(uint32_t), s);
   cudaMemsetAsync(pl->ctr, 0, 4 * sizeof(uint32_t), s);
+}
+
+void enqueue_post(ah_plan* pl, cudaStream_t s);
+
+void enqueue_step(ah_plan* pl, cudaStream_t s) {
+  enqueue_pre(pl, s);
   // external records become event-record nodes of the captured graph
   cudaEventRecordWithFlags(pl->scan_ev[0], s, cudaEventRecordExternal);
-  launch_scan_kernel(s, pl->kern, b, pl->slots, pl->tile_count, pl->slot_cap, pl->ctx->d_status,
+  launch_scan_kernel(s, pl->kern, pl->b, pl->slots, pl->tile_count, pl->slot_cap, pl->ctx->d_status,
                      (unsigned long long*)(pl->ctr + 2), pl->n_tiles, pl->grid);
   cudaEventRecordWithFlags(pl->scan_ev[1], s, cudaEventRecordExternal);
+  enqueue_post(pl, s);
+}
+
+void enqueue_post(ah_plan* pl, cudaStream_t s) {
+  const ah_batch* b = pl->b;
+  const ah_primers* p = pl->p;
+  const ah_plan_params& q = pl->prm;
   launch_tile_max(s, pl->tile_count, pl->n_tiles, pl->ctr + 0);
   launch_tile_sort(s, pl->slots, pl->tile_count, pl->slot_cap, pl->n_tiles, p->n_pairs, pl->tpc, pl->big,
                    pl->ctx->sm_count);
@@ -130,7 +148,7 @@ void enqueue_step(ah_plan* pl, cudaStream_t s) {
   launch_pair_walk(s, true, pl->hits, pl->hit_cap, n_hits, pl->pair_off, p->d_plen, q.min_len, q.max_len,
                    q.orient_mask & 15u, nullptr, pl->poff, pl->amps, pl->amp_cap, pl->ctr + 1);
   const uint64_t* n_amps = pl->poff + pl->hit_cap;
-  launch_tm(s, pl->tm_run, pl->hits, pl->hit_cap, n_hits, p->d_pk, p->clamp, pl->ctx->d_status, b->planes, b->rec_group, p->d_plen, p->d_psets, pl->hit_tm,
+  launch_tm(s, pl->tm_run, pl->hits, pl->hit_cap, n_hits, p, pl->ctx->d_status, b->planes, b->rec_group, pl->hit_tm,
             pl->amps, pl->amp_cap, n_amps, q.tm.filter, q.tm.min_tm, pl->keep);
   const ah_amplicon* out = pl->amps;
   const uint64_t* n_out = n_amps;
@@ -394,6 +412,77 @@ ah_status ah_plan_launch(ah_plan* pl) {
   AH_CUDA(c, cudaGraphLaunch(x, c->stream));
   c->n_launches += pl->kernel_nodes;
   c->scan_ops_per_group = pl->kern.alu_ops_per_group;
+  return AH_OK;
+}
+
+namespace {
+
+// the post-scan graph, captured on first use after the plan's buffers last changed
+ah_status ensure_post(ah_plan* pl) {
+  if (pl->post_exec) return AH_OK;
+  ah_ctx* c = pl->ctx;
+  cudaStream_t s = c->stream;
+  AH_CUDA(c, cudaStreamSynchronize(s));
+  prepare_tile_sort(pl->slot_cap, nullptr);
+  AH_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  enqueue_post(pl, s);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess) return fail(c, AH_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  size_t n = 0;
+  cudaGraphGetNodes(g, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n) cudaGraphGetNodes(g, nodes.data(), &n);
+  pl->post_kernel_nodes = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) pl->post_kernel_nodes++;
+  }
+  e = cudaGraphInstantiate(&pl->post_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(c, AH_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  return AH_OK;
+}
+
+}  // namespace
+
+ah_status ah_plan_launch_host(ah_plan* pl, const uint8_t* h_seq, const uint64_t* h_offsets) {
+  if (!pl || !h_seq || !h_offsets) return AH_EINVAL;
+  ah_ctx* c = pl->ctx;
+  cudaSetDevice(c->device);
+  ah_status st;
+  if (!pl->range_kern.fn) {
+    if (pl->cfg.persistent) {
+      ScanConfig cfg = pl->cfg;
+      cfg.persistent = 0;
+      if ((st = c->jit->get(c, pl->p->pats, cfg, &pl->range_kern))) return st;
+    } else {
+      pl->range_kern = pl->kern;
+    }
+  }
+  if ((st = ensure_post(pl))) return st;
+  ah_batch* b = const_cast<ah_batch*>(pl->b);
+  enqueue_pre(pl, c->stream);
+  // tiles whose groups and the group after them are packed are scanned at once, while the next
+  // chunk crosses the link
+  const uint64_t tg = (uint64_t)pl->range_kern.threads * pl->range_kern.groups_per_thread;
+  uint64_t scanned = 0;
+  uint64_t scan_launches = 0;
+  auto on_chunk = [&](uint64_t done) {
+    const uint64_t upto = done >= b->n_groups ? b->n_groups : (done > 0 ? (done - 1) / tg * tg : 0);
+    if (upto > scanned) {
+      launch_scan_range(c->stream, pl->range_kern, b, pl->slots, pl->tile_count, pl->slot_cap, c->d_status, scanned,
+                        upto);
+      scanned = upto;
+      ++scan_launches;
+    }
+  };
+  if ((st = pack_host_staged(c, b, h_seq, h_offsets, on_chunk))) return st;
+  on_chunk(b->n_groups);
+  AH_CUDA(c, cudaGetLastError());
+  AH_CUDA(c, cudaGraphLaunch(pl->post_exec, c->stream));
+  c->n_launches += pl->post_kernel_nodes + scan_launches;
+  c->scan_ops_per_group = pl->range_kern.alu_ops_per_group;
   return AH_OK;
 }
 

@@ -346,6 +346,16 @@ void launch_scan_kernel(cudaStream_t s, const ScanKernel& k, const ah_batch* b, 
   cudaLaunchKernel((const void*)k.fn, dim3((unsigned)(grid > 0 ? grid : n_tiles)), dim3((unsigned)k.threads), args, 0, s);
 }
 
+void launch_scan_range(cudaStream_t s, const ScanKernel& k, const ah_batch* b, uint64_t* slots, uint32_t* tile_count,
+                       uint32_t cap, uint32_t* status, uint64_t g0, uint64_t g1) {
+  const uint64_t tg = (uint64_t)k.threads * k.groups_per_thread;
+  if (g1 <= g0) return;
+  ScanParamsHost P{b->planes, b->invalid, b->rec_group, b->rec_len, b->n_records, cap, g0, g1 - g0,
+                   slots, tile_count, status, tg, nullptr, 0};
+  void* args[] = {&P};
+  cudaLaunchKernel((const void*)k.fn, dim3((unsigned)((g1 - g0 + tg - 1) / tg)), dim3((unsigned)k.threads), args, 0, s);
+}
+
 void launch_tile_max(cudaStream_t s, const uint32_t* tile_count, uint64_t n_tiles, uint32_t* out) {
   k_tile_max<<<std::max<uint64_t>(1, std::min<uint64_t>(1024, (n_tiles + 255) / 256)), 256, 0, s>>>(tile_count, n_tiles,
                                                                                                      out);

@@ -2,12 +2,18 @@
 //
 // The database is one packed batch kept in HBM.  A request brings a primer set, its parameters and
 // a genome subset (a contiguous range of database records).  The server runs `n_slots` workers,
-// each with its own context (CUDA stream) and host thread.  Requests wait in arrival order; the
-// first one is admitted as soon as a worker is free and its estimated device memory fits under the
-// budget next to the requests already running, so requests of different sizes that arrive while
-// others are on the GPU join as slots and memory free up, and their kernels overlap on the device.
+// each with its own context (CUDA stream) and host thread.  Requests queue in arrival order; one
+// is admitted as soon as a worker is free and its device memory fits under the budget next to the
+// requests already running, so requests of different sizes that arrive while others are on the
+// GPU join as slots and memory free up, and their kernels overlap on the device.
 // Each admitted request runs the whole path on a slice of the database (no copy of the genomes)
 // and its results are copied to host memory owned by the request's result.
+//
+// Admission takes the oldest queued request that fits, so a small request is not held behind a
+// large one that must wait for memory; a request that has been passed over kMaxBypass times is
+// then waited for, so large requests are not starved.  A running request's reservation starts at
+// its estimate and grows to the memory its context's pool actually holds, measured after each
+// stage (sites, amplicons and sequences are only known then), so later admissions see real use.
 //
 // Each worker owns one CUDA stream per priority class.  A request runs on the stream of its class,
 // chosen by its scan work (bases x 4 x pairs): the smaller the request, the higher the priority,
@@ -41,9 +47,16 @@ struct Job {
   std::vector<uint8_t> k;
   ah_request req{};
   uint64_t est_bytes = 0;
+  uint64_t reserved = 0;          // bytes held against the budget while it runs
+  int bypassed = 0;               // later requests admitted ahead of it
+  std::atomic<bool> cancel{false};
+  int inject_enomem = 0;          // device allocations of this run that fail (fault injection)
   ah_result* result = nullptr;
   bool done = false;
 };
+
+// later requests that may be admitted ahead of a waiting one before it blocks the queue
+constexpr int kMaxBypass = 8;
 
 }  // namespace
 
@@ -63,6 +76,8 @@ struct ah_server {
   uint64_t next_ticket = 1;
   bool stop = false;
   int running = 0;
+  int inject_enomem = 0;          // admitted requests still to fail their first device allocation
+  uint64_t reserved_peak = 0;
 };
 
 namespace ah {
@@ -84,6 +99,30 @@ uint64_t estimate_bytes(const ah_server* s, const ah_request& r, int slot_cap, u
 int priority_class(double work, int n_classes) {
   const int c = work < 1e11 ? 0 : work < 1e12 ? 1 : 2;
   return std::min(c, n_classes - 1);
+}
+
+// index in the queue of the request to admit now, or -1: the oldest that fits beside the running
+// ones (any request when nothing runs), but none past a request that has been passed over
+// kMaxBypass times
+long pick_job(const ah_server* s) {
+  for (size_t q = 0; q < s->queue.size(); ++q) {
+    const Job* j = s->queue[q];
+    if (s->reserved == 0 || s->reserved + j->reserved <= s->budget) return (long)q;
+    if (j->bypassed >= kMaxBypass) return -1;
+  }
+  return -1;
+}
+
+// grow a running request's reservation to what its context's pool holds now
+void account(ah_server* s, Job* j, ah_ctx* ctx) {
+  unsigned long long used = 0;   // the attribute is a 64-bit unsigned count
+  if (cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lock(s->mu);
+  if ((uint64_t)used > j->reserved) {
+    s->reserved += (uint64_t)used - j->reserved;
+    j->reserved = (uint64_t)used;
+    s->reserved_peak = std::max(s->reserved_peak, s->reserved);
+  }
 }
 
 void fill_error(ah_result* res, ah_status st, const char* msg) {
@@ -113,16 +152,25 @@ void run_job(ah_server* s, int slot, Job* j) {
   for (uint32_t i = 0; i < r.n_pairs; ++i) f[i] = j->fwd[i].c_str(), rv[i] = j->rev[i].c_str();
   // stage end times; a stage that synchronises the stream anyway is timed when it returns
   auto stage = [&](int i) { res->t_stage[i] = now_s(s->t0); };
-  ah_status st = ah_batch_slice(ctx, s->db, r.first_record, r.n_records, &slice);
+  ctx->fail_allocs = j->inject_enomem;
+  // between stages: a cancelled request stops, and its reservation follows its real use
+  auto next = [&](ah_status st) {
+    account(s, j, ctx);
+    if (!st && j->cancel.load()) return fail(ctx, AH_ECANCELED, "request cancelled");
+    return st;
+  };
+  ah_status st = j->cancel.load() ? fail(ctx, AH_ECANCELED, "request cancelled") : AH_OK;
+  if (!st) st = ah_batch_slice(ctx, s->db, r.first_record, r.n_records, &slice);
   if (!st) st = ah_primers_create(ctx, r.n_pairs, f.data(), rv.data(), j->k.data(), r.clamp, &pr);
   stage(0);
-  if (!st) st = ah_scan_primers(ctx, slice, pr, &h);
+  if (!st) st = next(ah_scan_primers(ctx, slice, pr, &h));
   stage(1);
-  if (!st) st = ah_pair_amplicons(ctx, slice, pr, h, r.min_len, r.max_len, r.orient_mask, &a);
+  if (!st) st = next(ah_pair_amplicons(ctx, slice, pr, h, r.min_len, r.max_len, r.orient_mask, &a));
   stage(2);
-  if (!st) st = ah_tm_filter(ctx, slice, pr, h, a, &r.tm);
+  if (!st) st = next(ah_tm_filter(ctx, slice, pr, h, a, &r.tm));
   stage(3);
-  if (!st && r.extract) st = ah_extract_barcodes(ctx, slice, pr, h, a, r.trim, r.fb_len, r.rb_len);
+  if (!st && r.extract) st = next(ah_extract_barcodes(ctx, slice, pr, h, a, r.trim, r.fb_len, r.rb_len));
+  ctx->fail_allocs = 0;
   if (!st) {
     res->n_hits = h->n;
     res->n_amps = a->n;
@@ -155,19 +203,25 @@ void worker(ah_server* s, int slot) {
     Job* j = nullptr;
     {
       std::unique_lock<std::mutex> lock(s->mu);
+      long q = -1;
       s->cv_work.wait(lock, [&] {
-        if (s->stop) return true;
-        if (s->queue.empty()) return false;
-        // admit the oldest request when its memory fits next to the running ones (always when the
-        // device is otherwise idle, so an oversized request still runs alone)
-        return s->reserved == 0 || s->reserved + s->queue.front()->est_bytes <= s->budget;
+        if (s->stop && s->queue.empty()) return true;
+        // the oldest request whose memory fits next to the running ones (always one when the device
+        // is otherwise idle, so an oversized request still runs alone)
+        q = pick_job(s);
+        return q >= 0;
       });
-      if (s->stop && s->queue.empty()) return;
-      if (s->queue.empty()) continue;
-      j = s->queue.front();
-      s->queue.pop_front();
-      s->reserved += j->est_bytes;
+      if (q < 0) return;   // stopping, nothing queued
+      j = s->queue[(size_t)q];
+      for (long e = 0; e < q; ++e) s->queue[(size_t)e]->bypassed++;
+      s->queue.erase(s->queue.begin() + q);
+      s->reserved += j->reserved;
+      s->reserved_peak = std::max(s->reserved_peak, s->reserved);
       s->running++;
+      if (s->inject_enomem > 0) {
+        s->inject_enomem--;
+        j->inject_enomem = 1;
+      }
       j->result->t_admit = now_s(s->t0);
     }
     s->cv_work.notify_all();
@@ -175,7 +229,7 @@ void worker(ah_server* s, int slot) {
     {
       std::lock_guard<std::mutex> lock(s->mu);
       j->result->t_done = j->result->t_stage[4] = now_s(s->t0);
-      s->reserved -= j->est_bytes;
+      s->reserved -= j->reserved;
       s->running--;
       j->done = true;
     }
@@ -265,6 +319,7 @@ ah_status ah_server_submit(ah_server* s, const ah_request* r, uint64_t* ticket) 
   j->req.k = nullptr;
   j->result = (ah_result*)calloc(1, sizeof(ah_result));
   j->est_bytes = estimate_bytes(s, *r, 64, (uint64_t)s->ctxs[0]->scan_cfg.threads * s->ctxs[0]->scan_cfg.groups_per_thread);
+  j->reserved = j->est_bytes;
   {
     std::lock_guard<std::mutex> lock(s->mu);
     j->ticket = s->next_ticket++;
@@ -289,6 +344,51 @@ ah_status ah_server_wait(ah_server* s, uint64_t ticket, ah_result** out) {
   *out = j->result;
   delete j;
   return (*out)->status;
+}
+
+ah_status ah_server_cancel(ah_server* s, uint64_t ticket) {
+  if (!s) return AH_EINVAL;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end()) return AH_EINVAL;
+    Job* j = it->second;
+    auto q = std::find(s->queue.begin(), s->queue.end(), j);
+    if (q != s->queue.end()) {   // still queued: finished at once, never admitted
+      s->queue.erase(q);
+      fill_error(j->result, AH_ECANCELED, "request cancelled before admission");
+      j->result->t_admit = j->result->t_done = now_s(s->t0);
+      j->done = true;
+    } else {
+      j->cancel.store(true);     // running: stops at its next stage boundary
+    }
+  }
+  s->cv_done.notify_all();
+  s->cv_work.notify_all();
+  return AH_OK;
+}
+
+ah_status ah_server_inject_alloc_failures(ah_server* s, int n) {
+  if (!s || n < 0) return AH_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->inject_enomem = n;
+  return AH_OK;
+}
+
+ah_status ah_server_request_bytes(const ah_server* s, const ah_request* r, uint64_t* bytes) {
+  if (!s || !r || !bytes || r->n_records == 0 || (uint64_t)r->first_record + r->n_records > s->db->n_records)
+    return AH_EINVAL;
+  *bytes = estimate_bytes(s, *r, 64, (uint64_t)s->ctxs[0]->scan_cfg.threads * s->ctxs[0]->scan_cfg.groups_per_thread);
+  return AH_OK;
+}
+
+ah_status ah_server_memory(const ah_server* s, uint64_t* budget, uint64_t* reserved, uint64_t* reserved_peak) {
+  if (!s) return AH_EINVAL;
+  std::lock_guard<std::mutex> lock(const_cast<ah_server*>(s)->mu);
+  if (budget) *budget = s->budget;
+  if (reserved) *reserved = s->reserved;
+  if (reserved_peak) *reserved_peak = s->reserved_peak;
+  return AH_OK;
 }
 
 ah_status ah_server_set_scan_mode(ah_server* s, int mode) {

@@ -6,6 +6,7 @@
 // site values.  All arithmetic is FP64: the Tm threshold decision needs it.  The parameter tables
 // below are expanded on the host into direct lookups indexed by the four base codes of a step
 // (top 5'-ab-3' over bottom 3'-xy-5'), so a step costs one constant-memory load.
+#include <climits>
 #include <cmath>
 #include <cstring>
 
@@ -491,6 +492,8 @@ template <>
 __device__ __forceinline__ double no_score<double>() { return -INFINITY; }
 template <>
 __device__ __forceinline__ long long no_score<long long>() { return LLONG_MIN; }
+template <>
+__device__ __forceinline__ int no_score<int>() { return INT_MIN; }
 
 template <typename T>
 __device__ bool chain_viterbi(const SiteVariants& V, T A, T B, T* best_score, int* dh10, int* ds10) {
@@ -610,7 +613,7 @@ __device__ ChainResult site_tm_chain(const SiteVariants& V, const TmRun& R, doub
 // is defined.  Up to kEnumSmall qualifying variants are enumerated; more take the chain method (salt
 // methods 0-5), and where that does not apply they are enumerated up to kEnumLimit.  Beyond that the
 // site gets NaN and ST_TM_LIMIT is raised.
-__device__ double site_tm(const uint8_t* sets, const uint8_t* s, int L, int k, int clamp, const TmRun& R,
+__device__ __noinline__ double site_tm(const uint8_t* sets, const uint8_t* s, int L, int k, int clamp, const TmRun& R,
                           uint32_t* status) {
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   SiteVariants V;
@@ -633,6 +636,289 @@ __device__ __forceinline__ uint8_t base_code(const uint2* planes, uint64_t group
   const uint2 w = planes[group0 + (x >> 5)];
   const uint32_t bit = (uint32_t)(x & 31);
   return (uint8_t)(((w.x >> bit) & 1u) | (((w.y >> bit) & 1u) << 1));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Degenerate site Tm, one group of G lanes per site (G = 4, 8, 16 or 32 lanes of one warp).
+//
+// The chain of the variants only branches at the primer's degenerate positions: a position with a
+// single choice contributes fixed terms.  So the chain is first compressed onto the D degenerate
+// positions d_0 < ... < d_{D-1}: the sums of every edge between d_t and d_{t+1} are folded into one
+// weight per pair of choices (a at d_t, b at d_{t+1}), those before d_0 into a weight per choice at
+// d_0 and those after d_{D-1} into one per choice at d_{D-1}.  The weights are exact integer sums
+// (tenths) packed as dH * 65536 + dS, computed once per site into shared memory; the passes then
+// walk D - 1 steps instead of L - 1 and read no parameter table.  A step between two single-choice
+// positions lies on every variant, so one without a parameter leaves the site undefined at once.
+//
+// In a pass, lane r of the group holds the state (base r / W, mismatches r % W), W = k + 1 with a
+// mismatch budget k (else W = 1), and takes its best predecessor from the lanes of the previous
+// position by shuffles.  The group's lanes share every loop bound, so they stay converged.
+//
+// The iteration is site_tm_chain's with two passes saved: the sign condition (every variant's
+// entropy sum D < 0) is first tried with a bound (the sum of each step's largest dS), and the pass
+// that finds the largest dS runs only when the bound does not settle it; after the start pass the
+// iterations run in exact arithmetic at once (64-bit fixed point, double beyond 4000 K), so the pass
+// that shows the optimum is also the one that proves it.  Sites whose chain does not apply (salt
+// methods 6 and 7, L < 3, an entropy sum that could reach zero, state widths above G / 4) are handed
+// whole to site_tm by the group's first lane.
+constexpr int32_t kNoEdge = INT32_MIN;  // packed weight of a transition with no parameter
+
+struct TmGroupSh {      // per site, in shared memory; followed by the (D - 1) x 16 step weights
+  uint8_t set[32];      // the primer's IUPAC sets (5'->3')
+  uint8_t s[32];        // the site's base codes in the primer's orientation
+  uint8_t c[32];        // their complements (the opposite strand, 3'->5')
+  uint8_t ch[32];       // the choices that count at each position (the clamp holds the site's base)
+  uint8_t dpos[32];     // the positions where the chain branches, in order
+  int32_t pre[4], suf[4];
+};
+constexpr int kTmGroupHeadWords = (int)(sizeof(TmGroupSh) / 4);
+static_assert(sizeof(TmGroupSh) % 16 == 0, "group header keeps 16-byte alignment");
+
+// words of shared memory per site for chains of at most dmax branch positions; the stride is 4 more
+// than a multiple of 32 words, so the groups of one warp read different banks
+__host__ __device__ inline int tm_group_words(int dmax) {
+  const int w = kTmGroupHeadWords + 16 * (dmax > 1 ? dmax - 1 : 0);
+  return (w + 31) / 32 * 32 + 4;
+}
+
+__device__ __forceinline__ int unpack_ds(int32_t p) { return (int16_t)(p & 0xffff); }
+__device__ __forceinline__ int unpack_dh(int32_t p) { return (p - unpack_ds(p)) >> 16; }
+__device__ __forceinline__ int fixed_base(uint32_t ch) { return __ffs(ch) - 1; }
+__device__ __forceinline__ int32_t add_packed(int32_t p, int32_t q) {
+  return (p == kNoEdge || q == kNoEdge) ? kNoEdge : p + q;
+}
+
+// packed sums (tenths) of edge i with base x at i and y at i + 1, kNoEdge without a parameter
+__device__ __forceinline__ int32_t edge_packed(const TmGroupSh& sh, int L, int i, int x, int y) {
+  int eh, es;
+  if (!edge_sums(i, L, (uint8_t)x, (uint8_t)y, sh.c, &eh, &es)) return kNoEdge;
+  return eh * 65536 + es;
+}
+
+// One Viterbi pass of the compressed chain: the best score A * dS10 - B * dH10 over the qualifying
+// variants and that variant's exact sums, the same in every lane of the group.
+template <typename T, int G>
+__device__ bool group_viterbi(const TmGroupSh& sh, const int32_t* __restrict__ w, int D, int W, int K, int m0,
+                              int r, unsigned gmask, T A, T B, T* best, int* dh10, int* ds10) {
+  const T none = no_score<T>();
+  const bool live = r < 4 * W;
+  const int b = live ? r / W : 0, m = live ? r % W : 0;
+  T cur = none;
+  int32_t cs = 0;
+  uint32_t chp = sh.ch[sh.dpos[0]];
+  {
+    const int d0 = sh.dpos[0];
+    const int mm = m0 + ((K >= 0 && b != sh.s[d0]) ? 1 : 0);
+    if (live && ((chp >> b) & 1) && mm == m && sh.pre[b] != kNoEdge) {
+      cs = sh.pre[b];
+      cur = A * (T)unpack_ds(cs) - B * (T)unpack_dh(cs);
+    }
+  }
+  for (int t = 0; t + 1 < D; ++t) {
+    const int dn = sh.dpos[t + 1];
+    const uint32_t chn = sh.ch[dn];
+    const int ib = (K >= 0 && b != sh.s[dn]) ? 1 : 0;
+    const int mp = m - ib;
+    const bool ok = live && ((chn >> b) & 1) && mp >= 0;
+    const int32_t* wt = w + t * 16 + b;
+    T nx = none;
+    int32_t ns = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (!((chp >> a) & 1)) continue;  // the same in every lane of the group
+      const int src = a * W + (mp >= 0 ? mp : 0);
+      const T c = __shfl_sync(gmask, cur, src, G);
+      const int32_t pc = __shfl_sync(gmask, cs, src, G);
+      const int32_t p = wt[a * 4];
+      if (ok && c != none && p != kNoEdge) {
+        const T sc = c + (A * (T)unpack_ds(p) - B * (T)unpack_dh(p));
+        if (sc > nx) nx = sc, ns = pc + p;
+      }
+    }
+    cur = nx, cs = ns, chp = chn;
+  }
+  if (cur != none) {
+    const int32_t p = sh.suf[b];
+    if (p == kNoEdge) {
+      cur = none;
+    } else {
+      cur = cur + (A * (T)unpack_ds(p) - B * (T)unpack_dh(p));
+      cs += p;
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const T oc = __shfl_xor_sync(gmask, cur, o, G);
+    const int32_t ocs = __shfl_xor_sync(gmask, cs, o, G);
+    if (oc > cur || (oc == cur && ocs > cs)) cur = oc, cs = ocs;
+  }
+  if (cur == none) return false;
+  *best = cur;
+  *ds10 = unpack_ds(cs);
+  *dh10 = unpack_dh(cs);
+  return true;
+}
+
+// Tm of the site held in sh (set, s and c filled, L its length) for a primer with mismatch budget k
+// (k >= L: none) and clamp: the maximum over qualifying variants, as site_tm returns it.  Called by
+// all G lanes of the group (lane r, mask gmask); w: the group's weight area (room for dmax - 1 steps).
+template <int G>
+__device__ double group_site_tm(TmGroupSh& sh, int32_t* w, int L, int k, int clamp, const TmRun& R, uint32_t* status,
+                                int r, unsigned gmask) {
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  const int K = k >= L ? -1 : k, W = K < 0 ? 1 : K + 1;
+  // choices per position, the branch positions, and the fixed positions' mismatches
+  uint32_t dmask = 0, empty = 0, fixed_mm = 0;
+  for (int j = r; j < L; j += G) {
+    uint8_t ch = sh.set[j];
+    if (j >= L - clamp) ch &= (uint8_t)(1u << sh.s[j]);
+    sh.ch[j] = ch;
+    const int n = __popc(ch);
+    if (n == 0) empty |= 1u << j;
+    if (n >= 2) dmask |= 1u << j;
+    if (n == 1 && K >= 0 && ch != (1u << sh.s[j])) fixed_mm |= 1u << j;
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    dmask |= __shfl_xor_sync(gmask, dmask, o, G);
+    empty |= __shfl_xor_sync(gmask, empty, o, G);
+    fixed_mm |= __shfl_xor_sync(gmask, fixed_mm, o, G);
+  }
+  if (empty) return nan;
+  const int m0 = __popc(fixed_mm);
+  if (K >= 0 && m0 > K) return nan;
+  if (R.saltcorr >= 6 || L < 3 || W * 4 > G) {
+    __syncwarp(gmask);
+    double t = nan;
+    if (r == 0) t = site_tm(sh.set, sh.s, L, k, clamp, R, status);
+    return __shfl_sync(gmask, t, 0, G);
+  }
+  __syncwarp(gmask);
+  {  // steps between two single-choice positions are on every variant
+    bool bad = false;
+    for (int i = r; i + 1 < L; i += G)
+      if (!((dmask >> i) & 3u) && edge_packed(sh, L, i, fixed_base(sh.ch[i]), fixed_base(sh.ch[i + 1])) == kNoEdge)
+        bad = true;
+    if (__any_sync(gmask, bad)) return nan;
+  }
+  if (!dmask) dmask = 1;  // a concrete primer: a chain of one node with a single choice
+  const int D = __popc(dmask);
+  for (int t = r; t < D; t += G) {  // the t-th set bit of dmask
+    uint32_t x = dmask;
+    for (int q = 0; q < t; ++q) x &= x - 1;
+    sh.dpos[t] = (uint8_t)(__ffs(x) - 1);
+  }
+  __syncwarp(gmask);
+  // weights: before d_0, after d_{D-1}, and between consecutive branch positions
+  if (r < 4) {
+    const int d0 = sh.dpos[0], dl = sh.dpos[D - 1];
+    int32_t p = kNoEdge, q = kNoEdge;
+    if ((sh.ch[d0] >> r) & 1) {
+      int eh, es;
+      end_sums(0, L, (uint8_t)(d0 == 0 ? r : fixed_base(sh.ch[0])), &eh, &es);
+      p = eh * 65536 + es;
+      for (int i = 0; i < d0; ++i)
+        p = add_packed(p, edge_packed(sh, L, i, fixed_base(sh.ch[i]), i + 1 == d0 ? r : fixed_base(sh.ch[i + 1])));
+    }
+    if ((sh.ch[dl] >> r) & 1) {
+      int eh, es;
+      end_sums(L - 1, L, (uint8_t)(dl == L - 1 ? r : fixed_base(sh.ch[L - 1])), &eh, &es);
+      q = eh * 65536 + es;
+      for (int i = dl; i + 1 < L; ++i)
+        q = add_packed(q, edge_packed(sh, L, i, i == dl ? r : fixed_base(sh.ch[i]), fixed_base(sh.ch[i + 1])));
+    }
+    sh.pre[r] = p;
+    sh.suf[r] = q;
+  }
+  for (int t = r; t + 1 < D; t += G) {
+    const int lo = sh.dpos[t], hi = sh.dpos[t + 1];
+    const uint32_t cha = sh.ch[lo], chb = sh.ch[hi];
+    int32_t* wt = w + t * 16;
+    if (hi == lo + 1) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          wt[a * 4 + b] = ((cha >> a) & 1) && ((chb >> b) & 1) ? edge_packed(sh, L, lo, a, b) : kNoEdge;
+    } else {
+      // left step (choice a, then a fixed base), the fixed steps, right step (fixed base, then b)
+      int32_t mid = 0, left[4], right[4];
+      for (int i = lo + 1; i + 1 < hi; ++i)
+        mid += edge_packed(sh, L, i, fixed_base(sh.ch[i]), fixed_base(sh.ch[i + 1]));  // defined: checked above
+      const int fl = fixed_base(sh.ch[lo + 1]), fr = fixed_base(sh.ch[hi - 1]);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        left[a] = (cha >> a) & 1 ? edge_packed(sh, L, lo, a, fl) : kNoEdge;
+        right[a] = (chb >> a) & 1 ? edge_packed(sh, L, hi - 1, fr, a) : kNoEdge;
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) wt[a * 4 + b] = add_packed(add_packed(left[a], mid), right[b]);
+    }
+  }
+  __syncwarp(gmask);
+  // a bound on every variant's dS: each step's largest (tenths)
+  int bound = 0;
+  for (int t = r; t + 1 < D; t += G) {
+    int mx = INT_MIN;
+    for (int e = 0; e < 16; ++e) {
+      const int32_t p = w[t * 16 + e];
+      if (p != kNoEdge) mx = max(mx, unpack_ds(p));
+    }
+    bound += mx == INT_MIN ? 0 : mx;
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) bound += __shfl_xor_sync(gmask, bound, o, G);
+  {
+    int mp = INT_MIN, ms = INT_MIN;
+    for (int x = 0; x < 4; ++x) {
+      if (sh.pre[x] != kNoEdge) mp = max(mp, unpack_ds(sh.pre[x]));
+      if (sh.suf[x] != kNoEdge) ms = max(ms, unpack_ds(sh.suf[x]));
+    }
+    if (mp == INT_MIN || ms == INT_MIN) return nan;  // no choice at an end has its terms
+    bound += mp + ms;
+  }
+  const double S0 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
+  const double H0 = kInitH + kOneGCH + R.sym_h, Sc = kInitS + kOneGCS + R.sym_s;
+  const double shift = R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0;
+  auto ratio = [&](int dh10, int ds10) { return 1000.0 * (0.1 * dh10 + H0) / (0.1 * ds10 + Sc + S0); };
+  int dh10, ds10;
+  float scf;
+  if (0.1 * bound + Sc + S0 >= 0.0) {  // the bound leaves the sign open: the largest dS itself
+    if (!group_viterbi<float, G>(sh, w, D, W, K, m0, r, gmask, 1.f, 0.f, &scf, &dh10, &ds10)) return nan;
+    if (0.1 * ds10 + Sc + S0 >= 0.0) {  // some variant's entropy sum could reach zero: enumerate
+      double t = nan;
+      if (r == 0) t = site_tm(sh.set, sh.s, L, k, clamp, R, status);
+      return __shfl_sync(gmask, t, 0, G);
+    }
+  }
+  // start from the variant that maximises dS - dH / 300 (any defined variant works)
+  if (!group_viterbi<float, G>(sh, w, D, W, K, m0, r, gmask, 300.f, 1000.f, &scf, &dh10, &ds10)) return nan;
+  double lam = ratio(dh10, ds10);
+  int best_h = dh10, best_s = ds10;
+  // exact iterations: a pass that finds no variant scoring above the incumbent at lam proves it
+  // optimal; otherwise the better variant's ratio is the next lam
+  constexpr double kScale = 68719476736.0;  // 2^36
+  for (int it = 0; it < 64; ++it) {
+    bool better;
+    if (fabs(lam) < 4000.0) {
+      const long long Lq = llrint(lam * kScale), Bq = (long long)(1000.0 * kScale);
+      long long sc;
+      if (!group_viterbi<long long, G>(sh, w, D, W, K, m0, r, gmask, Lq, Bq, &sc, &dh10, &ds10)) break;
+      better = sc > Lq * best_s - Bq * best_h;
+    } else {
+      double sc;
+      if (!group_viterbi<double, G>(sh, w, D, W, K, m0, r, gmask, lam, 1000.0, &sc, &dh10, &ds10)) break;
+      const double inc = lam * best_s - 1000.0 * best_h;
+      better = sc > inc + 1e-12 * fabs(inc);
+    }
+    if (!better) break;
+    const double q = ratio(dh10, ds10);
+    if (!(q > lam)) break;
+    lam = q, best_h = dh10, best_s = ds10;
+  }
+  return lam + shift - 273.15;
 }
 
 // Only the sites that some amplicon pairs need a Tm (an amplicon's Tm is the lower of its two
@@ -658,8 +944,15 @@ __global__ void __launch_bounds__(kTmBlock) k_tm_hits(const ah_hit* __restrict__
                           const uint2* __restrict__ planes,
                           const uint64_t* __restrict__ rec_group, const uint8_t* __restrict__ plen,
                           const uint8_t* __restrict__ psets, const uint8_t* __restrict__ pk, int clamp,
-                          const TmRun R, double* __restrict__ out, uint32_t* status,
+                          const TmRun Rp, double* __restrict__ out, uint32_t* status,
                           const uint64_t* __restrict__ d_n = nullptr) {
+  // the run constants in shared memory: device functions take them by reference, and a reference
+  // to a kernel parameter would make the compiler copy it to local memory for every thread
+  __shared__ TmRun R_sh;
+  if (threadIdx.x == 0) R_sh = Rp;
+  __syncthreads();
+  const TmRun& R = R_sh;
+
   __shared__ uint32_t keys[kTmBlock];
   const uint64_t base = (uint64_t)blockIdx.x * kTmBlock;
   const uint64_t n_here = d_n ? min(n, *d_n) : n;
@@ -700,6 +993,656 @@ __global__ void __launch_bounds__(kTmBlock) k_tm_hits(const ah_hit* __restrict__
   out[i] = R.variants ? site_tm(sets, site, L, pk[pair], clamp, R, status) : site_tm(sets, site, L, L, 0, R, status);
 }
 
+// Whether edge i of a variant with bases x at i and y at i + 1 has a parameter, over the opposite
+// strand cc (2-bit codes of position j at bits 2j); the lookups of edge_sums.
+__device__ __forceinline__ bool edge_defined(int i, int L, int x, int y, uint64_t cc) {
+  const int c0 = (int)(cc >> (2 * i)) & 3, c1 = (int)(cc >> (2 * i + 2)) & 3;
+  if (i == 0 && __ldg(&c_nni.term_h[c1 * 64 + c0 * 16 + y * 4 + x]) != kNoParam) return true;
+  if (i == L - 2 && __ldg(&c_nni.term_h[x * 64 + y * 16 + c0 * 4 + c1]) != kNoParam) return true;
+  return __ldg(&c_nni.step_h[x * 64 + y * 16 + c0 * 4 + c1]) != kNoParam;
+}
+
+// The group-per-site form of k_tm_hits.  A block takes a window of kTmWindow site slots, one per
+// thread.  Each thread first settles its slot where that needs no chain: not wanted (no amplicon
+// pairs it), or undefined (a site base outside the clamp's choice, too many fixed mismatches, or a
+// step between single-choice positions without a parameter; the group repeats these checks).  The
+// remaining sites are sorted by primer (so neighbouring groups walk chains of one shape) and taken
+// by the block's S groups of G lanes in rounds.
+// Shared memory: the window's keys and packed site codes, then S site areas of tm_group_words(dmax).
+constexpr int kTmWindow = 128;
+
+template <int G>
+__global__ void __launch_bounds__(kTmWindow) k_tm_hits_g(const ah_hit* __restrict__ hits, uint64_t n,
+                                                         const uint2* __restrict__ planes,
+                                                         const uint64_t* __restrict__ rec_group,
+                                                         const uint8_t* __restrict__ plen,
+                                                         const uint8_t* __restrict__ psets,
+                                                         const uint8_t* __restrict__ pk, int clamp, const TmRun Rp,
+                                                         double* __restrict__ out, uint32_t* status, int dmax,
+                                                         int n_groups, const uint64_t* __restrict__ d_n) {
+  // the run constants in shared memory: device functions take them by reference, and a reference
+  // to a kernel parameter would make the compiler copy it to local memory for every thread
+  __shared__ TmRun R_sh;
+  if (threadIdx.x == 0) R_sh = Rp;
+  __syncthreads();
+  const TmRun& R = R_sh;
+
+  extern __shared__ __align__(16) uint32_t tm_smem[];
+  uint32_t* keys = tm_smem;                                         // kTmWindow
+  uint64_t* codes = reinterpret_cast<uint64_t*>(tm_smem + kTmWindow);  // kTmWindow
+  uint32_t* areas = tm_smem + 3 * kTmWindow;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  const uint64_t base = (uint64_t)blockIdx.x * kTmWindow;
+  const uint64_t n_here = d_n ? min(n, *d_n) : n;
+  {
+    const int t = threadIdx.x;
+    const uint64_t i = base + t;
+    uint32_t key = 0xFFFFFFFFu;
+    if (i < n_here && (unsigned long long)__double_as_longlong(out[i]) == kSiteWanted) {
+      const ah_hit h = hits[i];
+      const int L = plen[h.pattern];
+      const uint32_t pair = h.pattern >> 2, primer = h.pattern & 1u, strand = (h.pattern >> 1) & 1u;
+      // the site's bases over [pos, pos + L) (L <= 32 spans at most two plane words), in the primer's
+      // orientation, 2 bits per position
+      const uint64_t x0 = rec_group[h.record] * 32 + h.pos;
+      const uint2 w0 = planes[x0 >> 5], w1 = planes[(x0 >> 5) + 1];
+      const int sh0 = (int)(x0 & 31);
+      const uint64_t lo = (((uint64_t)w1.x << 32) | w0.x) >> sh0, hi = (((uint64_t)w1.y << 32) | w0.y) >> sh0;
+      uint64_t code = 0;
+      for (int j = 0; j < L; ++j) {
+        const int q = strand == 0 ? j : L - 1 - j;
+        const uint64_t b = ((lo >> q) & 1u) | (((hi >> q) & 1u) << 1);
+        code |= (strand == 0 ? b : b ^ 2u) << (2 * j);
+      }
+      const uint64_t cc = code ^ 0xAAAAAAAAAAAAAAAAull;  // complements: code ^ 2 per position
+      const uint8_t* ps = psets + (pair * 2 + primer) * 32;
+      const int kk = R.variants ? (int)pk[pair] : L, cl = R.variants ? clamp : 0;
+      bool undefined = false;
+      int mism = 0, prev = -1;  // prev: the fixed base of position j - 1 (-1: a choice)
+      for (int j = 0; j < L && !undefined; ++j) {
+        const int sj = (int)(code >> (2 * j)) & 3;
+        uint32_t ch = ps[j];
+        if (j >= L - cl) ch &= 1u << sj;
+        if (!ch) undefined = true;
+        const int cur = __popc(ch) == 1 ? fixed_base(ch) : -1;
+        if (cur >= 0 && cur != sj) ++mism;
+        if (j > 0 && cur >= 0 && prev >= 0 && !edge_defined(j - 1, L, prev, cur, cc)) undefined = true;
+        prev = cur;
+      }
+      if (kk < L && mism > kk) undefined = true;
+      if (undefined) {
+        out[i] = nan;
+      } else {
+        key = ((pair * 2 + primer) << 16) | (uint32_t)t;
+        codes[t] = code;
+      }
+    }
+    keys[t] = key;
+  }
+  const int n_valid = __syncthreads_count(keys[threadIdx.x] != 0xFFFFFFFFu);
+  if (n_valid == 0) return;
+  for (int size = 2; size <= kTmWindow; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const int t = threadIdx.x, o = t ^ stride;
+      if (o > t) {
+        const uint32_t x = keys[t], y = keys[o];
+        const bool up = (t & size) == 0;
+        if ((x > y) == up) keys[t] = y, keys[o] = x;
+      }
+      __syncthreads();
+    }
+  const int g = threadIdx.x / G, r = threadIdx.x % G;
+  if (g >= n_groups) return;
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+  TmGroupSh& sh = *reinterpret_cast<TmGroupSh*>(areas + g * tm_group_words(dmax));
+  int32_t* w = reinterpret_cast<int32_t*>(&sh + 1);
+  for (int q = g; q < n_valid; q += n_groups) {
+    const uint32_t t = keys[q] & 0xFFFFu;
+    const uint64_t i = base + t;
+    const ah_hit h = hits[i];
+    const int L = plen[h.pattern];
+    const uint32_t pair = h.pattern >> 2, primer = h.pattern & 1u;
+    const uint64_t code = codes[t];
+    __syncwarp(gmask);  // the previous round's reads of the area are done
+    for (int j = r; j < L; j += G) {
+      const uint8_t sj = (uint8_t)((code >> (2 * j)) & 3u);
+      sh.s[j] = sj;
+      sh.c[j] = sj ^ 2u;
+      sh.set[j] = psets[(pair * 2 + primer) * 32 + j];
+    }
+    __syncwarp(gmask);
+    const double tm = R.variants ? group_site_tm<G>(sh, w, L, pk[pair], clamp, R, status, r, gmask)
+                                 : group_site_tm<G>(sh, w, L, L, 0, R, status, r, gmask);
+    if (r == 0) out[i] = tm;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Degenerate site Tm over every concrete variant (the default reading), one thread per site.
+//
+// With no mismatch budget the chain's states are the 4 bases, so a thread keeps them in registers
+// and takes each step's transitions itself, a fraction of the instructions that lane groups spend
+// on shuffles.  Sites come from the same pre-pass and sort by primer as in k_tm_hits_g, so the
+// threads of a warp share the chain's shape (their loops have the same bounds) and warps are full.
+// The compressed chain's step weights are stored per thread in shared memory, only for pairs of
+// allowed choices and strided by the block size (a warp's accesses fall in different banks); the
+// parameter tables are copied to shared memory; the passes score in integers: the start pass with
+// the exact int32 score 300 dS - 1000 dH, the proving passes in 64-bit fixed point (double beyond
+// 4000 K).  The chain and its exactness are site_tm_chain's; sites it does not cover (salt methods 6
+// and 7, L < 3, an entropy sum that could reach zero) go to site_tm.
+constexpr int kTmThreads = 128;
+
+struct TmTabs {               // packed dH * 65536 + dS (tenths), kNoEdge without a parameter
+  int32_t step[256], term[256];
+};
+
+__device__ __forceinline__ int32_t edge_tab(const TmTabs& T, int i, int L, int x, int y, uint64_t cc) {
+  const int c0 = (int)(cc >> (2 * i)) & 3, c1 = (int)(cc >> (2 * i + 2)) & 3;
+  if (i == 0) {
+    const int32_t p = T.term[c1 * 64 + c0 * 16 + y * 4 + x];
+    if (p != kNoEdge) return p;
+  }
+  if (i == L - 2) {
+    const int32_t p = T.term[x * 64 + y * 16 + c0 * 4 + c1];
+    if (p != kNoEdge) return p;
+  }
+  return T.step[x * 64 + y * 16 + c0 * 4 + c1];
+}
+
+__device__ __forceinline__ int32_t end_packed(int j, int L, int v) {
+  int dh, ds;
+  end_sums(j, L, (uint8_t)v, &dh, &ds);
+  return dh * 65536 + ds;
+}
+
+// the primer as four position masks, one per base code (bit j: position j allows the code)
+struct PrimerMasks {
+  uint32_t m[4];
+  __device__ __forceinline__ uint32_t ch(int j) const {
+    return ((m[0] >> j) & 1u) | (((m[1] >> j) & 1u) << 1) | (((m[2] >> j) & 1u) << 2) | (((m[3] >> j) & 1u) << 3);
+  }
+  __device__ __forceinline__ int fixed(int j) const {  // the one code of a single-choice position
+    return (int)((m[1] >> j) & 1u) + 2 * (int)((m[2] >> j) & 1u) + 3 * (int)((m[3] >> j) & 1u);
+  }
+  // positions with at least two choices
+  __device__ __forceinline__ uint32_t branching(int L) const {
+    const uint32_t b = (m[0] & m[1]) | (m[0] & m[2]) | (m[0] & m[3]) | (m[1] & m[2]) | (m[1] & m[3]) | (m[2] & m[3]);
+    return L >= 32 ? b : b & ((1u << L) - 1u);
+  }
+};
+
+__device__ __forceinline__ int rank_of(uint32_t ch, int a) { return __popc(ch & ((1u << a) - 1u)); }
+
+// One pass over the compressed chain in score arithmetic S: the best A * dS10 - B * dH10 and that
+// variant's exact packed sums.  W: this thread's weights (stride `ws` words); dmask: branch
+// positions (never empty).
+template <typename S>
+__device__ __forceinline__ bool thread_pass(const int32_t* __restrict__ W, int ws, const PrimerMasks P, uint32_t dmask,
+                                            S A, S B, S* best, int32_t* bsum) {
+  const S none = no_score<S>();
+  S cur[4];
+  int32_t cs[4];
+  int lo = __ffs(dmask) - 1;
+  uint32_t rest = dmask & (dmask - 1);
+  uint32_t cha = P.ch(lo);
+  int off = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    cur[a] = none;
+    cs[a] = 0;
+    if ((cha >> a) & 1u) {
+      const int32_t p = W[(off + rank_of(cha, a)) * ws];
+      if (p != kNoEdge) cur[a] = A * (S)unpack_ds(p) - B * (S)unpack_dh(p), cs[a] = p;
+    }
+  }
+  off += __popc(cha);
+  while (rest) {
+    const int hi = __ffs(rest) - 1;
+    rest &= rest - 1;
+    const uint32_t chb = P.ch(hi);
+    const int nb = __popc(chb);
+    S nx[4];
+    int32_t ns[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) nx[b] = none, ns[b] = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (!((cha >> a) & 1u) || cur[a] == none) continue;
+      const int row = off + rank_of(cha, a) * nb;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (!((chb >> b) & 1u)) continue;
+        const int32_t p = W[(row + rank_of(chb, b)) * ws];
+        if (p == kNoEdge) continue;
+        const S sc = cur[a] + (A * (S)unpack_ds(p) - B * (S)unpack_dh(p));
+        if (sc > nx[b]) nx[b] = sc, ns[b] = cs[a] + p;
+      }
+    }
+    off += __popc(cha) * nb;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) cur[b] = nx[b], cs[b] = ns[b];
+    cha = chb;
+  }
+  S bs = none;
+  int32_t bp = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    if (!((cha >> a) & 1u) || cur[a] == none) continue;
+    const int32_t p = W[(off + rank_of(cha, a)) * ws];
+    if (p == kNoEdge) continue;
+    const S sc = cur[a] + (A * (S)unpack_ds(p) - B * (S)unpack_dh(p));
+    if (sc > bs) bs = sc, bp = cs[a] + p;
+  }
+  if (bs == none) return false;
+  *best = bs;
+  *bsum = bp;
+  return true;
+}
+
+// The weights of one site's compressed chain into W (stride ws): one per choice at the first branch
+// position (with everything before it), one per pair of choices at consecutive ones (with the fixed
+// steps between them), one per choice at the last (with everything after it).  Returns a bound on
+// every variant's dS (tenths): the sum of each block's largest.
+__device__ __forceinline__ int thread_weights(const TmTabs& T, int32_t* __restrict__ W, int ws, const PrimerMasks P,
+                                              uint32_t dmask, uint64_t cc, int L) {
+  int bound = 0, off = 0;
+  {
+    const int d0 = __ffs(dmask) - 1;
+    const uint32_t ch0 = P.ch(d0);
+    int mx = INT_MIN;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (!((ch0 >> a) & 1u)) continue;
+      int32_t p = end_packed(0, L, d0 == 0 ? a : P.fixed(0));
+      for (int i = 0; i < d0; ++i)
+        p = add_packed(p, edge_tab(T, i, L, P.fixed(i), i + 1 == d0 ? a : P.fixed(i + 1), cc));
+      W[(off + rank_of(ch0, a)) * ws] = p;
+      if (p != kNoEdge) mx = max(mx, unpack_ds(p));
+    }
+    off += __popc(ch0);
+    bound += mx == INT_MIN ? 0 : mx;
+  }
+  int lo = __ffs(dmask) - 1;
+  for (uint32_t rest = dmask & (dmask - 1); rest; rest &= rest - 1) {
+    const int hi = __ffs(rest) - 1;
+    const uint32_t cha = P.ch(lo), chb = P.ch(hi);
+    const int nb = __popc(chb);
+    int32_t mid = 0, left[4], right[4];
+    const bool adjacent = hi == lo + 1;
+    if (!adjacent) {
+      for (int i = lo + 1; i + 1 < hi; ++i) mid += edge_tab(T, i, L, P.fixed(i), P.fixed(i + 1), cc);
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        left[x] = (cha >> x) & 1u ? edge_tab(T, lo, L, x, P.fixed(lo + 1), cc) : kNoEdge;
+        right[x] = (chb >> x) & 1u ? edge_tab(T, hi - 1, L, P.fixed(hi - 1), x, cc) : kNoEdge;
+      }
+    }
+    int mx = INT_MIN;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (!((cha >> a) & 1u)) continue;
+      const int row = off + rank_of(cha, a) * nb;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (!((chb >> b) & 1u)) continue;
+        const int32_t p = adjacent ? edge_tab(T, lo, L, a, b, cc) : add_packed(add_packed(left[a], mid), right[b]);
+        W[(row + rank_of(chb, b)) * ws] = p;
+        if (p != kNoEdge) mx = max(mx, unpack_ds(p));
+      }
+    }
+    off += __popc(cha) * nb;
+    bound += mx == INT_MIN ? 0 : mx;
+    lo = hi;
+  }
+  {
+    const uint32_t chl = P.ch(lo);
+    int mx = INT_MIN;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if (!((chl >> b) & 1u)) continue;
+      int32_t p = end_packed(L - 1, L, lo == L - 1 ? b : P.fixed(L - 1));
+      for (int i = lo; i + 1 < L; ++i)
+        p = add_packed(p, edge_tab(T, i, L, i == lo ? b : P.fixed(i), P.fixed(i + 1), cc));
+      W[(off + rank_of(chl, b)) * ws] = p;
+      if (p != kNoEdge) mx = max(mx, unpack_ds(p));
+    }
+    bound += mx == INT_MIN ? 0 : mx;
+  }
+  return bound;
+}
+
+// the branch positions of a primer of length L (a concrete primer: its first position)
+__device__ __forceinline__ uint32_t chain_nodes(const PrimerMasks P, int L) {
+  const uint32_t d = P.branching(L);
+  return d ? d : 1u;
+}
+
+// Tm of one site over every variant of its primer (k unlimited, no clamp restriction) by the chain
+// method, its fixed steps known to have parameters.  Returns false when the chain does not apply
+// (salt methods 6 and 7, L < 3, an entropy sum that could reach zero): the site is then enumerated
+// by warp_enumerate.  W: room for this primer's weights at stride ws.
+__device__ __forceinline__ bool thread_site_tm(const TmTabs& T, int32_t* __restrict__ W, int ws, const PrimerMasks P,
+                                               uint64_t code, int L, const TmRun& R, double* tm) {
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  if (R.saltcorr >= 6 || L < 3) return false;
+  const uint64_t cc = code ^ 0xAAAAAAAAAAAAAAAAull;
+  const uint32_t dmask = chain_nodes(P, L);
+  const int bound = thread_weights(T, W, ws, P, dmask, cc, L);
+  const double S0 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
+  const double H0 = kInitH + kOneGCH + R.sym_h, Sc = kInitS + kOneGCS + R.sym_s;
+  const double shift = R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0;
+  auto ratio = [&](int32_t p) { return 1000.0 * (0.1 * unpack_dh(p) + H0) / (0.1 * unpack_ds(p) + Sc + S0); };
+  int32_t bp;
+  if (0.1 * bound + Sc + S0 >= 0.0) {  // the bound leaves the sign open: the largest dS itself
+    int sc;
+    if (!thread_pass<int>(W, ws, P, dmask, 1, 0, &sc, &bp)) {
+      *tm = nan;
+      return true;
+    }
+    if (0.1 * unpack_ds(bp) + Sc + S0 >= 0.0) return false;
+  }
+  {
+    int sc;
+    if (!thread_pass<int>(W, ws, P, dmask, 300, 1000, &sc, &bp)) {
+      *tm = nan;
+      return true;
+    }
+  }
+  double lam = ratio(bp);
+  int32_t inc = bp;
+  constexpr double kScale = 68719476736.0;  // 2^36
+  for (int it = 0; it < 64; ++it) {
+    bool better;
+    int32_t cand;
+    if (fabs(lam) < 4000.0) {
+      const long long Lq = llrint(lam * kScale), Bq = (long long)(1000.0 * kScale);
+      long long sc;
+      if (!thread_pass<long long>(W, ws, P, dmask, Lq, Bq, &sc, &cand)) break;
+      better = sc > Lq * unpack_ds(inc) - Bq * unpack_dh(inc);
+    } else {
+      double sc;
+      if (!thread_pass<double>(W, ws, P, dmask, lam, 1000.0, &sc, &cand)) break;
+      const double ref = lam * unpack_ds(inc) - 1000.0 * unpack_dh(inc);
+      better = sc > ref + 1e-12 * fabs(ref);
+    }
+    if (!better) break;
+    const double q = ratio(cand);
+    if (!(q > lam)) break;
+    lam = q, inc = cand;
+  }
+  *tm = lam + shift - 273.15;
+  return true;
+}
+
+// v / n and v % n for the 1 to 4 choices of an IUPAC code
+__device__ __forceinline__ uint32_t take_digit(uint32_t* v, int n) {
+  uint32_t d;
+  if (n == 4) d = *v & 3u, *v >>= 2;
+  else if (n == 2) d = *v & 1u, *v >>= 1;
+  else if (n == 3) { const uint32_t q = (uint32_t)(((uint64_t)*v * 0xAAAAAAABull) >> 33); d = *v - 3u * q, *v = q; }
+  else d = 0;
+  return d;
+}
+
+// the d-th allowed code of a choice set
+__device__ __forceinline__ int nth_code(uint32_t ch, uint32_t d) {
+  for (uint32_t k = 0; k < d; ++k) ch &= ch - 1;
+  return __ffs(ch) - 1;
+}
+
+// Every variant of a site's primer (every concrete variant counting), enumerated by the 32 lanes of
+// a warp from the compressed chain's weights in each lane's W: the maximum Tm, each variant's as
+// enum_max computes it (exact integer sums, one FP64 evaluation).  A first sweep evaluates every
+// variant in single precision; the second evaluates in FP64 those within a margin of the largest
+// single-precision value (the margin covers its rounding: 1 K plus 2e-4 of the absolute
+// temperature) and those whose entropy sum is within 2 cal/(K mol) of zero, where single precision
+// says little.  More than 2^20 variants: NaN and ST_TM_LIMIT.
+__device__ __noinline__ double warp_enumerate(const int32_t* __restrict__ W, int ws, const PrimerMasks P, int L,
+                                              const TmRun& R, uint32_t* status, int lane) {
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  const uint32_t dmask = chain_nodes(P, L);
+  const uint32_t lmask = L >= 32 ? 0xFFFFFFFFu : ((1u << L) - 1u);
+  const int gc_fixed = __popc((P.m[1] | P.m[3]) & ~dmask & lmask);  // C and G at single-choice positions
+  uint64_t count = 1;
+  int off_suf = 0, prev_n = 0;
+  for (uint32_t x = dmask; x; x &= x - 1) {
+    const int n = __popc(P.ch(__ffs(x) - 1));
+    off_suf += prev_n ? prev_n * n : n;
+    prev_n = n;
+    count = min(count * (uint64_t)n, kEnumLimit + 1);
+  }
+  if (count > kEnumLimit) {
+    if (lane == 0) atomicOr(status, (uint32_t)ST_TM_LIMIT);
+    return nan;
+  }
+  // constant parts of dH and dS, and the Tm from the sums, in single precision
+  const float Hf = (float)(kInitH + R.sym_h);
+  const float Sf = (float)(kInitS + R.sym_s + (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk);
+  const float shiftf = R.saltcorr >= 1 && R.saltcorr <= 4 ? (float)R.corr_const : 0.f;
+  // one variant: its packed sums (kNoEdge if undefined) and G/C count
+  auto variant = [&](uint32_t v, int* gc) -> int32_t {
+    uint32_t x = dmask;
+    int hi = 31 - __clz(x);
+    uint32_t ch = P.ch(hi);
+    int n_next = __popc(ch);
+    uint32_t d_next = take_digit(&v, n_next);
+    int off = off_suf;
+    int32_t sum = W[(off + d_next) * ws];
+    int g = gc_fixed + (nth_code(ch, d_next) & 1);
+    x &= ~(1u << hi);
+    while (x) {
+      hi = 31 - __clz(x);
+      ch = P.ch(hi);
+      const int n = __popc(ch);
+      const uint32_t d = take_digit(&v, n);
+      off -= n * n_next;
+      sum = add_packed(sum, W[(off + d * n_next + d_next) * ws]);
+      g += nth_code(ch, d) & 1;
+      n_next = n, d_next = d;
+      x &= ~(1u << hi);
+    }
+    *gc = g;
+    return add_packed(sum, W[d_next * ws]);
+  };
+  auto tm_float = [&](int32_t p, int gc, bool* near_zero) {
+    const float dh = 0.1f * (float)unpack_dh(p) + Hf, ds = 0.1f * (float)unpack_ds(p) + Sf;
+    *near_zero = fabsf(ds) < 2.f;
+    float t = 1000.f * dh / ds - 273.15f + shiftf;
+    if (R.saltcorr >= 6) {
+      const float corr = (float)(R.rc0 + R.rc1 * ((double)gc / (double)L) + R.rc2 / (2.0 * (double)(L - 1)));
+      t = 1.f / (1.f / (t + 273.15f) + corr) - 273.15f;
+    }
+    return t;
+  };
+  float best_f = -INFINITY;
+  double best = -INFINITY;
+  for (uint32_t v = lane; v < (uint32_t)count; v += 32) {
+    int gc;
+    const int32_t p = variant(v, &gc);
+    if (p == kNoEdge) continue;
+    bool nz;
+    const float t = tm_float(p, gc, &nz);
+    if (nz) best = fmax(best, tm_of_tenths(unpack_dh(p), unpack_ds(p), gc, L, R));
+    else if (t > best_f) best_f = t;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best_f = fmaxf(best_f, __shfl_xor_sync(0xffffffffu, best_f, o));
+  if (best_f > -INFINITY) {
+    const float floor_f = best_f - (1.f + 2e-4f * fabsf(best_f + 273.15f));
+    for (uint32_t v = lane; v < (uint32_t)count; v += 32) {
+      int gc;
+      const int32_t p = variant(v, &gc);
+      if (p == kNoEdge) continue;
+      bool nz;
+      const float t = tm_float(p, gc, &nz);
+      if (!nz && t >= floor_f) best = fmax(best, tm_of_tenths(unpack_dh(p), unpack_ds(p), gc, L, R));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  return best > -INFINITY ? best : nan;
+}
+
+// The site Tm of every marked site, every concrete variant counting (params variants = 0).  Blocks
+// of kTmThreads threads take windows of kTmSlots site slots.  Each thread first settles its slots
+// where that needs no chain (not wanted, or a step between single-choice positions without a
+// parameter); the rest are sorted by primer and taken in that order, kTmThreads at a time, so a
+// warp's threads share the primer (the same loop bounds) and the warps are full.  Shared memory:
+// the tables, the window's keys and site codes, then the weights of each thread (see
+// thread_weight_words), strided by the block size.
+constexpr int kTmSlots = 8 * kTmThreads;
+
+__global__ void __launch_bounds__(kTmThreads, 4) k_tm_hits_t(const ah_hit* __restrict__ hits, uint64_t n,
+                                                             const uint2* __restrict__ planes,
+                                                             const uint64_t* __restrict__ rec_group,
+                                                             const uint8_t* __restrict__ plen,
+                                                             const uint8_t* __restrict__ psets,
+                                                             const uint4* __restrict__ pmask, const TmRun Rp,
+                                                             double* __restrict__ out, uint32_t* status,
+                                                             const uint64_t* __restrict__ d_n) {
+  // the run constants in shared memory: device functions take them by reference, and a reference
+  // to a kernel parameter would make the compiler copy it to local memory for every thread
+  __shared__ TmRun R_sh;
+  __shared__ int n_valid;
+  if (threadIdx.x == 0) R_sh = Rp, n_valid = 0;
+  const TmRun& R = R_sh;
+  extern __shared__ __align__(16) uint32_t tm_smem[];
+  TmTabs& T = *reinterpret_cast<TmTabs*>(tm_smem);
+  uint32_t* keys = tm_smem + 512;
+  uint64_t* codes = reinterpret_cast<uint64_t*>(tm_smem + 512 + kTmSlots);
+  int32_t* W = reinterpret_cast<int32_t*>(tm_smem + 512 + 3 * kTmSlots) + threadIdx.x;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  for (int e = threadIdx.x; e < 256; e += kTmThreads) {
+    const int sh = c_nni.step_h[e], th = c_nni.term_h[e];
+    T.step[e] = sh == kNoParam ? kNoEdge : sh * 65536 + c_nni.step_s[e];
+    T.term[e] = th == kNoParam ? kNoEdge : th * 65536 + c_nni.term_s[e];
+  }
+  __syncthreads();
+  const uint64_t base = (uint64_t)blockIdx.x * kTmSlots;
+  const uint64_t n_here = d_n ? min(n, *d_n) : n;
+  int mine = 0;
+  for (int t = threadIdx.x; t < kTmSlots; t += kTmThreads) {
+    const uint64_t i = base + t;
+    uint32_t key = 0xFFFFFFFFu;
+    if (i < n_here && (unsigned long long)__double_as_longlong(out[i]) == kSiteWanted) {
+      const ah_hit h = hits[i];
+      const int L = plen[h.pattern];
+      const uint32_t pr = (h.pattern >> 2) * 2 + (h.pattern & 1u), strand = (h.pattern >> 1) & 1u;
+      const uint64_t x0 = rec_group[h.record] * 32 + h.pos;
+      const uint2 w0 = planes[x0 >> 5], w1 = planes[(x0 >> 5) + 1];
+      const int sh0 = (int)(x0 & 31);
+      const uint64_t lo = (((uint64_t)w1.x << 32) | w0.x) >> sh0, hi = (((uint64_t)w1.y << 32) | w0.y) >> sh0;
+      uint64_t code = 0;
+      for (int j = 0; j < L; ++j) {
+        const int q = strand == 0 ? j : L - 1 - j;
+        const uint64_t b = ((lo >> q) & 1u) | (((hi >> q) & 1u) << 1);
+        code |= (strand == 0 ? b : b ^ 2u) << (2 * j);
+      }
+      const uint64_t cc = code ^ 0xAAAAAAAAAAAAAAAAull;
+      const uint4 mk = pmask[pr];
+      const PrimerMasks P{{mk.x, mk.y, mk.z, mk.w}};
+      const uint32_t fixed = ~P.branching(L) & (L >= 32 ? 0xFFFFFFFFu : ((1u << L) - 1u));
+      bool undefined = false;
+      for (uint32_t f = fixed & (fixed >> 1); f && !undefined; f &= f - 1) {  // steps j, j + 1 both fixed
+        const int j = __ffs(f) - 1;
+        if (edge_tab(T, j, L, P.fixed(j), P.fixed(j + 1), cc) == kNoEdge) undefined = true;
+      }
+      if (undefined) {
+        out[i] = nan;
+      } else {
+        key = (pr << 16) | (uint32_t)t;
+        codes[t] = code;
+        ++mine;
+      }
+    }
+    keys[t] = key;
+  }
+  if (mine) atomicAdd(&n_valid, mine);
+  __syncthreads();
+  if (n_valid == 0) return;
+  for (int size = 2; size <= kTmSlots; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < kTmSlots; t += kTmThreads) {
+        const int o = t ^ stride;
+        if (o > t) {
+          const uint32_t x = keys[t], y = keys[o];
+          const bool up = (t & size) == 0;
+          if ((x > y) == up) keys[t] = y, keys[o] = x;
+        }
+      }
+      __syncthreads();
+    }
+  constexpr uint32_t kDeferred = 0x80000000u;  // a key whose site the chain does not cover
+  int deferred = 0;
+  for (int q = threadIdx.x; q < n_valid; q += kTmThreads) {
+    const uint32_t key = keys[q];
+    const uint32_t t = key & 0xFFFFu, pr = key >> 16;
+    const uint64_t i = base + t;
+    const int L = plen[hits[i].pattern];
+    const uint4 mk = pmask[pr];
+    const PrimerMasks P{{mk.x, mk.y, mk.z, mk.w}};
+    double tm;
+    if (thread_site_tm(T, W, kTmThreads, P, codes[t], L, R, &tm)) {
+      out[i] = tm;
+    } else {
+      keys[q] = key | kDeferred;
+      ++deferred;
+    }
+  }
+  // sites the chain does not cover: one warp each, every lane computing the site's weights in its
+  // own area and enumerating a share of the variants
+  if (!__syncthreads_or(deferred)) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = warp; q < n_valid; q += kTmThreads / 32) {
+    const uint32_t key = keys[q];
+    if (!(key & kDeferred)) continue;
+    const uint32_t t = key & 0xFFFFu, pr = (key & ~kDeferred) >> 16;
+    const uint64_t i = base + t;
+    const int L = plen[hits[i].pattern];
+    const uint4 mk = pmask[pr];
+    const PrimerMasks P{{mk.x, mk.y, mk.z, mk.w}};
+    thread_weights(T, W, kTmThreads, P, chain_nodes(P, L), codes[t] ^ 0xAAAAAAAAAAAAAAAAull, L);
+    const double tm = warp_enumerate(W, kTmThreads, P, L, R, status, lane);
+    if (lane == 0) out[i] = tm;
+  }
+}
+
+// ah_tm_sites in the group form: sites given as IUPAC sets and base codes, n_groups per block of
+// kTmWindow threads
+template <int G>
+__global__ void __launch_bounds__(kTmWindow) k_tm_sites_g(const uint8_t* __restrict__ sets,
+                                                          const uint8_t* __restrict__ site,
+                                                          const uint32_t* __restrict__ len,
+                                                          const uint8_t* __restrict__ kc, uint32_t n, const TmRun Rp,
+                                                          double* __restrict__ out, uint32_t* status, int dmax,
+                                                          int n_groups) {
+  // the run constants in shared memory: device functions take them by reference, and a reference
+  // to a kernel parameter would make the compiler copy it to local memory for every thread
+  __shared__ TmRun R_sh;
+  if (threadIdx.x == 0) R_sh = Rp;
+  __syncthreads();
+  const TmRun& R = R_sh;
+
+  extern __shared__ __align__(16) uint32_t tm_smem[];
+  const int g = threadIdx.x / G, r = threadIdx.x % G;
+  if (g >= n_groups) return;
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+  const uint64_t i = (uint64_t)blockIdx.x * n_groups + g;
+  if (i >= n) return;
+  TmGroupSh& sh = *reinterpret_cast<TmGroupSh*>(tm_smem + 3 * kTmWindow + g * tm_group_words(dmax));
+  int32_t* w = reinterpret_cast<int32_t*>(&sh + 1);
+  const int L = (int)len[i];
+  for (int j = r; j < L; j += G) {
+    const uint8_t sj = site[32 * i + j];
+    sh.s[j] = sj;
+    sh.c[j] = sj ^ 2u;
+    sh.set[j] = sets[32 * i + j];
+  }
+  __syncwarp(gmask);
+  const double t = group_site_tm<G>(sh, w, L, kc[2 * i], kc[2 * i + 1], R, status, r, gmask);
+  if (r == 0) out[i] = t;
+}
+
 __global__ void k_tm_amps(ah_amplicon* __restrict__ a, uint64_t n, const double* __restrict__ hit_tm, int filter,
                           double min_tm, uint32_t* __restrict__ keep, const uint64_t* __restrict__ d_n = nullptr) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -733,7 +1676,14 @@ __global__ void k_compact_amps(const ah_amplicon* __restrict__ in, uint64_t n, c
 }
 
 __global__ void k_tm_duplexes(const uint8_t* __restrict__ v, const uint8_t* __restrict__ c,
-                              const uint32_t* __restrict__ len, uint32_t n, const TmRun R, double* __restrict__ out) {
+                              const uint32_t* __restrict__ len, uint32_t n, const TmRun Rp, double* __restrict__ out) {
+  // the run constants in shared memory: device functions take them by reference, and a reference
+  // to a kernel parameter would make the compiler copy it to local memory for every thread
+  __shared__ TmRun R_sh;
+  if (threadIdx.x == 0) R_sh = Rp;
+  __syncthreads();
+  const TmRun& R = R_sh;
+
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double t;
@@ -744,11 +1694,106 @@ __global__ void k_tm_duplexes(const uint8_t* __restrict__ v, const uint8_t* __re
 
 __global__ void k_tm_sites(const uint8_t* __restrict__ sets, const uint8_t* __restrict__ site,
                            const uint32_t* __restrict__ len, const uint8_t* __restrict__ kc, uint32_t n,
-                           const TmRun R, double* __restrict__ out, uint32_t* status) {
+                           const TmRun Rp, double* __restrict__ out, uint32_t* status) {
+  // the run constants in shared memory: device functions take them by reference, and a reference
+  // to a kernel parameter would make the compiler copy it to local memory for every thread
+  __shared__ TmRun R_sh;
+  if (threadIdx.x == 0) R_sh = Rp;
+  __syncthreads();
+  const TmRun& R = R_sh;
+
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   out[i] = site_tm(sets + 32 * (uint64_t)i, site + 32 * (uint64_t)i, (int)len[i], kc[2 * i], kc[2 * i + 1], R,
                    status);
+}
+
+// Launch shape of the group kernels: G lanes per site from the largest state width W (= k + 1 with a
+// mismatch budget, else 1) the launch can meet, and S sites per block within 48 KB of shared memory
+// for chains of at most dmax branch positions.  G = 0: widths above 8, left to the per-thread kernels.
+struct TmShape {
+  int G = 0, S = 0, dmax = 1;
+  size_t smem = 0;
+};
+
+TmShape tm_shape(int wmax, int dmax) {
+  TmShape t;
+  t.dmax = std::max(1, dmax);
+  t.G = wmax <= 1 ? 4 : wmax <= 2 ? 8 : wmax <= 4 ? 16 : wmax <= 8 ? 32 : 0;
+  if (!t.G) return t;
+  const size_t words = (size_t)tm_group_words(t.dmax);
+  t.S = kTmWindow / t.G;
+  while (t.S > 1 && 4 * (3 * kTmWindow + t.S * words) > 48 * 1024) --t.S;
+  t.smem = 4 * (3 * kTmWindow + t.S * words);
+  return t;
+}
+
+// positions of a primer with more than one IUPAC choice
+int degenerate_positions(const std::string& primer) {
+  int d = 0;
+  for (char ch : primer) d += __builtin_popcount(iupac_set(ch)) >= 2;
+  return d;
+}
+
+TmShape hits_shape(const ah_primers* p, int variants) {
+  int wmax = 1, dmax = 1;
+  for (uint32_t q = 0; q < p->n_pairs; ++q) {
+    const size_t lmin = std::min(p->fwd[q].size(), p->rev[q].size());
+    if (variants && p->k[q] < lmin) wmax = std::max(wmax, (int)p->k[q] + 1);
+    dmax = std::max({dmax, degenerate_positions(p->fwd[q]), degenerate_positions(p->rev[q])});
+  }
+  return tm_shape(wmax, dmax);
+}
+
+// weights one thread of k_tm_hits_t stores for a primer: one per choice at the first and last branch
+// positions, one per pair of choices at consecutive ones (a primer without a branch position: its
+// first position, one choice)
+int thread_weight_words(const std::string& primer) {
+  std::vector<int> n;
+  for (char ch : primer)
+    if (__builtin_popcount(iupac_set(ch)) >= 2) n.push_back(__builtin_popcount(iupac_set(ch)));
+  if (n.empty()) n.push_back(1);
+  int w = n.front() + n.back();
+  for (size_t t = 0; t + 1 < n.size(); ++t) w += n[t] * n[t + 1];
+  return w;
+}
+
+constexpr int kTmThreadFixedWords = 512 + 3 * kTmSlots;  // tables, keys, site codes
+constexpr size_t kTmSmemCap = 48 * 1024;
+
+// the Tm of every marked site (hit_tm holds kSiteWanted there): one thread per site for the default
+// reading when its weights fit, else the group kernel where the state width allows, else k_tm_hits
+void launch_tm_hits(cudaStream_t s, const TmRun& R, const ah_primers* p, const ah_hit* hits, uint64_t cap,
+                    const uint64_t* d_n, const uint2* planes, const uint64_t* rec_group, double* hit_tm,
+                    uint32_t* status) {
+  if (!R.variants) {
+    int ww = 1;
+    for (uint32_t q = 0; q < p->n_pairs; ++q)
+      ww = std::max({ww, thread_weight_words(p->fwd[q]), thread_weight_words(p->rev[q])});
+    const size_t smem = 4 * ((size_t)kTmThreadFixedWords + (size_t)ww * kTmThreads);
+    if (smem <= kTmSmemCap) {
+      k_tm_hits_t<<<(unsigned)std::max<uint64_t>(1, (cap + kTmSlots - 1) / kTmSlots), kTmThreads, smem, s>>>(
+          hits, cap, planes, rec_group, p->d_plen, p->d_psets, p->d_pmask, R, hit_tm, status, d_n);
+      return;
+    }
+  }
+  const TmShape t = hits_shape(p, R.variants);
+  if (!t.G) {
+    k_tm_hits<<<(unsigned)std::max<uint64_t>(1, (cap + kTmBlock - 1) / kTmBlock), kTmBlock, 0, s>>>(
+        hits, cap, planes, rec_group, p->d_plen, p->d_psets, p->d_pk, p->clamp, R, hit_tm, status, d_n);
+    return;
+  }
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, (cap + kTmWindow - 1) / kTmWindow);
+#define AH_TM_HITS_G(GG)                                                                                        \
+  k_tm_hits_g<GG><<<grid, kTmWindow, t.smem, s>>>(hits, cap, planes, rec_group, p->d_plen, p->d_psets, p->d_pk, \
+                                                  p->clamp, R, hit_tm, status, t.dmax, t.S, d_n)
+  switch (t.G) {
+    case 4: AH_TM_HITS_G(4); break;
+    case 8: AH_TM_HITS_G(8); break;
+    case 16: AH_TM_HITS_G(16); break;
+    default: AH_TM_HITS_G(32); break;
+  }
+#undef AH_TM_HITS_G
 }
 
 }  // namespace
@@ -790,7 +1835,27 @@ ah_status tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const ch
   AH_CUDA(ctx, cudaMemcpyAsync(dv, sv.data(), sv.size(), cudaMemcpyHostToDevice, ctx->stream));
   AH_CUDA(ctx, cudaMemcpyAsync(dl, len.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
   AH_CUDA(ctx, cudaMemcpyAsync(dk, kc.data(), kc.size(), cudaMemcpyHostToDevice, ctx->stream));
-  k_tm_sites<<<(n + 63) / 64, 64, 0, ctx->stream>>>(ds, dv, dl, dk, n, R, dout, ctx->d_status);
+  int wmax = 1, dmax = 1;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (kc[2 * (size_t)i] < len[i]) wmax = std::max(wmax, kc[2 * (size_t)i] + 1);
+    dmax = std::max(dmax, degenerate_positions(primers[i]));
+  }
+  const TmShape t = tm_shape(wmax, dmax);
+  if (!t.G) {
+    k_tm_sites<<<(n + 63) / 64, 64, 0, ctx->stream>>>(ds, dv, dl, dk, n, R, dout, ctx->d_status);
+  } else {
+    const unsigned grid = (unsigned)((n + t.S - 1) / t.S);
+#define AH_TM_SITES_G(GG)                                                                       \
+  k_tm_sites_g<GG><<<grid, kTmWindow, t.smem, ctx->stream>>>(ds, dv, dl, dk, n, R, dout, ctx->d_status, \
+                                                             t.dmax, t.S)
+    switch (t.G) {
+      case 4: AH_TM_SITES_G(4); break;
+      case 8: AH_TM_SITES_G(8); break;
+      case 16: AH_TM_SITES_G(16); break;
+      default: AH_TM_SITES_G(32); break;
+    }
+#undef AH_TM_SITES_G
+  }
   launched(ctx);
   AH_CUDA(ctx, cudaGetLastError());
   AH_CUDA(ctx, cudaMemcpyAsync(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -812,14 +1877,12 @@ ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, siz
 }
 
 void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit_cap, const uint64_t* d_nhits,
-               const uint8_t* pk, int clamp, uint32_t* status, const uint2* planes, const uint64_t* rec_group, const uint8_t* plen, const uint8_t* psets, double* hit_tm,
+               const ah_primers* p, uint32_t* status, const uint2* planes, const uint64_t* rec_group, double* hit_tm,
                ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep) {
   const TmRun R = *(const TmRun*)run;
   cudaMemsetAsync(hit_tm, 0, std::max<uint64_t>(1, hit_cap) * sizeof(double), s);
   k_mark_sites<<<(unsigned)std::max<uint64_t>(1, (amp_cap + 255) / 256), 256, 0, s>>>(amps, amp_cap, hit_tm, d_namps);
-  k_tm_hits<<<(unsigned)std::max<uint64_t>(1, (hit_cap + kTmBlock - 1) / kTmBlock), kTmBlock, 0, s>>>(hits, hit_cap, planes, rec_group,
-                                                                                  plen, psets, pk, clamp, R, hit_tm,
-                                                                                  status, d_nhits);
+  launch_tm_hits(s, R, p, hits, hit_cap, d_nhits, planes, rec_group, hit_tm, status);
   k_tm_amps<<<(unsigned)std::max<uint64_t>(1, (amp_cap + 255) / 256), 256, 0, s>>>(amps, amp_cap, hit_tm, filter,
                                                                                   min_tm, keep, d_namps);
 }
@@ -843,10 +1906,7 @@ ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const a
     k_mark_sites<<<(unsigned)((a->n + 255) / 256), 256, 0, ctx->stream>>>(a->d, a->n, hit_tm);
     launched(ctx);
   }
-  if (h->n && a->n)
-    k_tm_hits<<<(unsigned)((h->n + kTmBlock - 1) / kTmBlock), kTmBlock, 0, ctx->stream>>>(h->d, h->n, b->planes, b->rec_group, p->d_plen,
-                                                                      p->d_psets, p->d_pk, p->clamp, R, hit_tm,
-                                                                      ctx->d_status);
+  if (h->n && a->n) launch_tm_hits(ctx->stream, R, p, h->d, h->n, nullptr, b->planes, b->rec_group, hit_tm, ctx->d_status);
   if (h->n && a->n) launched(ctx);
   if (params->filter && (st = dalloc(ctx, &keep, a->n))) return st;
   if (a->n)

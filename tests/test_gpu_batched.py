@@ -178,3 +178,40 @@ def test_plan_copy_results(engine):
             ah.ah_plan_free(plan)
     finally:
         ah.ah_batch_free(batch)
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_launch_host_matches_launch(engine, persistent):
+    """The step on genomes in host memory, each range of scan tiles launched as its bases land
+    (ah_plan_launch_host), equals the plan's replay on the same genomes packed beforehand.  The
+    genomes span two staged chunks of the upload, and the plan's batch holds other bases before
+    the call, so a range scanned before its bases landed would show."""
+    import torch
+
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Params
+
+    wl = synth.batched(n_genomes=200, n_pairs=2)
+    assert wl.total_bp > (256 << 20)
+    wl.trim, wl.fb_len, wl.rb_len = True, 10, 8
+    p = Params.from_workload(wl)
+    text = torch.empty(wl.total_bp, dtype=torch.uint8, pin_memory=True)
+    text.numpy()[:] = wl.seq
+    other = torch.full((wl.total_bp,), ord("A"), dtype=torch.uint8, pin_memory=True)
+    offs = np.ascontiguousarray(wl.offsets, dtype=np.uint64)
+    batch = engine.pack(wl.seq, wl.offsets)
+    try:
+        plan = engine.plan(batch, p, with_seqs=True, persistent=persistent)
+        try:
+            ah.ah_plan_run(plan, engine.ctx)
+            ref = engine.plan_output(plan)
+            assert len(ref.amps) > 0
+            for _ in range(2):
+                ah.ah_batch_pack_range(engine.ctx, batch, 0, other.data_ptr(), offs)
+                ah.ah_plan_launch_host(plan, text.data_ptr(), offs, engine.ctx)
+                ah.ah_plan_check(plan, engine.ctx)
+                _same(engine.plan_output(plan), ref)
+        finally:
+            ah.ah_plan_free(plan)
+    finally:
+        ah.ah_batch_free(batch)

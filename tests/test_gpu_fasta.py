@@ -336,3 +336,45 @@ def test_fastq_pack_host_text_in_several_chunks(ah_ctx):
         ah.ah_batch_free(batch)
         ah.ah_batch_free(ref)
         ah.ah_quals_free(q)
+
+
+def test_fasta_and_fastq_files(ah_ctx, tmp_path):
+    """The file front end gives the batch, names and qualities of the same text passed in memory;
+    a missing file is refused with its name in the message."""
+    ah, ctx = ah_ctx
+    text = _random_fasta(11, 30, False, True)
+    path = tmp_path / "genomes.fa"
+    path.write_bytes(text)
+    b_mem, n_mem = ah.ah_fasta_pack(ctx, text)
+    b_file, n_file = ah.ah_fasta_pack_file(ctx, str(path))
+    try:
+        assert n_mem == n_file and len(n_file) > 0
+        assert _batch_bytes(ah, b_mem) == _batch_bytes(ah, b_file)
+    finally:
+        ah.ah_batch_free(b_mem)
+        ah.ah_batch_free(b_file)
+    st = synth.Stream(synth.make_key(12, 4321, 0))
+    recs = []
+    for r in range(50):
+        seq = "".join(st.choice("ACGTN") for _ in range(st.randint(0, 400)))
+        qual = "".join(chr(33 + st.randint(0, 40)) for _ in seq)
+        recs.append(f"@read{r} x\n{seq}\n+\n{qual}\n")
+    fq = "".join(recs).encode()
+    fq_path = tmp_path / "reads.fq"
+    fq_path.write_bytes(fq)
+    b1, q1, names1 = ah.ah_fastq_pack(ctx, fq)
+    b2, q2, names2 = ah.ah_fastq_pack_file(ctx, str(fq_path))
+    try:
+        assert names1 == names2
+        assert _batch_bytes(ah, b1) == _batch_bytes(ah, b2)
+        qa, oa = ah.ah_quals_copy(q1)
+        qb, ob = ah.ah_quals_copy(q2)
+        assert qa == qb and np.array_equal(oa, ob)
+    finally:
+        for b in (b1, b2):
+            ah.ah_batch_free(b)
+        for q in (q1, q2):
+            ah.ah_quals_free(q)
+    with pytest.raises(ah.AhError) as e:
+        ah.ah_fasta_pack_file(ctx, str(tmp_path / "missing.fa"))
+    assert e.value.status == ah.AH_EINVAL and "missing.fa" in str(e.value)
