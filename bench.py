@@ -55,16 +55,30 @@ def alg_ops_per_base(fwd, rev, clamp):
     return total / 32.0
 
 
-# DRAM bytes per base of scan kernels captured with ncu (dram__bytes_read.sum + dram__bytes_write.sum
-# of the scan node of a plan replay on the full plain_scale workload, one 1-pass capture), keyed by
-# what identifies the kernel: LOP3/SHF per 32 positions of its circuit, threads, groups per thread,
-# shift mode, persistent.  A kernel not in this table reports traffic null.
+# DRAM bytes per base of scan kernels captured with ncu on a smaller case of the same kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum of a warm replay's scan, plain_scale's first 200
+# genomes, 756,529,120 bases, 189 MB of planes, larger than L2), scaled to a launch by its bases
+# (the traffic is one pass over the planes), keyed by what identifies the kernel: LOP3/SHF per 32
+# positions of its circuit, threads, groups per thread, shift mode, persistent.  A kernel not in
+# this table reports traffic null.
 SCAN_TRAFFIC = {
-    (188, 256, 8, 0, 0): 1_910_472_704 / 7_536_412_189,
+    (188, 256, 8, 0, 0): (189_573_376 + 1_627_392) / 756_529_120,
 }
 
 
-def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms, shape=None):
+# ALU-pipe work the scan kernel actually executes, from ncu on a smaller case of the same circuit
+# (smsp__inst_executed_pipe_alu.sum x 32 lanes / bases scanned, and sm__pipe_alu_cycles_active as a
+# fraction of peak), keyed by the circuit's LOP3/SHF per 32 positions.  profiles/ holds the captures.
+SCAN_PIPE = {
+    # the bench pair (19/20 nt, k=3, clamp 3): plain_scale's first 200 genomes (756.5 Mbp), autotuned
+    # 256 threads x 8 groups, shift mode 0; 113,306,255 ALU-pipe warp instructions per launch
+    188: {"alu_lane_ops_per_base": 113_306_255 * 32 / 756_529_120, "alu_pipe_busy": 0.967,
+          "source": "ncu smsp__inst_executed_pipe_alu.sum x 32 / bases of one launch, plain_scale 200 genomes "
+                    "(profiles/ah_scan_jit_alu_pipe.md)"},
+}
+
+
+def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms, shape=None, sm_mhz=None):
     """ALU roofline of one scan launch.  `achieved` is algorithmic: the per-base lane-op count of the
     bit-sliced method (3 per non-clamp and 2 per clamp position of every oriented pattern, 32
     positions per lane-op) times the bases of the launch, over its CUDA-event time.  The generated
@@ -86,7 +100,8 @@ def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms, shape=None):
     return {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tlane-op/s",
             "frac": achieved / ALU_PEAK_TOPS, "traffic": traffic,
             "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel (same circuit and "
-                               "shape), scaled to the bases of one launch") if traffic is not None else None,
+                               "shape) on plain_scale's first 200 genomes, scaled to the bases of this launch")
+                              if traffic is not None else None,
             "kernel": "ah_scan_jit (bit-sliced scan)", "kernel_ms": ms,
             "ops_per_base": norm, "ops_source": "algorithmic: sum over oriented patterns of (3 (L - c) + 2 c) / 32",
             "peak_source": "derived: 152 SMs x 64 ALU lanes/clk x 2.07 GHz",
@@ -95,7 +110,24 @@ def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms, shape=None):
                                   "(warps skip phase two when all their windows failed phase one)"},
             "hbm": {"achieved_gbs": hbm, "peak_gbs": hbm_peak,
                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "frac": hbm / hbm_peak,
-                    "algorithmic_bytes_per_base": 0.25}}
+                    "algorithmic_bytes_per_base": 0.25},
+            "executed": _executed(ops_per_group, bases, ms, sm_mhz)}
+
+
+def _executed(ops_per_group, bases, ms, sm_mhz):
+    """The scan's executed ALU-pipe lane-ops per second against the pipe's peak at the clock the run
+    saw (152 SMs x 64 lanes x sampled SM clock): a fraction of at most 1 that says how busy the pipe
+    the kernel is bound by is kept."""
+    rec = SCAN_PIPE.get(ops_per_group)
+    if rec is None:
+        return None
+    mhz = sm_mhz or SM_MAX_GHZ * 1e3
+    peak = SM_COUNT * ALU_LANES_PER_SM_CLK * mhz / 1e6   # T lane-ops/s
+    achieved = rec["alu_lane_ops_per_base"] * bases / (ms * 1e-3) / 1e12
+    return {"ops_per_base": rec["alu_lane_ops_per_base"], "achieved": achieved, "peak": peak, "unit": "Tlane-op/s",
+            "frac": achieved / peak, "alu_pipe_busy_ncu": rec["alu_pipe_busy"],
+            "peak_source": f"derived: 152 SMs x 64 ALU lanes/clk x {mhz:.0f} MHz (median SM clock sampled in the run)",
+            "ops_source": rec["source"]}
 
 
 class ClockSampler:
@@ -399,7 +431,8 @@ def run_engine(args):
     scan_ms = stats["scan_ms"] / max(1, stats["scan_launches"])
     bases_per_launch = stats["scan_bases"] / max(1, stats["scan_launches"])
     roofline = scan_roofline(stats["scan_ops_per_group"], wl.fwd, wl.rev, wl.clamp, bases_per_launch, scan_ms,
-                             (info["threads"], info["groups_per_thread"], info["shift_mode"], info["persistent"]))
+                             (info["threads"], info["groups_per_thread"], info["shift_mode"], info["persistent"]),
+                             clk.summary().get("sm_mhz"))
     roofline["step_gbps_frac_of_alu_bound"] = value / world / (ALU_PEAK_TOPS * 1e3 / roofline["circuit"]["ops_per_base"])
 
     # end to end through the C ABI from pinned host memory: every step packs the records from host
@@ -428,8 +461,7 @@ def run_engine(args):
         for it in range(1 + args.e2e_steps):
             torch.cuda.synchronize()
             t = time.perf_counter()
-            ah.ah_batch_pack_range(eng.ctx, batch, 0, pinned.data_ptr(), offs)
-            ah.ah_plan_launch(plan, eng.ctx)
+            ah.ah_plan_launch_host(plan, pinned.data_ptr(), offs, eng.ctx)
             ah.ah_plan_copy_results(plan, eng.ctx, *bufs)
             dt = time.perf_counter() - t
             if it > 0:
@@ -440,8 +472,23 @@ def run_engine(args):
                 i2["arena_bytes"] + 8 * (5 * i2["n_kept"] + 1) if with_seqs else 0)
         e2e = {"value": wl.total_bp / statistics.median(times) / 1e9, "unit": "Gbp/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": len(times), "ms_per_step": statistics.median(times) * 1e3,
-               "path": "pinned host ASCII -> ah_batch_pack_range (chunked copies, packed as they land) -> "
-                       "ah_plan_launch -> ah_plan_copy_results (sites, amplicons, sequences) into pinned host buffers"}
+               "path": "pinned host ASCII -> ah_plan_launch_host (chunked copies, packed as they land, each range of "
+                       "scan tiles scanned once its bases are in, the rest of the step after the last chunk) -> "
+                       "ah_plan_copy_results (sites, amplicons, sequences) into pinned host buffers"}
+        # the same with the scan after the whole upload (pack, then the plan's replay)
+        times = []
+        for it in range(1 + args.e2e_steps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ah.ah_batch_pack_range(eng.ctx, batch, 0, pinned.data_ptr(), offs)
+            ah.ah_plan_launch(plan, eng.ctx)
+            ah.ah_plan_copy_results(plan, eng.ctx, *bufs)
+            dt = time.perf_counter() - t
+            if it > 0:
+                times.append(dt)
+        e2e["scan_after_upload"] = {"value": wl.total_bp / statistics.median(times) / 1e9, "unit": "Gbp/s",
+                                    "ms_per_step": statistics.median(times) * 1e3,
+                                    "path": "ah_batch_pack_range -> ah_plan_launch -> ah_plan_copy_results"}
         del pinned
         # the same from stored 2-bit batches (the paper streams its 2-bit batch files): exported
         # planes and sparse invalid words in pinned memory, imported every step
@@ -480,7 +527,15 @@ def run_engine(args):
     eng.close()
     if on_device:
         wl.d_seq = None
-        torch.cuda.empty_cache()
+    torch.cuda.empty_cache()
+    # the other measured rows of the path at one GPU (batched plan against the plain per-record
+    # form, the dense-hit stress, serving latency), each with its own clock record
+    extras = {}
+    if world == 1 and not args.no_extras and args.workload == "plain_scale":
+        extras["batched"] = batched_record(args, min(args.steps, 5), 3)
+        extras["dense"] = dense_record(args, min(args.steps, 10), 3)
+        stable, loaded = serving_record(args, [(args.serve_requests, args.serve_rate), (args.serve_burst, 200.0)])
+        extras["serving"] = {"stable_rate": stable, "offered_200_per_s": loaded}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gbp/s", "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -491,13 +546,83 @@ def run_engine(args):
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": stats["kernel_launches"],
                 "gpu_launches_per_step": stats["kernel_launches"] / args.steps, "roofline": roofline,
                 "cpu_baseline": base}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------------------------------ dense arm
+def dense_record(args, steps, warmup):
+    """The dense-hit workload (tandem repeats, highly degenerate primers, about one site per kb) as one
+    graph-captured plan: scan, compaction, pairing and the FP64 Tm of every paired site."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth.gpu as sg
+
+    __graft_entry__.build()
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Engine, Params
+
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    wl = sg.dense(n_genomes=5000)
+    eng = Engine(0)
+    batch = eng.pack_device(wl.d_seq.data_ptr(), wl.offsets.astype(np.uint64), wl.genome_ids)
+    ah.ah_ctx_synchronize(eng.ctx)
+    gen_s = time.perf_counter() - t0
+    wl.d_seq = None
+    torch.cuda.empty_cache()
+    params = Params.from_workload(wl)
+    stream = torch.cuda.ExternalStream(ah.ah_ctx_stream(eng.ctx))
+    plan = eng.plan(batch, params, with_seqs=getattr(wl, "extract", True), autotune=True, persistent=-1)
+    for _ in range(max(3, warmup)):
+        ah.ah_plan_launch(plan, eng.ctx)
+    ah.ah_ctx_synchronize(eng.ctx)
+    ah.ah_plan_check(plan, eng.ctx)
+    ah.ah_ctx_stats_reset(eng.ctx)
+    ah.ah_ctx_set_timing(eng.ctx, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(steps):
+            ah.ah_plan_launch(plan, eng.ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ah.ah_ctx_set_timing(eng.ctx, False)
+    ah.ah_plan_check(plan, eng.ctx)
+    ms = e0.elapsed_time(e1) / steps
+    st = ah.ah_ctx_stats_get(eng.ctx)
+    info = ah.ah_plan_info_get(plan)
+    scan_ms = st["scan_ms"] / max(1, st["scan_launches"])
+    line = {"workload": "dense", "value": wl.total_bp / (ms * 1e-3) / 1e9, "unit": "Gbp/s", "steps": steps,
+            "warmup": max(3, warmup), "ms_per_step": ms,
+            "config": {"workload": f"dense: {wl.n_records} genomes, {wl.total_bp / 1e9:.2f} Gbp, 30 % with tandem "
+                                   f"repeats; {len(wl.fwd)} pair of {len(wl.fwd[0])}/{len(wl.rev[0])} nt with "
+                                   f"degenerate codes, k={wl.k}, window {wl.min_len}-{wl.max_len}, all orientations, "
+                                   "Tm of every paired site (no sequences)",
+                       "bases": wl.total_bp, "l2": "inputs larger than L2"},
+            "sites": info["n_hits"], "amplicons": info["n_amps"],
+            "sites_per_kb": info["n_hits"] / (wl.total_bp / 1e3),
+            "scan_kernel_ms": scan_ms, "rest_of_step_ms": ms - scan_ms,
+            "gpu_launches_per_step": st["kernel_launches"] / steps, "generate_and_pack_s": gen_s,
+            "clocks": clk.summary()}
+    ah.ah_plan_free(plan)
+    ah.ah_batch_free(batch)
+    eng.close()
+    torch.cuda.empty_cache()
+    return line
+
+
 # ------------------------------------------------------------------------------------------ batched arm
 def run_batched(args):
+    print(json.dumps(batched_record(args, args.steps, args.warmup)), flush=True)
+
+
+def batched_record(args, steps, warmup):
     """The batched workload (many genomes x 8 pairs) as one graph-captured plan, against the plain
     form (one scan launch per genome per pair) and the one-launch scan on the same GPU."""
     import numpy as np
@@ -525,7 +650,7 @@ def run_batched(args):
     plan = eng.plan(batch, p, with_seqs=True, autotune=True, persistent=-1)
     plan_s = time.perf_counter() - t0
     info = ah.ah_plan_info_get(plan)
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         ah.ah_plan_run(plan, eng.ctx)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ah.ah_ctx_stats_reset(eng.ctx)
@@ -533,19 +658,20 @@ def run_batched(args):
     torch.cuda.synchronize()
     with ClockSampler(0) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             ah.ah_plan_launch(plan, eng.ctx)
         e1.record(stream)
         torch.cuda.synchronize()
     ah.ah_ctx_set_timing(eng.ctx, False)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     ah.ah_plan_check(plan, eng.ctx)
     info = ah.ah_plan_info_get(plan)
     st = ah.ah_ctx_stats_get(eng.ctx)
-    launches_per_step = st["kernel_launches"] / args.steps
+    launches_per_step = st["kernel_launches"] / steps
     scan_ms = st["scan_ms"] / st["scan_launches"]
     roof = scan_roofline(st["scan_ops_per_group"], wl.fwd, wl.rev, wl.clamp, wl.total_bp, scan_ms,
-                         (info["threads"], info["groups_per_thread"], info["shift_mode"], info["persistent"]))
+                         (info["threads"], info["groups_per_thread"], info["shift_mode"], info["persistent"]),
+                         clk.summary().get("sm_mhz"))
     pr = eng.primers(p)
     # the plain form: one launch per genome per pair
     ah.ah_ctx_stats_reset(eng.ctx)
@@ -558,7 +684,7 @@ def run_batched(args):
     st2 = ah.ah_ctx_stats_get(eng.ctx)
     ah.ah_ctx_set_timing(eng.ctx, False)
     line = {"metric": METRIC, "workload": "batched", "value": wl.total_bp / (ms * 1e-3) / 1e9, "unit": "Gbp/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "n_gpus": 1, "steps": steps, "warmup": max(3, warmup), "ms_per_step": ms,
             "higher_is_better": True, "dtype": "u32+f64", "data": "synthetic",
             "config": {"workload": f"batched: {wl.n_records} genomes log-uniform 10 kbp-12 Mbp, "
                                    f"{wl.total_bp / 1e9:.2f} Gbp, {len(wl.fwd)} pairs of 17-26 nt, k=i mod 4, "
@@ -577,12 +703,18 @@ def run_batched(args):
     ah.ah_plan_free(plan)
     ah.ah_batch_free(batch)
     eng.close()
-    print(json.dumps(line), flush=True)
+    torch.cuda.empty_cache()
+    return line
 
 
 # ------------------------------------------------------------------------------------------ serving arm
 def run_serving(args):
-    """A Poisson request stream against a device-resident database, continuous batching."""
+    print(json.dumps(serving_record(args, [(args.requests, args.rate)])[0]), flush=True)
+
+
+def serving_record(args, runs):
+    """Poisson request streams against one device-resident database, continuous batching: one line
+    per (requests, rate) in runs, each a fixed seeded trace."""
     import numpy as np
     import torch
 
@@ -606,7 +738,21 @@ def run_serving(args):
         torch.cuda.empty_cache()
     gen_s = time.perf_counter() - t0
     db_bp = int(sum(lengths))
-    trace = synth.serving_trace(synth.SEED, args.requests, args.rate, n_db)
+    lines = []
+    for n_req, rate in runs:
+        lines.append(_serve_trace(args, ah, db, n_db, db_bp, gen_s, n_req, rate))
+    ah.ah_batch_free(db)
+    eng.close()
+    torch.cuda.empty_cache()
+    return lines
+
+
+def _serve_trace(args, ah, db, n_db, db_bp, gen_s, n_requests, rate):
+    import numpy as np
+
+    import synth
+
+    trace = synth.serving_trace(synth.SEED, n_requests, rate, n_db)
     srv = ah.ah_server_create(db, n_slots=args.slots)
     ah.ah_server_set_scan_mode(srv, args.scan_mode)
     keys = ("fwd", "rev", "k", "clamp", "first_record", "n_records", "min_len", "max_len", "orient_mask")
@@ -628,15 +774,15 @@ def run_serving(args):
     line = {"metric": METRIC, "workload": "serving", "value": bases / span / 1e9, "unit": "Gbp/s",
             "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "config": {"workload": f"serving: {n_db} genomes ({db_bp / 1e9:.1f} Gbp, "
-                                   f"{db_bp / 4e9:.1f} GB packed) resident; Poisson {args.rate} req/s, "
-                                   f"{args.requests} requests of 1-32 pairs (17-26 nt, k 0-3) over contiguous "
+                                   f"{db_bp / 4e9:.1f} GB packed) resident; Poisson {rate} req/s, "
+                                   f"{n_requests} requests of 1-32 pairs (17-26 nt, k 0-3) over contiguous "
                                    "subsets of 1-100 % of the database", "slots": args.slots,
                        "scan_mode": {0: "generated kernels (compiled per primer set)", 1: "generic kernel (no compile)",
                                      2: "generic kernel while the generated kernels compile"}[args.scan_mode]},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "mean": float(lat.mean()), "max": float(lat.max())},
             "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
-            "completed": len(res), "makespan_s": span, "offered_rate": args.rate,
+            "completed": len(res), "makespan_s": span, "offered_rate": rate,
             "served_rate": len(res) / span, "pattern_gbp_per_s": pattern_bases / span / 1e9,
             "db_build_s": gen_s, "clocks": clk.summary()}
     if args.dump_requests:
@@ -645,9 +791,7 @@ def run_serving(args):
                         "bases": x["bases"],
                         "pairs": len(r["fwd"]), "hits": len(x["hits"]), "amps": len(x["amps"])}
                        for x, r in zip(res, trace)], f)
-    ah.ah_batch_free(db)
-    eng.close()
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------------------------------------------ FASTQ reads arm
@@ -746,6 +890,11 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--dump-requests", default="", help="serving: write per-request times to this JSON file")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the batched, dense and serving sub-records")
+    ap.add_argument("--serve-requests", type=int, default=40, help="sub-record: requests of the stable-rate trace")
+    ap.add_argument("--serve-rate", type=float, default=3.0, help="sub-record: arrival rate of the stable trace")
+    ap.add_argument("--serve-burst", type=int, default=100, help="sub-record: requests offered at 200 req/s")
     ap.add_argument("--scan-mode", type=int, default=2,
                     help="serving: 0 generated scan kernels, 1 generic kernel, 2 generic while compiling")
     args = ap.parse_args()
@@ -757,6 +906,8 @@ def main():
         run_serving(args)
     elif args.workload == "amplicon_reads":
         run_reads(args)
+    elif args.workload == "dense_step":
+        print(json.dumps(dense_record(args, args.steps, args.warmup)), flush=True)
     else:
         run_engine(args)
 
