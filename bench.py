@@ -75,6 +75,11 @@ SCAN_PIPE = {
     188: {"alu_lane_ops_per_base": 113_306_255 * 32 / 756_529_120, "alu_pipe_busy": 0.967,
           "source": "ncu smsp__inst_executed_pipe_alu.sum x 32 / bases of one launch, plain_scale 200 genomes "
                     "(profiles/ah_scan_jit_alu_pipe.md)"},
+    # the batched set (8 pairs = 32 patterns, k = i mod 4): its first 2,000 genomes (3.49 Gbp),
+    # 128 threads x 8 groups, shift mode 0; 2,175,188,671 ALU-pipe warp instructions per launch
+    1050: {"alu_lane_ops_per_base": 2_175_188_671 * 32 / 3_487_157_421, "alu_pipe_busy": 0.790,
+           "source": "ncu smsp__inst_executed_pipe_alu.sum x 32 / bases of one launch, batched 2,000 genomes "
+                     "(profiles/ah_scan_jit_alu_pipe.md)"},
 }
 
 

@@ -292,7 +292,8 @@ constexpr size_t kTmRunBytes = 128;  // room for the Tm run constants a plan kee
 ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, size_t run_size);
 void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit_cap, const uint64_t* d_nhits,
                const ah_primers* p, uint32_t* status, const uint2* planes, const uint64_t* rec_group, double* hit_tm,
-               ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep);
+               ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep,
+               uint32_t* defer, int sm_count);
 void launch_compact_amps(cudaStream_t s, const ah_amplicon* in, uint64_t cap, const uint32_t* keep, const uint64_t* off,
                          ah_amplicon* out);
 void launch_extract(cudaStream_t s, bool write, const ah_amplicon* amps, uint64_t cap, const uint64_t* d_n,

@@ -38,6 +38,7 @@ struct ah_plan {
   uint64_t* poff = nullptr;     // hit_cap + 1; [hit_cap] = amplicons found
   ah_amplicon* amps = nullptr;
   double* hit_tm = nullptr;
+  uint32_t* tm_defer = nullptr;  // hit_cap + 1: sites the Tm chain does not cover
   uint32_t* keep = nullptr;
   uint64_t* koff = nullptr;     // amp_cap + 1; [amp_cap] = amplicons kept
   ah_amplicon* kept = nullptr;
@@ -76,12 +77,12 @@ void free_buffers(ah_plan* pl) {
   ah_ctx* c = pl->ctx;
   for (void* q : {(void*)pl->slots, (void*)pl->tile_count, (void*)pl->tpc, (void*)pl->big, (void*)pl->tpc_off, (void*)pl->scratch,
                   (void*)pl->hits, (void*)pl->pair_off, (void*)pl->pcount, (void*)pl->poff, (void*)pl->amps,
-                  (void*)pl->hit_tm, (void*)pl->keep, (void*)pl->koff, (void*)pl->kept, (void*)pl->elen,
+                  (void*)pl->hit_tm, (void*)pl->tm_defer, (void*)pl->keep, (void*)pl->koff, (void*)pl->kept, (void*)pl->elen,
                   (void*)pl->ebase, (void*)pl->arena, (void*)pl->field_off, (void*)pl->ctr})
     dfree(c, q);
   pl->slots = nullptr, pl->tile_count = nullptr, pl->tpc = nullptr, pl->big = nullptr, pl->tpc_off = nullptr, pl->scratch = nullptr;
   pl->hits = nullptr, pl->pair_off = nullptr, pl->pcount = nullptr, pl->poff = nullptr, pl->amps = nullptr;
-  pl->hit_tm = nullptr, pl->keep = nullptr, pl->koff = nullptr, pl->kept = nullptr, pl->elen = nullptr;
+  pl->hit_tm = nullptr, pl->tm_defer = nullptr, pl->keep = nullptr, pl->koff = nullptr, pl->kept = nullptr, pl->elen = nullptr;
   pl->ebase = nullptr, pl->arena = nullptr, pl->field_off = nullptr, pl->ctr = nullptr;
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->post_exec) cudaGraphExecDestroy(pl->post_exec);
@@ -102,7 +103,8 @@ ah_status alloc_buffers(ah_plan* pl) {
       (st = dalloc(c, &pl->scratch, scan_scratch_elems(scan_n))) || (st = dalloc(c, &pl->hits, pl->hit_cap)) ||
       (st = dalloc(c, &pl->pair_off, pl->p->n_pairs + 1)) || (st = dalloc(c, &pl->pcount, pl->hit_cap)) ||
       (st = dalloc(c, &pl->poff, pl->hit_cap + 1)) || (st = dalloc(c, &pl->amps, pl->amp_cap)) ||
-      (st = dalloc(c, &pl->hit_tm, pl->hit_cap)) || (st = dalloc(c, &pl->keep, pl->amp_cap)) ||
+      (st = dalloc(c, &pl->hit_tm, pl->hit_cap)) || (st = dalloc(c, &pl->tm_defer, pl->hit_cap + 1)) ||
+      (st = dalloc(c, &pl->keep, pl->amp_cap)) ||
       (st = dalloc(c, &pl->koff, pl->amp_cap + 1)) || (st = dalloc(c, &pl->kept, pl->amp_cap)) ||
       (st = dalloc(c, &pl->elen, pl->amp_cap)) || (st = dalloc(c, &pl->ebase, pl->amp_cap + 1)) ||
       (st = dalloc(c, &pl->arena, pl->arena_cap)) || (st = dalloc(c, &pl->field_off, 5 * pl->amp_cap + 1)) ||
@@ -149,7 +151,7 @@ void enqueue_post(ah_plan* pl, cudaStream_t s) {
                    q.orient_mask & 15u, nullptr, pl->poff, pl->amps, pl->amp_cap, pl->ctr + 1);
   const uint64_t* n_amps = pl->poff + pl->hit_cap;
   launch_tm(s, pl->tm_run, pl->hits, pl->hit_cap, n_hits, p, pl->ctx->d_status, b->planes, b->rec_group, pl->hit_tm,
-            pl->amps, pl->amp_cap, n_amps, q.tm.filter, q.tm.min_tm, pl->keep);
+            pl->amps, pl->amp_cap, n_amps, q.tm.filter, q.tm.min_tm, pl->keep, pl->tm_defer, pl->ctx->sm_count);
   const ah_amplicon* out = pl->amps;
   const uint64_t* n_out = n_amps;
   if (q.tm.filter) {

@@ -1492,6 +1492,24 @@ __device__ __noinline__ double warp_enumerate(const int32_t* __restrict__ W, int
 // thread_weight_words), strided by the block size.
 constexpr int kTmSlots = 8 * kTmThreads;
 
+// the site's bases over [pos, pos + L) (L <= 32 spans at most two plane words), in the primer's
+// orientation, 2 bits per position
+__device__ __forceinline__ uint64_t site_code(const uint2* __restrict__ planes, const uint64_t* __restrict__ rec_group,
+                                              const ah_hit& h, int L) {
+  const uint32_t strand = (h.pattern >> 1) & 1u;
+  const uint64_t x0 = rec_group[h.record] * 32 + h.pos;
+  const uint2 w0 = planes[x0 >> 5], w1 = planes[(x0 >> 5) + 1];
+  const int sh0 = (int)(x0 & 31);
+  const uint64_t lo = (((uint64_t)w1.x << 32) | w0.x) >> sh0, hi = (((uint64_t)w1.y << 32) | w0.y) >> sh0;
+  uint64_t code = 0;
+  for (int j = 0; j < L; ++j) {
+    const int q = strand == 0 ? j : L - 1 - j;
+    const uint64_t b = ((lo >> q) & 1u) | (((hi >> q) & 1u) << 1);
+    code |= (strand == 0 ? b : b ^ 2u) << (2 * j);
+  }
+  return code;
+}
+
 __global__ void __launch_bounds__(kTmThreads, 4) k_tm_hits_t(const ah_hit* __restrict__ hits, uint64_t n,
                                                              const uint2* __restrict__ planes,
                                                              const uint64_t* __restrict__ rec_group,
@@ -1499,6 +1517,7 @@ __global__ void __launch_bounds__(kTmThreads, 4) k_tm_hits_t(const ah_hit* __res
                                                              const uint8_t* __restrict__ psets,
                                                              const uint4* __restrict__ pmask, const TmRun Rp,
                                                              double* __restrict__ out, uint32_t* status,
+                                                             uint32_t* __restrict__ defer,
                                                              const uint64_t* __restrict__ d_n) {
   // the run constants in shared memory: device functions take them by reference, and a reference
   // to a kernel parameter would make the compiler copy it to local memory for every thread
@@ -1527,17 +1546,8 @@ __global__ void __launch_bounds__(kTmThreads, 4) k_tm_hits_t(const ah_hit* __res
     if (i < n_here && (unsigned long long)__double_as_longlong(out[i]) == kSiteWanted) {
       const ah_hit h = hits[i];
       const int L = plen[h.pattern];
-      const uint32_t pr = (h.pattern >> 2) * 2 + (h.pattern & 1u), strand = (h.pattern >> 1) & 1u;
-      const uint64_t x0 = rec_group[h.record] * 32 + h.pos;
-      const uint2 w0 = planes[x0 >> 5], w1 = planes[(x0 >> 5) + 1];
-      const int sh0 = (int)(x0 & 31);
-      const uint64_t lo = (((uint64_t)w1.x << 32) | w0.x) >> sh0, hi = (((uint64_t)w1.y << 32) | w0.y) >> sh0;
-      uint64_t code = 0;
-      for (int j = 0; j < L; ++j) {
-        const int q = strand == 0 ? j : L - 1 - j;
-        const uint64_t b = ((lo >> q) & 1u) | (((hi >> q) & 1u) << 1);
-        code |= (strand == 0 ? b : b ^ 2u) << (2 * j);
-      }
+      const uint32_t pr = (h.pattern >> 2) * 2 + (h.pattern & 1u);
+      const uint64_t code = site_code(planes, rec_group, h, L);
       const uint64_t cc = code ^ 0xAAAAAAAAAAAAAAAAull;
       const uint4 mk = pmask[pr];
       const PrimerMasks P{{mk.x, mk.y, mk.z, mk.w}};
@@ -1572,8 +1582,6 @@ __global__ void __launch_bounds__(kTmThreads, 4) k_tm_hits_t(const ah_hit* __res
       }
       __syncthreads();
     }
-  constexpr uint32_t kDeferred = 0x80000000u;  // a key whose site the chain does not cover
-  int deferred = 0;
   for (int q = threadIdx.x; q < n_valid; q += kTmThreads) {
     const uint32_t key = keys[q];
     const uint32_t t = key & 0xFFFFu, pr = key >> 16;
@@ -1582,26 +1590,48 @@ __global__ void __launch_bounds__(kTmThreads, 4) k_tm_hits_t(const ah_hit* __res
     const uint4 mk = pmask[pr];
     const PrimerMasks P{{mk.x, mk.y, mk.z, mk.w}};
     double tm;
-    if (thread_site_tm(T, W, kTmThreads, P, codes[t], L, R, &tm)) {
+    if (thread_site_tm(T, W, kTmThreads, P, codes[t], L, R, &tm))
       out[i] = tm;
-    } else {
-      keys[q] = key | kDeferred;
-      ++deferred;
-    }
+    else  // the chain does not cover it: listed for k_tm_deferred
+      defer[1 + atomicAdd(defer, 1u)] = (uint32_t)i;
   }
-  // sites the chain does not cover: one warp each, every lane computing the site's weights in its
-  // own area and enumerating a share of the variants
-  if (!__syncthreads_or(deferred)) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int q = warp; q < n_valid; q += kTmThreads / 32) {
-    const uint32_t key = keys[q];
-    if (!(key & kDeferred)) continue;
-    const uint32_t t = key & 0xFFFFu, pr = (key & ~kDeferred) >> 16;
-    const uint64_t i = base + t;
-    const int L = plen[hits[i].pattern];
+}
+
+// The sites k_tm_hits_t listed (defer[0] of them at defer[1..]): one warp per site, every lane
+// computing the site's weights in its own area and enumerating a share of its variants.  A grid of
+// a few blocks per SM strides over the list, so sites that cluster (repeats) spread over the GPU.
+__global__ void __launch_bounds__(kTmThreads) k_tm_deferred(const ah_hit* __restrict__ hits,
+                                                           const uint2* __restrict__ planes,
+                                                           const uint64_t* __restrict__ rec_group,
+                                                           const uint8_t* __restrict__ plen,
+                                                           const uint4* __restrict__ pmask, const TmRun Rp,
+                                                           double* __restrict__ out, uint32_t* status,
+                                                           const uint32_t* __restrict__ defer) {
+  __shared__ TmRun R_sh;
+  if (threadIdx.x == 0) R_sh = Rp;
+  const TmRun& R = R_sh;
+  extern __shared__ __align__(16) uint32_t tm_smem[];
+  TmTabs& T = *reinterpret_cast<TmTabs*>(tm_smem);
+  int32_t* W = reinterpret_cast<int32_t*>(tm_smem + 512) + threadIdx.x;
+  const uint32_t n_def = defer[0];
+  if (blockIdx.x * (kTmThreads / 32) >= n_def) return;  // the whole block has nothing to do
+  for (int e = threadIdx.x; e < 256; e += kTmThreads) {
+    const int sh = c_nni.step_h[e], th = c_nni.term_h[e];
+    T.step[e] = sh == kNoParam ? kNoEdge : sh * 65536 + c_nni.step_s[e];
+    T.term[e] = th == kNoParam ? kNoEdge : th * 65536 + c_nni.term_s[e];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (kTmThreads / 32);
+  for (uint32_t q = blockIdx.x * (kTmThreads / 32) + (threadIdx.x >> 5); q < n_def; q += warps) {
+    const uint64_t i = defer[1 + q];
+    const ah_hit h = hits[i];
+    const int L = plen[h.pattern];
+    const uint32_t pr = (h.pattern >> 2) * 2 + (h.pattern & 1u);
     const uint4 mk = pmask[pr];
     const PrimerMasks P{{mk.x, mk.y, mk.z, mk.w}};
-    thread_weights(T, W, kTmThreads, P, chain_nodes(P, L), codes[t] ^ 0xAAAAAAAAAAAAAAAAull, L);
+    const uint64_t code = site_code(planes, rec_group, h, L);
+    thread_weights(T, W, kTmThreads, P, chain_nodes(P, L), code ^ 0xAAAAAAAAAAAAAAAAull, L);
     const double tm = warp_enumerate(W, kTmThreads, P, L, R, status, lane);
     if (lane == 0) out[i] = tm;
   }
@@ -1763,19 +1793,29 @@ constexpr size_t kTmSmemCap = 48 * 1024;
 
 // the Tm of every marked site (hit_tm holds kSiteWanted there): one thread per site for the default
 // reading when its weights fit, else the group kernel where the state width allows, else k_tm_hits
+// one-thread-per-site kernel's shared memory for this primer set (0: the weights do not fit)
+size_t thread_kernel_smem(const ah_primers* p, int variants) {
+  if (variants) return 0;
+  int ww = 1;
+  for (uint32_t q = 0; q < p->n_pairs; ++q)
+    ww = std::max({ww, thread_weight_words(p->fwd[q]), thread_weight_words(p->rev[q])});
+  const size_t smem = 4 * ((size_t)kTmThreadFixedWords + (size_t)ww * kTmThreads);
+  return smem <= kTmSmemCap ? smem : 0;
+}
+
+// defer: cap + 1 words of device scratch for the sites the chain does not cover (the thread kernel
+// lists them there for k_tm_deferred)
 void launch_tm_hits(cudaStream_t s, const TmRun& R, const ah_primers* p, const ah_hit* hits, uint64_t cap,
                     const uint64_t* d_n, const uint2* planes, const uint64_t* rec_group, double* hit_tm,
-                    uint32_t* status) {
-  if (!R.variants) {
-    int ww = 1;
-    for (uint32_t q = 0; q < p->n_pairs; ++q)
-      ww = std::max({ww, thread_weight_words(p->fwd[q]), thread_weight_words(p->rev[q])});
-    const size_t smem = 4 * ((size_t)kTmThreadFixedWords + (size_t)ww * kTmThreads);
-    if (smem <= kTmSmemCap) {
-      k_tm_hits_t<<<(unsigned)std::max<uint64_t>(1, (cap + kTmSlots - 1) / kTmSlots), kTmThreads, smem, s>>>(
-          hits, cap, planes, rec_group, p->d_plen, p->d_psets, p->d_pmask, R, hit_tm, status, d_n);
-      return;
-    }
+                    uint32_t* status, uint32_t* defer, int sm_count) {
+  if (const size_t smem = thread_kernel_smem(p, R.variants)) {
+    cudaMemsetAsync(defer, 0, sizeof(uint32_t), s);
+    k_tm_hits_t<<<(unsigned)std::max<uint64_t>(1, (cap + kTmSlots - 1) / kTmSlots), kTmThreads, smem, s>>>(
+        hits, cap, planes, rec_group, p->d_plen, p->d_psets, p->d_pmask, R, hit_tm, status, defer, d_n);
+    const size_t smem_d = smem - 4 * (size_t)(3 * kTmSlots);  // tables and weights only
+    k_tm_deferred<<<(unsigned)std::max(1, 4 * sm_count), kTmThreads, smem_d, s>>>(hits, planes, rec_group, p->d_plen,
+                                                                                p->d_pmask, R, hit_tm, status, defer);
+    return;
   }
   const TmShape t = hits_shape(p, R.variants);
   if (!t.G) {
@@ -1878,11 +1918,12 @@ ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, siz
 
 void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit_cap, const uint64_t* d_nhits,
                const ah_primers* p, uint32_t* status, const uint2* planes, const uint64_t* rec_group, double* hit_tm,
-               ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep) {
+               ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep,
+               uint32_t* defer, int sm_count) {
   const TmRun R = *(const TmRun*)run;
   cudaMemsetAsync(hit_tm, 0, std::max<uint64_t>(1, hit_cap) * sizeof(double), s);
   k_mark_sites<<<(unsigned)std::max<uint64_t>(1, (amp_cap + 255) / 256), 256, 0, s>>>(amps, amp_cap, hit_tm, d_namps);
-  launch_tm_hits(s, R, p, hits, hit_cap, d_nhits, planes, rec_group, hit_tm, status);
+  launch_tm_hits(s, R, p, hits, hit_cap, d_nhits, planes, rec_group, hit_tm, status, defer, sm_count);
   k_tm_amps<<<(unsigned)std::max<uint64_t>(1, (amp_cap + 255) / 256), 256, 0, s>>>(amps, amp_cap, hit_tm, filter,
                                                                                   min_tm, keep, d_namps);
 }
@@ -1906,7 +1947,12 @@ ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const a
     k_mark_sites<<<(unsigned)((a->n + 255) / 256), 256, 0, ctx->stream>>>(a->d, a->n, hit_tm);
     launched(ctx);
   }
-  if (h->n && a->n) launch_tm_hits(ctx->stream, R, p, h->d, h->n, nullptr, b->planes, b->rec_group, hit_tm, ctx->d_status);
+  uint32_t* defer = nullptr;
+  if (h->n && a->n) {
+    if ((st = dalloc(ctx, &defer, h->n + 1))) return st;
+    launch_tm_hits(ctx->stream, R, p, h->d, h->n, nullptr, b->planes, b->rec_group, hit_tm, ctx->d_status, defer,
+                   ctx->sm_count);
+  }
   if (h->n && a->n) launched(ctx);
   if (params->filter && (st = dalloc(ctx, &keep, a->n))) return st;
   if (a->n)
@@ -1933,6 +1979,7 @@ ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const a
   }
   dfree(ctx, hit_tm);
   dfree(ctx, keep);
+  dfree(ctx, defer);
   return check_status(ctx);
 }
 
