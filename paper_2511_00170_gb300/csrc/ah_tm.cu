@@ -1131,22 +1131,43 @@ __global__ void __launch_bounds__(kTmWindow) k_tm_hits_g(const ah_hit* __restric
 // 4000 K).  The chain and its exactness are site_tm_chain's; sites it does not cover (salt methods 6
 // and 7, L < 3, an entropy sum that could reach zero) go to site_tm.
 constexpr int kTmThreads = 128;
+constexpr int kTmTabWords = 3 * 256;  // TmTabs
 
-struct TmTabs {               // packed dH * 65536 + dS (tenths), kNoEdge without a parameter
-  int32_t step[256], term[256];
+// Packed dH * 65536 + dS (tenths), kNoEdge without a parameter, laid out so that for the two
+// opposite-strand codes of an edge its 16 entries (the variant's two bases x, y) are one row:
+// step[(c0 4 + c1) 16 + x 4 + y] for edge i (c0, c1 at i, i + 1); term_l[(c1 4 + c0) 16 + y 4 + x] for
+// the left end read from the other strand; term_r[(c0 4 + c1) 16 + x 4 + y] for the right end.  With
+// x and y known at compile time a lookup is one shared load at a fixed offset from the row.
+struct TmTabs {
+  int32_t step[256], term_l[256], term_r[256];
 };
+
+__device__ __forceinline__ void fill_tabs(TmTabs& T) {
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
+    // e = a * 64 + b * 16 + c * 4 + d: the step 5'-ab-3' over 3'-cd-5'
+    const int a = e >> 6, b = (e >> 4) & 3, c = (e >> 2) & 3, d = e & 3;
+    const int sh = c_nni.step_h[e], th = c_nni.term_h[e];
+    const int32_t sp = sh == kNoParam ? kNoEdge : sh * 65536 + c_nni.step_s[e];
+    const int32_t tp = th == kNoParam ? kNoEdge : th * 65536 + c_nni.term_s[e];
+    T.step[(c * 4 + d) * 16 + a * 4 + b] = sp;
+    T.term_r[(c * 4 + d) * 16 + a * 4 + b] = tp;
+    // read from the other strand: 5'-ab-3' = 5'-c1 c0-3' over 3'-y x-5' with row (c1, c0) = (a, b)
+    T.term_l[(a * 4 + b) * 16 + c * 4 + d] = tp;
+  }
+}
 
 __device__ __forceinline__ int32_t edge_tab(const TmTabs& T, int i, int L, int x, int y, uint64_t cc) {
   const int c0 = (int)(cc >> (2 * i)) & 3, c1 = (int)(cc >> (2 * i + 2)) & 3;
+  const int row = (c0 * 4 + c1) * 16;
   if (i == 0) {
-    const int32_t p = T.term[c1 * 64 + c0 * 16 + y * 4 + x];
+    const int32_t p = T.term_l[(c1 * 4 + c0) * 16 + y * 4 + x];
     if (p != kNoEdge) return p;
   }
   if (i == L - 2) {
-    const int32_t p = T.term[x * 64 + y * 16 + c0 * 4 + c1];
+    const int32_t p = T.term_r[row + x * 4 + y];
     if (p != kNoEdge) return p;
   }
-  return T.step[x * 64 + y * 16 + c0 * 4 + c1];
+  return T.step[row + x * 4 + y];
 }
 
 __device__ __forceinline__ int32_t end_packed(int j, int L, int v) {
@@ -1176,9 +1197,17 @@ __device__ __forceinline__ int rank_of(uint32_t ch, int a) { return __popc(ch & 
 // One pass over the compressed chain in score arithmetic S: the best A * dS10 - B * dH10 and that
 // variant's exact packed sums.  W: this thread's weights (stride `ws` words); dmask: branch
 // positions (never empty).
+// A step between adjacent branch positions lo, lo + 1 that are not the duplex's end edges is one
+// parameter lookup per pair of bases: its weights are the step table's row for the site's two
+// opposite-strand codes there, read in place rather than copied per site.
+__device__ __forceinline__ bool direct_step(int lo, int hi, int L) { return hi == lo + 1 && lo != 0 && lo != L - 2; }
+__device__ __forceinline__ int row_of(uint64_t cc, int i) {
+  return (int)(((cc >> (2 * i)) & 3u) * 4 + ((cc >> (2 * i + 2)) & 3u)) * 16;
+}
+
 template <typename S>
-__device__ __forceinline__ bool thread_pass(const int32_t* __restrict__ W, int ws, const PrimerMasks P, uint32_t dmask,
-                                            S A, S B, S* best, int32_t* bsum) {
+__device__ __forceinline__ bool thread_pass(const TmTabs& T, const int32_t* __restrict__ W, int ws, const PrimerMasks P,
+                                            uint32_t dmask, uint64_t cc, int L, S A, S B, S* best, int32_t* bsum) {
   const S none = no_score<S>();
   S cur[4];
   int32_t cs[4];
@@ -1201,6 +1230,8 @@ __device__ __forceinline__ bool thread_pass(const int32_t* __restrict__ W, int w
     rest &= rest - 1;
     const uint32_t chb = P.ch(hi);
     const int nb = __popc(chb);
+    const bool direct = direct_step(lo, hi, L);
+    const int32_t* trow = T.step + row_of(cc, lo);
     S nx[4];
     int32_t ns[4];
 #pragma unroll
@@ -1212,16 +1243,17 @@ __device__ __forceinline__ bool thread_pass(const int32_t* __restrict__ W, int w
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         if (!((chb >> b) & 1u)) continue;
-        const int32_t p = W[(row + rank_of(chb, b)) * ws];
+        const int32_t p = direct ? trow[a * 4 + b] : W[(row + rank_of(chb, b)) * ws];
         if (p == kNoEdge) continue;
         const S sc = cur[a] + (A * (S)unpack_ds(p) - B * (S)unpack_dh(p));
         if (sc > nx[b]) nx[b] = sc, ns[b] = cs[a] + p;
       }
     }
-    off += __popc(cha) * nb;
+    if (!direct) off += __popc(cha) * nb;
 #pragma unroll
     for (int b = 0; b < 4; ++b) cur[b] = nx[b], cs[b] = ns[b];
     cha = chb;
+    lo = hi;
   }
   S bs = none;
   int32_t bp = 0;
@@ -1267,6 +1299,20 @@ __device__ __forceinline__ int thread_weights(const TmTabs& T, int32_t* __restri
     const int hi = __ffs(rest) - 1;
     const uint32_t cha = P.ch(lo), chb = P.ch(hi);
     const int nb = __popc(chb);
+    if (direct_step(lo, hi, L)) {  // read in place by the passes: only its part of the bound
+      const int32_t* trow = T.step + row_of(cc, lo);
+      int mx = INT_MIN;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int32_t p = trow[a * 4 + b];
+          if (((cha >> a) & 1u) && ((chb >> b) & 1u) && p != kNoEdge) mx = max(mx, unpack_ds(p));
+        }
+      bound += mx == INT_MIN ? 0 : mx;
+      lo = hi;
+      continue;
+    }
     int32_t mid = 0, left[4], right[4];
     const bool adjacent = hi == lo + 1;
     if (!adjacent) {
@@ -1335,7 +1381,7 @@ __device__ __forceinline__ bool thread_site_tm(const TmTabs& T, int32_t* __restr
   int32_t bp;
   if (0.1 * bound + Sc + S0 >= 0.0) {  // the bound leaves the sign open: the largest dS itself
     int sc;
-    if (!thread_pass<int>(W, ws, P, dmask, 1, 0, &sc, &bp)) {
+    if (!thread_pass<int>(T, W, ws, P, dmask, cc, L, 1, 0, &sc, &bp)) {
       *tm = nan;
       return true;
     }
@@ -1343,7 +1389,7 @@ __device__ __forceinline__ bool thread_site_tm(const TmTabs& T, int32_t* __restr
   }
   {
     int sc;
-    if (!thread_pass<int>(W, ws, P, dmask, 300, 1000, &sc, &bp)) {
+    if (!thread_pass<int>(T, W, ws, P, dmask, cc, L, 300, 1000, &sc, &bp)) {
       *tm = nan;
       return true;
     }
@@ -1357,11 +1403,11 @@ __device__ __forceinline__ bool thread_site_tm(const TmTabs& T, int32_t* __restr
     if (fabs(lam) < 4000.0) {
       const long long Lq = llrint(lam * kScale), Bq = (long long)(1000.0 * kScale);
       long long sc;
-      if (!thread_pass<long long>(W, ws, P, dmask, Lq, Bq, &sc, &cand)) break;
+      if (!thread_pass<long long>(T, W, ws, P, dmask, cc, L, Lq, Bq, &sc, &cand)) break;
       better = sc > Lq * unpack_ds(inc) - Bq * unpack_dh(inc);
     } else {
       double sc;
-      if (!thread_pass<double>(W, ws, P, dmask, lam, 1000.0, &sc, &cand)) break;
+      if (!thread_pass<double>(T, W, ws, P, dmask, cc, L, lam, 1000.0, &sc, &cand)) break;
       const double ref = lam * unpack_ds(inc) - 1000.0 * unpack_dh(inc);
       better = sc > ref + 1e-12 * fabs(ref);
     }
@@ -1397,18 +1443,20 @@ __device__ __forceinline__ int nth_code(uint32_t ch, uint32_t d) {
 // single-precision value (the margin covers its rounding: 1 K plus 2e-4 of the absolute
 // temperature) and those whose entropy sum is within 2 cal/(K mol) of zero, where single precision
 // says little.  More than 2^20 variants: NaN and ST_TM_LIMIT.
-__device__ __noinline__ double warp_enumerate(const int32_t* __restrict__ W, int ws, const PrimerMasks P, int L,
-                                              const TmRun& R, uint32_t* status, int lane) {
+__device__ __noinline__ double warp_enumerate(const TmTabs& T, const int32_t* __restrict__ W, int ws, const PrimerMasks P,
+                                              uint64_t cc, int L, const TmRun& R, uint32_t* status, int lane) {
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   const uint32_t dmask = chain_nodes(P, L);
   const uint32_t lmask = L >= 32 ? 0xFFFFFFFFu : ((1u << L) - 1u);
   const int gc_fixed = __popc((P.m[1] | P.m[3]) & ~dmask & lmask);  // C and G at single-choice positions
   uint64_t count = 1;
-  int off_suf = 0, prev_n = 0;
+  int off_suf = 0, prev_n = 0, prev_pos = -1;
   for (uint32_t x = dmask; x; x &= x - 1) {
-    const int n = __popc(P.ch(__ffs(x) - 1));
-    off_suf += prev_n ? prev_n * n : n;
-    prev_n = n;
+    const int pos = __ffs(x) - 1;
+    const int n = __popc(P.ch(pos));
+    if (prev_pos < 0) off_suf += n;
+    else if (!direct_step(prev_pos, pos, L)) off_suf += prev_n * n;
+    prev_n = n, prev_pos = pos;
     count = min(count * (uint64_t)n, kEnumLimit + 1);
   }
   if (count > kEnumLimit) {
@@ -1426,19 +1474,26 @@ __device__ __noinline__ double warp_enumerate(const int32_t* __restrict__ W, int
     uint32_t ch = P.ch(hi);
     int n_next = __popc(ch);
     uint32_t d_next = take_digit(&v, n_next);
+    int code_next = nth_code(ch, d_next);
     int off = off_suf;
     int32_t sum = W[(off + d_next) * ws];
-    int g = gc_fixed + (nth_code(ch, d_next) & 1);
+    int g = gc_fixed + (code_next & 1);
     x &= ~(1u << hi);
+    int pos_next = hi;
     while (x) {
       hi = 31 - __clz(x);
       ch = P.ch(hi);
       const int n = __popc(ch);
       const uint32_t d = take_digit(&v, n);
-      off -= n * n_next;
-      sum = add_packed(sum, W[(off + d * n_next + d_next) * ws]);
-      g += nth_code(ch, d) & 1;
-      n_next = n, d_next = d;
+      const int code = nth_code(ch, d);
+      if (direct_step(hi, pos_next, L)) {
+        sum = add_packed(sum, T.step[row_of(cc, hi) + code * 4 + code_next]);
+      } else {
+        off -= n * n_next;
+        sum = add_packed(sum, W[(off + d * n_next + d_next) * ws]);
+      }
+      g += code & 1;
+      n_next = n, d_next = d, code_next = code, pos_next = hi;
       x &= ~(1u << hi);
     }
     *gc = g;
@@ -1488,26 +1543,37 @@ __device__ __noinline__ double warp_enumerate(const int32_t* __restrict__ W, int
 // where that needs no chain (not wanted, or a step between single-choice positions without a
 // parameter); the rest are sorted by primer and taken in that order, kTmThreads at a time, so a
 // warp's threads share the primer (the same loop bounds) and the warps are full.  Shared memory:
-// the tables, the window's keys and site codes, then the weights of each thread (see
+// the tables, the window's keys and their order by primer, then the weights of each thread (see
 // thread_weight_words), strided by the block size.
 constexpr int kTmSlots = 8 * kTmThreads;
+constexpr int kTmBins = 256;  // primer bins of the counting sort (a multiple of 32)
+
+// the bits of x at the even positions of a 64-bit word (bit j to bit 2j)
+__device__ __forceinline__ uint64_t spread_bits(uint32_t x) {
+  uint64_t v = x;
+  v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
+  v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
+  v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  v = (v | (v << 2)) & 0x3333333333333333ull;
+  return (v | (v << 1)) & 0x5555555555555555ull;
+}
 
 // the site's bases over [pos, pos + L) (L <= 32 spans at most two plane words), in the primer's
-// orientation, 2 bits per position
+// orientation, 2 bits per position (position j at bits 2j, 2j + 1; nothing past L)
 __device__ __forceinline__ uint64_t site_code(const uint2* __restrict__ planes, const uint64_t* __restrict__ rec_group,
                                               const ah_hit& h, int L) {
-  const uint32_t strand = (h.pattern >> 1) & 1u;
   const uint64_t x0 = rec_group[h.record] * 32 + h.pos;
   const uint2 w0 = planes[x0 >> 5], w1 = planes[(x0 >> 5) + 1];
   const int sh0 = (int)(x0 & 31);
-  const uint64_t lo = (((uint64_t)w1.x << 32) | w0.x) >> sh0, hi = (((uint64_t)w1.y << 32) | w0.y) >> sh0;
-  uint64_t code = 0;
-  for (int j = 0; j < L; ++j) {
-    const int q = strand == 0 ? j : L - 1 - j;
-    const uint64_t b = ((lo >> q) & 1u) | (((hi >> q) & 1u) << 1);
-    code |= (strand == 0 ? b : b ^ 2u) << (2 * j);
+  uint32_t lo = (uint32_t)(((((uint64_t)w1.x << 32) | w0.x) >> sh0));
+  uint32_t hi = (uint32_t)(((((uint64_t)w1.y << 32) | w0.y) >> sh0));
+  const uint64_t mask = L >= 32 ? ~0ull : ((1ull << (2 * L)) - 1);
+  if ((h.pattern >> 1) & 1u) {  // the reverse strand: reversed and complemented (code ^ 2)
+    lo = __brev(lo) >> (32 - L);
+    hi = __brev(hi) >> (32 - L);
+    return ((spread_bits(lo) | (spread_bits(hi) << 1)) ^ 0xAAAAAAAAAAAAAAAAull) & mask;
   }
-  return code;
+  return (spread_bits(lo) | (spread_bits(hi) << 1)) & mask;
 }
 
 __global__ void __launch_bounds__(kTmThreads, 4) k_tm_hits_t(const ah_hit* __restrict__ hits, uint64_t n,
@@ -1523,19 +1589,16 @@ __global__ void __launch_bounds__(kTmThreads, 4) k_tm_hits_t(const ah_hit* __res
   // to a kernel parameter would make the compiler copy it to local memory for every thread
   __shared__ TmRun R_sh;
   __shared__ int n_valid;
+  __shared__ uint32_t bins[kTmBins];
   if (threadIdx.x == 0) R_sh = Rp, n_valid = 0;
   const TmRun& R = R_sh;
   extern __shared__ __align__(16) uint32_t tm_smem[];
   TmTabs& T = *reinterpret_cast<TmTabs*>(tm_smem);
-  uint32_t* keys = tm_smem + 512;
-  uint64_t* codes = reinterpret_cast<uint64_t*>(tm_smem + 512 + kTmSlots);
-  int32_t* W = reinterpret_cast<int32_t*>(tm_smem + 512 + 3 * kTmSlots) + threadIdx.x;
+  uint32_t* keys = tm_smem + kTmTabWords;
+  uint32_t* order = tm_smem + kTmTabWords + kTmSlots;
+  int32_t* W = reinterpret_cast<int32_t*>(tm_smem + kTmTabWords + 2 * kTmSlots) + threadIdx.x;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
-  for (int e = threadIdx.x; e < 256; e += kTmThreads) {
-    const int sh = c_nni.step_h[e], th = c_nni.term_h[e];
-    T.step[e] = sh == kNoParam ? kNoEdge : sh * 65536 + c_nni.step_s[e];
-    T.term[e] = th == kNoParam ? kNoEdge : th * 65536 + c_nni.term_s[e];
-  }
+  fill_tabs(T);
   __syncthreads();
   const uint64_t base = (uint64_t)blockIdx.x * kTmSlots;
   const uint64_t n_here = d_n ? min(n, *d_n) : n;
@@ -1561,7 +1624,6 @@ __global__ void __launch_bounds__(kTmThreads, 4) k_tm_hits_t(const ah_hit* __res
         out[i] = nan;
       } else {
         key = (pr << 16) | (uint32_t)t;
-        codes[t] = code;
         ++mine;
       }
     }
@@ -1570,27 +1632,41 @@ __global__ void __launch_bounds__(kTmThreads, 4) k_tm_hits_t(const ah_hit* __res
   if (mine) atomicAdd(&n_valid, mine);
   __syncthreads();
   if (n_valid == 0) return;
-  for (int size = 2; size <= kTmSlots; size <<= 1)
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < kTmSlots; t += kTmThreads) {
-        const int o = t ^ stride;
-        if (o > t) {
-          const uint32_t x = keys[t], y = keys[o];
-          const bool up = (t & size) == 0;
-          if ((x > y) == up) keys[t] = y, keys[o] = x;
-        }
-      }
-      __syncthreads();
+  // group the sites by primer: a counting sort over the primers (their ids folded into kTmBins
+  // bins, which can only mix shapes, never lose a site); order within a primer does not matter
+  for (int k = threadIdx.x; k < kTmBins; k += kTmThreads) bins[k] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < kTmSlots; t += kTmThreads)
+    if (keys[t] != 0xFFFFFFFFu) atomicAdd(&bins[(keys[t] >> 16) % kTmBins], 1u);
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive scan of the bins, kTmBins / 32 per lane
+    constexpr int per = kTmBins / 32;
+    uint32_t v[per], sum = 0;
+    for (int k = 0; k < per; ++k) v[k] = bins[threadIdx.x * per + k], sum += v[k];
+    uint32_t x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((int)threadIdx.x >= o) x += y;
     }
+    uint32_t run = x - sum;
+    for (int k = 0; k < per; ++k) bins[threadIdx.x * per + k] = run, run += v[k];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kTmSlots; t += kTmThreads) {
+    const uint32_t key = keys[t];
+    if (key != 0xFFFFFFFFu) order[atomicAdd(&bins[(key >> 16) % kTmBins], 1u)] = key;
+  }
+  __syncthreads();
   for (int q = threadIdx.x; q < n_valid; q += kTmThreads) {
-    const uint32_t key = keys[q];
+    const uint32_t key = order[q];
     const uint32_t t = key & 0xFFFFu, pr = key >> 16;
     const uint64_t i = base + t;
-    const int L = plen[hits[i].pattern];
+    const ah_hit h = hits[i];
+    const int L = plen[h.pattern];
     const uint4 mk = pmask[pr];
     const PrimerMasks P{{mk.x, mk.y, mk.z, mk.w}};
     double tm;
-    if (thread_site_tm(T, W, kTmThreads, P, codes[t], L, R, &tm))
+    if (thread_site_tm(T, W, kTmThreads, P, site_code(planes, rec_group, h, L), L, R, &tm))
       out[i] = tm;
     else  // the chain does not cover it: listed for k_tm_deferred
       defer[1 + atomicAdd(defer, 1u)] = (uint32_t)i;
@@ -1612,14 +1688,10 @@ __global__ void __launch_bounds__(kTmThreads) k_tm_deferred(const ah_hit* __rest
   const TmRun& R = R_sh;
   extern __shared__ __align__(16) uint32_t tm_smem[];
   TmTabs& T = *reinterpret_cast<TmTabs*>(tm_smem);
-  int32_t* W = reinterpret_cast<int32_t*>(tm_smem + 512) + threadIdx.x;
+  int32_t* W = reinterpret_cast<int32_t*>(tm_smem + kTmTabWords) + threadIdx.x;
   const uint32_t n_def = defer[0];
   if (blockIdx.x * (kTmThreads / 32) >= n_def) return;  // the whole block has nothing to do
-  for (int e = threadIdx.x; e < 256; e += kTmThreads) {
-    const int sh = c_nni.step_h[e], th = c_nni.term_h[e];
-    T.step[e] = sh == kNoParam ? kNoEdge : sh * 65536 + c_nni.step_s[e];
-    T.term[e] = th == kNoParam ? kNoEdge : th * 65536 + c_nni.term_s[e];
-  }
+  fill_tabs(T);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * (kTmThreads / 32);
@@ -1632,7 +1704,7 @@ __global__ void __launch_bounds__(kTmThreads) k_tm_deferred(const ah_hit* __rest
     const PrimerMasks P{{mk.x, mk.y, mk.z, mk.w}};
     const uint64_t code = site_code(planes, rec_group, h, L);
     thread_weights(T, W, kTmThreads, P, chain_nodes(P, L), code ^ 0xAAAAAAAAAAAAAAAAull, L);
-    const double tm = warp_enumerate(W, kTmThreads, P, L, R, status, lane);
+    const double tm = warp_enumerate(T, W, kTmThreads, P, code ^ 0xAAAAAAAAAAAAAAAAull, L, R, status, lane);
     if (lane == 0) out[i] = tm;
   }
 }
@@ -1779,17 +1851,21 @@ TmShape hits_shape(const ah_primers* p, int variants) {
 // positions, one per pair of choices at consecutive ones (a primer without a branch position: its
 // first position, one choice)
 int thread_weight_words(const std::string& primer) {
-  std::vector<int> n;
-  for (char ch : primer)
-    if (__builtin_popcount(iupac_set(ch)) >= 2) n.push_back(__builtin_popcount(iupac_set(ch)));
-  if (n.empty()) n.push_back(1);
+  const int L = (int)primer.size();
+  std::vector<int> n, pos;
+  for (int j = 0; j < L; ++j)
+    if (__builtin_popcount(iupac_set(primer[j])) >= 2) n.push_back(__builtin_popcount(iupac_set(primer[j]))), pos.push_back(j);
+  if (n.empty()) n.push_back(1), pos.push_back(0);
   int w = n.front() + n.back();
-  for (size_t t = 0; t + 1 < n.size(); ++t) w += n[t] * n[t + 1];
+  for (size_t t = 0; t + 1 < n.size(); ++t) {
+    const bool direct = pos[t + 1] == pos[t] + 1 && pos[t] != 0 && pos[t] != L - 2;  // see direct_step
+    if (!direct) w += n[t] * n[t + 1];
+  }
   return w;
 }
 
-constexpr int kTmThreadFixedWords = 512 + 3 * kTmSlots;  // tables, keys, site codes
-constexpr size_t kTmSmemCap = 48 * 1024;
+constexpr int kTmThreadFixedWords = kTmTabWords + 2 * kTmSlots;  // tables, keys and their order
+constexpr size_t kTmSmemCap = 46 * 1024;  // dynamic shared memory, beside the kernels' static arrays
 
 // the Tm of every marked site (hit_tm holds kSiteWanted there): one thread per site for the default
 // reading when its weights fit, else the group kernel where the state width allows, else k_tm_hits
@@ -1812,7 +1888,7 @@ void launch_tm_hits(cudaStream_t s, const TmRun& R, const ah_primers* p, const a
     cudaMemsetAsync(defer, 0, sizeof(uint32_t), s);
     k_tm_hits_t<<<(unsigned)std::max<uint64_t>(1, (cap + kTmSlots - 1) / kTmSlots), kTmThreads, smem, s>>>(
         hits, cap, planes, rec_group, p->d_plen, p->d_psets, p->d_pmask, R, hit_tm, status, defer, d_n);
-    const size_t smem_d = smem - 4 * (size_t)(3 * kTmSlots);  // tables and weights only
+    const size_t smem_d = smem - 4 * (size_t)(2 * kTmSlots);  // tables and weights only
     k_tm_deferred<<<(unsigned)std::max(1, 4 * sm_count), kTmThreads, smem_d, s>>>(hits, planes, rec_group, p->d_plen,
                                                                                 p->d_pmask, R, hit_tm, status, defer);
     return;
