@@ -35,6 +35,19 @@ SM_COUNT, ALU_LANES_PER_SM_CLK, SM_MAX_GHZ = 152, 64, 2.07
 ALU_PEAK_TOPS = SM_COUNT * ALU_LANES_PER_SM_CLK * SM_MAX_GHZ / 1e3   # T lane-ops/s
 
 
+TM_KERNELS = {"generated": 0, "builtin": 1}
+
+
+def engine_for(args, device):
+    """An engine on `device` with the degenerate-site Tm kernel the command line asks for."""
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Engine
+
+    eng = Engine(device)
+    ah.ah_ctx_set_tm_kernel(eng.ctx, TM_KERNELS[getattr(args, "tm_kernel", "generated")])
+    return eng
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -373,7 +386,7 @@ def run_engine(args):
     from paper_2511_00170_gb300 import ah
     from paper_2511_00170_gb300.pipeline import Engine, Params
 
-    eng = Engine(local)
+    eng = engine_for(args, local)
     stream = torch.cuda.ExternalStream(ah.ah_ctx_stream(eng.ctx))
     params = Params.from_workload(wl)
     on_device = hasattr(wl, "d_seq")   # drawn on the device
@@ -574,7 +587,7 @@ def dense_record(args, steps, warmup):
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
     wl = sg.dense(n_genomes=5000)
-    eng = Engine(0)
+    eng = engine_for(args, 0)
     batch = eng.pack_device(wl.d_seq.data_ptr(), wl.offsets.astype(np.uint64), wl.genome_ids)
     ah.ah_ctx_synchronize(eng.ctx)
     gen_s = time.perf_counter() - t0
@@ -643,7 +656,7 @@ def batched_record(args, steps, warmup):
     torch.cuda.set_device(0)
     t_gen = time.perf_counter()
     wl = sg.batched(n_genomes=args.genomes or 50_000)
-    eng = Engine(0)
+    eng = engine_for(args, 0)
     batch = eng.pack_device(wl.d_seq.data_ptr(), wl.offsets.astype(np.uint64), wl.genome_ids)
     ah.ah_ctx_synchronize(eng.ctx)
     gen_s = time.perf_counter() - t_gen
@@ -734,7 +747,7 @@ def serving_record(args, runs):
     torch.cuda.set_device(0)
     n_db = args.genomes or 40_000
     lengths, _ = sg.serving_layout(n_genomes=n_db)
-    eng = Engine(0)
+    eng = engine_for(args, 0)
     t0 = time.perf_counter()
     db = ah.ah_batch_create(eng.ctx, np.asarray(lengths, dtype=np.uint64))
     for first, d, offs in sg.serving_db_chunks(n_genomes=n_db):
@@ -820,7 +833,7 @@ def run_reads(args):
     text = torch.empty(text_np.nbytes, dtype=torch.uint8, pin_memory=True)
     text.numpy()[:] = text_np
     del text_np
-    eng = Engine(0)
+    eng = engine_for(args, 0)
     p = Params.from_workload(wl)
     L = ah.load()
     pinned = {}
@@ -900,6 +913,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=40, help="sub-record: requests of the stable-rate trace")
     ap.add_argument("--serve-rate", type=float, default=3.0, help="sub-record: arrival rate of the stable trace")
     ap.add_argument("--serve-burst", type=int, default=100, help="sub-record: requests offered at 200 req/s")
+    ap.add_argument("--tm-kernel", default="generated", choices=sorted(TM_KERNELS),
+                    help="degenerate-site Tm: the kernel generated per primer set, or the built-in one")
     ap.add_argument("--scan-mode", type=int, default=2,
                     help="serving: 0 generated scan kernels, 1 generic kernel, 2 generic while compiling")
     args = ap.parse_args()

@@ -89,6 +89,9 @@ typedef struct {
                                  scan by the generic kernel */
   uint64_t generic_scans;   /* scans run by the generic (compile-free) kernel, wholly or in part */
   uint64_t generic_bases;   /* bases of those scans the generic kernel covered (whole tiles) */
+  uint64_t tm_generated;    /* degenerate-site Tm launches of ah_tm_filter by a kernel generated for
+                               the primer set (see ah_ctx_set_tm_kernel) */
+  uint64_t tm_builtin;      /* ... by the kernel built into the library */
 } ah_ctx_stats;
 ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out);
 ah_status ah_ctx_stats_reset(ah_ctx* ctx);
@@ -114,6 +117,24 @@ ah_status ah_ctx_set_pairs_per_kernel(ah_ctx* ctx, int pairs);
  *     (a fixed hand-over point, for tests).
  * Plans always use a generated kernel.  AH_EINVAL for another mode. */
 ah_status ah_ctx_set_generic_scan(ah_ctx* ctx, int mode);
+
+/* Which kernel computes the degenerate-site Tm of the default reading (every concrete variant
+ * counts; Section "Primer degeneracy"); all give the same maximum within 1e-9 degC.
+ *   0 (the default): a kernel generated for the primer set: each primer's chain of variants as
+ *     straight-line code over the transitions that exist (compiled with NVRTC on first use, then
+ *     cached process-wide).  Sets of more than 16 pairs, or whose distinct primers hold more than 96
+ *     transitions between adjacent degenerate positions (their compile time), take the built-in
+ *     kernel.
+ *   1: the kernel built into the library, which walks any primer's chain from position masks.
+ *   2: the generated kernel when it is compiled already, else the built-in kernel while a host
+ *     thread of the context compiles it (server contexts use this mode).
+ * Plans use the generated kernel unless the mode is 1.  AH_EINVAL for another mode. */
+ah_status ah_ctx_set_tm_kernel(ah_ctx* ctx, int mode);
+/* Diagnostics (no device needed): generate the Tm kernel for n primers (IUPAC, 2..32 nt; index
+ * 2 * pair + primer as in a primer set) and compile it with NVRTC for compute capability sm (e.g.
+ * 103).  AH_OK if it compiles; AH_EJIT with the compiler's log in log (log_cap bytes, NUL-ended)
+ * if not; AH_EINVAL for a bad argument or more than 64 primers. */
+ah_status ah_tm_kernel_check(const char* const* primers, uint32_t n, int sm, char* log, uint64_t log_cap);
 
 /* Time every scan launch with CUDA events on the context's stream (scan_ms).  Synchronises the
  * stream to collect the timings of plan replays still pending. */

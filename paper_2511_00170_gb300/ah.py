@@ -77,7 +77,8 @@ class ah_ctx_stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("scan_launches", ctypes.c_uint64), ("scan_ms", ctypes.c_double),
                 ("scan_bases", ctypes.c_uint64), ("jit_compiles", ctypes.c_uint64), ("jit_ms", ctypes.c_double),
                 ("scan_ops_per_group", ctypes.c_int32), ("generic_scans", ctypes.c_uint64),
-                ("generic_bases", ctypes.c_uint64)]
+                ("generic_bases", ctypes.c_uint64), ("tm_generated", ctypes.c_uint64),
+                ("tm_builtin", ctypes.c_uint64)]
 
 
 class ah_batch_view(ctypes.Structure):
@@ -99,6 +100,8 @@ SIGNATURES = {
     "ah_ctx_stats_reset": (_I32, [_VP]),
     "ah_ctx_set_pairs_per_kernel": (_I32, [_VP, ctypes.c_int]),
     "ah_ctx_set_generic_scan": (_I32, [_VP, ctypes.c_int]),
+    "ah_ctx_set_tm_kernel": (_I32, [_VP, ctypes.c_int]),
+    "ah_tm_kernel_check": (_I32, [_VP, _U32, ctypes.c_int, ctypes.c_char_p, ctypes.c_uint64]),
     "ah_ctx_set_timing": (_I32, [_VP, _I32]),
     "ah_ctx_set_scan_config": (_I32, [_VP, _I32, _I32, _I32, _I32]),
     "ah_pack_batch": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
@@ -238,6 +241,20 @@ def ah_ctx_set_generic_scan(ctx, mode: int) -> None:
     """0: generated scan kernels; 1: the generic (compile-free) kernel; 2: the generic kernel while the
     primer set's kernels compile; 3: generic on the first half of the tiles, generated on the rest."""
     _check(load().ah_ctx_set_generic_scan(ctx, int(mode)), ctx)
+
+
+def ah_ctx_set_tm_kernel(ctx, mode: int) -> None:
+    """Degenerate-site Tm kernel: 0 generated for the primer set; 1 built in; 2 built in while the
+    generated one compiles."""
+    _check(load().ah_ctx_set_tm_kernel(ctx, int(mode)), ctx)
+
+
+def ah_tm_kernel_check(primers: Sequence[str], sm: int = 103) -> Tuple[int, str]:
+    """Generate and compile (NVRTC, no device) the Tm kernel for these primers: (status, log)."""
+    arr = (ctypes.c_char_p * len(primers))(*[p.encode() for p in primers])
+    log = ctypes.create_string_buffer(1 << 16)
+    st = load().ah_tm_kernel_check(ctypes.cast(arr, ctypes.c_void_p), len(primers), int(sm), log, len(log))
+    return st, log.value.decode(errors="replace")
 
 
 def ah_ctx_set_timing(ctx, enable: bool) -> None:

@@ -17,7 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libah.so")
 SOURCES = ["ah_api.cu", "ah_util.cu", "ah_scan.cu", "ah_pair.cu", "ah_tm.cu", "ah_extract.cu", "ah_plan.cu", "ah_fasta.cu", "ah_jit.cpp",
-           "ah_serve.cpp", "ah_output.cpp", "ah_files.cpp"]
+           "ah_tm_jit.cpp", "ah_serve.cpp", "ah_output.cpp", "ah_files.cpp"]
+# headers every translation unit may include; ah_tm_chain.cuh is also compiled at run time (its text
+# is embedded in the library by _embed)
+HEADERS = ["ah_internal.h", "ah_tm_chain.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,15 +38,32 @@ def _cuda_home(nvcc: str) -> str:
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "ah_internal.h"), os.path.join(HERE, "..", "include", "ah.h")]
+    deps = [src, *(os.path.join(CSRC, h) for h in HEADERS), os.path.join(HERE, "..", "include", "ah.h")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps if os.path.exists(d))
+
+
+def _embed(header: str, out: str) -> None:
+    """Write header's text as a C++ raw string literal (rewritten only when it changes)."""
+    with open(header) as f:
+        text = f.read()
+    assert ")AHSRC\"" not in text
+    lit = 'R"AHSRC(' + text + ')AHSRC"\n'
+    if os.path.exists(out):
+        with open(out) as f:
+            if f.read() == lit:
+                return
+    with open(out + ".tmp", "w") as f:
+        f.write(lit)
+    os.replace(out + ".tmp", out)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     cuda = _cuda_home(nvcc)
     os.makedirs(BUILD, exist_ok=True)
-    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(HERE, "..", "include")]
+    _embed(os.path.join(CSRC, "ah_tm_chain.cuh"), os.path.join(BUILD, "ah_tm_chain_src.inc"))
+    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(HERE, "..", "include"),
+              "-I", BUILD]
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)

@@ -500,6 +500,8 @@ ah_status ah_ctx_stats_get(const ah_ctx* ctx, ah_ctx_stats* out) {
   out->jit_ms = ctx->jit_ms;
   out->scan_ops_per_group = ctx->scan_ops_per_group;
   out->generic_scans = ctx->n_generic_scans;
+  out->tm_generated = ctx->n_tm_generated;
+  out->tm_builtin = ctx->n_tm_builtin;
   out->generic_bases = ctx->generic_bases;
   return AH_OK;
 }
@@ -509,6 +511,7 @@ ah_status ah_ctx_stats_reset(ah_ctx* ctx) {
   ah_status st = drain_timings(ctx);  // timings of replays before the reset do not count after it
   if (st) return st;
   ctx->n_launches = ctx->n_scan_launches = ctx->scan_bases = ctx->jit_compiles = ctx->n_generic_scans = ctx->generic_bases = 0;
+  ctx->n_tm_generated = ctx->n_tm_builtin = 0;
   ctx->scan_ms = ctx->jit_ms = 0.0;
   return AH_OK;
 }
@@ -529,6 +532,13 @@ ah_status ah_ctx_set_pairs_per_kernel(ah_ctx* ctx, int pairs) {
   if (!ctx) return AH_EINVAL;
   if (pairs < 0 || pairs > 256) return fail(ctx, AH_EINVAL, "ah_ctx_set_pairs_per_kernel: 0..256");
   ctx->scan_cfg.pairs_per_kernel = pairs;
+  return AH_OK;
+}
+
+ah_status ah_ctx_set_tm_kernel(ah_ctx* ctx, int mode) {
+  if (!ctx) return AH_EINVAL;
+  if (mode < 0 || mode > 2) return fail(ctx, AH_EINVAL, "ah_ctx_set_tm_kernel: mode 0 to 2");
+  ctx->tm_kernel = mode;
   return AH_OK;
 }
 

@@ -125,6 +125,11 @@ struct ah_ctx {
   uint64_t drain_gen = 0;
   // fault injection on the host: this many of the next device allocations fail with AH_ENOMEM
   int fail_allocs = 0;
+  // degenerate-site Tm kernel: 0 the kernel generated for the primer set (compiled on first use),
+  // 1 the built-in kernel, 2 the built-in kernel while the generated one compiles in the background
+  int tm_kernel = 0;
+  uint64_t n_tm_generated = 0;  // Tm launches (outside plans) by a generated kernel
+  uint64_t n_tm_builtin = 0;    // ... by the built-in one
 };
 
 struct ah_batch {
@@ -290,10 +295,32 @@ void launch_pair_walk(cudaStream_t s, bool emit, const ah_hit* hits, uint64_t ca
                       uint32_t* overflow);
 constexpr size_t kTmRunBytes = 128;  // room for the Tm run constants a plan keeps
 ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, size_t run_size);
+// A degenerate-site Tm kernel generated for one primer set (ah_tm_jit.cpp); fn null: the built-in one.
+struct TmKernel {
+  cudaKernel_t fn = nullptr;
+  int weight_words = 0;        // weight words per thread
+  const int32_t* image = nullptr;  // the parameter tables as the kernel's shared memory holds them
+};
+// Larger primer sets take the built-in kernel: compile time grows with the primers and, about 40 ms
+// each, with the transitions between adjacent degenerate positions.
+constexpr int kTmJitMaxPrimers = 32;
+constexpr int kTmJitMaxAdjacent = 96;
+// transitions between adjacent degenerate positions over a set's distinct primers
+int tm_chain_adjacent(const std::vector<std::string>& primers);
+// The kernel for p by the context's choice (ctx->tm_kernel): generated (compiled now if need be,
+// unless !wait and mode 2), or fn = null for the built-in kernel.
+ah_status tm_kernel_for(ah_ctx* ctx, const ah_primers* p, bool wait, TmKernel* out);
+std::string tm_chain_source(const std::vector<std::string>& primers, int* weight_words);
+// packed initiation terms (tenths) of end base v at position j of a length-L variant (ah_tm.cu)
+int32_t tm_end_packed(int j, int L, int v);
+size_t tm_run_bytes();
+// the parameter tables laid out as the generated kernels copy them into shared memory, on ctx's
+// device (built once per device)
+ah_status tm_tab_image(ah_ctx* ctx, const int32_t** out);
 void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit_cap, const uint64_t* d_nhits,
                const ah_primers* p, uint32_t* status, const uint2* planes, const uint64_t* rec_group, double* hit_tm,
                ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep,
-               uint32_t* defer, int sm_count);
+               uint32_t* defer, int sm_count, const TmKernel& tk);
 void launch_compact_amps(cudaStream_t s, const ah_amplicon* in, uint64_t cap, const uint32_t* keep, const uint64_t* off,
                          ah_amplicon* out);
 void launch_extract(cudaStream_t s, bool write, const ah_amplicon* amps, uint64_t cap, const uint64_t* d_n,
@@ -308,6 +335,12 @@ struct ScanKernel {
   int alu_ops_per_group = 0;  // LOP3 + funnel-shift instructions of the generated circuit per 32 positions
 };
 std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg, int* alu_ops_per_group = nullptr);
+// NVRTC for this device's architecture (host work only); fills cubin or returns a message
+ah_status nvrtc_compile(int device, const std::string& src, const char* name, std::vector<char>* cubin,
+                        std::string* err);
+// the same for compute capability sm (e.g. 103), with no device needed
+ah_status nvrtc_compile_sm(int sm, const std::string& src, const char* name, std::vector<char>* cubin,
+                           std::string* err);
 // Generated scan kernels, one process-wide cache keyed by source text: a kernel is compiled once,
 // callers that ask for it while it compiles wait for that compile.  Kernels stay loaded for the
 // life of the process.

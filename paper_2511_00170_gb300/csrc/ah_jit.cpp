@@ -510,24 +510,22 @@ struct JitCache::Entry {
   ScanKernel k{};
 };
 
-JitCache& JitCache::global() {
-  static JitCache* cache = new JitCache();  // never destroyed: kernels stay loaded until exit
-  return *cache;
-}
-
-namespace {
-
-// NVRTC for this device's architecture (host work only); fills cubin or returns a message
-ah_status compile(int device, const std::string& src, std::vector<char>* cubin, std::string* err) {
-  nvrtcProgram prog;
-  if (nvrtcCreateProgram(&prog, src.c_str(), "ah_scan_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
-    *err = "nvrtcCreateProgram failed";
-    return AH_EJIT;
-  }
+ah_status nvrtc_compile(int device, const std::string& src, const char* name, std::vector<char>* cubin,
+                        std::string* err) {
   int major = 0, minor = 0;
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
-  std::string arch = "-arch=sm_" + std::to_string(major * 10 + minor) + (major >= 9 ? "a" : "");
+  return nvrtc_compile_sm(major * 10 + minor, src, name, cubin, err);
+}
+
+ah_status nvrtc_compile_sm(int sm, const std::string& src, const char* name, std::vector<char>* cubin,
+                           std::string* err) {
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), name, 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+    *err = "nvrtcCreateProgram failed";
+    return AH_EJIT;
+  }
+  std::string arch = "-arch=sm_" + std::to_string(sm) + (sm >= 90 ? "a" : "");
   const char* opts[] = {arch.c_str(), "-default-device", "-lineinfo"};
   nvrtcResult r = nvrtcCompileProgram(prog, 3, opts);
   if (r != NVRTC_SUCCESS) {
@@ -536,7 +534,7 @@ ah_status compile(int device, const std::string& src, std::vector<char>* cubin, 
     std::string log(n, '\0');
     nvrtcGetProgramLog(prog, &log[0]);
     nvrtcDestroyProgram(&prog);
-    *err = "scan kernel compilation failed: " + log.substr(0, 2000);
+    *err = std::string(name) + ": compilation failed: " + log.substr(0, 2000);
     return AH_EJIT;
   }
   size_t cubin_size = 0;
@@ -545,6 +543,18 @@ ah_status compile(int device, const std::string& src, std::vector<char>* cubin, 
   nvrtcGetCUBIN(prog, cubin->data());
   nvrtcDestroyProgram(&prog);
   return AH_OK;
+}
+
+
+JitCache& JitCache::global() {
+  static JitCache* cache = new JitCache();  // never destroyed: kernels stay loaded until exit
+  return *cache;
+}
+
+namespace {
+
+ah_status compile(int device, const std::string& src, std::vector<char>* cubin, std::string* err) {
+  return nvrtc_compile(device, src, "ah_scan_jit.cu", cubin, err);
 }
 
 // the runtime's library API (no link-time driver dependency); fills k or returns a message

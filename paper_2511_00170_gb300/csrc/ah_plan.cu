@@ -49,6 +49,7 @@ struct ah_plan {
   uint32_t* ctr = nullptr;      // [0] fullest tile, [1] overflow bits, [2..3] persistent work counter
   uint64_t* h_out = nullptr;    // pinned: counters read back after a run
   alignas(8) unsigned char tm_run[ah::kTmRunBytes];
+  ah::TmKernel tm_k;  // the degenerate-site Tm kernel generated for p (fn null: the built-in one)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   // The scan node is bracketed by two event-record nodes.  Timed replays use a ring of executable
@@ -151,7 +152,8 @@ void enqueue_post(ah_plan* pl, cudaStream_t s) {
                    q.orient_mask & 15u, nullptr, pl->poff, pl->amps, pl->amp_cap, pl->ctr + 1);
   const uint64_t* n_amps = pl->poff + pl->hit_cap;
   launch_tm(s, pl->tm_run, pl->hits, pl->hit_cap, n_hits, p, pl->ctx->d_status, b->planes, b->rec_group, pl->hit_tm,
-            pl->amps, pl->amp_cap, n_amps, q.tm.filter, q.tm.min_tm, pl->keep, pl->tm_defer, pl->ctx->sm_count);
+            pl->amps, pl->amp_cap, n_amps, q.tm.filter, q.tm.min_tm, pl->keep, pl->tm_defer, pl->ctx->sm_count,
+            pl->tm_k);
   const ah_amplicon* out = pl->amps;
   const uint64_t* n_out = n_amps;
   if (q.tm.filter) {
@@ -291,6 +293,7 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
   pl->cfg = ctx->scan_cfg;
   pl->cfg.pairs_per_kernel = 0;  // a plan captures one scan kernel over every pair
   ah_status st = tm_prepare(ctx, &prm->tm, pl->tm_run, sizeof pl->tm_run);
+  if (!st && !prm->tm.variants) st = tm_kernel_for(ctx, p, true, &pl->tm_k);
   for (int i = 0; i < 2 && !st; ++i)
     if (cudaEventCreate(&pl->scan_ev[i]) != cudaSuccess) st = fail(ctx, AH_ECUDA, "ah_plan_create: event creation failed");
   const auto t0 = std::chrono::steady_clock::now();

@@ -143,6 +143,9 @@ void run_job(ah_server* s, int slot, Job* j) {
     const double work = (double)(g1 - g0) * 32.0 * 4.0 * r.n_pairs;
     ctx->stream = s->streams[slot][priority_class(work, (int)s->streams[slot].size())];
     ctx->generic_scan = s->scan_mode.load();
+    // the Tm kernel generated for a new primer set compiles in the background, like its scan
+    // kernels, unless the request asked for built-in kernels only
+    ctx->tm_kernel = ctx->generic_scan == 1 ? 1 : 2;
   }
   ah_batch* slice = nullptr;
   ah_primers* pr = nullptr;

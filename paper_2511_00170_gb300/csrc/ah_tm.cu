@@ -168,12 +168,14 @@ void build_tables(NNTables* t) {
 
 std::mutex g_tables_mu;
 bool g_tables_loaded[64] = {};
+NNTablesI g_host_i;                   // the integer tables as uploaded
+const int32_t* g_tab_image[64] = {};  // per device: TmTabs for the generated Tm kernels
 
 ah_status load_tables(ah_ctx* ctx) {
   std::lock_guard<std::mutex> lock(g_tables_mu);
   if (ctx->device < 64 && g_tables_loaded[ctx->device]) return AH_OK;
   static NNTables host;
-  static NNTablesI host_i;
+  NNTablesI& host_i = g_host_i;
   build_tables(&host);
   auto tenths = [](double x) -> int16_t {
     if (std::isnan(x)) return kNoParam;
@@ -191,17 +193,9 @@ ah_status load_tables(ah_ctx* ctx) {
   return AH_OK;
 }
 
-// run constants computed once on the host
-struct TmRun {
-  double rlnk;        // R ln(C)
-  double ln_mon;      // ln of the monovalent-equivalent concentration (M)
-  double corr_const;  // methods 1-4: Tm correction
-  // methods 6 and 7: correction to 1/Tm, rc0 + rc1 f + rc2 / (2 (L - 1)) with f the G/C fraction
-  double rc0, rc1, rc2;
-  double sym_h, sym_s;  // self-complementary duplexes: the symmetry terms (else 0)
-  int saltcorr;
-  int variants;       // 1: degenerate site Tm over the variants matching the site only
-};
+// run constants, packed sums, table layout, site codes and the per-site chain driver shared with the
+// kernels generated at run time
+#include "ah_tm_chain.cuh"
 
 // Free Mg2+ (M) beside dNTPs binding it one to one, association constant 3e4 per M (Owczarzy et al.
 // 2008): the positive root of Ka x^2 + (Ka (dNTP - Mg) + 1) x - Mg = 0.
@@ -232,6 +226,8 @@ ah_status make_run(ah_ctx* ctx, const ah_tm_params* p, TmRun* r) {
   r->variants = p->variants;
   r->sym_h = p->selfcomp ? kSymH : 0.0;
   r->sym_s = p->selfcomp ? kSymS : 0.0;
+  r->h0 = kInitH + kOneGCH + r->sym_h;
+  r->s0 = kInitS + kOneGCS + r->sym_s;
   r->corr_const = r->rc0 = r->rc1 = r->rc2 = 0.0;
   const double lm = r->ln_mon;
   switch (p->saltcorr) {
@@ -374,7 +370,7 @@ __device__ __forceinline__ bool edge_sums(int i, int L, uint8_t a, uint8_t b, co
 }
 
 // initiation terms (tenths) that depend on the variant's end bases
-__device__ __forceinline__ void end_sums(int j, int L, uint8_t v, int* dh, int* ds) {
+__host__ __device__ __forceinline__ void end_sums(int j, int L, uint8_t v, int* dh, int* ds) {
   *dh = (v & 1) ? kTermGCH10 : kTermATH10;
   *ds = (v & 1) ? kTermGCS10 : kTermATS10;
   if (j == 0 && v == 2) *dh += k5TAH10, *ds += k5TAS10;       // 5' T
@@ -484,17 +480,6 @@ enum ChainResult { kChainOk, kChainUndefined, kChainUnbounded };
 // forward with each state (no backtracking).  T is float for the search passes and int64 (fixed
 // point) for the confirming pass.  States are (position, base, mismatches so far), at most
 // 4 x (k + 1) per position.
-template <typename T>
-__device__ __forceinline__ T no_score();
-template <>
-__device__ __forceinline__ float no_score<float>() { return -INFINITY; }
-template <>
-__device__ __forceinline__ double no_score<double>() { return -INFINITY; }
-template <>
-__device__ __forceinline__ long long no_score<long long>() { return LLONG_MIN; }
-template <>
-__device__ __forceinline__ int no_score<int>() { return INT_MIN; }
-
 template <typename T>
 __device__ bool chain_viterbi(const SiteVariants& V, T A, T B, T* best_score, int* dh10, int* ds10) {
   constexpr int M = kMaxK + 1;
@@ -661,7 +646,6 @@ __device__ __forceinline__ uint8_t base_code(const uint2* planes, uint64_t group
 // that shows the optimum is also the one that proves it.  Sites whose chain does not apply (salt
 // methods 6 and 7, L < 3, an entropy sum that could reach zero, state widths above G / 4) are handed
 // whole to site_tm by the group's first lane.
-constexpr int32_t kNoEdge = INT32_MIN;  // packed weight of a transition with no parameter
 
 struct TmGroupSh {      // per site, in shared memory; followed by the (D - 1) x 16 step weights
   uint8_t set[32];      // the primer's IUPAC sets (5'->3')
@@ -681,12 +665,7 @@ __host__ __device__ inline int tm_group_words(int dmax) {
   return (w + 31) / 32 * 32 + 4;
 }
 
-__device__ __forceinline__ int unpack_ds(int32_t p) { return (int16_t)(p & 0xffff); }
-__device__ __forceinline__ int unpack_dh(int32_t p) { return (p - unpack_ds(p)) >> 16; }
 __device__ __forceinline__ int fixed_base(uint32_t ch) { return __ffs(ch) - 1; }
-__device__ __forceinline__ int32_t add_packed(int32_t p, int32_t q) {
-  return (p == kNoEdge || q == kNoEdge) ? kNoEdge : p + q;
-}
 
 // packed sums (tenths) of edge i with base x at i and y at i + 1, kNoEdge without a parameter
 __device__ __forceinline__ int32_t edge_packed(const TmGroupSh& sh, int L, int i, int x, int y) {
@@ -922,9 +901,8 @@ __device__ double group_site_tm(TmGroupSh& sh, int32_t* w, int L, int k, int cla
 }
 
 // Only the sites that some amplicon pairs need a Tm (an amplicon's Tm is the lower of its two
-// sites'): the amplicons first write this word (a NaN no Tm computation returns) into hit_tm at
-// their two sites, over an array cleared to zero, and the Tm kernel takes only the marked sites.
-constexpr unsigned long long kSiteWanted = 0xFFFFFFFFFFFFFFFFull;
+// sites'): the amplicons first write kSiteWanted into hit_tm at their two sites, over an array
+// cleared to zero, and the Tm kernels take only the marked sites.
 
 __global__ void k_mark_sites(const ah_amplicon* __restrict__ a, uint64_t n, double* __restrict__ hit_tm,
                              const uint64_t* __restrict__ d_n = nullptr) {
@@ -1127,47 +1105,26 @@ __global__ void __launch_bounds__(kTmWindow) k_tm_hits_g(const ah_hit* __restric
 // The compressed chain's step weights are stored per thread in shared memory, only for pairs of
 // allowed choices and strided by the block size (a warp's accesses fall in different banks); the
 // parameter tables are copied to shared memory; the passes score in integers: the start pass with
-// the exact int32 score 300 dS - 1000 dH, the proving passes in 64-bit fixed point (double beyond
-// 4000 K).  The chain and its exactness are site_tm_chain's; sites it does not cover (salt methods 6
-// and 7, L < 3, an entropy sum that could reach zero) go to site_tm.
-constexpr int kTmThreads = 128;
-constexpr int kTmTabWords = 3 * 256;  // TmTabs
+// the exact int32 score 300 dS - 1000 dH, the proving passes in 64-bit fixed point
+// (chain_site_tm).  Sites the chain does not cover (salt methods 6 and 7, L < 3, an entropy sum
+// that could reach zero) are enumerated by k_tm_deferred.  The kernels generated per primer set
+// (ah_tm_jit.cpp) share the driver and the kernel body and replace only the chain's passes.
 
-// Packed dH * 65536 + dS (tenths), kNoEdge without a parameter, laid out so that for the two
-// opposite-strand codes of an edge its 16 entries (the variant's two bases x, y) are one row:
-// step[(c0 4 + c1) 16 + x 4 + y] for edge i (c0, c1 at i, i + 1); term_l[(c1 4 + c0) 16 + y 4 + x] for
-// the left end read from the other strand; term_r[(c0 4 + c1) 16 + x 4 + y] for the right end.  With
-// x and y known at compile time a lookup is one shared load at a fixed offset from the row.
-struct TmTabs {
-  int32_t step[256], term_l[256], term_r[256];
-};
-
-__device__ __forceinline__ void fill_tabs(TmTabs& T) {
-  for (int e = threadIdx.x; e < 256; e += blockDim.x) {
-    // e = a * 64 + b * 16 + c * 4 + d: the step 5'-ab-3' over 3'-cd-5'
-    const int a = e >> 6, b = (e >> 4) & 3, c = (e >> 2) & 3, d = e & 3;
-    const int sh = c_nni.step_h[e], th = c_nni.term_h[e];
-    const int32_t sp = sh == kNoParam ? kNoEdge : sh * 65536 + c_nni.step_s[e];
-    const int32_t tp = th == kNoParam ? kNoEdge : th * 65536 + c_nni.term_s[e];
-    T.step[(c * 4 + d) * 16 + a * 4 + b] = sp;
-    T.term_r[(c * 4 + d) * 16 + a * 4 + b] = tp;
-    // read from the other strand: 5'-ab-3' = 5'-c1 c0-3' over 3'-y x-5' with row (c1, c0) = (a, b)
-    T.term_l[(a * 4 + b) * 16 + c * 4 + d] = tp;
-  }
+// table entry e = a * 64 + b * 16 + c * 4 + d (the step 5'-ab-3' over 3'-cd-5') into its TmTabs places
+__host__ __device__ __forceinline__ void put_tab_entry(TmTabs& T, const NNTablesI& ti, int e) {
+  const int a = e >> 6, b = (e >> 4) & 3, c = (e >> 2) & 3, d = e & 3;
+  const int sh = ti.step_h[e], th = ti.term_h[e];
+  const int32_t sp = sh == kNoParam ? kNoEdge : sh * 65536 + ti.step_s[e];
+  const int32_t tp = th == kNoParam ? kNoEdge : th * 65536 + ti.term_s[e];
+  T.step[(c * 4 + d) * 16 + a * 4 + b] = sp;
+  T.term_r[(c * 4 + d) * 16 + a * 4 + b] = tp;
+  // read from the other strand: 5'-ab-3' = 5'-c1 c0-3' over 3'-y x-5' with row (c1, c0) = (a, b)
+  T.term_l[(a * 4 + b) * 16 + c * 4 + d] = tp;
 }
 
-__device__ __forceinline__ int32_t edge_tab(const TmTabs& T, int i, int L, int x, int y, uint64_t cc) {
-  const int c0 = (int)(cc >> (2 * i)) & 3, c1 = (int)(cc >> (2 * i + 2)) & 3;
-  const int row = (c0 * 4 + c1) * 16;
-  if (i == 0) {
-    const int32_t p = T.term_l[(c1 * 4 + c0) * 16 + y * 4 + x];
-    if (p != kNoEdge) return p;
-  }
-  if (i == L - 2) {
-    const int32_t p = T.term_r[row + x * 4 + y];
-    if (p != kNoEdge) return p;
-  }
-  return T.step[row + x * 4 + y];
+// TmTabs from the parameter tables (row_ds is not filled: only the generated chains read it)
+__device__ __forceinline__ void fill_tabs(TmTabs& T) {
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) put_tab_entry(T, c_nni, e);
 }
 
 __device__ __forceinline__ int32_t end_packed(int j, int L, int v) {
@@ -1175,22 +1132,6 @@ __device__ __forceinline__ int32_t end_packed(int j, int L, int v) {
   end_sums(j, L, (uint8_t)v, &dh, &ds);
   return dh * 65536 + ds;
 }
-
-// the primer as four position masks, one per base code (bit j: position j allows the code)
-struct PrimerMasks {
-  uint32_t m[4];
-  __device__ __forceinline__ uint32_t ch(int j) const {
-    return ((m[0] >> j) & 1u) | (((m[1] >> j) & 1u) << 1) | (((m[2] >> j) & 1u) << 2) | (((m[3] >> j) & 1u) << 3);
-  }
-  __device__ __forceinline__ int fixed(int j) const {  // the one code of a single-choice position
-    return (int)((m[1] >> j) & 1u) + 2 * (int)((m[2] >> j) & 1u) + 3 * (int)((m[3] >> j) & 1u);
-  }
-  // positions with at least two choices
-  __device__ __forceinline__ uint32_t branching(int L) const {
-    const uint32_t b = (m[0] & m[1]) | (m[0] & m[2]) | (m[0] & m[3]) | (m[1] & m[2]) | (m[1] & m[3]) | (m[2] & m[3]);
-    return L >= 32 ? b : b & ((1u << L) - 1u);
-  }
-};
 
 __device__ __forceinline__ int rank_of(uint32_t ch, int a) { return __popc(ch & ((1u << a) - 1u)); }
 
@@ -1201,9 +1142,6 @@ __device__ __forceinline__ int rank_of(uint32_t ch, int a) { return __popc(ch & 
 // parameter lookup per pair of bases: its weights are the step table's row for the site's two
 // opposite-strand codes there, read in place rather than copied per site.
 __device__ __forceinline__ bool direct_step(int lo, int hi, int L) { return hi == lo + 1 && lo != 0 && lo != L - 2; }
-__device__ __forceinline__ int row_of(uint64_t cc, int i) {
-  return (int)(((cc >> (2 * i)) & 3u) * 4 + ((cc >> (2 * i + 2)) & 3u)) * 16;
-}
 
 template <typename S>
 __device__ __forceinline__ bool thread_pass(const TmTabs& T, const int32_t* __restrict__ W, int ws, const PrimerMasks P,
@@ -1363,62 +1301,31 @@ __device__ __forceinline__ uint32_t chain_nodes(const PrimerMasks P, int L) {
   return d ? d : 1u;
 }
 
-// Tm of one site over every variant of its primer (k unlimited, no clamp restriction) by the chain
-// method, its fixed steps known to have parameters.  Returns false when the chain does not apply
-// (salt methods 6 and 7, L < 3, an entropy sum that could reach zero): the site is then enumerated
-// by warp_enumerate.  W: room for this primer's weights at stride ws.
-__device__ __forceinline__ bool thread_site_tm(const TmTabs& T, int32_t* __restrict__ W, int ws, const PrimerMasks P,
-                                               uint64_t code, int L, const TmRun& R, double* tm) {
-  const double nan = __longlong_as_double(0x7ff8000000000000ll);
-  if (R.saltcorr >= 6 || L < 3) return false;
-  const uint64_t cc = code ^ 0xAAAAAAAAAAAAAAAAull;
-  const uint32_t dmask = chain_nodes(P, L);
-  const int bound = thread_weights(T, W, ws, P, dmask, cc, L);
-  const double S0 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
-  const double H0 = kInitH + kOneGCH + R.sym_h, Sc = kInitS + kOneGCS + R.sym_s;
-  const double shift = R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0;
-  auto ratio = [&](int32_t p) { return 1000.0 * (0.1 * unpack_dh(p) + H0) / (0.1 * unpack_ds(p) + Sc + S0); };
-  int32_t bp;
-  if (0.1 * bound + Sc + S0 >= 0.0) {  // the bound leaves the sign open: the largest dS itself
-    int sc;
-    if (!thread_pass<int>(T, W, ws, P, dmask, cc, L, 1, 0, &sc, &bp)) {
-      *tm = nan;
-      return true;
-    }
-    if (0.1 * unpack_ds(bp) + Sc + S0 >= 0.0) return false;
+// Any primer's compressed chain, walked from its position masks (the chain type of chain_site_tm).
+struct GenericChain {
+  PrimerMasks P;
+  uint32_t dmask;  // branch positions
+  uint64_t cc;     // the site's opposite-strand codes
+  int L;
+  __device__ __forceinline__ int weights(const TmTabs& T, int32_t* __restrict__ W, int ws) const {
+    return thread_weights(T, W, ws, P, dmask, cc, L);
   }
-  {
-    int sc;
-    if (!thread_pass<int>(T, W, ws, P, dmask, cc, L, 300, 1000, &sc, &bp)) {
-      *tm = nan;
-      return true;
-    }
+  template <typename S>
+  __device__ __forceinline__ bool pass(const TmTabs& T, const int32_t* __restrict__ W, int ws, S A, S B, S* best,
+                                       int32_t* bsum) const {
+    return thread_pass<S>(T, W, ws, P, dmask, cc, L, A, B, best, bsum);
   }
-  double lam = ratio(bp);
-  int32_t inc = bp;
-  constexpr double kScale = 68719476736.0;  // 2^36
-  for (int it = 0; it < 64; ++it) {
-    bool better;
-    int32_t cand;
-    if (fabs(lam) < 4000.0) {
-      const long long Lq = llrint(lam * kScale), Bq = (long long)(1000.0 * kScale);
-      long long sc;
-      if (!thread_pass<long long>(T, W, ws, P, dmask, cc, L, Lq, Bq, &sc, &cand)) break;
-      better = sc > Lq * unpack_ds(inc) - Bq * unpack_dh(inc);
-    } else {
-      double sc;
-      if (!thread_pass<double>(T, W, ws, P, dmask, cc, L, lam, 1000.0, &sc, &cand)) break;
-      const double ref = lam * unpack_ds(inc) - 1000.0 * unpack_dh(inc);
-      better = sc > ref + 1e-12 * fabs(ref);
-    }
-    if (!better) break;
-    const double q = ratio(cand);
-    if (!(q > lam)) break;
-    lam = q, inc = cand;
+};
+
+// the built-in kernel's sites: tables from the parameter arrays, every primer by GenericChain
+struct GenericSites {
+  static __device__ __forceinline__ void fill(TmTabs& T, const int32_t*) { fill_tabs(T); }
+  static __device__ __forceinline__ bool site(uint32_t, const TmTabs& T, int32_t* __restrict__ W, int ws,
+                                              const PrimerMasks P, uint64_t code, int L, const TmRun& R, double* tm) {
+    const GenericChain c{P, chain_nodes(P, L), code ^ 0xAAAAAAAAAAAAAAAAull, L};
+    return chain_site_tm(T, W, ws, c, L, R, tm);
   }
-  *tm = lam + shift - 273.15;
-  return true;
-}
+};
 
 // v / n and v % n for the 1 to 4 choices of an IUPAC code
 __device__ __forceinline__ uint32_t take_digit(uint32_t* v, int n) {
@@ -1538,139 +1445,16 @@ __device__ __noinline__ double warp_enumerate(const TmTabs& T, const int32_t* __
   return best > -INFINITY ? best : nan;
 }
 
-// The site Tm of every marked site, every concrete variant counting (params variants = 0).  Blocks
-// of kTmThreads threads take windows of kTmSlots site slots.  Each thread first settles its slots
-// where that needs no chain (not wanted, or a step between single-choice positions without a
-// parameter); the rest are sorted by primer and taken in that order, kTmThreads at a time, so a
-// warp's threads share the primer (the same loop bounds) and the warps are full.  Shared memory:
-// the tables, the window's keys and their order by primer, then the weights of each thread (see
-// thread_weight_words), strided by the block size.
-constexpr int kTmSlots = 8 * kTmThreads;
-constexpr int kTmBins = 256;  // primer bins of the counting sort (a multiple of 32)
-
-// the bits of x at the even positions of a 64-bit word (bit j to bit 2j)
-__device__ __forceinline__ uint64_t spread_bits(uint32_t x) {
-  uint64_t v = x;
-  v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
-  v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
-  v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
-  v = (v | (v << 2)) & 0x3333333333333333ull;
-  return (v | (v << 1)) & 0x5555555555555555ull;
-}
-
-// the site's bases over [pos, pos + L) (L <= 32 spans at most two plane words), in the primer's
-// orientation, 2 bits per position (position j at bits 2j, 2j + 1; nothing past L)
-__device__ __forceinline__ uint64_t site_code(const uint2* __restrict__ planes, const uint64_t* __restrict__ rec_group,
-                                              const ah_hit& h, int L) {
-  const uint64_t x0 = rec_group[h.record] * 32 + h.pos;
-  const uint2 w0 = planes[x0 >> 5], w1 = planes[(x0 >> 5) + 1];
-  const int sh0 = (int)(x0 & 31);
-  uint32_t lo = (uint32_t)(((((uint64_t)w1.x << 32) | w0.x) >> sh0));
-  uint32_t hi = (uint32_t)(((((uint64_t)w1.y << 32) | w0.y) >> sh0));
-  const uint64_t mask = L >= 32 ? ~0ull : ((1ull << (2 * L)) - 1);
-  if ((h.pattern >> 1) & 1u) {  // the reverse strand: reversed and complemented (code ^ 2)
-    lo = __brev(lo) >> (32 - L);
-    hi = __brev(hi) >> (32 - L);
-    return ((spread_bits(lo) | (spread_bits(hi) << 1)) ^ 0xAAAAAAAAAAAAAAAAull) & mask;
-  }
-  return (spread_bits(lo) | (spread_bits(hi) << 1)) & mask;
-}
-
+// The site Tm of every marked site, every concrete variant counting (params variants = 0): the
+// shared kernel body (tm_hits_body) over GenericChain.  Weights: thread_weight_words per thread.
 __global__ void __launch_bounds__(kTmThreads, 4) k_tm_hits_t(const ah_hit* __restrict__ hits, uint64_t n,
                                                              const uint2* __restrict__ planes,
                                                              const uint64_t* __restrict__ rec_group,
                                                              const uint8_t* __restrict__ plen,
-                                                             const uint8_t* __restrict__ psets,
                                                              const uint4* __restrict__ pmask, const TmRun Rp,
-                                                             double* __restrict__ out, uint32_t* status,
-                                                             uint32_t* __restrict__ defer,
+                                                             double* __restrict__ out, uint32_t* __restrict__ defer,
                                                              const uint64_t* __restrict__ d_n) {
-  // the run constants in shared memory: device functions take them by reference, and a reference
-  // to a kernel parameter would make the compiler copy it to local memory for every thread
-  __shared__ TmRun R_sh;
-  __shared__ int n_valid;
-  __shared__ uint32_t bins[kTmBins];
-  if (threadIdx.x == 0) R_sh = Rp, n_valid = 0;
-  const TmRun& R = R_sh;
-  extern __shared__ __align__(16) uint32_t tm_smem[];
-  TmTabs& T = *reinterpret_cast<TmTabs*>(tm_smem);
-  uint32_t* keys = tm_smem + kTmTabWords;
-  uint32_t* order = tm_smem + kTmTabWords + kTmSlots;
-  int32_t* W = reinterpret_cast<int32_t*>(tm_smem + kTmTabWords + 2 * kTmSlots) + threadIdx.x;
-  const double nan = __longlong_as_double(0x7ff8000000000000ll);
-  fill_tabs(T);
-  __syncthreads();
-  const uint64_t base = (uint64_t)blockIdx.x * kTmSlots;
-  const uint64_t n_here = d_n ? min(n, *d_n) : n;
-  int mine = 0;
-  for (int t = threadIdx.x; t < kTmSlots; t += kTmThreads) {
-    const uint64_t i = base + t;
-    uint32_t key = 0xFFFFFFFFu;
-    if (i < n_here && (unsigned long long)__double_as_longlong(out[i]) == kSiteWanted) {
-      const ah_hit h = hits[i];
-      const int L = plen[h.pattern];
-      const uint32_t pr = (h.pattern >> 2) * 2 + (h.pattern & 1u);
-      const uint64_t code = site_code(planes, rec_group, h, L);
-      const uint64_t cc = code ^ 0xAAAAAAAAAAAAAAAAull;
-      const uint4 mk = pmask[pr];
-      const PrimerMasks P{{mk.x, mk.y, mk.z, mk.w}};
-      const uint32_t fixed = ~P.branching(L) & (L >= 32 ? 0xFFFFFFFFu : ((1u << L) - 1u));
-      bool undefined = false;
-      for (uint32_t f = fixed & (fixed >> 1); f && !undefined; f &= f - 1) {  // steps j, j + 1 both fixed
-        const int j = __ffs(f) - 1;
-        if (edge_tab(T, j, L, P.fixed(j), P.fixed(j + 1), cc) == kNoEdge) undefined = true;
-      }
-      if (undefined) {
-        out[i] = nan;
-      } else {
-        key = (pr << 16) | (uint32_t)t;
-        ++mine;
-      }
-    }
-    keys[t] = key;
-  }
-  if (mine) atomicAdd(&n_valid, mine);
-  __syncthreads();
-  if (n_valid == 0) return;
-  // group the sites by primer: a counting sort over the primers (their ids folded into kTmBins
-  // bins, which can only mix shapes, never lose a site); order within a primer does not matter
-  for (int k = threadIdx.x; k < kTmBins; k += kTmThreads) bins[k] = 0;
-  __syncthreads();
-  for (int t = threadIdx.x; t < kTmSlots; t += kTmThreads)
-    if (keys[t] != 0xFFFFFFFFu) atomicAdd(&bins[(keys[t] >> 16) % kTmBins], 1u);
-  __syncthreads();
-  if (threadIdx.x < 32) {  // exclusive scan of the bins, kTmBins / 32 per lane
-    constexpr int per = kTmBins / 32;
-    uint32_t v[per], sum = 0;
-    for (int k = 0; k < per; ++k) v[k] = bins[threadIdx.x * per + k], sum += v[k];
-    uint32_t x = sum;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if ((int)threadIdx.x >= o) x += y;
-    }
-    uint32_t run = x - sum;
-    for (int k = 0; k < per; ++k) bins[threadIdx.x * per + k] = run, run += v[k];
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < kTmSlots; t += kTmThreads) {
-    const uint32_t key = keys[t];
-    if (key != 0xFFFFFFFFu) order[atomicAdd(&bins[(key >> 16) % kTmBins], 1u)] = key;
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < n_valid; q += kTmThreads) {
-    const uint32_t key = order[q];
-    const uint32_t t = key & 0xFFFFu, pr = key >> 16;
-    const uint64_t i = base + t;
-    const ah_hit h = hits[i];
-    const int L = plen[h.pattern];
-    const uint4 mk = pmask[pr];
-    const PrimerMasks P{{mk.x, mk.y, mk.z, mk.w}};
-    double tm;
-    if (thread_site_tm(T, W, kTmThreads, P, site_code(planes, rec_group, h, L), L, R, &tm))
-      out[i] = tm;
-    else  // the chain does not cover it: listed for k_tm_deferred
-      defer[1 + atomicAdd(defer, 1u)] = (uint32_t)i;
-  }
+  tm_hits_body<GenericSites>(hits, n, planes, rec_group, plen, pmask, Rp, out, defer, d_n, nullptr);
 }
 
 // The sites k_tm_hits_t listed (defer[0] of them at defer[1..]): one warp per site, every lane
@@ -1883,11 +1667,23 @@ size_t thread_kernel_smem(const ah_primers* p, int variants) {
 // lists them there for k_tm_deferred)
 void launch_tm_hits(cudaStream_t s, const TmRun& R, const ah_primers* p, const ah_hit* hits, uint64_t cap,
                     const uint64_t* d_n, const uint2* planes, const uint64_t* rec_group, double* hit_tm,
-                    uint32_t* status, uint32_t* defer, int sm_count) {
+                    uint32_t* status, uint32_t* defer, int sm_count, const TmKernel& tk, bool* generated) {
+  if (generated) *generated = false;
   if (const size_t smem = thread_kernel_smem(p, R.variants)) {
     cudaMemsetAsync(defer, 0, sizeof(uint32_t), s);
-    k_tm_hits_t<<<(unsigned)std::max<uint64_t>(1, (cap + kTmSlots - 1) / kTmSlots), kTmThreads, smem, s>>>(
-        hits, cap, planes, rec_group, p->d_plen, p->d_psets, p->d_pmask, R, hit_tm, status, defer, d_n);
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, (cap + kTmSlots - 1) / kTmSlots);
+    const size_t smem_j = 4 * ((size_t)kTmThreadFixedWords + (size_t)tk.weight_words * kTmThreads);
+    if (tk.fn && tk.image && smem_j <= kTmSmemCap) {  // the kernel generated for this primer set
+      const uint8_t* plen = p->d_plen;
+      const uint4* pmask = p->d_pmask;
+      void* args[] = {(void*)&hits, (void*)&cap, (void*)&planes, (void*)&rec_group, (void*)&plen, (void*)&pmask,
+                      (void*)&R, (void*)&hit_tm, (void*)&defer, (void*)&d_n, (void*)&tk.image};
+      cudaLaunchKernel((const void*)tk.fn, dim3(grid), dim3(kTmThreads), args, smem_j, s);
+      if (generated) *generated = true;
+    } else {
+      k_tm_hits_t<<<grid, kTmThreads, smem, s>>>(hits, cap, planes, rec_group, p->d_plen, p->d_pmask, R, hit_tm, defer,
+                                                 d_n);
+    }
     const size_t smem_d = smem - 4 * (size_t)(2 * kTmSlots);  // tables and weights only
     k_tm_deferred<<<(unsigned)std::max(1, 4 * sm_count), kTmThreads, smem_d, s>>>(hits, planes, rec_group, p->d_plen,
                                                                                 p->d_pmask, R, hit_tm, status, defer);
@@ -1985,6 +1781,44 @@ ah_status tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const ch
 
 static_assert(sizeof(TmRun) <= kTmRunBytes, "Tm run constants exceed a plan's buffer");
 
+int32_t tm_end_packed(int j, int L, int v) {
+  int dh, ds;
+  end_sums(j, L, (uint8_t)v, &dh, &ds);
+  return dh * 65536 + ds;
+}
+
+size_t tm_run_bytes() { return sizeof(TmRun); }
+
+ah_status tm_tab_image(ah_ctx* ctx, const int32_t** out) {
+  *out = nullptr;
+  ah_status st;
+  if ((st = load_tables(ctx))) return st;
+  std::lock_guard<std::mutex> lock(g_tables_mu);
+  if (ctx->device >= 64) return fail(ctx, AH_EINTERNAL, "tm_tab_image: device index above 63");
+  if (!g_tab_image[ctx->device]) {
+    TmTabs T;
+    for (int e = 0; e < 256; ++e) put_tab_entry(T, g_host_i, e);
+    for (int r = 0; r < 16; ++r) {  // the largest dS of each step row over its defined entries
+      int mx = 0;
+      bool any = false;
+      for (int k = 0; k < 16; ++k) {
+        const int32_t p = T.step[r * 16 + k];
+        if (p == kNoEdge) continue;
+        const int ds = (int16_t)(p & 0xffff);
+        mx = any ? std::max(mx, ds) : ds;
+        any = true;
+      }
+      T.row_ds[r] = mx;
+    }
+    int32_t* d = nullptr;
+    AH_CUDA(ctx, cudaMalloc(&d, sizeof T));  // kept for the life of the process, like the tables
+    AH_CUDA(ctx, cudaMemcpy(d, &T, sizeof T, cudaMemcpyHostToDevice));
+    g_tab_image[ctx->device] = d;
+  }
+  *out = g_tab_image[ctx->device];
+  return AH_OK;
+}
+
 ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, size_t run_size) {
   ah_status st;
   if ((st = load_tables(ctx))) return st;
@@ -1995,11 +1829,11 @@ ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, siz
 void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit_cap, const uint64_t* d_nhits,
                const ah_primers* p, uint32_t* status, const uint2* planes, const uint64_t* rec_group, double* hit_tm,
                ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep,
-               uint32_t* defer, int sm_count) {
+               uint32_t* defer, int sm_count, const TmKernel& tk) {
   const TmRun R = *(const TmRun*)run;
   cudaMemsetAsync(hit_tm, 0, std::max<uint64_t>(1, hit_cap) * sizeof(double), s);
   k_mark_sites<<<(unsigned)std::max<uint64_t>(1, (amp_cap + 255) / 256), 256, 0, s>>>(amps, amp_cap, hit_tm, d_namps);
-  launch_tm_hits(s, R, p, hits, hit_cap, d_nhits, planes, rec_group, hit_tm, status, defer, sm_count);
+  launch_tm_hits(s, R, p, hits, hit_cap, d_nhits, planes, rec_group, hit_tm, status, defer, sm_count, tk, nullptr);
   k_tm_amps<<<(unsigned)std::max<uint64_t>(1, (amp_cap + 255) / 256), 256, 0, s>>>(amps, amp_cap, hit_tm, filter,
                                                                                   min_tm, keep, d_namps);
 }
@@ -2026,8 +1860,12 @@ ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const a
   uint32_t* defer = nullptr;
   if (h->n && a->n) {
     if ((st = dalloc(ctx, &defer, h->n + 1))) return st;
+    TmKernel tk;
+    if (!R.variants && (st = tm_kernel_for(ctx, p, false, &tk))) return st;
+    bool generated = false;
     launch_tm_hits(ctx->stream, R, p, h->d, h->n, nullptr, b->planes, b->rec_group, hit_tm, ctx->d_status, defer,
-                   ctx->sm_count);
+                   ctx->sm_count, tk, &generated);
+    (generated ? ctx->n_tm_generated : ctx->n_tm_builtin)++;
   }
   if (h->n && a->n) launched(ctx);
   if (params->filter && (st = dalloc(ctx, &keep, a->n))) return st;
