@@ -1327,16 +1327,6 @@ struct GenericSites {
   }
 };
 
-// v / n and v % n for the 1 to 4 choices of an IUPAC code
-__device__ __forceinline__ uint32_t take_digit(uint32_t* v, int n) {
-  uint32_t d;
-  if (n == 4) d = *v & 3u, *v >>= 2;
-  else if (n == 2) d = *v & 1u, *v >>= 1;
-  else if (n == 3) { const uint32_t q = (uint32_t)(((uint64_t)*v * 0xAAAAAAABull) >> 33); d = *v - 3u * q, *v = q; }
-  else d = 0;
-  return d;
-}
-
 // the d-th allowed code of a choice set
 __device__ __forceinline__ int nth_code(uint32_t ch, uint32_t d) {
   for (uint32_t k = 0; k < d; ++k) ch &= ch - 1;
@@ -1350,62 +1340,65 @@ __device__ __forceinline__ int nth_code(uint32_t ch, uint32_t d) {
 // single-precision value (the margin covers its rounding: 1 K plus 2e-4 of the absolute
 // temperature) and those whose entropy sum is within 2 cal/(K mol) of zero, where single precision
 // says little.  More than 2^20 variants: NaN and ST_TM_LIMIT.
+//
+// A variant is a number in mixed radix, digit q the choice at the q-th branch position counted from
+// the 3' end.  Its sums are suffix(d_0) + sum over q of step_q(d_(q+1), d_q) + prefix(d_(m-1)).  Each
+// lane walks a contiguous block of variants like an odometer and keeps U[q], the sum of the terms
+// of digits q and above: a variant then costs the terms of digit 0, and a carry recomputes U only
+// up to the highest digit that changed.
+constexpr int kEnumMaxBranch = 32;
 __device__ __noinline__ double warp_enumerate(const TmTabs& T, const int32_t* __restrict__ W, int ws, const PrimerMasks P,
                                               uint64_t cc, int L, const TmRun& R, uint32_t* status, int lane) {
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   const uint32_t dmask = chain_nodes(P, L);
   const uint32_t lmask = L >= 32 ? 0xFFFFFFFFu : ((1u << L) - 1u);
   const int gc_fixed = __popc((P.m[1] | P.m[3]) & ~dmask & lmask);  // C and G at single-choice positions
+  // branch positions from the 3' end: position, choices, and where the weights of the step to the
+  // next one (toward 5') start in W (-1: read in place from the table)
+  uint8_t pos[kEnumMaxBranch], ch[kEnumMaxBranch], rad[kEnumMaxBranch];
+  int16_t offq[kEnumMaxBranch];
+  int m = 0;
+  int off_suf = 0;
   uint64_t count = 1;
-  int off_suf = 0, prev_n = 0, prev_pos = -1;
-  for (uint32_t x = dmask; x; x &= x - 1) {
-    const int pos = __ffs(x) - 1;
-    const int n = __popc(P.ch(pos));
-    if (prev_pos < 0) off_suf += n;
-    else if (!direct_step(prev_pos, pos, L)) off_suf += prev_n * n;
-    prev_n = n, prev_pos = pos;
-    count = min(count * (uint64_t)n, kEnumLimit + 1);
+  {
+    int prev_n = 0, prev_pos = -1;
+    for (uint32_t x = dmask; x; x &= x - 1) {  // 5' to 3': the offsets of the blocks
+      const int p = __ffs(x) - 1;
+      const int n = __popc(P.ch(p));
+      if (prev_pos < 0) off_suf += n;
+      else if (!direct_step(prev_pos, p, L)) off_suf += prev_n * n;
+      prev_n = n, prev_pos = p;
+      count = min(count * (uint64_t)n, kEnumLimit + 1);
+    }
+    if (count > kEnumLimit) {
+      if (lane == 0) atomicOr(status, (uint32_t)ST_TM_LIMIT);
+      return nan;
+    }
+    int off = off_suf;
+    for (uint32_t x = dmask; x; ++m) {  // 3' to 5'
+      const int p = 31 - __clz(x);
+      x &= ~(1u << p);
+      pos[m] = (uint8_t)p;
+      ch[m] = (uint8_t)P.ch(p);
+      rad[m] = (uint8_t)__popc(ch[m]);
+      offq[m] = -1;
+      if (m > 0) {
+        if (!direct_step(p, pos[m - 1], L)) {
+          off -= rad[m] * rad[m - 1];
+          offq[m - 1] = (int16_t)off;
+        }
+      }
+    }
   }
-  if (count > kEnumLimit) {
-    if (lane == 0) atomicOr(status, (uint32_t)ST_TM_LIMIT);
-    return nan;
-  }
+  // the step between digit q + 1 (toward 5') and digit q, for digits dq1, dq
+  auto step_w = [&](int q, uint32_t dq1, uint32_t dq) -> int32_t {
+    if (offq[q] < 0) return T.step[row_of(cc, pos[q + 1]) + nth_code(ch[q + 1], dq1) * 4 + nth_code(ch[q], dq)];
+    return W[(offq[q] + dq1 * rad[q] + dq) * ws];
+  };
   // constant parts of dH and dS, and the Tm from the sums, in single precision
   const float Hf = (float)(kInitH + R.sym_h);
   const float Sf = (float)(kInitS + R.sym_s + (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk);
   const float shiftf = R.saltcorr >= 1 && R.saltcorr <= 4 ? (float)R.corr_const : 0.f;
-  // one variant: its packed sums (kNoEdge if undefined) and G/C count
-  auto variant = [&](uint32_t v, int* gc) -> int32_t {
-    uint32_t x = dmask;
-    int hi = 31 - __clz(x);
-    uint32_t ch = P.ch(hi);
-    int n_next = __popc(ch);
-    uint32_t d_next = take_digit(&v, n_next);
-    int code_next = nth_code(ch, d_next);
-    int off = off_suf;
-    int32_t sum = W[(off + d_next) * ws];
-    int g = gc_fixed + (code_next & 1);
-    x &= ~(1u << hi);
-    int pos_next = hi;
-    while (x) {
-      hi = 31 - __clz(x);
-      ch = P.ch(hi);
-      const int n = __popc(ch);
-      const uint32_t d = take_digit(&v, n);
-      const int code = nth_code(ch, d);
-      if (direct_step(hi, pos_next, L)) {
-        sum = add_packed(sum, T.step[row_of(cc, hi) + code * 4 + code_next]);
-      } else {
-        off -= n * n_next;
-        sum = add_packed(sum, W[(off + d * n_next + d_next) * ws]);
-      }
-      g += code & 1;
-      n_next = n, d_next = d, code_next = code, pos_next = hi;
-      x &= ~(1u << hi);
-    }
-    *gc = g;
-    return add_packed(sum, W[d_next * ws]);
-  };
   auto tm_float = [&](int32_t p, int gc, bool* near_zero) {
     const float dh = 0.1f * (float)unpack_dh(p) + Hf, ds = 0.1f * (float)unpack_ds(p) + Sf;
     *near_zero = fabsf(ds) < 2.f;
@@ -1416,29 +1409,71 @@ __device__ __noinline__ double warp_enumerate(const TmTabs& T, const int32_t* __
     }
     return t;
   };
+  // this lane's block of variants
+  const uint64_t per = (count + 31) / 32;
+  const uint64_t v_begin = min(count, (uint64_t)lane * per), v_end = min(count, v_begin + per);
+  // one sweep over the block: fn(packed sums, G/C count) for every defined variant
+  auto sweep = [&](auto&& fn) {
+    if (v_begin >= v_end) return;
+    uint8_t d[kEnumMaxBranch];
+    int32_t U[kEnumMaxBranch];
+    int G[kEnumMaxBranch];
+    {
+      uint64_t v = v_begin;
+      for (int q = 0; q < m; ++q) d[q] = (uint8_t)(v % rad[q]), v /= rad[q];
+    }
+    int top = m - 1;  // U[q] and G[q] are stale for q <= top
+    for (uint64_t v = v_begin; v < v_end;) {
+      for (int q = top; q >= 1; --q) {
+        if (q == m - 1) {
+          U[q] = W[d[q] * ws];
+          G[q] = gc_fixed + (nth_code(ch[q], d[q]) & 1);
+        } else {
+          U[q] = add_packed(U[q + 1], step_w(q, d[q + 1], d[q]));
+          G[q] = G[q + 1] + (nth_code(ch[q], d[q]) & 1);
+        }
+      }
+      // digit 0 runs through its choices with the rest fixed
+      for (uint32_t d0 = d[0]; d0 < rad[0] && v < v_end; ++d0, ++v) {
+        int32_t p;
+        int gc;
+        const int c0 = nth_code(ch[0], d0);
+        if (m == 1) {
+          p = add_packed(W[d0 * ws], W[(off_suf + d0) * ws]);
+          gc = gc_fixed + (c0 & 1);
+        } else {
+          p = add_packed(add_packed(U[1], step_w(0, d[1], d0)), W[(off_suf + d0) * ws]);
+          gc = G[1] + (c0 & 1);
+        }
+        if (p != kNoEdge) fn(p, gc);
+      }
+      // carry
+      d[0] = 0;
+      top = 0;
+      for (int q = 1; q < m; ++q) {
+        top = q;
+        if (++d[q] < rad[q]) break;
+        d[q] = 0;
+      }
+    }
+  };
   float best_f = -INFINITY;
   double best = -INFINITY;
-  for (uint32_t v = lane; v < (uint32_t)count; v += 32) {
-    int gc;
-    const int32_t p = variant(v, &gc);
-    if (p == kNoEdge) continue;
+  sweep([&](int32_t p, int gc) {
     bool nz;
     const float t = tm_float(p, gc, &nz);
     if (nz) best = fmax(best, tm_of_tenths(unpack_dh(p), unpack_ds(p), gc, L, R));
     else if (t > best_f) best_f = t;
-  }
+  });
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) best_f = fmaxf(best_f, __shfl_xor_sync(0xffffffffu, best_f, o));
   if (best_f > -INFINITY) {
     const float floor_f = best_f - (1.f + 2e-4f * fabsf(best_f + 273.15f));
-    for (uint32_t v = lane; v < (uint32_t)count; v += 32) {
-      int gc;
-      const int32_t p = variant(v, &gc);
-      if (p == kNoEdge) continue;
+    sweep([&](int32_t p, int gc) {
       bool nz;
       const float t = tm_float(p, gc, &nz);
       if (!nz && t >= floor_f) best = fmax(best, tm_of_tenths(unpack_dh(p), unpack_ds(p), gc, L, R));
-    }
+    });
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
