@@ -241,7 +241,9 @@ ah_status layout_batch(ah_ctx* ctx, uint32_t n_rec, const uint64_t* lens, const 
 // record also writes the record's padding groups
 void add_items(std::vector<PackItem>& items, const ah_batch* b, uint32_t r, uint64_t from, uint64_t to,
                uint64_t src_off) {
-  const uint64_t piece = 1ull << 20;  // bases per item (multiple of 32)
+  // bases per item (a multiple of 32): a staged chunk of 256 Mi bases is then 1,024 blocks of the
+  // packing kernel, enough to fill the GPU while the next chunk crosses the link
+  const uint64_t piece = 1ull << 18;
   const uint64_t len = b->h_rec_len[r];
   const uint64_t rec_groups = record_groups(len);
   for (uint64_t a = from; a < to || (a == from && to == from && from == 0 && len == 0); a += piece) {
