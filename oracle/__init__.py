@@ -43,7 +43,7 @@ class _TmParams(ctypes.Structure):
     _fields_ = [("Na", ctypes.c_double), ("K", ctypes.c_double), ("Tris", ctypes.c_double),
                 ("Mg", ctypes.c_double), ("dNTPs", ctypes.c_double), ("dnac1", ctypes.c_double),
                 ("dnac2", ctypes.c_double), ("saltcorr", ctypes.c_int), ("selfcomp", ctypes.c_int),
-                ("variants", ctypes.c_int)]
+                ("variants", ctypes.c_int), ("nn_table", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -71,6 +71,9 @@ def _get():
             L.or_duplex_sums.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
             L.or_duplex_sums.restype = ctypes.c_int
+            L.or_duplex_sums_set.argtypes = [ctypes.c_int, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+            L.or_duplex_sums_set.restype = ctypes.c_int
             L.or_tm_duplex.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int,
                                        ctypes.POINTER(_TmParams), ctypes.POINTER(ctypes.c_int)]
             L.or_tm_duplex.restype = ctypes.c_double
@@ -86,6 +89,9 @@ def _get():
             L.or_nn_entry.argtypes = [ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]
             L.or_nn_entry.restype = ctypes.c_int
+            L.or_nn_entry_set.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
+            L.or_nn_entry_set.restype = ctypes.c_int
             L.or_free_mg.argtypes = [ctypes.c_double, ctypes.c_double]
             L.or_free_mg.restype = ctypes.c_double
             _lib = L
@@ -95,7 +101,7 @@ def _get():
 def _params(tm) -> _TmParams:
     return _TmParams(float(tm.Na), float(tm.K), float(tm.Tris), float(tm.Mg), float(tm.dNTPs), float(tm.dnac1),
                      float(tm.dnac2), int(tm.saltcorr), int(getattr(tm, "selfcomp", 0)),
-                     int(getattr(tm, "variants", 0)))
+                     int(getattr(tm, "variants", 0)), int(getattr(tm, "nn_table", 0)))
 
 
 def _strs(xs: Sequence[str]):
@@ -147,20 +153,26 @@ def pair(wl, hits: np.ndarray, orient_mask: Optional[int] = None) -> np.ndarray:
 
 
 # ------------------------------------------------------------------------------------------ Tm
-def duplex_sums(seq: str, cseq: str) -> Optional[Tuple[float, float]]:
+def duplex_sums(seq: str, cseq: str, nn_table: int = 0) -> Optional[Tuple[float, float]]:
     """(dH kcal/mol, dS cal/(K mol)) before salt and concentration terms, or None if undefined."""
     dh, ds = ctypes.c_double(), ctypes.c_double()
-    ok = _get().or_duplex_sums(seq.encode(), cseq.encode(), len(seq), ctypes.byref(dh), ctypes.byref(ds))
+    ok = _get().or_duplex_sums_set(nn_table, seq.encode(), cseq.encode(), len(seq), ctypes.byref(dh),
+                                   ctypes.byref(ds))
     return (dh.value, ds.value) if ok else None
 
 
 NN_WC, NN_INTERNAL, NN_TERMINAL, NN_SCALAR = range(4)
 
 
-def nn_entry(table: int, key: str) -> Optional[Tuple[float, float]]:
-    """One stored parameter (dH, dS) as written in the oracle's tables, or None (for pins only)."""
+# nearest-neighbour sets, Biopython's numbering (6 and 7, RNA_NN2 and RNA_NN3, are not built)
+NN_SETS = {0: "DNA_NN3", 1: "DNA_NN1", 2: "DNA_NN2", 3: "DNA_NN3", 4: "DNA_NN4", 5: "RNA_NN1", 8: "R_DNA_NN1"}
+
+
+def nn_entry(table: int, key: str, nn_table: int = 0) -> Optional[Tuple[float, float]]:
+    """One stored parameter (dH, dS) as written in the oracle's tables, or None (for pins only);
+    table NN_WC and NN_SCALAR read set nn_table."""
     dh, ds = ctypes.c_double(), ctypes.c_double()
-    ok = _get().or_nn_entry(table, key.encode(), ctypes.byref(dh), ctypes.byref(ds))
+    ok = _get().or_nn_entry_set(nn_table, table, key.encode(), ctypes.byref(dh), ctypes.byref(ds))
     return (dh.value, ds.value) if ok else None
 
 

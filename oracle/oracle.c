@@ -364,20 +364,75 @@ typedef struct {
 } nn_param;
 
 /* Watson-Crick stacks: Allawi & SantaLucia (1997) Biochemistry 36:10581; identical to the
- * unified set of SantaLucia (1998) PNAS 95:1460. */
+ * unified set of SantaLucia (1998) PNAS 95:1460.  The default set (nn_table 0 or 3). */
 static const nn_param WC_STACK[] = {
     {"AA/TT", -7.9, -22.2}, {"AT/TA", -7.2, -20.4}, {"TA/AT", -7.2, -21.3}, {"CA/GT", -8.5, -22.7},
     {"GT/CA", -8.4, -22.4}, {"CT/GA", -7.8, -21.0}, {"GA/CT", -8.2, -22.2}, {"CG/GC", -10.6, -27.2},
     {"GC/CG", -9.8, -24.4}, {"GG/CC", -8.0, -19.9},
 };
-/* initiation terms of the same set */
-static const double INIT_DH = 0.0, INIT_DS = 0.0;
-static const double INIT_AT_DH = 2.3, INIT_AT_DS = 4.1;    /* per terminal A.T pair */
-static const double INIT_GC_DH = 0.1, INIT_GC_DS = -2.8;   /* per terminal G.C pair */
-static const double INIT_ONEGC_DH = 0.0, INIT_ONEGC_DS = 0.0;
-static const double INIT_ALLAT_DH = 0.0, INIT_ALLAT_DS = 0.0;
-static const double INIT_5TA_DH = 0.0, INIT_5TA_DS = 0.0;
-static const double SYM_DH = 0.0, SYM_DS = -1.4;
+/* Breslauer et al. (1986) PNAS 83:3746 (nn_table 1). */
+static const nn_param WC_BRESLAUER86[] = {
+    {"AA/TT", -9.1, -24.0}, {"AT/TA", -8.6, -23.9}, {"TA/AT", -6.0, -16.9}, {"CA/GT", -5.8, -12.9},
+    {"GT/CA", -6.5, -17.3}, {"CT/GA", -7.8, -20.8}, {"GA/CT", -5.6, -13.5}, {"CG/GC", -11.9, -27.8},
+    {"GC/CG", -11.1, -26.7}, {"GG/CC", -11.0, -26.6},
+};
+/* Sugimoto et al. (1996) Nucleic Acids Res 24:4501 (nn_table 2). */
+static const nn_param WC_SUGIMOTO96[] = {
+    {"AA/TT", -8.0, -21.9}, {"AT/TA", -5.6, -15.2}, {"TA/AT", -6.6, -18.4}, {"CA/GT", -8.2, -21.0},
+    {"GT/CA", -9.4, -25.5}, {"CT/GA", -6.6, -16.4}, {"GA/CT", -8.8, -23.5}, {"CG/GC", -11.8, -29.0},
+    {"GC/CG", -10.5, -26.4}, {"GG/CC", -10.9, -28.4},
+};
+/* SantaLucia & Hicks (2004) Annu Rev Biophys Biomol Struct 33:415 (nn_table 4). */
+static const nn_param WC_SANTALUCIA04[] = {
+    {"AA/TT", -7.6, -21.3}, {"AT/TA", -7.2, -20.4}, {"TA/AT", -7.2, -21.3}, {"CA/GT", -8.5, -22.7},
+    {"GT/CA", -8.4, -22.4}, {"CT/GA", -7.8, -21.0}, {"GA/CT", -8.2, -22.2}, {"CG/GC", -10.6, -27.2},
+    {"GC/CG", -9.8, -24.4}, {"GG/CC", -8.0, -19.9},
+};
+/* RNA, Freier et al. (1986) PNAS 83:9373 (nn_table 5); U written as T. */
+static const nn_param WC_FREIER86[] = {
+    {"AA/TT", -6.6, -18.4}, {"AT/TA", -5.7, -15.5}, {"TA/AT", -8.1, -22.6}, {"CA/GT", -10.5, -27.8},
+    {"GT/CA", -10.2, -26.2}, {"CT/GA", -7.6, -19.2}, {"GA/CT", -13.3, -35.5}, {"CG/GC", -8.0, -19.4},
+    {"GC/CG", -14.2, -34.9}, {"GG/CC", -12.2, -29.7},
+};
+/* RNA/DNA hybrids, Sugimoto et al. (1995) Biochemistry 34:11211 (nn_table 8): the written strand
+ * is the RNA, so all 16 steps are listed as written (U written as T). */
+static const nn_param WC_SUGIMOTO95[] = {
+    {"AA/TT", -7.8, -21.9}, {"AC/TG", -5.9, -12.3}, {"AG/TC", -9.1, -23.5}, {"AT/TA", -8.3, -23.9},
+    {"CA/GT", -9.0, -26.1}, {"CC/GG", -9.3, -23.2}, {"CG/GC", -16.3, -47.1}, {"CT/GA", -7.0, -19.7},
+    {"GA/CT", -5.5, -13.5}, {"GC/CG", -8.0, -17.1}, {"GG/CC", -12.8, -31.9}, {"GT/CA", -7.8, -21.6},
+    {"TA/AT", -7.8, -23.2}, {"TC/AG", -8.6, -22.9}, {"TG/AC", -10.4, -28.4}, {"TT/AA", -11.5, -36.4},
+};
+
+#define NELEM(a) ((int)(sizeof(a) / sizeof((a)[0])))
+
+/* One nearest-neighbour set: its stacks and the scalar terms of Biopython's Tm_NN tables, as
+ * dH/dS pairs: "init" (every duplex), "init_A/T" and "init_G/C" (per terminal pair of that kind on
+ * the written strand), "init_oneG/C" / "init_allA/T" (the duplex holds some / no G or C),
+ * "init_5T/A" (each of a 5' T and a 3' A of the written strand), "sym" (self-complementary). */
+typedef struct {
+  const nn_param* wc;
+  int n_wc;
+  double init[2], at[2], gc[2], onegc[2], allat[2], t5a[2], sym[2];
+} nn_set;
+
+static const nn_set NN_SETS[] = {
+    /* 0 and 3: Allawi & SantaLucia 1997 */
+    {WC_STACK, NELEM(WC_STACK), {0, 0}, {2.3, 4.1}, {0.1, -2.8}, {0, 0}, {0, 0}, {0, 0}, {0, -1.4}},
+    {WC_BRESLAUER86, NELEM(WC_BRESLAUER86), {0, 0}, {0, 0}, {0, 0}, {0, -16.8}, {0, -20.1}, {0, 0}, {0, -1.3}},
+    {WC_SUGIMOTO96, NELEM(WC_SUGIMOTO96), {0.6, -9.0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, -1.4}},
+    {WC_STACK, NELEM(WC_STACK), {0, 0}, {2.3, 4.1}, {0.1, -2.8}, {0, 0}, {0, 0}, {0, 0}, {0, -1.4}},
+    {WC_SANTALUCIA04, NELEM(WC_SANTALUCIA04), {0.2, -5.7}, {2.2, 6.9}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, -1.4}},
+    {WC_FREIER86, NELEM(WC_FREIER86), {0, -10.8}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, -1.4}},
+    {NULL, 0, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}}, /* 6: not built */
+    {NULL, 0, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}}, /* 7: not built */
+    {WC_SUGIMOTO95, NELEM(WC_SUGIMOTO95), {1.9, -3.9}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},
+};
+
+/* the set of nn_table t, NULL when there is none */
+static const nn_set* nn_set_of(int t) {
+  if (t < 0 || t >= NELEM(NN_SETS) || !NN_SETS[t].wc) return NULL;
+  return &NN_SETS[t];
+}
 
 /* Internal single mismatches next to a Watson-Crick pair, plus the tandem G.T steps.
  * G.T: Allawi & SantaLucia (1997) Biochemistry 36:10581.  G.A: Allawi & SantaLucia (1998)
@@ -422,7 +477,6 @@ static const nn_param TERMINAL_MM[] = {
     {"GG/CT", -5.7, -15.9}, {"GT/CG", -5.9, -16.1}, {"TG/AT", -3.9, -10.5}, {"TT/AG", -3.6, -9.8},
 };
 
-#define NELEM(a) ((int)(sizeof(a) / sizeof((a)[0])))
 
 static int find_param(const nn_param* t, int n, const char* key, double* dh, double* ds) {
   for (int i = 0; i < n; ++i)
@@ -435,31 +489,35 @@ static int find_param(const nn_param* t, int n, const char* key, double* dh, dou
 }
 
 /* Read access to one parameter entry, exactly as stored (no lookup rules, no arithmetic), so that
- * tests can hold the tables against published values: table 0 the Watson-Crick stacks, 1 the
- * internal mismatches, 2 the terminal mismatches, 3 the scalar terms ("init", "init_A/T",
- * "init_G/C", "init_oneG/C", "init_allA/T", "init_5T/A", "sym").  Returns 1 if the key exists. */
-int or_nn_entry(int table, const char* key, double* dh, double* ds) {
+ * tests can hold the tables against published values: table 0 the Watson-Crick stacks of set
+ * `set` (nn_table numbering), 1 the internal mismatches, 2 the terminal mismatches, 3 the set's
+ * scalar terms ("init", "init_A/T", "init_G/C", "init_oneG/C", "init_allA/T", "init_5T/A",
+ * "sym").  Returns 1 if the key exists. */
+int or_nn_entry_set(int set, int table, const char* key, double* dh, double* ds) {
   *dh = *ds = 0.0;
+  const nn_set* S = nn_set_of(set);
+  if (!S) return 0;
   switch (table) {
-    case 0: return find_param(WC_STACK, NELEM(WC_STACK), key, dh, ds);
+    case 0: return find_param(S->wc, S->n_wc, key, dh, ds);
     case 1: return find_param(INTERNAL_MM, NELEM(INTERNAL_MM), key, dh, ds);
     case 2: return find_param(TERMINAL_MM, NELEM(TERMINAL_MM), key, dh, ds);
     default: break;
   }
-  static const struct { const char* key; const double *dh, *ds; } scalars[] = {
-      {"init", &INIT_DH, &INIT_DS},           {"init_A/T", &INIT_AT_DH, &INIT_AT_DS},
-      {"init_G/C", &INIT_GC_DH, &INIT_GC_DS}, {"init_oneG/C", &INIT_ONEGC_DH, &INIT_ONEGC_DS},
-      {"init_allA/T", &INIT_ALLAT_DH, &INIT_ALLAT_DS}, {"init_5T/A", &INIT_5TA_DH, &INIT_5TA_DS},
-      {"sym", &SYM_DH, &SYM_DS},
+  const struct { const char* key; const double* v; } scalars[] = {
+      {"init", S->init},   {"init_A/T", S->at},       {"init_G/C", S->gc}, {"init_oneG/C", S->onegc},
+      {"init_allA/T", S->allat}, {"init_5T/A", S->t5a}, {"sym", S->sym},
   };
   for (int i = 0; i < NELEM(scalars); ++i)
     if (strcmp(scalars[i].key, key) == 0) {
-      *dh = *scalars[i].dh;
-      *ds = *scalars[i].ds;
+      *dh = scalars[i].v[0];
+      *ds = scalars[i].v[1];
       return 1;
     }
   return 0;
 }
+
+/* the same for the default set */
+int or_nn_entry(int table, const char* key, double* dh, double* ds) { return or_nn_entry_set(0, table, key, dh, ds); }
 
 typedef struct {
   double Na, K, Tris, Mg, dNTPs; /* mM */
@@ -467,6 +525,8 @@ typedef struct {
   int saltcorr;                  /* 0 none, 1..7 */
   int selfcomp;
   int variants;                  /* 0: every concrete variant (R14); 1: only those matching the site */
+  int nn_table;                  /* nearest-neighbour set, Biopython's numbering: 0 or 3 DNA_NN3 (the
+                                    default), 1 DNA_NN1, 2 DNA_NN2, 4 DNA_NN4, 5 RNA_NN1, 8 R_DNA_NN1 */
 } or_tm_params;
 
 static double gc_fraction(const char* s, int L) {
@@ -558,8 +618,10 @@ static double salt_correction(const or_tm_params* p, const char* seq, int L, int
  *      Watson-Crick table, read in either direction.
  * Salt and strand concentration are applied by or_tm_duplex.
  */
-int or_duplex_sums(const char* seq, const char* cseq, int L, double* dh_out, double* ds_out) {
+int or_duplex_sums_set(int set, const char* seq, const char* cseq, int L, double* dh_out, double* ds_out) {
   double dh = 0.0, ds = 0.0;
+  const nn_set* S = nn_set_of(set);
+  if (!S) return 0;
   int lo = 0, hi = L; /* active pairs [lo, hi) */
   char key[6];
   if (L < 2) return 0;
@@ -580,31 +642,31 @@ int or_duplex_sums(const char* seq, const char* cseq, int L, double* dh_out, dou
     if (find_param(TERMINAL_MM, NELEM(TERMINAL_MM), key, &dh, &ds)) hi -= 1;
   }
   /* 2. initiation */
-  dh += INIT_DH;
-  ds += INIT_DS;
+  dh += S->init[0];
+  ds += S->init[1];
   if (gc_fraction(seq, L) == 0.0) {
-    dh += INIT_ALLAT_DH;
-    ds += INIT_ALLAT_DS;
+    dh += S->allat[0];
+    ds += S->allat[1];
   } else {
-    dh += INIT_ONEGC_DH;
-    ds += INIT_ONEGC_DS;
+    dh += S->onegc[0];
+    ds += S->onegc[1];
   }
   if (seq[0] == 'T') {
-    dh += INIT_5TA_DH;
-    ds += INIT_5TA_DS;
+    dh += S->t5a[0];
+    ds += S->t5a[1];
   }
   if (seq[L - 1] == 'A') {
-    dh += INIT_5TA_DH;
-    ds += INIT_5TA_DS;
+    dh += S->t5a[0];
+    ds += S->t5a[1];
   }
   for (int e = 0; e < 2; ++e) {
     char c = e == 0 ? seq[0] : seq[L - 1];
     if (c == 'A' || c == 'T') {
-      dh += INIT_AT_DH;
-      ds += INIT_AT_DS;
+      dh += S->at[0];
+      ds += S->at[1];
     } else if (c == 'G' || c == 'C') {
-      dh += INIT_GC_DH;
-      ds += INIT_GC_DS;
+      dh += S->gc[0];
+      ds += S->gc[1];
     }
   }
   /* 3. stacks */
@@ -620,8 +682,8 @@ int or_duplex_sums(const char* seq, const char* cseq, int L, double* dh_out, dou
     rev[5] = 0;
     if (find_param(INTERNAL_MM, NELEM(INTERNAL_MM), key, &dh, &ds)) continue;
     if (find_param(INTERNAL_MM, NELEM(INTERNAL_MM), rev, &dh, &ds)) continue;
-    if (find_param(WC_STACK, NELEM(WC_STACK), key, &dh, &ds)) continue;
-    if (find_param(WC_STACK, NELEM(WC_STACK), rev, &dh, &ds)) continue;
+    if (find_param(S->wc, S->n_wc, key, &dh, &ds)) continue;
+    if (find_param(S->wc, S->n_wc, rev, &dh, &ds)) continue;
     return 0;
   }
   *dh_out = dh;
@@ -629,18 +691,24 @@ int or_duplex_sums(const char* seq, const char* cseq, int L, double* dh_out, dou
   return 1;
 }
 
+/* the same with the default set */
+int or_duplex_sums(const char* seq, const char* cseq, int L, double* dh_out, double* ds_out) {
+  return or_duplex_sums_set(0, seq, cseq, L, dh_out, ds_out);
+}
+
 /* Melting temperature (degrees C): salt correction, then Tm = 1000 dH / (dS + R ln(C)) - 273.15
  * with R = 1.987 cal/(K mol) and C = (c1 - c2/2) nM (c1 alone, plus the symmetry term, for a
  * self-complementary duplex).  *defined = 0 when the sums or the salt method are undefined. */
 double or_tm_duplex(const char* seq, const char* cseq, int L, const or_tm_params* p, int* defined) {
   double dh = 0.0, ds = 0.0;
-  *defined = or_duplex_sums(seq, cseq, L, &dh, &ds);
+  *defined = or_duplex_sums_set(p->nn_table, seq, cseq, L, &dh, &ds);
   if (!*defined) return NAN;
   double k = (p->dnac1 - p->dnac2 / 2.0) * 1e-9;
   if (p->selfcomp) {
+    const nn_set* S = nn_set_of(p->nn_table);
     k = p->dnac1 * 1e-9;
-    dh += SYM_DH;
-    ds += SYM_DS;
+    dh += S->sym[0];
+    ds += S->sym[1];
   }
   int ok = 1;
   double corr = salt_correction(p, seq, L, &ok);

@@ -160,6 +160,7 @@ class TmParams:
     min_tm: Optional[float] = None   # None: annotate only, no filtering
     variants: int = 0     # degenerate Tm over 0: every concrete variant, 1: those matching the site
     selfcomp: int = 0     # 1: the duplexes are self-complementary (symmetry term, C = dnac1)
+    nn_table: int = 0     # nearest-neighbour set (Biopython's numbering; 0 the default DNA_NN3)
 
 
 @dataclass

@@ -8,7 +8,9 @@ These pins tie the oracle to published numbers, not to a second transcription of
 * the Tm that Biopython's documentation prints for a 28-mer under the defaults fixes those terms,
   salt method 5 and the strand-concentration term together;
 * the salt corrections that Biopython's documentation prints fix methods 1 and 2, the Tris/2 term
-  and the Na+-equivalent of Mg2+.
+  and the Na+-equivalent of Mg2+;
+* the free energies printed beside the other Watson-Crick sets (Breslauer 1986, Sugimoto 1996,
+  SantaLucia & Hicks 2004, Freier 1986, Sugimoto 1995) fix each set's stacks and scalar terms.
 """
 import os
 import re
@@ -97,3 +99,61 @@ def test_published_salt_correction(method, na, tris, mg, corr, seq):
     with_corr = oracle.tm_duplex(seq, cseq, synth.TmParams(Na=na, Tris=tris, Mg=mg, saltcorr=method))
     without = oracle.tm_duplex(seq, cseq, synth.TmParams(Na=na, Tris=tris, Mg=mg, saltcorr=0))
     assert f"{with_corr - without:.2f}" == f"{corr:.2f}", with_corr - without
+
+
+# ---------------------------------------------------------------------------------------- other sets
+_SET_STACKS = {1: 10, 2: 10, 4: 10, 5: 10, 8: 16}   # stacks each set stores (8: RNA/DNA, not symmetric)
+
+
+def test_sets_complete():
+    rows = _table("sets")
+    for st, n in _SET_STACKS.items():
+        steps = {r[1] for r in rows if int(r[0]) == st and "/" in r[1] and not r[1].startswith("init")}
+        assert len(steps) == n, (st, len(steps))
+        for s in steps:
+            top, bottom = s.split("/")
+            assert "".join(COMP[c] for c in top) == bottom
+            assert oracle.nn_entry(oracle.NN_WC, s, st) is not None, (st, s)
+
+
+@pytest.mark.parametrize("row", _table("sets"), ids=lambda r: f"set{r[0]}-{r[1]}")
+def test_set_free_energy(row):
+    st, term, T, dg, tol = int(row[0]), row[1], float(row[2]), float(row[3]), float(row[4])
+    wc = "/" in term and not term.startswith("init")
+    got = oracle.nn_entry(oracle.NN_WC if wc else oracle.NN_SCALAR, term, st)
+    assert got is not None, (st, term)
+    val = got[0] - T * got[1] / 1000.0
+    assert abs(val - dg) <= tol, (st, term, got, val, dg)
+
+
+@pytest.mark.parametrize("st", sorted(_SET_STACKS))
+def test_set_sums_use_the_pinned_entries(st):
+    """A fully paired duplex's sums under set `st` are its pinned stacks plus the set's pinned
+    initiation terms: every duplex, per terminal pair, G/C present or absent, 5' T and 3' A.  The
+    shared mismatch tables play no part, so this reaches every entry of the set's stack table."""
+    stacks = {r[1]: oracle.nn_entry(oracle.NN_WC, r[1], st) for r in _table("sets")
+              if int(r[0]) == st and "/" in r[1] and not r[1].startswith("init")}
+    sc = {k: oracle.nn_entry(oracle.NN_SCALAR, k, st)
+          for k in ("init", "init_A/T", "init_G/C", "init_oneG/C", "init_allA/T", "init_5T/A")}
+    st_rng = synth.Stream(synth.make_key(st, 77, 2))
+    for _ in range(200):
+        L = st_rng.randint(2, 30)
+        seq = "".join(st_rng.choice(st_rng.choice(["ACGT", "AT"])) for _ in range(L))
+        cseq = "".join(COMP[c] for c in seq)
+        terms = [sc["init"], sc["init_oneG/C"] if any(c in "GC" for c in seq) else sc["init_allA/T"]]
+        terms += [sc["init_G/C"] if c in "GC" else sc["init_A/T"] for c in (seq[0], seq[-1])]
+        terms += [sc["init_5T/A"]] * ((seq[0] == "T") + (seq[-1] == "A"))
+        for i in range(L - 1):
+            fwd = seq[i:i + 2] + "/" + cseq[i:i + 2]
+            rev = cseq[i + 1] + cseq[i] + "/" + seq[i + 1] + seq[i]
+            terms.append(stacks.get(fwd) or stacks.get(rev))
+        dh, ds = sum(t[0] for t in terms), sum(t[1] for t in terms)
+        got = oracle.duplex_sums(seq, cseq, st)
+        assert abs(got[0] - dh) < 1e-9 and abs(got[1] - ds) < 1e-9, (st, seq)
+
+
+def test_unbuilt_sets_are_refused():
+    """RNA_NN2 and RNA_NN3 (6, 7) are not built: no entries, no sums."""
+    for st in (6, 7, 9, -1):
+        assert oracle.nn_entry(oracle.NN_WC, "AA/TT", st) is None
+        assert oracle.duplex_sums("ACGT", "TGCA", st) is None
