@@ -393,6 +393,14 @@ typedef struct {
   int32_t variants;              /* degenerate primers: 0 every concrete variant (default);
                                     1 only variants matching the site within k and the clamp */
   int32_t selfcomp;              /* 1: self-complementary duplexes (symmetry term, C = dnac1) */
+  int32_t nn_table;              /* Watson-Crick nearest-neighbour set, Biopython's Tm_NN numbering:
+                                    0 or 3 DNA_NN3, Allawi & SantaLucia 1997 (the default);
+                                    1 DNA_NN1, Breslauer et al. 1986; 2 DNA_NN2, Sugimoto et al.
+                                    1996; 4 DNA_NN4, SantaLucia & Hicks 2004; 5 RNA_NN1, Freier et
+                                    al. 1986; 8 R_DNA_NN1, Sugimoto et al. 1995 (the primer strand
+                                    taken as the RNA).  6 and 7 (RNA_NN2, RNA_NN3) are not built:
+                                    AH_EINVAL.  The mismatch tables are the default ones for every
+                                    set, as in Tm_NN. */
 } ah_tm_params;
 
 /* Fill tm and flags of every amplicon (Section "Implementations": Biopython's Tm_NN in C; Section

@@ -37,7 +37,7 @@ class ah_tm_params(ctypes.Structure):
     _fields_ = [("Na", ctypes.c_double), ("K", ctypes.c_double), ("Tris", ctypes.c_double), ("Mg", ctypes.c_double),
                 ("dNTPs", ctypes.c_double), ("dnac1", ctypes.c_double), ("dnac2", ctypes.c_double),
                 ("saltcorr", ctypes.c_int32), ("filter", ctypes.c_int32), ("min_tm", ctypes.c_double),
-                ("variants", ctypes.c_int32), ("selfcomp", ctypes.c_int32)]
+                ("variants", ctypes.c_int32), ("selfcomp", ctypes.c_int32), ("nn_table", ctypes.c_int32)]
 
 
 class ah_plan_params(ctypes.Structure):
@@ -617,14 +617,15 @@ def ah_pair_amplicons_noalloc(stream: int, d_hits: int, n_hits: int, d_pair_offs
 
 # ------------------------------------------------------------------------------------------ Tm
 def tm_params(Na=50.0, K=0.0, Tris=0.0, Mg=0.0, dNTPs=0.0, dnac1=25.0, dnac2=25.0, saltcorr=5, min_tm=None,
-              variants=0, selfcomp=0, filter=None) -> ah_tm_params:
+              variants=0, selfcomp=0, filter=None, nn_table=0) -> ah_tm_params:
     """min_tm None: no threshold (flags bit0 then marks a defined Tm).  filter None: filter iff a
     threshold is given; False with a threshold only annotates the decision in the flags."""
     flt = (min_tm is not None) if filter is None else bool(filter)
     if flt and min_tm is None:
         raise ValueError("filtering needs min_tm")
     return ah_tm_params(Na, K, Tris, Mg, dNTPs, dnac1, dnac2, saltcorr, int(flt),
-                        float("-inf") if min_tm is None else float(min_tm), int(variants), int(selfcomp))
+                        float("-inf") if min_tm is None else float(min_tm), int(variants), int(selfcomp),
+                        int(nn_table))
 
 
 def ah_tm_filter(ctx, batch, primers, hits, amps, params: ah_tm_params) -> None:

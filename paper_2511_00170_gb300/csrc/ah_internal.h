@@ -293,7 +293,7 @@ void launch_pair_walk(cudaStream_t s, bool emit, const ah_hit* hits, uint64_t ca
                       const uint64_t* pair_off, const uint8_t* plen, uint32_t min_len, uint32_t max_len, uint32_t mask,
                       uint32_t* counts, const uint64_t* out_off, ah_amplicon* out, uint64_t out_cap,
                       uint32_t* overflow);
-constexpr size_t kTmRunBytes = 128;  // room for the Tm run constants a plan keeps
+constexpr size_t kTmRunBytes = 256;  // room for the Tm run constants a plan keeps
 ah_status tm_prepare(ah_ctx* ctx, const ah_tm_params* params, void* run_out, size_t run_size);
 // A degenerate-site Tm kernel generated for one primer set (ah_tm_jit.cpp); fn null: the built-in one.
 struct TmKernel {
@@ -309,14 +309,14 @@ constexpr int kTmJitMaxAdjacent = 96;
 int tm_chain_adjacent(const std::vector<std::string>& primers);
 // The kernel for p by the context's choice (ctx->tm_kernel): generated (compiled now if need be,
 // unless !wait and mode 2), or fn = null for the built-in kernel.
-ah_status tm_kernel_for(ah_ctx* ctx, const ah_primers* p, bool wait, TmKernel* out);
+// slot: the nearest-neighbour set of the run (tm_run_slot), whose tables the kernel reads.
+ah_status tm_kernel_for(ah_ctx* ctx, const ah_primers* p, bool wait, int slot, TmKernel* out);
+int tm_run_slot(const void* run);
 std::string tm_chain_source(const std::vector<std::string>& primers, int* weight_words);
-// packed initiation terms (tenths) of end base v at position j of a length-L variant (ah_tm.cu)
-int32_t tm_end_packed(int j, int L, int v);
 size_t tm_run_bytes();
-// the parameter tables laid out as the generated kernels copy them into shared memory, on ctx's
-// device (built once per device)
-ah_status tm_tab_image(ah_ctx* ctx, const int32_t** out);
+// the parameter tables of nearest-neighbour set `slot` laid out as the generated kernels copy them
+// into shared memory, on ctx's device (built once per device and set)
+ah_status tm_tab_image(ah_ctx* ctx, int slot, const int32_t** out);
 void launch_tm(cudaStream_t s, const void* run, const ah_hit* hits, uint64_t hit_cap, const uint64_t* d_nhits,
                const ah_primers* p, uint32_t* status, const uint2* planes, const uint64_t* rec_group, double* hit_tm,
                ah_amplicon* amps, uint64_t amp_cap, const uint64_t* d_namps, int filter, double min_tm, uint32_t* keep,

@@ -293,7 +293,7 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
   pl->cfg = ctx->scan_cfg;
   pl->cfg.pairs_per_kernel = 0;  // a plan captures one scan kernel over every pair
   ah_status st = tm_prepare(ctx, &prm->tm, pl->tm_run, sizeof pl->tm_run);
-  if (!st && !prm->tm.variants) st = tm_kernel_for(ctx, p, true, &pl->tm_k);
+  if (!st && !prm->tm.variants) st = tm_kernel_for(ctx, p, true, tm_run_slot(pl->tm_run), &pl->tm_k);
   for (int i = 0; i < 2 && !st; ++i)
     if (cudaEventCreate(&pl->scan_ev[i]) != cudaSuccess) st = fail(ctx, AH_ECUDA, "ah_plan_create: event creation failed");
   const auto t0 = std::chrono::steady_clock::now();

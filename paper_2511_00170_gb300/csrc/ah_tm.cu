@@ -80,13 +80,76 @@ const Step kTerminal[] = {
     {'G', 'T', 'C', 'G', -5.9, -16.1}, {'T', 'G', 'A', 'T', -3.9, -10.5}, {'T', 'T', 'A', 'G', -3.6, -9.8},
 };
 
-// Initiation terms of the same parameter set.
-constexpr double kInitH = 0.0, kInitS = 0.0;
-constexpr double kTermATH = 2.3, kTermATS = 4.1;
-constexpr double kTermGCH = 0.1, kTermGCS = -2.8;
-constexpr double kOneGCH = 0.0, kOneGCS = 0.0, kAllATH = 0.0, kAllATS = 0.0, k5TAH = 0.0, k5TAS = 0.0;
-// symmetry correction of a self-complementary duplex
-constexpr double kSymH = 0.0, kSymS = -1.4;
+// The other Watson-Crick sets of Tm_NN (Biopython's DNA_NN1, DNA_NN2, DNA_NN4, RNA_NN1, R_DNA_NN1).
+// Breslauer et al. 1986, PNAS 83:3746.
+const Step kBreslauer86[] = {
+    {'A', 'A', 'T', 'T', -9.1, -24.0}, {'A', 'T', 'T', 'A', -8.6, -23.9}, {'T', 'A', 'A', 'T', -6.0, -16.9},
+    {'C', 'A', 'G', 'T', -5.8, -12.9}, {'G', 'T', 'C', 'A', -6.5, -17.3}, {'C', 'T', 'G', 'A', -7.8, -20.8},
+    {'G', 'A', 'C', 'T', -5.6, -13.5}, {'C', 'G', 'G', 'C', -11.9, -27.8}, {'G', 'C', 'C', 'G', -11.1, -26.7},
+    {'G', 'G', 'C', 'C', -11.0, -26.6},
+};
+// Sugimoto et al. 1996, Nucleic Acids Res 24:4501.
+const Step kSugimoto96[] = {
+    {'A', 'A', 'T', 'T', -8.0, -21.9}, {'A', 'T', 'T', 'A', -5.6, -15.2}, {'T', 'A', 'A', 'T', -6.6, -18.4},
+    {'C', 'A', 'G', 'T', -8.2, -21.0}, {'G', 'T', 'C', 'A', -9.4, -25.5}, {'C', 'T', 'G', 'A', -6.6, -16.4},
+    {'G', 'A', 'C', 'T', -8.8, -23.5}, {'C', 'G', 'G', 'C', -11.8, -29.0}, {'G', 'C', 'C', 'G', -10.5, -26.4},
+    {'G', 'G', 'C', 'C', -10.9, -28.4},
+};
+// SantaLucia & Hicks 2004, Annu Rev Biophys Biomol Struct 33:415.
+const Step kSantaLucia04[] = {
+    {'A', 'A', 'T', 'T', -7.6, -21.3}, {'A', 'T', 'T', 'A', -7.2, -20.4}, {'T', 'A', 'A', 'T', -7.2, -21.3},
+    {'C', 'A', 'G', 'T', -8.5, -22.7}, {'G', 'T', 'C', 'A', -8.4, -22.4}, {'C', 'T', 'G', 'A', -7.8, -21.0},
+    {'G', 'A', 'C', 'T', -8.2, -22.2}, {'C', 'G', 'G', 'C', -10.6, -27.2}, {'G', 'C', 'C', 'G', -9.8, -24.4},
+    {'G', 'G', 'C', 'C', -8.0, -19.9},
+};
+// RNA, Freier et al. 1986, PNAS 83:9373 (U as T).
+const Step kFreier86[] = {
+    {'A', 'A', 'T', 'T', -6.6, -18.4}, {'A', 'T', 'T', 'A', -5.7, -15.5}, {'T', 'A', 'A', 'T', -8.1, -22.6},
+    {'C', 'A', 'G', 'T', -10.5, -27.8}, {'G', 'T', 'C', 'A', -10.2, -26.2}, {'C', 'T', 'G', 'A', -7.6, -19.2},
+    {'G', 'A', 'C', 'T', -13.3, -35.5}, {'C', 'G', 'G', 'C', -8.0, -19.4}, {'G', 'C', 'C', 'G', -14.2, -34.9},
+    {'G', 'G', 'C', 'C', -12.2, -29.7},
+};
+// RNA/DNA hybrids, Sugimoto et al. 1995, Biochemistry 34:11211: the written strand is the RNA (U
+// as T), every step as written.
+const Step kSugimoto95[] = {
+    {'A', 'A', 'T', 'T', -7.8, -21.9}, {'A', 'C', 'T', 'G', -5.9, -12.3}, {'A', 'G', 'T', 'C', -9.1, -23.5},
+    {'A', 'T', 'T', 'A', -8.3, -23.9}, {'C', 'A', 'G', 'T', -9.0, -26.1}, {'C', 'C', 'G', 'G', -9.3, -23.2},
+    {'C', 'G', 'G', 'C', -16.3, -47.1}, {'C', 'T', 'G', 'A', -7.0, -19.7}, {'G', 'A', 'C', 'T', -5.5, -13.5},
+    {'G', 'C', 'C', 'G', -8.0, -17.1}, {'G', 'G', 'C', 'C', -12.8, -31.9}, {'G', 'T', 'C', 'A', -7.8, -21.6},
+    {'T', 'A', 'A', 'T', -7.8, -23.2}, {'T', 'C', 'A', 'G', -8.6, -22.9}, {'T', 'G', 'A', 'C', -10.4, -28.4},
+    {'T', 'T', 'A', 'A', -11.5, -36.4},
+};
+
+// One nearest-neighbour set: its stacks and the scalar terms of Tm_NN's tables (dH kcal/mol, dS
+// cal/(K mol)): every duplex (init), per terminal A.T and G.C pair of the written strand (at, gc),
+// a duplex with some / no G or C (onegc, allat), each of a 5' T and a 3' A (t5a), the symmetry
+// term of a self-complementary duplex (sym).  The internal and terminal mismatch tables are shared.
+struct NNSet {
+  const Step* stacks;
+  int n_stacks;
+  double init[2], at[2], gc[2], onegc[2], allat[2], t5a[2], sym[2];
+};
+// slots of the sets on the device; nn_table (Biopython's numbering) -> slot, -1: not built
+constexpr int kNNSlots = 6;
+const NNSet kNNSets[kNNSlots] = {
+    {kStacks, 10, {0, 0}, {2.3, 4.1}, {0.1, -2.8}, {0, 0}, {0, 0}, {0, 0}, {0, -1.4}},  // DNA_NN3
+    {kBreslauer86, 10, {0, 0}, {0, 0}, {0, 0}, {0, -16.8}, {0, -20.1}, {0, 0}, {0, -1.3}},  // DNA_NN1
+    {kSugimoto96, 10, {0.6, -9.0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, -1.4}},  // DNA_NN2
+    {kSantaLucia04, 10, {0.2, -5.7}, {2.2, 6.9}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, -1.4}},  // DNA_NN4
+    {kFreier86, 10, {0, -10.8}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, -1.4}},  // RNA_NN1
+    {kSugimoto95, 16, {1.9, -3.9}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}},  // R_DNA_NN1
+};
+int nn_slot(int nn_table) {
+  switch (nn_table) {
+    case 0: case 3: return 0;
+    case 1: return 1;
+    case 2: return 2;
+    case 4: return 3;
+    case 5: return 4;
+    case 8: return 5;
+    default: return -1;
+  }
+}
 
 // degenerate site Tm: largest mismatch budget, and the enumeration bounds
 constexpr int kMaxK = 15;
@@ -98,7 +161,7 @@ struct NNTables {
 };
 // global (not constant) memory: threads of a warp look up different steps, which the constant cache
 // would serialise
-__device__ NNTables c_nn;
+__device__ NNTables c_nn[kNNSlots];
 // The same values as integers in units of 0.1 (every published value has one decimal), for the
 // degenerate-site search: sums of them are exact in any arithmetic.  kNoParam marks a missing entry.
 constexpr int16_t kNoParam = INT16_MIN;
@@ -106,7 +169,7 @@ struct NNTablesI {
   int16_t step_h[256], step_s[256];
   int16_t term_h[256], term_s[256];
 };
-__device__ NNTablesI c_nni;
+__device__ NNTablesI c_nni[kNNSlots];
 
 int code_of(char c) {  // A=0, C=1, T=2, G=3
   switch (c) {
@@ -139,7 +202,7 @@ uint8_t iupac_set(char ch) {
   }
 }
 
-void build_tables(NNTables* t) {
+void build_tables(NNTables* t, const NNSet& set) {
   const double nan = std::nan("");
   for (int i = 0; i < 256; ++i) t->step_h[i] = t->step_s[i] = t->term_h[i] = t->term_s[i] = nan;
   // step lookup: internal-mismatch entry as written, then read from the other strand, then the
@@ -157,8 +220,8 @@ void build_tables(NNTables* t) {
   };
   put(kInternal, sizeof kInternal / sizeof kInternal[0], false);
   put(kInternal, sizeof kInternal / sizeof kInternal[0], true);
-  put(kStacks, sizeof kStacks / sizeof kStacks[0], false);
-  put(kStacks, sizeof kStacks / sizeof kStacks[0], true);
+  put(set.stacks, set.n_stacks, false);
+  put(set.stacks, set.n_stacks, true);
   for (const Step& s : kTerminal) {
     int k = idx4(code_of(s.a), code_of(s.b), code_of(s.x), code_of(s.y));
     t->term_h[k] = s.dh;
@@ -168,26 +231,28 @@ void build_tables(NNTables* t) {
 
 std::mutex g_tables_mu;
 bool g_tables_loaded[64] = {};
-NNTablesI g_host_i;                   // the integer tables as uploaded
-const int32_t* g_tab_image[64] = {};  // per device: TmTabs for the generated Tm kernels
+NNTablesI g_host_i[kNNSlots];                   // the integer tables as uploaded
+const int32_t* g_tab_image[64][kNNSlots] = {};  // per device and set: TmTabs for the generated kernels
 
 ah_status load_tables(ah_ctx* ctx) {
   std::lock_guard<std::mutex> lock(g_tables_mu);
   if (ctx->device < 64 && g_tables_loaded[ctx->device]) return AH_OK;
-  static NNTables host;
-  NNTablesI& host_i = g_host_i;
-  build_tables(&host);
+  static NNTables host[kNNSlots];
   auto tenths = [](double x) -> int16_t {
     if (std::isnan(x)) return kNoParam;
     const double t = std::round(x * 10.0);
     return (int16_t)t;
   };
-  for (int i = 0; i < 256; ++i) {
-    host_i.step_h[i] = tenths(host.step_h[i]), host_i.step_s[i] = tenths(host.step_s[i]);
-    host_i.term_h[i] = tenths(host.term_h[i]), host_i.term_s[i] = tenths(host.term_s[i]);
+  for (int k = 0; k < kNNSlots; ++k) {
+    build_tables(&host[k], kNNSets[k]);
+    NNTablesI& host_i = g_host_i[k];
+    for (int i = 0; i < 256; ++i) {
+      host_i.step_h[i] = tenths(host[k].step_h[i]), host_i.step_s[i] = tenths(host[k].step_s[i]);
+      host_i.term_h[i] = tenths(host[k].term_h[i]), host_i.term_s[i] = tenths(host[k].term_s[i]);
+    }
   }
-  AH_CUDA(ctx, cudaMemcpyToSymbolAsync(c_nn, &host, sizeof host, 0, cudaMemcpyHostToDevice, ctx->stream));
-  AH_CUDA(ctx, cudaMemcpyToSymbolAsync(c_nni, &host_i, sizeof host_i, 0, cudaMemcpyHostToDevice, ctx->stream));
+  AH_CUDA(ctx, cudaMemcpyToSymbolAsync(c_nn, host, sizeof host, 0, cudaMemcpyHostToDevice, ctx->stream));
+  AH_CUDA(ctx, cudaMemcpyToSymbolAsync(c_nni, g_host_i, sizeof g_host_i, 0, cudaMemcpyHostToDevice, ctx->stream));
   AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->device < 64) g_tables_loaded[ctx->device] = true;
   return AH_OK;
@@ -207,6 +272,10 @@ double free_magnesium(double mg, double dntps) {
 
 ah_status make_run(ah_ctx* ctx, const ah_tm_params* p, TmRun* r) {
   if (p->variants != 0 && p->variants != 1) return fail(ctx, AH_EINVAL, "Tm: variants must be 0 or 1");
+  const int slot = nn_slot(p->nn_table);
+  if (slot < 0)
+    return fail(ctx, AH_EINVAL, "Tm: nearest-neighbour table %d is not available (0-5 and 8; RNA_NN2 and RNA_NN3 "
+                "are not built)", p->nn_table);
   if (p->selfcomp != 0 && p->selfcomp != 1) return fail(ctx, AH_EINVAL, "Tm: selfcomp must be 0 or 1");
   double mon_mM = p->Na + p->K + p->Tris / 2.0;
   // Na+-equivalent of Mg2+ (von Ahsen et al. 2001) for methods 1-6; method 7 models Mg2+ itself
@@ -224,10 +293,26 @@ ah_status make_run(ah_ctx* ctx, const ah_tm_params* p, TmRun* r) {
   r->ln_mon = mon > 0 ? std::log(mon) : 0.0;
   r->saltcorr = p->saltcorr;
   r->variants = p->variants;
-  r->sym_h = p->selfcomp ? kSymH : 0.0;
-  r->sym_s = p->selfcomp ? kSymS : 0.0;
-  r->h0 = kInitH + kOneGCH + r->sym_h;
-  r->s0 = kInitS + kOneGCS + r->sym_s;
+  const NNSet& set = kNNSets[slot];
+  r->nn = slot;
+  r->sym_h = p->selfcomp ? set.sym[0] : 0.0;
+  r->sym_s = p->selfcomp ? set.sym[1] : 0.0;
+  r->init_h = set.init[0], r->init_s = set.init[1];
+  r->at_h = set.at[0], r->at_s = set.at[1];
+  r->gc_h = set.gc[0], r->gc_s = set.gc[1];
+  r->onegc_h = set.onegc[0], r->onegc_s = set.onegc[1];
+  r->allat_h = set.allat[0], r->allat_s = set.allat[1];
+  r->t5a_h = set.t5a[0], r->t5a_s = set.t5a[1];
+  r->gc_split = set.onegc[0] != set.allat[0] || set.onegc[1] != set.allat[1];
+  r->h0 = set.init[0] + set.onegc[0] + r->sym_h;
+  r->s0 = set.init[1] + set.onegc[1] + r->sym_s;
+  auto tenth = [](double x) { return (int32_t)std::lround(x * 10.0); };
+  for (int v = 0; v < 4; ++v) {  // A=0, C=1, T=2, G=3
+    const double* e = (v & 1) ? set.gc : set.at;
+    const int32_t h = tenth(e[0]), sd = tenth(e[1]);
+    r->end_l[v] = (h + (v == 2 ? tenth(set.t5a[0]) : 0)) * 65536 + sd + (v == 2 ? tenth(set.t5a[1]) : 0);  // 5' T
+    r->end_r[v] = (h + (v == 0 ? tenth(set.t5a[0]) : 0)) * 65536 + sd + (v == 0 ? tenth(set.t5a[1]) : 0);  // 3' A
+  }
   r->corr_const = r->rc0 = r->rc1 = r->rc2 = 0.0;
   const double lm = r->ln_mon;
   switch (p->saltcorr) {
@@ -284,97 +369,92 @@ __device__ bool duplex_tm(const uint8_t* v, const uint8_t* c, int L, const TmRun
   {
     // left end read from the opposite strand: 5'-c1 c0-3' over 3'-v1 v0-5'
     const int k = c[1] * 64 + c[0] * 16 + v[1] * 4 + v[0];
-    const double th = __ldg(&c_nn.term_h[k]);
+    const double th = __ldg(&c_nn[R.nn].term_h[k]);
     if (!isnan(th)) {
       dh += th;
-      ds += __ldg(&c_nn.term_s[k]);
+      ds += __ldg(&c_nn[R.nn].term_s[k]);
       lo = 1;
     }
   }
   if (hi - lo >= 2) {
     const int k = v[L - 2] * 64 + v[L - 1] * 16 + c[L - 2] * 4 + c[L - 1];
-    const double th = __ldg(&c_nn.term_h[k]);
+    const double th = __ldg(&c_nn[R.nn].term_h[k]);
     if (!isnan(th)) {
       dh += th;
-      ds += __ldg(&c_nn.term_s[k]);
+      ds += __ldg(&c_nn[R.nn].term_s[k]);
       hi = L - 1;
     }
   }
   // initiation, from the variant's own end bases (A=0, C=1, T=2, G=3: A/T have bit 0 clear)
-  dh += kInitH;
-  ds += kInitS;
+  dh += R.init_h;
+  ds += R.init_s;
   int gc = 0;
   for (int j = 0; j < L; ++j) gc += v[j] & 1;
   if (gc == 0) {
-    dh += kAllATH;
-    ds += kAllATS;
+    dh += R.allat_h;
+    ds += R.allat_s;
   } else {
-    dh += kOneGCH;
-    ds += kOneGCS;
+    dh += R.onegc_h;
+    ds += R.onegc_s;
   }
   if (v[0] == 2) {  // 5' T
-    dh += k5TAH;
-    ds += k5TAS;
+    dh += R.t5a_h;
+    ds += R.t5a_s;
   }
   if (v[L - 1] == 0) {  // 3' A
-    dh += k5TAH;
-    ds += k5TAS;
+    dh += R.t5a_h;
+    ds += R.t5a_s;
   }
-  if (v[0] & 1) { dh += kTermGCH; ds += kTermGCS; } else { dh += kTermATH; ds += kTermATS; }
-  if (v[L - 1] & 1) { dh += kTermGCH; ds += kTermGCS; } else { dh += kTermATH; ds += kTermATS; }
+  if (v[0] & 1) { dh += R.gc_h; ds += R.gc_s; } else { dh += R.at_h; ds += R.at_s; }
+  if (v[L - 1] & 1) { dh += R.gc_h; ds += R.gc_s; } else { dh += R.at_h; ds += R.at_s; }
   for (int i = lo; i + 1 < hi; ++i) {
     const int k = v[i] * 64 + v[i + 1] * 16 + c[i] * 4 + c[i + 1];
-    const double sh = __ldg(&c_nn.step_h[k]);
+    const double sh = __ldg(&c_nn[R.nn].step_h[k]);
     if (isnan(sh)) return false;
     dh += sh;
-    ds += __ldg(&c_nn.step_s[k]);
+    ds += __ldg(&c_nn[R.nn].step_s[k]);
   }
   *tm = tm_of_sums(dh, ds, gc, L, R);
   return true;
 }
 
-// the end-dependent initiation terms in tenths
-constexpr int tenths_of(double x) { return (int)(x * 10.0 + (x >= 0 ? 0.5 : -0.5)); }
-constexpr int kTermATH10 = tenths_of(kTermATH), kTermATS10 = tenths_of(kTermATS);
-constexpr int kTermGCH10 = tenths_of(kTermGCH), kTermGCS10 = tenths_of(kTermGCS);
-constexpr int k5TAH10 = tenths_of(k5TAH), k5TAS10 = tenths_of(k5TAS);
 
 // nearest-neighbour sums (tenths) of edge (i, i+1) of the variant chain for bases (a, b) at
 // positions i, i+1 over the opposite-strand codes c: the terminal-mismatch entry replaces the stack
 // at either end; false when the step has no parameter
-__device__ __forceinline__ bool edge_sums(int i, int L, uint8_t a, uint8_t b, const uint8_t* c, int* dh, int* ds) {
+__device__ __forceinline__ bool edge_sums(const NNTablesI& ti, int i, int L, uint8_t a, uint8_t b, const uint8_t* c,
+                                          int* dh, int* ds) {
   if (i == 0) {
     const int k = c[1] * 64 + c[0] * 16 + b * 4 + a;  // left end read from the opposite strand
-    const int th = __ldg(&c_nni.term_h[k]);
+    const int th = __ldg(&ti.term_h[k]);
     if (th != kNoParam) {
       *dh = th;
-      *ds = __ldg(&c_nni.term_s[k]);
+      *ds = __ldg(&ti.term_s[k]);
       return true;
     }
   }
   if (i == L - 2) {
     const int k = a * 64 + b * 16 + c[L - 2] * 4 + c[L - 1];
-    const int th = __ldg(&c_nni.term_h[k]);
+    const int th = __ldg(&ti.term_h[k]);
     if (th != kNoParam) {
       *dh = th;
-      *ds = __ldg(&c_nni.term_s[k]);
+      *ds = __ldg(&ti.term_s[k]);
       return true;
     }
   }
   const int k = a * 64 + b * 16 + c[i] * 4 + c[i + 1];
-  const int sh = __ldg(&c_nni.step_h[k]);
+  const int sh = __ldg(&ti.step_h[k]);
   if (sh == kNoParam) return false;
   *dh = sh;
-  *ds = __ldg(&c_nni.step_s[k]);
+  *ds = __ldg(&ti.step_s[k]);
   return true;
 }
 
 // initiation terms (tenths) that depend on the variant's end bases
-__host__ __device__ __forceinline__ void end_sums(int j, int L, uint8_t v, int* dh, int* ds) {
-  *dh = (v & 1) ? kTermGCH10 : kTermATH10;
-  *ds = (v & 1) ? kTermGCS10 : kTermATS10;
-  if (j == 0 && v == 2) *dh += k5TAH10, *ds += k5TAS10;       // 5' T
-  if (j == L - 1 && v == 0) *dh += k5TAH10, *ds += k5TAS10;   // 3' A
+__device__ __forceinline__ void end_sums(const TmRun& R, int j, int L, uint8_t v, int* dh, int* ds) {
+  const int32_t p = j == 0 ? R.end_l[v] : R.end_r[v];
+  *dh = unpack_dh(p);
+  *ds = unpack_ds(p);
 }
 
 // The variants that count at a site (reading R14): per position the primer's codes, only the site's
@@ -418,8 +498,8 @@ __device__ uint64_t count_variants(const SiteVariants& V, uint64_t cap) {
 
 // Tm of a variant from its exact sums (tenths) and G/C count
 __device__ __forceinline__ double tm_of_tenths(int dh10, int ds10, int gc, int L, const TmRun& R) {
-  const double dh = 0.1 * dh10 + kInitH + (gc ? kOneGCH : kAllATH);
-  const double ds = 0.1 * ds10 + kInitS + (gc ? kOneGCS : kAllATS);
+  const double dh = 0.1 * dh10 + R.init_h + (gc ? R.onegc_h : R.allat_h);
+  const double ds = 0.1 * ds10 + R.init_s + (gc ? R.onegc_s : R.allat_s);
   return tm_of_sums(dh, ds, gc, L, R);
 }
 
@@ -449,15 +529,15 @@ __device__ bool enum_max(const SiteVariants& V, const TmRun& R, double* out) {
     if (V.k >= 0 && m > V.k) continue;
     int eh, es;
     if (j == 0) {
-      end_sums(0, L, b, &eh, &es);
-    } else if (!edge_sums(j - 1, L, v[j - 1], b, V.c, &eh, &es)) {
+      end_sums(R, 0, L, b, &eh, &es);
+    } else if (!edge_sums(c_nni[R.nn], j - 1, L, v[j - 1], b, V.c, &eh, &es)) {
       continue;
     }
     const int dh = sh[j] + eh, ds = ss[j] + es;
     v[j] = b;
     const int gc = gcs[j] + (b & 1);
     if (j == L - 1) {
-      end_sums(L - 1, L, b, &eh, &es);
+      end_sums(R, L - 1, L, b, &eh, &es);
       any = true;
       best = fmax(best, tm_of_tenths(dh + eh, ds + es, gc, L, R));
       continue;
@@ -481,7 +561,7 @@ enum ChainResult { kChainOk, kChainUndefined, kChainUnbounded };
 // point) for the confirming pass.  States are (position, base, mismatches so far), at most
 // 4 x (k + 1) per position.
 template <typename T>
-__device__ bool chain_viterbi(const SiteVariants& V, T A, T B, T* best_score, int* dh10, int* ds10) {
+__device__ bool chain_viterbi(const SiteVariants& V, const TmRun& R, T A, T B, T* best_score, int* dh10, int* ds10) {
   constexpr int M = kMaxK + 1;
   const int L = V.L, K = V.k < 0 ? 0 : V.k, W = K + 1;  // a base's states: mismatch counts 0..K
   auto inc = [&](int j, int a) { return (V.k >= 0 && V.ch[j][a] != V.s[j]) ? 1 : 0; };
@@ -493,7 +573,7 @@ __device__ bool chain_viterbi(const SiteVariants& V, T A, T B, T* best_score, in
   for (int x = 0; x < 4 * W; ++x) cur[x] = none;
   for (int a = 0; a < V.nch[0]; ++a) {
     int dh, ds;
-    end_sums(0, L, V.ch[0][a], &dh, &ds);
+    end_sums(R, 0, L, V.ch[0][a], &dh, &ds);
     const int x = a * W + inc(0, a);
     cur[x] = A * (T)ds - B * (T)dh;
     cs[x] = dh * 65536 + ds;
@@ -503,10 +583,10 @@ __device__ bool chain_viterbi(const SiteVariants& V, T A, T B, T* best_score, in
     for (int b = 0; b < V.nch[i + 1]; ++b) {
       const int ib = inc(i + 1, b);
       int th = 0, ts = 0;
-      if (i + 1 == L - 1) end_sums(L - 1, L, V.ch[i + 1][b], &th, &ts);
+      if (i + 1 == L - 1) end_sums(R, L - 1, L, V.ch[i + 1][b], &th, &ts);
       for (int a = 0; a < V.nch[i]; ++a) {
         int dh, ds;
-        if (!edge_sums(i, L, V.ch[i][a], V.ch[i + 1][b], V.c, &dh, &ds)) continue;
+        if (!edge_sums(c_nni[R.nn], i, L, V.ch[i][a], V.ch[i + 1][b], V.c, &dh, &ds)) continue;
         dh += th, ds += ts;
         const T w = A * (T)ds - B * (T)dh;
         const int32_t pw = dh * 65536 + ds;
@@ -547,22 +627,22 @@ __device__ ChainResult site_tm_chain(const SiteVariants& V, const TmRun& R, doub
   const int L = V.L;
     // constant part of D: salt (method 5) and R ln(C); methods 1-4 shift Tm by a constant
   const double S0 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
-  // all-A/T and one-G/C terms are equal here
-  const double H0 = kInitH + kOneGCH + R.sym_h, Sc = kInitS + kOneGCS + R.sym_s;
+  // every qualifying variant holds G or C, or the set's initiation does not depend on it
+  const double H0 = R.h0, Sc = R.s0;
   const double shift = R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0;
   auto ratio = [&](int dh10, int ds10) { return 1000.0 * (0.1 * dh10 + H0) / (0.1 * ds10 + Sc + S0); };
   int dh10, ds10;
   float scf;
   // D must stay negative for every qualifying variant
-  if (!chain_viterbi<float>(V, 1.f, 0.f, &scf, &dh10, &ds10)) return kChainUndefined;
+  if (!chain_viterbi<float>(V, R, 1.f, 0.f, &scf, &dh10, &ds10)) return kChainUndefined;
   if (0.1 * ds10 + Sc + S0 >= 0.0) return kChainUnbounded;
   // start from the variant that maximises dS - dH / 300 (any defined variant works)
-  if (!chain_viterbi<float>(V, 300.f, 1000.f, &scf, &dh10, &ds10)) return kChainUndefined;
+  if (!chain_viterbi<float>(V, R, 300.f, 1000.f, &scf, &dh10, &ds10)) return kChainUndefined;
   double lam = ratio(dh10, ds10);
   int best_h = dh10, best_s = ds10;
   // single-precision search: stop when a pass proposes no variant with a larger exact ratio
   for (int it = 0; it < 64; ++it) {
-    if (!chain_viterbi<float>(V, (float)lam, 1000.f, &scf, &dh10, &ds10)) break;
+    if (!chain_viterbi<float>(V, R, (float)lam, 1000.f, &scf, &dh10, &ds10)) break;
     const double r = ratio(dh10, ds10);
     if (!(r > lam)) break;
     lam = r, best_h = dh10, best_s = ds10;
@@ -576,11 +656,11 @@ __device__ ChainResult site_tm_chain(const SiteVariants& V, const TmRun& R, doub
     if (fabs(lam) < 4000.0) {
       const long long Lq = llrint(lam * kScale), Bq = (long long)(1000.0 * kScale);
       long long sc;
-      if (!chain_viterbi<long long>(V, Lq, Bq, &sc, &dh10, &ds10)) break;
+      if (!chain_viterbi<long long>(V, R, Lq, Bq, &sc, &dh10, &ds10)) break;
       better = sc > Lq * best_s - Bq * best_h;
     } else {
       double sc;
-      if (!chain_viterbi<double>(V, lam, 1000.0, &sc, &dh10, &ds10)) break;
+      if (!chain_viterbi<double>(V, R, lam, 1000.0, &sc, &dh10, &ds10)) break;
       const double inc = lam * best_s - 1000.0 * best_h;
       better = sc > inc + 1e-12 * fabs(inc);
     }
@@ -605,7 +685,13 @@ __device__ __noinline__ double site_tm(const uint8_t* sets, const uint8_t* s, in
   if (!site_variants(sets, s, L, k, clamp, &V)) return nan;
   const uint64_t nv = count_variants(V, kEnumLimit);
   double t;
-  if (nv > kEnumSmall && L >= 3 && R.saltcorr <= 5) {
+  bool some_gc = !R.gc_split;  // the chain's constant terms assume G or C in every variant
+  for (int j = 0; j < L && !some_gc; ++j) {
+    bool only = V.nch[j] > 0;
+    for (int a = 0; a < V.nch[j]; ++a) only = only && (V.ch[j][a] & 1);
+    some_gc = only;
+  }
+  if (nv > kEnumSmall && L >= 3 && R.saltcorr <= 5 && some_gc) {
     const ChainResult r = site_tm_chain(V, R, &t);
     if (r == kChainOk) return t;
     if (r == kChainUndefined) return nan;
@@ -668,9 +754,9 @@ __host__ __device__ inline int tm_group_words(int dmax) {
 __device__ __forceinline__ int fixed_base(uint32_t ch) { return __ffs(ch) - 1; }
 
 // packed sums (tenths) of edge i with base x at i and y at i + 1, kNoEdge without a parameter
-__device__ __forceinline__ int32_t edge_packed(const TmGroupSh& sh, int L, int i, int x, int y) {
+__device__ __forceinline__ int32_t edge_packed(const TmGroupSh& sh, const TmRun& R, int L, int i, int x, int y) {
   int eh, es;
-  if (!edge_sums(i, L, (uint8_t)x, (uint8_t)y, sh.c, &eh, &es)) return kNoEdge;
+  if (!edge_sums(c_nni[R.nn], i, L, (uint8_t)x, (uint8_t)y, sh.c, &eh, &es)) return kNoEdge;
   return eh * 65536 + es;
 }
 
@@ -766,7 +852,7 @@ __device__ double group_site_tm(TmGroupSh& sh, int32_t* w, int L, int k, int cla
   if (empty) return nan;
   const int m0 = __popc(fixed_mm);
   if (K >= 0 && m0 > K) return nan;
-  if (R.saltcorr >= 6 || L < 3 || W * 4 > G) {
+  if (R.saltcorr >= 6 || L < 3 || W * 4 > G || R.gc_split) {
     __syncwarp(gmask);
     double t = nan;
     if (r == 0) t = site_tm(sh.set, sh.s, L, k, clamp, R, status);
@@ -776,7 +862,7 @@ __device__ double group_site_tm(TmGroupSh& sh, int32_t* w, int L, int k, int cla
   {  // steps between two single-choice positions are on every variant
     bool bad = false;
     for (int i = r; i + 1 < L; i += G)
-      if (!((dmask >> i) & 3u) && edge_packed(sh, L, i, fixed_base(sh.ch[i]), fixed_base(sh.ch[i + 1])) == kNoEdge)
+      if (!((dmask >> i) & 3u) && edge_packed(sh, R, L, i, fixed_base(sh.ch[i]), fixed_base(sh.ch[i + 1])) == kNoEdge)
         bad = true;
     if (__any_sync(gmask, bad)) return nan;
   }
@@ -794,17 +880,17 @@ __device__ double group_site_tm(TmGroupSh& sh, int32_t* w, int L, int k, int cla
     int32_t p = kNoEdge, q = kNoEdge;
     if ((sh.ch[d0] >> r) & 1) {
       int eh, es;
-      end_sums(0, L, (uint8_t)(d0 == 0 ? r : fixed_base(sh.ch[0])), &eh, &es);
+      end_sums(R, 0, L, (uint8_t)(d0 == 0 ? r : fixed_base(sh.ch[0])), &eh, &es);
       p = eh * 65536 + es;
       for (int i = 0; i < d0; ++i)
-        p = add_packed(p, edge_packed(sh, L, i, fixed_base(sh.ch[i]), i + 1 == d0 ? r : fixed_base(sh.ch[i + 1])));
+        p = add_packed(p, edge_packed(sh, R, L, i, fixed_base(sh.ch[i]), i + 1 == d0 ? r : fixed_base(sh.ch[i + 1])));
     }
     if ((sh.ch[dl] >> r) & 1) {
       int eh, es;
-      end_sums(L - 1, L, (uint8_t)(dl == L - 1 ? r : fixed_base(sh.ch[L - 1])), &eh, &es);
+      end_sums(R, L - 1, L, (uint8_t)(dl == L - 1 ? r : fixed_base(sh.ch[L - 1])), &eh, &es);
       q = eh * 65536 + es;
       for (int i = dl; i + 1 < L; ++i)
-        q = add_packed(q, edge_packed(sh, L, i, i == dl ? r : fixed_base(sh.ch[i]), fixed_base(sh.ch[i + 1])));
+        q = add_packed(q, edge_packed(sh, R, L, i, i == dl ? r : fixed_base(sh.ch[i]), fixed_base(sh.ch[i + 1])));
     }
     sh.pre[r] = p;
     sh.suf[r] = q;
@@ -818,17 +904,17 @@ __device__ double group_site_tm(TmGroupSh& sh, int32_t* w, int L, int k, int cla
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b)
-          wt[a * 4 + b] = ((cha >> a) & 1) && ((chb >> b) & 1) ? edge_packed(sh, L, lo, a, b) : kNoEdge;
+          wt[a * 4 + b] = ((cha >> a) & 1) && ((chb >> b) & 1) ? edge_packed(sh, R, L, lo, a, b) : kNoEdge;
     } else {
       // left step (choice a, then a fixed base), the fixed steps, right step (fixed base, then b)
       int32_t mid = 0, left[4], right[4];
       for (int i = lo + 1; i + 1 < hi; ++i)
-        mid += edge_packed(sh, L, i, fixed_base(sh.ch[i]), fixed_base(sh.ch[i + 1]));  // defined: checked above
+        mid += edge_packed(sh, R, L, i, fixed_base(sh.ch[i]), fixed_base(sh.ch[i + 1]));  // defined: checked above
       const int fl = fixed_base(sh.ch[lo + 1]), fr = fixed_base(sh.ch[hi - 1]);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        left[a] = (cha >> a) & 1 ? edge_packed(sh, L, lo, a, fl) : kNoEdge;
-        right[a] = (chb >> a) & 1 ? edge_packed(sh, L, hi - 1, fr, a) : kNoEdge;
+        left[a] = (cha >> a) & 1 ? edge_packed(sh, R, L, lo, a, fl) : kNoEdge;
+        right[a] = (chb >> a) & 1 ? edge_packed(sh, R, L, hi - 1, fr, a) : kNoEdge;
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
@@ -859,7 +945,7 @@ __device__ double group_site_tm(TmGroupSh& sh, int32_t* w, int L, int k, int cla
     bound += mp + ms;
   }
   const double S0 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
-  const double H0 = kInitH + kOneGCH + R.sym_h, Sc = kInitS + kOneGCS + R.sym_s;
+  const double H0 = R.h0, Sc = R.s0;
   const double shift = R.saltcorr >= 1 && R.saltcorr <= 4 ? R.corr_const : 0.0;
   auto ratio = [&](int dh10, int ds10) { return 1000.0 * (0.1 * dh10 + H0) / (0.1 * ds10 + Sc + S0); };
   int dh10, ds10;
@@ -973,11 +1059,11 @@ __global__ void __launch_bounds__(kTmBlock) k_tm_hits(const ah_hit* __restrict__
 
 // Whether edge i of a variant with bases x at i and y at i + 1 has a parameter, over the opposite
 // strand cc (2-bit codes of position j at bits 2j); the lookups of edge_sums.
-__device__ __forceinline__ bool edge_defined(int i, int L, int x, int y, uint64_t cc) {
+__device__ __forceinline__ bool edge_defined(const NNTablesI& ti, int i, int L, int x, int y, uint64_t cc) {
   const int c0 = (int)(cc >> (2 * i)) & 3, c1 = (int)(cc >> (2 * i + 2)) & 3;
-  if (i == 0 && __ldg(&c_nni.term_h[c1 * 64 + c0 * 16 + y * 4 + x]) != kNoParam) return true;
-  if (i == L - 2 && __ldg(&c_nni.term_h[x * 64 + y * 16 + c0 * 4 + c1]) != kNoParam) return true;
-  return __ldg(&c_nni.step_h[x * 64 + y * 16 + c0 * 4 + c1]) != kNoParam;
+  if (i == 0 && __ldg(&ti.term_h[c1 * 64 + c0 * 16 + y * 4 + x]) != kNoParam) return true;
+  if (i == L - 2 && __ldg(&ti.term_h[x * 64 + y * 16 + c0 * 4 + c1]) != kNoParam) return true;
+  return __ldg(&ti.step_h[x * 64 + y * 16 + c0 * 4 + c1]) != kNoParam;
 }
 
 // The group-per-site form of k_tm_hits.  A block takes a window of kTmWindow site slots, one per
@@ -1044,7 +1130,7 @@ __global__ void __launch_bounds__(kTmWindow) k_tm_hits_g(const ah_hit* __restric
         if (!ch) undefined = true;
         const int cur = __popc(ch) == 1 ? fixed_base(ch) : -1;
         if (cur >= 0 && cur != sj) ++mism;
-        if (j > 0 && cur >= 0 && prev >= 0 && !edge_defined(j - 1, L, prev, cur, cc)) undefined = true;
+        if (j > 0 && cur >= 0 && prev >= 0 && !edge_defined(c_nni[R.nn], j - 1, L, prev, cur, cc)) undefined = true;
         prev = cur;
       }
       if (kk < L && mism > kk) undefined = true;
@@ -1123,14 +1209,12 @@ __host__ __device__ __forceinline__ void put_tab_entry(TmTabs& T, const NNTables
 }
 
 // TmTabs from the parameter tables (row_ds is not filled: only the generated chains read it)
-__device__ __forceinline__ void fill_tabs(TmTabs& T) {
-  for (int e = threadIdx.x; e < 256; e += blockDim.x) put_tab_entry(T, c_nni, e);
+__device__ __forceinline__ void fill_tabs(TmTabs& T, int slot) {
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) put_tab_entry(T, c_nni[slot], e);
 }
 
-__device__ __forceinline__ int32_t end_packed(int j, int L, int v) {
-  int dh, ds;
-  end_sums(j, L, (uint8_t)v, &dh, &ds);
-  return dh * 65536 + ds;
+__device__ __forceinline__ int32_t end_packed(const TmRun& R, int j, int L, int v) {
+  return j == 0 ? R.end_l[v] : R.end_r[v];
 }
 
 __device__ __forceinline__ int rank_of(uint32_t ch, int a) { return __popc(ch & ((1u << a) - 1u)); }
@@ -1213,7 +1297,8 @@ __device__ __forceinline__ bool thread_pass(const TmTabs& T, const int32_t* __re
 // position (with everything before it), one per pair of choices at consecutive ones (with the fixed
 // steps between them), one per choice at the last (with everything after it).  Returns a bound on
 // every variant's dS (tenths): the sum of each block's largest.
-__device__ __forceinline__ int thread_weights(const TmTabs& T, int32_t* __restrict__ W, int ws, const PrimerMasks P,
+__device__ __forceinline__ int thread_weights(const TmRun& R, const TmTabs& T, int32_t* __restrict__ W, int ws,
+                                              const PrimerMasks P,
                                               uint32_t dmask, uint64_t cc, int L) {
   int bound = 0, off = 0;
   {
@@ -1223,7 +1308,7 @@ __device__ __forceinline__ int thread_weights(const TmTabs& T, int32_t* __restri
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       if (!((ch0 >> a) & 1u)) continue;
-      int32_t p = end_packed(0, L, d0 == 0 ? a : P.fixed(0));
+      int32_t p = end_packed(R, 0, L, d0 == 0 ? a : P.fixed(0));
       for (int i = 0; i < d0; ++i)
         p = add_packed(p, edge_tab(T, i, L, P.fixed(i), i + 1 == d0 ? a : P.fixed(i + 1), cc));
       W[(off + rank_of(ch0, a)) * ws] = p;
@@ -1284,7 +1369,7 @@ __device__ __forceinline__ int thread_weights(const TmTabs& T, int32_t* __restri
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       if (!((chl >> b) & 1u)) continue;
-      int32_t p = end_packed(L - 1, L, lo == L - 1 ? b : P.fixed(L - 1));
+      int32_t p = end_packed(R, L - 1, L, lo == L - 1 ? b : P.fixed(L - 1));
       for (int i = lo; i + 1 < L; ++i)
         p = add_packed(p, edge_tab(T, i, L, i == lo ? b : P.fixed(i), P.fixed(i + 1), cc));
       W[(off + rank_of(chl, b)) * ws] = p;
@@ -1307,8 +1392,9 @@ struct GenericChain {
   uint32_t dmask;  // branch positions
   uint64_t cc;     // the site's opposite-strand codes
   int L;
+  const TmRun* R;  // the run constants (shared memory)
   __device__ __forceinline__ int weights(const TmTabs& T, int32_t* __restrict__ W, int ws) const {
-    return thread_weights(T, W, ws, P, dmask, cc, L);
+    return thread_weights(*R, T, W, ws, P, dmask, cc, L);
   }
   template <typename S>
   __device__ __forceinline__ bool pass(const TmTabs& T, const int32_t* __restrict__ W, int ws, S A, S B, S* best,
@@ -1319,11 +1405,11 @@ struct GenericChain {
 
 // the built-in kernel's sites: tables from the parameter arrays, every primer by GenericChain
 struct GenericSites {
-  static __device__ __forceinline__ void fill(TmTabs& T, const int32_t*) { fill_tabs(T); }
+  static __device__ __forceinline__ void fill(TmTabs& T, const int32_t*, int slot) { fill_tabs(T, slot); }
   static __device__ __forceinline__ bool site(uint32_t, const TmTabs& T, int32_t* __restrict__ W, int ws,
                                               const PrimerMasks P, uint64_t code, int L, const TmRun& R, double* tm) {
-    const GenericChain c{P, chain_nodes(P, L), code ^ 0xAAAAAAAAAAAAAAAAull, L};
-    return chain_site_tm(T, W, ws, c, L, R, tm);
+    const GenericChain c{P, chain_nodes(P, L), code ^ 0xAAAAAAAAAAAAAAAAull, L, &R};
+    return chain_site_tm(T, W, ws, c, L, R, P.some_gc(L), tm);
   }
 };
 
@@ -1395,12 +1481,14 @@ __device__ __noinline__ double warp_enumerate(const TmTabs& T, const int32_t* __
     if (offq[q] < 0) return T.step[row_of(cc, pos[q + 1]) + nth_code(ch[q + 1], dq1) * 4 + nth_code(ch[q], dq)];
     return W[(offq[q] + dq1 * rad[q] + dq) * ws];
   };
-  // constant parts of dH and dS, and the Tm from the sums, in single precision
-  const float Hf = (float)(kInitH + R.sym_h);
-  const float Sf = (float)(kInitS + R.sym_s + (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk);
+  // constant parts of dH and dS (a variant with and without G or C), and the Tm from the sums, in
+  // single precision
+  const double S1 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
+  const float Hg = (float)R.h0, Sg = (float)(R.s0 + S1);
+  const float Ha = (float)(R.init_h + R.allat_h + R.sym_h), Sa = (float)(R.init_s + R.allat_s + R.sym_s + S1);
   const float shiftf = R.saltcorr >= 1 && R.saltcorr <= 4 ? (float)R.corr_const : 0.f;
   auto tm_float = [&](int32_t p, int gc, bool* near_zero) {
-    const float dh = 0.1f * (float)unpack_dh(p) + Hf, ds = 0.1f * (float)unpack_ds(p) + Sf;
+    const float dh = 0.1f * (float)unpack_dh(p) + (gc ? Hg : Ha), ds = 0.1f * (float)unpack_ds(p) + (gc ? Sg : Sa);
     *near_zero = fabsf(ds) < 2.f;
     float t = 1000.f * dh / ds - 273.15f + shiftf;
     if (R.saltcorr >= 6) {
@@ -1510,7 +1598,7 @@ __global__ void __launch_bounds__(kTmThreads) k_tm_deferred(const ah_hit* __rest
   int32_t* W = reinterpret_cast<int32_t*>(tm_smem + kTmTabWords) + threadIdx.x;
   const uint32_t n_def = defer[0];
   if (blockIdx.x * (kTmThreads / 32) >= n_def) return;  // the whole block has nothing to do
-  fill_tabs(T);
+  fill_tabs(T, Rp.nn);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * (kTmThreads / 32);
@@ -1522,7 +1610,7 @@ __global__ void __launch_bounds__(kTmThreads) k_tm_deferred(const ah_hit* __rest
     const uint4 mk = pmask[pr];
     const PrimerMasks P{{mk.x, mk.y, mk.z, mk.w}};
     const uint64_t code = site_code(planes, rec_group, h, L);
-    thread_weights(T, W, kTmThreads, P, chain_nodes(P, L), code ^ 0xAAAAAAAAAAAAAAAAull, L);
+    thread_weights(R, T, W, kTmThreads, P, chain_nodes(P, L), code ^ 0xAAAAAAAAAAAAAAAAull, L);
     const double tm = warp_enumerate(T, W, kTmThreads, P, code ^ 0xAAAAAAAAAAAAAAAAull, L, R, status, lane);
     if (lane == 0) out[i] = tm;
   }
@@ -1816,23 +1904,19 @@ ah_status tm_sites(ah_ctx* ctx, uint32_t n, const char* const* primers, const ch
 
 static_assert(sizeof(TmRun) <= kTmRunBytes, "Tm run constants exceed a plan's buffer");
 
-int32_t tm_end_packed(int j, int L, int v) {
-  int dh, ds;
-  end_sums(j, L, (uint8_t)v, &dh, &ds);
-  return dh * 65536 + ds;
-}
-
 size_t tm_run_bytes() { return sizeof(TmRun); }
 
-ah_status tm_tab_image(ah_ctx* ctx, const int32_t** out) {
+int tm_run_slot(const void* run) { return ((const TmRun*)run)->nn; }
+
+ah_status tm_tab_image(ah_ctx* ctx, int slot, const int32_t** out) {
   *out = nullptr;
   ah_status st;
   if ((st = load_tables(ctx))) return st;
   std::lock_guard<std::mutex> lock(g_tables_mu);
-  if (ctx->device >= 64) return fail(ctx, AH_EINTERNAL, "tm_tab_image: device index above 63");
-  if (!g_tab_image[ctx->device]) {
+  if (ctx->device >= 64 || slot < 0 || slot >= kNNSlots) return fail(ctx, AH_EINTERNAL, "tm_tab_image: bad device or set");
+  if (!g_tab_image[ctx->device][slot]) {
     TmTabs T;
-    for (int e = 0; e < 256; ++e) put_tab_entry(T, g_host_i, e);
+    for (int e = 0; e < 256; ++e) put_tab_entry(T, g_host_i[slot], e);
     for (int r = 0; r < 16; ++r) {  // the largest dS of each step row over its defined entries
       int mx = 0;
       bool any = false;
@@ -1848,9 +1932,9 @@ ah_status tm_tab_image(ah_ctx* ctx, const int32_t** out) {
     int32_t* d = nullptr;
     AH_CUDA(ctx, cudaMalloc(&d, sizeof T));  // kept for the life of the process, like the tables
     AH_CUDA(ctx, cudaMemcpy(d, &T, sizeof T, cudaMemcpyHostToDevice));
-    g_tab_image[ctx->device] = d;
+    g_tab_image[ctx->device][slot] = d;
   }
-  *out = g_tab_image[ctx->device];
+  *out = g_tab_image[ctx->device][slot];
   return AH_OK;
 }
 
@@ -1896,7 +1980,7 @@ ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const a
   if (h->n && a->n) {
     if ((st = dalloc(ctx, &defer, h->n + 1))) return st;
     TmKernel tk;
-    if (!R.variants && (st = tm_kernel_for(ctx, p, false, &tk))) return st;
+    if (!R.variants && (st = tm_kernel_for(ctx, p, false, R.nn, &tk))) return st;
     bool generated = false;
     launch_tm_hits(ctx->stream, R, p, h->d, h->n, nullptr, b->planes, b->rec_group, hit_tm, ctx->d_status, defer,
                    ctx->sm_count, tk, &generated);

@@ -49,10 +49,19 @@ struct TmRun {
   double corr_const;  // methods 1-4: Tm correction
   // methods 6 and 7: correction to 1/Tm, rc0 + rc1 f + rc2 / (2 (L - 1)) with f the G/C fraction
   double rc0, rc1, rc2;
-  double sym_h, sym_s;  // self-complementary duplexes: the symmetry terms (else 0)
-  double h0, s0;      // the variant-independent initiation terms plus the symmetry terms
+  double sym_h, sym_s;  // self-complementary duplexes: the set's symmetry terms (else 0)
+  double h0, s0;      // the duplex-wide initiation terms of a duplex holding G or C, plus symmetry
+  // the nearest-neighbour set's initiation terms (kcal/mol, cal/(K mol)): every duplex; per
+  // terminal A.T and G.C pair of the written strand; a duplex with some / no G or C; each of a 5' T
+  // and a 3' A of the written strand
+  double init_h, init_s, at_h, at_s, gc_h, gc_s, onegc_h, onegc_s, allat_h, allat_s, t5a_h, t5a_s;
+  // the same end terms packed in tenths (dH * 65536 + dS) per variant base (A, C, T, G) at the
+  // 5' end (end_l) and the 3' end (end_r)
+  int32_t end_l[4], end_r[4];
   int saltcorr;
   int variants;       // 1: degenerate site Tm over the variants matching the site only
+  int nn;             // the set's slot in the device tables
+  int gc_split;       // 1: the set's initiation differs between duplexes with and without G or C
 };
 
 constexpr int kTmThreads = 128;
@@ -100,6 +109,11 @@ struct PrimerMasks {
   __device__ __forceinline__ int fixed(int j) const {  // the one code of a single-choice position
     return (int)((m[1] >> j) & 1u) + 2 * (int)((m[2] >> j) & 1u) + 3 * (int)((m[3] >> j) & 1u);
   }
+  // every variant holds G or C: some position allows only those
+  __device__ __forceinline__ bool some_gc(int L) const {
+    const uint32_t only_gc = (m[1] | m[3]) & ~(m[0] | m[2]);
+    return (L >= 32 ? only_gc : only_gc & ((1u << L) - 1u)) != 0;
+  }
   // positions with at least two choices
   __device__ __forceinline__ uint32_t branching(int L) const {
     const uint32_t b = (m[0] & m[1]) | (m[0] & m[2]) | (m[0] & m[3]) | (m[1] & m[2]) | (m[1] & m[3]) | (m[2] & m[3]);
@@ -138,6 +152,9 @@ __device__ __forceinline__ uint64_t site_code(const uint2* __restrict__ planes, 
 // Tm of one site over every variant of its primer by the chain method.  Returns false when the chain
 // does not apply (salt methods 6 and 7, L < 3, an entropy sum that could reach zero, a ratio beyond
 // the fixed-point range): the site is then enumerated variant by variant.
+//  - The chain's constant terms assume a duplex holding G or C (some_gc: a position of the primer
+//    allows only C and G); where the set's initiation depends on that and the primer does not
+//    guarantee it, the site is enumerated.
 //  - The sign condition: every variant's entropy sum must stay negative.  The chain's bound is tried
 //    first; the exact largest dS is found only when the bound leaves the sign open.
 //  - The start pass scores 300 dS - 1000 dH exactly in int32; each proving pass scores
@@ -146,9 +163,9 @@ __device__ __forceinline__ uint64_t site_code(const uint2* __restrict__ planes, 
 //    shows it optimal; otherwise the better variant's ratio is the next lambda.
 template <class C>
 __device__ __forceinline__ bool chain_site_tm(const TmTabs& T, int32_t* __restrict__ W, int ws, const C& chain, int L,
-                                              const TmRun& R, double* tm) {
+                                              const TmRun& R, bool some_gc, double* tm) {
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
-  if (R.saltcorr >= 6 || L < 3) return false;
+  if (R.saltcorr >= 6 || L < 3 || (R.gc_split && !some_gc)) return false;
   const int bound = chain.weights(T, W, ws);
   const double S0 = (R.saltcorr == 5 ? 0.368 * (double)(L - 1) * R.ln_mon : 0.0) + R.rlnk;
   const double H0 = R.h0, Sc = R.s0;
@@ -202,7 +219,7 @@ __device__ __forceinline__ bool chain_site_tm(const TmTabs& T, int32_t* __restri
 // of a warp share the chain's shape and the warps are full.  Sites the chain does not cover go to
 // the list defer (count at defer[0]) for the enumerating kernel.  Shared memory: the tables, the
 // window's keys and their order by primer, then each thread's weights, strided by the block size.
-// D supplies fill(TmTabs&, const int32_t* image) and site(pr, T, W, ws, P, code, L, R, &tm).
+// D supplies fill(TmTabs&, const int32_t* image, int slot) and site(pr, T, W, ws, P, code, L, R, &tm).
 template <class D>
 __device__ __forceinline__ void tm_hits_body(const ah_hit* __restrict__ hits, uint64_t n,
                                              const uint2* __restrict__ planes, const uint64_t* __restrict__ rec_group,
@@ -222,7 +239,7 @@ __device__ __forceinline__ void tm_hits_body(const ah_hit* __restrict__ hits, ui
   uint32_t* order = tm_smem + kTmTabWords + kTmSlots;
   int32_t* W = reinterpret_cast<int32_t*>(tm_smem + kTmTabWords + 2 * kTmSlots) + threadIdx.x;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
-  D::fill(T, image);
+  D::fill(T, image, Rp.nn);
   __syncthreads();
   const uint64_t base = (uint64_t)blockIdx.x * kTmSlots;
   const uint64_t n_here = d_n && *d_n < n ? *d_n : n;

@@ -96,7 +96,7 @@ struct Chain {
   uint8_t set[32] = {};
   std::vector<int> D;
   std::vector<int> node_slot;  // first slot of node t (one per choice); -1: its weights are literals
-  std::vector<std::vector<int32_t>> node_lit;  // those literals, one per choice
+  std::vector<std::vector<std::string>> node_lit;  // those weights, one per choice: "0" or an end term
   std::vector<int> edge_slot;  // adjacent steps at the duplex's ends: first slot (|A| x |B|), else -1
   int words = 0;
   bool adjacent(int t) const { return D[t + 1] == D[t] + 1; }
@@ -113,8 +113,8 @@ Chain make_chain(const std::string& primer) {
   const int n = (int)c.D.size();
   for (int t = 0; t < n; ++t) {
     const int d = c.D[t];
-    // a node whose weight holds no step (only end terms, or nothing) is a literal per choice
-    bool steps = (t == 0 && d >= 1) || (t == n - 1 && d + 1 < c.L);
+    // a node whose weight holds nothing (no step and no end term) is a literal zero
+    bool steps = t == 0 || t == n - 1;
     if (t > 0 && !c.adjacent(t - 1)) steps = true;
     if (t + 1 < n && !c.adjacent(t)) steps = true;
     c.node_lit.emplace_back();
@@ -125,10 +125,10 @@ Chain make_chain(const std::string& primer) {
     }
     c.node_slot.push_back(-1);
     for (int a : codes(c.set[d])) {
-      int32_t v = 0;
-      if (d == 0) v += tm_end_packed(0, c.L, a);
-      if (d == c.L - 1) v += tm_end_packed(c.L - 1, c.L, a);
-      c.node_lit.back().push_back(v);
+      std::string v;
+      if (d == 0) v = "R->end_l[" + std::to_string(a) + "]";
+      if (d == c.L - 1) v += (v.empty() ? "" : " + ") + std::string("R->end_r[") + std::to_string(a) + "]";
+      c.node_lit.back().push_back(v.empty() ? "0" : v);
     }
   }
   for (int t = 0; t + 1 < n; ++t) {
@@ -159,14 +159,13 @@ std::string rows_decl(const Chain& c, const std::vector<int>& edges, const char*
   return os.str();
 }
 
-std::string packed_lit(int32_t p) { return "(int32_t)" + std::to_string(p); }
 
 // struct C<q> { uint64_t cc; weights(); pass<S>(); } for one primer
 std::string chain_struct(const Chain& c, int q) {
   std::ostringstream os;
   const int L = c.L, n = (int)c.D.size();
   auto fixed_at = [&](int j) { return only(c.set[j]); };
-  os << "struct C" << q << " {  // L = " << L << ", " << n << " branch position(s)\n  uint64_t cc;\n";
+  os << "struct C" << q << " {  // L = " << L << ", " << n << " branch position(s)\n  uint64_t cc;\n  const TmRun* R;\n";
   if (L < 3) {  // the driver defers these before any pass
     os << "  __device__ __forceinline__ int weights(const TmTabs&, int32_t*, int) const { return 0; }\n";
     os << "  template <typename S> __device__ __forceinline__ bool pass(const TmTabs&, const int32_t*, int, S, S, S*,"
@@ -183,36 +182,37 @@ std::string chain_struct(const Chain& c, int q) {
   os << "    int bound = 0;\n";
   for (int t = 0; t < n; ++t) {
     const int d = c.D[t];
-    if (c.node_slot[t] < 0) {  // literal weights: only their part of the bound
-      int mx = -2147483647 - 1;
-      for (int32_t v : c.node_lit[t]) mx = std::max(mx, (int)(int16_t)(v & 0xffff));
-      if (mx) os << "    bound += " << mx << ";  // node " << t << " at position " << d << " (literal)\n";
+    if (c.node_slot[t] < 0) {  // weights without steps: only their part of the bound
+      if (c.node_lit[t][0] == "0") continue;
+      os << "    {  // node " << t << " at position " << d << " (end terms only)\n      int mx = unpack_ds("
+         << c.node_lit[t][0] << ");\n";
+      for (size_t k = 1; k < c.node_lit[t].size(); ++k) os << "      mx = max(mx, unpack_ds(" << c.node_lit[t][k] << "));\n";
+      os << "      bound += mx;\n    }\n";
       continue;
     }
     // fixed part: ends not at a branch position, fixed steps before the first / after the last
     // branch position and between separated ones
     std::vector<std::string> fixed;
-    int32_t konst = 0;
+    std::string konst = "0";
     if (t == 0) {
-      if (d != 0) konst += tm_end_packed(0, L, fixed_at(0));
+      if (d != 0) konst += " + R->end_l[" + std::to_string(fixed_at(0)) + "]";
       for (int i = 0; i + 2 <= d; ++i) fixed.push_back(edge_expr(c, i, fixed_at(i), fixed_at(i + 1)));
     }
     if (t == n - 1) {
-      if (d != L - 1) konst += tm_end_packed(L - 1, L, fixed_at(L - 1));
+      if (d != L - 1) konst += " + R->end_r[" + std::to_string(fixed_at(L - 1)) + "]";
       for (int i = d + 1; i + 1 < L; ++i) fixed.push_back(edge_expr(c, i, fixed_at(i), fixed_at(i + 1)));
     }
     if (t + 1 < n && !c.adjacent(t))
       for (int i = d + 1; i + 2 <= c.D[t + 1]; ++i) fixed.push_back(edge_expr(c, i, fixed_at(i), fixed_at(i + 1)));
-    os << "    {  // node " << t << " at position " << d << "\n      const int32_t f = " << packed_lit(konst);
+    os << "    {  // node " << t << " at position " << d << "\n      const int32_t f = " << konst;
     for (auto& e : fixed) os << "\n          + " << e;
     os << ";\n      int mx = -2147483647 - 1;\n";
     const std::vector<int> ch = codes(c.set[d]);
     for (size_t k = 0; k < ch.size(); ++k) {
       const int a = ch[k];
-      int32_t ka = 0;
-      if (d == 0) ka += tm_end_packed(0, L, a);
-      if (d == L - 1) ka += tm_end_packed(L - 1, L, a);
-      std::string p = "f + " + packed_lit(ka);
+      std::string p = "f";
+      if (d == 0) p += " + R->end_l[" + std::to_string(a) + "]";
+      if (d == L - 1) p += " + R->end_r[" + std::to_string(a) + "]";
       if (d >= 1 && (t == 0 || !c.adjacent(t - 1))) p = "add_packed(" + edge_expr(c, d - 1, fixed_at(d - 1), a) + ", " + p + ")";
       if (d + 1 < L && (t == n - 1 || !c.adjacent(t))) p = "add_packed(" + edge_expr(c, d, a, fixed_at(d + 1)) + ", " + p + ")";
       os << "      { const int32_t p = " << p << ";\n        W[" << (c.node_slot[t] + (int)k)
@@ -254,8 +254,8 @@ std::string chain_struct(const Chain& c, int q) {
         const int a = ch[k];
         os << "      S c" << t << "_" << a << " = none;\n      int32_t s" << t << "_" << a << " = 0;\n";
         if (c.node_slot[t] < 0)
-          os << "      c" << t << "_" << a << " = score<S>(" << packed_lit(c.node_lit[t][k]) << ", A, B), s" << t << "_" << a
-             << " = " << packed_lit(c.node_lit[t][k]) << ";\n";
+          os << "      c" << t << "_" << a << " = score<S>(" << c.node_lit[t][k] << ", A, B), s" << t << "_" << a
+             << " = " << c.node_lit[t][k] << ";\n";
         else
           os << "      { const int32_t p = W[" << (c.node_slot[t] + (int)k) << " * ws]; if (p != kNoEdge) c" << t << "_"
              << a << " = score<S>(p, A, B), s" << t << "_" << a << " = p; }\n";
@@ -279,8 +279,8 @@ std::string chain_struct(const Chain& c, int q) {
              << (u - 1) << "_" << a << " + e; } }\n";
         }
         if (c.node_slot[u] < 0) {
-          const std::string lit = packed_lit(c.node_lit[u][kb]);
-          if (c.node_lit[u][kb] == 0)
+          const std::string lit = c.node_lit[u][kb];
+          if (lit == "0")
             os << "        if (m != none) c" << u << "_" << b << " = m, s" << u << "_" << b << " = ms;\n      }\n";
           else
             os << "        if (m != none) c" << u << "_" << b << " = m + score<S>(" << lit << ", A, B), s" << u << "_" << b
@@ -339,26 +339,27 @@ std::string tm_chain_source(const std::vector<std::string>& primers, int* weight
   }
   // one driver for every primer: the chain's two calls switch on the primer (warp-uniform after the
   // kernel's sort), so the driver is compiled once and only the chains per primer
-  os << "struct Chains {\n  uint32_t pr;\n  uint64_t cc;\n";
+  os << "struct Chains {\n  uint32_t pr;\n  uint64_t cc;\n  const TmRun* R;\n";
   os << "  __device__ __forceinline__ int weights(const TmTabs& T, int32_t* __restrict__ W, int ws) const {\n"
         "    switch (pr) {\n";
   for (size_t q = 0; q < primers.size(); ++q)
-    os << "      case " << q << ": return C" << index[q] << "{cc}.weights(T, W, ws);\n";
+    os << "      case " << q << ": return C" << index[q] << "{cc, R}.weights(T, W, ws);\n";
   os << "      default: return 0;\n    }\n  }\n";
   os << "  template <typename S>\n  __device__ __forceinline__ bool pass(const TmTabs& T, const int32_t* __restrict__ W, "
         "int ws, S A, S B, S* best, int32_t* bsum) const {\n    switch (pr) {\n";
   for (size_t q = 0; q < primers.size(); ++q)
-    os << "      case " << q << ": return C" << index[q] << "{cc}.template pass<S>(T, W, ws, A, B, best, bsum);\n";
+    os << "      case " << q << ": return C" << index[q] << "{cc, R}.template pass<S>(T, W, ws, A, B, best, bsum);\n";
   os << "      default: return false;\n    }\n  }\n};\n";
   os << "struct GenSites {\n";
-  os << "  static __device__ __forceinline__ void fill(TmTabs& T, const int32_t* __restrict__ image) {\n";
+  os << "  static __device__ __forceinline__ void fill(TmTabs& T, const int32_t* __restrict__ image, int) {\n";
   os << "    int32_t* d = reinterpret_cast<int32_t*>(&T);\n";
   os << "    for (int e = threadIdx.x; e < kTmTabWords; e += blockDim.x) d[e] = image[e];\n  }\n";
   os << "  static __device__ __forceinline__ bool site(uint32_t pr, const TmTabs& T, int32_t* __restrict__ W, int ws,\n"
-        "                                              const PrimerMasks, uint64_t code, int L, const TmRun& R,"
+        "                                              const PrimerMasks P, uint64_t code, int L, const TmRun& R,"
         " double* tm) {\n";
   os << "    if (pr >= " << primers.size() << "u) return false;\n";
-  os << "    return chain_site_tm(T, W, ws, Chains{pr, code ^ 0xAAAAAAAAAAAAAAAAull}, L, R, tm);\n  }\n};\n";
+  os << "    return chain_site_tm(T, W, ws, Chains{pr, code ^ 0xAAAAAAAAAAAAAAAAull, &R}, L, R, P.some_gc(L), tm);\n"
+        "  }\n};\n";
   os << "extern \"C\" __global__ void __launch_bounds__(kTmThreads, 4) ah_tm_jit(\n"
         "    const ah_hit* __restrict__ hits, uint64_t n, const uint2* __restrict__ planes,\n"
         "    const uint64_t* __restrict__ rec_group, const uint8_t* __restrict__ plen, const uint4* __restrict__ pmask,\n"
@@ -488,14 +489,14 @@ Lookup lookup(int device, const std::vector<std::string>& primers, TmKernel* out
 
 }  // namespace
 
-ah_status tm_kernel_for(ah_ctx* ctx, const ah_primers* p, bool wait, TmKernel* out) {
+ah_status tm_kernel_for(ah_ctx* ctx, const ah_primers* p, bool wait, int slot, TmKernel* out) {
   *out = TmKernel{};
   if (ctx->tm_kernel == 1 || p->n_pairs == 0 || 2 * p->n_pairs > (uint32_t)kTmJitMaxPrimers) return AH_OK;
   const std::vector<std::string> primers = primer_list(p);
   if (tm_chain_adjacent(primers) > kTmJitMaxAdjacent) return AH_OK;
   if (ctx->tm_kernel == 2 && !wait) {  // the built-in kernel until the generated one is compiled
     const Lookup l = lookup(ctx->device, primers, out);
-    if (l == kReady) return tm_tab_image(ctx, &out->image);
+    if (l == kReady) return tm_tab_image(ctx, slot, &out->image);
     *out = TmKernel{};
     if (l == kAbsent) {
       const int device = ctx->device;
@@ -524,7 +525,7 @@ ah_status tm_kernel_for(ah_ctx* ctx, const ah_primers* p, bool wait, TmKernel* o
     *out = TmKernel{};
     return fail(ctx, st, "%s", err.c_str());
   }
-  return tm_tab_image(ctx, &out->image);
+  return tm_tab_image(ctx, slot, &out->image);
 }
 
 }  // namespace ah

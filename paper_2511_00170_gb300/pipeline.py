@@ -36,17 +36,18 @@ class Params:
     variants: int = 0
     selfcomp: int = 0
     filter: Optional[bool] = None   # None: filter iff min_tm is set; False: annotate the decision only
+    nn_table: int = 0               # nearest-neighbour set (Biopython's numbering; 0 the default DNA_NN3)
 
     @classmethod
     def from_workload(cls, wl) -> "Params":
         t = wl.tm
         return cls(list(wl.fwd), list(wl.rev), list(wl.k), wl.clamp, wl.min_len, wl.max_len, wl.orient_mask, t.Na, t.K,
                    t.Tris, t.Mg, t.dNTPs, t.dnac1, t.dnac2, t.saltcorr, t.min_tm, wl.trim, wl.fb_len, wl.rb_len,
-                   getattr(t, "variants", 0), getattr(t, "selfcomp", 0))
+                   getattr(t, "variants", 0), getattr(t, "selfcomp", 0), None, getattr(t, "nn_table", 0))
 
     def tm_params(self) -> ah.ah_tm_params:
         return ah.tm_params(self.Na, self.K, self.Tris, self.Mg, self.dNTPs, self.dnac1, self.dnac2, self.saltcorr,
-                            self.min_tm, self.variants, self.selfcomp, self.filter)
+                            self.min_tm, self.variants, self.selfcomp, self.filter, self.nn_table)
 
 
 @dataclass
