@@ -520,22 +520,32 @@ def run_engine(args):
         words = w_t.numpy().view(np.uint32)[:len(words0)]
         groups[:] = groups0
         words[:] = words0
-        times = []
-        for it in range(1 + args.e2e_steps):
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            ah.ah_batch_import(eng.ctx, batch, planes, groups, words)
-            ah.ah_plan_launch(plan, eng.ctx)
-            ah.ah_plan_copy_results(plan, eng.ctx, *bufs)
-            dt = time.perf_counter() - t
-            if it > 0:
-                times.append(dt)
+        def packed_steps(overlap):
+            times = []
+            for it in range(1 + args.e2e_steps):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                if overlap:
+                    ah.ah_plan_launch_packed(plan, planes, groups, words, eng.ctx)
+                else:
+                    ah.ah_batch_import(eng.ctx, batch, planes, groups, words)
+                    ah.ah_plan_launch(plan, eng.ctx)
+                ah.ah_plan_copy_results(plan, eng.ctx, *bufs)
+                dt = time.perf_counter() - t
+                if it > 0:
+                    times.append(dt)
+            return statistics.median(times)
+
+        t_overlap, t_serial = packed_steps(True), packed_steps(False)
         e2e["from_packed_batches"] = {
-            "value": wl.total_bp / statistics.median(times) / 1e9, "unit": "Gbp/s",
+            "value": wl.total_bp / t_overlap / 1e9, "unit": "Gbp/s",
             "h2d_bytes_per_step": planes.nbytes + groups.nbytes + words.nbytes, "d2h_bytes_per_step": d2h,
-            "ms_per_step": statistics.median(times) * 1e3,
-            "path": "pinned 2-bit planes + sparse invalid words -> ah_batch_import -> ah_plan_launch -> "
-                    "ah_plan_copy_results into pinned host buffers"}
+            "ms_per_step": t_overlap * 1e3,
+            "path": "pinned 2-bit planes + sparse invalid words -> ah_plan_launch_packed (invalid words first, "
+                    "planes in 256 Mi-base chunks, each range of scan tiles scanned as its planes land) -> "
+                    "ah_plan_copy_results into pinned host buffers",
+            "import_then_step": {"value": wl.total_bp / t_serial / 1e9, "unit": "Gbp/s", "ms_per_step": t_serial * 1e3,
+                                 "path": "ah_batch_import -> ah_plan_launch -> ah_plan_copy_results"}}
         del pl_t, g_t, w_t
         if args.e2e_fasta:
             e2e["from_fasta"] = e2e_from_fasta(ah, eng, wl, batch, plan, bufs, on_device, args.e2e_steps)
@@ -560,7 +570,8 @@ def run_engine(args):
                 "vs_baseline": None, "dtype": "u32+f64", "data": "synthetic",
                 "config": dict(describe(wl), launch=f"one CUDA-graph replay of the whole step per step; autotuned scan "
                                f"{info['threads']} threads x {info['groups_per_thread']} groups, shift mode "
-                               f"{info['shift_mode']}, persistent {info['persistent']}"),
+                               f"{info['shift_mode']}, persistent {info['persistent']}, register bound "
+                               f"{info['min_blocks']} blocks/SM (0: none)"),
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": stats["kernel_launches"],
                 "gpu_launches_per_step": stats["kernel_launches"] / args.steps, "roofline": roofline,
                 "cpu_baseline": base}
@@ -708,7 +719,7 @@ def batched_record(args, steps, warmup):
                                    f"{wl.total_bp / 1e9:.2f} Gbp, {len(wl.fwd)} pairs of 17-26 nt, k=i mod 4, "
                                    "graph-captured plan (scan, compaction, pairing, Tm, extraction)",
                        "bases": wl.total_bp, "patterns": 4 * len(wl.fwd)},
-            "plan": {k: info[k] for k in ("threads", "groups_per_thread", "shift_mode", "persistent", "grid",
+            "plan": {k: info[k] for k in ("threads", "groups_per_thread", "shift_mode", "persistent", "min_blocks", "grid",
                                           "n_hits", "n_amps", "arena_bytes")},
             "plan_create_s": plan_s, "autotune_ms": info["autotune_ms"], "generate_and_pack_s": gen_s,
             "scan_kernel_ms": scan_ms, "gpu_launches_per_step": launches_per_step,

@@ -517,6 +517,7 @@ typedef struct {
   uint64_t hit_capacity, amp_capacity, arena_capacity;
   uint64_t n_hits, n_amps, n_kept, arena_bytes; /* of the last checked run */
   double autotune_ms, best_scan_ms;
+  int32_t min_blocks;   /* the scan kernel's register bound: blocks per SM it allows (0: none) */
 } ah_plan_info;
 /* Build: autotune, size every buffer from one exact run of the regular path, capture, then one
  * checked replay that grows whatever this batch overflowed (per-tile slot lists included).  The
@@ -537,6 +538,17 @@ ah_status ah_plan_launch(ah_plan* plan);
  * valid until the stream is synchronised (page-locked memory is fastest).  The plan's batch is
  * overwritten. */
 ah_status ah_plan_launch_host(ah_plan* plan, const uint8_t* h_seq, const uint64_t* h_offsets);
+/* The step on genomes stored as 2-bit batches in host memory (the layout ah_batch_export writes for
+ * the plan's batch: planes, n_invalid sparse invalid words at groups inv_groups; Abstract and Section
+ * "Implementations": AHv2 streams 2-bit batches): the invalid words are written first, then the
+ * planes cross the link in chunks of 256 Mi bases straight into the batch, and each range of scan
+ * tiles whose groups (and the group after them) have landed is scanned while the next chunk is
+ * copied; the rest of the step follows as one graph launch.  Results as after ah_plan_launch.
+ * Returns with the work enqueued on the context's stream; the host arrays must stay valid until the
+ * stream is synchronised (page-locked memory is fastest).  AH_EINVAL for a group past the batch or a
+ * plan over a slice.  The plan's batch is overwritten. */
+ah_status ah_plan_launch_packed(ah_plan* plan, const void* h_planes, uint64_t n_invalid, const uint64_t* inv_groups,
+                                const uint32_t* inv_words);
 /* Synchronise and check the last run: AH_EOVERFLOW when a capacity was exceeded (sizes in the info). */
 ah_status ah_plan_check(ah_plan* plan);
 /* Launch and check, growing capacities and re-capturing on overflow. */

@@ -54,7 +54,7 @@ class ah_plan_info(ctypes.Structure):
                 ("max_tile_sites", ctypes.c_uint32), ("hit_capacity", ctypes.c_uint64),
                 ("amp_capacity", ctypes.c_uint64), ("arena_capacity", ctypes.c_uint64), ("n_hits", ctypes.c_uint64),
                 ("n_amps", ctypes.c_uint64), ("n_kept", ctypes.c_uint64), ("arena_bytes", ctypes.c_uint64),
-                ("autotune_ms", ctypes.c_double), ("best_scan_ms", ctypes.c_double)]
+                ("autotune_ms", ctypes.c_double), ("best_scan_ms", ctypes.c_double), ("min_blocks", ctypes.c_int32)]
 
 
 class ah_request(ctypes.Structure):
@@ -169,6 +169,7 @@ SIGNATURES = {
     "ah_server_inject_alloc_failures": (_I32, [_VP, ctypes.c_int]),
     "ah_ctx_inject_alloc_failures": (_I32, [_VP, ctypes.c_int]),
     "ah_plan_launch_host": (_I32, [_VP, _VP, _VP]),
+    "ah_plan_launch_packed": (_I32, [_VP, _VP, ctypes.c_uint64, _VP, _VP]),
     "ah_fasta_pack_file": (_I32, [_VP, ctypes.c_char_p, _VP, _PVP, _PVP]),
     "ah_fastq_pack_file": (_I32, [_VP, ctypes.c_char_p, _VP, _PVP, _PVP, _PVP]),
     "ah_result_free": (None, [ctypes.POINTER(ah_result)]),
@@ -800,6 +801,15 @@ def ah_server_memory(server) -> dict:
 
 def ah_server_inject_alloc_failures(server, n: int) -> None:
     _check(load().ah_server_inject_alloc_failures(server, int(n)))
+
+
+def ah_plan_launch_packed(plan, planes: np.ndarray, inv_groups: np.ndarray, inv_words: np.ndarray, ctx=None) -> None:
+    """The plan's step on 2-bit batches in host memory (planes, sparse invalid words as ah_batch_export
+    writes them), the scan overlapping the upload."""
+    g = np.ascontiguousarray(inv_groups, dtype=np.uint64)
+    w = np.ascontiguousarray(inv_words, dtype=np.uint32)
+    _check(load().ah_plan_launch_packed(plan, planes.ctypes.data, len(g), g.ctypes.data if len(g) else None,
+                                        w.ctypes.data if len(w) else None), ctx)
 
 
 def ah_plan_launch_host(plan, h_seq: int, offsets: np.ndarray, ctx=None) -> None:

@@ -882,6 +882,38 @@ ah_status ah_batch_export(const ah_batch* b, void* planes_out, uint64_t* n_inval
   return AH_OK;
 }
 
+}  // extern "C"
+
+// the batch's invalid words from a sparse list (groups checked by the caller), enqueued on the
+// context's stream: every word cleared, then the listed ones written
+ah_status ah::upload_invalid_list(ah_ctx* ctx, uint64_t n_invalid, const uint64_t* inv_groups, const uint32_t* inv_words,
+                                  InvalidList* out) {
+  *out = InvalidList{};
+  out->n = n_invalid;
+  if (!n_invalid) return AH_OK;
+  ah_status st;
+  if ((st = dalloc(ctx, &out->groups, n_invalid)) || (st = dalloc(ctx, &out->words, n_invalid))) return st;
+  AH_CUDA(ctx, cudaMemcpyAsync(out->groups, inv_groups, n_invalid * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                               ctx->stream));
+  AH_CUDA(ctx, cudaMemcpyAsync(out->words, inv_words, n_invalid * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+  return AH_OK;
+}
+
+ah_status ah::scatter_invalid_list(ah_ctx* ctx, ah_batch* b, InvalidList* l) {
+  AH_CUDA(ctx, cudaMemsetAsync(b->invalid, 0, b->n_groups * sizeof(uint32_t), ctx->stream));
+  if (!l->n) return AH_OK;
+  k_scatter_invalid<<<(unsigned)std::min<uint64_t>((l->n + 255) / 256, 65535), 256, 0, ctx->stream>>>(
+      l->groups, l->words, l->n, b->invalid, b->n_groups, ctx->d_status);
+  launched(ctx);
+  AH_CUDA(ctx, cudaGetLastError());
+  dfree(ctx, l->groups);
+  dfree(ctx, l->words);
+  *l = InvalidList{};
+  return AH_OK;
+}
+
+extern "C" {
+
 ah_status ah_batch_import(ah_ctx* ctx, ah_batch* b, const void* planes, uint64_t n_invalid, const uint64_t* inv_groups,
                           const uint32_t* inv_words) {
   if (!ctx || !b || !planes || (n_invalid && (!inv_groups || !inv_words)) || b->view)
@@ -893,21 +925,10 @@ ah_status ah_batch_import(ah_ctx* ctx, ah_batch* b, const void* planes, uint64_t
                   (unsigned long long)i, (unsigned long long)inv_groups[i], (unsigned long long)b->n_groups);
   cudaSetDevice(ctx->device);
   AH_CUDA(ctx, cudaMemcpyAsync(b->planes, planes, b->n_groups * sizeof(uint2), cudaMemcpyHostToDevice, ctx->stream));
-  AH_CUDA(ctx, cudaMemsetAsync(b->invalid, 0, b->n_groups * sizeof(uint32_t), ctx->stream));
-  if (n_invalid) {
-    uint64_t* dg = nullptr;
-    uint32_t* dw = nullptr;
-    ah_status st;
-    if ((st = dalloc(ctx, &dg, n_invalid)) || (st = dalloc(ctx, &dw, n_invalid))) return st;
-    AH_CUDA(ctx, cudaMemcpyAsync(dg, inv_groups, n_invalid * sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
-    AH_CUDA(ctx, cudaMemcpyAsync(dw, inv_words, n_invalid * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
-    k_scatter_invalid<<<(unsigned)std::min<uint64_t>((n_invalid + 255) / 256, 65535), 256, 0, ctx->stream>>>(
-        dg, dw, n_invalid, b->invalid, b->n_groups, ctx->d_status);
-    launched(ctx);
-    AH_CUDA(ctx, cudaGetLastError());
-    dfree(ctx, dg);
-    dfree(ctx, dw);
-  }
+  InvalidList l;
+  ah_status st = upload_invalid_list(ctx, n_invalid, inv_groups, inv_words, &l);
+  if (!st) st = scatter_invalid_list(ctx, b, &l);
+  if (st) return st;
   AH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return check_status(ctx);
 }

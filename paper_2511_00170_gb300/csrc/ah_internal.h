@@ -78,6 +78,8 @@ struct ScanConfig {
   int shift_mode = 0;       // pattern-position alignment: 0 funnel shifts (ALU pipe), 1 multiply pairs
                             // (FMA pipe), 2 alternate the two
   int persistent = 0;       // 1: CTAs loop over tiles taken from a device counter
+  int min_blocks = 0;       // generated kernels: blocks per SM the register allocation must allow
+                            // (0: no bound); large circuits run more warps with a few spills
   int pairs_per_kernel = 0; // regular scans: kernels of at most this many pairs, compiled in parallel
                             // and launched one after another (0: one kernel for every pair)
 };
@@ -242,6 +244,17 @@ ah_status pack_batch_ranked(ah_ctx* ctx, uint32_t n, const uint8_t* d_seq, const
 // the stream.
 ah_status pack_host_staged(ah_ctx* ctx, ah_batch* b, const uint8_t* h_seq, const uint64_t* h_offsets,
                            const std::function<void(uint64_t)>& on_chunk);
+// The batch's invalid words from a sparse host list (groups already checked against the batch), in
+// two steps on the context's stream: the list's upload (copies), then every word cleared and the
+// listed ones written (kernels), which also releases the list.
+struct InvalidList {
+  uint64_t n = 0;
+  uint64_t* groups = nullptr;
+  uint32_t* words = nullptr;
+};
+ah_status upload_invalid_list(ah_ctx* ctx, uint64_t n_invalid, const uint64_t* inv_groups, const uint32_t* inv_words,
+                              InvalidList* out);
+ah_status scatter_invalid_list(ah_ctx* ctx, ah_batch* b, InvalidList* l);
 // read and clear the device status word (synchronises)
 ah_status check_status(ah_ctx* ctx);
 // accumulate the pending scan-node timings of graph replays into the context's counters (syncs)

@@ -482,7 +482,8 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg,
     os << "      }\n";
   }
   os << "    }\n  }\n}\n";
-  os << "extern \"C\" __global__ void __launch_bounds__(NT) ah_scan_jit(const ScanParams P) {\n";
+  os << "extern \"C\" __global__ void __launch_bounds__(NT" << (cfg.min_blocks > 0 ? ", " + std::to_string(cfg.min_blocks) : "")
+     << ") ah_scan_jit(const ScanParams P) {\n";
   if (cfg.persistent) {
     // persistent CTAs take tiles from a counter until none are left
     os << "  __shared__ u64 s_tile;\n  for (;;) {\n";

@@ -316,6 +316,14 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
         if (ms < best * 0.97) best = ms, win = c;
       }
     }
+    // a large circuit (the 8-pair batched set: 166 registers, 3 blocks of 128 threads per SM) may
+    // run faster with registers bounded for 4 blocks: more warps, a few spills to L1
+    if (!st && win.threads == 128 && ctx->scan_ops_per_group > 400) {
+      ScanConfig c = win;
+      c.min_blocks = 4;
+      double ms = 0;
+      if (!(st = time_shape(ctx, b, p, c, 2, &ms, &n_hits)) && ms < best * 0.97) best = ms, win = c;
+    }
     if (!st && prm->persistent != 0) {
       ScanConfig c = win;
       c.persistent = 1;
@@ -391,6 +399,7 @@ ah_status ah_plan_create(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, co
   pl->info.groups_per_thread = pl->cfg.groups_per_thread;
   pl->info.shift_mode = pl->cfg.shift_mode;
   pl->info.persistent = pl->cfg.persistent;
+  pl->info.min_blocks = pl->cfg.min_blocks;
   pl->info.grid = pl->grid ? pl->grid : (int32_t)pl->n_tiles;
   *out = pl;
   return AH_OK;
@@ -486,6 +495,80 @@ ah_status ah_plan_launch_host(ah_plan* pl, const uint8_t* h_seq, const uint64_t*
   on_chunk(b->n_groups);
   AH_CUDA(c, cudaGetLastError());
   AH_CUDA(c, cudaGraphLaunch(pl->post_exec, c->stream));
+  c->n_launches += pl->post_kernel_nodes + scan_launches;
+  c->scan_ops_per_group = pl->range_kern.alu_ops_per_group;
+  return AH_OK;
+}
+
+ah_status ah_plan_launch_packed(ah_plan* pl, const void* h_planes, uint64_t n_invalid, const uint64_t* inv_groups,
+                               const uint32_t* inv_words) {
+  if (!pl || !h_planes || (n_invalid && (!inv_groups || !inv_words))) return AH_EINVAL;
+  ah_ctx* c = pl->ctx;
+  ah_batch* b = const_cast<ah_batch*>(pl->b);
+  if (b->view) return fail(c, AH_EINVAL, "ah_plan_launch_packed: the plan's batch is a slice of another batch");
+  for (uint64_t i = 0; i < n_invalid; ++i)
+    if (inv_groups[i] >= b->n_groups)
+      return fail(c, AH_EINVAL, "ah_plan_launch_packed: invalid word %llu at group %llu, past the batch's %llu groups",
+                  (unsigned long long)i, (unsigned long long)inv_groups[i], (unsigned long long)b->n_groups);
+  cudaSetDevice(c->device);
+  ah_status st;
+  if (!pl->range_kern.fn) {
+    if (pl->cfg.persistent) {
+      ScanConfig cfg = pl->cfg;
+      cfg.persistent = 0;
+      if ((st = c->jit->get(c, pl->p->pats, cfg, &pl->range_kern))) return st;
+    } else {
+      pl->range_kern = pl->kern;
+    }
+  }
+  if ((st = ensure_post(pl))) return st;
+  enqueue_pre(pl, c->stream);
+  // the invalid words first (a small list), then the planes in chunks of kChunkBases bases on a
+  // copy stream straight into the batch; each range of scan tiles whose groups (and the group after
+  // them) have landed is scanned while the next chunk crosses the link
+  const uint64_t chunk = kChunkBases / kGroupBases;  // groups per copy (64 MiB of planes)
+  const uint64_t n_chunks = (b->n_groups + chunk - 1) / chunk;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ready = nullptr;
+  std::vector<cudaEvent_t> landed(n_chunks, nullptr);
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+  for (uint64_t k = 0; k < n_chunks && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&landed[k], cudaEventDisableTiming);
+  // the sparse list crosses the link first (the planes' chunks would queue it behind them on the copy
+  // engine); the plane copies wait for earlier work that may still read the planes, and the invalid
+  // words are written by kernels meanwhile (only the scans read them)
+  InvalidList il;
+  if (e == cudaSuccess && (st = upload_invalid_list(c, n_invalid, inv_groups, inv_words, &il))) e = cudaErrorUnknown;
+  if (e == cudaSuccess) e = cudaEventRecord(ready, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
+  if (e == cudaSuccess && (st = scatter_invalid_list(c, b, &il))) e = cudaErrorUnknown;
+  const uint64_t tg = (uint64_t)pl->range_kern.threads * pl->range_kern.groups_per_thread;
+  uint64_t scanned = 0, scan_launches = 0;
+  for (uint64_t k = 0; k < n_chunks && e == cudaSuccess; ++k) {
+    const uint64_t g0 = k * chunk, g1 = std::min(b->n_groups, g0 + chunk);
+    e = cudaMemcpyAsync(b->planes + g0, (const uint2*)h_planes + g0, (g1 - g0) * sizeof(uint2), cudaMemcpyHostToDevice,
+                        cs);
+    if (e == cudaSuccess) e = cudaEventRecord(landed[k], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, landed[k], 0);
+    const uint64_t upto = g1 >= b->n_groups ? b->n_groups : (g1 - 1) / tg * tg;
+    if (e == cudaSuccess && upto > scanned) {
+      launch_scan_range(c->stream, pl->range_kern, b, pl->slots, pl->tile_count, pl->slot_cap, c->d_status, scanned,
+                        upto);
+      scanned = upto;
+      ++scan_launches;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGraphLaunch(pl->post_exec, c->stream);
+  if (il.groups) dfree(c, il.groups);  // a list left over when a step before its scatter failed
+  if (il.words) dfree(c, il.words);
+  // the stream and events are released once their work is done
+  for (cudaEvent_t x : landed)
+    if (x) cudaEventDestroy(x);
+  if (ready) cudaEventDestroy(ready);
+  if (cs) cudaStreamDestroy(cs);
+  if (st) return st;
+  if (e != cudaSuccess) return fail(c, AH_ECUDA, "ah_plan_launch_packed: %s", cudaGetErrorString(e));
   c->n_launches += pl->post_kernel_nodes + scan_launches;
   c->scan_ops_per_group = pl->range_kern.alu_ops_per_group;
   return AH_OK;

@@ -215,3 +215,49 @@ def test_launch_host_matches_launch(engine, persistent):
             ah.ah_plan_free(plan)
     finally:
         ah.ah_batch_free(batch)
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_launch_packed_matches_launch(engine, persistent):
+    """The step on 2-bit batches in host memory, each range of scan tiles launched as its planes land
+    (ah_plan_launch_packed), equals the plan's replay on the batch packed from text.  The planes span
+    several copy chunks, the genomes carry runs of invalid bases (sparse invalid words), and the plan's
+    batch holds other bases before the call, so a range scanned early, or an invalid word not yet
+    written, would show."""
+    import torch
+
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Params
+
+    wl = synth.batched(n_genomes=800, n_pairs=2)
+    assert wl.total_bp > (2 * 256 << 20)
+    wl.trim, wl.fb_len, wl.rb_len = True, 10, 8
+    p = Params.from_workload(wl)
+    other = torch.full((wl.total_bp,), ord("C"), dtype=torch.uint8, pin_memory=True)
+    offs = np.ascontiguousarray(wl.offsets, dtype=np.uint64)
+    batch = engine.pack(wl.seq, wl.offsets)
+    try:
+        v = ah.ah_batch_view_get(batch)
+        pl_t = torch.empty(v["n_groups"] * 8, dtype=torch.uint8, pin_memory=True)
+        planes = pl_t.numpy().view(np.uint32).reshape(-1, 2)
+        _, groups, words = ah.ah_batch_export(batch, planes)
+        assert len(groups) > 0
+        plan = engine.plan(batch, p, with_seqs=True, persistent=persistent)
+        try:
+            ah.ah_plan_run(plan, engine.ctx)
+            ref = engine.plan_output(plan)
+            assert len(ref.amps) > 0
+            for _ in range(2):
+                ah.ah_batch_pack_range(engine.ctx, batch, 0, other.data_ptr(), offs)
+                ah.ah_plan_launch_packed(plan, planes, groups, words, engine.ctx)
+                ah.ah_plan_check(plan, engine.ctx)
+                _same(engine.plan_output(plan), ref)
+            # a group past the batch is refused before anything is enqueued
+            bad = np.array([v["n_groups"]], dtype=np.uint64)
+            with pytest.raises(ah.AhError) as e:
+                ah.ah_plan_launch_packed(plan, planes, bad, np.array([1], dtype=np.uint32), engine.ctx)
+            assert e.value.status == ah.AH_EINVAL
+        finally:
+            ah.ah_plan_free(plan)
+    finally:
+        ah.ah_batch_free(batch)
