@@ -81,7 +81,8 @@ SCAN_TRAFFIC = {
 
 # ALU-pipe work the scan kernel actually executes, from ncu on a smaller case of the same circuit
 # (smsp__inst_executed_pipe_alu.sum x 32 lanes / bases scanned, and sm__pipe_alu_cycles_active as a
-# fraction of peak), keyed by the circuit's LOP3/SHF per 32 positions.  profiles/ holds the captures.
+# fraction of peak), keyed by the circuit's LOP3/SHF per 32 positions, then by the register bound
+# (blocks per SM, 0 for none) where it changes the code.  profiles/ holds the captures.
 SCAN_PIPE = {
     # the bench pair (19/20 nt, k=3, clamp 3): plain_scale's first 200 genomes (756.5 Mbp), autotuned
     # 256 threads x 8 groups, shift mode 0; 113,306,255 ALU-pipe warp instructions per launch
@@ -93,10 +94,15 @@ SCAN_PIPE = {
     1050: {"alu_lane_ops_per_base": 2_175_188_671 * 32 / 3_487_157_421, "alu_pipe_busy": 0.790,
            "source": "ncu smsp__inst_executed_pipe_alu.sum x 32 / bases of one launch, batched 2,000 genomes "
                      "(profiles/ah_scan_jit_alu_pipe.md)"},
+    # the same circuit with registers bounded for 4 blocks per SM (128 registers, spills to L1): ptxas
+    # rematerialises some values, 2,293,188,236 ALU-pipe warp instructions per launch
+    (1050, 4): {"alu_lane_ops_per_base": 2_293_188_236 * 32 / 3_487_157_421, "alu_pipe_busy": 0.872,
+                "source": "ncu smsp__inst_executed_pipe_alu.sum x 32 / bases of one launch, batched 2,000 genomes, "
+                          "register bound 4 blocks/SM (profiles/ah_scan_jit_alu_pipe.md)"},
 }
 
 
-def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms, shape=None, sm_mhz=None):
+def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms, shape=None, sm_mhz=None, min_blocks=0):
     """ALU roofline of one scan launch.  `achieved` is algorithmic: the per-base lane-op count of the
     bit-sliced method (3 per non-clamp and 2 per clamp position of every oriented pattern, 32
     positions per lane-op) times the bases of the launch, over its CUDA-event time.  The generated
@@ -129,14 +135,14 @@ def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms, shape=None, sm_mhz=
             "hbm": {"achieved_gbs": hbm, "peak_gbs": hbm_peak,
                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "frac": hbm / hbm_peak,
                     "algorithmic_bytes_per_base": 0.25},
-            "executed": _executed(ops_per_group, bases, ms, sm_mhz)}
+            "executed": _executed(ops_per_group, bases, ms, sm_mhz, min_blocks)}
 
 
-def _executed(ops_per_group, bases, ms, sm_mhz):
+def _executed(ops_per_group, bases, ms, sm_mhz, min_blocks=0):
     """The scan's executed ALU-pipe lane-ops per second against the pipe's peak at the clock the run
     saw (152 SMs x 64 lanes x sampled SM clock): a fraction of at most 1 that says how busy the pipe
     the kernel is bound by is kept."""
-    rec = SCAN_PIPE.get(ops_per_group)
+    rec = SCAN_PIPE.get((ops_per_group, min_blocks)) if min_blocks else SCAN_PIPE.get(ops_per_group)
     if rec is None:
         return None
     mhz = sm_mhz or SM_MAX_GHZ * 1e3
@@ -450,7 +456,7 @@ def run_engine(args):
     bases_per_launch = stats["scan_bases"] / max(1, stats["scan_launches"])
     roofline = scan_roofline(stats["scan_ops_per_group"], wl.fwd, wl.rev, wl.clamp, bases_per_launch, scan_ms,
                              (info["threads"], info["groups_per_thread"], info["shift_mode"], info["persistent"]),
-                             clk.summary().get("sm_mhz"))
+                             clk.summary().get("sm_mhz"), info["min_blocks"])
     roofline["step_gbps_frac_of_alu_bound"] = value / world / (ALU_PEAK_TOPS * 1e3 / roofline["circuit"]["ops_per_base"])
 
     # end to end through the C ABI from pinned host memory: every step packs the records from host
@@ -700,7 +706,7 @@ def batched_record(args, steps, warmup):
     scan_ms = st["scan_ms"] / st["scan_launches"]
     roof = scan_roofline(st["scan_ops_per_group"], wl.fwd, wl.rev, wl.clamp, wl.total_bp, scan_ms,
                          (info["threads"], info["groups_per_thread"], info["shift_mode"], info["persistent"]),
-                         clk.summary().get("sm_mhz"))
+                         clk.summary().get("sm_mhz"), info["min_blocks"])
     pr = eng.primers(p)
     # the plain form: one launch per genome per pair
     ah.ah_ctx_stats_reset(eng.ctx)
