@@ -342,8 +342,10 @@ def fasta_into(dst, seq, offsets, width=80):
 
 
 def e2e_from_fasta(ah, eng, wl, batch, plan, bufs, on_device, steps):
-    """End to end from FASTA text in pinned host memory: ah_fasta_pack_into (copy, parse and pack on
-    the device) -> plan replay -> results into pinned host buffers."""
+    """End to end from FASTA text in pinned host memory: ah_plan_launch_fasta (the text parsed on the
+    device in chunks as it lands, the completed records packed and their tiles scanned at once, the
+    rest of the step after the last chunk) -> results into pinned host buffers; and beside it the
+    form that parses and packs all of the text before the step."""
     import numpy as np
     import torch
 
@@ -352,21 +354,32 @@ def e2e_from_fasta(ah, eng, wl, batch, plan, bufs, on_device, steps):
     t_text = torch.empty(n, dtype=torch.uint8, pin_memory=True)
     fasta_into(t_text.numpy(), seq, wl.offsets)
     del seq
-    times = []
-    for it in range(1 + steps):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        ah.ah_fasta_pack_into(eng.ctx, t_text.data_ptr(), batch, n_bytes=n)
-        ah.ah_plan_launch(plan, eng.ctx)
-        ah.ah_plan_copy_results(plan, eng.ctx, *bufs)
-        dt = time.perf_counter() - t
-        if it > 0:
-            times.append(dt)
+
+    def timed(overlap):
+        times = []
+        for it in range(1 + steps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            if overlap:
+                ah.ah_plan_launch_fasta(plan, t_text.data_ptr(), n, eng.ctx)
+            else:
+                ah.ah_fasta_pack_into(eng.ctx, t_text.data_ptr(), batch, n_bytes=n)
+                ah.ah_plan_launch(plan, eng.ctx)
+            ah.ah_plan_copy_results(plan, eng.ctx, *bufs)
+            dt = time.perf_counter() - t
+            if it > 0:
+                times.append(dt)
+        return statistics.median(times)
+
+    t_overlap, t_serial = timed(True), timed(False)
     del t_text
-    return {"value": wl.total_bp / statistics.median(times) / 1e9, "unit": "Gbp/s", "h2d_bytes_per_step": n,
-            "ms_per_step": statistics.median(times) * 1e3,
-            "path": "pinned FASTA text (80-column lines) -> ah_fasta_pack_into (one copy, parsed and packed on "
-                    "the device) -> ah_plan_launch -> ah_plan_copy_results into pinned host buffers"}
+    return {"value": wl.total_bp / t_overlap / 1e9, "unit": "Gbp/s", "h2d_bytes_per_step": n,
+            "ms_per_step": t_overlap * 1e3,
+            "path": "pinned FASTA text (80-column lines) -> ah_plan_launch_fasta (parsed on the device in 256 MiB "
+                    "chunks as they land, completed records packed and their tiles scanned at once) -> "
+                    "ah_plan_copy_results into pinned host buffers",
+            "parse_then_step": {"value": wl.total_bp / t_serial / 1e9, "unit": "Gbp/s", "ms_per_step": t_serial * 1e3,
+                                "path": "ah_fasta_pack_into -> ah_plan_launch -> ah_plan_copy_results"}}
 
 
 def run_engine(args):

@@ -549,6 +549,15 @@ ah_status ah_plan_launch_host(ah_plan* plan, const uint8_t* h_seq, const uint64_
  * plan over a slice.  The plan's batch is overwritten. */
 ah_status ah_plan_launch_packed(ah_plan* plan, const void* h_planes, uint64_t n_invalid, const uint64_t* inv_groups,
                                 const uint32_t* inv_words);
+/* The step on FASTA text (host or device memory; Abstract: the pipeline starts from FASTA files)
+ * whose records have the plan's batch's number and lengths: the text is parsed on the device in
+ * chunks as it lands (as ah_fasta_pack_into does), the record bases each chunk completes are
+ * packed into the batch at once, and each range of scan tiles whose groups (and the group after
+ * them) are packed is scanned while the next chunk crosses the link; the rest of the step follows
+ * as one graph launch.  Results as after ah_plan_launch.  AH_EINVAL when the text's records differ
+ * from the batch's (found after the last chunk; the results are then not valid).  Synchronises
+ * the stream between chunks; the plan's batch is overwritten. */
+ah_status ah_plan_launch_fasta(ah_plan* plan, const char* text, uint64_t n_bytes);
 /* Synchronise and check the last run: AH_EOVERFLOW when a capacity was exceeded (sizes in the info). */
 ah_status ah_plan_check(ah_plan* plan);
 /* Launch and check, growing capacities and re-capturing on overflow. */

@@ -170,6 +170,7 @@ SIGNATURES = {
     "ah_ctx_inject_alloc_failures": (_I32, [_VP, ctypes.c_int]),
     "ah_plan_launch_host": (_I32, [_VP, _VP, _VP]),
     "ah_plan_launch_packed": (_I32, [_VP, _VP, ctypes.c_uint64, _VP, _VP]),
+    "ah_plan_launch_fasta": (_I32, [_VP, _VP, ctypes.c_uint64]),
     "ah_fasta_pack_file": (_I32, [_VP, ctypes.c_char_p, _VP, _PVP, _PVP]),
     "ah_fastq_pack_file": (_I32, [_VP, ctypes.c_char_p, _VP, _PVP, _PVP, _PVP]),
     "ah_result_free": (None, [ctypes.POINTER(ah_result)]),
@@ -810,6 +811,12 @@ def ah_plan_launch_packed(plan, planes: np.ndarray, inv_groups: np.ndarray, inv_
     w = np.ascontiguousarray(inv_words, dtype=np.uint32)
     _check(load().ah_plan_launch_packed(plan, planes.ctypes.data, len(g), g.ctypes.data if len(g) else None,
                                         w.ctypes.data if len(w) else None), ctx)
+
+
+def ah_plan_launch_fasta(plan, text_ptr: int, n_bytes: int, ctx=None) -> None:
+    """The plan's step on FASTA text at address text_ptr (host or device), records matching the
+    plan's batch; the parse, the packing and the scan overlap the upload."""
+    _check(load().ah_plan_launch_fasta(plan, text_ptr, int(n_bytes)), ctx)
 
 
 def ah_plan_launch_host(plan, h_seq: int, offsets: np.ndarray, ctx=None) -> None:

@@ -738,6 +738,37 @@ ah_status pack_host_staged(ah_ctx* ctx, ah_batch* b, const uint8_t* h_seq, const
   }
   return pack_records(ctx, b, 0, b->n_records, src.data(), true, on_chunk);
 }
+
+ah_status pack_concat_upto(ah_ctx* ctx, ah_batch* b, const uint8_t* d_src, const uint64_t* start, uint64_t to,
+                           ConcatCursor* cur, uint64_t* done_groups) {
+  std::vector<PackItem> items;
+  while (cur->r < b->n_records) {
+    const uint32_t r = cur->r;
+    const uint64_t s = start[r], len = b->h_rec_len[r];
+    uint64_t avail = to > s ? std::min(len, to - s) : 0;
+    if (avail < len) avail &= ~uint64_t(31);  // a record not yet complete: whole groups only
+    if (len == 0) {
+      add_items(items, b, r, 0, 0, 0);  // its padding groups (nothing is read)
+    } else if (avail > cur->off) {
+      add_items(items, b, r, cur->off, avail, s + cur->off);
+      cur->off = avail;
+    }
+    if (cur->off < len) break;
+    cur->r++, cur->off = 0;
+  }
+  *done_groups = cur->r < b->n_records ? b->h_rec_group[cur->r] + cur->off / 32 : b->n_groups;
+  if (items.empty()) return AH_OK;
+  PackItem* d_items = nullptr;
+  ah_status st = dalloc(ctx, &d_items, items.size());
+  if (st) return st;
+  // pageable source: the copy is staged before the call returns, so `items` may go
+  AH_CUDA(ctx, cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(PackItem), cudaMemcpyHostToDevice,
+                               ctx->stream));
+  launch_pack(ctx->stream, d_src, d_items, items.data(), items.size(), b, ctx);
+  AH_CUDA(ctx, cudaGetLastError());
+  dfree(ctx, d_items);
+  return AH_OK;
+}
 }  // namespace ah
 
 extern "C" {

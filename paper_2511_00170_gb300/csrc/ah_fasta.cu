@@ -511,8 +511,11 @@ namespace {
 
 // Parse and pack: into a new batch (*batch_out) or, with `into`, into an existing batch whose record
 // lengths must equal the text's.
+// hook (into mode only): after each chunk, the compacted record bases so far (the first record's first
+// base at d_concat, `avail` of them, last = false), and once all are in and the records checked
+// against the batch (last = true); it then packs them instead of the final pack
 ah_status fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint32_t* genome_ids, ah_batch* into,
-                     ah_batch** batch_out, ah_fasta** names_out) {
+                     ah_batch** batch_out, ah_fasta** names_out, const FastaChunkHook* hook = nullptr) {
   cudaSetDevice(ctx->device);
   cudaPointerAttributes pa;
   const bool on_device = cudaPointerGetAttributes(&pa, text) == cudaSuccess &&
@@ -533,6 +536,7 @@ ah_status fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint
   cudaStream_t cs = nullptr;
   std::vector<cudaEvent_t> landed;
   uint64_t total_seq = 0, total_hdr = 0;
+  uint64_t rank0 = ~0ull;  // the first record's first base in the compacted text (hook only)
   auto cleanup = [&] {
     if (cs) {
       cudaStreamSynchronize(cs);
@@ -636,6 +640,10 @@ ah_status fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint
       launched(ctx);
       total_seq += c_seq;
       total_hdr += c_hdr;
+      if (hook && total_hdr) {
+        if (rank0 == ~0ull && (st = read_u64(ctx, seq_rank, &rank0))) break;
+        if ((st = (*hook)(compact + rank0, total_seq - rank0, false))) break;
+      }
     }
     if (st) break;
     if (total_hdr == 0) {
@@ -663,7 +671,8 @@ ah_status fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint
         st = fail(ctx, AH_EINVAL, "ah_fasta_pack_into: the text's records differ from the batch's in number or length");
         break;
       }
-      st = ah_batch_pack_range(ctx, into, 0, n_rec, compact + h_rank[0], offs.data());
+      st = hook ? (*hook)(compact + h_rank[0], offs[n_rec], true)
+                : ah_batch_pack_range(ctx, into, 0, n_rec, compact + h_rank[0], offs.data());
     } else {
       st = ah_pack_batch_device(ctx, n_rec, compact + h_rank[0], offs.data(), genome_ids, batch_out);
     }
@@ -712,6 +721,10 @@ ah_status fasta_pack(ah_ctx* ctx, const char* text, uint64_t n_bytes, const uint
 }
 
 }  // namespace
+
+ah_status fasta_pack_hooked(ah_ctx* ctx, const char* text, uint64_t n_bytes, ah_batch* into, const FastaChunkHook& hook) {
+  return fasta_pack(ctx, text, n_bytes, nullptr, into, nullptr, nullptr, &hook);
+}
 }  // namespace ah
 
 extern "C" {

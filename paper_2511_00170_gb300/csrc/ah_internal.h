@@ -255,6 +255,21 @@ struct InvalidList {
 ah_status upload_invalid_list(ah_ctx* ctx, uint64_t n_invalid, const uint64_t* inv_groups, const uint32_t* inv_words,
                               InvalidList* out);
 ah_status scatter_invalid_list(ah_ctx* ctx, ah_batch* b, InvalidList* l);
+// The batch's records laid end to end in device memory (record r's bases at d_src[start[r],
+// start[r] + its length)), packed into the batch as they become available: every call packs what
+// lies below `to` and the cursor has not packed yet (a record not complete in whole groups only),
+// and returns in done_groups the groups written so far from the batch's first (all of a record's
+// padding groups once it is complete).  Enqueued on the context's stream.
+struct ConcatCursor {
+  uint32_t r = 0;     // the first record not packed completely
+  uint64_t off = 0;   // its bases packed
+};
+ah_status pack_concat_upto(ah_ctx* ctx, ah_batch* b, const uint8_t* d_src, const uint64_t* start, uint64_t to,
+                           ConcatCursor* cur, uint64_t* done_groups);
+// FASTA text into an existing batch (as ah_fasta_pack_into) with a hook that packs the compacted
+// record bases chunk by chunk (see fasta_pack in ah_fasta.cu)
+using FastaChunkHook = std::function<ah_status(const uint8_t* d_concat, uint64_t avail, bool last)>;
+ah_status fasta_pack_hooked(ah_ctx* ctx, const char* text, uint64_t n_bytes, ah_batch* into, const FastaChunkHook& hook);
 // read and clear the device status word (synchronises)
 ah_status check_status(ah_ctx* ctx);
 // accumulate the pending scan-node timings of graph replays into the context's counters (syncs)

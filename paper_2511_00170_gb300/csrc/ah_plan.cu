@@ -574,6 +574,53 @@ ah_status ah_plan_launch_packed(ah_plan* pl, const void* h_planes, uint64_t n_in
   return AH_OK;
 }
 
+ah_status ah_plan_launch_fasta(ah_plan* pl, const char* text, uint64_t n_bytes) {
+  if (!pl || !text || n_bytes == 0) return AH_EINVAL;
+  ah_ctx* c = pl->ctx;
+  ah_batch* b = const_cast<ah_batch*>(pl->b);
+  if (b->view) return fail(c, AH_EINVAL, "ah_plan_launch_fasta: the plan's batch is a slice of another batch");
+  cudaSetDevice(c->device);
+  ah_status st;
+  if (!pl->range_kern.fn) {
+    if (pl->cfg.persistent) {
+      ScanConfig cfg = pl->cfg;
+      cfg.persistent = 0;
+      if ((st = c->jit->get(c, pl->p->pats, cfg, &pl->range_kern))) return st;
+    } else {
+      pl->range_kern = pl->kern;
+    }
+  }
+  if ((st = ensure_post(pl))) return st;
+  enqueue_pre(pl, c->stream);
+  // the records laid end to end as the parser compacts them
+  std::vector<uint64_t> start(b->n_records + 1, 0);
+  for (uint32_t r = 0; r < b->n_records; ++r) start[r + 1] = start[r] + b->h_rec_len[r];
+  ConcatCursor cur;
+  const uint64_t tg = (uint64_t)pl->range_kern.threads * pl->range_kern.groups_per_thread;
+  uint64_t scanned = 0, scan_launches = 0;
+  // after each chunk: pack the record bases it completed, then scan the tiles whose groups (and the
+  // group after them) are packed, while the next chunk of text crosses the link
+  const FastaChunkHook hook = [&](const uint8_t* d_concat, uint64_t avail, bool last) -> ah_status {
+    uint64_t done = 0;
+    ah_status s = pack_concat_upto(c, b, d_concat, start.data(), last ? start[b->n_records] : avail, &cur, &done);
+    if (s) return s;
+    const uint64_t upto = done >= b->n_groups ? b->n_groups : (done > 0 ? (done - 1) / tg * tg : 0);
+    if (upto > scanned) {
+      launch_scan_range(c->stream, pl->range_kern, b, pl->slots, pl->tile_count, pl->slot_cap, c->d_status, scanned,
+                        upto);
+      scanned = upto;
+      ++scan_launches;
+    }
+    return AH_OK;
+  };
+  if ((st = fasta_pack_hooked(c, text, n_bytes, b, hook))) return st;
+  AH_CUDA(c, cudaGetLastError());
+  AH_CUDA(c, cudaGraphLaunch(pl->post_exec, c->stream));
+  c->n_launches += pl->post_kernel_nodes + scan_launches;
+  c->scan_ops_per_group = pl->range_kern.alu_ops_per_group;
+  return AH_OK;
+}
+
 ah_status ah_plan_check(ah_plan* pl) {
   if (!pl) return AH_EINVAL;
   ah_ctx* c = pl->ctx;

@@ -261,3 +261,64 @@ def test_launch_packed_matches_launch(engine, persistent):
             ah.ah_plan_free(plan)
     finally:
         ah.ah_batch_free(batch)
+
+
+def _fasta_text(seq, offsets, width=80):
+    """The records as FASTA, `width`-column sequence lines (uint8 array)."""
+    parts = []
+    for r in range(len(offsets) - 1):
+        s = seq[int(offsets[r]):int(offsets[r + 1])]
+        L = len(s)
+        full = (L // width) * width
+        body = np.full(full + full // width, 10, dtype=np.uint8)
+        if full:
+            body.reshape(-1, width + 1)[:, :width] = s[:full].reshape(-1, width)
+        tail = np.concatenate([s[full:], [10]]).astype(np.uint8) if L > full else np.zeros(0, np.uint8)
+        parts += [np.frombuffer(b">genome_%d synthetic\n" % r, dtype=np.uint8), body, tail]
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_launch_fasta_matches_launch(engine, on_device):
+    """The step on FASTA text, parsed chunk by chunk as it lands with the completed records packed and
+    their tiles scanned at once (ah_plan_launch_fasta), equals the plan's replay on the batch packed
+    beforehand; the text spans four copy chunks, and the plan's batch holds other bases before the
+    call.  A text missing a record is refused."""
+    import torch
+
+    from paper_2511_00170_gb300 import ah
+    from paper_2511_00170_gb300.pipeline import Params
+
+    wl = synth.batched(n_genomes=600, n_pairs=2)
+    wl.trim, wl.fb_len, wl.rb_len = True, 10, 8
+    p = Params.from_workload(wl)
+    text = _fasta_text(wl.seq, wl.offsets)
+    assert len(text) > 3 * (256 << 20)
+    if on_device:
+        t_text = torch.from_numpy(text).to("cuda:0")
+    else:
+        t_text = torch.empty(len(text), dtype=torch.uint8, pin_memory=True)
+        t_text.numpy()[:] = text
+    other = torch.full((wl.total_bp,), ord("G"), dtype=torch.uint8, pin_memory=True)
+    offs = np.ascontiguousarray(wl.offsets, dtype=np.uint64)
+    batch = engine.pack(wl.seq, wl.offsets)
+    try:
+        plan = engine.plan(batch, p, with_seqs=True)
+        try:
+            ah.ah_plan_run(plan, engine.ctx)
+            ref = engine.plan_output(plan)
+            assert len(ref.amps) > 0
+            for _ in range(2):
+                ah.ah_batch_pack_range(engine.ctx, batch, 0, other.data_ptr(), offs)
+                ah.ah_plan_launch_fasta(plan, t_text.data_ptr(), len(text), engine.ctx)
+                ah.ah_plan_check(plan, engine.ctx)
+                _same(engine.plan_output(plan), ref)
+            last = int(np.flatnonzero(text == ord(">"))[-1])   # the text without its last record
+            with pytest.raises(ah.AhError) as e:
+                ah.ah_plan_launch_fasta(plan, t_text.data_ptr(), last, engine.ctx)
+            assert e.value.status == ah.AH_EINVAL
+            ah.ah_ctx_synchronize(engine.ctx)
+        finally:
+            ah.ah_plan_free(plan)
+    finally:
+        ah.ah_batch_free(batch)
