@@ -45,7 +45,17 @@ def engine_for(args, device):
 
     eng = Engine(device)
     ah.ah_ctx_set_tm_kernel(eng.ctx, TM_KERNELS[getattr(args, "tm_kernel", "generated")])
+    fixed = getattr(args, "scan_fixed", "")
+    if fixed:
+        t, g, mode, mb, w = (int(x) for x in fixed.split(","))
+        ah.ah_ctx_set_scan_config(eng.ctx, t, g, 256, mode)
+        ah.ah_ctx_set_scan_circuit(eng.ctx, mb, w)
     return eng
+
+
+def autotune(args):
+    """Plans choose their scan kernel by timing candidates unless --scan-fixed names one."""
+    return not getattr(args, "scan_fixed", "")
 
 
 def measured_peaks():
@@ -75,7 +85,7 @@ def alg_ops_per_base(fwd, rev, clamp):
 # positions of its circuit, threads, groups per thread, shift mode, persistent.  A kernel not in
 # this table reports traffic null.
 SCAN_TRAFFIC = {
-    (188, 256, 8, 0, 0): (189_573_376 + 1_627_392) / 756_529_120,
+    (186, 256, 8, 0, 0): (189_561_088 + 1_595_904) / 756_529_120,
 }
 
 
@@ -85,18 +95,23 @@ SCAN_TRAFFIC = {
 # (blocks per SM, 0 for none) where it changes the code.  profiles/ holds the captures.
 SCAN_PIPE = {
     # the bench pair (19/20 nt, k=3, clamp 3): plain_scale's first 200 genomes (756.5 Mbp), autotuned
-    # 256 threads x 8 groups, shift mode 0; 113,306,255 ALU-pipe warp instructions per launch
-    188: {"alu_lane_ops_per_base": 113_306_255 * 32 / 756_529_120, "alu_pipe_busy": 0.967,
+    # 256 threads x 8 groups, shift mode 0; 109,810,167 ALU-pipe warp instructions per launch
+    186: {"alu_lane_ops_per_base": 109_810_167 * 32 / 756_529_120, "alu_pipe_busy": 0.966,
           "source": "ncu smsp__inst_executed_pipe_alu.sum x 32 / bases of one launch, plain_scale 200 genomes "
                     "(profiles/ah_scan_jit_alu_pipe.md)"},
-    # the batched set (8 pairs = 32 patterns, k = i mod 4): its first 2,000 genomes (3.49 Gbp),
-    # 128 threads x 8 groups, shift mode 0; 2,175,188,671 ALU-pipe warp instructions per launch
-    1050: {"alu_lane_ops_per_base": 2_175_188_671 * 32 / 3_487_157_421, "alu_pipe_busy": 0.790,
+    # the batched set (8 pairs = 32 patterns, k = i mod 4): its first 2,000 genomes (3.49 Gbp), the
+    # kernel the autotuner keeps: 128 threads x 8 groups, shift mode 0, registers bounded for 4 blocks
+    # per SM, phase split drawn for 4,096 windows per vote (996 LOP3/SHF per 32 positions);
+    # 2,178,723,827 ALU-pipe warp instructions per launch
+    (996, 4): {"alu_lane_ops_per_base": 2_178_723_827 * 32 / 3_487_157_421, "alu_pipe_busy": 0.876,
+               "source": "ncu smsp__inst_executed_pipe_alu.sum x 32 / bases of one launch, batched 2,000 genomes, "
+                         "register bound 4 blocks/SM, split for 4,096 windows (profiles/ah_scan_jit_alu_pipe.md)"},
+    # the circuit split for 1,024 windows per vote (1,030 LOP3/SHF per 32 positions), without and with
+    # the register bound: 2,215,146,059 and 2,205,943,674 ALU-pipe warp instructions per launch
+    1030: {"alu_lane_ops_per_base": 2_215_146_059 * 32 / 3_487_157_421, "alu_pipe_busy": 0.783,
            "source": "ncu smsp__inst_executed_pipe_alu.sum x 32 / bases of one launch, batched 2,000 genomes "
                      "(profiles/ah_scan_jit_alu_pipe.md)"},
-    # the same circuit with registers bounded for 4 blocks per SM (128 registers, spills to L1): ptxas
-    # rematerialises some values, 2,293,188,236 ALU-pipe warp instructions per launch
-    (1050, 4): {"alu_lane_ops_per_base": 2_293_188_236 * 32 / 3_487_157_421, "alu_pipe_busy": 0.872,
+    (1030, 4): {"alu_lane_ops_per_base": 2_205_943_674 * 32 / 3_487_157_421, "alu_pipe_busy": 0.863,
                 "source": "ncu smsp__inst_executed_pipe_alu.sum x 32 / bases of one launch, batched 2,000 genomes, "
                           "register bound 4 blocks/SM (profiles/ah_scan_jit_alu_pipe.md)"},
 }
@@ -419,7 +434,7 @@ def run_engine(args):
 
     # the whole step as one autotuned, graph-captured plan (sized by one exact run of the step)
     with_seqs = getattr(wl, "extract", True)
-    plan = eng.plan(batch, params, with_seqs=with_seqs, autotune=True, persistent=-1)
+    plan = eng.plan(batch, params, with_seqs=with_seqs, autotune=autotune(args), persistent=-1)
     info = ah.ah_plan_info_get(plan)
 
     def one_step():
@@ -590,7 +605,8 @@ def run_engine(args):
                 "config": dict(describe(wl), launch=f"one CUDA-graph replay of the whole step per step; autotuned scan "
                                f"{info['threads']} threads x {info['groups_per_thread']} groups, shift mode "
                                f"{info['shift_mode']}, persistent {info['persistent']}, register bound "
-                               f"{info['min_blocks']} blocks/SM (0: none)"),
+                               f"{info['min_blocks']} blocks/SM (0: none), phase split drawn for {info['vote_windows']} windows "
+                               f"per warp vote"),
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": stats["kernel_launches"],
                 "gpu_launches_per_step": stats["kernel_launches"] / args.steps, "roofline": roofline,
                 "cpu_baseline": base}
@@ -625,7 +641,7 @@ def dense_record(args, steps, warmup):
     torch.cuda.empty_cache()
     params = Params.from_workload(wl)
     stream = torch.cuda.ExternalStream(ah.ah_ctx_stream(eng.ctx))
-    plan = eng.plan(batch, params, with_seqs=getattr(wl, "extract", True), autotune=True, persistent=-1)
+    plan = eng.plan(batch, params, with_seqs=getattr(wl, "extract", True), autotune=autotune(args), persistent=-1)
     for _ in range(max(3, warmup)):
         ah.ah_plan_launch(plan, eng.ctx)
     ah.ah_ctx_synchronize(eng.ctx)
@@ -695,7 +711,7 @@ def batched_record(args, steps, warmup):
     p = Params(wl.fwd, wl.rev, wl.k, wl.clamp, wl.min_len, wl.max_len, wl.orient_mask)
     stream = torch.cuda.ExternalStream(ah.ah_ctx_stream(eng.ctx))
     t0 = time.perf_counter()
-    plan = eng.plan(batch, p, with_seqs=True, autotune=True, persistent=-1)
+    plan = eng.plan(batch, p, with_seqs=True, autotune=autotune(args), persistent=-1)
     plan_s = time.perf_counter() - t0
     info = ah.ah_plan_info_get(plan)
     for _ in range(max(3, warmup)):
@@ -738,8 +754,8 @@ def batched_record(args, steps, warmup):
                                    f"{wl.total_bp / 1e9:.2f} Gbp, {len(wl.fwd)} pairs of 17-26 nt, k=i mod 4, "
                                    "graph-captured plan (scan, compaction, pairing, Tm, extraction)",
                        "bases": wl.total_bp, "patterns": 4 * len(wl.fwd)},
-            "plan": {k: info[k] for k in ("threads", "groups_per_thread", "shift_mode", "persistent", "min_blocks", "grid",
-                                          "n_hits", "n_amps", "arena_bytes")},
+            "plan": {k: info[k] for k in ("threads", "groups_per_thread", "shift_mode", "persistent", "min_blocks",
+                                          "vote_windows", "grid", "n_hits", "n_amps", "arena_bytes")},
             "plan_create_s": plan_s, "autotune_ms": info["autotune_ms"], "generate_and_pack_s": gen_s,
             "scan_kernel_ms": scan_ms, "gpu_launches_per_step": launches_per_step,
             "roofline": roof,
@@ -945,6 +961,9 @@ def main():
     ap.add_argument("--serve-burst", type=int, default=100, help="sub-record: requests offered at 200 req/s")
     ap.add_argument("--tm-kernel", default="generated", choices=sorted(TM_KERNELS),
                     help="degenerate-site Tm: the kernel generated per primer set, or the built-in one")
+    ap.add_argument("--scan-fixed", default="",
+                    help="threads,groups,shift_mode,min_blocks,vote_windows: plans take this scan kernel "
+                         "instead of autotuning (for profiling one kernel)")
     ap.add_argument("--scan-mode", type=int, default=2,
                     help="serving: 0 generated scan kernels, 1 generic kernel, 2 generic while compiling")
     args = ap.parse_args()

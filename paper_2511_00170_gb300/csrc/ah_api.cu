@@ -530,6 +530,15 @@ ah_status ah_ctx_set_scan_config(ah_ctx* ctx, int threads, int groups_per_thread
   return AH_OK;
 }
 
+ah_status ah_ctx_set_scan_circuit(ah_ctx* ctx, int min_blocks, int vote_windows) {
+  if (!ctx) return AH_EINVAL;
+  if (min_blocks < 0 || min_blocks > 32 || vote_windows < 1 || vote_windows > (1 << 20))
+    return fail(ctx, AH_EINVAL, "ah_ctx_set_scan_circuit: values out of range");
+  ctx->scan_cfg.min_blocks = min_blocks;
+  ctx->scan_cfg.vote_windows = vote_windows;
+  return AH_OK;
+}
+
 ah_status ah_ctx_set_pairs_per_kernel(ah_ctx* ctx, int pairs) {
   if (!ctx) return AH_EINVAL;
   if (pairs < 0 || pairs > 256) return fail(ctx, AH_EINVAL, "ah_ctx_set_pairs_per_kernel: 0..256");

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstring>
 #include <atomic>
@@ -191,10 +192,10 @@ void count_ge(Emitter& E, std::map<int, std::vector<Val>>& bits, int wsat, int T
 
 // Failure word of one pattern: bit set iff a clamp position mismatches or the non-clamp mismatches
 // reach k+1.  Phase A (emitted with every pattern's, sharing shifted planes) covers the clamp and the
-// counted positions most likely to mismatch, until a window survives them with probability below
-// kSurvive; phase B adds the rest to the same carry-save sums.  The kernel runs phase B only when
-// some window of the warp survived phase A (a warp vote): for the others the answer is already
-// "fail", so the result is exact either way.
+// h counted positions most likely to mismatch; phase B adds the rest to the same carry-save sums.
+// The kernel runs phase B only when some window of the warp survived phase A (a warp vote): for the
+// others the answer is already "fail", so the result is exact for any h.  h is the one with the
+// least expected work (choose_split).
 struct PatternCode {
   Val fail_a;                               // failure word after phase A (final without phase B)
   bool has_b = false;
@@ -204,52 +205,62 @@ struct PatternCode {
   int ops_b = 0;
 };
 
-constexpr double kSurvive = 1.5e-4;
-
-PatternCode gen_pattern(Emitter& EA, int* tmp, const Pattern& P, std::map<std::pair<int, int>, bool>& used_a) {
+// One pattern's evaluated positions: the clamp, and the counted ones most likely to mismatch first,
+// with surv[i] the probability that a window of uniform random bases passes the clamp and has fewer
+// than T = k + 1 mismatches among the first i counted positions.
+struct PatternIn {
   struct In {
     Val x;
     int kind, j;
     double p_mis;
   };
   std::vector<In> clamp, counted;
+  int T = 1, wsat = 1;
+  std::vector<double> surv;
+};
+
+PatternIn pattern_in(const Pattern& P) {
+  PatternIn S;
   for (int j = 0; j < P.len; ++j) {
     int kind;
     bool inv;
     if (!set_plane(P.set[j], &kind, &inv)) continue;  // N never mismatches
     // mismatch bit: the complement of the match plane; its probability on uniform bases
     const int n_bases = __builtin_popcount(P.set[j]);
-    In in{Val{plane_name(kind, j), !inv, false}, kind, j, (4 - n_bases) / 4.0};
-    (j >= P.clamp_lo && j < P.clamp_hi ? clamp : counted).push_back(in);
+    PatternIn::In in{Val{plane_name(kind, j), !inv, false}, kind, j, (4 - n_bases) / 4.0};
+    (j >= P.clamp_lo && j < P.clamp_hi ? S.clamp : S.counted).push_back(in);
   }
-  const int T = P.k + 1;  // failing count
-  int wsat = 1;
-  while (wsat < T) wsat *= 2;
-  // phase A: the clamp and the most mismatch-prone counted positions, until survival < kSurvive
-  std::stable_sort(counted.begin(), counted.end(), [](const In& a, const In& b) { return a.p_mis > b.p_mis; });
+  S.T = P.k + 1;  // failing count
+  while (S.wsat < S.T) S.wsat *= 2;
+  std::stable_sort(S.counted.begin(), S.counted.end(),
+                   [](const PatternIn::In& a, const PatternIn::In& b) { return a.p_mis > b.p_mis; });
   double p_clamp = 1.0;
-  for (const In& c : clamp) p_clamp *= 1.0 - c.p_mis;
-  size_t h = counted.size();
-  {
-    std::vector<double> dist(T + 1, 0.0);  // P(count = c) for c < T, dist[T]: count >= T
-    dist[0] = 1.0;
-    for (size_t i = 0; i < counted.size(); ++i) {
-      std::vector<double> nd(T + 1, 0.0);
-      for (int c = 0; c <= T; ++c) {
-        nd[std::min(T, c + 1)] += dist[c] * counted[i].p_mis;
-        nd[c] += dist[c] * (1.0 - counted[i].p_mis);
-      }
-      dist.swap(nd);
-      const double survive = p_clamp * (1.0 - dist[T]);
-      if (survive < kSurvive && counted.size() - (i + 1) >= 3) {
-        h = i + 1;
-        break;
-      }
+  for (const auto& c : S.clamp) p_clamp *= 1.0 - c.p_mis;
+  std::vector<double> dist(S.T + 1, 0.0);  // P(count = c) for c < T, dist[T]: count >= T
+  dist[0] = 1.0;
+  S.surv.push_back(p_clamp);
+  for (const auto& c : S.counted) {
+    std::vector<double> nd(S.T + 1, 0.0);
+    for (int v = 0; v <= S.T; ++v) {
+      nd[std::min(S.T, v + 1)] += dist[v] * c.p_mis;
+      nd[v] += dist[v] * (1.0 - c.p_mis);
     }
+    dist.swap(nd);
+    S.surv.push_back(p_clamp * (1.0 - dist[S.T]));
   }
+  return S;
+}
+
+// the pattern's code with phase A over the clamp and counted[0, h); used_a collects the shifted
+// planes phase A reads
+PatternCode emit_pattern(Emitter& EA, int* tmp, const PatternIn& S, size_t h,
+                         std::map<std::pair<int, int>, bool>& used_a) {
+  const auto& clamp = S.clamp;
+  const auto& counted = S.counted;
+  const int T = S.T, wsat = S.wsat;
   PatternCode out;
   std::vector<Val> fail_terms;
-  for (const In& c : clamp) {
+  for (const auto& c : clamp) {
     used_a[{c.kind, c.j}] = true;
     fail_terms.push_back(c.x);
   }
@@ -307,6 +318,49 @@ PatternCode gen_pattern(Emitter& EA, int* tmp, const Pattern& P, std::map<std::p
   EA.tmp = EB.tmp;  // temporaries stay unique across phases
   *tmp = EB.tmp;
   return out;
+}
+
+// instructions of the vote and its branch, paid by every warp whenever the pattern has a phase B
+constexpr double kVoteOps = 2.0;
+
+// Phase A's length h with the least expected ALU work per group of 32 positions: phase A's LOP3
+// and the funnel shifts of planes no earlier pattern reads, plus phase B's times the probability
+// that one of the `windows` windows a vote covers survives phase A (on uniform random bases; one
+// vote covers 32 lanes x 32 positions, and larger values stand for genomes whose composition lets
+// more windows through).  Phase B keeps at least 3 positions; h = all counted positions means a
+// single phase.
+size_t choose_split(const PatternIn& S, const std::map<std::pair<int, int>, bool>& used, double windows) {
+  const size_t n = S.counted.size();
+  if ((int)n < S.T) return n;
+  auto shifts_new = [&](const std::pair<int, int>& pl, const std::map<std::pair<int, int>, bool>& have) {
+    return pl.second > 0 && !have.count(pl) ? 1 : 0;
+  };
+  size_t best_h = n;
+  double best = 0.0;
+  bool have = false;
+  for (size_t h = 0; h <= n; ++h) {
+    if (h < n && n - h < 3) continue;
+    Emitter E;
+    int tmp = 0;
+    std::map<std::pair<int, int>, bool> u = used;
+    const PatternCode pc = emit_pattern(E, &tmp, S, h, u);
+    double cost = E.ops;
+    for (const auto& pl : u) cost += used.count(pl.first) ? 0 : (pl.first.second > 0);
+    if (pc.has_b) {
+      double b = pc.ops_b;
+      for (const auto& pl : pc.planes_b) b += shifts_new(pl, u);
+      const double p_any = -std::expm1(windows * std::log1p(-std::min(S.surv[h], 1.0 - 1e-12)));
+      cost += kVoteOps + p_any * b;
+    }
+    if (!have || cost < best - 1e-9) best = cost, best_h = h, have = true;
+  }
+  return best_h;
+}
+
+PatternCode gen_pattern(Emitter& EA, int* tmp, const Pattern& P, std::map<std::pair<int, int>, bool>& used_a,
+                        double windows) {
+  const PatternIn S = pattern_in(P);
+  return emit_pattern(EA, tmp, S, choose_split(S, used_a, windows), used_a);
 }
 
 const char* kPrelude = R"(
@@ -403,7 +457,7 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg,
   std::map<std::pair<int, int>, bool> used;
   std::vector<PatternCode> pc(Q);
   int tmpc = 0;
-  for (int q = 0; q < Q; ++q) pc[q] = gen_pattern(E, &tmpc, pats[q], used);
+  for (int q = 0; q < Q; ++q) pc[q] = gen_pattern(E, &tmpc, pats[q], used, std::max(1, cfg.vote_windows));
   bool kind_used[K_COUNT] = {};
   for (auto& u : used) kind_used[u.first.first] = true;
   for (auto& c : pc)

@@ -360,7 +360,14 @@ std::string tm_chain_source(const std::vector<std::string>& primers, int* weight
   os << "    if (pr >= " << primers.size() << "u) return false;\n";
   os << "    return chain_site_tm(T, W, ws, Chains{pr, code ^ 0xAAAAAAAAAAAAAAAAull, &R}, L, R, P.some_gc(L), tm);\n"
         "  }\n};\n";
-  os << "extern \"C\" __global__ void __launch_bounds__(kTmThreads, 4) ah_tm_jit(\n"
+  // blocks per SM the register allocation must allow: as many as shared memory holds (228 KB per SM,
+  // 1 KB of it reserved per block), from 4 to 8; more resident warps hide the chains' latencies (the
+  // 64 registers of 8 blocks cost a few dozen bytes of spills)
+  os << "constexpr int kTmJitSmem = 4 * (kTmTabWords + 2 * kTmSlots + " << words
+     << " * kTmThreads) + (int)sizeof(TmRun) + 4 + 4 * kTmBins + 1024;\n"
+        "constexpr int kTmJitFit = 228 * 1024 / kTmJitSmem;\n"
+        "constexpr int kTmJitBlocks = kTmJitFit < 4 ? 4 : kTmJitFit > 8 ? 8 : kTmJitFit;\n";
+  os << "extern \"C\" __global__ void __launch_bounds__(kTmThreads, kTmJitBlocks) ah_tm_jit(\n"
         "    const ah_hit* __restrict__ hits, uint64_t n, const uint2* __restrict__ planes,\n"
         "    const uint64_t* __restrict__ rec_group, const uint8_t* __restrict__ plen, const uint4* __restrict__ pmask,\n"
         "    const TmRun Rp, double* __restrict__ out, uint32_t* __restrict__ defer, const uint64_t* __restrict__ d_n,\n"

@@ -94,6 +94,9 @@ def test_context_settings_refused(env):
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_scan_config, ctx, 100, 4, 256, 0)   # not a multiple of 32
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_scan_config, ctx, 256, 4, 300, 0)   # slots not a power of 2
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_scan_config, ctx, 256, 4, 256, 3)   # no such shift mode
+    _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_scan_circuit, ctx, 33, 1024)        # bound too high
+    _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_scan_circuit, ctx, 0, 0)            # no windows
+    _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_scan_circuit, ctx, 0, (1 << 20) + 1)
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_pairs_per_kernel, ctx, 257)
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_generic_scan, ctx, 4)
     _still_works(ah, ctx, wl, batch)

@@ -123,6 +123,20 @@ def test_scan_shapes_and_shift_modes(engine, threads, gpt, slots, shift):
         ah.ah_ctx_set_scan_config(engine.ctx, 256, 4, 256, 0)
 
 
+@pytest.mark.parametrize("min_blocks,windows", [(0, 1), (0, 64), (4, 4096), (0, 1 << 20), (8, 1024)])
+def test_scan_circuit_splits(engine, min_blocks, windows):
+    """The circuit's phase split drawn for any number of windows per vote (1: the shortest first
+    phase, 2^20: one phase for most patterns) and any register bound gives the same sites."""
+    from paper_2511_00170_gb300 import ah
+
+    ah.ah_ctx_set_scan_circuit(engine.ctx, min_blocks, windows)
+    try:
+        _run_both(engine, synth.batched(n_genomes=12, len_lo=2e3, len_hi=3e5, n_pairs=4))
+        _run_both(engine, _random_case(2000 + windows % 97 + min_blocks))
+    finally:
+        ah.ah_ctx_set_scan_circuit(engine.ctx, 0, 1024)
+
+
 def test_several_pairs(engine):
     wl = synth.batched(n_genomes=40, len_lo=2e3, len_hi=2e5, n_pairs=8)
     _run_both(engine, wl)
