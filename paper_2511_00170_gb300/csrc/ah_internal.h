@@ -311,7 +311,6 @@ void launch_scan_kernel(cudaStream_t s, const ScanKernel& k, const ah_batch* b, 
 void launch_scan_range(cudaStream_t s, const ScanKernel& k, const ah_batch* b, uint64_t* slots, uint32_t* tile_count,
                        uint32_t cap, uint32_t* status, uint64_t g0, uint64_t g1);
 void launch_tile_max(cudaStream_t s, const uint32_t* tile_count, uint64_t n_tiles, uint32_t* out);
-size_t prepare_tile_sort(uint32_t cap, int* warps_out);
 // sorts every tile's keys and counts them per pair; big: n_tiles + 1 words of device scratch, used
 // when cap exceeds 256; returns the kernels launched
 int launch_tile_sort(cudaStream_t s, uint64_t* slots, const uint32_t* tile_count, uint32_t cap, uint64_t n_tiles,

@@ -384,33 +384,60 @@ struct ScanParams {
 };
 static __device__ __forceinline__ u32 fshr(u32 a, u32 b, u32 s) { return __funnelshift_r(a, b, s); }
 
-// Candidate bits: an exact re-check by a second method (the window's bases against per-position set
-// masks, mismatches counted by popcount), the invalid-base test, and the slot append.  Every record
-// is followed by at least one invalid padding base, so a window that leaves its record holds an
-// invalid base and the one test covers record bounds too.
-static __device__ __noinline__ void emit(u32 h, int q, u64 g, uint2 a, uint2 b, const ScanParams& P) {
+// Candidate bits of up to four patterns q0 .. q0+3 (words c[0..3], 0 where a pattern is absent): an
+// exact re-check by a second method (the window's bases against per-position set masks, mismatches
+// counted by popcount), the invalid-base test, and the slot append.  Every record is followed by at
+// least one invalid padding base, so a window that leaves its record holds an invalid base and the
+// one test covers record bounds too.  The lanes that reach this call together work in rounds, one
+// candidate bit per lane per round, and the lanes of one tile take their slots with one atomic add
+// per round.  EMIT_INLINE: inlined for small pattern sets (frequent sites then cost no call and
+// no saving of the loop's registers), a call for large ones (whose loop keeps many registers live).
+static __device__ EMIT_INLINE void emit4(u32 c0, u32 c1, u32 c2, u32 c3, int q0, u64 g, uint2 a, uint2 b,
+                                          const ScanParams& P) {
+  const u32 mask = __activemask();
+  const u32 lane = threadIdx.x & 31u;
   const u64 tile = g / P.tile_groups, tile_pos = tile * P.tile_groups * 32ull;
+  const u32 peers = __match_any_sync(mask, tile);
+  const u32 leader = __ffs(peers) - 1, below = peers & ((1u << lane) - 1u);
   const u64 lo64 = (u64)a.x | ((u64)b.x << 32), hi64 = (u64)a.y | ((u64)b.y << 32);
   const u64 inv64 = (u64)P.invalid[g] | ((u64)P.invalid[g + 1] << 32);
-  const int L = PLEN[q];
-  const u32 wm = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
-  const u32 mA = MSET[q][0], mC = MSET[q][1], mT = MSET[q][2], mG = MSET[q][3];
-  while (h) {
-    const int i = __ffs(h) - 1;
-    h &= h - 1;
-    const u32 wl = (u32)(lo64 >> i), wh = (u32)(hi64 >> i);  // base j of the window at bit j
-    const u32 match = (~wl & ~wh & mA) | (wl & ~wh & mC) | (~wl & wh & mT) | (wl & wh & mG);
-    const u32 mis = ~match & wm;
-    const int mism = __popc(mis);
-    if ((mis & PCLAMP[q]) || mism > PK[q]) {
-      atomicOr(P.status, 1u);
-      continue;
+  u32 w[4] = {c0, c1, c2, c3};
+  for (;;) {
+    int k = -1, i = 0;
+    for (int t = 0; t < 4; ++t)
+      if (k < 0 && w[t]) {
+        k = t;
+        i = __ffs(w[t]) - 1;
+        w[t] &= w[t] - 1;
+      }
+    if (!__any_sync(mask, k >= 0)) break;
+    bool ok = false;
+    u64 key = 0;
+    if (k >= 0) {
+      const int q = q0 + k;
+      const int L = PLEN[q];
+      const u32 wm = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
+      const u32 wl = (u32)(lo64 >> i), wh = (u32)(hi64 >> i);  // base j of the window at bit j
+      const u32 match = (~wl & ~wh & MSET[q][0]) | (wl & ~wh & MSET[q][1]) | (~wl & wh & MSET[q][2]) |
+                        (wl & wh & MSET[q][3]);
+      const u32 mis = ~match & wm;
+      const int mism = __popc(mis);
+      if ((mis & PCLAMP[q]) || mism > PK[q]) {
+        atomicOr(P.status, 1u);
+      } else if (!((u32)(inv64 >> i) & wm)) {
+        const u64 pos = g * 32ull + (u64)i;
+        key = ((u64)PPAIR[q] << 48) | ((pos - tile_pos) << 16) | ((u64)PORIENT[q] << 8) | (u64)mism;
+        ok = true;
+      }
     }
-    if ((u32)(inv64 >> i) & wm) continue;
-    const u64 pos = g * 32ull + (u64)i;
-    const u64 key = ((u64)PPAIR[q] << 48) | ((pos - tile_pos) << 16) | ((u64)PORIENT[q] << 8) | (u64)mism;
-    const u32 idx = atomicAdd(P.tile_count + tile, 1u);
-    if (idx < P.slot_cap) P.slots[tile * (u64)P.slot_cap + idx] = key;
+    const u32 vb = __ballot_sync(mask, ok) & peers;
+    u32 base = 0;
+    if (lane == leader && vb) base = atomicAdd(P.tile_count + tile, (u32)__popc(vb));
+    base = __shfl_sync(mask, base, leader);
+    if (ok) {
+      const u32 idx = base + __popc(vb & below);
+      if (idx < P.slot_cap) P.slots[tile * (u64)P.slot_cap + idx] = key;
+    }
   }
 }
 )";
@@ -450,6 +477,9 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg,
     for (int j = p.clamp_lo; j < p.clamp_hi; ++j) m |= 1u << j;
     return m;
   });
+  // the emission routine is inlined at up to two call sites (8 patterns): measured on GB300, the
+  // dense-site workload (4 patterns) scanned 5 % faster inlined, the 32-pattern set 5 % slower
+  os << "#define EMIT_INLINE " << (Q <= 8 ? "__forceinline__" : "__noinline__") << "\n";
   os << kPrelude;
 
   // body: per group of 32 positions
@@ -531,9 +561,9 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg,
     int q1 = std::min(Q, q0 + 4);
     os << "      if (__builtin_expect((";
     for (int q = q0; q < q1; ++q) os << (q > q0 ? " & " : "") << "f" << q;
-    os << ") != 0xffffffffu, 0)) {\n";
-    for (int q = q0; q < q1; ++q) os << "        if (~f" << q << ") emit(~f" << q << ", " << q << ", g, a, b, P);\n";
-    os << "      }\n";
+    os << ") != 0xffffffffu, 0)) emit4(";
+    for (int q = q0; q < q0 + 4; ++q) os << (q < q1 ? "~f" + std::to_string(q) : std::string("0u")) << ", ";
+    os << q0 << ", g, a, b, P);\n";
   }
   os << "    }\n  }\n}\n";
   os << "extern \"C\" __global__ void __launch_bounds__(NT" << (cfg.min_blocks > 0 ? ", " + std::to_string(cfg.min_blocks) : "")

@@ -178,7 +178,6 @@ ah_status capture(ah_plan* pl) {
   AH_CUDA(c, cudaStreamSynchronize(s));
   ah_status dst = drain_timings(c);  // the ring's events are recorded afresh from here on
   if (dst) return dst;
-  prepare_tile_sort(pl->slot_cap, nullptr);
   AH_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   enqueue_step(pl, s);
   cudaGraph_t g = nullptr;
@@ -447,7 +446,6 @@ ah_status ensure_post(ah_plan* pl) {
   ah_ctx* c = pl->ctx;
   cudaStream_t s = c->stream;
   AH_CUDA(c, cudaStreamSynchronize(s));
-  prepare_tile_sort(pl->slot_cap, nullptr);
   AH_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   enqueue_post(pl, s);
   cudaGraph_t g = nullptr;

@@ -49,32 +49,67 @@ __device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* a, uint32_t 
   return lo;
 }
 
-// Sort one tile's keys (one warp, bitonic in the warp's shared-memory buffer), write them back and
-// count them per pair (pair in the top 16 bits).
-__device__ __forceinline__ void sort_tile(uint64_t* tk, uint32_t n, uint64_t* buf, uint64_t t, uint64_t n_tiles,
-                                          uint32_t n_pairs, uint32_t* tile_pair_count, int lane) {
-  if (n > 1) {
-    uint32_t m = 2;
-    while (m < n) m <<= 1;
-    for (uint32_t i = lane; i < m; i += 32) buf[i] = i < n ? tk[i] : ~0ull;
-    __syncwarp();
-    for (uint32_t k = 2; k <= m; k <<= 1) {
-      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        for (uint32_t i = lane; i < m; i += 32) {
-          const uint32_t ixj = i ^ j;
-          if (ixj > i) {
-            const uint64_t a = buf[i], b = buf[ixj];
-            const bool up = (i & k) == 0;
-            if ((a > b) == up) {
-              buf[i] = b;
-              buf[ixj] = a;
-            }
+// Bitonic sort of 32 R keys held by one warp, key r * 32 + lane in v[r] of that lane: exchanges
+// between lanes (distance below 32) by shuffles, between a lane's own registers (distance 32 and
+// above) in place.  The loops have constant bounds, so every register index is resolved at compile
+// time.
+template <int R>
+__device__ __forceinline__ void warp_bitonic(uint64_t (&v)[R], int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int d = j >> 5;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (r & d) continue;
+          const bool up = (((r << 5) | lane) & k) == 0;
+          const uint64_t x = v[r], y = v[r | d];
+          if ((x > y) == up) {
+            v[r] = y;
+            v[r | d] = x;
           }
         }
-        __syncwarp();
+      } else {
+        const bool lower = (lane & j) == 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint64_t o = __shfl_xor_sync(0xffffffffu, v[r], j);
+          const bool up = (((r << 5) | lane) & k) == 0;
+          const bool take_min = lower == up;
+          v[r] = take_min ? (o < v[r] ? o : v[r]) : (o > v[r] ? o : v[r]);
+        }
       }
     }
-    for (uint32_t i = lane; i < n; i += 32) tk[i] = buf[i];
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void sort_regs(uint64_t* tk, uint32_t n, int lane) {
+  uint64_t v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t i = (uint32_t)(r << 5) | (uint32_t)lane;
+    v[r] = i < n ? tk[i] : ~0ull;
+  }
+  warp_bitonic<R>(v, lane);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t i = (uint32_t)(r << 5) | (uint32_t)lane;
+    if (i < n) tk[i] = v[r];
+  }
+}
+
+// Sort one tile's n <= kSmallTile keys in the registers of one warp, write them back and count them
+// per pair (pair in the top 16 bits).
+__device__ __forceinline__ void sort_tile(uint64_t* tk, uint32_t n, uint64_t t, uint64_t n_tiles, uint32_t n_pairs,
+                                          uint32_t* tile_pair_count, int lane) {
+  if (n > 1) {
+    if (n <= 32) sort_regs<1>(tk, n, lane);
+    else if (n <= 64) sort_regs<2>(tk, n, lane);
+    else if (n <= 128) sort_regs<4>(tk, n, lane);
+    else sort_regs<8>(tk, n, lane);
     __syncwarp();
   }
   const uint32_t p_first = (uint32_t)(tk[0] >> 48), p_last = (uint32_t)(tk[n - 1] >> 48);
@@ -85,14 +120,13 @@ __device__ __forceinline__ void sort_tile(uint64_t* tk, uint32_t n, uint64_t* bu
   }
 }
 
-constexpr uint32_t kSmallTile = 256;  // keys a tile may hold to be sorted by the small-buffer kernel
+constexpr uint32_t kSmallTile = 256;  // keys a tile may hold to be sorted by one warp in registers
 
-// One warp per tile with a kSmallTile-key buffer per warp (high occupancy).  Tiles holding more
-// keys are appended to big[1..] (count in big[0]) for k_tile_sort_big.
+// One warp per tile.  Tiles holding more keys are appended to big[1..] (count in big[0]) for
+// k_tile_sort_big.
 __global__ void k_tile_sort(uint64_t* __restrict__ slots, const uint32_t* __restrict__ tile_count, uint32_t cap,
                             uint64_t n_tiles, uint32_t n_pairs, uint32_t* __restrict__ tile_pair_count,
                             uint32_t* __restrict__ big) {
-  __shared__ uint64_t sm[8 * kSmallTile];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (t >= n_tiles) return;
@@ -102,20 +136,51 @@ __global__ void k_tile_sort(uint64_t* __restrict__ slots, const uint32_t* __rest
     if (lane == 0) big[1 + atomicAdd(big, 1u)] = (uint32_t)t;
     return;
   }
-  sort_tile(slots + t * cap, n, sm + warp * kSmallTile, t, n_tiles, n_pairs, tile_pair_count, lane);
+  sort_tile(slots + t * cap, n, t, n_tiles, n_pairs, tile_pair_count, lane);
 }
 
-// The listed tiles, one warp each with a buffer of cap_pow2 keys, over a fixed grid.
-__global__ void k_tile_sort_big(uint64_t* __restrict__ slots, const uint32_t* __restrict__ tile_count, uint32_t cap,
-                                uint32_t cap_pow2, uint64_t n_tiles, uint32_t n_pairs,
-                                uint32_t* __restrict__ tile_pair_count, const uint32_t* __restrict__ big) {
-  extern __shared__ uint64_t sm_big[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+// The listed tiles, one block of kBigSortThreads each (a tile holds at most kBigSortKeys keys): the
+// keys, padded to a power of two m, are sorted by a bitonic network in shared memory, every thread
+// taking m / 2 / kBigSortThreads compare-exchanges of each of its log m (log m + 1) / 2 stages.
+// A fixed grid strides over the list.
+constexpr int kBigSortThreads = 256;
+constexpr uint32_t kBigSortKeys = 4096;
+__global__ void __launch_bounds__(kBigSortThreads) k_tile_sort_big(uint64_t* __restrict__ slots,
+                                                                   const uint32_t* __restrict__ tile_count,
+                                                                   uint32_t cap, uint64_t n_tiles, uint32_t n_pairs,
+                                                                   uint32_t* __restrict__ tile_pair_count,
+                                                                   const uint32_t* __restrict__ big) {
+  __shared__ uint64_t buf[kBigSortKeys];
   const uint32_t n_big = big[0];
-  for (uint32_t i = blockIdx.x * warps + warp; i < n_big; i += gridDim.x * warps) {
+  for (uint32_t i = blockIdx.x; i < n_big; i += gridDim.x) {
     const uint64_t t = big[1 + i];
-    sort_tile(slots + t * cap, min(tile_count[t], cap), sm_big + (uint64_t)warp * cap_pow2, t, n_tiles, n_pairs,
-              tile_pair_count, lane);
+    const uint32_t n = min(min(tile_count[t], cap), kBigSortKeys);
+    uint64_t* tk = slots + t * cap;
+    uint32_t m = 2;
+    while (m < n) m <<= 1;
+    for (uint32_t e = threadIdx.x; e < m; e += kBigSortThreads) buf[e] = e < n ? tk[e] : ~0ull;
+    __syncthreads();
+    for (uint32_t k = 2; k <= m; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t e = threadIdx.x; e < m / 2; e += kBigSortThreads) {
+          const uint32_t lo = ((e & ~(j - 1)) << 1) | (e & (j - 1)), hi = lo + j;  // lo has bit j clear
+          const uint64_t x = buf[lo], y = buf[hi];
+          if ((x > y) == ((lo & k) == 0)) {
+            buf[lo] = y;
+            buf[hi] = x;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (uint32_t e = threadIdx.x; e < n; e += kBigSortThreads) tk[e] = buf[e];
+    const uint32_t p_first = (uint32_t)(buf[0] >> 48), p_last = (uint32_t)(buf[n - 1] >> 48);
+    for (uint32_t p = p_first + threadIdx.x; p <= p_last && p < n_pairs; p += kBigSortThreads) {
+      const uint32_t lo = lower_bound_u64(buf, n, (uint64_t)p << 48);
+      const uint32_t hi = lower_bound_u64(buf, n, (uint64_t)(p + 1) << 48);
+      if (hi > lo) tile_pair_count[(uint64_t)p * n_tiles + t] = hi - lo;
+    }
+    __syncthreads();  // the buffer is refilled for the next tile
   }
 }
 
@@ -361,24 +426,6 @@ void launch_tile_max(cudaStream_t s, const uint32_t* tile_count, uint64_t n_tile
                                                                                                      out);
 }
 
-// warps per block and shared memory of the large-tile sort for slot lists of `cap` keys
-size_t big_sort_shape(uint32_t cap, int* warps_out, uint32_t* cap_pow2_out) {
-  uint32_t cap_pow2 = 2;
-  while (cap_pow2 < cap) cap_pow2 <<= 1;
-  const int warps = (int)std::max<uint32_t>(1, std::min<uint32_t>(8, 16384 / cap_pow2));
-  if (warps_out) *warps_out = warps;
-  if (cap_pow2_out) *cap_pow2_out = cap_pow2;
-  return (size_t)warps * cap_pow2 * sizeof(uint64_t);
-}
-
-// sets the large-tile sort's shared-memory attribute when it exceeds the default (call before any
-// stream capture, which does not allow it)
-size_t prepare_tile_sort(uint32_t cap, int* warps_out) {
-  const size_t smem = big_sort_shape(cap, warps_out, nullptr);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_tile_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return smem;
-}
-
 // sort every tile's keys and count them per pair; `big` (n_tiles + 1 words) is needed only when
 // cap > kSmallTile
 int launch_tile_sort(cudaStream_t s, uint64_t* slots, const uint32_t* tile_count, uint32_t cap, uint64_t n_tiles,
@@ -386,12 +433,8 @@ int launch_tile_sort(cudaStream_t s, uint64_t* slots, const uint32_t* tile_count
   if (cap > kSmallTile) cudaMemsetAsync(big, 0, sizeof(uint32_t), s);
   k_tile_sort<<<(unsigned)((n_tiles + 7) / 8), 256, 0, s>>>(slots, tile_count, cap, n_tiles, n_pairs, tpc, big);
   if (cap <= kSmallTile) return 1;
-  int warps = 1;
-  uint32_t cap_pow2 = 2;
-  const size_t smem = big_sort_shape(cap, &warps, &cap_pow2);
-  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n_tiles + warps - 1) / warps,
-                                                                           4ull * (uint64_t)std::max(1, sm_count)));
-  k_tile_sort_big<<<grid, warps * 32, smem, s>>>(slots, tile_count, cap, cap_pow2, n_tiles, n_pairs, tpc, big);
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, 4ull * (uint64_t)std::max(1, sm_count)));
+  k_tile_sort_big<<<grid, kBigSortThreads, 0, s>>>(slots, tile_count, cap, n_tiles, n_pairs, tpc, big);
   return 2;
 }
 
@@ -658,7 +701,6 @@ ah_status scan_sites(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, bool p
   AH_CUDA(ctx, cudaMemsetAsync(tpc, 0, n_cells * sizeof(uint32_t), ctx->stream));
   uint32_t* big = nullptr;  // tiles with more than 256 keys, sorted by the large-buffer kernel
   if (cap > 256 && (st = dalloc(ctx, &big, n_tiles + 1))) return st;
-  prepare_tile_sort(cap, nullptr);
   const int sorts = launch_tile_sort(ctx->stream, slots, tile_count, cap, n_tiles, n_pairs, tpc, big, ctx->sm_count);
   for (int i = 0; i < sorts; ++i) launched(ctx);
   AH_CUDA(ctx, cudaGetLastError());

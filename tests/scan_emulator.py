@@ -70,18 +70,15 @@ def failure_words(src, lo0, hi0, lo1, hi1, phase_a=None):
                 if (lut >> idx) & 1:
                     r |= (a if idx & 4 else M ^ a) & (b if idx & 2 else M ^ b) & (c if idx & 1 else M ^ c)
             env[m.group(1)] = r
-    out = []
+    # the candidate words handed to the emission routine, four patterns per call (~f<q>, or 0u where
+    # the block of four has no pattern)
+    names = []
+    for args in re.findall(r"emit4\(([^;]*?), \d+, g, a, b, P\)", src):
+        names += [x[1:] for x in (a.strip() for a in args.split(",")) if x != "0u"]
     if phase_a is not None:
-        for f in re.findall(r"if \(~(\(~\w+\)|\w+)\) emit", src):
+        for f in names:
             phase_a.append(env.get("phase_a_" + f, env.get(f)))
-    for f in re.findall(r"if \(~(\(~\w+\)|\w+)\) emit", src):
-        if f.startswith("(~"):
-            out.append(M ^ env[f[2:-1]])
-        elif f == "0u":
-            out.append(zero)
-        else:
-            out.append(env[f])
-    return out
+    return [env[f] for f in names]
 
 
 def exact_failure_words(primers, k, clamp, lo0, hi0, lo1, hi1):
