@@ -47,9 +47,9 @@ def engine_for(args, device):
     ah.ah_ctx_set_tm_kernel(eng.ctx, TM_KERNELS[getattr(args, "tm_kernel", "generated")])
     fixed = getattr(args, "scan_fixed", "")
     if fixed:
-        t, g, mode, mb, w = (int(x) for x in fixed.split(","))
+        t, g, mode, mb, w, queue = (int(x) for x in fixed.split(","))
         ah.ah_ctx_set_scan_config(eng.ctx, t, g, 256, mode)
-        ah.ah_ctx_set_scan_circuit(eng.ctx, mb, w)
+        ah.ah_ctx_set_scan_circuit(eng.ctx, mb, w, queue)
     return eng
 
 
@@ -606,7 +606,7 @@ def run_engine(args):
                                f"{info['threads']} threads x {info['groups_per_thread']} groups, shift mode "
                                f"{info['shift_mode']}, persistent {info['persistent']}, register bound "
                                f"{info['min_blocks']} blocks/SM (0: none), phase split drawn for {info['vote_windows']} windows "
-                               f"per warp vote"),
+                               f"per warp vote, candidate queue {info['emit_queue']}"),
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": stats["kernel_launches"],
                 "gpu_launches_per_step": stats["kernel_launches"] / args.steps, "roofline": roofline,
                 "cpu_baseline": base}
@@ -755,7 +755,7 @@ def batched_record(args, steps, warmup):
                                    "graph-captured plan (scan, compaction, pairing, Tm, extraction)",
                        "bases": wl.total_bp, "patterns": 4 * len(wl.fwd)},
             "plan": {k: info[k] for k in ("threads", "groups_per_thread", "shift_mode", "persistent", "min_blocks",
-                                          "vote_windows", "grid", "n_hits", "n_amps", "arena_bytes")},
+                                          "vote_windows", "emit_queue", "grid", "n_hits", "n_amps", "arena_bytes")},
             "plan_create_s": plan_s, "autotune_ms": info["autotune_ms"], "generate_and_pack_s": gen_s,
             "scan_kernel_ms": scan_ms, "gpu_launches_per_step": launches_per_step,
             "roofline": roof,
@@ -962,7 +962,7 @@ def main():
     ap.add_argument("--tm-kernel", default="generated", choices=sorted(TM_KERNELS),
                     help="degenerate-site Tm: the kernel generated per primer set, or the built-in one")
     ap.add_argument("--scan-fixed", default="",
-                    help="threads,groups,shift_mode,min_blocks,vote_windows: plans take this scan kernel "
+                    help="threads,groups,shift_mode,min_blocks,vote_windows,emit_queue: plans take this scan kernel "
                          "instead of autotuning (for profiling one kernel)")
     ap.add_argument("--scan-mode", type=int, default=2,
                     help="serving: 0 generated scan kernels, 1 generic kernel, 2 generic while compiling")

@@ -152,11 +152,13 @@ ah_status ah_ctx_inject_alloc_failures(ah_ctx* ctx, int n);
 ah_status ah_ctx_set_scan_config(ah_ctx* ctx, int threads, int groups_per_thread, int slot_cap, int shift_mode);
 /* The generated scan circuit of this context (tuning knobs, results do not depend on them):
  * min_blocks, the blocks per SM the kernel's register allocation must allow (0: no bound, else
- * 1..32), and vote_windows, the windows per warp vote the split between the circuit's two phases
- * is drawn for (1..1048576; 1024 = 32 lanes x 32 positions on uniform random bases, larger values
- * give a longer first phase).  A plan without autotuning takes them as set here; the autotuner
- * starts from them.  AH_EINVAL outside those ranges. */
-ah_status ah_ctx_set_scan_circuit(ah_ctx* ctx, int min_blocks, int vote_windows);
+ * 1..32); vote_windows, the windows per warp vote the split between the circuit's two phases is
+ * drawn for (1..1048576; 1024 = 32 lanes x 32 positions on uniform random bases, larger values
+ * give a longer first phase); emit_queue, 0 to emit candidate sites where they are found, 1 to
+ * queue them per warp and emit them with the whole warp after its block (faster where sites are
+ * dense).  A plan without autotuning takes them as set here; the autotuner starts from them.
+ * AH_EINVAL outside those ranges. */
+ah_status ah_ctx_set_scan_circuit(ah_ctx* ctx, int min_blocks, int vote_windows, int emit_queue);
 
 /* ------------------------------------------------------------------------------------------ */
 /* 1. packing                                                                                   */
@@ -527,6 +529,7 @@ typedef struct {
   int32_t min_blocks;   /* the scan kernel's register bound: blocks per SM it allows (0: none) */
   int32_t vote_windows; /* windows per warp vote the scan circuit's phase split was drawn for (1024:
                            uniform random bases; the autotuner also tries 4x that) */
+  int32_t emit_queue;   /* 1: candidate sites queued per warp and emitted after its block */
 } ah_plan_info;
 /* Build: autotune, size every buffer from one exact run of the regular path, capture, then one
  * checked replay that grows whatever this batch overflowed (per-tile slot lists included).  The

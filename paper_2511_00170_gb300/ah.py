@@ -55,7 +55,7 @@ class ah_plan_info(ctypes.Structure):
                 ("amp_capacity", ctypes.c_uint64), ("arena_capacity", ctypes.c_uint64), ("n_hits", ctypes.c_uint64),
                 ("n_amps", ctypes.c_uint64), ("n_kept", ctypes.c_uint64), ("arena_bytes", ctypes.c_uint64),
                 ("autotune_ms", ctypes.c_double), ("best_scan_ms", ctypes.c_double), ("min_blocks", ctypes.c_int32),
-                ("vote_windows", ctypes.c_int32)]
+                ("vote_windows", ctypes.c_int32), ("emit_queue", ctypes.c_int32)]
 
 
 class ah_request(ctypes.Structure):
@@ -105,7 +105,7 @@ SIGNATURES = {
     "ah_tm_kernel_check": (_I32, [_VP, _U32, ctypes.c_int, ctypes.c_char_p, ctypes.c_uint64]),
     "ah_ctx_set_timing": (_I32, [_VP, _I32]),
     "ah_ctx_set_scan_config": (_I32, [_VP, _I32, _I32, _I32, _I32]),
-    "ah_ctx_set_scan_circuit": (_I32, [_VP, _I32, _I32]),
+    "ah_ctx_set_scan_circuit": (_I32, [_VP, _I32, _I32, _I32]),
     "ah_pack_batch": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
     "ah_pack_batch_device": (_I32, [_VP, _U32, _VP, _VP, _VP, _PVP]),
     "ah_fasta_pack": (_I32, [_VP, _VP, _U64, _VP, _PVP, _PVP]),
@@ -270,10 +270,11 @@ def ah_ctx_set_scan_config(ctx, threads: int = 256, groups_per_thread: int = 4, 
     _check(load().ah_ctx_set_scan_config(ctx, threads, groups_per_thread, slot_cap, shift_mode), ctx)
 
 
-def ah_ctx_set_scan_circuit(ctx, min_blocks: int = 0, vote_windows: int = 1024) -> None:
-    """Register bound (blocks per SM, 0 none) and the phase split's windows per vote of the generated
-    scan circuit; a plan without autotuning uses them as set."""
-    _check(load().ah_ctx_set_scan_circuit(ctx, min_blocks, vote_windows), ctx)
+def ah_ctx_set_scan_circuit(ctx, min_blocks: int = 0, vote_windows: int = 1024, emit_queue: int = 0) -> None:
+    """Register bound (blocks per SM, 0 none), the phase split's windows per vote and the candidate
+    queue (1) or direct emission (0) of the generated scan kernel; a plan without autotuning uses
+    them as set."""
+    _check(load().ah_ctx_set_scan_circuit(ctx, min_blocks, vote_windows, emit_queue), ctx)
 
 
 # ------------------------------------------------------------------------------------------ packing

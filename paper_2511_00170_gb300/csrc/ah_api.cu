@@ -530,12 +530,14 @@ ah_status ah_ctx_set_scan_config(ah_ctx* ctx, int threads, int groups_per_thread
   return AH_OK;
 }
 
-ah_status ah_ctx_set_scan_circuit(ah_ctx* ctx, int min_blocks, int vote_windows) {
+ah_status ah_ctx_set_scan_circuit(ah_ctx* ctx, int min_blocks, int vote_windows, int emit_queue) {
   if (!ctx) return AH_EINVAL;
-  if (min_blocks < 0 || min_blocks > 32 || vote_windows < 1 || vote_windows > (1 << 20))
+  if (min_blocks < 0 || min_blocks > 32 || vote_windows < 1 || vote_windows > (1 << 20) || emit_queue < 0 ||
+      emit_queue > 1)
     return fail(ctx, AH_EINVAL, "ah_ctx_set_scan_circuit: values out of range");
   ctx->scan_cfg.min_blocks = min_blocks;
   ctx->scan_cfg.vote_windows = vote_windows;
+  ctx->scan_cfg.emit_queue = emit_queue;
   return AH_OK;
 }
 

@@ -82,6 +82,8 @@ struct ScanConfig {
                             // (0: no bound); large circuits run more warps with a few spills
   int pairs_per_kernel = 0; // regular scans: kernels of at most this many pairs, compiled in parallel
                             // and launched one after another (0: one kernel for every pair)
+  int emit_queue = 0;       // generated kernels: 0 candidates emitted where found, 1 queued per warp and
+                            // emitted by the whole warp after its block (dense sites)
   int vote_windows = 1024;  // generated kernels: windows the phase-split cost model takes one warp vote
                             // to cover (1024 = 32 lanes x 32 positions on uniform random bases; larger
                             // values weigh phase two as if windows survived phase one more often)

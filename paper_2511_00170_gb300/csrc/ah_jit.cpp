@@ -384,21 +384,56 @@ struct ScanParams {
 };
 static __device__ __forceinline__ u32 fshr(u32 a, u32 b, u32 s) { return __funnelshift_r(a, b, s); }
 
-// Candidate bits of up to four patterns q0 .. q0+3 (words c[0..3], 0 where a pattern is absent): an
-// exact re-check by a second method (the window's bases against per-position set masks, mismatches
-// counted by popcount), the invalid-base test, and the slot append.  Every record is followed by at
-// least one invalid padding base, so a window that leaves its record holds an invalid base and the
-// one test covers record bounds too.  The lanes that reach this call together work in rounds, one
-// candidate bit per lane per round, and the lanes of one tile take their slots with one atomic add
-// per round.  EMIT_INLINE: inlined for small pattern sets (frequent sites then cost no call and
-// no saving of the loop's registers), a call for large ones (whose loop keeps many registers live).
+// One candidate bit (window at bit i of group g, pattern q): an exact re-check by a second method
+// (the window's bases against per-position set masks, mismatches counted by popcount), then the
+// invalid-base test.  Every record is followed by at least one invalid padding base, so a window
+// that leaves its record holds an invalid base and the one test covers record bounds too.  True
+// with the window's slot key when it is a site; a disagreement with the circuit sets the status.
+static __device__ __forceinline__ bool check_bit(int q, int i, u64 lo64, u64 hi64, u64 inv64, u64 g, u64 tile_pos,
+                                                 const ScanParams& P, u64* key) {
+  const int L = PLEN[q];
+  const u32 wm = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
+  const u32 wl = (u32)(lo64 >> i), wh = (u32)(hi64 >> i);  // base j of the window at bit j
+  const u32 match = (~wl & ~wh & MSET[q][0]) | (wl & ~wh & MSET[q][1]) | (~wl & wh & MSET[q][2]) |
+                    (wl & wh & MSET[q][3]);
+  const u32 mis = ~match & wm;
+  const int mism = __popc(mis);
+  if ((mis & PCLAMP[q]) || mism > PK[q]) {
+    atomicOr(P.status, 1u);
+    return false;
+  }
+  if ((u32)(inv64 >> i) & wm) return false;
+  const u64 pos = g * 32ull + (u64)i;
+  *key = ((u64)PPAIR[q] << 48) | ((pos - tile_pos) << 16) | ((u64)PORIENT[q] << 8) | (u64)mism;
+  return true;
+}
+
+// Slot append for the lanes of `mask` whose ok is set: the lanes of one tile (peers, led by
+// leader) take their slots with one atomic add and write at their rank among them.
+static __device__ __forceinline__ void append(u32 mask, u32 peers, u32 leader, bool ok, u64 key, u64 tile,
+                                              const ScanParams& P) {
+  const u32 lane = threadIdx.x & 31u;
+  const u32 vb = __ballot_sync(mask, ok) & peers;
+  u32 base = 0;
+  if (lane == leader && vb) base = atomicAdd(P.tile_count + tile, (u32)__popc(vb));
+  base = __shfl_sync(mask, base, leader);
+  if (ok) {
+    const u32 idx = base + __popc(vb & ((1u << lane) - 1u));
+    if (idx < P.slot_cap) P.slots[tile * (u64)P.slot_cap + idx] = key;
+  }
+}
+
+// Candidate words of up to four patterns q0 .. q0+3 (c[0..3], 0 where absent) handled at once by
+// the lanes that reach this call together, one candidate bit per lane per round: where the words
+// are found, or when a warp's candidate queue is full.  EMIT_INLINE: inlined where the words are
+// found for small pattern sets (frequent sites then cost no call and no saving of the loop's
+// registers), a call otherwise.
 static __device__ EMIT_INLINE void emit4(u32 c0, u32 c1, u32 c2, u32 c3, int q0, u64 g, uint2 a, uint2 b,
                                           const ScanParams& P) {
   const u32 mask = __activemask();
-  const u32 lane = threadIdx.x & 31u;
   const u64 tile = g / P.tile_groups, tile_pos = tile * P.tile_groups * 32ull;
   const u32 peers = __match_any_sync(mask, tile);
-  const u32 leader = __ffs(peers) - 1, below = peers & ((1u << lane) - 1u);
+  const u32 leader = __ffs(peers) - 1;
   const u64 lo64 = (u64)a.x | ((u64)b.x << 32), hi64 = (u64)a.y | ((u64)b.y << 32);
   const u64 inv64 = (u64)P.invalid[g] | ((u64)P.invalid[g + 1] << 32);
   u32 w[4] = {c0, c1, c2, c3};
@@ -411,32 +446,65 @@ static __device__ EMIT_INLINE void emit4(u32 c0, u32 c1, u32 c2, u32 c3, int q0,
         w[t] &= w[t] - 1;
       }
     if (!__any_sync(mask, k >= 0)) break;
-    bool ok = false;
     u64 key = 0;
-    if (k >= 0) {
-      const int q = q0 + k;
-      const int L = PLEN[q];
-      const u32 wm = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
-      const u32 wl = (u32)(lo64 >> i), wh = (u32)(hi64 >> i);  // base j of the window at bit j
-      const u32 match = (~wl & ~wh & MSET[q][0]) | (wl & ~wh & MSET[q][1]) | (~wl & wh & MSET[q][2]) |
-                        (wl & wh & MSET[q][3]);
-      const u32 mis = ~match & wm;
-      const int mism = __popc(mis);
-      if ((mis & PCLAMP[q]) || mism > PK[q]) {
-        atomicOr(P.status, 1u);
-      } else if (!((u32)(inv64 >> i) & wm)) {
-        const u64 pos = g * 32ull + (u64)i;
-        key = ((u64)PPAIR[q] << 48) | ((pos - tile_pos) << 16) | ((u64)PORIENT[q] << 8) | (u64)mism;
-        ok = true;
-      }
+    const bool ok = k >= 0 && check_bit(q0 + k, i, lo64, hi64, inv64, g, tile_pos, P, &key);
+    append(mask, peers, leader, ok, key, tile, P);
+  }
+}
+
+// A warp's queue of candidate words: QCAP entries of (word, pattern | group offset in the block << 16)
+#define QCAP 64
+
+// A lane's candidate words of patterns q0 .. q0+3 (group at offset off in the block) into its warp's
+// queue; a full queue sends the word on at once.
+static __device__ __forceinline__ void push4(u32 c0, u32 c1, u32 c2, u32 c3, int q0, u32 off, u64 g, uint2 a,
+                                             uint2 b, const ScanParams& P, u32* qw, u32* qm, u32* qn) {
+  const u32 c[4] = {c0, c1, c2, c3};
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if (!c[t]) continue;
+    const u32 idx = atomicAdd(qn, 1u);
+    if (idx < QCAP) {
+      qw[idx] = c[t];
+      qm[idx] = (off << 16) | (u32)(q0 + t);
+    } else {
+      emit4(t == 0 ? c[t] : 0u, t == 1 ? c[t] : 0u, t == 2 ? c[t] : 0u, t == 3 ? c[t] : 0u, q0, g, a, b, P);
     }
-    const u32 vb = __ballot_sync(mask, ok) & peers;
-    u32 base = 0;
-    if (lane == leader && vb) base = atomicAdd(P.tile_count + tile, (u32)__popc(vb));
-    base = __shfl_sync(mask, base, leader);
-    if (ok) {
-      const u32 idx = base + __popc(vb & below);
-      if (idx < P.slot_cap) P.slots[tile * (u64)P.slot_cap + idx] = key;
+  }
+}
+
+// The warp's queued candidate words (n of them), 32 at a time, one word per lane, one bit per lane
+// per round; every lane of the warp takes part.
+static __device__ __forceinline__ void drain(const ScanParams& P, u64 first, const u32* qw, const u32* qm, u32 n) {
+  const u32 lane = threadIdx.x & 31u;
+  for (u32 e0 = 0; e0 < n; e0 += 32) {
+    const u32 e = e0 + lane;
+    u32 h = 0;
+    int q = 0;
+    u64 g = 0, lo64 = 0, hi64 = 0, inv64 = 0;
+    if (e < n) {
+      h = qw[e];
+      const u32 m = qm[e];
+      q = (int)(m & 0xffffu);
+      g = P.group_begin + first + (m >> 16);
+      const uint2 a = __ldg(P.planes + g), b = __ldg(P.planes + g + 1);
+      lo64 = (u64)a.x | ((u64)b.x << 32);
+      hi64 = (u64)a.y | ((u64)b.y << 32);
+      inv64 = (u64)P.invalid[g] | ((u64)P.invalid[g + 1] << 32);
+    }
+    const u64 tile = g / P.tile_groups, tile_pos = tile * P.tile_groups * 32ull;
+    const u32 peers = __match_any_sync(0xffffffffu, tile);
+    const u32 leader = __ffs(peers) - 1;
+    for (;;) {
+      int i = -1;
+      if (h) {
+        i = __ffs(h) - 1;
+        h &= h - 1;
+      }
+      if (!__any_sync(0xffffffffu, i >= 0)) break;
+      u64 key = 0;
+      const bool ok = i >= 0 && check_bit(q, i, lo64, hi64, inv64, g, tile_pos, P, &key);
+      append(0xffffffffu, peers, leader, ok, key, tile, P);
     }
   }
 }
@@ -477,9 +545,10 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg,
     for (int j = p.clamp_lo; j < p.clamp_hi; ++j) m |= 1u << j;
     return m;
   });
-  // the emission routine is inlined at up to two call sites (8 patterns): measured on GB300, the
-  // dense-site workload (4 patterns) scanned 5 % faster inlined, the 32-pattern set 5 % slower
-  os << "#define EMIT_INLINE " << (Q <= 8 ? "__forceinline__" : "__noinline__") << "\n";
+  // direct emission: the routine inlined at up to two call sites (8 patterns; measured on GB300 the
+  // dense-site workload, 4 patterns, scanned 5 % faster inlined and the 32-pattern set 5 % slower);
+  // with the queue it is only the rare fallback
+  os << "#define EMIT_INLINE " << (!cfg.emit_queue && Q <= 8 ? "__forceinline__" : "__noinline__") << "\n";
   os << kPrelude;
 
   // body: per group of 32 positions
@@ -508,6 +577,11 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg,
 
   // one block of the launch: NT threads x GPT groups of 32 positions, from group_begin
   os << "static __device__ __forceinline__ void scan_block(const ScanParams& P, const u64 blk) {\n";
+  if (cfg.emit_queue) {
+    os << "  __shared__ u32 cand_w[NT / 32][QCAP], cand_m[NT / 32][QCAP], cand_n[NT / 32];\n";
+    os << "  const u32 wp = threadIdx.x >> 5;\n";
+    os << "  if ((threadIdx.x & 31u) == 0) cand_n[wp] = 0;\n  __syncwarp();\n";
+  }
   os << "  const u64 first = blk * (u64)(NT * GPT);\n";
   os << "  u64 gl = first + threadIdx.x;\n";
   os << "  uint2 na = make_uint2(0u, 0u), nb = na;\n";
@@ -561,11 +635,18 @@ std::string scan_source(const std::vector<Pattern>& pats, const ScanConfig& cfg,
     int q1 = std::min(Q, q0 + 4);
     os << "      if (__builtin_expect((";
     for (int q = q0; q < q1; ++q) os << (q > q0 ? " & " : "") << "f" << q;
-    os << ") != 0xffffffffu, 0)) emit4(";
+    os << ") != 0xffffffffu, 0)) " << (cfg.emit_queue ? "push4(" : "emit4(");
     for (int q = q0; q < q0 + 4; ++q) os << (q < q1 ? "~f" + std::to_string(q) : std::string("0u")) << ", ";
-    os << q0 << ", g, a, b, P);\n";
+    if (cfg.emit_queue)
+      os << q0 << ", (u32)(gl - first), g, a, b, P, cand_w[wp], cand_m[wp], &cand_n[wp]);\n";
+    else
+      os << q0 << ", g, a, b, P);\n";
   }
-  os << "    }\n  }\n}\n";
+  os << "    }\n  }\n";
+  // the queued candidates, by the whole warp once its groups are done
+  if (cfg.emit_queue)
+    os << "  __syncwarp();\n  drain(P, first, cand_w[wp], cand_m[wp], min(cand_n[wp], (u32)QCAP));\n";
+  os << "}\n";
   os << "extern \"C\" __global__ void __launch_bounds__(NT" << (cfg.min_blocks > 0 ? ", " + std::to_string(cfg.min_blocks) : "")
      << ") ah_scan_jit(const ScanParams P) {\n";
   if (cfg.persistent) {

@@ -70,10 +70,10 @@ def failure_words(src, lo0, hi0, lo1, hi1, phase_a=None):
                 if (lut >> idx) & 1:
                     r |= (a if idx & 4 else M ^ a) & (b if idx & 2 else M ^ b) & (c if idx & 1 else M ^ c)
             env[m.group(1)] = r
-    # the candidate words handed to the emission routine, four patterns per call (~f<q>, or 0u where
-    # the block of four has no pattern)
+    # the candidate words handed to the emission routine or the warp's queue, four patterns per call
+    # (~f<q>, or 0u where the block of four has no pattern)
     names = []
-    for args in re.findall(r"emit4\(([^;]*?), \d+, g, a, b, P\)", src):
+    for args in re.findall(r"(?:emit4|push4)\(([^;]*?), \d+, (?:\(u32\)\(gl - first\), )?g, a, b, P[,)]", src):
         names += [x[1:] for x in (a.strip() for a in args.split(",")) if x != "0u"]
     if phase_a is not None:
         for f in names:

@@ -97,6 +97,7 @@ def test_context_settings_refused(env):
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_scan_circuit, ctx, 33, 1024)        # bound too high
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_scan_circuit, ctx, 0, 0)            # no windows
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_scan_circuit, ctx, 0, (1 << 20) + 1)
+    _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_scan_circuit, ctx, 0, 1024, 2)       # no such emission
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_pairs_per_kernel, ctx, 257)
     _refused(ah, ctx, ah.AH_EINVAL, ah.ah_ctx_set_generic_scan, ctx, 4)
     _still_works(ah, ctx, wl, batch)

@@ -123,18 +123,40 @@ def test_scan_shapes_and_shift_modes(engine, threads, gpt, slots, shift):
         ah.ah_ctx_set_scan_config(engine.ctx, 256, 4, 256, 0)
 
 
-@pytest.mark.parametrize("min_blocks,windows", [(0, 1), (0, 64), (4, 4096), (0, 1 << 20), (8, 1024)])
-def test_scan_circuit_splits(engine, min_blocks, windows):
+@pytest.mark.parametrize("min_blocks,windows,queue", [(0, 1, 0), (0, 64, 1), (4, 4096, 0), (0, 1 << 20, 1),
+                                                      (8, 1024, 1), (4, 4096, 1)])
+def test_scan_circuit_splits(engine, min_blocks, windows, queue):
     """The circuit's phase split drawn for any number of windows per vote (1: the shortest first
-    phase, 2^20: one phase for most patterns) and any register bound gives the same sites."""
+    phase, 2^20: one phase for most patterns), any register bound, and candidates emitted where
+    found or queued per warp give the same sites."""
     from paper_2511_00170_gb300 import ah
 
-    ah.ah_ctx_set_scan_circuit(engine.ctx, min_blocks, windows)
+    ah.ah_ctx_set_scan_circuit(engine.ctx, min_blocks, windows, queue)
     try:
         _run_both(engine, synth.batched(n_genomes=12, len_lo=2e3, len_hi=3e5, n_pairs=4))
-        _run_both(engine, _random_case(2000 + windows % 97 + min_blocks))
+        _run_both(engine, _random_case(2000 + windows % 97 + min_blocks + queue))
     finally:
-        ah.ah_ctx_set_scan_circuit(engine.ctx, 0, 1024)
+        ah.ah_ctx_set_scan_circuit(engine.ctx, 0, 1024, 0)
+
+
+def test_candidate_queue_overflow(engine):
+    """A site at every position: each warp's candidate queue overflows and the rest of its words are
+    emitted where found; the sites still match the oracle's."""
+    from paper_2511_00170_gb300 import ah
+
+    g = "A" * 200_000 + "ACGT" * 500 + "T" * 100_000
+    wl = synth.random_small(3, n_records=1, len_lo=10, len_hi=10, n_pairs=1, plant=0)
+    wl.seq = np.frombuffer(g.encode(), dtype=np.uint8).copy()
+    wl.offsets = np.array([0, len(g)], dtype=np.int64)
+    wl.fwd, wl.rev, wl.k, wl.clamp = ["AAAAAAAAAA"], ["AAAAAAAAAAAA"], [1], 2
+    wl.min_len, wl.max_len, wl.orient_mask = 20, 60, 15
+    wl.fb_len = wl.rb_len = 3
+    ah.ah_ctx_set_scan_circuit(engine.ctx, 0, 1024, 1)
+    try:
+        out, ref = _run_both(engine, wl)
+        assert len(ref.hits) > 300_000
+    finally:
+        ah.ah_ctx_set_scan_circuit(engine.ctx, 0, 1024, 0)
 
 
 def test_several_pairs(engine):
