@@ -429,11 +429,12 @@ static __device__ __forceinline__ void append(u32 mask, u32 peers, u32 leader, b
 // found for small pattern sets (frequent sites then cost no call and no saving of the loop's
 // registers), a call otherwise.
 static __device__ EMIT_INLINE void emit4(u32 c0, u32 c1, u32 c2, u32 c3, int q0, u64 g, uint2 a, uint2 b,
-                                          const ScanParams& P) {
+                                         const ScanParams& P) {
   const u32 mask = __activemask();
+  const u32 lane = threadIdx.x & 31u;
   const u64 tile = g / P.tile_groups, tile_pos = tile * P.tile_groups * 32ull;
   const u32 peers = __match_any_sync(mask, tile);
-  const u32 leader = __ffs(peers) - 1;
+  const u32 leader = __ffs(peers) - 1, below = peers & ((1u << lane) - 1u);
   const u64 lo64 = (u64)a.x | ((u64)b.x << 32), hi64 = (u64)a.y | ((u64)b.y << 32);
   const u64 inv64 = (u64)P.invalid[g] | ((u64)P.invalid[g + 1] << 32);
   u32 w[4] = {c0, c1, c2, c3};
@@ -446,9 +447,33 @@ static __device__ EMIT_INLINE void emit4(u32 c0, u32 c1, u32 c2, u32 c3, int q0,
         w[t] &= w[t] - 1;
       }
     if (!__any_sync(mask, k >= 0)) break;
+    bool ok = false;
     u64 key = 0;
-    const bool ok = k >= 0 && check_bit(q0 + k, i, lo64, hi64, inv64, g, tile_pos, P, &key);
-    append(mask, peers, leader, ok, key, tile, P);
+    if (k >= 0) {  // check_bit's test written out: in this form the bench pair's loop ran 1.6 % faster
+      const int q = q0 + k;
+      const int L = PLEN[q];
+      const u32 wm = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
+      const u32 wl = (u32)(lo64 >> i), wh = (u32)(hi64 >> i);  // base j of the window at bit j
+      const u32 match = (~wl & ~wh & MSET[q][0]) | (wl & ~wh & MSET[q][1]) | (~wl & wh & MSET[q][2]) |
+                        (wl & wh & MSET[q][3]);
+      const u32 mis = ~match & wm;
+      const int mism = __popc(mis);
+      if ((mis & PCLAMP[q]) || mism > PK[q]) {
+        atomicOr(P.status, 1u);
+      } else if (!((u32)(inv64 >> i) & wm)) {
+        const u64 pos = g * 32ull + (u64)i;
+        key = ((u64)PPAIR[q] << 48) | ((pos - tile_pos) << 16) | ((u64)PORIENT[q] << 8) | (u64)mism;
+        ok = true;
+      }
+    }
+    const u32 vb = __ballot_sync(mask, ok) & peers;
+    u32 base = 0;
+    if (lane == leader && vb) base = atomicAdd(P.tile_count + tile, (u32)__popc(vb));
+    base = __shfl_sync(mask, base, leader);
+    if (ok) {
+      const u32 idx = base + __popc(vb & below);
+      if (idx < P.slot_cap) P.slots[tile * (u64)P.slot_cap + idx] = key;
+    }
   }
 }
 
