@@ -130,6 +130,12 @@ ah_status ah_ctx_set_generic_scan(ah_ctx* ctx, int mode);
  *     thread of the context compiles it (server contexts use this mode).
  * Plans use the generated kernel unless the mode is 1.  AH_EINVAL for another mode. */
 ah_status ah_ctx_set_tm_kernel(ah_ctx* ctx, int mode);
+/* Site capacity from which the generated Tm kernel is launched once per group of primers (at most
+ * 4 launches), so that each launch runs fewer primers' straight-line code and it stays in the
+ * instruction cache; each launch re-reads the site marks.  0 restores the default (4 Mi sites),
+ * UINT64_MAX keeps one launch, 1 always splits.  Results do not depend on it.  A plan takes the
+ * value set when it is created. */
+ah_status ah_ctx_set_tm_split(ah_ctx* ctx, uint64_t sites);
 /* Diagnostics (no device needed): generate the Tm kernel for n primers (IUPAC, 2..32 nt; index
  * 2 * pair + primer as in a primer set) and compile it with NVRTC for compute capability sm (e.g.
  * 103).  AH_OK if it compiles; AH_EJIT with the compiler's log in log (log_cap bytes, NUL-ended)

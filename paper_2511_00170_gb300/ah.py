@@ -102,6 +102,7 @@ SIGNATURES = {
     "ah_ctx_set_pairs_per_kernel": (_I32, [_VP, ctypes.c_int]),
     "ah_ctx_set_generic_scan": (_I32, [_VP, ctypes.c_int]),
     "ah_ctx_set_tm_kernel": (_I32, [_VP, ctypes.c_int]),
+    "ah_ctx_set_tm_split": (_I32, [_VP, ctypes.c_uint64]),
     "ah_tm_kernel_check": (_I32, [_VP, _U32, ctypes.c_int, ctypes.c_char_p, ctypes.c_uint64]),
     "ah_ctx_set_timing": (_I32, [_VP, _I32]),
     "ah_ctx_set_scan_config": (_I32, [_VP, _I32, _I32, _I32, _I32]),
@@ -251,6 +252,12 @@ def ah_ctx_set_tm_kernel(ctx, mode: int) -> None:
     """Degenerate-site Tm kernel: 0 generated for the primer set; 1 built in; 2 built in while the
     generated one compiles."""
     _check(load().ah_ctx_set_tm_kernel(ctx, int(mode)), ctx)
+
+
+def ah_ctx_set_tm_split(ctx, sites: int = 0) -> None:
+    """Site capacity from which the generated Tm kernel runs as one launch per group of primers
+    (0: the default, 2**64 - 1: never)."""
+    _check(load().ah_ctx_set_tm_split(ctx, int(sites)), ctx)
 
 
 def ah_tm_kernel_check(primers: Sequence[str], sm: int = 103) -> Tuple[int, str]:

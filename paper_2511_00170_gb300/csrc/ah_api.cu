@@ -555,6 +555,12 @@ ah_status ah_ctx_set_tm_kernel(ah_ctx* ctx, int mode) {
   return AH_OK;
 }
 
+ah_status ah_ctx_set_tm_split(ah_ctx* ctx, uint64_t sites) {
+  if (!ctx) return AH_EINVAL;
+  ctx->tm_split_sites = sites ? sites : ah::kTmSplitSitesDefault;
+  return AH_OK;
+}
+
 ah_status ah_ctx_set_generic_scan(ah_ctx* ctx, int mode) {
   if (!ctx) return AH_EINVAL;
   if (mode < 0 || mode > 3) return fail(ctx, AH_EINVAL, "ah_ctx_set_generic_scan: mode 0 to 3");

@@ -89,6 +89,10 @@ struct ScanConfig {
                             // values weigh phase two as if windows survived phase one more often)
 };
 
+// default of ah_ctx::tm_split_sites: each launch re-reads the window's site marks, which pays once
+// the chains of fewer primers per launch keep the instruction cache warm
+constexpr uint64_t kTmSplitSitesDefault = 4ull << 20;
+
 class JitCache;
 
 }  // namespace ah
@@ -135,6 +139,7 @@ struct ah_ctx {
   // degenerate-site Tm kernel: 0 the kernel generated for the primer set (compiled on first use),
   // 1 the built-in kernel, 2 the built-in kernel while the generated one compiles in the background
   int tm_kernel = 0;
+  uint64_t tm_split_sites = ah::kTmSplitSitesDefault;  // see ah::TmKernel::split_sites
   uint64_t n_tm_generated = 0;  // Tm launches (outside plans) by a generated kernel
   uint64_t n_tm_builtin = 0;    // ... by the built-in one
 };
@@ -332,6 +337,7 @@ struct TmKernel {
   cudaKernel_t fn = nullptr;
   int weight_words = 0;        // weight words per thread
   const int32_t* image = nullptr;  // the parameter tables as the kernel's shared memory holds them
+  uint64_t split_sites = ~0ull;    // site capacity from which it is launched once per group of primers
 };
 // Larger primer sets take the built-in kernel: compile time grows with the primers and, about 40 ms
 // each, with the transitions between adjacent degenerate positions.

@@ -1577,7 +1577,7 @@ __global__ void __launch_bounds__(kTmThreads, 4) k_tm_hits_t(const ah_hit* __res
                                                              const uint4* __restrict__ pmask, const TmRun Rp,
                                                              double* __restrict__ out, uint32_t* __restrict__ defer,
                                                              const uint64_t* __restrict__ d_n) {
-  tm_hits_body<GenericSites>(hits, n, planes, rec_group, plen, pmask, Rp, out, defer, d_n, nullptr);
+  tm_hits_body<GenericSites>(hits, n, planes, rec_group, plen, pmask, Rp, out, defer, d_n, nullptr, 0u, ~0u);
 }
 
 // The sites k_tm_hits_t listed (defer[0] of them at defer[1..]): one warp per site, every lane
@@ -1773,6 +1773,8 @@ int thread_weight_words(const std::string& primer) {
 
 constexpr int kTmThreadFixedWords = kTmTabWords + 2 * kTmSlots;  // tables, keys and their order
 constexpr size_t kTmSmemCap = 46 * 1024;  // dynamic shared memory, beside the kernels' static arrays
+// the most launches of the generated Tm kernel, each for a group of primers (TmKernel::split_sites)
+constexpr uint32_t kTmPrimerLaunches = 4;
 
 // the Tm of every marked site (hit_tm holds kSiteWanted there): one thread per site for the default
 // reading when its weights fit, else the group kernel where the state width allows, else k_tm_hits
@@ -1787,11 +1789,12 @@ size_t thread_kernel_smem(const ah_primers* p, int variants) {
 }
 
 // defer: cap + 1 words of device scratch for the sites the chain does not cover (the thread kernel
-// lists them there for k_tm_deferred)
-void launch_tm_hits(cudaStream_t s, const TmRun& R, const ah_primers* p, const ah_hit* hits, uint64_t cap,
+// lists them there for k_tm_deferred).  Returns the kernels launched.
+int launch_tm_hits(cudaStream_t s, const TmRun& R, const ah_primers* p, const ah_hit* hits, uint64_t cap,
                     const uint64_t* d_n, const uint2* planes, const uint64_t* rec_group, double* hit_tm,
                     uint32_t* status, uint32_t* defer, int sm_count, const TmKernel& tk, bool* generated) {
   if (generated) *generated = false;
+  int n_launched = 0;
   if (const size_t smem = thread_kernel_smem(p, R.variants)) {
     cudaMemsetAsync(defer, 0, sizeof(uint32_t), s);
     const unsigned grid = (unsigned)std::max<uint64_t>(1, (cap + kTmSlots - 1) / kTmSlots);
@@ -1799,24 +1802,34 @@ void launch_tm_hits(cudaStream_t s, const TmRun& R, const ah_primers* p, const a
     if (tk.fn && tk.image && smem_j <= kTmSmemCap) {  // the kernel generated for this primer set
       const uint8_t* plen = p->d_plen;
       const uint4* pmask = p->d_pmask;
-      void* args[] = {(void*)&hits, (void*)&cap, (void*)&planes, (void*)&rec_group, (void*)&plen, (void*)&pmask,
-                      (void*)&R, (void*)&hit_tm, (void*)&defer, (void*)&d_n, (void*)&tk.image};
-      cudaLaunchKernel((const void*)tk.fn, dim3(grid), dim3(kTmThreads), args, smem_j, s);
+      // many sites: one launch per group of primers (at most kTmPrimerLaunches), so that each
+      // launch runs fewer primers' straight-line chains and they stay in the instruction cache
+      const uint32_t n_pr = 2 * p->n_pairs;
+      const uint32_t parts = cap >= tk.split_sites ? std::min<uint32_t>(n_pr, kTmPrimerLaunches) : 1;
+      for (uint32_t k = 0; k < parts; ++k) {
+        uint32_t pr_lo = parts > 1 ? n_pr * k / parts : 0u, pr_hi = parts > 1 ? n_pr * (k + 1) / parts : ~0u;
+        void* args[] = {(void*)&hits, (void*)&cap,    (void*)&planes, (void*)&rec_group, (void*)&plen, (void*)&pmask,
+                        (void*)&R,    (void*)&hit_tm, (void*)&defer,  (void*)&d_n,       (void*)&tk.image,
+                        (void*)&pr_lo, (void*)&pr_hi};
+        cudaLaunchKernel((const void*)tk.fn, dim3(grid), dim3(kTmThreads), args, smem_j, s);
+      }
       if (generated) *generated = true;
+      n_launched += parts;
     } else {
       k_tm_hits_t<<<grid, kTmThreads, smem, s>>>(hits, cap, planes, rec_group, p->d_plen, p->d_pmask, R, hit_tm, defer,
                                                  d_n);
+      ++n_launched;
     }
     const size_t smem_d = smem - 4 * (size_t)(2 * kTmSlots);  // tables and weights only
     k_tm_deferred<<<(unsigned)std::max(1, 4 * sm_count), kTmThreads, smem_d, s>>>(hits, planes, rec_group, p->d_plen,
                                                                                 p->d_pmask, R, hit_tm, status, defer);
-    return;
+    return n_launched + 1;
   }
   const TmShape t = hits_shape(p, R.variants);
   if (!t.G) {
     k_tm_hits<<<(unsigned)std::max<uint64_t>(1, (cap + kTmBlock - 1) / kTmBlock), kTmBlock, 0, s>>>(
         hits, cap, planes, rec_group, p->d_plen, p->d_psets, p->d_pk, p->clamp, R, hit_tm, status, d_n);
-    return;
+    return 1;
   }
   const unsigned grid = (unsigned)std::max<uint64_t>(1, (cap + kTmWindow - 1) / kTmWindow);
 #define AH_TM_HITS_G(GG)                                                                                        \
@@ -1829,6 +1842,7 @@ void launch_tm_hits(cudaStream_t s, const TmRun& R, const ah_primers* p, const a
     default: AH_TM_HITS_G(32); break;
   }
 #undef AH_TM_HITS_G
+  return 1;
 }
 
 }  // namespace
@@ -1982,11 +1996,10 @@ ah_status tm_filter(ah_ctx* ctx, const ah_batch* b, const ah_primers* p, const a
     TmKernel tk;
     if (!R.variants && (st = tm_kernel_for(ctx, p, false, R.nn, &tk))) return st;
     bool generated = false;
-    launch_tm_hits(ctx->stream, R, p, h->d, h->n, nullptr, b->planes, b->rec_group, hit_tm, ctx->d_status, defer,
-                   ctx->sm_count, tk, &generated);
+    launched(ctx, launch_tm_hits(ctx->stream, R, p, h->d, h->n, nullptr, b->planes, b->rec_group, hit_tm,
+                                 ctx->d_status, defer, ctx->sm_count, tk, &generated));
     (generated ? ctx->n_tm_generated : ctx->n_tm_builtin)++;
   }
-  if (h->n && a->n) launched(ctx);
   if (params->filter && (st = dalloc(ctx, &keep, a->n))) return st;
   if (a->n)
     k_tm_amps<<<(unsigned)((a->n + 255) / 256), 256, 0, ctx->stream>>>(a->d, a->n, hit_tm, params->filter,

@@ -220,12 +220,15 @@ __device__ __forceinline__ bool chain_site_tm(const TmTabs& T, int32_t* __restri
 // the list defer (count at defer[0]) for the enumerating kernel.  Shared memory: the tables, the
 // window's keys and their order by primer, then each thread's weights, strided by the block size.
 // D supplies fill(TmTabs&, const int32_t* image, int slot) and site(pr, T, W, ws, P, code, L, R, &tm).
+// Only the sites of primers [pr_lo, pr_hi) are taken; the others are left as they are for another
+// launch (a launch per primer keeps one primer's code hot in the instruction cache).
 template <class D>
 __device__ __forceinline__ void tm_hits_body(const ah_hit* __restrict__ hits, uint64_t n,
                                              const uint2* __restrict__ planes, const uint64_t* __restrict__ rec_group,
                                              const uint8_t* __restrict__ plen, const uint4* __restrict__ pmask,
                                              const TmRun& Rp, double* __restrict__ out, uint32_t* __restrict__ defer,
-                                             const uint64_t* __restrict__ d_n, const int32_t* __restrict__ image) {
+                                             const uint64_t* __restrict__ d_n, const int32_t* __restrict__ image,
+                                             uint32_t pr_lo, uint32_t pr_hi) {
   // the run constants in shared memory: device functions take them by reference, and a reference
   // to a kernel parameter would make the compiler copy it to local memory for every thread
   __shared__ TmRun R_sh;
@@ -249,8 +252,12 @@ __device__ __forceinline__ void tm_hits_body(const ah_hit* __restrict__ hits, ui
     uint32_t key = 0xFFFFFFFFu;
     if (i < n_here && (unsigned long long)__double_as_longlong(out[i]) == kSiteWanted) {
       const ah_hit h = hits[i];
-      const int L = plen[h.pattern];
       const uint32_t pr = (h.pattern >> 2) * 2 + (h.pattern & 1u);
+      if (pr < pr_lo || pr >= pr_hi) {
+        keys[t] = key;
+        continue;
+      }
+      const int L = plen[h.pattern];
       const uint64_t code = site_code(planes, rec_group, h, L);
       const uint64_t cc = code ^ 0xAAAAAAAAAAAAAAAAull;
       const uint4 mk = pmask[pr];

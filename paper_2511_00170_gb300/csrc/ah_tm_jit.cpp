@@ -371,8 +371,8 @@ std::string tm_chain_source(const std::vector<std::string>& primers, int* weight
         "    const ah_hit* __restrict__ hits, uint64_t n, const uint2* __restrict__ planes,\n"
         "    const uint64_t* __restrict__ rec_group, const uint8_t* __restrict__ plen, const uint4* __restrict__ pmask,\n"
         "    const TmRun Rp, double* __restrict__ out, uint32_t* __restrict__ defer, const uint64_t* __restrict__ d_n,\n"
-        "    const int32_t* __restrict__ image) {\n"
-        "  tm_hits_body<GenSites>(hits, n, planes, rec_group, plen, pmask, Rp, out, defer, d_n, image);\n}\n";
+        "    const int32_t* __restrict__ image, uint32_t pr_lo, uint32_t pr_hi) {\n"
+        "  tm_hits_body<GenSites>(hits, n, planes, rec_group, plen, pmask, Rp, out, defer, d_n, image, pr_lo, pr_hi);\n}\n";
   if (weight_words) *weight_words = words;
   return os.str();
 }
@@ -503,7 +503,10 @@ ah_status tm_kernel_for(ah_ctx* ctx, const ah_primers* p, bool wait, int slot, T
   if (tm_chain_adjacent(primers) > kTmJitMaxAdjacent) return AH_OK;
   if (ctx->tm_kernel == 2 && !wait) {  // the built-in kernel until the generated one is compiled
     const Lookup l = lookup(ctx->device, primers, out);
-    if (l == kReady) return tm_tab_image(ctx, slot, &out->image);
+    if (l == kReady) {
+      out->split_sites = ctx->tm_split_sites;
+      return tm_tab_image(ctx, slot, &out->image);
+    }
     *out = TmKernel{};
     if (l == kAbsent) {
       const int device = ctx->device;
@@ -532,6 +535,7 @@ ah_status tm_kernel_for(ah_ctx* ctx, const ah_primers* p, bool wait, int slot, T
     *out = TmKernel{};
     return fail(ctx, st, "%s", err.c_str());
   }
+  out->split_sites = ctx->tm_split_sites;
   return tm_tab_image(ctx, slot, &out->image);
 }
 

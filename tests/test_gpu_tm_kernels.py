@@ -128,3 +128,25 @@ def test_large_sets_take_the_builtin_kernel(engine):
     out, st = _step(engine, wl, 0)
     assert st["tm_builtin"] == 1 and st["tm_generated"] == 0, st
     compare.assert_same_amplicons(out, ref, filtered=False)
+
+
+def test_per_primer_launches(engine):
+    """The generated kernel launched once per primer (as it runs for many sites) gives every site the
+    Tm of a single launch, bit for bit, and the oracle's."""
+    from paper_2511_00170_gb300 import ah
+
+    fwd, rev, k = SHAPES[6]
+    wl = _planted_case(70, fwd, rev, k)
+    ref = oracle.run(wl, with_seqs=False)
+    runs = []
+    for sites in (1, 2**64 - 1):
+        ah.ah_ctx_set_tm_split(engine.ctx, sites)
+        try:
+            runs.append(_step(engine, wl, 0))
+        finally:
+            ah.ah_ctx_set_tm_split(engine.ctx, 0)
+    (split, s_split), (one, s_one) = runs
+    assert s_split["tm_generated"] == 1 and s_one["tm_generated"] == 1
+    assert s_split["kernel_launches"] == s_one["kernel_launches"] + 1   # two primers: two launches
+    compare.assert_same_amplicons(split, ref, filtered=False)
+    assert np.array_equal(split.amps["tm"].view(np.int64), one.amps["tm"].view(np.int64))
