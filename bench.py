@@ -45,6 +45,8 @@ def engine_for(args, device):
 
     eng = Engine(device)
     ah.ah_ctx_set_tm_kernel(eng.ctx, TM_KERNELS[getattr(args, "tm_kernel", "generated")])
+    if getattr(args, "tm_split", 0):
+        ah.ah_ctx_set_tm_split(eng.ctx, args.tm_split)
     fixed = getattr(args, "scan_fixed", "")
     if fixed:
         t, g, mode, mb, w, queue = (int(x) for x in fixed.split(","))
@@ -961,6 +963,9 @@ def main():
     ap.add_argument("--serve-burst", type=int, default=100, help="sub-record: requests offered at 200 req/s")
     ap.add_argument("--tm-kernel", default="generated", choices=sorted(TM_KERNELS),
                     help="degenerate-site Tm: the kernel generated per primer set, or the built-in one")
+    ap.add_argument("--tm-split", type=int, default=0,
+                    help="site count from which the generated Tm kernel runs once per group of primers "
+                         "(0: the library's default)")
     ap.add_argument("--scan-fixed", default="",
                     help="threads,groups,shift_mode,min_blocks,vote_windows,emit_queue: plans take this scan kernel "
                          "instead of autotuning (for profiling one kernel)")

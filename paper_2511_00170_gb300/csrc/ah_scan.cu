@@ -196,15 +196,41 @@ __global__ void k_emit_hits(const uint64_t* __restrict__ slots, const uint32_t* 
   const uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (t >= n_tiles) return;
   const uint32_t n = min(tile_count[t], cap);
+  if (n == 0) return;
   const uint64_t* tk = slots + t * cap;
   const uint64_t tile_pos = tile_base ? tile_base[t] : t * tile_groups * 32ull;
+  // the records the tile's sites fall in, [r_lo, r_hi]: lane 0 finds the one holding the smallest
+  // position, lane 1 the one holding the largest, so a site's record search spans those only
+  uint64_t p_min = ~0ull, p_max = 0;
+  for (uint32_t i = lane; i < n; i += 32) {
+    const uint64_t x = (tk[i] >> 16) & 0xffffffffull;
+    p_min = min(p_min, x);
+    p_max = max(p_max, x);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    p_min = min(p_min, __shfl_xor_sync(0xffffffffu, p_min, o));
+    p_max = max(p_max, __shfl_xor_sync(0xffffffffu, p_max, o));
+  }
+  uint32_t r = 0;
+  if (lane < 2) {
+    const uint64_t pos = tile_pos + (lane ? p_max : p_min);
+    uint32_t lo = 0, hi = n_rec;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (rec_group[mid] * 32ull <= pos) lo = mid; else hi = mid;
+    }
+    r = lo;
+  }
+  const uint32_t r_lo = __shfl_sync(0xffffffffu, r, 0), r_hi = __shfl_sync(0xffffffffu, r, 1);
+  const bool one_pair = (tk[0] >> 48) == (tk[n - 1] >> 48);  // keys are sorted by pair first
   for (uint32_t i = lane; i < n; i += 32) {
     const uint64_t key = tk[i];
     const uint32_t pair = (uint32_t)(key >> 48);
-    const uint32_t first = lower_bound_u64(tk, n, (uint64_t)pair << 48);
+    const uint32_t first = one_pair ? 0u : lower_bound_u64(tk, n, (uint64_t)pair << 48);
     const uint64_t o = off[(uint64_t)pair * n_tiles + t] + (i - first);
     const uint64_t pos = tile_pos + ((key >> 16) & 0xffffffffull);
-    uint32_t lo = 0, hi = n_rec;
+    uint32_t lo = r_lo, hi = r_hi + 1;
     while (hi - lo > 1) {
       const uint32_t mid = (lo + hi) >> 1;
       if (rec_group[mid] * 32ull <= pos) lo = mid; else hi = mid;
