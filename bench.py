@@ -49,7 +49,7 @@ def engine_for(args, device):
         ah.ah_ctx_set_tm_split(eng.ctx, args.tm_split)
     fixed = getattr(args, "scan_fixed", "")
     if fixed:
-        t, g, mode, mb, w, queue = (int(x) for x in fixed.split(","))
+        t, g, mode, mb, w, queue = ([int(x) for x in fixed.split(",")] + [0])[:6]   # queue defaults to 0
         ah.ah_ctx_set_scan_config(eng.ctx, t, g, 256, mode)
         ah.ah_ctx_set_scan_circuit(eng.ctx, mb, w, queue)
     return eng
