@@ -85,8 +85,10 @@ __device__ __forceinline__ void warp_bitonic(uint64_t (&v)[R], int lane) {
   }
 }
 
+// Sorts n <= 32 R keys in the warp's registers and writes them back; returns (to every lane) the
+// pairs of the first and last keys.
 template <int R>
-__device__ __forceinline__ void sort_regs(uint64_t* tk, uint32_t n, int lane) {
+__device__ __forceinline__ uint2 sort_regs(uint64_t* tk, uint32_t n, int lane) {
   uint64_t v[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -94,25 +96,32 @@ __device__ __forceinline__ void sort_regs(uint64_t* tk, uint32_t n, int lane) {
     v[r] = i < n ? tk[i] : ~0ull;
   }
   warp_bitonic<R>(v, lane);
+  uint64_t last = 0;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const uint32_t i = (uint32_t)(r << 5) | (uint32_t)lane;
     if (i < n) tk[i] = v[r];
+    const uint64_t x = __shfl_sync(0xffffffffu, v[r], (int)((n - 1) & 31u));
+    if (r == (int)((n - 1) >> 5)) last = x;
   }
+  return make_uint2((uint32_t)(__shfl_sync(0xffffffffu, v[0], 0) >> 48), (uint32_t)(last >> 48));
 }
 
 // Sort one tile's n <= kSmallTile keys in the registers of one warp, write them back and count them
-// per pair (pair in the top 16 bits).
+// per pair (pair in the top 16 bits).  A tile of one pair needs no search for the counts.
 __device__ __forceinline__ void sort_tile(uint64_t* tk, uint32_t n, uint64_t t, uint64_t n_tiles, uint32_t n_pairs,
                                           uint32_t* tile_pair_count, int lane) {
-  if (n > 1) {
-    if (n <= 32) sort_regs<1>(tk, n, lane);
-    else if (n <= 64) sort_regs<2>(tk, n, lane);
-    else if (n <= 128) sort_regs<4>(tk, n, lane);
-    else sort_regs<8>(tk, n, lane);
-    __syncwarp();
+  uint2 pp;
+  if (n <= 32) pp = sort_regs<1>(tk, n, lane);
+  else if (n <= 64) pp = sort_regs<2>(tk, n, lane);
+  else if (n <= 128) pp = sort_regs<4>(tk, n, lane);
+  else pp = sort_regs<8>(tk, n, lane);
+  const uint32_t p_first = pp.x, p_last = pp.y;
+  if (p_first == p_last) {
+    if (lane == 0 && p_first < n_pairs) tile_pair_count[(uint64_t)p_first * n_tiles + t] = n;
+    return;
   }
-  const uint32_t p_first = (uint32_t)(tk[0] >> 48), p_last = (uint32_t)(tk[n - 1] >> 48);
+  __syncwarp();  // the other lanes' keys are written before they are searched
   for (uint32_t p = p_first + lane; p <= p_last && p < n_pairs; p += 32) {
     const uint32_t a = lower_bound_u64(tk, n, (uint64_t)p << 48);
     const uint32_t b = lower_bound_u64(tk, n, (uint64_t)(p + 1) << 48);
