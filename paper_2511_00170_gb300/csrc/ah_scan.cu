@@ -54,9 +54,9 @@ __device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* a, uint32_t 
 // above) in place.  The loops have constant bounds, so every register index is resolved at compile
 // time.
 template <int R>
-__device__ __forceinline__ void warp_bitonic(uint64_t (&v)[R], int lane) {
+__device__ __forceinline__ void warp_bitonic(uint64_t (&v)[R], int lane, int m = 32 * R) {
 #pragma unroll
-  for (int k = 2; k <= 32 * R; k <<= 1) {
+  for (int k = 2; k <= m; k <<= 1) {
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
       if (j >= 32) {
@@ -86,7 +86,8 @@ __device__ __forceinline__ void warp_bitonic(uint64_t (&v)[R], int lane) {
 }
 
 // Sorts n <= 32 R keys in the warp's registers and writes them back; returns (to every lane) the
-// pairs of the first and last keys.
+// pairs of the first and last keys.  With one key per lane the network spans only the next power of
+// two above n (lanes past it hold padding and stay put).
 template <int R>
 __device__ __forceinline__ uint2 sort_regs(uint64_t* tk, uint32_t n, int lane) {
   uint64_t v[R];
@@ -95,7 +96,13 @@ __device__ __forceinline__ uint2 sort_regs(uint64_t* tk, uint32_t n, int lane) {
     const uint32_t i = (uint32_t)(r << 5) | (uint32_t)lane;
     v[r] = i < n ? tk[i] : ~0ull;
   }
-  warp_bitonic<R>(v, lane);
+  if (R == 1) {
+    int m = 1;
+    while (m < (int)n) m <<= 1;
+    warp_bitonic<R>(v, lane, m);
+  } else {
+    warp_bitonic<R>(v, lane);
+  }
   uint64_t last = 0;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
