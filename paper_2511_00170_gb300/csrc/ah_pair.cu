@@ -23,52 +23,68 @@ __global__ void k_pair_walk(const ah_hit* __restrict__ hits, uint64_t n, const u
                             ah_amplicon* __restrict__ out, const uint64_t* __restrict__ d_n = nullptr,
                             uint64_t out_cap = ~0ull, uint32_t* __restrict__ overflow = nullptr) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
   const uint64_t n_live = d_n ? min(*d_n, n) : n;
-  if (i >= n_live) {
-    if (!kEmit) counts[i] = 0;
-    return;
-  }
-  const ah_hit a = hits[i];
+  const uint32_t lane = threadIdx.x & 31u;
+  const bool live = i < n_live;
+  ah_hit a{};
+  if (live) a = hits[i];
   const uint32_t oa = a.pattern & 3u;
+  bool walking = live && oa < 2;  // anchors are + strand sites
+  const uint32_t pair = a.pattern >> 2;
+  const uint64_t seg_end = walking ? min(pair_off[pair + 1], n_live) : 0;
   uint32_t cnt = 0;
-  uint64_t w = kEmit ? out_off[i] : 0;
-  if (oa < 2) {  // anchors are + strand sites
-    const uint32_t pair = a.pattern >> 2;
-    const uint64_t seg_end = min(pair_off[pair + 1], n_live);
-    for (uint64_t j = i + 1; j < seg_end; ++j) {
-      const ah_hit b = hits[j];
-      if (b.record != a.record) break;
-      const uint32_t ob = b.pattern & 3u;
-      if (ob < 2) break;  // a same-sense site stops the walk
-      const uint64_t end = (uint64_t)b.pos + plen[b.pattern];
-      const uint64_t length = end - a.pos;
-      if (length > max_len) break;
-      if (length < min_len) continue;
-      const uint8_t o = orientation(oa & 1u, ob & 1u);
-      if (!((mask >> o) & 1u)) continue;
-      if (kEmit) {
-        ah_amplicon m;
-        m.hit_i = (uint32_t)i;
-        m.hit_j = (uint32_t)j;
-        m.record = a.record;
-        m.start = a.pos;
-        m.end = (uint32_t)end;
-        m.pair = (uint16_t)pair;
-        m.orient = o;
-        m.flags = 0;
-        m.tm = __longlong_as_double(0x7ff8000000000000ll);
-        if (w < out_cap)
-          out[w] = m;
-        else if (overflow)
-          atomicOr(overflow, 4u);
-        ++w;
-      } else {
-        ++cnt;
-      }
+  uint64_t w = kEmit && live ? out_off[i] : 0;
+  // partner j of the anchor: false when the walk ends there
+  auto partner = [&](uint64_t j, uint32_t b_record, uint32_t b_pos, uint32_t b_pattern) -> bool {
+    if (b_record != a.record) return false;
+    const uint32_t ob = b_pattern & 3u;
+    if (ob < 2) return false;  // a same-sense site stops the walk
+    const uint64_t end = (uint64_t)b_pos + plen[b_pattern];
+    const uint64_t length = end - a.pos;
+    if (length > max_len) return false;
+    if (length < min_len) return true;
+    const uint8_t o = orientation(oa & 1u, ob & 1u);
+    if (!((mask >> o) & 1u)) return true;
+    if (kEmit) {
+      ah_amplicon m;
+      m.hit_i = (uint32_t)i;
+      m.hit_j = (uint32_t)j;
+      m.record = a.record;
+      m.start = a.pos;
+      m.end = (uint32_t)end;
+      m.pair = (uint16_t)pair;
+      m.orient = o;
+      m.flags = 0;
+      m.tm = __longlong_as_double(0x7ff8000000000000ll);
+      if (w < out_cap)
+        out[w] = m;
+      else if (overflow)
+        atomicOr(overflow, 4u);
+      ++w;
+    } else {
+      ++cnt;
     }
+    return true;
+  };
+  // the partners the warp's own lanes hold (site i + d is lane + d's), passed by shuffles; every
+  // lane takes part until no walk can go on inside the warp
+  uint64_t j = i + 1;
+  for (uint32_t d = 1; d < 32; ++d) {
+    const uint32_t b_record = __shfl_down_sync(0xffffffffu, a.record, d);
+    const uint32_t b_pos = __shfl_down_sync(0xffffffffu, a.pos, d);
+    const uint32_t b_pattern = __shfl_down_sync(0xffffffffu, (uint32_t)a.pattern, d);
+    if (walking && lane + d < 32) {
+      walking = j < seg_end && partner(j, b_record, b_pos, b_pattern);
+      ++j;
+    }
+    if (!__any_sync(0xffffffffu, walking && lane + d + 1 < 32)) break;
   }
-  if (!kEmit) counts[i] = cnt;
+  // past the warp's sites: from memory
+  for (; walking && j < seg_end; ++j) {
+    const ah_hit b = hits[j];
+    walking = partner(j, b.record, b.pos, b.pattern);
+  }
+  if (!kEmit && i < n) counts[i] = cnt;
 }
 
 }  // namespace

@@ -77,8 +77,9 @@ __device__ __forceinline__ void warp_bitonic(uint64_t (&v)[R], int lane, int m =
         for (int r = 0; r < R; ++r) {
           const uint64_t o = __shfl_xor_sync(0xffffffffu, v[r], j);
           const bool up = (((r << 5) | lane) & k) == 0;
-          const bool take_min = lower == up;
-          v[r] = take_min ? (o < v[r] ? o : v[r]) : (o > v[r] ? o : v[r]);
+          // keep the smaller of the two when this lane holds the lower index of an ascending pair
+          // or the upper of a descending one, else the larger: one comparison and a select
+          if ((o < v[r]) == (lower == up)) v[r] = o;
         }
       }
     }
