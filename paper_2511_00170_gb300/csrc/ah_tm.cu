@@ -1191,7 +1191,7 @@ __global__ void __launch_bounds__(kTmWindow) k_tm_hits_g(const ah_hit* __restric
 // The compressed chain's step weights are stored per thread in shared memory, only for pairs of
 // allowed choices and strided by the block size (a warp's accesses fall in different banks); the
 // parameter tables are copied to shared memory; the passes score in integers: the start pass with
-// the exact int32 score 300 dS - 1000 dH, the proving passes in 64-bit fixed point
+// the exact int32 score 280 dS - 1000 dH, the proving passes in 64-bit fixed point
 // (chain_site_tm).  Sites the chain does not cover (salt methods 6 and 7, L < 3, an entropy sum
 // that could reach zero) are enumerated by k_tm_deferred.  The kernels generated per primer set
 // (ah_tm_jit.cpp) share the driver and the kernel body and replace only the chain's passes.

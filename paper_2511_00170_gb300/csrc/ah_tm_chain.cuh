@@ -157,7 +157,9 @@ __device__ __forceinline__ uint64_t site_code(const uint2* __restrict__ planes, 
 //    guarantee it, the site is enumerated.
 //  - The sign condition: every variant's entropy sum must stay negative.  The chain's bound is tried
 //    first; the exact largest dS is found only when the bound leaves the sign open.
-//  - The start pass scores 300 dS - 1000 dH exactly in int32; each proving pass scores
+//  - The start pass scores 280 dS - 1000 dH exactly in int32 (|score| < 5e7; the proving passes
+//    reach the same optimum from any start, and one below the usual site Tm needed the fewest:
+//    on the dense-site workload 280 K ran faster than 300, 315 and 330 K); each proving pass scores
 //    lambda dS - 1000 dH in 64-bit fixed point with lambda scaled by 2^s (s = 36 below 4000 K, less
 //    beyond, so that products stay below 2^63).  A pass that finds no variant above the incumbent
 //    shows it optimal; otherwise the better variant's ratio is the next lambda.
@@ -181,7 +183,7 @@ __device__ __forceinline__ bool chain_site_tm(const TmTabs& T, int32_t* __restri
   }
   {
     int sc;
-    if (!chain.template pass<int>(T, W, ws, 300, 1000, &sc, &bp)) {
+    if (!chain.template pass<int>(T, W, ws, 280, 1000, &sc, &bp)) {
       *tm = nan;
       return true;
     }
