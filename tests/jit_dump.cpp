@@ -2,8 +2,10 @@
 // argument "gen") the pattern table of the generic scan kernel, one pattern per block:
 //   len k n_eval n_clamp width clamp_mask mset0 mset1 mset2 mset3
 //   then n_eval lines "j c0 c1 c2 c3" (coefficients as 0 / 4294967295)
-// usage: jit_dump [gen] [shift=N] k clamp primer [primer ...]   (each primer gives its + and -
-// strand patterns; shift=N sets the scan source's shift mode, 0 by default)
+// usage: jit_dump [gen] [shift=N] [windows=N] [queue=N] k clamp primer [primer ...]   (each primer
+// gives its + and - strand patterns; shift=N sets the scan source's shift mode, 0 by default;
+// windows=N the windows per warp vote its phase split is drawn for, 1024 by default; queue=1 the
+// candidate queue)
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -24,8 +26,10 @@ static uint8_t comp(uint8_t s) { return (uint8_t)(((s & 1) << 2) | ((s & 4) >> 2
 int main(int argc, char** argv) {
   const bool gen = argc > 1 && !strcmp(argv[1], "gen");
   if (gen) ++argv, --argc;
-  int shift_mode = 0;
+  int shift_mode = 0, windows = 1024, queue = 0;
   if (argc > 1 && !strncmp(argv[1], "shift=", 6)) shift_mode = atoi(argv[1] + 6), ++argv, --argc;
+  if (argc > 1 && !strncmp(argv[1], "windows=", 8)) windows = atoi(argv[1] + 8), ++argv, --argc;
+  if (argc > 1 && !strncmp(argv[1], "queue=", 6)) queue = atoi(argv[1] + 6), ++argv, --argc;
   const int k = atoi(argv[1]), clamp = atoi(argv[2]);
   std::vector<ah::Pattern> pats;
   for (int a = 3; a < argc; ++a)
@@ -52,6 +56,8 @@ int main(int argc, char** argv) {
   }
   ah::ScanConfig cfg;
   cfg.shift_mode = shift_mode;
+  cfg.vote_windows = windows;
+  cfg.emit_queue = queue;
   puts(ah::scan_source(pats, cfg).c_str());
   return 0;
 }

@@ -30,8 +30,9 @@ def dump():
         cuda_inc = "/usr/local/cuda/include"
         subprocess.check_call(["g++", "-std=c++17", "-O1", "-I", cuda_inc, src, "-o", exe, "-L", lib, "-lah",
                                f"-Wl,-rpath,{lib}"])
-    return lambda k, c, prims, gen=False, shift=0: subprocess.check_output(
-        [exe] + (["gen"] if gen else []) + [f"shift={shift}", str(k), str(c)] + prims, text=True)
+    return lambda k, c, prims, gen=False, shift=0, windows=1024, queue=0: subprocess.check_output(
+        [exe] + (["gen"] if gen else []) + [f"shift={shift}", f"windows={windows}", f"queue={queue}", str(k), str(c)]
+        + prims, text=True)
 
 
 CASES = [(2, 3, ["AGATACCKWCAACAACTGC", "CTCCTCGTATAWTMTCRACC"]), (0, 0, ["ACGTACGT"]),
@@ -40,8 +41,8 @@ CASES = [(2, 3, ["AGATACCKWCAACAACTGC", "CTCCTCGTATAWTMTCRACC"]), (0, 0, ["ACGTA
          (4, 4, ["ACGTNACGTNACGTNACGTN"]), (6, 3, ["RRRRRRRRRRYYYYYYYYYY"]), (0, 2, ["AC"]), (1, 0, ["NN"])]
 
 
-def _check(dump, k, clamp, primers, seed, n=2000, shift=0):
-    src = dump(k, clamp, primers, shift=shift)
+def _check(dump, k, clamp, primers, seed, n=2000, shift=0, windows=1024, queue=0):
+    src = dump(k, clamp, primers, shift=shift, windows=windows, queue=queue)
     rng = np.random.default_rng(seed)
     planes = [rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32) for _ in range(4)]
     _check_planes(src, k, clamp, primers, planes)
@@ -74,6 +75,40 @@ def test_generated_logic_multiply_shifts(dump, k, clamp, primers, shift):
     src = dump(k, clamp, primers, shift=shift)
     assert "mad.hi.u32" in src or "fshr(" not in src
     _check(dump, k, clamp, primers, 2, shift=shift)
+
+
+@pytest.mark.parametrize("windows", [1, 64, 4096, 1 << 20])
+@pytest.mark.parametrize("k,clamp,primers", CASES[:5] + CASES[8:10])
+def test_generated_logic_phase_splits(dump, k, clamp, primers, windows):
+    """The phase split is drawn by least expected work for a number of windows per warp vote: from
+    1 (phase one as short as it gets) to 2^20 (one phase for most patterns), the words are exact and
+    phase one never fails a matching window."""
+    _check(dump, k, clamp, primers, 3, windows=windows)
+
+
+def test_phase_split_follows_the_vote_width(dump):
+    """For the bench pair (k=3, clamp 3) the split moves positions from phase two to phase one as the
+    vote covers more windows (phase two then runs in more warps): the gates after the first vote
+    never grow, and shrink from 1 window per vote to 2^20."""
+    primers = ["AGATACCKWCAACAACTGC", "CTCCTCGTATAWTMTCRACC"]
+
+    def phase_two_gates(windows):
+        src = dump(3, 3, primers, windows=windows)
+        body = src[src.index("const u32 lo0 = a.x"):src.index("if (__builtin_expect")]
+        first_vote = body.find("__any_sync(__activemask()")
+        return 0 if first_vote < 0 else body[first_vote:].count("lop3.b32")
+
+    gates = [phase_two_gates(w) for w in (1, 64, 1024, 4096, 1 << 20)]
+    assert all(x >= y for x, y in zip(gates, gates[1:])), gates
+    assert gates[0] > gates[-1], gates
+
+
+@pytest.mark.parametrize("k,clamp,primers", CASES[:4])
+def test_generated_logic_candidate_queue(dump, k, clamp, primers):
+    """With candidates queued per warp the circuit is the same and hands its words to the queue."""
+    src = dump(k, clamp, primers, queue=1)
+    assert "push4(" in src and "drain(P, first" in src
+    _check(dump, k, clamp, primers, 4, queue=1)
 
 
 @pytest.mark.parametrize("seed", range(8))
