@@ -81,13 +81,18 @@ def alg_ops_per_base(fwd, rev, clamp):
 
 
 # DRAM bytes per base of scan kernels captured with ncu on a smaller case of the same kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum of a warm replay's scan, plain_scale's first 200
-# genomes, 756,529,120 bases, 189 MB of planes, larger than L2), scaled to a launch by its bases
-# (the traffic is one pass over the planes), keyed by what identifies the kernel: LOP3/SHF per 32
-# positions of its circuit, threads, groups per thread, shift mode, persistent.  A kernel not in
-# this table reports traffic null.
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch, larger than L2), scaled to a launch by
+# its bases (the traffic is one pass over the planes), keyed by what identifies the kernel: LOP3/SHF
+# per 32 positions of its circuit, threads, groups per thread, shift mode, persistent.  A kernel not
+# in this table reports traffic null.
 SCAN_TRAFFIC = {
-    (186, 256, 8, 0, 0): (189_561_088 + 1_595_904) / 756_529_120,
+    # the bench pair: plain_scale's first 200 genomes, 756,529,120 bases, 189 MB of planes
+    (186, 256, 8, 0, 0): ((189_561_088 + 1_595_904) / 756_529_120,
+                          "plain_scale's first 200 genomes (profiles/ah_scan_jit_alu_pipe.md)"),
+    # the batched set: its first 2,000 genomes, 3,487,157,421 bases, 872 MB of planes (the kernel the
+    # autotuner keeps, registers bounded for 4 blocks per SM)
+    (996, 128, 8, 0, 0): ((873_291_008 + 743_168) / 3_487_157_421,
+                          "the batched set's first 2,000 genomes (profiles/ah_scan_jit_alu_pipe.md)"),
 }
 
 
@@ -130,8 +135,8 @@ def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms, shape=None, sm_mhz=
     count with every phase run (an upper bound on what executes).  `shape` = (threads, groups per
     thread, shift mode, persistent) of the launch."""
     ops = ops_per_group / 32.0
-    per_base = SCAN_TRAFFIC.get((ops_per_group,) + tuple(shape)) if shape is not None else None
-    traffic = per_base * bases if per_base is not None else None
+    rec = SCAN_TRAFFIC.get((ops_per_group,) + tuple(shape)) if shape is not None else None
+    traffic = rec[0] * bases if rec is not None else None
     norm = alg_ops_per_base(fwd, rev, clamp)
     achieved = norm * bases / (ms * 1e-3) / 1e12
     circuit = ops * bases / (ms * 1e-3) / 1e12
@@ -141,8 +146,8 @@ def scan_roofline(ops_per_group, fwd, rev, clamp, bases, ms, shape=None, sm_mhz=
     return {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tlane-op/s",
             "frac": achieved / ALU_PEAK_TOPS, "traffic": traffic,
             "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel (same circuit and "
-                               "shape) on plain_scale's first 200 genomes, scaled to the bases of this launch")
-                              if traffic is not None else None,
+                               f"shape) on {rec[1]}, scaled to the bases of this launch")
+                              if rec is not None else None,
             "kernel": "ah_scan_jit (bit-sliced scan)", "kernel_ms": ms,
             "ops_per_base": norm, "ops_source": "algorithmic: sum over oriented patterns of (3 (L - c) + 2 c) / 32",
             "peak_source": "derived: 152 SMs x 64 ALU lanes/clk x 2.07 GHz",
