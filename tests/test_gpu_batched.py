@@ -31,8 +31,11 @@ def _same(a, b):
         assert np.array_equal(a.field_off, b.field_off)
 
 
-@pytest.mark.parametrize("persistent,autotune", [(0, False), (1, False), (-1, True)])
-def test_plan_matches_regular_path_and_oracle(engine, persistent, autotune):
+@pytest.mark.parametrize("persistent,autotune,queue", [(0, False, 0), (1, False, 0), (-1, True, 0), (0, False, 1),
+                                                       (1, False, 1)])
+def test_plan_matches_regular_path_and_oracle(engine, persistent, autotune, queue):
+    """The plan (one CTA per tile or persistent CTAs, candidates emitted where found or queued per
+    warp) gives the regular path's bytes and the oracle's sites, amplicons and sequences."""
     from paper_2511_00170_gb300 import ah
     from paper_2511_00170_gb300.pipeline import Params
 
@@ -41,6 +44,7 @@ def test_plan_matches_regular_path_and_oracle(engine, persistent, autotune):
     wl.trim, wl.fb_len, wl.rb_len = True, 12, 9
     p = Params.from_workload(wl)
     batch = engine.pack(wl.seq, wl.offsets)
+    ah.ah_ctx_set_scan_circuit(engine.ctx, 0, 1024, queue)
     try:
         ref = engine.step(batch, p)
         plan = engine.plan(batch, p, with_seqs=True, autotune=autotune, persistent=persistent)
@@ -53,10 +57,13 @@ def test_plan_matches_regular_path_and_oracle(engine, persistent, autotune):
             ah.ah_plan_free(plan)
     finally:
         ah.ah_batch_free(batch)
+        ah.ah_ctx_set_scan_circuit(engine.ctx, 0, 1024, 0)
     _same(out, ref)
     assert info["n_hits"] == len(ref.hits) and info["n_kept"] == len(ref.amps)
     if persistent == 1:
         assert info["persistent"] == 1
+    if not autotune:
+        assert info["emit_queue"] == queue
     orc = oracle.run(wl)
     compare.assert_same_hits(out, orc)
     compare.assert_same_amplicons(out, orc, filtered=True)
