@@ -2,10 +2,13 @@
 // argument "gen") the pattern table of the generic scan kernel, one pattern per block:
 //   len k n_eval n_clamp width clamp_mask mset0 mset1 mset2 mset3
 //   then n_eval lines "j c0 c1 c2 c3" (coefficients as 0 / 4294967295)
-// usage: jit_dump [gen] [shift=N] [windows=N] [queue=N] k clamp primer [primer ...]   (each primer
-// gives its + and - strand patterns; shift=N sets the scan source's shift mode, 0 by default;
-// windows=N the windows per warp vote its phase split is drawn for, 1024 by default; queue=1 the
-// candidate queue)
+// usage: jit_dump [gen] [compile] [shift=N] [windows=N] [queue=N] [persistent=N] [min_blocks=N]
+//                 k clamp primer [primer ...]
+// (each primer gives its + and - strand patterns; shift=N sets the scan source's shift mode, 0 by
+// default; windows=N the windows per warp vote its phase split is drawn for, 1024 by default;
+// queue=1 the candidate queue; persistent=1 the persistent form; min_blocks=N the register bound.
+// "compile" compiles the source for sm_103a with NVRTC, no device needed, and prints
+// "compiled <cubin bytes>" or the compiler's log)
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -26,10 +29,14 @@ static uint8_t comp(uint8_t s) { return (uint8_t)(((s & 1) << 2) | ((s & 4) >> 2
 int main(int argc, char** argv) {
   const bool gen = argc > 1 && !strcmp(argv[1], "gen");
   if (gen) ++argv, --argc;
-  int shift_mode = 0, windows = 1024, queue = 0;
+  const bool compile = argc > 1 && !strcmp(argv[1], "compile");
+  if (compile) ++argv, --argc;
+  int shift_mode = 0, windows = 1024, queue = 0, persistent = 0, min_blocks = 0;
   if (argc > 1 && !strncmp(argv[1], "shift=", 6)) shift_mode = atoi(argv[1] + 6), ++argv, --argc;
   if (argc > 1 && !strncmp(argv[1], "windows=", 8)) windows = atoi(argv[1] + 8), ++argv, --argc;
   if (argc > 1 && !strncmp(argv[1], "queue=", 6)) queue = atoi(argv[1] + 6), ++argv, --argc;
+  if (argc > 1 && !strncmp(argv[1], "persistent=", 11)) persistent = atoi(argv[1] + 11), ++argv, --argc;
+  if (argc > 1 && !strncmp(argv[1], "min_blocks=", 11)) min_blocks = atoi(argv[1] + 11), ++argv, --argc;
   const int k = atoi(argv[1]), clamp = atoi(argv[2]);
   std::vector<ah::Pattern> pats;
   for (int a = 3; a < argc; ++a)
@@ -58,6 +65,19 @@ int main(int argc, char** argv) {
   cfg.shift_mode = shift_mode;
   cfg.vote_windows = windows;
   cfg.emit_queue = queue;
-  puts(ah::scan_source(pats, cfg).c_str());
+  cfg.persistent = persistent;
+  cfg.min_blocks = min_blocks;
+  const std::string src = ah::scan_source(pats, cfg);
+  if (!compile) {
+    puts(src.c_str());
+    return 0;
+  }
+  std::vector<char> cubin;
+  std::string err;
+  if (ah::nvrtc_compile_sm(103, src, "ah_scan_jit.cu", &cubin, &err) != AH_OK) {
+    printf("error: %s\n", err.c_str());
+    return 1;
+  }
+  printf("compiled %zu\n", cubin.size());
   return 0;
 }

@@ -30,9 +30,13 @@ def dump():
         cuda_inc = "/usr/local/cuda/include"
         subprocess.check_call(["g++", "-std=c++17", "-O1", "-I", cuda_inc, src, "-o", exe, "-L", lib, "-lah",
                                f"-Wl,-rpath,{lib}"])
-    return lambda k, c, prims, gen=False, shift=0, windows=1024, queue=0: subprocess.check_output(
-        [exe] + (["gen"] if gen else []) + [f"shift={shift}", f"windows={windows}", f"queue={queue}", str(k), str(c)]
-        + prims, text=True)
+    def run(k, c, prims, gen=False, shift=0, windows=1024, queue=0, persistent=0, min_blocks=0, compile=False):
+        args = (["gen"] if gen else []) + (["compile"] if compile else [])
+        args += [f"shift={shift}", f"windows={windows}", f"queue={queue}", f"persistent={persistent}",
+                 f"min_blocks={min_blocks}", str(k), str(c)]
+        return subprocess.run([exe] + args + prims, text=True, capture_output=True, check=not compile).stdout
+
+    return run
 
 
 CASES = [(2, 3, ["AGATACCKWCAACAACTGC", "CTCCTCGTATAWTMTCRACC"]), (0, 0, ["ACGTACGT"]),
@@ -109,6 +113,24 @@ def test_generated_logic_candidate_queue(dump, k, clamp, primers):
     src = dump(k, clamp, primers, queue=1)
     assert "push4(" in src and "drain(P, first" in src
     _check(dump, k, clamp, primers, 4, queue=1)
+
+
+@pytest.mark.parametrize("queue", [0, 1])
+@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("shift,min_blocks", [(0, 0), (1, 4), (2, 0)])
+def test_scan_kernel_variants_compile(dump, queue, persistent, shift, min_blocks):
+    """Every form the autotuner may build compiles for sm_103a (NVRTC on the host, no device): one
+    pair and the 8-pair batched set (inlined and called emission), each shift mode, the register
+    bound, persistent CTAs, the candidate queue."""
+    one = ["AGATACCKWCAACAACTGC", "CTCCTCGTATAWTMTCRACC"]
+    eight = ["CGATANRNCGCGCCRCATMGTA", "MYGTGCTGYCACAACRCGA", "GTYAGCAAWGCACTCGMAAC", "GGCGMCGCGGGTYACRGTTGA",
+             "CNGRRTATATSARCWGTATC", "CTAACCGGTAAACACTCACGA", "AGCGCTCAGTACAGCTAT", "TGCARTGAATCCTCWGCAGCCT",
+             "GTRTGGGAGTGGTRAGTCGNTTACA", "CAGCAGTTCGGRTGCTCTGG", "CCGGCGTGTAGATCCTGTGATTA",
+             "GGGCGTKTAGTGTSTGTTGTACACT", "AGGGSMGMAAGARARCMCGA", "TTAGCACWGATTTSGAACCAG", "CACKANCRKACCRCCCACA",
+             "SGKGAATAGTTTARWTGTAG"]
+    for prims in (one, eight):
+        out = dump(2, 3, prims, shift=shift, queue=queue, persistent=persistent, min_blocks=min_blocks, compile=True)
+        assert out.startswith("compiled "), out[:2000]
 
 
 @pytest.mark.parametrize("seed", range(8))
