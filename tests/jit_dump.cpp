@@ -8,7 +8,8 @@
 // default; windows=N the windows per warp vote its phase split is drawn for, 1024 by default;
 // queue=1 the candidate queue; persistent=1 the persistent form; min_blocks=N the register bound.
 // "compile" compiles the source for sm_103a with NVRTC, no device needed, and prints
-// "compiled <cubin bytes>" or the compiler's log)
+// "compiled <cubin bytes>" or the compiler's log; "ops" prints the circuit's LOP3/SHF count per 32
+// positions with every phase run.  A primer may carry its own mismatch budget as "PRIMER:k".)
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -31,6 +32,8 @@ int main(int argc, char** argv) {
   if (gen) ++argv, --argc;
   const bool compile = argc > 1 && !strcmp(argv[1], "compile");
   if (compile) ++argv, --argc;
+  const bool ops_only = argc > 1 && !strcmp(argv[1], "ops");
+  if (ops_only) ++argv, --argc;
   int shift_mode = 0, windows = 1024, queue = 0, persistent = 0, min_blocks = 0;
   if (argc > 1 && !strncmp(argv[1], "shift=", 6)) shift_mode = atoi(argv[1] + 6), ++argv, --argc;
   if (argc > 1 && !strncmp(argv[1], "windows=", 8)) windows = atoi(argv[1] + 8), ++argv, --argc;
@@ -44,9 +47,10 @@ int main(int argc, char** argv) {
       ah::Pattern P;
       memset(&P, 0, sizeof P);
       const char* pr = argv[a];
-      const int L = (int)strlen(pr);
+      const char* colon = strchr(pr, ':');
+      const int L = colon ? (int)(colon - pr) : (int)strlen(pr);
       P.len = (uint8_t)L;
-      P.k = (uint8_t)k;
+      P.k = (uint8_t)(colon ? atoi(colon + 1) : k);
       P.id = (uint16_t)pats.size();
       for (int j = 0; j < L; ++j) P.set[j] = strand == 0 ? set_of(pr[j]) : comp(set_of(pr[L - 1 - j]));
       P.clamp_lo = (uint8_t)(strand == 0 ? L - clamp : 0);
@@ -67,7 +71,12 @@ int main(int argc, char** argv) {
   cfg.emit_queue = queue;
   cfg.persistent = persistent;
   cfg.min_blocks = min_blocks;
-  const std::string src = ah::scan_source(pats, cfg);
+  int ops = 0;
+  const std::string src = ah::scan_source(pats, cfg, &ops);
+  if (ops_only) {
+    printf("%d\n", ops);
+    return 0;
+  }
   if (!compile) {
     puts(src.c_str());
     return 0;

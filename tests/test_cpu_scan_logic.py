@@ -30,8 +30,9 @@ def dump():
         cuda_inc = "/usr/local/cuda/include"
         subprocess.check_call(["g++", "-std=c++17", "-O1", "-I", cuda_inc, src, "-o", exe, "-L", lib, "-lah",
                                f"-Wl,-rpath,{lib}"])
-    def run(k, c, prims, gen=False, shift=0, windows=1024, queue=0, persistent=0, min_blocks=0, compile=False):
-        args = (["gen"] if gen else []) + (["compile"] if compile else [])
+    def run(k, c, prims, gen=False, shift=0, windows=1024, queue=0, persistent=0, min_blocks=0, compile=False,
+            ops=False):
+        args = (["gen"] if gen else []) + (["compile"] if compile else []) + (["ops"] if ops else [])
         args += [f"shift={shift}", f"windows={windows}", f"queue={queue}", f"persistent={persistent}",
                  f"min_blocks={min_blocks}", str(k), str(c)]
         return subprocess.run([exe] + args + prims, text=True, capture_output=True, check=not compile).stdout
@@ -131,6 +132,23 @@ def test_scan_kernel_variants_compile(dump, queue, persistent, shift, min_blocks
     for prims in (one, eight):
         out = dump(2, 3, prims, shift=shift, queue=queue, persistent=persistent, min_blocks=min_blocks, compile=True)
         assert out.startswith("compiled "), out[:2000]
+
+
+def test_bench_tables_describe_the_generated_circuits(dump):
+    """bench.py keys its measured ALU-pipe and DRAM figures by circuit size.  The generator still
+    builds the circuits they were measured on: the bench pair at 1,024 windows per vote, 186
+    LOP3/SHF per 32 positions; the 8-pair batched set (k = i mod 4) at 4,096 windows (the
+    autotuner's choice), 996, and at 1,024, 1,030."""
+    import bench
+
+    plain = ["AGATACCKWCAACAACTGC", "CTCCTCGTATAWTMTCRACC"]
+    assert int(dump(3, 3, plain, ops=True)) == 186
+    wl = synth.batched(n_genomes=3)
+    batched = [f"{p}:{k}" for f, r, k in zip(wl.fwd, wl.rev, wl.k) for p in (f, r)]
+    assert int(dump(0, wl.clamp, batched, windows=4096, ops=True)) == 996
+    assert int(dump(0, wl.clamp, batched, windows=1024, ops=True)) == 1030
+    assert 186 in bench.SCAN_PIPE and (186, 256, 8, 0, 0) in bench.SCAN_TRAFFIC
+    assert (996, 4) in bench.SCAN_PIPE and (996, 128, 8, 0, 0) in bench.SCAN_TRAFFIC
 
 
 @pytest.mark.parametrize("seed", range(8))
