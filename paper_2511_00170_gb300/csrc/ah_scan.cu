@@ -1,10 +1,11 @@
 // Scan stage (Supplementary, "Primer matching and clamp logic"; "We sort candidate sites"):
 //   1. the run-time specialised bit-sliced kernel marks candidate sites and appends a 64-bit key
 //      (pair | tile-local position | orient | mismatches) to its tile's slot list;
-//   2. each tile's keys are sorted (warp bitonic sort in shared memory) and counted per pair;
+//   2. each tile's keys are sorted (a warp's bitonic network in registers, or a block's in shared
+//      memory for tiles of more than 256 keys) and counted per pair;
 //   3. an exclusive scan over the pair-major (pair, tile) counts gives every tile's output range;
-//   4. keys become ah_hit records (record lookup by binary search) in (pair, record, pos, orient)
-//      order, so pairing needs no global sort.
+//   4. keys become ah_hit records (record lookup by binary search within the tile's records) in
+//      (pair, record, pos, orient) order, so pairing needs no global sort.
 #include <algorithm>
 #include <thread>
 
